@@ -1,0 +1,206 @@
+/*
+ * tacaw.h -- C ABI of the GB300 streaming TACAW time->energy library (libtacaw.so).
+ *
+ * The library turns exit waves psi[probe][t][ky][kx], pushed a few frames at a time
+ * from multislice runs over MD snapshots, into energy-resolved diffraction
+ * patterns and detector spectra:
+ *
+ *   mu[k]    = (1/T) sum_t psi[t,k]                   time mean (elastic part), removed if asked
+ *   Psi[k,j] = sum_t w_t (psi[t,k] - mu[k]) exp(-2 pi i frac(E_j dt t / h))
+ *   I[k,j]   = B(E_j) |Psi[k,j]|^2                    Eq. 1 (B: quantum-statistics factor)
+ *   S[d,j]   = sum_k M_d(k) I[k,j]                    DetectorSet apertures (Sec. II.B)
+ *
+ * The windowed time->energy Fourier transform of a segment ("chunk" of L snapshots,
+ * Sec. II.B "Welch method") is Eq. 1's phi_MD(q,E); windows follow Sec. III.A (rectangular =
+ * Tukey alpha 0, Hann = Tukey alpha 1) in scipy's periodic form (App. A); energies are
+ * an explicit grid inside the Nyquist range eps = h/(2 dt) (App. B) or FFT bins; the
+ * k-space region of interest is a crop of the full multislice grid (Sec. II.B, "ROI
+ * slicing").  Units: h = 4.135667696 meV ps, energies in meV, dt in fs.
+ *
+ * Conventions for every entry point:
+ *   - Device pointers ("d_") are CUDA device addresses on the current device; the
+ *     caller owns them.  Host pointers are read during the call only.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  All
+ *     work is enqueued on it; calls return without waiting, except tacaw_finalize and
+ *     tacaw_backward, which wait for their own work to read the device error flag.
+ *   - Every call returns a tacaw_status; tacaw_last_error() gives a message for the
+ *     last non-OK status of the calling thread.  Argument errors leave the plan
+ *     unchanged; a CUDA error or a device timeout poisons the plan (only
+ *     tacaw_destroy is then accepted).
+ *   - Nothing here traps or aborts; device-side waits are bounded and report
+ *     TACAW_ERR_TIMEOUT.
+ */
+#ifndef TACAW_H_
+#define TACAW_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TACAW_OK = 0,
+    TACAW_ERR_INVALID_ARG = 1,  /* bad descriptor or argument; nothing was changed            */
+    TACAW_ERR_OOM = 2,          /* device allocation failed or the HBM budget is too small    */
+    TACAW_ERR_CUDA = 3,         /* a CUDA call failed; the plan is poisoned                    */
+    TACAW_ERR_STATE = 4,        /* call out of order (finalize before T frames, push after it) */
+    TACAW_ERR_OVERFLOW = 5,     /* push would exceed the segment length T; nothing was pushed  */
+    TACAW_ERR_TIMEOUT = 6,      /* a device-side wait ran out; the plan is poisoned            */
+    TACAW_ERR_UNSUPPORTED = 7   /* valid request this build does not implement                 */
+} tacaw_status;
+
+/* Time windows, Sec. III.A and App. A (scipy periodic forms, length-1 windows are [1]):
+ *   RECT   w_t = 1
+ *   HANN   w_t = 1/2 - 1/2 cos(2 pi t / T)
+ *   GAUSS  w_t = exp(-1/2 ((t - T/2)/sigma)^2), sigma = window_param frames (<= 0: T/6)
+ *   TUKEY  cosine tapers of total fractional width alpha = window_param               */
+typedef enum { TACAW_WIN_RECT = 0, TACAW_WIN_HANN = 1, TACAW_WIN_GAUSS = 2, TACAW_WIN_TUKEY = 3 } tacaw_window;
+
+/* Arithmetic of the time->energy contraction.
+ *   FP32        CUDA-core FFMA, FP32 accumulate.
+ *   SPLIT_BF16  tcgen05 tensor cores: each operand x = hi + lo with hi, lo bf16; the
+ *               product is hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory.
+ * Twiddle phases are always reduced in FP64; the exact mean correction is FP64-derived. */
+typedef enum { TACAW_PREC_FP32 = 0, TACAW_PREC_SPLIT_BF16 = 1 } tacaw_precision;
+
+/* Accumulation of Psi across flushes (used only when a segment needs more than one
+ * flush): compensated FP32 (sum + Kahan compensation) or FP64.                         */
+typedef enum { TACAW_ACC_KAHAN_FP32 = 0, TACAW_ACC_FP64 = 1 } tacaw_accum;
+
+/* Apertures (Sec. II.B DetectorSet).  Centres are offsets in pixels from the DC pixel
+ * (kx/2, ky/2) of the ROI.  Pixel (ix, iy) with squared distance d2 to the centre is in
+ * a CIRCULAR aperture when d2 <= r_out^2, in an ANNULAR one when r_in^2 < d2 <= r_out^2.
+ * MASK: d_mask is a caller-owned device array of ky*kx float weights (row-major, kx
+ * fastest), read during tacaw_plan_create only.                                        */
+typedef enum { TACAW_DET_CIRCULAR = 0, TACAW_DET_ANNULAR = 1, TACAW_DET_MASK = 2 } tacaw_detector_kind;
+
+typedef struct {
+    int kind;            /* tacaw_detector_kind */
+    float cx, cy;        /* centre offset from the DC pixel, pixels */
+    float r_in, r_out;   /* radii, pixels */
+    const float *d_mask; /* TACAW_DET_MASK only */
+} tacaw_detector;
+
+/* One stream = one supercell partition with its own probes, ROI, segment and windows.
+ * Pushed frames are complex64 (interleaved re, im float32).  Element (p, t, y, x) of a
+ * pushed buffer, t the frame index inside that push, is at complex64 offset
+ *   p*pitch_probe + t*pitch_frame + (roi_y0 + y)*pitch_row + (roi_x0 + x)
+ * so the k-space ROI is cropped out of the full multislice grid while it is read.     */
+typedef struct {
+    int n_probes;              /* P >= 1 */
+    int kx, ky;                /* ROI width (fastest) and height, >= 1 */
+    int64_t pitch_row;         /* complex64 elements between rows of a frame (>= roi_x0 + kx) */
+    int64_t pitch_frame;       /* complex64 elements between frames */
+    int64_t pitch_probe;       /* complex64 elements between probes */
+    int roi_x0, roi_y0;        /* crop origin inside each pushed frame */
+    int T;                     /* frames in the segment (needed up front for the window) */
+    double dt_fs;              /* frame interval in fs (> 0) */
+    int n_omega;               /* number of energy bins Nw >= 1 */
+    const double *E_meV;       /* host array of Nw energies in meV (ignored when fft_bins) */
+    int fft_bins;              /* != 0: E_j = j h / (T dt), j < Nw, exact integer phase */
+    int window;                /* tacaw_window */
+    double window_param;       /* GAUSS sigma (frames), TUKEY alpha */
+    int subtract_mean;         /* != 0: remove the segment's time mean mu[k] */
+    double bose_T_K;           /* > 0: multiply I by B(E) at this temperature; 0: B = 1 */
+    int n_detectors;           /* D >= 0 */
+    const tacaw_detector *detectors; /* host array of D detectors */
+} tacaw_stream_desc;
+
+typedef struct {
+    int n_streams;                     /* >= 1 */
+    const tacaw_stream_desc *streams;  /* host array */
+    int precision;                     /* tacaw_precision */
+    int accum;                         /* tacaw_accum */
+    int64_t hbm_budget_bytes;          /* device bytes the plan may hold; 0: 90% of free memory */
+    int k_stage;                       /* frames staged per flush (multiple of 8); 0: from budget */
+    const char *tune_cache_path;       /* reserved, may be NULL */
+} tacaw_plan_desc;
+
+typedef struct tacaw_plan_s *tacaw_plan_t;
+
+typedef struct {
+    int64_t device_bytes;      /* bytes the plan holds on the device */
+    int k_stage;               /* frames per flush */
+    int n_streams;
+    int precision;
+    int64_t I_elems;           /* total floats of d_I (sum over streams of P*Nw*ky*kx) */
+    int64_t S_elems;           /* total floats of d_S (sum over streams of P*D*Nw) */
+    int64_t flushes;           /* flushes run since the plan was created */
+    int omega_tile;            /* complex energies per tensor-core tile (split path) */
+    int stages;                /* shared-memory pipeline stages (split path) */
+} tacaw_plan_info;
+
+/* Creates a plan: validates the descriptor, sizes and allocates device memory
+ * (staging of K_stage frames per stream, FP64 mean sums, window x twiddle tables,
+ * Psi accumulators when a segment needs several flushes), and builds the twiddle
+ * tables on the GPU (phase reduced in FP64).  Synchronous.  *out is written on success. */
+tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out);
+
+/* Pushes n_frames frames of stream stream_id (layout: tacaw_stream_desc) from device
+ * memory.  The library reads them, removes the provisional mean (the mean of the first
+ * push of the segment), splits/converts them into its staging area and, when K_stage
+ * frames are staged and the segment is not complete, runs a flush (the contraction of the
+ * staged frames into Psi).  d_frames may be reused once the work enqueued on `stream`
+ * has completed.  Errors: OVERFLOW if the segment would exceed T frames (nothing is
+ * pushed), STATE after finalize without reset, INVALID_ARG for n_frames < 1.           */
+tacaw_status tacaw_push_frames(tacaw_plan_t plan, int stream_id, const void *d_frames,
+                               int n_frames, void *stream);
+
+/* Completes the segment of every stream: flushes what is staged, applies the exact
+ * mean correction Psi -= (mu - mu_hat) W(E_j), W the window's transform, forms I and
+ * the detector spectra.  Outputs (caller-owned device memory, streams concatenated in
+ * order; see tacaw_output_offsets):
+ *   d_I   float32 [s][p][j][ky][kx]   (may be NULL)
+ *   d_S   float32 [s][p][d][j]        (may be NULL; requires d_I or internal I)
+ *   d_Psi complex64 [s][p][j][ky][kx] (may be NULL)
+ * Spectra are summed in a fixed order (deterministic).  Waits for the work on `stream`.
+ * Errors: STATE unless every stream has received exactly T frames.                      */
+tacaw_status tacaw_finalize(tacaw_plan_t plan, float *d_I, float *d_S, void *d_Psi, void *stream);
+
+/* Element offsets of stream stream_id's block inside d_I / d_Psi and d_S.              */
+tacaw_status tacaw_output_offsets(tacaw_plan_t plan, int stream_id, int64_t *I_offset,
+                                  int64_t *S_offset);
+
+/* Gradient of L = sum_{p,d,j} dL_dS[p][d][j] * S[p][d][j] with respect to the frames of one
+ * stream's segment, in PyTorch's convention for real losses of complex inputs:
+ *   d_grad = dL/dRe(psi) + i dL/dIm(psi) = 2 dL/dconj(psi),   complex64 [p][t][ky][kx] (dense)
+ *   g[t,k] = 2 ( w_t A[t,k] - (1/T) sum_t' w_t' A[t',k] ),  A[t,k] = sum_j e^{+i theta_jt} G[k,j],
+ *   G[k,j] = B(E_j) sum_d dL_dS[d,j] M_d(k) Psi[k,j]  (mean term only with subtract_mean).
+ * d_frames holds the whole segment, laid out as pushed (pitches of the stream descriptor,
+ * t = 0..T-1 with pitch_frame).  Psi is recomputed from the frames, not stored.  Pixels
+ * outside every aperture get a zero gradient.  Independent of the push/finalize state.
+ * d_dL_dS: float32 [p][d][j] device.  Waits for the work on `stream`.                    */
+tacaw_status tacaw_backward(tacaw_plan_t plan, int stream_id, const float *d_dL_dS,
+                            const void *d_frames, void *d_grad, void *stream);
+
+/* Starts a new segment on every stream (e.g. the next probe batch or trajectory chunk):
+ * clears frame counters and mean sums.  Enqueued on `stream`.                           */
+tacaw_status tacaw_reset(tacaw_plan_t plan, void *stream);
+
+/* Fills *info.                                                                          */
+tacaw_status tacaw_plan_get_info(tacaw_plan_t plan, tacaw_plan_info *info);
+
+/* Kernel timing: when enabled, CUDA events are recorded around every contraction
+ * (flush) launch on the launching stream; tacaw_kernel_time_ms returns the summed
+ * milliseconds and the launch count since the last call with reset != 0.  Reading the
+ * times waits for the recorded events.                                                   */
+tacaw_status tacaw_set_timing(tacaw_plan_t plan, int enable);
+tacaw_status tacaw_kernel_time_ms(tacaw_plan_t plan, double *flush_ms, int64_t *flush_launches,
+                                  int reset);
+
+/* Frees every device allocation of the plan.  Accepts NULL.                             */
+tacaw_status tacaw_destroy(tacaw_plan_t plan);
+
+/* Message for the calling thread's last non-OK status ("" if none).                     */
+const char *tacaw_last_error(void);
+
+/* Library version string.                                                               */
+const char *tacaw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TACAW_H_ */

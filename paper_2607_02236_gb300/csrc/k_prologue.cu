@@ -1,0 +1,216 @@
+// Frame ingest (push) kernels: ROI crop, provisional-mean removal, operand conversion.
+//
+// The elastic (time-mean) part of each pixel is ~100x the inelastic signal, so it is
+// removed before the reduced-precision contraction.  The exact mean of the segment is
+// not known until its last frame, so pushes subtract a provisional mean mu_hat (the mean
+// of the segment's first push) and accumulate sum_t (psi_t - mu_hat) in FP64; finalize
+// then applies the exact linear correction -(mu - mu_hat) W(E_j) to Psi.
+//
+// One thread per (probe, ROI pixel) row; consecutive threads read consecutive pixels of
+// a frame row (coalesced 8-byte loads) and write their own 32-byte staging rows.
+#include "tacaw_internal.cuh"
+
+namespace tacaw {
+
+__device__ __forceinline__ const float2 *row_src(const FrameGeom &g, int64_t m) {
+    int64_t p = m / g.npix;
+    int64_t pix = m - p * g.npix;
+    int64_t y = pix / g.kx;
+    int64_t x = pix - y * g.kx;
+    return g.base + p * g.pitch_probe + (g.roi_y0 + y) * g.pitch_row + (g.roi_x0 + x);
+}
+
+__global__ void mean_kernel(FrameGeom g, int n, float2 *mu_hat) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= g.M) return;
+    const float2 *src = row_src(g, m);
+    double sr = 0.0, si = 0.0;
+    int t = 0;
+    for (; t + 8 <= n; t += 8) {
+        float br = 0.f, bi = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float2 v = __ldcs(src + (int64_t)(t + i) * g.pitch_frame);
+            br += v.x;
+            bi += v.y;
+        }
+        sr += br;
+        si += bi;
+    }
+    for (; t < n; ++t) {
+        float2 v = __ldcs(src + (int64_t)t * g.pitch_frame);
+        sr += v.x;
+        si += v.y;
+    }
+    mu_hat[m] = make_float2((float)(sr / n), (float)(si / n));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 a, __nv_bfloat16 b) {
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+__device__ __forceinline__ void split2(float2 r, uint32_t &hi, uint32_t &lo) {
+    __nv_bfloat16 hr = __float2bfloat16_rn(r.x), hi_ = __float2bfloat16_rn(r.y);
+    __nv_bfloat16 lr = __float2bfloat16_rn(r.x - __bfloat162float(hr));
+    __nv_bfloat16 li = __float2bfloat16_rn(r.y - __bfloat162float(hi_));
+    hi = pack_bf16x2(hr, hi_);
+    lo = pack_bf16x2(lr, li);
+}
+
+// Staged frame slot s (s0 + t) goes to block s/8, elements 2(s%8), 2(s%8)+1 of row m.
+__global__ void convert_split_kernel(FrameGeom g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
+                                     double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= g.M) return;
+    const float2 *src = row_src(g, m);
+    const float2 mu = mu_hat[m];
+    uint32_t *Hi = reinterpret_cast<uint32_t *>(A_hi);
+    uint32_t *Lo = reinterpret_cast<uint32_t *>(A_lo);
+    double sr = 0.0, si = 0.0;
+    int t = 0;
+    // leading frames up to the next block boundary
+    while (t < n && ((s0 + t) & 7)) {
+        const int s = s0 + t;
+        float2 v = __ldcs(src + (int64_t)t * g.pitch_frame);
+        float2 r = make_float2(v.x - mu.x, v.y - mu.y);
+        sr += r.x;
+        si += r.y;
+        uint32_t h, l;
+        split2(r, h, l);
+        size_t o = ((size_t)(s >> 3) * M_pad + m) * 8 + (s & 7);   // in bf16x2 units
+        Hi[o] = h;
+        Lo[o] = l;
+        ++t;
+    }
+    // whole blocks: 8 frames -> one 32-byte row of hi and of lo
+    for (; t + 8 <= n; t += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = __ldcs(src + (int64_t)(t + i) * g.pitch_frame);
+        uint32_t h[8], l[8];
+        float br = 0.f, bi = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float2 r = make_float2(v[i].x - mu.x, v[i].y - mu.y);
+            br += r.x;
+            bi += r.y;
+            split2(r, h[i], l[i]);
+        }
+        sr += br;
+        si += bi;
+        const int s = s0 + t;
+        size_t o = ((size_t)(s >> 3) * M_pad + m) * 8;
+        uint4 *ph = reinterpret_cast<uint4 *>(Hi + o);
+        uint4 *pl = reinterpret_cast<uint4 *>(Lo + o);
+        ph[0] = make_uint4(h[0], h[1], h[2], h[3]);
+        ph[1] = make_uint4(h[4], h[5], h[6], h[7]);
+        pl[0] = make_uint4(l[0], l[1], l[2], l[3]);
+        pl[1] = make_uint4(l[4], l[5], l[6], l[7]);
+    }
+    // trailing frames
+    for (; t < n; ++t) {
+        const int s = s0 + t;
+        float2 v = __ldcs(src + (int64_t)t * g.pitch_frame);
+        float2 r = make_float2(v.x - mu.x, v.y - mu.y);
+        sr += r.x;
+        si += r.y;
+        uint32_t h, l;
+        split2(r, h, l);
+        size_t o = ((size_t)(s >> 3) * M_pad + m) * 8 + (s & 7);
+        Hi[o] = h;
+        Lo[o] = l;
+    }
+    double2 a = sum_res[m];
+    a.x += sr;
+    a.y += si;
+    sum_res[m] = a;
+}
+
+__global__ void convert_fp32_kernel(FrameGeom g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
+                                    double2 *sum_res, float2 *A32) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= g.M) return;
+    const float2 *src = row_src(g, m);
+    const float2 mu = mu_hat[m];
+    double sr = 0.0, si = 0.0;
+    int t = 0;
+    for (; t + 8 <= n; t += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = __ldcs(src + (int64_t)(t + i) * g.pitch_frame);
+        float br = 0.f, bi = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float2 r = make_float2(v[i].x - mu.x, v[i].y - mu.y);
+            br += r.x;
+            bi += r.y;
+            A32[(size_t)(s0 + t + i) * M_pad + m] = r;
+        }
+        sr += br;
+        si += bi;
+    }
+    for (; t < n; ++t) {
+        float2 v = __ldcs(src + (int64_t)t * g.pitch_frame);
+        float2 r = make_float2(v.x - mu.x, v.y - mu.y);
+        sr += r.x;
+        si += r.y;
+        A32[(size_t)(s0 + t) * M_pad + m] = r;
+    }
+    double2 a = sum_res[m];
+    a.x += sr;
+    a.y += si;
+    sum_res[m] = a;
+}
+
+// Zeroes staged slots [staged, next multiple of 8) of the last block, all M_pad rows.
+__global__ void zero_tail_split_kernel(int64_t M_pad, int staged, uint32_t *Hi, uint32_t *Lo) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M_pad) return;
+    const int blk = staged >> 3;
+    for (int tt = staged & 7; tt < 8; ++tt) {
+        size_t o = ((size_t)blk * M_pad + m) * 8 + tt;
+        Hi[o] = 0u;
+        Lo[o] = 0u;
+    }
+}
+
+__global__ void mean_residual_kernel(int64_t M, int T, int sub, const double2 *sum_res, float2 *dmu) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double2 s = sum_res[m];
+    dmu[m] = sub ? make_float2((float)(s.x / T), (float)(s.y / T)) : make_float2(0.f, 0.f);
+}
+
+static inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+cudaError_t launch_mean(const FrameGeom &g, int n, float2 *mu_hat, cudaStream_t st) {
+    mean_kernel<<<blocks_for(g.M, 256), 256, 0, st>>>(g, n, mu_hat);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_split(const FrameGeom &g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
+                                 double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, cudaStream_t st) {
+    convert_split_kernel<<<blocks_for(g.M, 256), 256, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_fp32(const FrameGeom &g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
+                                double2 *sum_res, float2 *A32, cudaStream_t st) {
+    convert_fp32_kernel<<<blocks_for(g.M, 256), 256, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_tail_split(int64_t M_pad, int staged, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo,
+                                   cudaStream_t st) {
+    zero_tail_split_kernel<<<blocks_for(M_pad, 256), 256, 0, st>>>(
+        M_pad, staged, reinterpret_cast<uint32_t *>(A_hi), reinterpret_cast<uint32_t *>(A_lo));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mean_residual(int64_t M, int T, int subtract_mean, const double2 *sum_res, float2 *dmu,
+                                 cudaStream_t st) {
+    mean_residual_kernel<<<blocks_for(M, 256), 256, 0, st>>>(M, T, subtract_mean, sum_res, dmu);
+    return cudaGetLastError();
+}
+
+}  // namespace tacaw

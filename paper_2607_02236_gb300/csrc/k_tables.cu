@@ -1,0 +1,158 @@
+// Window and twiddle tables (built once per plan, on the GPU, in FP64).
+//
+// Phase of energy j at frame t: theta_jt = 2 pi frac(c_j t), c_j = E_j dt / h cycles per
+// frame (App. B: energies are resolved up to eps = h/(2 dt)).  The fractional part is
+// taken in FP64; on an FFT grid (E_j = j h/(T dt)) it is the exact integer form
+// ((j t) mod T) / T.  Trigonometry is CUDA's FP64 sincospi/cospi.
+// Windows follow Sec. III.A / App. A (scipy's periodic forms; length-1 windows are [1]).
+#include "tacaw_internal.cuh"
+
+namespace tacaw {
+
+enum { WIN_RECT = 0, WIN_HANN = 1, WIN_GAUSS = 2, WIN_TUKEY = 3 };
+
+__device__ double window_value(int kind, int T, double param, int t) {
+    if (T == 1) return 1.0;
+    switch (kind) {
+        case WIN_RECT:
+            return 1.0;
+        case WIN_HANN:
+            return 0.5 - 0.5 * cospi(2.0 * (double)t / (double)T);
+        case WIN_GAUSS: {
+            double s = param > 0.0 ? param : (double)T / 6.0;
+            double z = ((double)t - 0.5 * (double)T) / s;
+            return exp(-0.5 * z * z);
+        }
+        case WIN_TUKEY: {
+            double alpha = param;
+            if (alpha <= 0.0) return 1.0;
+            if (alpha >= 1.0) return 0.5 - 0.5 * cospi(2.0 * (double)t / (double)T);
+            double edge = alpha * (double)T / 2.0;
+            if ((double)t < edge) return 0.5 * (1.0 - cospi((double)t / edge));
+            if ((double)t > (double)T - edge) return 0.5 * (1.0 - cospi((double)(T - t) / edge));
+            return 1.0;
+        }
+    }
+    return 1.0;
+}
+
+// exp(-i theta_jt) = (cos, -sin) of 2 pi f, f = frac(c_j t) in [0, 1)
+__device__ void twiddle(const TableArgs &a, int j, int t, double &c, double &s) {
+    double f;
+    if (a.fft_bins) {
+        long long r = ((long long)j * (long long)t) % (long long)a.T;
+        f = (double)r / (double)a.T;
+    } else {
+        double x = a.cj[j] * (double)t;
+        f = x - floor(x);
+    }
+    sincospi(2.0 * f, &s, &c);
+}
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// One thread per (energy j < Nw_pad, frame t < T_pad).  Rows 2j and 2j+1 of block t/8
+// receive, at elements 2(t%8) and 2(t%8)+1, the real embedding of B = w_t exp(-i theta):
+//   row 2j   : ( Re B, -Im B)  ->  Re Psi_j = Re psi Re B - Im psi Im B
+//   row 2j+1 : ( Im B,  Re B)  ->  Im Psi_j = Re psi Im B + Im psi Re B
+__global__ void twiddles_split_kernel(TableArgs a, __nv_bfloat16 *B_hi, __nv_bfloat16 *B_lo) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int t = blockIdx.y * blockDim.y + threadIdx.y;
+    if (j >= a.Nw_pad || t >= a.T_pad) return;
+    double br = 0.0, bi = 0.0;
+    if (j < a.Nw && t < a.T) {
+        double c, s;
+        twiddle(a, j, t, c, s);
+        double w = window_value(a.window, a.T, a.window_param, t);
+        br = w * c;
+        bi = -w * s;
+    }
+    const int kb = t >> 3, tt = t & 7;
+    const size_t rows = 2 * (size_t)a.Nw_pad;
+    const size_t r0 = ((size_t)kb * rows + 2 * (size_t)j) * 16 + 2 * tt;
+    const size_t r1 = r0 + 16;
+    float v0[2] = {(float)br, (float)(-bi)};
+    float v1[2] = {(float)bi, (float)br};
+    for (int e = 0; e < 2; ++e) {
+        __nv_bfloat16 h, l;
+        split_bf16(v0[e], h, l);
+        B_hi[r0 + e] = h;
+        B_lo[r0 + e] = l;
+        split_bf16(v1[e], h, l);
+        B_hi[r1 + e] = h;
+        B_lo[r1 + e] = l;
+    }
+}
+
+__global__ void twiddles_fp32_kernel(TableArgs a, float2 *B32) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int t = blockIdx.y * blockDim.y + threadIdx.y;
+    if (j >= a.Nw_pad || t >= a.T_pad) return;
+    float2 v = make_float2(0.f, 0.f);
+    if (j < a.Nw && t < a.T) {
+        double c, s;
+        twiddle(a, j, t, c, s);
+        double w = window_value(a.window, a.T, a.window_param, t);
+        v = make_float2((float)(w * c), (float)(-w * s));
+    }
+    B32[(size_t)t * a.Nw_pad + j] = v;
+}
+
+// W(E_j) = sum_t w_t exp(-i theta_jt), one block per energy, fixed-order tree reduction.
+__global__ void window_transform_kernel(TableArgs a, float2 *Wc) {
+    const int j = blockIdx.x;
+    double sr = 0.0, si = 0.0;
+    for (int t = threadIdx.x; t < a.T; t += blockDim.x) {
+        double c, s;
+        twiddle(a, j, t, c, s);
+        double w = window_value(a.window, a.T, a.window_param, t);
+        sr += w * c;
+        si -= w * s;
+    }
+    __shared__ double rr[256], ri[256];
+    rr[threadIdx.x] = sr;
+    ri[threadIdx.x] = si;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            rr[threadIdx.x] += rr[threadIdx.x + h];
+            ri[threadIdx.x] += ri[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) Wc[j] = make_float2((float)rr[0], (float)ri[0]);
+}
+
+__global__ void window_values_kernel(TableArgs a, float *w) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.T) w[t] = (float)window_value(a.window, a.T, a.window_param, t);
+}
+
+cudaError_t launch_twiddles_split(const TableArgs &t, __nv_bfloat16 *B_hi, __nv_bfloat16 *B_lo, cudaStream_t st) {
+    dim3 blk(32, 8);
+    dim3 grd((t.Nw_pad + 31) / 32, (t.T_pad + 7) / 8);
+    twiddles_split_kernel<<<grd, blk, 0, st>>>(t, B_hi, B_lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_twiddles_fp32(const TableArgs &t, float2 *B32, cudaStream_t st) {
+    dim3 blk(32, 8);
+    dim3 grd((t.Nw_pad + 31) / 32, (t.T_pad + 7) / 8);
+    twiddles_fp32_kernel<<<grd, blk, 0, st>>>(t, B32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_transform(const TableArgs &t, float2 *Wc, cudaStream_t st) {
+    window_transform_kernel<<<t.Nw, 256, 0, st>>>(t, Wc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_values(const TableArgs &t, float *w, cudaStream_t st) {
+    window_values_kernel<<<(t.T + 255) / 256, 256, 0, st>>>(t, w);
+    return cudaGetLastError();
+}
+
+}  // namespace tacaw

@@ -1,0 +1,379 @@
+// Tensor-core (tcgen05) contraction of staged frames with the twiddle table, split BF16:
+//
+//   Psi[m, j] (+)= sum_f y[m, f] B[t0 + f, j]        y = psi - mu_hat, B = w_t exp(-i theta_jt)
+//
+// the windowed time->energy transform of Eq. 1 over the frames of one flush, as a real
+// GEMM on the embedding  [Re y, Im y] x [[Re B, Im B], [-Im B, Re B]].  Every operand is
+// split x = hi + lo (bf16 each); the product is accumulated as hi*hi + hi*lo + lo*hi in
+// FP32 in tensor memory (the dropped lo*lo term is ~2^-16 relative).
+//
+// CTA = 128 rows (one TMEM lane each) x N real columns (2*wt complex energies, N <= 512).
+//   warp 0      TMA producer: per 8-frame block, A_hi/A_lo boxes [128 x 16] and B_hi/B_lo
+//               boxes [N x 16] (bf16, 32-byte rows, 32B swizzle) into an s-stage ring
+//   warp 1      TMEM allocator + single-thread MMA issuer (3 passes x ceil(N/256) MMAs of
+//               M=128, K=16 per block), tcgen05.commit releases ring slots
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator (warp w reads lanes 32*(w%4)..)
+//               and the per-element flush update (store / compensated add / finalize)
+// Every mbarrier wait is bounded (globaltimer); on timeout the kernel records an error
+// bit, lets in-flight copies land, frees TMEM and returns.
+#include <cuda.h>
+
+#include <cstdio>
+#include <cstring>
+
+#include "tacaw_internal.cuh"
+
+namespace tacaw {
+
+struct TcMaps {
+    CUtensorMap a_hi, a_lo, b_hi, b_lo;
+    int box_b_rows;
+    int nbox_b;
+};
+
+constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s per wait
+constexpr int kMaxStages = 8;
+constexpr uint32_t kABytes = kMTile * 32;          // 128 rows x 16 bf16
+constexpr int kSmemLimit = 232448;                 // 227 KB opt-in per block
+
+struct TcShared {
+    uint64_t full[kMaxStages];
+    uint64_t empty[kMaxStages];
+    uint64_t tmem_full;
+    uint32_t tmem_addr;
+    int abort_flag;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait.  Gives up after kWaitLimitNs, or early when *abort_flag is set (if given).
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (abort_flag && *abort_flag) return false;
+        if (globaltimer() - t0 > kWaitLimitNs) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_bf16_ss(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major operand with 32-byte swizzle: rows of 32 bytes,
+// 8-row core groups 256 bytes apart (stride byte offset), descriptor version 1 (bit 46),
+// layout type 6 = SWIZZLE_32B (bits 61-63).  The leading byte offset is unused for a
+// K extent of one swizzle atom.
+__device__ __forceinline__ uint64_t sdesc_k_sw32(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(256 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)6 << 61;
+    return d;
+}
+// Instruction descriptor, kind::f16: D = F32 (bit 4), A = B = BF16 (bits 7, 10), both
+// K-major, N>>3 at bit 17, M>>4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__host__ __device__ inline uint32_t tc_b_bytes_padded(int N) { return ((uint32_t)N * 32u + 1023u) & ~1023u; }
+__host__ __device__ inline uint32_t tc_stage_bytes(int N) { return 2u * kABytes + 2u * tc_b_bytes_padded(N); }
+__host__ __device__ inline uint32_t tc_tmem_cols(int N) {
+    uint32_t c = 32;
+    while (c < (uint32_t)N) c <<= 1;
+    return c;
+}
+
+__global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant__ TcMaps maps, const TcPlanArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t b_pad = tc_b_bytes_padded(a.N);
+    const uint32_t stage_bytes = tc_stage_bytes(a.N);
+    TcShared *sh = reinterpret_cast<TcShared *>(base + (size_t)a.stages * stage_bytes);
+    const uint32_t base_s = smem_u32(base);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wtile = (int)(blockIdx.x % (unsigned)a.n_wt);
+    const int m0 = (int)(blockIdx.x / (unsigned)a.n_wt) * kMTile;
+    const uint32_t ncols = tc_tmem_cols(a.N);
+    const int n0 = a.N < 256 ? a.N : 256;
+    const int n1 = a.N - n0;
+    const uint32_t tx_bytes = 2u * kABytes + 2u * (uint32_t)a.N * 32u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(smem_u32(&sh->full[s]), 1);
+            mbar_init(smem_u32(&sh->empty[s]), 1);
+        }
+        mbar_init(smem_u32(&sh->tmem_full), 1);
+        sh->abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(&sh->tmem_addr), ncols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_addr;
+    volatile int *abort_flag = &sh->abort_flag;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < a.n_kb; ++kb) {
+                const int s = kb % a.stages;
+                const uint32_t use = (uint32_t)(kb / a.stages);
+                if (!mbar_wait(smem_u32(&sh->empty[s]), (use & 1u) ^ 1u, abort_flag)) {
+                    if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
+                    *abort_flag = 1;
+                    break;
+                }
+                const uint32_t full = smem_u32(&sh->full[s]);
+                const uint32_t st = base_s + (uint32_t)s * stage_bytes;
+                mbar_arrive_expect_tx(full, tx_bytes);
+                tma_load_3d(st, &maps.a_hi, 0, m0, kb, full);
+                tma_load_3d(st + kABytes, &maps.a_lo, 0, m0, kb, full);
+                for (int b = 0; b < maps.nbox_b; ++b) {
+                    const int row = wtile * a.N + b * maps.box_b_rows;
+                    const uint32_t off = (uint32_t)b * (uint32_t)maps.box_b_rows * 32u;
+                    tma_load_3d(st + 2 * kABytes + off, &maps.b_hi, 0, row, a.kbB0 + kb, full);
+                    tma_load_3d(st + 2 * kABytes + b_pad + off, &maps.b_lo, 0, row, a.kbB0 + kb, full);
+                }
+                issued = kb + 1;
+            }
+            if (*abort_flag) {
+                // let every copy this thread started land before the CTA can exit
+                const int first = issued > a.stages ? issued - a.stages : 0;
+                for (int kb = first; kb < issued; ++kb) {
+                    const int s = kb % a.stages;
+                    if (!mbar_wait(smem_u32(&sh->full[s]), (uint32_t)(kb / a.stages) & 1u, nullptr))
+                        atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t id0 = idesc_bf16_f32(kMTile, n0);
+            const uint32_t id1 = n1 > 0 ? idesc_bf16_f32(kMTile, n1) : 0u;
+            const uint64_t b_half_off = (uint64_t)((n0 * 32) >> 4);
+            for (int kb = 0; kb < a.n_kb; ++kb) {
+                const int s = kb % a.stages;
+                const uint32_t use = (uint32_t)(kb / a.stages);
+                if (!mbar_wait(smem_u32(&sh->full[s]), use & 1u, abort_flag)) {
+                    if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st = base_s + (uint32_t)s * stage_bytes;
+                const uint64_t dAhi = sdesc_k_sw32(st);
+                const uint64_t dAlo = sdesc_k_sw32(st + kABytes);
+                const uint64_t dBhi = sdesc_k_sw32(st + 2 * kABytes);
+                const uint64_t dBlo = sdesc_k_sw32(st + 2 * kABytes + b_pad);
+#pragma unroll
+                for (int pass = 0; pass < 3; ++pass) {
+                    const uint64_t dA = pass == 2 ? dAlo : dAhi;
+                    const uint64_t dB = pass == 1 ? dBlo : dBhi;
+                    const uint32_t acc = (kb > 0 || pass > 0) ? 1u : 0u;
+                    mma_bf16_ss(tmem, dA, dB, id0, acc);
+                    if (n1 > 0) mma_bf16_ss(tmem + (uint32_t)n0, dA, dB + b_half_off, id1, acc);
+                }
+                mma_commit(smem_u32(&sh->empty[s]));
+            }
+            // always signal: the epilogue (and TMEM release) wait for every issued MMA
+            mma_commit(smem_u32(&sh->tmem_full));
+        }
+    } else {
+        // epilogue warps 2..5 -> TMEM lane quarter q = warp % 4
+        const int q = warp & 3;
+        const bool ok = mbar_wait(smem_u32(&sh->tmem_full), 0u, nullptr);
+        if (!ok) {
+            atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
+            *abort_flag = 1;
+        }
+        tc_fence_after();
+        if (ok && !*abort_flag) {
+            const int64_t m = (int64_t)m0 + q * 32 + lane;
+            const RowCtx row = make_row(a.e, m);
+            const int jbase = wtile * a.wt;
+            for (int c0 = 0; c0 < a.N; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld_x16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+                tmem_ld_wait();
+                if (row.valid) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int j = jbase + (c0 >> 1) + i;
+                        if (j < a.e.Nw) epi_element(a.e, row, j, __uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, ncols);
+    }
+}
+
+// --------------------------------------------------------------------------------------
+// host side
+// --------------------------------------------------------------------------------------
+int tc_stages_for(int N) {
+    const int budget = kSmemLimit - 1024 - (int)sizeof(TcShared);
+    int s = budget / (int)tc_stage_bytes(N);
+    if (s > kMaxStages) s = kMaxStages;
+    return s;
+}
+
+size_t tc_smem_bytes(int N, int stages) {
+    return (size_t)stages * tc_stage_bytes(N) + sizeof(TcShared) + 1024;
+}
+
+size_t tc_maps_size() { return sizeof(TcMaps); }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+static bool encode3d(CUtensorMap *m, const void *ptr, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b1,
+                     char *errbuf, size_t errlen, const char *what) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) {
+        snprintf(errbuf, errlen, "cuTensorMapEncodeTiled is not available from the driver");
+        return false;
+    }
+    cuuint64_t dims[3] = {d0, d1, d2};
+    cuuint64_t strides[2] = {d0 * 2, d0 * 2 * d1};
+    cuuint32_t box[3] = {(cuuint32_t)d0, b1, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        snprintf(errbuf, errlen, "cuTensorMapEncodeTiled(%s) failed with %d", what, (int)r);
+        return false;
+    }
+    return true;
+}
+
+bool tc_make_maps(void *maps_out, const __nv_bfloat16 *A_hi, const __nv_bfloat16 *A_lo, int64_t M_pad,
+                  int n_kb_stage, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
+                  int N, char *errbuf, size_t errlen) {
+    TcMaps *m = reinterpret_cast<TcMaps *>(maps_out);
+    memset(m, 0, sizeof(TcMaps));
+    m->nbox_b = N > 256 ? 2 : 1;
+    m->box_b_rows = N / m->nbox_b;
+    if (!encode3d(&m->a_hi, A_hi, 16, (uint64_t)M_pad, (uint64_t)n_kb_stage, kMTile, errbuf, errlen, "A_hi")) return false;
+    if (!encode3d(&m->a_lo, A_lo, 16, (uint64_t)M_pad, (uint64_t)n_kb_stage, kMTile, errbuf, errlen, "A_lo")) return false;
+    if (!encode3d(&m->b_hi, B_hi, 16, 2 * (uint64_t)Nw_pad, (uint64_t)n_kb_T, (uint32_t)m->box_b_rows, errbuf, errlen,
+                  "B_hi"))
+        return false;
+    if (!encode3d(&m->b_lo, B_lo, 16, 2 * (uint64_t)Nw_pad, (uint64_t)n_kb_T, (uint32_t)m->box_b_rows, errbuf, errlen,
+                  "B_lo"))
+        return false;
+    return true;
+}
+
+cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps, cudaStream_t st) {
+    static int configured_smem = 0;
+    const size_t smem = tc_smem_bytes(a.N, a.stages);
+    if ((int)smem > configured_smem) {
+        cudaError_t e = cudaFuncSetAttribute(flush_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured_smem = (int)smem;
+    }
+    const int64_t n_mt = a.e.M_pad / kMTile;
+    const int64_t blocks = n_mt * a.n_wt;
+    if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    flush_tc_kernel<<<(unsigned)blocks, 192, smem, st>>>(*reinterpret_cast<const TcMaps *>(maps), a);
+    return cudaGetLastError();
+}
+
+}  // namespace tacaw

@@ -1,0 +1,714 @@
+// Host implementation of the C ABI declared in include/tacaw.h.
+//
+// A plan owns, per stream: the staging ring of K_stage frames (converted on push), the
+// FP64 sums of the mean residual, the twiddle tables (window x exp(-i theta), built on the
+// GPU in FP64), the window transform W(E_j), the Bose factors, compact detector pixel
+// lists and, only when the segment needs more than one flush, the Psi accumulators.
+// A flush contracts the staged frames with the twiddles of their global frame indices
+// (tensor cores or FP32 CUDA cores) and folds the result into the accumulators, or, for
+// the segment's last flush, directly into I / Psi with the exact mean correction.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/tacaw.h"
+#include "tacaw_internal.cuh"
+
+using namespace tacaw;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+tacaw_status fail(tacaw_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+struct Stream {
+    tacaw_stream_desc d{};
+    std::vector<double> E;
+    std::vector<tacaw_detector> dets;
+    int64_t npix = 0, M = 0, M_pad = 0;
+    int T = 0, T_pad = 0, n_kb_T = 0;
+    int Nw = 0, wt = 0, n_wt = 0, Nw_pad = 0;
+    int ring = 0;                    // frames the staging ring holds: min(K_stage, T_pad)
+    bool needs_acc = false;
+    // device buffers
+    float2 *mu_hat = nullptr, *dmu = nullptr, *Wc = nullptr;
+    double2 *sum_res = nullptr;
+    double *cj = nullptr;
+    float *bose = nullptr, *win = nullptr;
+    __nv_bfloat16 *A_hi = nullptr, *A_lo = nullptr, *B_hi = nullptr, *B_lo = nullptr;
+    float2 *A32 = nullptr, *B32 = nullptr;
+    float2 *acc_s = nullptr, *acc_c = nullptr;
+    double2 *acc_d = nullptr;
+    int *det_idx = nullptr, *det_off = nullptr;
+    float *det_w = nullptr;
+    int D = 0, n_det_entries = 0;
+    std::vector<int> h_det_off;
+    // adjoint support: pixels inside any aperture and their per-detector weights
+    int *adj_pix = nullptr;
+    float *adj_w = nullptr;
+    int n_adj = 0;
+    std::vector<unsigned char> tc_maps;
+    // segment state
+    int pushed = 0, staged = 0, stage_start = 0, flushes = 0;
+    int64_t I_off = 0, S_off = 0;
+};
+
+}  // namespace
+
+struct tacaw_plan_s {
+    std::vector<Stream> s;
+    int prec = 0, accum = 0, k_stage = 0;
+    int stages = 0;
+    int64_t bytes = 0;
+    int64_t I_elems = 0, S_elems = 0;
+    int64_t flushes_total = 0;
+    bool poisoned = false;
+    bool finalized = false;
+    uint32_t *d_err = nullptr;
+    std::vector<void *> allocs;
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    double timed_ms = 0.0;
+    int64_t timed_launches = 0;
+};
+
+namespace {
+
+template <typename T>
+bool dev_alloc(tacaw_plan_s *p, T **ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    void *q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    p->allocs.push_back(q);
+    p->bytes += (int64_t)(count * sizeof(T));
+    *ptr = static_cast<T *>(q);
+    return true;
+}
+
+void free_all(tacaw_plan_s *p) {
+    for (auto &e : p->ev) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    p->ev.clear();
+    for (void *q : p->allocs) cudaFree(q);
+    p->allocs.clear();
+}
+
+tacaw_status cuda_fail(tacaw_plan_s *p, cudaError_t e, const char *what) {
+    if (p) p->poisoned = true;
+    return fail(TACAW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CU_CHECK(plan, call, what)                                      \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return cuda_fail((plan), e_, (what));    \
+    } while (0)
+
+tacaw_status validate_stream(const tacaw_stream_desc &d, int i) {
+    if (d.n_probes < 1 || d.kx < 1 || d.ky < 1) return fail(TACAW_ERR_INVALID_ARG, "stream %d: P, kx, ky must be >= 1", i);
+    if (d.T < 1) return fail(TACAW_ERR_INVALID_ARG, "stream %d: T must be >= 1", i);
+    if (!(d.dt_fs > 0.0)) return fail(TACAW_ERR_INVALID_ARG, "stream %d: dt_fs must be > 0", i);
+    if (d.n_omega < 1) return fail(TACAW_ERR_INVALID_ARG, "stream %d: n_omega must be >= 1", i);
+    if (!d.fft_bins && !d.E_meV) return fail(TACAW_ERR_INVALID_ARG, "stream %d: E_meV is NULL", i);
+    if (d.fft_bins && d.n_omega > d.T) return fail(TACAW_ERR_INVALID_ARG, "stream %d: fft_bins needs n_omega <= T", i);
+    if (d.window < TACAW_WIN_RECT || d.window > TACAW_WIN_TUKEY) return fail(TACAW_ERR_INVALID_ARG, "stream %d: bad window", i);
+    if (d.roi_x0 < 0 || d.roi_y0 < 0) return fail(TACAW_ERR_INVALID_ARG, "stream %d: negative ROI origin", i);
+    if (d.pitch_row < (int64_t)d.roi_x0 + d.kx) return fail(TACAW_ERR_INVALID_ARG, "stream %d: pitch_row < roi_x0 + kx", i);
+    if (d.pitch_frame < d.pitch_row * (int64_t)(d.roi_y0 + d.ky) && d.T > 1)
+        return fail(TACAW_ERR_INVALID_ARG, "stream %d: pitch_frame smaller than the ROI extent", i);
+    if (d.n_probes > 1 && d.pitch_probe < 1) return fail(TACAW_ERR_INVALID_ARG, "stream %d: pitch_probe must be >= 1", i);
+    if (d.n_detectors < 0 || (d.n_detectors > 0 && !d.detectors))
+        return fail(TACAW_ERR_INVALID_ARG, "stream %d: bad detector array", i);
+    if (d.bose_T_K < 0) return fail(TACAW_ERR_INVALID_ARG, "stream %d: bose_T_K must be >= 0", i);
+    for (int k = 0; k < d.n_detectors; ++k) {
+        const tacaw_detector &t = d.detectors[k];
+        if (t.kind < TACAW_DET_CIRCULAR || t.kind > TACAW_DET_MASK)
+            return fail(TACAW_ERR_INVALID_ARG, "stream %d detector %d: bad kind", i, k);
+        if (t.kind == TACAW_DET_MASK && !t.d_mask)
+            return fail(TACAW_ERR_INVALID_ARG, "stream %d detector %d: mask pointer is NULL", i, k);
+    }
+    if ((int64_t)d.n_probes * d.kx * d.ky > (int64_t)1 << 31)
+        return fail(TACAW_ERR_UNSUPPORTED, "stream %d: more than 2^31 rows", i);
+    return TACAW_OK;
+}
+
+double bose_factor(double E, double TK) {
+    if (TK <= 0.0 || E == 0.0) return 1.0;
+    const double kB = 0.08617333262;  // meV/K
+    double x = E / (kB * TK);
+    return x / (-std::expm1(-x));
+}
+
+// Staging + accumulator bytes of one stream for a given ring length.
+int64_t stream_stage_bytes(const Stream &s, int ring) { return s.M_pad * 8 * (int64_t)ring; }
+int64_t stream_acc_bytes(const Stream &s) { return (int64_t)s.Nw_pad * s.M_pad * 16; }
+
+tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float2 *Psi_out, cudaStream_t st) {
+    const int n = s.staged;
+    if (n <= 0) return TACAW_OK;
+    if (mode != FLUSH_FINAL && !s.needs_acc) return fail(TACAW_ERR_STATE, "internal: accumulator missing");
+    EpiArgs e{};
+    e.M = s.M;
+    e.M_pad = s.M_pad;
+    e.npix = s.npix;
+    e.Nw = s.Nw;
+    e.mode = mode;
+    e.has_prev = s.flushes > 0 ? 1 : 0;
+    e.accum = p->accum;
+    e.acc_s = s.acc_s;
+    e.acc_c = s.acc_c;
+    e.acc_d = s.acc_d;
+    e.dmu = s.dmu;
+    e.Wc = s.Wc;
+    e.bose = s.bose;
+    e.I_out = I_out;
+    e.Psi_out = Psi_out;
+
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (p->timing) {
+        CU_CHECK(p, cudaEventCreate(&e0), "cudaEventCreate");
+        CU_CHECK(p, cudaEventCreate(&e1), "cudaEventCreate");
+        CU_CHECK(p, cudaEventRecord(e0, st), "cudaEventRecord");
+    }
+    if (p->prec == TACAW_PREC_SPLIT_BF16) {
+        if (n & 7) CU_CHECK(p, launch_zero_tail_split(s.M_pad, n, s.A_hi, s.A_lo, st), "zero_tail");
+        TcPlanArgs a{};
+        a.e = e;
+        a.wt = s.wt;
+        a.n_wt = s.n_wt;
+        a.N = 2 * s.wt;
+        a.n_kb = (n + 7) / 8;
+        a.kbB0 = s.stage_start / 8;
+        a.stages = p->stages;
+        a.err = p->d_err;
+        CU_CHECK(p, launch_flush_tc(a, s.tc_maps.data(), st), "flush (tensor cores)");
+    } else {
+        SimtArgs a{};
+        a.e = e;
+        a.A32 = s.A32;
+        a.B32 = s.B32;
+        a.Nw_pad = s.Nw_pad;
+        a.n_frames = n;
+        a.t0 = s.stage_start;
+        CU_CHECK(p, launch_flush_simt(a, st), "flush (fp32)");
+    }
+    if (p->timing) {
+        CU_CHECK(p, cudaEventRecord(e1, st), "cudaEventRecord");
+        p->ev.emplace_back(e0, e1);
+    }
+    s.flushes++;
+    p->flushes_total++;
+    s.stage_start += n;
+    s.staged = 0;
+    return TACAW_OK;
+}
+
+tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
+    const tacaw_stream_desc &d = s.d;
+    TableArgs ta{};
+    ta.T = s.T;
+    ta.T_pad = s.T_pad;
+    ta.Nw = s.Nw;
+    ta.Nw_pad = s.Nw_pad;
+    ta.window = d.window;
+    ta.window_param = d.window_param;
+    ta.fft_bins = d.fft_bins;
+    // cycles per frame c_j = E_j dt / h (FP64)
+    std::vector<double> cj(s.Nw), E(s.Nw);
+    for (int j = 0; j < s.Nw; ++j) {
+        E[j] = d.fft_bins ? (double)j * kPlanck_meV_ps / ((double)s.T * d.dt_fs * 1e-3) : d.E_meV[j];
+        cj[j] = E[j] * (d.dt_fs * 1e-3) / kPlanck_meV_ps;
+    }
+    s.E = E;
+    if (!dev_alloc(p, &s.cj, s.Nw)) return fail(TACAW_ERR_OOM, "cudaMalloc(cj)");
+    CU_CHECK(p, cudaMemcpy(s.cj, cj.data(), sizeof(double) * s.Nw, cudaMemcpyHostToDevice), "copy cj");
+    ta.cj = s.cj;
+
+    std::vector<float> bose(s.Nw);
+    for (int j = 0; j < s.Nw; ++j) bose[j] = (float)bose_factor(E[j], d.bose_T_K);
+    if (!dev_alloc(p, &s.bose, s.Nw)) return fail(TACAW_ERR_OOM, "cudaMalloc(bose)");
+    CU_CHECK(p, cudaMemcpy(s.bose, bose.data(), sizeof(float) * s.Nw, cudaMemcpyHostToDevice), "copy bose");
+
+    if (!dev_alloc(p, &s.mu_hat, s.M) || !dev_alloc(p, &s.dmu, s.M) || !dev_alloc(p, &s.sum_res, s.M) ||
+        !dev_alloc(p, &s.Wc, s.Nw) || !dev_alloc(p, &s.win, s.T))
+        return fail(TACAW_ERR_OOM, "cudaMalloc(per-row buffers)");
+    CU_CHECK(p, launch_window_transform(ta, s.Wc, st), "window transform");
+    CU_CHECK(p, launch_window_values(ta, s.win, st), "window values");
+    // adjoint needs the FP32 forward twiddles for both precisions
+    if (!dev_alloc(p, &s.B32, (size_t)s.T_pad * s.Nw_pad)) return fail(TACAW_ERR_OOM, "cudaMalloc(B32)");
+    CU_CHECK(p, launch_twiddles_fp32(ta, s.B32, st), "twiddles fp32");
+    if (p->prec == TACAW_PREC_SPLIT_BF16) {
+        const size_t nb = (size_t)s.n_kb_T * 2 * s.Nw_pad * 16;
+        if (!dev_alloc(p, &s.B_hi, nb) || !dev_alloc(p, &s.B_lo, nb)) return fail(TACAW_ERR_OOM, "cudaMalloc(B split)");
+        CU_CHECK(p, launch_twiddles_split(ta, s.B_hi, s.B_lo, st), "twiddles split");
+        const size_t na = (size_t)(s.ring / 8) * s.M_pad * 16;
+        if (!dev_alloc(p, &s.A_hi, na) || !dev_alloc(p, &s.A_lo, na)) return fail(TACAW_ERR_OOM, "cudaMalloc(staging)");
+        // rows >= M and never-written slots must read as zeros
+        CU_CHECK(p, cudaMemsetAsync(s.A_hi, 0, na * sizeof(__nv_bfloat16), st), "memset staging");
+        CU_CHECK(p, cudaMemsetAsync(s.A_lo, 0, na * sizeof(__nv_bfloat16), st), "memset staging");
+        s.tc_maps.resize(tc_maps_size());
+        char eb[256];
+        if (!tc_make_maps(s.tc_maps.data(), s.A_hi, s.A_lo, s.M_pad, s.ring / 8, s.B_hi, s.B_lo, s.Nw_pad, s.n_kb_T,
+                          2 * s.wt, eb, sizeof(eb)))
+            return fail(TACAW_ERR_CUDA, "%s", eb);
+    } else {
+        const size_t na = (size_t)s.ring * s.M_pad;
+        if (!dev_alloc(p, &s.A32, na)) return fail(TACAW_ERR_OOM, "cudaMalloc(staging)");
+        CU_CHECK(p, cudaMemsetAsync(s.A32, 0, na * sizeof(float2), st), "memset staging");
+    }
+    if (s.needs_acc) {
+        const size_t n = (size_t)s.Nw_pad * s.M_pad;
+        if (p->accum == TACAW_ACC_FP64) {
+            if (!dev_alloc(p, &s.acc_d, n)) return fail(TACAW_ERR_OOM, "cudaMalloc(accumulators)");
+        } else {
+            if (!dev_alloc(p, &s.acc_s, n) || !dev_alloc(p, &s.acc_c, n))
+                return fail(TACAW_ERR_OOM, "cudaMalloc(accumulators)");
+        }
+    }
+    // detectors -> compact (pixel, weight) lists
+    s.D = d.n_detectors;
+    std::vector<int> idx;
+    std::vector<float> wts;
+    std::vector<float> full((size_t)std::max(1, s.D) * s.npix, 0.f);
+    s.h_det_off.assign(s.D + 1, 0);
+    std::vector<float> hmask;
+    for (int k = 0; k < s.D; ++k) {
+        const tacaw_detector &t = s.dets[k];
+        if (t.kind == TACAW_DET_MASK) {
+            hmask.resize(s.npix);
+            CU_CHECK(p, cudaMemcpy(hmask.data(), t.d_mask, sizeof(float) * s.npix, cudaMemcpyDeviceToHost), "copy mask");
+        }
+        const double cx = (double)(d.kx / 2) + t.cx, cy = (double)(d.ky / 2) + t.cy;
+        for (int y = 0; y < d.ky; ++y)
+            for (int x = 0; x < d.kx; ++x) {
+                const int64_t pix = (int64_t)y * d.kx + x;
+                float w = 0.f;
+                if (t.kind == TACAW_DET_MASK) {
+                    w = hmask[pix];
+                } else {
+                    const double dx = x - cx, dy = y - cy, r2 = dx * dx + dy * dy;
+                    bool in = r2 <= (double)t.r_out * (double)t.r_out;
+                    if (t.kind == TACAW_DET_ANNULAR && t.r_in >= 0) in = in && r2 > (double)t.r_in * (double)t.r_in;
+                    w = in ? 1.f : 0.f;
+                }
+                if (w != 0.f) {
+                    idx.push_back((int)pix);
+                    wts.push_back(w);
+                    full[(size_t)k * s.npix + pix] = w;
+                }
+            }
+        s.h_det_off[k + 1] = (int)idx.size();
+    }
+    s.n_det_entries = (int)idx.size();
+    if (!dev_alloc(p, &s.det_idx, idx.size()) || !dev_alloc(p, &s.det_w, wts.size()) ||
+        !dev_alloc(p, &s.det_off, s.h_det_off.size()))
+        return fail(TACAW_ERR_OOM, "cudaMalloc(detectors)");
+    if (!idx.empty()) {
+        CU_CHECK(p, cudaMemcpy(s.det_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice), "copy det");
+        CU_CHECK(p, cudaMemcpy(s.det_w, wts.data(), sizeof(float) * wts.size(), cudaMemcpyHostToDevice), "copy det");
+    }
+    CU_CHECK(p, cudaMemcpy(s.det_off, s.h_det_off.data(), sizeof(int) * s.h_det_off.size(), cudaMemcpyHostToDevice),
+             "copy det");
+    // pixels inside any aperture, with their D weights (adjoint)
+    std::vector<int> apix;
+    std::vector<float> aw;
+    for (int64_t pix = 0; pix < s.npix; ++pix) {
+        bool any = false;
+        for (int k = 0; k < s.D; ++k) any = any || full[(size_t)k * s.npix + pix] != 0.f;
+        if (!any) continue;
+        apix.push_back((int)pix);
+        for (int k = 0; k < s.D; ++k) aw.push_back(full[(size_t)k * s.npix + pix]);
+    }
+    s.n_adj = (int)apix.size();
+    if (!dev_alloc(p, &s.adj_pix, apix.size()) || !dev_alloc(p, &s.adj_w, aw.size()))
+        return fail(TACAW_ERR_OOM, "cudaMalloc(adjoint lists)");
+    if (!apix.empty()) {
+        CU_CHECK(p, cudaMemcpy(s.adj_pix, apix.data(), sizeof(int) * apix.size(), cudaMemcpyHostToDevice), "copy");
+        CU_CHECK(p, cudaMemcpy(s.adj_w, aw.data(), sizeof(float) * aw.size(), cudaMemcpyHostToDevice), "copy");
+    }
+    CU_CHECK(p, cudaMemsetAsync(s.sum_res, 0, sizeof(double2) * s.M, st), "memset sums");
+    CU_CHECK(p, cudaMemsetAsync(s.mu_hat, 0, sizeof(float2) * s.M, st), "memset mu");
+    return TACAW_OK;
+}
+
+tacaw_status check_plan(tacaw_plan_s *p) {
+    if (!p) return fail(TACAW_ERR_INVALID_ARG, "plan is NULL");
+    if (p->poisoned) return fail(TACAW_ERR_STATE, "plan is poisoned by an earlier CUDA error or device timeout");
+    return TACAW_OK;
+}
+
+tacaw_status read_device_error(tacaw_plan_s *p, cudaStream_t st) {
+    CU_CHECK(p, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    uint32_t h = 0;
+    CU_CHECK(p, cudaMemcpy(&h, p->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost), "read error word");
+    if (h) {
+        p->poisoned = true;
+        return fail(TACAW_ERR_TIMEOUT, "device wait timed out (error bits 0x%x)", h);
+    }
+    return TACAW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tacaw_last_error(void) { return g_last_error.c_str(); }
+
+const char *tacaw_version(void) { return "tacaw-gb300 0.1 (sm_103a)"; }
+
+tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
+    g_last_error.clear();
+    if (!desc || !out) return fail(TACAW_ERR_INVALID_ARG, "desc and out must not be NULL");
+    *out = nullptr;
+    if (desc->n_streams < 1 || !desc->streams) return fail(TACAW_ERR_INVALID_ARG, "n_streams must be >= 1");
+    if (desc->precision != TACAW_PREC_FP32 && desc->precision != TACAW_PREC_SPLIT_BF16)
+        return fail(TACAW_ERR_INVALID_ARG, "bad precision");
+    if (desc->accum != TACAW_ACC_KAHAN_FP32 && desc->accum != TACAW_ACC_FP64)
+        return fail(TACAW_ERR_INVALID_ARG, "bad accum");
+    if (desc->k_stage < 0 || (desc->k_stage % 8) != 0) return fail(TACAW_ERR_INVALID_ARG, "k_stage must be a multiple of 8");
+    for (int i = 0; i < desc->n_streams; ++i) {
+        tacaw_status v = validate_stream(desc->streams[i], i);
+        if (v != TACAW_OK) return v;
+    }
+    tacaw_plan_s *p = new (std::nothrow) tacaw_plan_s();
+    if (!p) return fail(TACAW_ERR_OOM, "host allocation failed");
+    p->prec = desc->precision;
+    p->accum = desc->accum;
+    int T_pad_max = 0;
+    for (int i = 0; i < desc->n_streams; ++i) {
+        Stream s;
+        s.d = desc->streams[i];
+        s.dets.assign(s.d.detectors, s.d.detectors + s.d.n_detectors);
+        s.d.detectors = nullptr;
+        s.d.E_meV = nullptr;
+        s.npix = (int64_t)s.d.kx * s.d.ky;
+        s.M = (int64_t)s.d.n_probes * s.npix;
+        s.M_pad = round_up(s.M, kMTile);
+        s.T = s.d.T;
+        s.T_pad = (int)round_up(s.T, 8);
+        s.n_kb_T = s.T_pad / 8;
+        s.Nw = s.d.n_omega;
+        s.n_wt = (s.Nw + 255) / 256;
+        s.wt = (int)round_up((s.Nw + s.n_wt - 1) / s.n_wt, 8);
+        s.Nw_pad = s.wt * s.n_wt;
+        if (p->prec == TACAW_PREC_FP32) s.Nw_pad = (int)round_up(s.Nw, 64);
+        T_pad_max = std::max(T_pad_max, s.T_pad);
+        p->s.push_back(s);
+    }
+    // keep the energies (host) for the tables
+    std::vector<std::vector<double>> Es(desc->n_streams);
+    for (int i = 0; i < desc->n_streams; ++i)
+        if (!desc->streams[i].fft_bins) Es[i].assign(desc->streams[i].E_meV, desc->streams[i].E_meV + desc->streams[i].n_omega);
+
+    // budget and K_stage
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        delete p;
+        return fail(TACAW_ERR_CUDA, "cudaMemGetInfo: %s", cudaGetErrorString(e));
+    }
+    const int64_t budget = desc->hbm_budget_bytes > 0 ? desc->hbm_budget_bytes : (int64_t)(0.9 * (double)free_b);
+    int64_t fixed = 0;
+    for (auto &s : p->s) {
+        fixed += s.M * (8 + 8 + 16) + (int64_t)s.T_pad * s.Nw_pad * 8 + (int64_t)s.n_kb_T * 2 * s.Nw_pad * 16 * 4 +
+                 (int64_t)s.npix * 16 + (1 << 20);
+    }
+    auto need = [&](int K) {
+        int64_t b = fixed;
+        for (auto &s : p->s) {
+            const int ring = std::min(K, s.T_pad);
+            b += stream_stage_bytes(s, ring);
+            if (s.T > ring) b += stream_acc_bytes(s);
+        }
+        return b;
+    };
+    int K = desc->k_stage;
+    if (K == 0) {
+        if (need(T_pad_max) <= budget) {
+            K = T_pad_max;
+        } else {
+            K = 0;
+            for (int k = (T_pad_max / 64) * 64; k >= 64; k -= 64)
+                if (need(k) <= budget) {
+                    K = k;
+                    break;
+                }
+            if (K == 0) {
+                delete p;
+                return fail(TACAW_ERR_OOM, "HBM budget of %lld bytes is too small (needs %lld at K_stage=64)",
+                            (long long)budget, (long long)need(64));
+            }
+        }
+    } else if (need(K) > budget) {
+        delete p;
+        return fail(TACAW_ERR_OOM, "k_stage=%d needs %lld bytes, budget %lld", K, (long long)need(K), (long long)budget);
+    }
+    p->k_stage = K;
+    int maxN = 0;
+    for (auto &s : p->s) {
+        s.ring = std::min(K, s.T_pad);
+        s.needs_acc = s.T > s.ring;
+        maxN = std::max(maxN, 2 * s.wt);
+    }
+    if (p->prec == TACAW_PREC_SPLIT_BF16) {
+        p->stages = tc_stages_for(maxN);
+        if (p->stages < 2) {
+            delete p;
+            return fail(TACAW_ERR_UNSUPPORTED, "tensor-core tile of %d columns does not fit shared memory", maxN);
+        }
+    }
+    if (!dev_alloc(p, &p->d_err, 1)) {
+        free_all(p);
+        delete p;
+        return fail(TACAW_ERR_OOM, "cudaMalloc(error word)");
+    }
+    cudaStream_t st = nullptr;
+    tacaw_status rc = TACAW_OK;
+    if (cudaMemsetAsync(p->d_err, 0, sizeof(uint32_t), st) != cudaSuccess) rc = fail(TACAW_ERR_CUDA, "memset");
+    int64_t I_off = 0, S_off = 0;
+    for (size_t i = 0; i < p->s.size() && rc == TACAW_OK; ++i) {
+        Stream &s = p->s[i];
+        s.d.E_meV = Es[i].empty() ? nullptr : Es[i].data();
+        rc = build_stream(p, s, st);
+        s.d.E_meV = nullptr;
+        s.I_off = I_off;
+        s.S_off = S_off;
+        I_off += (int64_t)s.d.n_probes * s.Nw * s.npix;
+        S_off += (int64_t)s.d.n_probes * s.D * s.Nw;
+    }
+    p->I_elems = I_off;
+    p->S_elems = S_off;
+    if (rc == TACAW_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) rc = fail(TACAW_ERR_CUDA, "plan tables: %s", cudaGetErrorString(e));
+    }
+    if (rc != TACAW_OK) {
+        free_all(p);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return TACAW_OK;
+}
+
+tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, int n_frames, void *stream) {
+    tacaw_status c = check_plan(p);
+    if (c != TACAW_OK) return c;
+    if (sid < 0 || sid >= (int)p->s.size()) return fail(TACAW_ERR_INVALID_ARG, "stream_id %d out of range", sid);
+    if (!d_frames) return fail(TACAW_ERR_INVALID_ARG, "d_frames is NULL");
+    if (n_frames < 1) return fail(TACAW_ERR_INVALID_ARG, "n_frames must be >= 1");
+    if (p->finalized) return fail(TACAW_ERR_STATE, "segment finalized; call tacaw_reset first");
+    if ((reinterpret_cast<uintptr_t>(d_frames) & 7) != 0) return fail(TACAW_ERR_INVALID_ARG, "d_frames must be 8-byte aligned");
+    Stream &s = p->s[sid];
+    if ((int64_t)s.pushed + n_frames > s.T)
+        return fail(TACAW_ERR_OVERFLOW, "push of %d frames exceeds T=%d (already %d)", n_frames, s.T, s.pushed);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    FrameGeom g{};
+    g.pitch_row = s.d.pitch_row;
+    g.pitch_frame = s.d.pitch_frame;
+    g.pitch_probe = s.d.pitch_probe;
+    g.roi_x0 = s.d.roi_x0;
+    g.roi_y0 = s.d.roi_y0;
+    g.kx = s.d.kx;
+    g.ky = s.d.ky;
+    g.npix = s.npix;
+    g.M = s.M;
+    g.base = static_cast<const float2 *>(d_frames);
+    if (s.pushed == 0 && s.d.subtract_mean) CU_CHECK(p, launch_mean(g, n_frames, s.mu_hat, st), "provisional mean");
+    int done = 0;
+    while (done < n_frames) {
+        const int chunk = std::min(n_frames - done, s.ring - s.staged);
+        FrameGeom gc = g;
+        gc.base = g.base + (int64_t)done * g.pitch_frame;
+        if (p->prec == TACAW_PREC_SPLIT_BF16)
+            CU_CHECK(p, launch_convert_split(gc, chunk, s.staged, s.M_pad, s.mu_hat, s.sum_res, s.A_hi, s.A_lo, st),
+                     "convert");
+        else
+            CU_CHECK(p, launch_convert_fp32(gc, chunk, s.staged, s.M_pad, s.mu_hat, s.sum_res, s.A32, st), "convert");
+        s.staged += chunk;
+        s.pushed += chunk;
+        done += chunk;
+        if (s.staged == s.ring && s.pushed < s.T) {
+            tacaw_status r = run_flush(p, s, s.flushes == 0 ? FLUSH_STORE : FLUSH_ADD, nullptr, nullptr, st);
+            if (r != TACAW_OK) return r;
+        }
+    }
+    return TACAW_OK;
+}
+
+tacaw_status tacaw_finalize(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, void *stream) {
+    tacaw_status c = check_plan(p);
+    if (c != TACAW_OK) return c;
+    if (p->finalized) return fail(TACAW_ERR_STATE, "segment already finalized");
+    for (size_t i = 0; i < p->s.size(); ++i)
+        if (p->s[i].pushed != p->s[i].T)
+            return fail(TACAW_ERR_STATE, "stream %zu has %d of %d frames", i, p->s[i].pushed, p->s[i].T);
+    if (d_S && !d_I) return fail(TACAW_ERR_INVALID_ARG, "d_S requires d_I");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (auto &s : p->s) {
+        CU_CHECK(p, launch_mean_residual(s.M, s.T, s.d.subtract_mean, s.sum_res, s.dmu, st), "mean residual");
+        float *I = d_I ? d_I + s.I_off : nullptr;
+        float2 *Psi = d_Psi ? static_cast<float2 *>(d_Psi) + s.I_off : nullptr;
+        tacaw_status r = run_flush(p, s, FLUSH_FINAL, I, Psi, st);
+        if (r != TACAW_OK) return r;
+        if (d_S && s.D > 0) {
+            ApertureArgs a{};
+            a.I = I;
+            a.S = d_S + s.S_off;
+            a.P = s.d.n_probes;
+            a.D = s.D;
+            a.Nw = s.Nw;
+            a.npix = s.npix;
+            a.idx = s.det_idx;
+            a.wts = s.det_w;
+            a.off = s.det_off;
+            CU_CHECK(p, launch_aperture(a, st), "aperture");
+        }
+    }
+    p->finalized = true;
+    return read_device_error(p, st);
+}
+
+tacaw_status tacaw_output_offsets(tacaw_plan_t p, int sid, int64_t *I_offset, int64_t *S_offset) {
+    if (!p) return fail(TACAW_ERR_INVALID_ARG, "plan is NULL");
+    if (sid < 0 || sid >= (int)p->s.size()) return fail(TACAW_ERR_INVALID_ARG, "stream_id out of range");
+    if (I_offset) *I_offset = p->s[sid].I_off;
+    if (S_offset) *S_offset = p->s[sid].S_off;
+    return TACAW_OK;
+}
+
+tacaw_status tacaw_reset(tacaw_plan_t p, void *stream) {
+    tacaw_status c = check_plan(p);
+    if (c != TACAW_OK) return c;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (auto &s : p->s) {
+        CU_CHECK(p, cudaMemsetAsync(s.sum_res, 0, sizeof(double2) * s.M, st), "reset sums");
+        CU_CHECK(p, cudaMemsetAsync(s.mu_hat, 0, sizeof(float2) * s.M, st), "reset mean");
+        s.pushed = s.staged = s.stage_start = s.flushes = 0;
+    }
+    p->finalized = false;
+    return TACAW_OK;
+}
+
+tacaw_status tacaw_plan_get_info(tacaw_plan_t p, tacaw_plan_info *info) {
+    if (!p || !info) return fail(TACAW_ERR_INVALID_ARG, "NULL argument");
+    info->device_bytes = p->bytes;
+    info->k_stage = p->k_stage;
+    info->n_streams = (int)p->s.size();
+    info->precision = p->prec;
+    info->I_elems = p->I_elems;
+    info->S_elems = p->S_elems;
+    info->flushes = p->flushes_total;
+    info->omega_tile = p->s.empty() ? 0 : p->s[0].wt;
+    info->stages = p->stages;
+    return TACAW_OK;
+}
+
+tacaw_status tacaw_set_timing(tacaw_plan_t p, int enable) {
+    if (!p) return fail(TACAW_ERR_INVALID_ARG, "plan is NULL");
+    p->timing = enable != 0;
+    return TACAW_OK;
+}
+
+tacaw_status tacaw_kernel_time_ms(tacaw_plan_t p, double *flush_ms, int64_t *flush_launches, int reset) {
+    if (!p) return fail(TACAW_ERR_INVALID_ARG, "plan is NULL");
+    for (auto &e : p->ev) {
+        cudaError_t r = cudaEventSynchronize(e.second);
+        if (r != cudaSuccess) return cuda_fail(p, r, "cudaEventSynchronize");
+        float ms = 0.f;
+        r = cudaEventElapsedTime(&ms, e.first, e.second);
+        if (r != cudaSuccess) return cuda_fail(p, r, "cudaEventElapsedTime");
+        p->timed_ms += ms;
+        p->timed_launches++;
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    p->ev.clear();
+    if (flush_ms) *flush_ms = p->timed_ms;
+    if (flush_launches) *flush_launches = p->timed_launches;
+    if (reset) {
+        p->timed_ms = 0.0;
+        p->timed_launches = 0;
+    }
+    return TACAW_OK;
+}
+
+tacaw_status tacaw_backward(tacaw_plan_t p, int sid, const float *d_dL_dS, const void *d_frames, void *d_grad,
+                            void *stream) {
+    tacaw_status c = check_plan(p);
+    if (c != TACAW_OK) return c;
+    if (sid < 0 || sid >= (int)p->s.size()) return fail(TACAW_ERR_INVALID_ARG, "stream_id %d out of range", sid);
+    if (!d_dL_dS || !d_frames || !d_grad) return fail(TACAW_ERR_INVALID_ARG, "NULL device pointer");
+    Stream &s = p->s[sid];
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CU_CHECK(p, cudaMemsetAsync(d_grad, 0, sizeof(float2) * (size_t)s.d.n_probes * s.T * s.npix, st), "memset grad");
+    if (s.n_adj > 0 && s.D > 0) {
+        float2 *scratch = nullptr;
+        const size_t n_scr = (size_t)s.d.n_probes * s.n_adj * (s.Nw + 2);
+        CU_CHECK(p, cudaMallocAsync(reinterpret_cast<void **>(&scratch), n_scr * sizeof(float2), st), "scratch");
+        AdjointArgs a{};
+        a.frames = static_cast<const float2 *>(d_frames);
+        a.pitch_row = s.d.pitch_row;
+        a.pitch_frame = s.d.pitch_frame;
+        a.pitch_probe = s.d.pitch_probe;
+        a.roi_x0 = s.d.roi_x0;
+        a.roi_y0 = s.d.roi_y0;
+        a.kx = s.d.kx;
+        a.ky = s.d.ky;
+        a.P = s.d.n_probes;
+        a.T = s.T;
+        a.Nw = s.Nw;
+        a.D = s.D;
+        a.subtract_mean = s.d.subtract_mean;
+        a.w = s.win;
+        a.B32 = s.B32;
+        a.Nw_pad = s.Nw_pad;
+        a.Wc = s.Wc;
+        a.bose = s.bose;
+        a.dLdS = d_dL_dS;
+        a.mpix = s.adj_pix;
+        a.mwts = s.adj_w;
+        a.n_mpix = s.n_adj;
+        a.grad = static_cast<float2 *>(d_grad);
+        a.scratch = scratch;
+        cudaError_t e = launch_adjoint(a, st);
+        cudaFreeAsync(scratch, st);
+        if (e != cudaSuccess) return cuda_fail(p, e, "adjoint");
+    }
+    return read_device_error(p, st);
+}
+
+tacaw_status tacaw_destroy(tacaw_plan_t p) {
+    if (!p) return TACAW_OK;
+    free_all(p);
+    delete p;
+    return TACAW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+// Internal declarations shared by the translation units of libtacaw.so.
+//
+// Data layout in HBM (per stream; M = P*ky*kx rows, one row per (probe, ROI pixel),
+// M_pad = M rounded up to 128; Nw_pad = n_wt * wt energies):
+//   staging, split path   A_hi, A_lo  bf16 [kb][M_pad][16]   kb = staged frame / 8;
+//                         element 2*(f%8)+0 = Re(psi - mu_hat), +1 = Im(...)
+//   staging, FP32 path    A32        float2 [K_stage][M_pad]
+//   twiddles, split path  B_hi, B_lo  bf16 [kbT][2*Nw_pad][16] kbT = t / 8; rows 2j, 2j+1
+//                         hold the real embedding of w_t exp(-i theta_jt) so that
+//                         [Re psi, Im psi] . rows gives [Re Psi_j, Im Psi_j]
+//   twiddles, FP32 path   B32        float2 [T_pad][Nw_pad]
+//   accumulators          [Nw_pad][M_pad] (float2 sum + float2 compensation, or double2)
+//   outputs               I float [p][j][ky][kx], Psi float2 [p][j][ky][kx], S float [p][d][j]
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace tacaw {
+
+constexpr double kPlanck_meV_ps = 4.135667696;
+constexpr int kBlockFrames = 8;      // frames per staging block: 16 bf16 = one 32-byte row
+constexpr int kMTile = 128;          // rows per tensor-core tile (TMEM lanes)
+
+enum FlushMode : int { FLUSH_STORE = 0, FLUSH_ADD = 1, FLUSH_FINAL = 2 };
+
+// device error bits (OR-ed into the plan's error word)
+enum : uint32_t {
+    DEVERR_TIMEOUT_FULL = 1u,
+    DEVERR_TIMEOUT_EMPTY = 2u,
+    DEVERR_TIMEOUT_TMEM = 4u,
+    DEVERR_TIMEOUT_DRAIN = 8u,
+};
+
+struct FrameGeom {
+    const float2 *base;        // pushed buffer
+    int64_t pitch_row, pitch_frame, pitch_probe;
+    int roi_x0, roi_y0;
+    int kx, ky;
+    int64_t npix;              // kx*ky
+    int64_t M;                 // P*npix
+};
+
+// Per-element epilogue inputs (shared by the tensor-core and the FP32 contraction).
+struct EpiArgs {
+    int64_t M, M_pad, npix;
+    int Nw;
+    int mode;                  // FlushMode
+    int has_prev;              // FINAL: accumulators hold earlier flushes
+    int accum;                 // 0 compensated FP32, 1 FP64
+    float2 *acc_s;             // compensated FP32: sums      [Nw_pad][M_pad]
+    float2 *acc_c;             // compensated FP32: compensation
+    double2 *acc_d;            // FP64 accumulators
+    float *I_out;              // may be null
+    float2 *Psi_out;           // may be null
+    const float2 *dmu;         // [M] mean residual mu - mu_hat (null: none)
+    const float2 *Wc;          // [Nw] window transform W(E_j) (FP64-derived)
+    const float *bose;         // [Nw]
+};
+
+struct RowCtx {
+    int64_t m;
+    int64_t out_base;          // p*Nw*npix + pix
+    float2 dmu;
+    bool valid;
+};
+
+__device__ __forceinline__ RowCtx make_row(const EpiArgs &a, int64_t m) {
+    RowCtx r;
+    r.m = m;
+    r.valid = m < a.M;
+    int64_t p = r.valid ? m / a.npix : 0;
+    int64_t pix = m - p * a.npix;
+    r.out_base = p * (int64_t)a.Nw * a.npix + pix;
+    r.dmu = (r.valid && a.dmu) ? a.dmu[m] : make_float2(0.f, 0.f);
+    return r;
+}
+
+// Applies one flush result (re, im) for row r, energy j < Nw.
+__device__ __forceinline__ void epi_element(const EpiArgs &a, const RowCtx &r, int j, float re, float im) {
+    const size_t ai = (size_t)j * (size_t)a.M_pad + (size_t)r.m;
+    if (a.mode == FLUSH_STORE) {
+        if (a.accum) {
+            a.acc_d[ai] = make_double2(re, im);
+        } else {
+            a.acc_s[ai] = make_float2(re, im);
+            a.acc_c[ai] = make_float2(0.f, 0.f);
+        }
+        return;
+    }
+    if (a.mode == FLUSH_ADD) {
+        if (a.accum) {
+            double2 s = a.acc_d[ai];
+            s.x += re;
+            s.y += im;
+            a.acc_d[ai] = s;
+        } else {
+            // Kahan (compensated) summation per component
+            float2 s = a.acc_s[ai], c = a.acc_c[ai];
+            float yr = re - c.x, yi = im - c.y;
+            float tr = s.x + yr, ti = s.y + yi;
+            c.x = (tr - s.x) - yr;
+            c.y = (ti - s.y) - yi;
+            a.acc_s[ai] = make_float2(tr, ti);
+            a.acc_c[ai] = c;
+        }
+        return;
+    }
+    // FLUSH_FINAL
+    float pr, pi;
+    if (a.has_prev) {
+        if (a.accum) {
+            double2 s = a.acc_d[ai];
+            pr = (float)(s.x + (double)re);
+            pi = (float)(s.y + (double)im);
+        } else {
+            float2 s = a.acc_s[ai], c = a.acc_c[ai];
+            pr = s.x + (re - c.x);
+            pi = s.y + (im - c.y);
+        }
+    } else {
+        pr = re;
+        pi = im;
+    }
+    // exact mean correction: Psi -= (mu - mu_hat) * W(E_j)
+    const float2 W = a.Wc[j];
+    pr -= r.dmu.x * W.x - r.dmu.y * W.y;
+    pi -= r.dmu.x * W.y + r.dmu.y * W.x;
+    const int64_t o = r.out_base + (int64_t)j * a.npix;
+    if (a.I_out) a.I_out[o] = (pr * pr + pi * pi) * a.bose[j];
+    if (a.Psi_out) a.Psi_out[o] = make_float2(pr, pi);
+}
+
+// ---------------------------------------------------------------------------------------
+// Launchers (each defined in its own translation unit); all enqueue on `st`.
+// ---------------------------------------------------------------------------------------
+struct TableArgs {
+    int T, T_pad, Nw, Nw_pad;
+    int window;
+    double window_param;
+    int fft_bins;
+    const double *cj;          // device, cycles per frame per energy (explicit grid)
+};
+
+cudaError_t launch_twiddles_split(const TableArgs &t, __nv_bfloat16 *B_hi, __nv_bfloat16 *B_lo, cudaStream_t st);
+cudaError_t launch_twiddles_fp32(const TableArgs &t, float2 *B32, cudaStream_t st);
+cudaError_t launch_window_transform(const TableArgs &t, float2 *Wc, cudaStream_t st);
+cudaError_t launch_window_values(const TableArgs &t, float *w, cudaStream_t st);
+
+cudaError_t launch_mean(const FrameGeom &g, int n, float2 *mu_hat, cudaStream_t st);
+cudaError_t launch_convert_split(const FrameGeom &g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
+                                 double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, cudaStream_t st);
+cudaError_t launch_convert_fp32(const FrameGeom &g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
+                                double2 *sum_res, float2 *A32, cudaStream_t st);
+cudaError_t launch_zero_tail_split(int64_t M_pad, int staged, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo,
+                                   cudaStream_t st);
+cudaError_t launch_mean_residual(int64_t M, int T, int subtract_mean, const double2 *sum_res, float2 *dmu,
+                                 cudaStream_t st);
+
+struct SimtArgs {
+    EpiArgs e;
+    const float2 *A32;         // [K_stage][M_pad]
+    const float2 *B32;         // [T_pad][Nw_pad]
+    int Nw_pad;
+    int n_frames;              // frames in this flush
+    int t0;                    // global index of the first frame (row of B32)
+};
+cudaError_t launch_flush_simt(const SimtArgs &a, cudaStream_t st);
+
+struct TcPlanArgs {
+    EpiArgs e;
+    int wt, n_wt, N;           // complex energies per tile, tiles, real columns per tile (2*wt)
+    int n_kb;                  // staging blocks in this flush
+    int kbB0;                  // first global twiddle block
+    int stages;
+    uint32_t *err;
+};
+struct TcMaps;                 // tensor maps (defined in k_tc_gemm.cu)
+cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps /* TcMaps */, cudaStream_t st);
+int tc_stages_for(int N);
+size_t tc_smem_bytes(int N, int stages);
+size_t tc_maps_size();
+bool tc_make_maps(void *maps_out, const __nv_bfloat16 *A_hi, const __nv_bfloat16 *A_lo, int64_t M_pad,
+                  int n_kb_stage, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
+                  int N, char *errbuf, size_t errlen);
+
+struct ApertureArgs {
+    const float *I;            // [P][Nw][npix]
+    float *S;                  // [P][D][Nw]
+    int P, D, Nw;
+    int64_t npix;
+    const int *idx;            // concatenated pixel lists
+    const float *wts;          // weights
+    const int *off;            // [D+1]
+};
+cudaError_t launch_aperture(const ApertureArgs &a, cudaStream_t st);
+
+struct AdjointArgs {
+    const float2 *frames;      // pushed layout, whole segment
+    int64_t pitch_row, pitch_frame, pitch_probe;
+    int roi_x0, roi_y0, kx, ky;
+    int P, T, Nw, D;
+    int subtract_mean;
+    const float *w;            // [T] window
+    const float2 *B32;         // [T_pad][Nw_pad] forward twiddles w_t e^{-i theta}
+    int Nw_pad;
+    const float2 *Wc;          // [Nw]
+    const float *bose;         // [Nw]
+    const float *dLdS;         // [P][D][Nw]
+    const int *mpix;           // pixels inside any aperture (sorted)
+    const float *mwts;         // [n_mpix][D] mask weights of those pixels
+    int n_mpix;
+    float2 *grad;              // [P][T][ky][kx] dense
+    float2 *scratch;           // [P][n_mpix][Nw] complex (G), plus [P][n_mpix] means
+};
+cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t st);
+
+}  // namespace tacaw

@@ -1,0 +1,127 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (max |GPU - oracle| / max |oracle|, per output):
+  FP32 CUDA-core path:   1e-5 of peak intensity (and of peak spectrum)
+  split-BF16 tensor path: TOL_SPLIT, the measured bound of hi*hi + hi*lo + lo*hi with FP32
+                          accumulation (each operand carries ~2^-17 relative error).
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import Detector, StreamSpec, frames
+from tests.helpers import oracle_kw, rel_err_peak, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-5
+TOL_SPLIT = 3e-5
+TOL = {"fp32": TOL_FP32, "split_bf16": TOL_SPLIT}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2607_02236_gb300 import build
+    build.build_all()
+
+
+def random_frames(P, T, Ky, Kx, seed=0, elastic=1.0, signal=1e-2):
+    """Elastic offset per pixel plus small fluctuations (the regime the mean removal targets)."""
+    rng = np.random.default_rng(seed)
+    e = elastic * (rng.standard_normal((P, 1, Ky, Kx)) + 1j * rng.standard_normal((P, 1, Ky, Kx)))
+    s = signal * (rng.standard_normal((P, T, Ky, Kx)) + 1j * rng.standard_normal((P, T, Ky, Kx)))
+    return (e + s).astype(np.complex64)
+
+
+def check(spec, fr, precision, **kw):
+    out = run_gpu(spec, fr, precision, **kw)
+    ref = oracle.forward(fr, **oracle_kw(spec))
+    eI = rel_err_peak(out["I"], ref.I)
+    tol = TOL[precision]
+    assert eI <= tol, f"I error {eI:.3g} > {tol}"
+    if len(spec.detectors):
+        eS = rel_err_peak(out["S"], ref.S)
+        assert eS <= tol, f"S error {eS:.3g} > {tol}"
+    if "want_psi" in kw:
+        eP = rel_err_peak(out["Psi"], ref.Psi)
+        assert eP <= tol, f"Psi error {eP:.3g}"
+    return out, ref, eI
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split_bf16"])
+def test_tiny_config_whole(precision):
+    """4 probes, 64x64, T=256 in one push, first 128 FFT bins, Hann, mean removed, r=20 aperture."""
+    s = synth.tiny().streams[0]
+    fr = frames.frames(s, 0, 0, s.T)
+    out, ref, e = check(s, fr, precision, want_psi=True)
+    print(f"tiny {precision}: max rel I error {e:.3g}")
+
+
+CASES = {
+    # ragged rows (M=105 < 128), T not a multiple of 8, uneven pushes
+    "ragged": (StreamSpec(P=3, Kx=5, Ky=7, T=37, Tc=5, n_omega=19, E_max_meV=150.0, window="hann",
+                          detectors=(Detector("circular", 0, 0, -1, 2.0),)), [5, 11, 8, 13], 0),
+    # rows straddle probes (npix=144), several flushes with the accumulator
+    "multiflush": (StreamSpec(P=3, Kx=12, Ky=12, T=100, Tc=10, n_omega=40, E_max_meV=120.0, window="hann",
+                              detectors=(Detector("annular", 0, 0, 1.0, 4.0),)), None, 16),
+    "rect_nomean": (StreamSpec(P=2, Kx=16, Ky=16, T=64, Tc=64, fft_bins=64, window="rect", subtract_mean=False,
+                               detectors=(Detector("circular", 2, -3, -1, 3.0),)), None, 0),
+    "gauss_bose": (StreamSpec(P=2, Kx=16, Ky=8, T=96, Tc=32, n_omega=33, E_max_meV=100.0, window="gauss",
+                              bose_T_K=300.0, detectors=(Detector(), Detector("annular", 0, 0, 2, 5))), None, 0),
+    "tukey": (StreamSpec(P=1, Kx=32, Ky=32, T=80, Tc=16, n_omega=50, E_max_meV=90.0, window="tukey",
+                         window_param=0.1), None, 0),
+    "many_omega": (StreamSpec(P=1, Kx=16, Ky=16, T=48, Tc=48, n_omega=600, E_max_meV=400.0, window="hann",
+                              detectors=(Detector("circular", 0, 0, -1, 3.0),)), None, 0),
+    "one_omega_one_frame": (StreamSpec(P=2, Kx=8, Ky=8, T=1, Tc=1, n_omega=1, E_max_meV=10.0, window="hann",
+                                       subtract_mean=False), None, 0),
+}
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split_bf16"])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_edge_cases(name, precision):
+    spec, pushes, k_stage = CASES[name]
+    fr = random_frames(spec.P, spec.T, spec.Ky, spec.Kx, seed=zlib.crc32(name.encode()) % 1000)
+    out, ref, e = check(spec, fr, precision, pushes=pushes, k_stage=k_stage)
+    if k_stage:
+        assert out["info"]["flushes"] > 1
+
+
+@pytest.mark.parametrize("accum", ["kahan", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "split_bf16"])
+def test_streaming_flushes_match_single_flush(precision, accum):
+    """K_stage < T (accumulators in HBM) gives the oracle's result too."""
+    spec = StreamSpec(P=2, Kx=32, Ky=16, T=200, Tc=24, n_omega=70, E_max_meV=120.0, window="hann",
+                      n_modes=6, detectors=(Detector("circular", 0, 0, -1, 5.0),))
+    fr = frames.frames(spec, 3, 0, spec.T)
+    out, ref, e = check(spec, fr, precision, k_stage=48, accum=accum)
+    assert out["info"]["flushes"] == 5
+
+
+def test_errors_overflow_and_state():
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan, TacawError
+    from paper_2607_02236_gb300.tacaw import ERR_OVERFLOW, ERR_STATE
+    from tests.helpers import stream_config
+    spec = StreamSpec(P=1, Kx=8, Ky=8, T=16, Tc=8, n_omega=4)
+    buf = torch.zeros(32 * 64, dtype=torch.complex64, device="cuda")
+    with TacawPlan([stream_config(spec)], precision="fp32") as plan:
+        plan.push(0, buf, 8)
+        I = torch.empty(4 * 64, device="cuda")
+        with pytest.raises(TacawError) as ei:
+            plan.finalize(I)
+        assert ei.value.status == ERR_STATE
+        with pytest.raises(TacawError) as ei:
+            plan.push(0, buf, 9)
+        assert ei.value.status == ERR_OVERFLOW
+        plan.push(0, buf, 8)
+        plan.finalize(I)
+        with pytest.raises(TacawError) as ei:
+            plan.push(0, buf, 1)
+        assert ei.value.status == ERR_STATE
+        plan.reset()
+        plan.push(0, buf, 16)
+        plan.finalize(I)
