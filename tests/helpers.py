@@ -67,4 +67,6 @@ def run_gpu(spec: StreamSpec, frames: np.ndarray, precision: str, pushes=None, k
 
 def rel_err_peak(got, ref):
     """max |got - ref| / max |ref|"""
-    return float(np.max(np.abs(np.asarray(got, np.float64) - ref)) / max(np.max(np.abs(ref)), 1e-300))
+    g = np.asarray(got)
+    g = g.astype(np.complex128) if np.iscomplexobj(g) else g.astype(np.float64)
+    return float(np.max(np.abs(g - ref)) / max(np.max(np.abs(ref)), 1e-300))
