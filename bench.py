@@ -1,0 +1,413 @@
+#!/usr/bin/env python
+"""Throughput of the streaming TACAW time->energy stage on GB300.
+
+One step = one segment of the realistic workload through the C ABI: reset, 64 pushes of
+32 frames (64 probes, 256x256 k-ROI, complex64), finalize into I(k,E) (400 energies over
+0-120 meV, Hann window, elastic mean removed) and the r=20 px aperture spectra.
+Metric: complex MAC/s = P*K^2*T*Nw / step time (and EELS spectra/s = P*D / step time).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU (probe sets
+are independent: no collective on the data path); value = all ranks' CMAC / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "complex MAC/s of streaming TACAW DFT and EELS spectra/s on 1 GB300 at stated error vs FP64"
+UNIT = "CMAC/s"
+
+# DRAM bytes per launch of the contraction kernel from an ncu capture, keyed by the hash of
+# the kernel's source file at capture time (reported only while the source is unchanged).
+KERNEL_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32"])
+    ap.add_argument("--fp32-steps", type=int, default=2, help="steps of the FP32 path for comparison (0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=2, help="end-to-end steps from pinned host memory (0: skip)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU oracle baseline")
+    ap.add_argument("--small", action="store_true", help="small workload (profiling captures)")
+    return ap.parse_args()
+
+
+def stream_config(spec, P=None):
+    from paper_2607_02236_gb300 import DetectorConfig, StreamConfig
+    P = spec.P if P is None else P
+    gx, gy = spec.full_grid
+    rx, ry = spec.roi_origin
+    return StreamConfig(
+        n_probes=P, kx=spec.Kx, ky=spec.Ky, T=spec.T, dt_fs=spec.dt_fs,
+        pitch_row=gx, pitch_frame=P * gx * gy, pitch_probe=gx * gy, roi_x0=rx, roi_y0=ry,
+        E_meV=None if spec.fft_bins else [float(e) for e in spec.energies_meV()], fft_bins=spec.fft_bins,
+        window=spec.window, window_param=spec.window_sigma() if spec.window == "gauss" else spec.window_param,
+        subtract_mean=spec.subtract_mean, bose_T_K=spec.bose_T_K,
+        detectors=[DetectorConfig(d.kind, d.cx, d.cy, d.r_in, d.r_out) for d in spec.detectors])
+
+
+def workload(small: bool):
+    import synth
+    if small:
+        s = synth.StreamSpec(P=4, Kx=256, Ky=256, T=512, Tc=32, n_omega=400, E_max_meV=120.0, window="hann",
+                             n_modes=32, amp_law="smooth", noise=1e-3)
+        return "small-P4-K256-T512-W400", s
+    w = synth.realistic()
+    return w.name, w.streams[0]
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def file_hash(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+# ----------------------------------------------------------------------------------------------
+# CPU oracle timing (the cpu_baseline leg and the reference arm)
+# ----------------------------------------------------------------------------------------------
+def oracle_rate(series, spec, seconds: float):
+    """Times oracle.forward_pixels (as it stands) on pixel series [T, n]; CMAC/s and the sample used."""
+    import numpy as np
+    import oracle
+    kw = dict(window_kind=spec.window, E_meV=spec.energies_meV(), dt_fs=spec.dt_fs,
+              subtract_mean=spec.subtract_mean)
+    T, n = series.shape
+    t0 = time.perf_counter()
+    oracle.forward_pixels(series[:, :min(n, 32)], **kw)
+    dt = time.perf_counter() - t0
+    per_px = dt / min(n, 32)
+    m = int(max(32, seconds / max(per_px, 1e-9)))
+    t0 = time.perf_counter()
+    done = 0
+    while done < m:
+        k = min(1024, m - done, n)
+        s0 = done % max(1, n - k + 1)
+        oracle.forward_pixels(series[:, s0:s0 + k], **kw)
+        done += k
+    dt = time.perf_counter() - t0
+    return m * T * spec.Nw / dt, m, dt
+
+
+def reference_arm(args):
+    import numpy as np
+    from synth import frames
+    name, spec = workload(args.small)
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    rng = np.random.default_rng(0)
+    n_px = 256
+    pix = rng.integers(0, spec.Kx * spec.Ky, n_px)
+    probe = 0
+    series = frames.pixel_series(spec, 0, probe, pix // spec.Kx, pix % spec.Kx)
+    import oracle
+    kw = dict(window_kind=spec.window, E_meV=spec.energies_meV(), dt_fs=spec.dt_fs,
+              subtract_mean=spec.subtract_mean)
+    for _ in range(args.warmup):
+        oracle.forward_pixels(series, **kw)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.forward_pixels(series, **kw)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    cm = n_px * spec.T * spec.Nw
+    value = cm * len(times) / tot
+    cores = os.cpu_count()
+    sample = f"{n_px} pixels x T={spec.T} x Nw={spec.Nw} of {name} per step (FP64 NumPy oracle)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2607_02236_gb300 import TacawPlan
+    import synth.gpu as sg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    name, spec = workload(args.small)
+    P, K, T, Tc, Nw = spec.P, spec.Kx, spec.T, spec.Tc, spec.Nw
+    D = len(spec.detectors)
+    npix = K * K
+    frame_elems = P * npix
+    cmac_step = P * npix * T * Nw
+    stream = torch.cuda.current_stream()
+    st = stream.cuda_stream
+
+    # inputs resident in HBM: frames [T][P][K][K] complex64 (68.7 GB for the realistic workload)
+    x = torch.empty(T * frame_elems, dtype=torch.complex64, device="cuda")
+    base = x.data_ptr()
+    for t0 in range(0, T, 64):
+        n = min(64, T - t0)
+        sg.generate(spec, 1000 + rank, base + t0 * frame_elems * 8, t0, n, pitch_row=K,
+                    pitch_frame=frame_elems, pitch_probe=npix, stream=st)
+    torch.cuda.synchronize()
+    I = torch.empty(P * Nw * npix, dtype=torch.float32, device="cuda")
+    S = torch.empty(max(1, P * D * Nw), dtype=torch.float32, device="cuda")
+    n_push = (T + Tc - 1) // Tc
+
+    def run_step(plan):
+        plan.reset(st)
+        for i in range(n_push):
+            plan.push(0, base + i * Tc * frame_elems * 8, min(Tc, T - i * Tc), st)
+        plan.finalize(I, S, None, st)
+
+    def timed(plan, steps, warmup, sample_clocks=False):
+        for _ in range(warmup):
+            run_step(plan)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(local) if sample_clocks else None
+        plan.set_timing(True)
+        plan.kernel_time_ms(reset=True)
+        l0 = plan.info()["kernel_launches"]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            run_step(plan)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = clk.stop() if clk else None
+        ms = e0.elapsed_time(e1)
+        kms, kn = plan.kernel_time_ms(reset=True)
+        plan.set_timing(False)
+        launches = (plan.info()["kernel_launches"] - l0) // steps
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / steps, kms / max(kn, 1), kn // max(steps, 1), launches, clocks
+
+    plan = TacawPlan([stream_config(spec)], precision=args.precision)
+    info = plan.info()
+    ms_step, k_ms, k_per_step, launches, clocks = timed(plan, args.steps, args.warmup, sample_clocks=True)
+    value = world * cmac_step / (ms_step * 1e-3)
+    spectra_per_s = world * P * D / (ms_step * 1e-3)
+
+    # stated error vs FP64 at sampled pixels (all energies), incl. the bright centre
+    import oracle
+    rng = np.random.default_rng(rank)
+    probes = rng.integers(0, P, 24)
+    pix = np.concatenate([[K // 2 * K + K // 2, (K // 2 + 3) * K + K // 2 - 5],
+                          rng.integers(0, npix, 22)])
+    xv = x.view(T, P, npix)
+    series = xv[:, torch.as_tensor(probes, device="cuda"), torch.as_tensor(pix, device="cuda")].cpu().numpy()
+    Iv = I.view(P, Nw, npix)
+    got = Iv[torch.as_tensor(probes, device="cuda"), :, torch.as_tensor(pix, device="cuda")].cpu().numpy().T
+    _, ref = oracle.forward_pixels(series, window_kind=spec.window, E_meV=spec.energies_meV(), dt_fs=spec.dt_fs,
+                                   subtract_mean=spec.subtract_mean)
+    err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+
+    # end to end through the public API from pinned host memory (host ring of pushes, cycled)
+    e2e = None
+    if args.e2e_steps > 0:
+        ring = min(16, n_push)
+        push_elems = Tc * frame_elems
+        host = torch.empty(ring * push_elems, dtype=torch.complex64, pin_memory=True)
+        host.copy_(x[: ring * push_elems])
+        dev = [torch.empty(push_elems, dtype=torch.complex64, device="cuda") for _ in range(2)]
+        S_host = torch.empty(S.numel(), dtype=torch.float32, pin_memory=True)
+        cs = torch.cuda.Stream()
+        done_ev = [torch.cuda.Event() for _ in range(2)]
+        ready_ev = [torch.cuda.Event() for _ in range(2)]
+
+        def e2e_step():
+            plan.reset(st)
+            for i in range(n_push):
+                b = i % 2
+                n = min(Tc, T - i * Tc)
+                with torch.cuda.stream(cs):
+                    cs.wait_event(done_ev[b])
+                    dev[b][: n * frame_elems].copy_(host[(i % ring) * push_elems:(i % ring) * push_elems
+                                                        + n * frame_elems], non_blocking=True)
+                    ready_ev[b].record(cs)
+                stream.wait_event(ready_ev[b])
+                plan.push(0, dev[b].data_ptr(), n, st)
+                done_ev[b].record(stream)
+            plan.finalize(I, S, None, st)
+            S_host.copy_(S, non_blocking=True)
+            torch.cuda.synchronize()
+
+        for b in range(2):
+            done_ev[b].record(stream)
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        el = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * cmac_step * args.e2e_steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": T * frame_elems * 8, "d2h_bytes_per_step": S.numel() * 4,
+               "ms_per_step": 1e3 * el / args.e2e_steps,
+               "input": f"pinned host ring of {ring} pushes ({ring * push_elems * 8 / 1e9:.1f} GB) cycled"}
+        del host, dev
+    plan.close()
+
+    # FP32 CUDA-core path on the same input, for comparison at equal stated accuracy
+    fp32 = None
+    if args.fp32_steps > 0 and args.precision != "fp32":
+        with TacawPlan([stream_config(spec)], precision="fp32") as p32:
+            ms32, k32, _, _, _ = timed(p32, args.fp32_steps, 1)
+        got32 = Iv[torch.as_tensor(probes, device="cuda"), :, torch.as_tensor(pix, device="cuda")].cpu().numpy().T
+        err32 = float(np.max(np.abs(got32 - ref)) / np.max(np.abs(ref)))
+        fp32 = {"value": world * cmac_step / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32,
+                "flush_ms": k32, "max_rel_err_I_vs_fp64": err32}
+
+    # roofline of the dominant kernel (the contraction) from its live CUDA-event duration
+    peaks, peak_src = measured_peaks()
+    cmac_launch = cmac_step / max(k_per_step, 1)
+    if args.precision == "split_bf16":
+        # 3 bf16 products (hi*hi, hi*lo, lo*hi) x 4 real MAC per complex MAC = 24 flop per CMAC
+        achieved = cmac_launch * 24 / (k_ms * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        src = os.path.join(ROOT, "paper_2607_02236_gb300", "csrc", "k_tc_gemm.cu")
+        tr = KERNEL_TRAFFIC.get(file_hash(src))
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": (tr * cmac_launch if tr else None),
+                "kernel": "flush_tc_kernel", "flop_per_cmac": 24,
+                "peak_source": f"{peak_src} bf16 sustained (MEASURED_PEAKS.json)",
+                "kernel_ms": k_ms, "launches_per_step": k_per_step}
+    else:
+        achieved = cmac_launch * 8 / (k_ms * 1e-3) / 1e12
+        sm = 152
+        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak = sm * 128 * 2 * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "flush_simt_kernel", "flop_per_cmac": 8,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock", "kernel_ms": k_ms,
+                "launches_per_step": k_per_step}
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        n_cpu = 4096
+        cp = rng.integers(0, P, n_cpu)
+        cx = rng.integers(0, npix, n_cpu)
+        ser = xv[:, torch.as_tensor(cp, device="cuda"), torch.as_tensor(cx, device="cuda")].cpu().numpy()
+        rate, m, dt = oracle_rate(ser, spec, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{m} random (probe, pixel) series x T={T} x Nw={Nw} ({dt:.1f} s, FP64 NumPy)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16" if args.precision == "split_bf16" else "f32",
+                "data": "synthetic",
+                "config": {"workload": name, "probes": P, "k_roi": f"{K}x{K}", "T": T, "frames_per_push": Tc,
+                           "n_omega": Nw, "E_range_meV": [0, spec.E_max_meV], "window": spec.window,
+                           "precision": args.precision + (" (hi*hi+hi*lo+lo*hi, fp32 accumulate, fp64 phase)"
+                                                          if args.precision == "split_bf16" else ""),
+                           "k_stage": info["k_stage"], "omega_tile": info["omega_tile"],
+                           "smem_stages": info["stages"], "plan_device_GB": round(info["device_bytes"] / 1e9, 2),
+                           "l2": "inputs (%.1f GB) larger than L2, no flush" % (T * frame_elems * 8 / 1e9),
+                           "parallelism": f"replicas x{world}"},
+                "max_rel_err_I_vs_fp64": err, "error_sample": "24 (probe, pixel) series, all energies",
+                "spectra_per_s": spectra_per_s, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "fp32_path": fp32}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -130,6 +130,7 @@ typedef struct {
     int64_t flushes;           /* flushes run since the plan was created */
     int omega_tile;            /* complex energies per tensor-core tile (split path) */
     int stages;                /* shared-memory pipeline stages (split path) */
+    int64_t kernel_launches;   /* kernels launched by push/finalize/backward since creation */
 } tacaw_plan_info;
 
 /* Creates a plan: validates the descriptor, sizes and allocates device memory
@@ -153,10 +154,10 @@ tacaw_status tacaw_push_frames(tacaw_plan_t plan, int stream_id, const void *d_f
  * the detector spectra.  Outputs (caller-owned device memory, streams concatenated in
  * order; see tacaw_output_offsets):
  *   d_I   float32 [s][p][j][ky][kx]   (may be NULL)
- *   d_S   float32 [s][p][d][j]        (may be NULL; requires d_I or internal I)
+ *   d_S   float32 [s][p][d][j]        (may be NULL)
  *   d_Psi complex64 [s][p][j][ky][kx] (may be NULL)
- * Spectra are summed in a fixed order (deterministic).  Waits for the work on `stream`.
- * Errors: STATE unless every stream has received exactly T frames.                      */
+ * Spectra are summed in a fixed order (deterministic).  d_S requires d_I.  Waits for the
+ * work on `stream`.  Errors: STATE unless every stream has received exactly T frames.  */
 tacaw_status tacaw_finalize(tacaw_plan_t plan, float *d_I, float *d_S, void *d_Psi, void *stream);
 
 /* Element offsets of stream stream_id's block inside d_I / d_Psi and d_S.              */

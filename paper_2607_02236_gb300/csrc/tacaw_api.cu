@@ -81,6 +81,7 @@ struct tacaw_plan_s {
     int64_t bytes = 0;
     int64_t I_elems = 0, S_elems = 0;
     int64_t flushes_total = 0;
+    int64_t launches = 0;
     bool poisoned = false;
     bool finalized = false;
     uint32_t *d_err = nullptr;
@@ -196,7 +197,10 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         CU_CHECK(p, cudaEventRecord(e0, st), "cudaEventRecord");
     }
     if (p->prec == TACAW_PREC_SPLIT_BF16) {
-        if (n & 7) CU_CHECK(p, launch_zero_tail_split(s.M_pad, n, s.A_hi, s.A_lo, st), "zero_tail");
+        if (n & 7) {
+            CU_CHECK(p, launch_zero_tail_split(s.M_pad, n, s.A_hi, s.A_lo, st), "zero_tail");
+            p->launches++;
+        }
         TcPlanArgs a{};
         a.e = e;
         a.wt = s.wt;
@@ -207,6 +211,7 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         a.stages = p->stages;
         a.err = p->d_err;
         CU_CHECK(p, launch_flush_tc(a, s.tc_maps.data(), st), "flush (tensor cores)");
+        p->launches++;
     } else {
         SimtArgs a{};
         a.e = e;
@@ -216,6 +221,7 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         a.n_frames = n;
         a.t0 = s.stage_start;
         CU_CHECK(p, launch_flush_simt(a, st), "flush (fp32)");
+        p->launches++;
     }
     if (p->timing) {
         CU_CHECK(p, cudaEventRecord(e1, st), "cudaEventRecord");
@@ -540,7 +546,10 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
     g.npix = s.npix;
     g.M = s.M;
     g.base = static_cast<const float2 *>(d_frames);
-    if (s.pushed == 0 && s.d.subtract_mean) CU_CHECK(p, launch_mean(g, n_frames, s.mu_hat, st), "provisional mean");
+    if (s.pushed == 0 && s.d.subtract_mean) {
+        CU_CHECK(p, launch_mean(g, n_frames, s.mu_hat, st), "provisional mean");
+        p->launches++;
+    }
     int done = 0;
     while (done < n_frames) {
         const int chunk = std::min(n_frames - done, s.ring - s.staged);
@@ -551,6 +560,7 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
                      "convert");
         else
             CU_CHECK(p, launch_convert_fp32(gc, chunk, s.staged, s.M_pad, s.mu_hat, s.sum_res, s.A32, st), "convert");
+        p->launches++;
         s.staged += chunk;
         s.pushed += chunk;
         done += chunk;
@@ -573,6 +583,7 @@ tacaw_status tacaw_finalize(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     for (auto &s : p->s) {
         CU_CHECK(p, launch_mean_residual(s.M, s.T, s.d.subtract_mean, s.sum_res, s.dmu, st), "mean residual");
+        p->launches++;
         float *I = d_I ? d_I + s.I_off : nullptr;
         float2 *Psi = d_Psi ? static_cast<float2 *>(d_Psi) + s.I_off : nullptr;
         tacaw_status r = run_flush(p, s, FLUSH_FINAL, I, Psi, st);
@@ -589,6 +600,7 @@ tacaw_status tacaw_finalize(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi,
             a.wts = s.det_w;
             a.off = s.det_off;
             CU_CHECK(p, launch_aperture(a, st), "aperture");
+            p->launches++;
         }
     }
     p->finalized = true;
@@ -627,6 +639,7 @@ tacaw_status tacaw_plan_get_info(tacaw_plan_t p, tacaw_plan_info *info) {
     info->flushes = p->flushes_total;
     info->omega_tile = p->s.empty() ? 0 : p->s[0].wt;
     info->stages = p->stages;
+    info->kernel_launches = p->launches;
     return TACAW_OK;
 }
 
@@ -698,6 +711,7 @@ tacaw_status tacaw_backward(tacaw_plan_t p, int sid, const float *d_dL_dS, const
         a.grad = static_cast<float2 *>(d_grad);
         a.scratch = scratch;
         cudaError_t e = launch_adjoint(a, st);
+        p->launches += 2;
         cudaFreeAsync(scratch, st);
         if (e != cudaSuccess) return cuda_fail(p, e, "adjoint");
     }

@@ -59,7 +59,7 @@ class CPlanDesc(ctypes.Structure):
 class CPlanInfo(ctypes.Structure):
     _fields_ = [("device_bytes", c_int64), ("k_stage", c_int), ("n_streams", c_int), ("precision", c_int),
                 ("I_elems", c_int64), ("S_elems", c_int64), ("flushes", c_int64), ("omega_tile", c_int),
-                ("stages", c_int)]
+                ("stages", c_int), ("kernel_launches", c_int64)]
 
 
 _lib = None
