@@ -166,13 +166,14 @@ tacaw_status tacaw_output_offsets(tacaw_plan_t plan, int stream_id, int64_t *I_o
 
 /* Gradient of L = sum_{p,d,j} dL_dS[p][d][j] * S[p][d][j] with respect to the frames of one
  * stream's segment, in PyTorch's convention for real losses of complex inputs:
- *   d_grad = dL/dRe(psi) + i dL/dIm(psi) = 2 dL/dconj(psi),   complex64 [p][t][ky][kx] (dense)
+ *   grad = dL/dRe(psi) + i dL/dIm(psi) = 2 dL/dconj(psi)
  *   g[t,k] = 2 ( w_t A[t,k] - (1/T) sum_t' w_t' A[t',k] ),  A[t,k] = sum_j e^{+i theta_jt} G[k,j],
  *   G[k,j] = B(E_j) sum_d dL_dS[d,j] M_d(k) Psi[k,j]  (mean term only with subtract_mean).
- * d_frames holds the whole segment, laid out as pushed (pitches of the stream descriptor,
- * t = 0..T-1 with pitch_frame).  Psi is recomputed from the frames, not stored.  Pixels
- * outside every aperture get a zero gradient.  Independent of the push/finalize state.
- * d_dL_dS: float32 [p][d][j] device.  Waits for the work on `stream`.                    */
+ * d_frames holds the whole segment (t = 0..T-1) in the pushed layout of the stream
+ * descriptor; d_grad (complex64) has the same layout: every ROI element is written (zero
+ * outside the apertures), elements outside the ROI are not touched.  Psi is recomputed
+ * from the frames, not stored.  Independent of the push/finalize state of the plan.
+ * d_dL_dS: float32 [p][d][j] on the device.  Waits for the work on `stream`.             */
 tacaw_status tacaw_backward(tacaw_plan_t plan, int stream_id, const float *d_dL_dS,
                             const void *d_frames, void *d_grad, void *stream);
 

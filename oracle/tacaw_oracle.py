@@ -230,3 +230,32 @@ def forward_pixels(series, *, window_kind="hann", window_param=0.0, E_meV=None, 
     Psi = F.T @ y
     I = (Psi.real ** 2 + Psi.imag ** 2) * bose(E, bose_T_K)[:, None]
     return Psi, I
+
+
+def gradient_pixels(series, dLdS, mask_w, *, window_kind="hann", window_param=0.0, E_meV=None, dt_fs=5.0,
+                    fft_bins=0, subtract_mean=True, bose_T_K=0.0):
+    """The gradient above for independent pixel series: series [T, n], dLdS [D, Nw] (one probe),
+    mask_w [n, D] = M_d(k_i).  Returns g [T, n] = 2 dL/dconj(psi) at those pixels."""
+    x = np.asarray(series).astype(np.complex128)
+    T = x.shape[0]
+    E = fft_energies(T, dt_fs, fft_bins) if fft_bins else np.asarray(E_meV, dtype=np.float64)
+    theta = phase(T, E_meV=E, dt_fs=dt_fs, fft_bins=fft_bins)        # [T, Nw]
+    Psi, _ = forward_pixels(x, window_kind=window_kind, window_param=window_param, E_meV=E, dt_fs=dt_fs,
+                            fft_bins=fft_bins, subtract_mean=subtract_mean, bose_T_K=0.0)   # [Nw, n]
+    coef = np.asarray(dLdS, dtype=np.float64).T @ np.asarray(mask_w, dtype=np.float64).T     # [Nw, n]
+    G = coef * bose(E, bose_T_K)[:, None] * Psi
+    A = np.exp(1j * theta) @ G                                          # [T, n]
+    g = window(window_kind, T, window_param)[:, None] * A
+    if subtract_mean:
+        g = g - g.mean(axis=0, keepdims=True)
+    return 2.0 * g
+
+
+def loss_pixels(series, dLdS, mask_w, *, bose_T_K=0.0, **kw):
+    """sum over the given pixels of sum_{d,j} dLdS[d,j] M_d(k) I[k,j] (the pixels' share of L)."""
+    x = np.asarray(series).astype(np.complex128)
+    E = fft_energies(x.shape[0], kw.get("dt_fs", 5.0), kw["fft_bins"]) if kw.get("fft_bins") else \
+        np.asarray(kw["E_meV"], dtype=np.float64)
+    _, I = forward_pixels(x, bose_T_K=bose_T_K, **kw)
+    coef = np.asarray(dLdS, dtype=np.float64).T @ np.asarray(mask_w, dtype=np.float64).T
+    return float(np.sum(coef * I))

@@ -168,12 +168,32 @@ __global__ void __launch_bounds__(256) adj_backward_kernel(AdjointArgs a) {
         if (t < a.T) {
             for (int i = 0; i < npx; ++i) {
                 const int pix = a.mpix[g0 + i];
+                const int y = pix / a.kx, x = pix - (pix / a.kx) * a.kx;
                 const float2 K = Kc[(size_t)p * a.n_mpix + g0 + i];
-                a.grad[((size_t)p * a.T + t) * (size_t)(a.kx * a.ky) + pix] =
-                    make_float2(2.f * (cr[i] - K.x), 2.f * (ci[i] - K.y));
+                a.grad[(int64_t)p * a.pitch_probe + (int64_t)t * a.pitch_frame + (int64_t)(a.roi_y0 + y) * a.pitch_row +
+                       (a.roi_x0 + x)] = make_float2(2.f * (cr[i] - K.x), 2.f * (ci[i] - K.y));
             }
         }
     }
+}
+
+// zero every ROI element of the gradient (layout of the frames)
+__global__ void zero_roi_kernel(AdjointArgs a) {
+    const int64_t npix = (int64_t)a.kx * a.ky;
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (int64_t)a.P * a.T * npix) return;
+    const int64_t pix = id % npix;
+    const int64_t pt = id / npix;
+    const int t = (int)(pt % a.T), p = (int)(pt / a.T);
+    const int64_t y = pix / a.kx, x = pix - (pix / a.kx) * a.kx;
+    a.grad[(int64_t)p * a.pitch_probe + (int64_t)t * a.pitch_frame + (a.roi_y0 + y) * a.pitch_row + (a.roi_x0 + x)] =
+        make_float2(0.f, 0.f);
+}
+
+cudaError_t launch_zero_roi(const AdjointArgs &a, cudaStream_t st) {
+    const int64_t n = (int64_t)a.P * a.T * a.kx * a.ky;
+    zero_roi_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t st) {

@@ -680,35 +680,36 @@ tacaw_status tacaw_backward(tacaw_plan_t p, int sid, const float *d_dL_dS, const
     if (!d_dL_dS || !d_frames || !d_grad) return fail(TACAW_ERR_INVALID_ARG, "NULL device pointer");
     Stream &s = p->s[sid];
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CU_CHECK(p, cudaMemsetAsync(d_grad, 0, sizeof(float2) * (size_t)s.d.n_probes * s.T * s.npix, st), "memset grad");
+    AdjointArgs a{};
+    a.frames = static_cast<const float2 *>(d_frames);
+    a.pitch_row = s.d.pitch_row;
+    a.pitch_frame = s.d.pitch_frame;
+    a.pitch_probe = s.d.pitch_probe;
+    a.roi_x0 = s.d.roi_x0;
+    a.roi_y0 = s.d.roi_y0;
+    a.kx = s.d.kx;
+    a.ky = s.d.ky;
+    a.P = s.d.n_probes;
+    a.T = s.T;
+    a.Nw = s.Nw;
+    a.D = s.D;
+    a.subtract_mean = s.d.subtract_mean;
+    a.w = s.win;
+    a.B32 = s.B32;
+    a.Nw_pad = s.Nw_pad;
+    a.Wc = s.Wc;
+    a.bose = s.bose;
+    a.dLdS = d_dL_dS;
+    a.mpix = s.adj_pix;
+    a.mwts = s.adj_w;
+    a.n_mpix = s.n_adj;
+    a.grad = static_cast<float2 *>(d_grad);
+    CU_CHECK(p, launch_zero_roi(a, st), "zero gradient");
+    p->launches++;
     if (s.n_adj > 0 && s.D > 0) {
         float2 *scratch = nullptr;
         const size_t n_scr = (size_t)s.d.n_probes * s.n_adj * (s.Nw + 2);
         CU_CHECK(p, cudaMallocAsync(reinterpret_cast<void **>(&scratch), n_scr * sizeof(float2), st), "scratch");
-        AdjointArgs a{};
-        a.frames = static_cast<const float2 *>(d_frames);
-        a.pitch_row = s.d.pitch_row;
-        a.pitch_frame = s.d.pitch_frame;
-        a.pitch_probe = s.d.pitch_probe;
-        a.roi_x0 = s.d.roi_x0;
-        a.roi_y0 = s.d.roi_y0;
-        a.kx = s.d.kx;
-        a.ky = s.d.ky;
-        a.P = s.d.n_probes;
-        a.T = s.T;
-        a.Nw = s.Nw;
-        a.D = s.D;
-        a.subtract_mean = s.d.subtract_mean;
-        a.w = s.win;
-        a.B32 = s.B32;
-        a.Nw_pad = s.Nw_pad;
-        a.Wc = s.Wc;
-        a.bose = s.bose;
-        a.dLdS = d_dL_dS;
-        a.mpix = s.adj_pix;
-        a.mwts = s.adj_w;
-        a.n_mpix = s.n_adj;
-        a.grad = static_cast<float2 *>(d_grad);
         a.scratch = scratch;
         cudaError_t e = launch_adjoint(a, st);
         p->launches += 2;

@@ -211,9 +211,10 @@ struct AdjointArgs {
     const int *mpix;           // pixels inside any aperture (sorted)
     const float *mwts;         // [n_mpix][D] mask weights of those pixels
     int n_mpix;
-    float2 *grad;              // [P][T][ky][kx] dense
+    float2 *grad;              // same layout as frames (pitches above)
     float2 *scratch;           // [P][n_mpix][Nw] complex (G), plus [P][n_mpix] means
 };
 cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t st);
+cudaError_t launch_zero_roi(const AdjointArgs &a, cudaStream_t st);
 
 }  // namespace tacaw

@@ -360,3 +360,19 @@ def test_gradient_matches_torch_autograd():
     L = (torch.tensor(dLdS) * S).sum()
     L.backward()
     np.testing.assert_allclose(x.grad.numpy(), g, rtol=1e-10, atol=1e-12 * np.abs(g).max())
+
+
+def test_pixel_gradient_equals_full_gradient_on_pixels():
+    """Pixels are independent: the per-pixel gradient is the full gradient restricted to them."""
+    psi, dLdS, kw = _grad_case(11)
+    g = oracle.gradient(psi, dLdS, **kw)
+    P, T, Ky, Kx = psi.shape
+    M = oracle.detector_masks(Kx, Ky, kw["detectors"]).reshape(len(kw["detectors"]), -1)
+    kw2 = {k: v for k, v in kw.items() if k != "detectors"}
+    for p in range(P):
+        series = psi[p].reshape(T, -1)
+        gp = oracle.gradient_pixels(series, dLdS[p], M.T, **kw2)
+        np.testing.assert_allclose(gp, g[p].reshape(T, -1), rtol=1e-10, atol=1e-12 * np.abs(g).max())
+        Lp = oracle.loss_pixels(series, dLdS[p], M.T, **kw2)
+        Lfull = float(np.sum(dLdS[p] * oracle.forward(psi[p:p + 1], **kw).S[0]))
+        assert abs(Lp - Lfull) <= 1e-10 * abs(Lfull)
