@@ -192,6 +192,24 @@ tacaw_status tacaw_set_timing(tacaw_plan_t plan, int enable);
 tacaw_status tacaw_kernel_time_ms(tacaw_plan_t plan, double *flush_ms, int64_t *flush_launches,
                                   int reset);
 
+/* Detector spectra S[p][d][j] = sum_k M_d(k) I[p][j][k] from a caller-owned intensity array
+ * d_I (float32 [p][j][ky][kx], the layout tacaw_finalize writes) without a plan and without
+ * allocating device memory.  The paper has no counterpart of this entry point.  It is for
+ * callers that may not allocate device memory: code inside a framework that owns the whole
+ * device budget, real-time loops where cudaMalloc/cudaFree would synchronise the device,
+ * hosts that only hand over raw device pointers.
+ * Apertures follow tacaw_detector (MASK weights are read back from the device during the
+ * call).  Their (pixel, weight) lists go into one fixed device array that the library holds
+ * on every device that loads it, until the process exits: at most 2^20 pixel entries summed
+ * over all detectors and at most 1024 detectors; a larger request returns
+ * TACAW_ERR_INVALID_ARG before any device work.  The first call on a device looks up that
+ * array's address, so make it before any stream capture.  Every call reuses the same array:
+ * calls whose work overlaps on the GPU (other streams or threads) race, so serialise them.
+ * d_S: float32 [p][d][j].  Enqueued on `stream`; returns without waiting for the kernel.  */
+tacaw_status tacaw_detector_spectra_noalloc(const float *d_I, int n_probes, int n_omega, int kx, int ky,
+                                            const tacaw_detector *detectors, int n_detectors, float *d_S,
+                                            void *stream);
+
 /* Frees every device allocation of the plan.  Accepts NULL.                             */
 tacaw_status tacaw_destroy(tacaw_plan_t plan);
 

@@ -40,6 +40,14 @@ tacaw_status fail(tacaw_status st, const char *fmt, ...) {
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+}  // namespace
+
+namespace tacaw {
+void set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+}  // namespace tacaw
+
+namespace {
+
 struct Stream {
     tacaw_stream_desc d{};
     std::vector<double> E;

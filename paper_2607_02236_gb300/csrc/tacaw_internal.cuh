@@ -196,6 +196,9 @@ struct ApertureArgs {
 };
 cudaError_t launch_aperture(const ApertureArgs &a, cudaStream_t st);
 
+// records the calling thread's message for tacaw_last_error()
+void set_last_error(const char *msg);
+
 struct AdjointArgs {
     const float2 *frames;      // pushed layout, whole segment
     int64_t pitch_row, pitch_frame, pitch_probe;

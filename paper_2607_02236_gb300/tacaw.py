@@ -26,7 +26,8 @@ DET_KINDS = {"circular": 0, "annular": 1, "mask": 2}
 # Every symbol include/tacaw.h declares (checked by the CPU test that loads the library).
 EXPORTS = ["tacaw_plan_create", "tacaw_push_frames", "tacaw_finalize", "tacaw_output_offsets",
            "tacaw_backward", "tacaw_reset", "tacaw_plan_get_info", "tacaw_set_timing",
-           "tacaw_kernel_time_ms", "tacaw_destroy", "tacaw_last_error", "tacaw_version"]
+           "tacaw_kernel_time_ms", "tacaw_destroy", "tacaw_last_error", "tacaw_version",
+           "tacaw_detector_spectra_noalloc"]
 
 
 class TacawError(RuntimeError):
@@ -83,6 +84,8 @@ def lib():
     L.tacaw_set_timing.argtypes = [c_void_p, c_int]
     L.tacaw_kernel_time_ms.argtypes = [c_void_p, POINTER(c_double), POINTER(c_int64), c_int]
     L.tacaw_destroy.argtypes = [c_void_p]
+    L.tacaw_detector_spectra_noalloc.argtypes = [c_void_p, c_int, c_int, c_int, c_int, POINTER(CDetector), c_int,
+                                                 c_void_p, c_void_p]
     L.tacaw_last_error.restype = c_char_p
     L.tacaw_version.restype = c_char_p
     for name in EXPORTS:
@@ -234,6 +237,23 @@ class TacawPlan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def _c_detectors(dets):
+    arr = (CDetector * max(1, len(dets)))()
+    for k, t in enumerate(dets):
+        arr[k].kind, arr[k].cx, arr[k].cy = DET_KINDS[t.kind], t.cx, t.cy
+        arr[k].r_in, arr[k].r_out, arr[k].d_mask = t.r_in, t.r_out, t.mask_ptr or None
+    return arr
+
+
+def detector_spectra_noalloc(I, n_probes: int, n_omega: int, kx: int, ky: int, detectors, S, cuda_stream=None):
+    """S[p, d, E] from I[p, E, ky, kx] (device) through tacaw_detector_spectra_noalloc: no plan and no
+    device allocation (the aperture lists live in the library's fixed device array)."""
+    arr = _c_detectors(list(detectors))
+    _check(lib().tacaw_detector_spectra_noalloc(_ptr(I), int(n_probes), int(n_omega), int(kx), int(ky),
+                                                ctypes.cast(arr, POINTER(CDetector)), len(detectors), _ptr(S),
+                                                _stream(cuda_stream)))
 
 
 def version() -> str:
