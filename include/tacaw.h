@@ -116,6 +116,14 @@ typedef struct {
     int64_t hbm_budget_bytes;          /* device bytes the plan may hold; 0: 90% of free memory */
     int k_stage;                       /* frames staged per flush (multiple of 8); 0: from budget */
     const char *tune_cache_path;       /* reserved, may be NULL */
+    /* Tensor-core tiling (split path); 0 selects automatically.
+     *   tc_omega_tile     complex energies per tile (multiple of 8)
+     *   tc_accumulators   TMEM accumulators per tile: 1 (all products in one), 2 (hi*hi | small
+     *                     terms), 3 (hi*hi alternating over two | small terms; default)
+     *   tc_cluster        CTAs per cluster sharing the twiddle rows by TMA multicast: 1, 2, 4 */
+    int tc_omega_tile;
+    int tc_accumulators;
+    int tc_cluster;
 } tacaw_plan_desc;
 
 typedef struct tacaw_plan_s *tacaw_plan_t;
@@ -131,6 +139,8 @@ typedef struct {
     int omega_tile;            /* complex energies per tensor-core tile (split path) */
     int stages;                /* shared-memory pipeline stages (split path) */
     int64_t kernel_launches;   /* kernels launched by push/finalize/backward since creation */
+    int tc_accumulators;       /* TMEM accumulators per tile (split path) */
+    int tc_cluster;            /* cluster size of the contraction (split path, first stream) */
 } tacaw_plan_info;
 
 /* Creates a plan: validates the descriptor, sizes and allocates device memory

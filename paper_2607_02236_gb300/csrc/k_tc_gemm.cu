@@ -7,12 +7,20 @@
 // split x = hi + lo (bf16 each); the product is accumulated as hi*hi + hi*lo + lo*hi in
 // FP32 in tensor memory (the dropped lo*lo term is ~2^-16 relative).
 //
-// CTA = 128 rows (one TMEM lane each) x N real columns (2*wt complex energies, N <= 512).
-//   warp 0      TMA producer: per 8-frame block, A_hi/A_lo boxes [128 x 16] and B_hi/B_lo
-//               boxes [N x 16] (bf16, 32-byte rows, 32B swizzle) into an s-stage ring
-//   warp 1      TMEM allocator + single-thread MMA issuer (3 passes x ceil(N/256) MMAs of
-//               M=128, K=16 per block), tcgen05.commit releases ring slots
-//   warps 2..5  epilogue: tcgen05.ld of the accumulator (warp w reads lanes 32*(w%4)..)
+// Tensor-core FP32 accumulation rounds each accumulate step relative to the running sum,
+// so long K loops into one accumulator lose precision in proportion to their length.  With
+// split accumulators the hi*hi products alternate between two TMEM accumulators (even and
+// odd 8-frame blocks) and the small hi*lo + lo*hi terms go to a third, which keeps every
+// accumulate step short relative to its own sum; the epilogue adds the three.
+//
+// CTA = 128 rows (one TMEM lane each) x N real columns (2*wt complex energies).
+//   warp 0      TMA producer: per 8-frame block, A_hi/A_lo boxes [128 x 16] and this CTA's
+//               share of the B_hi/B_lo rows (bf16, 32-byte rows, 32B swizzle) into an s-stage
+//               ring; with a cluster of C CTAs (same energy tile, C consecutive row tiles)
+//               each CTA loads N/C rows of B and multicasts them to the whole cluster
+//   warp 1      TMEM allocator + single-thread MMA issuer; tcgen05.commit releases ring
+//               slots in every CTA of the cluster
+//   warps 2..5  epilogue: tcgen05.ld of the accumulators (warp w reads lanes 32*(w%4)..)
 //               and the per-element flush update (store / compensated add / finalize)
 // Every mbarrier wait is bounded (globaltimer); on timeout the kernel records an error
 // bit, lets in-flight copies land, frees TMEM and returns.
@@ -32,7 +40,7 @@ struct TcMaps {
 };
 
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s per wait
-constexpr int kMaxStages = 8;
+constexpr int kMaxStages = 12;
 constexpr uint32_t kABytes = kMTile * 32;          // 128 rows x 16 bf16
 constexpr int kSmemLimit = 232448;                 // 227 KB opt-in per block
 
@@ -116,6 +124,28 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
 }
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                               uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -162,17 +192,21 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
     const uint32_t base_s = smem_u32(base);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wtile = (int)(blockIdx.x % (unsigned)a.n_wt);
-    const int m0 = (int)(blockIdx.x / (unsigned)a.n_wt) * kMTile;
-    const uint32_t ncols = tc_tmem_cols(a.N);
-    const int n0 = a.N < 256 ? a.N : 256;
-    const int n1 = a.N - n0;
+    const int C = a.cluster;
+    const uint32_t crank = C > 1 ? cluster_ctarank() : 0u;
+    const unsigned cid = blockIdx.x / (unsigned)C;
+    const int wtile = (int)(cid % (unsigned)a.n_wt);
+    const int m0 = ((int)(cid / (unsigned)a.n_wt) * C + (int)crank) * kMTile;
+    const int n_acc = a.split ? a.n_big + 1 : 1;
+    const uint32_t ncols = tc_tmem_cols(n_acc * a.N);
     const uint32_t tx_bytes = 2u * kABytes + 2u * (uint32_t)a.N * 32u;
+    const int rows_cta = a.N / C;                 // B rows this CTA loads (for the whole cluster)
+    const uint16_t cmask = (uint16_t)((1u << C) - 1u);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
             mbar_init(smem_u32(&sh->full[s]), 1);
-            mbar_init(smem_u32(&sh->empty[s]), 1);
+            mbar_init(smem_u32(&sh->empty[s]), (uint32_t)C);   // one release per CTA of the cluster
         }
         mbar_init(smem_u32(&sh->tmem_full), 1);
         sh->abort_flag = 0;
@@ -184,6 +218,7 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
     }
     tc_fence_before();
     __syncthreads();
+    if (C > 1) cluster_sync();   // every CTA's barriers exist before any multicast reaches them
     tc_fence_after();
     const uint32_t tmem = sh->tmem_addr;
     volatile int *abort_flag = &sh->abort_flag;
@@ -205,15 +240,21 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
                 tma_load_3d(st, &maps.a_hi, 0, m0, kb, full);
                 tma_load_3d(st + kABytes, &maps.a_lo, 0, m0, kb, full);
                 for (int b = 0; b < maps.nbox_b; ++b) {
-                    const int row = wtile * a.N + b * maps.box_b_rows;
-                    const uint32_t off = (uint32_t)b * (uint32_t)maps.box_b_rows * 32u;
-                    tma_load_3d(st + 2 * kABytes + off, &maps.b_hi, 0, row, a.kbB0 + kb, full);
-                    tma_load_3d(st + 2 * kABytes + b_pad + off, &maps.b_lo, 0, row, a.kbB0 + kb, full);
+                    const int r0 = (int)crank * rows_cta + b * maps.box_b_rows;
+                    const int row = wtile * a.N + r0;
+                    const uint32_t off = (uint32_t)r0 * 32u;
+                    if (C > 1) {
+                        tma_load_3d_mc(st + 2 * kABytes + off, &maps.b_hi, 0, row, a.kbB0 + kb, full, cmask);
+                        tma_load_3d_mc(st + 2 * kABytes + b_pad + off, &maps.b_lo, 0, row, a.kbB0 + kb, full, cmask);
+                    } else {
+                        tma_load_3d(st + 2 * kABytes + off, &maps.b_hi, 0, row, a.kbB0 + kb, full);
+                        tma_load_3d(st + 2 * kABytes + b_pad + off, &maps.b_lo, 0, row, a.kbB0 + kb, full);
+                    }
                 }
                 issued = kb + 1;
             }
             if (*abort_flag) {
-                // let every copy this thread started land before the CTA can exit
+                // let every copy into this CTA's ring land before it can exit
                 const int first = issued > a.stages ? issued - a.stages : 0;
                 for (int kb = first; kb < issued; ++kb) {
                     const int s = kb % a.stages;
@@ -224,9 +265,12 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
         }
     } else if (warp == 1) {
         if (lane == 0) {
+            const int n0 = a.N < 256 ? a.N : 256;
+            const int n1 = a.N - n0;
             const uint32_t id0 = idesc_bf16_f32(kMTile, n0);
             const uint32_t id1 = n1 > 0 ? idesc_bf16_f32(kMTile, n1) : 0u;
             const uint64_t b_half_off = (uint64_t)((n0 * 32) >> 4);
+            const uint32_t acc_small = tmem + (uint32_t)(a.n_big * a.N);
             for (int kb = 0; kb < a.n_kb; ++kb) {
                 const int s = kb % a.stages;
                 const uint32_t use = (uint32_t)(kb / a.stages);
@@ -241,15 +285,26 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
                 const uint64_t dAlo = sdesc_k_sw32(st + kABytes);
                 const uint64_t dBhi = sdesc_k_sw32(st + 2 * kABytes);
                 const uint64_t dBlo = sdesc_k_sw32(st + 2 * kABytes + b_pad);
+                if (a.split) {
+                    // N <= 256: one MMA per product
+                    const int big = a.n_big == 2 ? (kb & 1) : 0;
+                    mma_bf16_ss(tmem + (uint32_t)(big * a.N), dAhi, dBhi, id0, kb >= a.n_big ? 1u : 0u);
+                    mma_bf16_ss(acc_small, dAhi, dBlo, id0, kb > 0 ? 1u : 0u);
+                    mma_bf16_ss(acc_small, dAlo, dBhi, id0, 1u);
+                } else {
 #pragma unroll
-                for (int pass = 0; pass < 3; ++pass) {
-                    const uint64_t dA = pass == 2 ? dAlo : dAhi;
-                    const uint64_t dB = pass == 1 ? dBlo : dBhi;
-                    const uint32_t acc = (kb > 0 || pass > 0) ? 1u : 0u;
-                    mma_bf16_ss(tmem, dA, dB, id0, acc);
-                    if (n1 > 0) mma_bf16_ss(tmem + (uint32_t)n0, dA, dB + b_half_off, id1, acc);
+                    for (int pass = 0; pass < 3; ++pass) {
+                        const uint64_t dA = pass == 2 ? dAlo : dAhi;
+                        const uint64_t dB = pass == 1 ? dBlo : dBhi;
+                        const uint32_t acc = (kb > 0 || pass > 0) ? 1u : 0u;
+                        mma_bf16_ss(tmem, dA, dB, id0, acc);
+                        if (n1 > 0) mma_bf16_ss(tmem + (uint32_t)n0, dA, dB + b_half_off, id1, acc);
+                    }
                 }
-                mma_commit(smem_u32(&sh->empty[s]));
+                if (C > 1)
+                    mma_commit_mc(smem_u32(&sh->empty[s]), cmask);
+                else
+                    mma_commit(smem_u32(&sh->empty[s]));
             }
             // always signal: the epilogue (and TMEM release) wait for every issued MMA
             mma_commit(smem_u32(&sh->tmem_full));
@@ -267,15 +322,32 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
             const int64_t m = (int64_t)m0 + q * 32 + lane;
             const RowCtx row = make_row(a.e, m);
             const int jbase = wtile * a.wt;
+            const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+            const int n_big_used = a.split ? (a.n_kb < a.n_big ? a.n_kb : a.n_big) : 0;
             for (int c0 = 0; c0 < a.N; c0 += 16) {
                 uint32_t r[16];
-                tmem_ld_x16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+                float v[16];
+                tmem_ld_x16(lane_base + (uint32_t)c0, r);
                 tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+                if (a.split) {
+                    if (n_big_used == 2) {
+                        tmem_ld_x16(lane_base + (uint32_t)(a.N + c0), r);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] += __uint_as_float(r[i]);
+                    }
+                    tmem_ld_x16(lane_base + (uint32_t)(a.n_big * a.N + c0), r);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += __uint_as_float(r[i]);
+                }
                 if (row.valid) {
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int j = jbase + (c0 >> 1) + i;
-                        if (j < a.e.Nw) epi_element(a.e, row, j, __uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+                        if (j < a.e.Nw) epi_element(a.e, row, j, v[2 * i], v[2 * i + 1]);
                     }
                 }
             }
@@ -283,6 +355,7 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
     }
     tc_fence_before();
     __syncthreads();
+    if (C > 1) cluster_sync();   // no CTA leaves while a peer may still signal its barriers
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, ncols);
@@ -343,13 +416,28 @@ static bool encode3d(CUtensorMap *m, const void *ptr, uint64_t d0, uint64_t d1, 
     return true;
 }
 
+// B rows loaded by one CTA: N / cluster, in boxes of at most 256 rows whose shared-memory
+// offsets stay on 256-byte (8-row) swizzle-atom boundaries.
+bool tc_b_boxes(int N, int cluster, int *box_rows, int *nbox) {
+    if (cluster < 1 || N % cluster) return false;
+    const int rows = N / cluster;
+    if (rows % 8) return false;
+    const int nb = (rows + 255) / 256;
+    if (rows % nb || (rows / nb) % 8) return false;
+    *box_rows = rows / nb;
+    *nbox = nb;
+    return true;
+}
+
 bool tc_make_maps(void *maps_out, const __nv_bfloat16 *A_hi, const __nv_bfloat16 *A_lo, int64_t M_pad,
                   int n_kb_stage, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
-                  int N, char *errbuf, size_t errlen) {
+                  int N, int cluster, char *errbuf, size_t errlen) {
     TcMaps *m = reinterpret_cast<TcMaps *>(maps_out);
     memset(m, 0, sizeof(TcMaps));
-    m->nbox_b = N > 256 ? 2 : 1;
-    m->box_b_rows = N / m->nbox_b;
+    if (!tc_b_boxes(N, cluster, &m->box_b_rows, &m->nbox_b)) {
+        snprintf(errbuf, errlen, "tile of %d columns cannot be split over a cluster of %d", N, cluster);
+        return false;
+    }
     if (!encode3d(&m->a_hi, A_hi, 16, (uint64_t)M_pad, (uint64_t)n_kb_stage, kMTile, errbuf, errlen, "A_hi")) return false;
     if (!encode3d(&m->a_lo, A_lo, 16, (uint64_t)M_pad, (uint64_t)n_kb_stage, kMTile, errbuf, errlen, "A_lo")) return false;
     if (!encode3d(&m->b_hi, B_hi, 16, 2 * (uint64_t)Nw_pad, (uint64_t)n_kb_T, (uint32_t)m->box_b_rows, errbuf, errlen,
@@ -361,19 +449,53 @@ bool tc_make_maps(void *maps_out, const __nv_bfloat16 *A_hi, const __nv_bfloat16
     return true;
 }
 
-cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps, cudaStream_t st) {
-    static int configured_smem = 0;
-    const size_t smem = tc_smem_bytes(a.N, a.stages);
-    if ((int)smem > configured_smem) {
-        cudaError_t e = cudaFuncSetAttribute(flush_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured_smem = (int)smem;
+// Co-resident CTAs of the contraction kernel for a cluster size (0 on error).
+int tc_resident_ctas(int N, int stages, int cluster) {
+    const size_t smem = tc_smem_bytes(N, stages);
+    if (cudaFuncSetAttribute(flush_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
     }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster * 1024, 1, 1);
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, flush_tc_kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n * cluster;
+}
+
+cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps, cudaStream_t st) {
+    const size_t smem = tc_smem_bytes(a.N, a.stages);
+    cudaError_t e = cudaFuncSetAttribute(flush_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     const int64_t n_mt = a.e.M_pad / kMTile;
-    const int64_t blocks = n_mt * a.n_wt;
+    const int64_t n_mt_pad = (n_mt + a.cluster - 1) / a.cluster * a.cluster;
+    const int64_t blocks = n_mt_pad * a.n_wt;
     if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    flush_tc_kernel<<<(unsigned)blocks, 192, smem, st>>>(*reinterpret_cast<const TcMaps *>(maps), a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks, 1, 1);
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = a.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, flush_tc_kernel, *reinterpret_cast<const TcMaps *>(maps), a);
 }
 
 }  // namespace tacaw

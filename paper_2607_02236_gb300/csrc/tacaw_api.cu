@@ -75,6 +75,7 @@ struct Stream {
     float *adj_w = nullptr;
     int n_adj = 0;
     std::vector<unsigned char> tc_maps;
+    int tc_cluster = 1;
     // segment state
     int pushed = 0, staged = 0, stage_start = 0, flushes = 0;
     int64_t I_off = 0, S_off = 0;
@@ -86,6 +87,7 @@ struct tacaw_plan_s {
     std::vector<Stream> s;
     int prec = 0, accum = 0, k_stage = 0;
     int stages = 0;
+    int tc_acc = 3;
     int64_t bytes = 0;
     int64_t I_elems = 0, S_elems = 0;
     int64_t flushes_total = 0;
@@ -173,6 +175,32 @@ double bose_factor(double E, double TK) {
     return x / (-std::expm1(-x));
 }
 
+// Complex energies per tensor-core tile: every accumulator holds 2*wt real columns and all
+// of them must fit the 512 TMEM columns (one accumulator may span two 256-column MMAs).
+// Among multiples of 8 the width with the least padded work plus a fixed per-tile cost
+// (operand A is re-read once per energy tile) wins; a requested width is clamped.
+void choose_omega_tile(Stream &s, int n_acc, int requested) {
+    const int max_cols = n_acc > 1 ? 512 / n_acc : 512;
+    const int wt_max = std::max(8, (max_cols / 2) / 8 * 8);
+    int best = 8;
+    if (requested > 0) {
+        best = std::min(requested, wt_max);
+    } else {
+        int64_t best_cost = INT64_MAX;
+        for (int wt = 8; wt <= wt_max; wt += 8) {
+            const int64_t n = (s.Nw + wt - 1) / wt;
+            const int64_t cost = n * (wt + 24);
+            if (cost < best_cost || (cost == best_cost && wt > best)) {
+                best_cost = cost;
+                best = wt;
+            }
+        }
+    }
+    s.wt = best;
+    s.n_wt = (s.Nw + best - 1) / best;
+    s.Nw_pad = s.wt * s.n_wt;
+}
+
 // Staging + accumulator bytes of one stream for a given ring length.
 int64_t stream_stage_bytes(const Stream &s, int ring) { return s.M_pad * 8 * (int64_t)ring; }
 int64_t stream_acc_bytes(const Stream &s) { return (int64_t)s.Nw_pad * s.M_pad * 16; }
@@ -217,6 +245,9 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         a.n_kb = (n + 7) / 8;
         a.kbB0 = s.stage_start / 8;
         a.stages = p->stages;
+        a.split = p->tc_acc > 1 ? 1 : 0;
+        a.n_big = p->tc_acc == 3 ? 2 : 1;
+        a.cluster = s.tc_cluster;
         a.err = p->d_err;
         CU_CHECK(p, launch_flush_tc(a, s.tc_maps.data(), st), "flush (tensor cores)");
         p->launches++;
@@ -288,7 +319,7 @@ tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
         s.tc_maps.resize(tc_maps_size());
         char eb[256];
         if (!tc_make_maps(s.tc_maps.data(), s.A_hi, s.A_lo, s.M_pad, s.ring / 8, s.B_hi, s.B_lo, s.Nw_pad, s.n_kb_T,
-                          2 * s.wt, eb, sizeof(eb)))
+                          2 * s.wt, s.tc_cluster, eb, sizeof(eb)))
             return fail(TACAW_ERR_CUDA, "%s", eb);
     } else {
         const size_t na = (size_t)s.ring * s.M_pad;
@@ -409,8 +440,15 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         tacaw_status v = validate_stream(desc->streams[i], i);
         if (v != TACAW_OK) return v;
     }
+    if (desc->tc_accumulators < 0 || desc->tc_accumulators > 3)
+        return fail(TACAW_ERR_INVALID_ARG, "tc_accumulators must be 0 (auto), 1, 2 or 3");
+    if (desc->tc_cluster != 0 && desc->tc_cluster != 1 && desc->tc_cluster != 2 && desc->tc_cluster != 4)
+        return fail(TACAW_ERR_INVALID_ARG, "tc_cluster must be 0 (auto), 1, 2 or 4");
+    if (desc->tc_omega_tile < 0 || desc->tc_omega_tile % 8)
+        return fail(TACAW_ERR_INVALID_ARG, "tc_omega_tile must be a multiple of 8");
     tacaw_plan_s *p = new (std::nothrow) tacaw_plan_s();
     if (!p) return fail(TACAW_ERR_OOM, "host allocation failed");
+    p->tc_acc = desc->tc_accumulators ? desc->tc_accumulators : 3;
     p->prec = desc->precision;
     p->accum = desc->accum;
     int T_pad_max = 0;
@@ -427,9 +465,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         s.T_pad = (int)round_up(s.T, 8);
         s.n_kb_T = s.T_pad / 8;
         s.Nw = s.d.n_omega;
-        s.n_wt = (s.Nw + 255) / 256;
-        s.wt = (int)round_up((s.Nw + s.n_wt - 1) / s.n_wt, 8);
-        s.Nw_pad = s.wt * s.n_wt;
+        choose_omega_tile(s, p->tc_acc, desc->tc_omega_tile);
         if (p->prec == TACAW_PREC_FP32) s.Nw_pad = (int)round_up(s.Nw, 64);
         T_pad_max = std::max(T_pad_max, s.T_pad);
         p->s.push_back(s);
@@ -494,6 +530,31 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         if (p->stages < 2) {
             delete p;
             return fail(TACAW_ERR_UNSUPPORTED, "tensor-core tile of %d columns does not fit shared memory", maxN);
+        }
+        for (auto &s : p->s) {
+            const int N = 2 * s.wt;
+            int br, nb;
+            const int64_t n_mt = s.M_pad / kMTile;
+            if (desc->tc_cluster) {
+                s.tc_cluster = desc->tc_cluster;
+                if (!tc_b_boxes(N, s.tc_cluster, &br, &nb)) {
+                    delete p;
+                    return fail(TACAW_ERR_INVALID_ARG, "tile of %d columns cannot be split over a cluster of %d", N,
+                                s.tc_cluster);
+                }
+            } else {
+                // largest cluster that keeps (almost) every SM busy
+                const int r1 = tc_resident_ctas(N, p->stages, 1);
+                s.tc_cluster = 1;
+                for (int c : {4, 2}) {
+                    if (!tc_b_boxes(N, c, &br, &nb) || n_mt < 2 * c) continue;
+                    const int rc = tc_resident_ctas(N, p->stages, c);
+                    if (r1 > 0 && rc >= (int)(0.97 * r1)) {
+                        s.tc_cluster = c;
+                        break;
+                    }
+                }
+            }
         }
     }
     if (!dev_alloc(p, &p->d_err, 1)) {
@@ -648,6 +709,8 @@ tacaw_status tacaw_plan_get_info(tacaw_plan_t p, tacaw_plan_info *info) {
     info->omega_tile = p->s.empty() ? 0 : p->s[0].wt;
     info->stages = p->stages;
     info->kernel_launches = p->launches;
+    info->tc_accumulators = p->prec == TACAW_PREC_SPLIT_BF16 ? p->tc_acc : 0;
+    info->tc_cluster = (p->prec == TACAW_PREC_SPLIT_BF16 && !p->s.empty()) ? p->s[0].tc_cluster : 0;
     return TACAW_OK;
 }
 

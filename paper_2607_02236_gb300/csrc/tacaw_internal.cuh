@@ -174,6 +174,9 @@ struct TcPlanArgs {
     int n_kb;                  // staging blocks in this flush
     int kbB0;                  // first global twiddle block
     int stages;
+    int split;                 // 1: separate TMEM accumulators for hi*hi and hi*lo + lo*hi (N <= 256)
+    int n_big;                 // hi*hi accumulators (1 or 2, alternating by block parity)
+    int cluster;               // CTAs sharing (multicasting) one energy tile's B rows: 1, 2 or 4
     uint32_t *err;
 };
 struct TcMaps;                 // tensor maps (defined in k_tc_gemm.cu)
@@ -183,7 +186,9 @@ size_t tc_smem_bytes(int N, int stages);
 size_t tc_maps_size();
 bool tc_make_maps(void *maps_out, const __nv_bfloat16 *A_hi, const __nv_bfloat16 *A_lo, int64_t M_pad,
                   int n_kb_stage, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
-                  int N, char *errbuf, size_t errlen);
+                  int N, int cluster, char *errbuf, size_t errlen);
+bool tc_b_boxes(int N, int cluster, int *box_rows, int *nbox);
+int tc_resident_ctas(int N, int stages, int cluster);
 
 struct ApertureArgs {
     const float *I;            // [P][Nw][npix]

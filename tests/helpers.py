@@ -35,7 +35,7 @@ def oracle_kw(spec: StreamSpec):
 
 
 def run_gpu(spec: StreamSpec, frames: np.ndarray, precision: str, pushes=None, k_stage: int = 0,
-            accum: str = "kahan", want_psi: bool = False):
+            accum: str = "kahan", want_psi: bool = False, **plan_kw):
     """frames: [P, T, Ky, Kx] complex64 host array (ROI only). Returns I, S, Psi (numpy)."""
     import torch
     from paper_2607_02236_gb300 import TacawPlan
@@ -49,7 +49,7 @@ def run_gpu(spec: StreamSpec, frames: np.ndarray, precision: str, pushes=None, k
     I = torch.empty(P * Nw * Ky * Kx, dtype=torch.float32, device="cuda")
     S = torch.empty(max(1, P * D * Nw), dtype=torch.float32, device="cuda")
     Psi = torch.empty(P * Nw * Ky * Kx, dtype=torch.complex64, device="cuda") if want_psi else None
-    with TacawPlan([stream_config(spec)], precision=precision, accum=accum, k_stage=k_stage) as plan:
+    with TacawPlan([stream_config(spec)], precision=precision, accum=accum, k_stage=k_stage, **plan_kw) as plan:
         t = 0
         fb = P * Ky * Kx * 8
         for n in pushes:
