@@ -120,10 +120,13 @@ typedef struct {
      *   tc_omega_tile     complex energies per tile (multiple of 8)
      *   tc_accumulators   TMEM accumulators per tile: 1 (all products in one), 2 (hi*hi | small
      *                     terms), 3 (hi*hi alternating over two | small terms; default)
-     *   tc_cluster        CTAs per cluster sharing the twiddle rows by TMA multicast: 1, 2, 4 */
+     *   tc_cluster        CTAs per cluster sharing the twiddle rows by TMA multicast: 1, 2, 4
+     *   tc_block_frames   frames per staged operand row: 8, 16 or 32 (32-, 64-, 128-byte rows);
+     *                     k_stage must be a multiple of it */
     int tc_omega_tile;
     int tc_accumulators;
     int tc_cluster;
+    int tc_block_frames;
 } tacaw_plan_desc;
 
 typedef struct tacaw_plan_s *tacaw_plan_t;
@@ -141,6 +144,7 @@ typedef struct {
     int64_t kernel_launches;   /* kernels launched by push/finalize/backward since creation */
     int tc_accumulators;       /* TMEM accumulators per tile (split path) */
     int tc_cluster;            /* cluster size of the contraction (split path, first stream) */
+    int tc_block_frames;       /* frames per staged operand row (split path) */
 } tacaw_plan_info;
 
 /* Creates a plan: validates the descriptor, sizes and allocates device memory

@@ -57,8 +57,9 @@ __device__ __forceinline__ void split2(float2 r, uint32_t &hi, uint32_t &lo) {
     lo = pack_bf16x2(lr, li);
 }
 
-// Staged frame slot s (s0 + t) goes to block s/8, elements 2(s%8), 2(s%8)+1 of row m.
-__global__ void convert_split_kernel(FrameGeom g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
+// Staged frame slot s (s0 + t) goes to block s/bf, elements 2(s%bf), 2(s%bf)+1 of row m
+// (rows of 2*bf bf16 = 4*bf bytes; bf is 8, 16 or 32).
+__global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t M_pad, const float2 *mu_hat,
                                      double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= g.M) return;
@@ -77,12 +78,12 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int64_t M_pad, 
         si += r.y;
         uint32_t h, l;
         split2(r, h, l);
-        size_t o = ((size_t)(s >> 3) * M_pad + m) * 8 + (s & 7);   // in bf16x2 units
+        size_t o = ((size_t)(s / bf) * M_pad + m) * bf + (s % bf);   // in bf16x2 units
         Hi[o] = h;
         Lo[o] = l;
         ++t;
     }
-    // whole blocks: 8 frames -> one 32-byte row of hi and of lo
+    // groups of 8 frames -> 32 bytes of the row of hi and of lo
     for (; t + 8 <= n; t += 8) {
         float2 v[8];
 #pragma unroll
@@ -99,7 +100,7 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int64_t M_pad, 
         sr += br;
         si += bi;
         const int s = s0 + t;
-        size_t o = ((size_t)(s >> 3) * M_pad + m) * 8;
+        size_t o = ((size_t)(s / bf) * M_pad + m) * bf + (s % bf);
         uint4 *ph = reinterpret_cast<uint4 *>(Hi + o);
         uint4 *pl = reinterpret_cast<uint4 *>(Lo + o);
         ph[0] = make_uint4(h[0], h[1], h[2], h[3]);
@@ -116,7 +117,7 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int64_t M_pad, 
         si += r.y;
         uint32_t h, l;
         split2(r, h, l);
-        size_t o = ((size_t)(s >> 3) * M_pad + m) * 8 + (s & 7);
+        size_t o = ((size_t)(s / bf) * M_pad + m) * bf + (s % bf);
         Hi[o] = h;
         Lo[o] = l;
     }
@@ -162,13 +163,13 @@ __global__ void convert_fp32_kernel(FrameGeom g, int n, int s0, int64_t M_pad, c
     sum_res[m] = a;
 }
 
-// Zeroes staged slots [staged, next multiple of 8) of the last block, all M_pad rows.
-__global__ void zero_tail_split_kernel(int64_t M_pad, int staged, uint32_t *Hi, uint32_t *Lo) {
+// Zeroes staged slots [staged, next multiple of bf) of the last block, all M_pad rows.
+__global__ void zero_tail_split_kernel(int64_t M_pad, int staged, int bf, uint32_t *Hi, uint32_t *Lo) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M_pad) return;
-    const int blk = staged >> 3;
-    for (int tt = staged & 7; tt < 8; ++tt) {
-        size_t o = ((size_t)blk * M_pad + m) * 8 + tt;
+    const int blk = staged / bf;
+    for (int tt = staged % bf; tt < bf; ++tt) {
+        size_t o = ((size_t)blk * M_pad + m) * bf + tt;
         Hi[o] = 0u;
         Lo[o] = 0u;
     }
@@ -188,9 +189,9 @@ cudaError_t launch_mean(const FrameGeom &g, int n, float2 *mu_hat, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_convert_split(const FrameGeom &g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
+cudaError_t launch_convert_split(const FrameGeom &g, int n, int s0, int bf, int64_t M_pad, const float2 *mu_hat,
                                  double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, cudaStream_t st) {
-    convert_split_kernel<<<blocks_for(g.M, 256), 256, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo);
+    convert_split_kernel<<<blocks_for(g.M, 256), 256, 0, st>>>(g, n, s0, bf, M_pad, mu_hat, sum_res, A_hi, A_lo);
     return cudaGetLastError();
 }
 
@@ -200,10 +201,10 @@ cudaError_t launch_convert_fp32(const FrameGeom &g, int n, int s0, int64_t M_pad
     return cudaGetLastError();
 }
 
-cudaError_t launch_zero_tail_split(int64_t M_pad, int staged, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo,
+cudaError_t launch_zero_tail_split(int64_t M_pad, int staged, int bf, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo,
                                    cudaStream_t st) {
     zero_tail_split_kernel<<<blocks_for(M_pad, 256), 256, 0, st>>>(
-        M_pad, staged, reinterpret_cast<uint32_t *>(A_hi), reinterpret_cast<uint32_t *>(A_lo));
+        M_pad, staged, bf, reinterpret_cast<uint32_t *>(A_hi), reinterpret_cast<uint32_t *>(A_lo));
     return cudaGetLastError();
 }
 

@@ -54,8 +54,9 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-// One thread per (energy j < Nw_pad, frame t < T_pad).  Rows 2j and 2j+1 of block t/8
-// receive, at elements 2(t%8) and 2(t%8)+1, the real embedding of B = w_t exp(-i theta):
+// One thread per (energy j < Nw_pad, frame t < T_pad).  Rows 2j and 2j+1 of block t/bf
+// (rows of 2*bf bf16) receive, at elements 2(t%bf) and 2(t%bf)+1, the real embedding of
+// B = w_t exp(-i theta):
 //   row 2j   : ( Re B, -Im B)  ->  Re Psi_j = Re psi Re B - Im psi Im B
 //   row 2j+1 : ( Im B,  Re B)  ->  Im Psi_j = Re psi Im B + Im psi Re B
 __global__ void twiddles_split_kernel(TableArgs a, __nv_bfloat16 *B_hi, __nv_bfloat16 *B_lo) {
@@ -70,10 +71,11 @@ __global__ void twiddles_split_kernel(TableArgs a, __nv_bfloat16 *B_hi, __nv_bfl
         br = w * c;
         bi = -w * s;
     }
-    const int kb = t >> 3, tt = t & 7;
+    const int bf = a.block_frames;
+    const int kb = t / bf, tt = t % bf;
     const size_t rows = 2 * (size_t)a.Nw_pad;
-    const size_t r0 = ((size_t)kb * rows + 2 * (size_t)j) * 16 + 2 * tt;
-    const size_t r1 = r0 + 16;
+    const size_t r0 = ((size_t)kb * rows + 2 * (size_t)j) * (2 * bf) + 2 * tt;
+    const size_t r1 = r0 + 2 * bf;
     float v0[2] = {(float)br, (float)(-bi)};
     float v1[2] = {(float)bi, (float)br};
     for (int e = 0; e < 2; ++e) {

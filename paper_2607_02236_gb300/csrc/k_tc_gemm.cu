@@ -14,10 +14,13 @@
 // accumulate step short relative to its own sum; the epilogue adds the three.
 //
 // CTA = 128 rows (one TMEM lane each) x N real columns (2*wt complex energies).
-//   warp 0      TMA producer: per 8-frame block, A_hi/A_lo boxes [128 x 16] and this CTA's
-//               share of the B_hi/B_lo rows (bf16, 32-byte rows, 32B swizzle) into an s-stage
-//               ring; with a cluster of C CTAs (same energy tile, C consecutive row tiles)
-//               each CTA loads N/C rows of B and multicasts them to the whole cluster
+//   warp 0      TMA producer: per staging block of bf frames (8, 16 or 32), A_hi/A_lo boxes
+//               [128 x 2bf] and this CTA's share of the B_hi/B_lo rows (bf16 rows of 32, 64
+//               or 128 bytes with the matching 32B/64B/128B swizzle) into an s-stage ring;
+//               with a cluster of C CTAs (same energy tile, C consecutive row tiles) each
+//               CTA loads N/C rows of B and multicasts them to the whole cluster
+//               Each stage holds bf/8 MMA K-steps of K=16: the descriptors of step k start
+//               32*k bytes into the swizzled rows.
 //   warp 1      TMEM allocator + single-thread MMA issuer; tcgen05.commit releases ring
 //               slots in every CTA of the cluster
 //   warps 2..5  epilogue: tcgen05.ld of the accumulators (warp w reads lanes 32*(w%4)..)
@@ -41,7 +44,6 @@ struct TcMaps {
 
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s per wait
 constexpr int kMaxStages = 12;
-constexpr uint32_t kABytes = kMTile * 32;          // 128 rows x 16 bf16
 constexpr int kSmemLimit = 232448;                 // 227 KB opt-in per block
 
 struct TcShared {
@@ -156,17 +158,18 @@ __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Shared-memory matrix descriptor, K-major operand with 32-byte swizzle: rows of 32 bytes,
-// 8-row core groups 256 bytes apart (stride byte offset), descriptor version 1 (bit 46),
-// layout type 6 = SWIZZLE_32B (bits 61-63).  The leading byte offset is unused for a
-// K extent of one swizzle atom.
-__device__ __forceinline__ uint64_t sdesc_k_sw32(uint32_t saddr) {
+// Shared-memory matrix descriptor, K-major operand whose rows are one swizzle atom wide
+// (32, 64 or 128 bytes): 8-row core groups 8*row_bytes apart (stride byte offset),
+// descriptor version 1 (bit 46), layout type (bits 61-63) 6 = SWIZZLE_32B, 4 = 64B,
+// 2 = 128B.  The leading byte offset is unused when the K extent stays inside one atom.
+__device__ __forceinline__ uint64_t sdesc_k(uint32_t saddr, uint32_t row_bytes) {
+    const uint64_t layout = row_bytes == 128 ? 2 : (row_bytes == 64 ? 4 : 6);
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(256 >> 4) << 32;
+    d |= (uint64_t)((8u * row_bytes) >> 4) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)6 << 61;
+    d |= layout << 61;
     return d;
 }
 // Instruction descriptor, kind::f16: D = F32 (bit 4), A = B = BF16 (bits 7, 10), both
@@ -175,8 +178,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__host__ __device__ inline uint32_t tc_b_bytes_padded(int N) { return ((uint32_t)N * 32u + 1023u) & ~1023u; }
-__host__ __device__ inline uint32_t tc_stage_bytes(int N) { return 2u * kABytes + 2u * tc_b_bytes_padded(N); }
+__host__ __device__ inline uint32_t tc_a_bytes(int bf) { return (uint32_t)kMTile * 4u * (uint32_t)bf; }
+__host__ __device__ inline uint32_t tc_b_bytes_padded(int N, int bf) {
+    return ((uint32_t)N * 4u * (uint32_t)bf + 1023u) & ~1023u;
+}
+__host__ __device__ inline uint32_t tc_stage_bytes(int N, int bf) { return 2u * tc_a_bytes(bf) + 2u * tc_b_bytes_padded(N, bf); }
 __host__ __device__ inline uint32_t tc_tmem_cols(int N) {
     uint32_t c = 32;
     while (c < (uint32_t)N) c <<= 1;
@@ -186,8 +192,10 @@ __host__ __device__ inline uint32_t tc_tmem_cols(int N) {
 __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant__ TcMaps maps, const TcPlanArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const uint32_t b_pad = tc_b_bytes_padded(a.N);
-    const uint32_t stage_bytes = tc_stage_bytes(a.N);
+    const uint32_t RB = 4u * (uint32_t)a.bf;           // bytes per operand row
+    const uint32_t kABytes = tc_a_bytes(a.bf);
+    const uint32_t b_pad = tc_b_bytes_padded(a.N, a.bf);
+    const uint32_t stage_bytes = tc_stage_bytes(a.N, a.bf);
     TcShared *sh = reinterpret_cast<TcShared *>(base + (size_t)a.stages * stage_bytes);
     const uint32_t base_s = smem_u32(base);
 
@@ -199,7 +207,7 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
     const int m0 = ((int)(cid / (unsigned)a.n_wt) * C + (int)crank) * kMTile;
     const int n_acc = a.split ? a.n_big + 1 : 1;
     const uint32_t ncols = tc_tmem_cols(n_acc * a.N);
-    const uint32_t tx_bytes = 2u * kABytes + 2u * (uint32_t)a.N * 32u;
+    const uint32_t tx_bytes = 2u * kABytes + 2u * (uint32_t)a.N * RB;
     const int rows_cta = a.N / C;                 // B rows this CTA loads (for the whole cluster)
     const uint16_t cmask = (uint16_t)((1u << C) - 1u);
 
@@ -242,7 +250,7 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
                 for (int b = 0; b < maps.nbox_b; ++b) {
                     const int r0 = (int)crank * rows_cta + b * maps.box_b_rows;
                     const int row = wtile * a.N + r0;
-                    const uint32_t off = (uint32_t)r0 * 32u;
+                    const uint32_t off = (uint32_t)r0 * RB;
                     if (C > 1) {
                         tma_load_3d_mc(st + 2 * kABytes + off, &maps.b_hi, 0, row, a.kbB0 + kb, full, cmask);
                         tma_load_3d_mc(st + 2 * kABytes + b_pad + off, &maps.b_lo, 0, row, a.kbB0 + kb, full, cmask);
@@ -269,8 +277,9 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
             const int n1 = a.N - n0;
             const uint32_t id0 = idesc_bf16_f32(kMTile, n0);
             const uint32_t id1 = n1 > 0 ? idesc_bf16_f32(kMTile, n1) : 0u;
-            const uint64_t b_half_off = (uint64_t)((n0 * 32) >> 4);
+            const uint64_t b_half_off = (uint64_t)((n0 * RB) >> 4);
             const uint32_t acc_small = tmem + (uint32_t)(a.n_big * a.N);
+            const int ksteps = a.bf / 8;
             for (int kb = 0; kb < a.n_kb; ++kb) {
                 const int s = kb % a.stages;
                 const uint32_t use = (uint32_t)(kb / a.stages);
@@ -281,24 +290,30 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
                 }
                 tc_fence_after();
                 const uint32_t st = base_s + (uint32_t)s * stage_bytes;
-                const uint64_t dAhi = sdesc_k_sw32(st);
-                const uint64_t dAlo = sdesc_k_sw32(st + kABytes);
-                const uint64_t dBhi = sdesc_k_sw32(st + 2 * kABytes);
-                const uint64_t dBlo = sdesc_k_sw32(st + 2 * kABytes + b_pad);
-                if (a.split) {
-                    // N <= 256: one MMA per product
-                    const int big = a.n_big == 2 ? (kb & 1) : 0;
-                    mma_bf16_ss(tmem + (uint32_t)(big * a.N), dAhi, dBhi, id0, kb >= a.n_big ? 1u : 0u);
-                    mma_bf16_ss(acc_small, dAhi, dBlo, id0, kb > 0 ? 1u : 0u);
-                    mma_bf16_ss(acc_small, dAlo, dBhi, id0, 1u);
-                } else {
+                const uint64_t dAhi0 = sdesc_k(st, RB);
+                const uint64_t dAlo0 = sdesc_k(st + kABytes, RB);
+                const uint64_t dBhi0 = sdesc_k(st + 2 * kABytes, RB);
+                const uint64_t dBlo0 = sdesc_k(st + 2 * kABytes + b_pad, RB);
+                for (int ks = 0; ks < ksteps; ++ks) {
+                    // K-step ks starts 32*ks bytes into the swizzled rows (start address in 16 B units)
+                    const uint64_t adv = (uint64_t)(2 * ks);
+                    const uint64_t dAhi = dAhi0 + adv, dAlo = dAlo0 + adv, dBhi = dBhi0 + adv, dBlo = dBlo0 + adv;
+                    const int g = kb * ksteps + ks;       // global K-step index
+                    if (a.split) {
+                        // N <= 256: one MMA per product
+                        const int big = a.n_big == 2 ? (g & 1) : 0;
+                        mma_bf16_ss(tmem + (uint32_t)(big * a.N), dAhi, dBhi, id0, g >= a.n_big ? 1u : 0u);
+                        mma_bf16_ss(acc_small, dAhi, dBlo, id0, g > 0 ? 1u : 0u);
+                        mma_bf16_ss(acc_small, dAlo, dBhi, id0, 1u);
+                    } else {
 #pragma unroll
-                    for (int pass = 0; pass < 3; ++pass) {
-                        const uint64_t dA = pass == 2 ? dAlo : dAhi;
-                        const uint64_t dB = pass == 1 ? dBlo : dBhi;
-                        const uint32_t acc = (kb > 0 || pass > 0) ? 1u : 0u;
-                        mma_bf16_ss(tmem, dA, dB, id0, acc);
-                        if (n1 > 0) mma_bf16_ss(tmem + (uint32_t)n0, dA, dB + b_half_off, id1, acc);
+                        for (int pass = 0; pass < 3; ++pass) {
+                            const uint64_t dA = pass == 2 ? dAlo : dAhi;
+                            const uint64_t dB = pass == 1 ? dBlo : dBhi;
+                            const uint32_t acc = (g > 0 || pass > 0) ? 1u : 0u;
+                            mma_bf16_ss(tmem, dA, dB, id0, acc);
+                            if (n1 > 0) mma_bf16_ss(tmem + (uint32_t)n0, dA, dB + b_half_off, id1, acc);
+                        }
                     }
                 }
                 if (C > 1)
@@ -323,7 +338,8 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
             const RowCtx row = make_row(a.e, m);
             const int jbase = wtile * a.wt;
             const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-            const int n_big_used = a.split ? (a.n_kb < a.n_big ? a.n_kb : a.n_big) : 0;
+            const int total_steps = a.n_kb * (a.bf / 8);
+            const int n_big_used = a.split ? (total_steps < a.n_big ? total_steps : a.n_big) : 0;
             for (int c0 = 0; c0 < a.N; c0 += 16) {
                 uint32_t r[16];
                 float v[16];
@@ -365,15 +381,15 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
 // --------------------------------------------------------------------------------------
 // host side
 // --------------------------------------------------------------------------------------
-int tc_stages_for(int N) {
+int tc_stages_for(int N, int bf) {
     const int budget = kSmemLimit - 1024 - (int)sizeof(TcShared);
-    int s = budget / (int)tc_stage_bytes(N);
+    int s = budget / (int)tc_stage_bytes(N, bf);
     if (s > kMaxStages) s = kMaxStages;
     return s;
 }
 
-size_t tc_smem_bytes(int N, int stages) {
-    return (size_t)stages * tc_stage_bytes(N) + sizeof(TcShared) + 1024;
+size_t tc_smem_bytes(int N, int bf, int stages) {
+    return (size_t)stages * tc_stage_bytes(N, bf) + sizeof(TcShared) + 1024;
 }
 
 size_t tc_maps_size() { return sizeof(TcMaps); }
@@ -397,6 +413,9 @@ static EncodeTiledFn encode_fn() {
 
 static bool encode3d(CUtensorMap *m, const void *ptr, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b1,
                      char *errbuf, size_t errlen, const char *what) {
+    // d0 bf16 elements per row: 16, 32 or 64 -> rows of 32, 64 or 128 bytes, swizzled alike
+    const CUtensorMapSwizzle sw = d0 == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                           : (d0 == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
     EncodeTiledFn fn = encode_fn();
     if (!fn) {
         snprintf(errbuf, errlen, "cuTensorMapEncodeTiled is not available from the driver");
@@ -407,7 +426,7 @@ static bool encode3d(CUtensorMap *m, const void *ptr, uint64_t d0, uint64_t d1, 
     cuuint32_t box[3] = {(cuuint32_t)d0, b1, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(ptr), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         snprintf(errbuf, errlen, "cuTensorMapEncodeTiled(%s) failed with %d", what, (int)r);
@@ -431,27 +450,28 @@ bool tc_b_boxes(int N, int cluster, int *box_rows, int *nbox) {
 
 bool tc_make_maps(void *maps_out, const __nv_bfloat16 *A_hi, const __nv_bfloat16 *A_lo, int64_t M_pad,
                   int n_kb_stage, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
-                  int N, int cluster, char *errbuf, size_t errlen) {
+                  int N, int cluster, int bf, char *errbuf, size_t errlen) {
     TcMaps *m = reinterpret_cast<TcMaps *>(maps_out);
+    const uint64_t d0 = 2 * (uint64_t)bf;
     memset(m, 0, sizeof(TcMaps));
     if (!tc_b_boxes(N, cluster, &m->box_b_rows, &m->nbox_b)) {
         snprintf(errbuf, errlen, "tile of %d columns cannot be split over a cluster of %d", N, cluster);
         return false;
     }
-    if (!encode3d(&m->a_hi, A_hi, 16, (uint64_t)M_pad, (uint64_t)n_kb_stage, kMTile, errbuf, errlen, "A_hi")) return false;
-    if (!encode3d(&m->a_lo, A_lo, 16, (uint64_t)M_pad, (uint64_t)n_kb_stage, kMTile, errbuf, errlen, "A_lo")) return false;
-    if (!encode3d(&m->b_hi, B_hi, 16, 2 * (uint64_t)Nw_pad, (uint64_t)n_kb_T, (uint32_t)m->box_b_rows, errbuf, errlen,
+    if (!encode3d(&m->a_hi, A_hi, d0, (uint64_t)M_pad, (uint64_t)n_kb_stage, kMTile, errbuf, errlen, "A_hi")) return false;
+    if (!encode3d(&m->a_lo, A_lo, d0, (uint64_t)M_pad, (uint64_t)n_kb_stage, kMTile, errbuf, errlen, "A_lo")) return false;
+    if (!encode3d(&m->b_hi, B_hi, d0, 2 * (uint64_t)Nw_pad, (uint64_t)n_kb_T, (uint32_t)m->box_b_rows, errbuf, errlen,
                   "B_hi"))
         return false;
-    if (!encode3d(&m->b_lo, B_lo, 16, 2 * (uint64_t)Nw_pad, (uint64_t)n_kb_T, (uint32_t)m->box_b_rows, errbuf, errlen,
+    if (!encode3d(&m->b_lo, B_lo, d0, 2 * (uint64_t)Nw_pad, (uint64_t)n_kb_T, (uint32_t)m->box_b_rows, errbuf, errlen,
                   "B_lo"))
         return false;
     return true;
 }
 
 // Co-resident CTAs of the contraction kernel for a cluster size (0 on error).
-int tc_resident_ctas(int N, int stages, int cluster) {
-    const size_t smem = tc_smem_bytes(N, stages);
+int tc_resident_ctas(int N, int bf, int stages, int cluster) {
+    const size_t smem = tc_smem_bytes(N, bf, stages);
     if (cudaFuncSetAttribute(flush_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -476,7 +496,7 @@ int tc_resident_ctas(int N, int stages, int cluster) {
 }
 
 cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps, cudaStream_t st) {
-    const size_t smem = tc_smem_bytes(a.N, a.stages);
+    const size_t smem = tc_smem_bytes(a.N, a.bf, a.stages);
     cudaError_t e = cudaFuncSetAttribute(flush_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t n_mt = a.e.M_pad / kMTile;

@@ -88,6 +88,7 @@ struct tacaw_plan_s {
     int prec = 0, accum = 0, k_stage = 0;
     int stages = 0;
     int tc_acc = 3;
+    int bf = 8;                // frames per staged operand row (split path)
     int64_t bytes = 0;
     int64_t I_elems = 0, S_elems = 0;
     int64_t flushes_total = 0;
@@ -233,8 +234,8 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         CU_CHECK(p, cudaEventRecord(e0, st), "cudaEventRecord");
     }
     if (p->prec == TACAW_PREC_SPLIT_BF16) {
-        if (n & 7) {
-            CU_CHECK(p, launch_zero_tail_split(s.M_pad, n, s.A_hi, s.A_lo, st), "zero_tail");
+        if (n % p->bf) {
+            CU_CHECK(p, launch_zero_tail_split(s.M_pad, n, p->bf, s.A_hi, s.A_lo, st), "zero_tail");
             p->launches++;
         }
         TcPlanArgs a{};
@@ -242,8 +243,9 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         a.wt = s.wt;
         a.n_wt = s.n_wt;
         a.N = 2 * s.wt;
-        a.n_kb = (n + 7) / 8;
-        a.kbB0 = s.stage_start / 8;
+        a.n_kb = (n + p->bf - 1) / p->bf;
+        a.kbB0 = s.stage_start / p->bf;
+        a.bf = p->bf;
         a.stages = p->stages;
         a.split = p->tc_acc > 1 ? 1 : 0;
         a.n_big = p->tc_acc == 3 ? 2 : 1;
@@ -283,6 +285,7 @@ tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
     ta.window = d.window;
     ta.window_param = d.window_param;
     ta.fft_bins = d.fft_bins;
+    ta.block_frames = p->bf;
     // cycles per frame c_j = E_j dt / h (FP64)
     std::vector<double> cj(s.Nw), E(s.Nw);
     for (int j = 0; j < s.Nw; ++j) {
@@ -308,18 +311,18 @@ tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
     if (!dev_alloc(p, &s.B32, (size_t)s.T_pad * s.Nw_pad)) return fail(TACAW_ERR_OOM, "cudaMalloc(B32)");
     CU_CHECK(p, launch_twiddles_fp32(ta, s.B32, st), "twiddles fp32");
     if (p->prec == TACAW_PREC_SPLIT_BF16) {
-        const size_t nb = (size_t)s.n_kb_T * 2 * s.Nw_pad * 16;
+        const size_t nb = (size_t)s.n_kb_T * 2 * s.Nw_pad * 2 * p->bf;
         if (!dev_alloc(p, &s.B_hi, nb) || !dev_alloc(p, &s.B_lo, nb)) return fail(TACAW_ERR_OOM, "cudaMalloc(B split)");
         CU_CHECK(p, launch_twiddles_split(ta, s.B_hi, s.B_lo, st), "twiddles split");
-        const size_t na = (size_t)(s.ring / 8) * s.M_pad * 16;
+        const size_t na = (size_t)(s.ring / p->bf) * s.M_pad * 2 * p->bf;
         if (!dev_alloc(p, &s.A_hi, na) || !dev_alloc(p, &s.A_lo, na)) return fail(TACAW_ERR_OOM, "cudaMalloc(staging)");
         // rows >= M and never-written slots must read as zeros
         CU_CHECK(p, cudaMemsetAsync(s.A_hi, 0, na * sizeof(__nv_bfloat16), st), "memset staging");
         CU_CHECK(p, cudaMemsetAsync(s.A_lo, 0, na * sizeof(__nv_bfloat16), st), "memset staging");
         s.tc_maps.resize(tc_maps_size());
         char eb[256];
-        if (!tc_make_maps(s.tc_maps.data(), s.A_hi, s.A_lo, s.M_pad, s.ring / 8, s.B_hi, s.B_lo, s.Nw_pad, s.n_kb_T,
-                          2 * s.wt, s.tc_cluster, eb, sizeof(eb)))
+        if (!tc_make_maps(s.tc_maps.data(), s.A_hi, s.A_lo, s.M_pad, s.ring / p->bf, s.B_hi, s.B_lo, s.Nw_pad,
+                          s.n_kb_T, 2 * s.wt, s.tc_cluster, p->bf, eb, sizeof(eb)))
             return fail(TACAW_ERR_CUDA, "%s", eb);
     } else {
         const size_t na = (size_t)s.ring * s.M_pad;
@@ -446,9 +449,23 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         return fail(TACAW_ERR_INVALID_ARG, "tc_cluster must be 0 (auto), 1, 2 or 4");
     if (desc->tc_omega_tile < 0 || desc->tc_omega_tile % 8)
         return fail(TACAW_ERR_INVALID_ARG, "tc_omega_tile must be a multiple of 8");
+    if (desc->tc_block_frames != 0 && desc->tc_block_frames != 8 && desc->tc_block_frames != 16 &&
+        desc->tc_block_frames != 32)
+        return fail(TACAW_ERR_INVALID_ARG, "tc_block_frames must be 0 (auto), 8, 16 or 32");
+    if (desc->precision == TACAW_PREC_SPLIT_BF16 && desc->tc_block_frames && desc->k_stage % desc->tc_block_frames)
+        return fail(TACAW_ERR_INVALID_ARG, "k_stage must be a multiple of tc_block_frames");
     tacaw_plan_s *p = new (std::nothrow) tacaw_plan_s();
     if (!p) return fail(TACAW_ERR_OOM, "host allocation failed");
     p->tc_acc = desc->tc_accumulators ? desc->tc_accumulators : 3;
+    if (desc->precision == TACAW_PREC_SPLIT_BF16) {
+        // widest rows first: fewer, larger TMA requests per MMA K-step
+        if (desc->tc_block_frames) {
+            p->bf = desc->tc_block_frames;
+        } else {
+            p->bf = 32;
+            while (p->bf > 8 && desc->k_stage % p->bf) p->bf /= 2;
+        }
+    }
     p->prec = desc->precision;
     p->accum = desc->accum;
     int T_pad_max = 0;
@@ -462,8 +479,8 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         s.M = (int64_t)s.d.n_probes * s.npix;
         s.M_pad = round_up(s.M, kMTile);
         s.T = s.d.T;
-        s.T_pad = (int)round_up(s.T, 8);
-        s.n_kb_T = s.T_pad / 8;
+        s.T_pad = (int)round_up(s.T, p->prec == TACAW_PREC_SPLIT_BF16 ? p->bf : 8);
+        s.n_kb_T = s.T_pad / (p->prec == TACAW_PREC_SPLIT_BF16 ? p->bf : 8);
         s.Nw = s.d.n_omega;
         choose_omega_tile(s, p->tc_acc, desc->tc_omega_tile);
         if (p->prec == TACAW_PREC_FP32) s.Nw_pad = (int)round_up(s.Nw, 64);
@@ -503,7 +520,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
             K = T_pad_max;
         } else {
             K = 0;
-            for (int k = (T_pad_max / 64) * 64; k >= 64; k -= 64)
+            for (int k = (T_pad_max / 64) * 64; k >= 64; k -= 64)  // multiples of 64: any block size divides
                 if (need(k) <= budget) {
                     K = k;
                     break;
@@ -526,7 +543,11 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         maxN = std::max(maxN, 2 * s.wt);
     }
     if (p->prec == TACAW_PREC_SPLIT_BF16) {
-        p->stages = tc_stages_for(maxN);
+        // keep at least 3 stages: narrow the block when the widest one leaves fewer
+        if (!desc->tc_block_frames)
+            while (p->bf > 8 && tc_stages_for(maxN, p->bf) < 3) p->bf /= 2;
+        p->stages = tc_stages_for(maxN, p->bf);
+        for (auto &s : p->s) s.n_kb_T = s.T_pad / p->bf;
         if (p->stages < 2) {
             delete p;
             return fail(TACAW_ERR_UNSUPPORTED, "tensor-core tile of %d columns does not fit shared memory", maxN);
@@ -544,11 +565,11 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
                 }
             } else {
                 // largest cluster that keeps (almost) every SM busy
-                const int r1 = tc_resident_ctas(N, p->stages, 1);
+                const int r1 = tc_resident_ctas(N, p->bf, p->stages, 1);
                 s.tc_cluster = 1;
                 for (int c : {4, 2}) {
                     if (!tc_b_boxes(N, c, &br, &nb) || n_mt < 2 * c) continue;
-                    const int rc = tc_resident_ctas(N, p->stages, c);
+                    const int rc = tc_resident_ctas(N, p->bf, p->stages, c);
                     if (r1 > 0 && rc >= (int)(0.97 * r1)) {
                         s.tc_cluster = c;
                         break;
@@ -625,7 +646,7 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
         FrameGeom gc = g;
         gc.base = g.base + (int64_t)done * g.pitch_frame;
         if (p->prec == TACAW_PREC_SPLIT_BF16)
-            CU_CHECK(p, launch_convert_split(gc, chunk, s.staged, s.M_pad, s.mu_hat, s.sum_res, s.A_hi, s.A_lo, st),
+            CU_CHECK(p, launch_convert_split(gc, chunk, s.staged, p->bf, s.M_pad, s.mu_hat, s.sum_res, s.A_hi, s.A_lo, st),
                      "convert");
         else
             CU_CHECK(p, launch_convert_fp32(gc, chunk, s.staged, s.M_pad, s.mu_hat, s.sum_res, s.A32, st), "convert");
@@ -711,6 +732,7 @@ tacaw_status tacaw_plan_get_info(tacaw_plan_t p, tacaw_plan_info *info) {
     info->kernel_launches = p->launches;
     info->tc_accumulators = p->prec == TACAW_PREC_SPLIT_BF16 ? p->tc_acc : 0;
     info->tc_cluster = (p->prec == TACAW_PREC_SPLIT_BF16 && !p->s.empty()) ? p->s[0].tc_cluster : 0;
+    info->tc_block_frames = p->prec == TACAW_PREC_SPLIT_BF16 ? p->bf : 0;
     return TACAW_OK;
 }
 

@@ -2,10 +2,11 @@
 //
 // Data layout in HBM (per stream; M = P*ky*kx rows, one row per (probe, ROI pixel),
 // M_pad = M rounded up to 128; Nw_pad = n_wt * wt energies):
-//   staging, split path   A_hi, A_lo  bf16 [kb][M_pad][16]   kb = staged frame / 8;
-//                         element 2*(f%8)+0 = Re(psi - mu_hat), +1 = Im(...)
+//   staging, split path   A_hi, A_lo  bf16 [kb][M_pad][2*bf] kb = staged frame / bf (bf = 8, 16
+//                         or 32 frames per block: 32-, 64- or 128-byte rows);
+//                         element 2*(f%bf)+0 = Re(psi - mu_hat), +1 = Im(...)
 //   staging, FP32 path    A32        float2 [K_stage][M_pad]
-//   twiddles, split path  B_hi, B_lo  bf16 [kbT][2*Nw_pad][16] kbT = t / 8; rows 2j, 2j+1
+//   twiddles, split path  B_hi, B_lo  bf16 [kbT][2*Nw_pad][2*bf] kbT = t / bf; rows 2j, 2j+1
 //                         hold the real embedding of w_t exp(-i theta_jt) so that
 //                         [Re psi, Im psi] . rows gives [Re Psi_j, Im Psi_j]
 //   twiddles, FP32 path   B32        float2 [T_pad][Nw_pad]
@@ -20,7 +21,6 @@
 namespace tacaw {
 
 constexpr double kPlanck_meV_ps = 4.135667696;
-constexpr int kBlockFrames = 8;      // frames per staging block: 16 bf16 = one 32-byte row
 constexpr int kMTile = 128;          // rows per tensor-core tile (TMEM lanes)
 
 enum FlushMode : int { FLUSH_STORE = 0, FLUSH_ADD = 1, FLUSH_FINAL = 2 };
@@ -141,6 +141,7 @@ struct TableArgs {
     double window_param;
     int fft_bins;
     const double *cj;          // device, cycles per frame per energy (explicit grid)
+    int block_frames;          // split-path staging block (8, 16 or 32 frames)
 };
 
 cudaError_t launch_twiddles_split(const TableArgs &t, __nv_bfloat16 *B_hi, __nv_bfloat16 *B_lo, cudaStream_t st);
@@ -149,11 +150,11 @@ cudaError_t launch_window_transform(const TableArgs &t, float2 *Wc, cudaStream_t
 cudaError_t launch_window_values(const TableArgs &t, float *w, cudaStream_t st);
 
 cudaError_t launch_mean(const FrameGeom &g, int n, float2 *mu_hat, cudaStream_t st);
-cudaError_t launch_convert_split(const FrameGeom &g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
+cudaError_t launch_convert_split(const FrameGeom &g, int n, int s0, int bf, int64_t M_pad, const float2 *mu_hat,
                                  double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, cudaStream_t st);
 cudaError_t launch_convert_fp32(const FrameGeom &g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
                                 double2 *sum_res, float2 *A32, cudaStream_t st);
-cudaError_t launch_zero_tail_split(int64_t M_pad, int staged, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo,
+cudaError_t launch_zero_tail_split(int64_t M_pad, int staged, int bf, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo,
                                    cudaStream_t st);
 cudaError_t launch_mean_residual(int64_t M, int T, int subtract_mean, const double2 *sum_res, float2 *dmu,
                                  cudaStream_t st);
@@ -173,6 +174,7 @@ struct TcPlanArgs {
     int wt, n_wt, N;           // complex energies per tile, tiles, real columns per tile (2*wt)
     int n_kb;                  // staging blocks in this flush
     int kbB0;                  // first global twiddle block
+    int bf;                    // frames per staging block (8, 16, 32): rows of 4*bf bytes
     int stages;
     int split;                 // 1: separate TMEM accumulators for hi*hi and hi*lo + lo*hi (N <= 256)
     int n_big;                 // hi*hi accumulators (1 or 2, alternating by block parity)
@@ -181,14 +183,14 @@ struct TcPlanArgs {
 };
 struct TcMaps;                 // tensor maps (defined in k_tc_gemm.cu)
 cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps /* TcMaps */, cudaStream_t st);
-int tc_stages_for(int N);
-size_t tc_smem_bytes(int N, int stages);
+int tc_stages_for(int N, int bf);
+size_t tc_smem_bytes(int N, int bf, int stages);
 size_t tc_maps_size();
 bool tc_make_maps(void *maps_out, const __nv_bfloat16 *A_hi, const __nv_bfloat16 *A_lo, int64_t M_pad,
                   int n_kb_stage, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
-                  int N, int cluster, char *errbuf, size_t errlen);
+                  int N, int cluster, int bf, char *errbuf, size_t errlen);
 bool tc_b_boxes(int N, int cluster, int *box_rows, int *nbox);
-int tc_resident_ctas(int N, int stages, int cluster);
+int tc_resident_ctas(int N, int bf, int stages, int cluster);
 
 struct ApertureArgs {
     const float *I;            // [P][Nw][npix]

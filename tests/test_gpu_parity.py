@@ -127,14 +127,18 @@ def test_errors_overflow_and_state():
         plan.finalize(I)
 
 
-TILINGS = [(1, 1, 0), (1, 2, 0), (2, 1, 0), (2, 2, 0), (3, 1, 0), (3, 2, 0), (3, 4, 0), (3, 4, 16), (3, 2, 24)]
+TILINGS = [(1, 1, 0, 8), (1, 2, 0, 16), (2, 1, 0, 32), (2, 2, 0, 16), (3, 1, 0, 8), (3, 2, 0, 32),
+           (3, 4, 0, 32), (3, 4, 16, 16), (3, 2, 24, 8), (1, 2, 200, 16), (2, 4, 128, 32)]
 
 
-@pytest.mark.parametrize("acc,cluster,wt", TILINGS)
-def test_tensor_core_tilings(acc, cluster, wt):
-    """Every accumulator split / multicast cluster / energy-tile width gives the oracle's result."""
-    spec = StreamSpec(P=2, Kx=64, Ky=48, T=160, Tc=40, n_omega=150, E_max_meV=120.0, window="hann", n_modes=6,
+@pytest.mark.parametrize("acc,cluster,wt,bf", TILINGS)
+def test_tensor_core_tilings(acc, cluster, wt, bf):
+    """Every accumulator split / multicast cluster / energy-tile width / staging row width gives
+    the oracle's result (T=168 is not a multiple of 32: the last block has a zeroed tail)."""
+    spec = StreamSpec(P=2, Kx=64, Ky=48, T=168, Tc=40, n_omega=150, E_max_meV=120.0, window="hann", n_modes=6,
                       noise=1e-3, detectors=(Detector("circular", 0, 0, -1, 6.0),))
     fr = frames.frames(spec, 8, 0, spec.T)
-    out, ref, e = check(spec, fr, "split_bf16", tc_accumulators=acc, tc_cluster=cluster, tc_omega_tile=wt)
-    assert out["info"]["tc_accumulators"] == acc and out["info"]["tc_cluster"] == cluster
+    out, ref, e = check(spec, fr, "split_bf16", tc_accumulators=acc, tc_cluster=cluster, tc_omega_tile=wt,
+                        tc_block_frames=bf)
+    info = out["info"]
+    assert (info["tc_accumulators"], info["tc_cluster"], info["tc_block_frames"]) == (acc, cluster, bf)
