@@ -7,7 +7,7 @@
 // then applies the exact linear correction -(mu - mu_hat) W(E_j) to Psi.
 //
 // One thread per (probe, ROI pixel) row; consecutive threads read consecutive pixels of
-// a frame row (coalesced 8-byte loads) and write their own 32-byte staging rows.
+// a frame row (coalesced 8-byte loads).
 #include "tacaw_internal.cuh"
 
 namespace tacaw {
@@ -127,6 +127,66 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t
     sum_res[m] = a;
 }
 
+// Whole staging blocks (s0 and n multiples of bf): 128 rows per CTA.  Each thread converts
+// its row's bf frames into a shared tile (16-byte chunks XOR-swizzled by row to spread the
+// banks); the CTA then writes the 128 contiguous rows of the block with consecutive
+// threads on consecutive 16-byte chunks, so every warp store is one contiguous 512 bytes.
+template <int BF>
+__global__ void __launch_bounds__(128) convert_split_tiled_kernel(FrameGeom g, int n, int s0, int64_t M_pad,
+                                                                  const float2 *mu_hat, double2 *sum_res,
+                                                                  __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo) {
+    constexpr int bf = BF;
+    constexpr int cpr = BF / 4;             // 16-byte chunks per row
+    __shared__ uint4 tile_h[128 * cpr], tile_l[128 * cpr];
+    const int r = threadIdx.x;
+    const int64_t m0 = (int64_t)blockIdx.x * 128;
+    const int64_t m = m0 + r;
+    const bool valid = m < g.M;
+    const float2 *src = valid ? row_src(g, m) : nullptr;
+    const float2 mu = valid ? mu_hat[m] : make_float2(0.f, 0.f);
+    uint4 *Hi = reinterpret_cast<uint4 *>(A_hi);
+    uint4 *Lo = reinterpret_cast<uint4 *>(A_lo);
+    double sr = 0.0, si = 0.0;
+    for (int t0 = 0; t0 < n; t0 += bf) {
+        float2 v[BF];
+#pragma unroll
+        for (int i = 0; i < BF; ++i)
+            v[i] = valid ? __ldcs(src + (int64_t)(t0 + i) * g.pitch_frame) : make_float2(0.f, 0.f);
+        float br = 0.f, bi = 0.f;
+#pragma unroll
+        for (int c = 0; c < cpr; ++c) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float2 q = valid ? make_float2(v[4 * c + i].x - mu.x, v[4 * c + i].y - mu.y) : make_float2(0.f, 0.f);
+                br += q.x;
+                bi += q.y;
+                split2(q, h[i], l[i]);
+            }
+            const int slot = r * cpr + (c ^ (r & (cpr - 1)));
+            tile_h[slot] = make_uint4(h[0], h[1], h[2], h[3]);
+            tile_l[slot] = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+        sr += br;
+        si += bi;
+        __syncthreads();
+        const size_t base = ((size_t)((s0 + t0) / bf) * M_pad + m0) * cpr;   // in 16-byte units
+        for (int q = r; q < 128 * cpr; q += 128) {
+            const int rr = q / cpr, c = q - (q / cpr) * cpr;
+            const int slot = rr * cpr + (c ^ (rr & (cpr - 1)));
+            Hi[base + q] = tile_h[slot];
+            Lo[base + q] = tile_l[slot];
+        }
+        __syncthreads();
+    }
+    if (valid) {
+        double2 a = sum_res[m];
+        a.x += sr;
+        a.y += si;
+        sum_res[m] = a;
+    }
+}
+
 __global__ void convert_fp32_kernel(FrameGeom g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
                                     double2 *sum_res, float2 *A32) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -191,6 +251,14 @@ cudaError_t launch_mean(const FrameGeom &g, int n, float2 *mu_hat, cudaStream_t 
 
 cudaError_t launch_convert_split(const FrameGeom &g, int n, int s0, int bf, int64_t M_pad, const float2 *mu_hat,
                                  double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, cudaStream_t st) {
+    if (bf >= 16 && s0 % bf == 0 && n % bf == 0) {
+        const unsigned grid = (unsigned)(M_pad / 128);
+        if (bf == 32)
+            convert_split_tiled_kernel<32><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo);
+        else
+            convert_split_tiled_kernel<16><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo);
+        return cudaGetLastError();
+    }
     convert_split_kernel<<<blocks_for(g.M, 256), 256, 0, st>>>(g, n, s0, bf, M_pad, mu_hat, sum_res, A_hi, A_lo);
     return cudaGetLastError();
 }

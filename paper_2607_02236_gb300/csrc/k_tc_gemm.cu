@@ -340,32 +340,52 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
             const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
             const int total_steps = a.n_kb * (a.bf / 8);
             const int n_big_used = a.split ? (total_steps < a.n_big ? total_steps : a.n_big) : 0;
-            for (int c0 = 0; c0 < a.N; c0 += 16) {
-                uint32_t r[16];
-                float v[16];
-                tmem_ld_x16(lane_base + (uint32_t)c0, r);
-                tmem_ld_wait();
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+            const uint32_t o_big1 = (uint32_t)a.N, o_small = (uint32_t)(a.n_big * a.N);
+            // 32 columns (16 energies) per round: every accumulator's loads are issued before one wait
+            for (int c0 = 0; c0 < a.N; c0 += 32) {
+                __syncwarp();
+                const bool two = c0 + 16 < a.N;
+                uint32_t r0[16], r1[16], s0[16], s1[16], t0[16], t1[16];
+                tmem_ld_x16(lane_base + (uint32_t)c0, r0);
+                if (two) tmem_ld_x16(lane_base + (uint32_t)(c0 + 16), r1);
                 if (a.split) {
                     if (n_big_used == 2) {
-                        tmem_ld_x16(lane_base + (uint32_t)(a.N + c0), r);
-                        tmem_ld_wait();
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] += __uint_as_float(r[i]);
+                        tmem_ld_x16(lane_base + o_big1 + (uint32_t)c0, s0);
+                        if (two) tmem_ld_x16(lane_base + o_big1 + (uint32_t)(c0 + 16), s1);
                     }
-                    tmem_ld_x16(lane_base + (uint32_t)(a.n_big * a.N + c0), r);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] += __uint_as_float(r[i]);
+                    tmem_ld_x16(lane_base + o_small + (uint32_t)c0, t0);
+                    if (two) tmem_ld_x16(lane_base + o_small + (uint32_t)(c0 + 16), t1);
                 }
+                tmem_ld_wait();
                 if (row.valid) {
+                    float v[32];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
+                    for (int i = 0; i < 16; ++i) {
+                        v[i] = __uint_as_float(r0[i]);
+                        v[16 + i] = two ? __uint_as_float(r1[i]) : 0.f;
+                    }
+                    if (a.split) {
+                        if (n_big_used == 2) {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                v[i] += __uint_as_float(s0[i]);
+                                if (two) v[16 + i] += __uint_as_float(s1[i]);
+                            }
+                        }
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            v[i] += __uint_as_float(t0[i]);
+                            if (two) v[16 + i] += __uint_as_float(t1[i]);
+                        }
+                    }
+                    const int jn = two ? 16 : 8;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
                         const int j = jbase + (c0 >> 1) + i;
-                        if (j < a.e.Nw) epi_element(a.e, row, j, v[2 * i], v[2 * i + 1]);
+                        if (i < jn && j < a.e.Nw) epi_element(a.e, row, j, v[2 * i], v[2 * i + 1]);
                     }
                 }
+                __syncwarp();   // the next round's tcgen05.ld needs the whole warp converged
             }
         }
     }
