@@ -122,11 +122,14 @@ typedef struct {
      *                     terms), 3 (hi*hi alternating over two | small terms; default)
      *   tc_cluster        CTAs per cluster sharing the twiddle rows by TMA multicast: 1, 2, 4
      *   tc_block_frames   frames per staged operand row: 8, 16 or 32 (32-, 64-, 128-byte rows);
-     *                     k_stage must be a multiple of it */
+     *                     k_stage must be a multiple of it
+     *   tc_prefetch       staging blocks of operand A prefetched into L2 ahead of the load ring
+     *                     (0: automatic, < 0: off) */
     int tc_omega_tile;
     int tc_accumulators;
     int tc_cluster;
     int tc_block_frames;
+    int tc_prefetch;
 } tacaw_plan_desc;
 
 typedef struct tacaw_plan_s *tacaw_plan_t;

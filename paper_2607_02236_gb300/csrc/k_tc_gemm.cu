@@ -100,6 +100,13 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
         : "memory");
 }
+// L2 prefetch of a tensor box (no shared-memory destination, no completion)
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *map, int c0, int c1, int c2) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+}
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
                  : "memory");
@@ -234,6 +241,13 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
     if (warp == 0) {
         if (lane == 0) {
             int issued = 0;
+            // operand A streams from HBM: prefetch its boxes into L2 ahead of the ring so that
+            // the ring's loads hit L2 (the twiddle rows are shared by all CTAs and stay in L2)
+            const int pf_dist = a.prefetch;
+            for (int kb = 0; kb < pf_dist && kb < a.n_kb; ++kb) {
+                tma_prefetch_3d(&maps.a_hi, 0, m0, kb);
+                tma_prefetch_3d(&maps.a_lo, 0, m0, kb);
+            }
             for (int kb = 0; kb < a.n_kb; ++kb) {
                 const int s = kb % a.stages;
                 const uint32_t use = (uint32_t)(kb / a.stages);
@@ -260,6 +274,10 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
                     }
                 }
                 issued = kb + 1;
+                if (pf_dist > 0 && kb + pf_dist < a.n_kb) {
+                    tma_prefetch_3d(&maps.a_hi, 0, m0, kb + pf_dist);
+                    tma_prefetch_3d(&maps.a_lo, 0, m0, kb + pf_dist);
+                }
             }
             if (*abort_flag) {
                 // let every copy into this CTA's ring land before it can exit

@@ -89,6 +89,7 @@ struct tacaw_plan_s {
     int stages = 0;
     int tc_acc = 3;
     int bf = 8;                // frames per staged operand row (split path)
+    int tc_prefetch = 0;       // L2 prefetch distance of operand A in staging blocks
     int64_t bytes = 0;
     int64_t I_elems = 0, S_elems = 0;
     int64_t flushes_total = 0;
@@ -250,6 +251,7 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         a.split = p->tc_acc > 1 ? 1 : 0;
         a.n_big = p->tc_acc == 3 ? 2 : 1;
         a.cluster = s.tc_cluster;
+        a.prefetch = p->tc_prefetch;
         a.err = p->d_err;
         CU_CHECK(p, launch_flush_tc(a, s.tc_maps.data(), st), "flush (tensor cores)");
         p->launches++;
@@ -548,6 +550,8 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
             while (p->bf > 8 && tc_stages_for(maxN, p->bf) < 3) p->bf /= 2;
         p->stages = tc_stages_for(maxN, p->bf);
         for (auto &s : p->s) s.n_kb_T = s.T_pad / p->bf;
+        // prefetch A about 256 frames beyond the ring (0 disables)
+        p->tc_prefetch = desc->tc_prefetch >= 0 ? (desc->tc_prefetch ? desc->tc_prefetch : p->stages + 256 / p->bf) : 0;
         if (p->stages < 2) {
             delete p;
             return fail(TACAW_ERR_UNSUPPORTED, "tensor-core tile of %d columns does not fit shared memory", maxN);
@@ -568,7 +572,8 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
                 const int r1 = tc_resident_ctas(N, p->bf, p->stages, 1);
                 s.tc_cluster = 1;
                 for (int c : {4, 2}) {
-                    if (!tc_b_boxes(N, c, &br, &nb) || n_mt < 2 * c) continue;
+                    // multicast pays off for wide tiles (one accumulator); narrow tiles run best alone
+                    if (N <= 256 || !tc_b_boxes(N, c, &br, &nb) || n_mt < 2 * c) continue;
                     const int rc = tc_resident_ctas(N, p->bf, p->stages, c);
                     if (r1 > 0 && rc >= (int)(0.97 * r1)) {
                         s.tc_cluster = c;

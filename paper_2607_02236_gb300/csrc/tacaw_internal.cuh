@@ -179,6 +179,7 @@ struct TcPlanArgs {
     int split;                 // 1: separate TMEM accumulators for hi*hi and hi*lo + lo*hi (N <= 256)
     int n_big;                 // hi*hi accumulators (1 or 2, alternating by block parity)
     int cluster;               // CTAs sharing (multicasting) one energy tile's B rows: 1, 2 or 4
+    int prefetch;              // staging blocks of A prefetched into L2 ahead of the current one (0: off)
     uint32_t *err;
 };
 struct TcMaps;                 // tensor maps (defined in k_tc_gemm.cu)
