@@ -124,7 +124,7 @@ typedef struct {
      *   tc_block_frames   frames per staged operand row: 8, 16 or 32 (32-, 64-, 128-byte rows);
      *                     k_stage must be a multiple of it
      *   tc_prefetch       staging blocks of operand A prefetched into L2 ahead of the load ring
-     *                     (0: automatic, < 0: off) */
+     *                     (<= 0: off) */
     int tc_omega_tile;
     int tc_accumulators;
     int tc_cluster;
@@ -201,13 +201,19 @@ tacaw_status tacaw_reset(tacaw_plan_t plan, void *stream);
 /* Fills *info.                                                                          */
 tacaw_status tacaw_plan_get_info(tacaw_plan_t plan, tacaw_plan_info *info);
 
-/* Kernel timing: when enabled, CUDA events are recorded around every contraction
+/* Kernel timing: when enable != 0, CUDA events are recorded around every contraction
  * (flush) launch on the launching stream; tacaw_kernel_time_ms returns the summed
  * milliseconds and the launch count since the last call with reset != 0.  Reading the
- * times waits for the recorded events.                                                   */
+ * times waits for the recorded events.  enable >= 2 also records, for every CTA of each
+ * tensor-core flush, eight 64-bit words: globaltimer stamps (ns) at entry, set-up done,
+ * first operands landed, last MMA issued, accumulators complete, epilogue done, exit, and
+ * the SM id; tacaw_flush_trace copies the last flush's words (n_ctas x 8, CTA-major) to
+ * host_out (at most max_ctas CTAs) and reports the CTA count.                             */
 tacaw_status tacaw_set_timing(tacaw_plan_t plan, int enable);
 tacaw_status tacaw_kernel_time_ms(tacaw_plan_t plan, double *flush_ms, int64_t *flush_launches,
                                   int reset);
+tacaw_status tacaw_flush_trace(tacaw_plan_t plan, unsigned long long *host_out, int64_t max_ctas,
+                               int64_t *n_ctas);
 
 /* Detector spectra S[p][d][j] = sum_k M_d(k) I[p][j][k] from a caller-owned intensity array
  * d_I (float32 [p][j][ky][kx], the layout tacaw_finalize writes) without a plan and without

@@ -62,6 +62,11 @@ __device__ __forceinline__ uint64_t globaltimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+__device__ __forceinline__ uint32_t smid() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
@@ -217,6 +222,11 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
     const uint32_t tx_bytes = 2u * kABytes + 2u * (uint32_t)a.N * RB;
     const int rows_cta = a.N / C;                 // B rows this CTA loads (for the whole cluster)
     const uint16_t cmask = (uint16_t)((1u << C) - 1u);
+    unsigned long long *trace = a.trace ? a.trace + (size_t)blockIdx.x * kTraceWords : nullptr;
+    if (trace && threadIdx.x == 0) {
+        trace[0] = globaltimer();
+        trace[7] = smid();
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
@@ -237,6 +247,7 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
     tc_fence_after();
     const uint32_t tmem = sh->tmem_addr;
     volatile int *abort_flag = &sh->abort_flag;
+    if (trace && threadIdx.x == 0) trace[1] = globaltimer();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -307,6 +318,7 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
                     break;
                 }
                 tc_fence_after();
+                if (trace && kb == 0) trace[2] = globaltimer();
                 const uint32_t st = base_s + (uint32_t)s * stage_bytes;
                 const uint64_t dAhi0 = sdesc_k(st, RB);
                 const uint64_t dAlo0 = sdesc_k(st + kABytes, RB);
@@ -341,6 +353,7 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
             }
             // always signal: the epilogue (and TMEM release) wait for every issued MMA
             mma_commit(smem_u32(&sh->tmem_full));
+            if (trace) trace[3] = globaltimer();
         }
     } else {
         // epilogue warps 2..5 -> TMEM lane quarter q = warp % 4
@@ -351,6 +364,7 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
             *abort_flag = 1;
         }
         tc_fence_after();
+        if (trace && warp == 2 && lane == 0) trace[4] = globaltimer();
         if (ok && !*abort_flag) {
             const int64_t m = (int64_t)m0 + q * 32 + lane;
             const RowCtx row = make_row(a.e, m);
@@ -407,6 +421,7 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
             }
         }
     }
+    if (trace && warp == 2 && lane == 0) trace[5] = globaltimer();
     tc_fence_before();
     __syncthreads();
     if (C > 1) cluster_sync();   // no CTA leaves while a peer may still signal its barriers
@@ -414,6 +429,7 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
         tc_fence_after();
         tmem_dealloc(tmem, ncols);
     }
+    if (trace && threadIdx.x == 0) trace[6] = globaltimer();
 }
 
 // --------------------------------------------------------------------------------------
@@ -531,6 +547,11 @@ int tc_resident_ctas(int N, int bf, int stages, int cluster) {
         return 0;
     }
     return n * cluster;
+}
+
+int64_t tc_grid_ctas(const TcPlanArgs &a) {
+    const int64_t n_mt = a.e.M_pad / kMTile;
+    return (n_mt + a.cluster - 1) / a.cluster * a.cluster * a.n_wt;
 }
 
 cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps, cudaStream_t st) {

@@ -99,6 +99,9 @@ struct tacaw_plan_s {
     uint32_t *d_err = nullptr;
     std::vector<void *> allocs;
     bool timing = false;
+    bool trace = false;                      // record per-CTA phase stamps of tensor-core flushes
+    unsigned long long *d_trace = nullptr;   // stamps of the last traced flush
+    int64_t trace_ctas = 0, trace_cap = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
     double timed_ms = 0.0;
     int64_t timed_launches = 0;
@@ -122,6 +125,8 @@ bool dev_alloc(tacaw_plan_s *p, T **ptr, size_t count) {
 }
 
 void free_all(tacaw_plan_s *p) {
+    if (p->d_trace) cudaFree(p->d_trace);
+    p->d_trace = nullptr;
     for (auto &e : p->ev) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
@@ -253,6 +258,19 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         a.cluster = s.tc_cluster;
         a.prefetch = p->tc_prefetch;
         a.err = p->d_err;
+        a.trace = nullptr;
+        if (p->trace) {
+            const int64_t n = tc_grid_ctas(a);
+            if (n > p->trace_cap) {
+                if (p->d_trace) cudaFree(p->d_trace);
+                p->d_trace = nullptr;
+                p->trace_cap = 0;
+                CU_CHECK(p, cudaMalloc(&p->d_trace, sizeof(unsigned long long) * kTraceWords * n), "trace buffer");
+                p->trace_cap = n;
+            }
+            p->trace_ctas = n;
+            a.trace = p->d_trace;
+        }
         CU_CHECK(p, launch_flush_tc(a, s.tc_maps.data(), st), "flush (tensor cores)");
         p->launches++;
     } else {
@@ -550,8 +568,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
             while (p->bf > 8 && tc_stages_for(maxN, p->bf) < 3) p->bf /= 2;
         p->stages = tc_stages_for(maxN, p->bf);
         for (auto &s : p->s) s.n_kb_T = s.T_pad / p->bf;
-        // prefetch A about 256 frames beyond the ring (0 disables)
-        p->tc_prefetch = desc->tc_prefetch >= 0 ? (desc->tc_prefetch ? desc->tc_prefetch : p->stages + 256 / p->bf) : 0;
+        p->tc_prefetch = desc->tc_prefetch > 0 ? desc->tc_prefetch : 0;
         if (p->stages < 2) {
             delete p;
             return fail(TACAW_ERR_UNSUPPORTED, "tensor-core tile of %d columns does not fit shared memory", maxN);
@@ -744,6 +761,19 @@ tacaw_status tacaw_plan_get_info(tacaw_plan_t p, tacaw_plan_info *info) {
 tacaw_status tacaw_set_timing(tacaw_plan_t p, int enable) {
     if (!p) return fail(TACAW_ERR_INVALID_ARG, "plan is NULL");
     p->timing = enable != 0;
+    p->trace = enable >= 2;
+    return TACAW_OK;
+}
+
+tacaw_status tacaw_flush_trace(tacaw_plan_t p, unsigned long long *host_out, int64_t max_ctas, int64_t *n_ctas) {
+    if (!p) return fail(TACAW_ERR_INVALID_ARG, "plan is NULL");
+    if (n_ctas) *n_ctas = p->trace_ctas;
+    if (!host_out || !p->d_trace || p->trace_ctas == 0) return TACAW_OK;
+    const int64_t n = std::min(max_ctas, p->trace_ctas);
+    if (n <= 0) return TACAW_OK;
+    cudaError_t e = cudaMemcpy(host_out, p->d_trace, sizeof(unsigned long long) * kTraceWords * n,
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(p, e, "copy trace");
     return TACAW_OK;
 }
 

@@ -25,6 +25,11 @@ constexpr int kMTile = 128;          // rows per tensor-core tile (TMEM lanes)
 
 enum FlushMode : int { FLUSH_STORE = 0, FLUSH_ADD = 1, FLUSH_FINAL = 2 };
 
+// Per-CTA trace of the tensor-core contraction (globaltimer, ns):
+//   0 entry  1 set-up done  2 first operands landed  3 last MMA issued
+//   4 accumulators complete (epilogue start)  5 epilogue done  6 exit  7 SM id
+constexpr int kTraceWords = 8;
+
 // device error bits (OR-ed into the plan's error word)
 enum : uint32_t {
     DEVERR_TIMEOUT_FULL = 1u,
@@ -180,10 +185,12 @@ struct TcPlanArgs {
     int n_big;                 // hi*hi accumulators (1 or 2, alternating by block parity)
     int cluster;               // CTAs sharing (multicasting) one energy tile's B rows: 1, 2 or 4
     int prefetch;              // staging blocks of A prefetched into L2 ahead of the current one (0: off)
+    unsigned long long *trace; // null, or kTraceWords globaltimer stamps per CTA (phase boundaries)
     uint32_t *err;
 };
 struct TcMaps;                 // tensor maps (defined in k_tc_gemm.cu)
 cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps /* TcMaps */, cudaStream_t st);
+int64_t tc_grid_ctas(const TcPlanArgs &a);
 int tc_stages_for(int N, int bf);
 size_t tc_smem_bytes(int N, int bf, int stages);
 size_t tc_maps_size();

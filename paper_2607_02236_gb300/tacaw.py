@@ -27,7 +27,7 @@ DET_KINDS = {"circular": 0, "annular": 1, "mask": 2}
 EXPORTS = ["tacaw_plan_create", "tacaw_push_frames", "tacaw_finalize", "tacaw_output_offsets",
            "tacaw_backward", "tacaw_reset", "tacaw_plan_get_info", "tacaw_set_timing",
            "tacaw_kernel_time_ms", "tacaw_destroy", "tacaw_last_error", "tacaw_version",
-           "tacaw_detector_spectra_noalloc"]
+           "tacaw_detector_spectra_noalloc", "tacaw_flush_trace"]
 
 
 class TacawError(RuntimeError):
@@ -86,6 +86,7 @@ def lib():
     L.tacaw_set_timing.argtypes = [c_void_p, c_int]
     L.tacaw_kernel_time_ms.argtypes = [c_void_p, POINTER(c_double), POINTER(c_int64), c_int]
     L.tacaw_destroy.argtypes = [c_void_p]
+    L.tacaw_flush_trace.argtypes = [c_void_p, c_void_p, c_int64, POINTER(c_int64)]
     L.tacaw_detector_spectra_noalloc.argtypes = [c_void_p, c_int, c_int, c_int, c_int, POINTER(CDetector), c_int,
                                                  c_void_p, c_void_p]
     L.tacaw_last_error.restype = c_char_p
@@ -217,8 +218,19 @@ class TacawPlan:
         _check(lib().tacaw_plan_get_info(self._h, ctypes.byref(i)))
         return {k: getattr(i, k) for k, _ in CPlanInfo._fields_}
 
-    def set_timing(self, on: bool):
-        _check(lib().tacaw_set_timing(self._h, int(bool(on))))
+    def set_timing(self, on):
+        """on: False/True, or 2 to also record per-CTA phase stamps of tensor-core flushes."""
+        _check(lib().tacaw_set_timing(self._h, int(on)))
+
+    def flush_trace(self):
+        """Per-CTA stamps of the last traced tensor-core flush: numpy uint64 [n_ctas, 8]."""
+        import numpy as np
+        n = c_int64()
+        _check(lib().tacaw_flush_trace(self._h, None, 0, ctypes.byref(n)))
+        out = np.zeros((max(n.value, 0), 8), dtype=np.uint64)
+        if n.value:
+            _check(lib().tacaw_flush_trace(self._h, out.ctypes.data, n.value, ctypes.byref(n)))
+        return out
 
     def kernel_time_ms(self, reset: bool = True):
         ms, n = c_double(), c_int64()
