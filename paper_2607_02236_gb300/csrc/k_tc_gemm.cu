@@ -52,6 +52,8 @@ struct TcShared {
     uint64_t tmem_full;
     uint32_t tmem_addr;
     int abort_flag;
+    float2 W[256];      // window transform W(E_j) of this CTA's energies
+    float bose[256];    // Bose factors of this CTA's energies
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -358,6 +360,16 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
     } else {
         // epilogue warps 2..5 -> TMEM lane quarter q = warp % 4
         const int q = warp & 3;
+        {
+            // while the main loop runs: stage this tile's per-energy constants in shared memory
+            const int jb = wtile * a.wt;
+            for (int i = threadIdx.x - 64; i < a.wt; i += 128) {
+                const int j = jb + i;
+                sh->W[i] = j < a.e.Nw ? __ldg(a.e.Wc + j) : make_float2(0.f, 0.f);
+                sh->bose[i] = j < a.e.Nw ? __ldg(a.e.bose + j) : 0.f;
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");   // the four epilogue warps only
+        }
         const bool ok = mbar_wait(smem_u32(&sh->tmem_full), 0u, nullptr);
         if (!ok) {
             atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
@@ -413,8 +425,10 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
                     const int jn = two ? 16 : 8;
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        const int j = jbase + (c0 >> 1) + i;
-                        if (i < jn && j < a.e.Nw) epi_element(a.e, row, j, v[2 * i], v[2 * i + 1]);
+                        const int jl = (c0 >> 1) + i;
+                        const int j = jbase + jl;
+                        if (i < jn && j < a.e.Nw)
+                            epi_element_wb(a.e, row, j, v[2 * i], v[2 * i + 1], sh->W[jl], sh->bose[jl]);
                     }
                 }
                 __syncwarp();   // the next round's tcgen05.ld needs the whole warp converged

@@ -82,8 +82,9 @@ __device__ __forceinline__ RowCtx make_row(const EpiArgs &a, int64_t m) {
     return r;
 }
 
-// Applies one flush result (re, im) for row r, energy j < Nw.
-__device__ __forceinline__ void epi_element(const EpiArgs &a, const RowCtx &r, int j, float re, float im) {
+// Applies one flush result (re, im) for row r, energy j < Nw, given W(E_j) and B(E_j).
+__device__ __forceinline__ void epi_element_wb(const EpiArgs &a, const RowCtx &r, int j, float re, float im,
+                                               float2 W, float bj) {
     const size_t ai = (size_t)j * (size_t)a.M_pad + (size_t)r.m;
     if (a.mode == FLUSH_STORE) {
         if (a.accum) {
@@ -129,12 +130,15 @@ __device__ __forceinline__ void epi_element(const EpiArgs &a, const RowCtx &r, i
         pi = im;
     }
     // exact mean correction: Psi -= (mu - mu_hat) * W(E_j)
-    const float2 W = a.Wc[j];
     pr -= r.dmu.x * W.x - r.dmu.y * W.y;
     pi -= r.dmu.x * W.y + r.dmu.y * W.x;
     const int64_t o = r.out_base + (int64_t)j * a.npix;
-    if (a.I_out) a.I_out[o] = (pr * pr + pi * pi) * a.bose[j];
+    if (a.I_out) a.I_out[o] = (pr * pr + pi * pi) * bj;
     if (a.Psi_out) a.Psi_out[o] = make_float2(pr, pi);
+}
+
+__device__ __forceinline__ void epi_element(const EpiArgs &a, const RowCtx &r, int j, float re, float im) {
+    epi_element_wb(a, r, j, re, im, __ldg(a.Wc + j), __ldg(a.bose + j));
 }
 
 // ---------------------------------------------------------------------------------------
