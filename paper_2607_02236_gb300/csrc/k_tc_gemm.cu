@@ -203,6 +203,62 @@ __host__ __device__ inline uint32_t tc_tmem_cols(int N) {
     return c;
 }
 
+// Epilogue of one row (one TMEM lane) of a tile: drains the accumulators 32 columns at a time
+// and applies the flush update of kind KIND to every energy of the tile.
+template <int KIND>
+__device__ __forceinline__ void tc_epilogue(const TcPlanArgs &a, const TcShared *sh, const RowCtx &row,
+                                            uint32_t lane_base, int jbase, int n_big_used) {
+    const uint32_t o_big1 = (uint32_t)a.N, o_small = (uint32_t)(a.n_big * a.N);
+    // 32 columns (16 energies) per round: every accumulator's loads are issued before one wait
+    for (int c0 = 0; c0 < a.N; c0 += 32) {
+        __syncwarp();
+        const bool two = c0 + 16 < a.N;
+        uint32_t r0[16], r1[16], s0[16], s1[16], t0[16], t1[16];
+        tmem_ld_x16(lane_base + (uint32_t)c0, r0);
+        if (two) tmem_ld_x16(lane_base + (uint32_t)(c0 + 16), r1);
+        if (a.split) {
+            if (n_big_used == 2) {
+                tmem_ld_x16(lane_base + o_big1 + (uint32_t)c0, s0);
+                if (two) tmem_ld_x16(lane_base + o_big1 + (uint32_t)(c0 + 16), s1);
+            }
+            tmem_ld_x16(lane_base + o_small + (uint32_t)c0, t0);
+            if (two) tmem_ld_x16(lane_base + o_small + (uint32_t)(c0 + 16), t1);
+        }
+        tmem_ld_wait();
+        if (row.valid) {
+            float v[32];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                v[i] = __uint_as_float(r0[i]);
+                v[16 + i] = two ? __uint_as_float(r1[i]) : 0.f;
+            }
+            if (a.split) {
+                if (n_big_used == 2) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        v[i] += __uint_as_float(s0[i]);
+                        if (two) v[16 + i] += __uint_as_float(s1[i]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    v[i] += __uint_as_float(t0[i]);
+                    if (two) v[16 + i] += __uint_as_float(t1[i]);
+                }
+            }
+            const int jn = two ? 16 : 8;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int jl = (c0 >> 1) + i;
+                const int j = jbase + jl;
+                if (i < jn && j < a.e.Nw)
+                    epi_apply<KIND>(a.e, row, j, v[2 * i], v[2 * i + 1], sh->W[jl], sh->bose[jl]);
+            }
+        }
+        __syncwarp();   // the next round's tcgen05.ld needs the whole warp converged
+    }
+}
+
 __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant__ TcMaps maps, const TcPlanArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -384,54 +440,14 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
             const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
             const int total_steps = a.n_kb * (a.bf / 8);
             const int n_big_used = a.split ? (total_steps < a.n_big ? total_steps : a.n_big) : 0;
-            const uint32_t o_big1 = (uint32_t)a.N, o_small = (uint32_t)(a.n_big * a.N);
-            // 32 columns (16 energies) per round: every accumulator's loads are issued before one wait
-            for (int c0 = 0; c0 < a.N; c0 += 32) {
-                __syncwarp();
-                const bool two = c0 + 16 < a.N;
-                uint32_t r0[16], r1[16], s0[16], s1[16], t0[16], t1[16];
-                tmem_ld_x16(lane_base + (uint32_t)c0, r0);
-                if (two) tmem_ld_x16(lane_base + (uint32_t)(c0 + 16), r1);
-                if (a.split) {
-                    if (n_big_used == 2) {
-                        tmem_ld_x16(lane_base + o_big1 + (uint32_t)c0, s0);
-                        if (two) tmem_ld_x16(lane_base + o_big1 + (uint32_t)(c0 + 16), s1);
-                    }
-                    tmem_ld_x16(lane_base + o_small + (uint32_t)c0, t0);
-                    if (two) tmem_ld_x16(lane_base + o_small + (uint32_t)(c0 + 16), t1);
-                }
-                tmem_ld_wait();
-                if (row.valid) {
-                    float v[32];
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        v[i] = __uint_as_float(r0[i]);
-                        v[16 + i] = two ? __uint_as_float(r1[i]) : 0.f;
-                    }
-                    if (a.split) {
-                        if (n_big_used == 2) {
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                v[i] += __uint_as_float(s0[i]);
-                                if (two) v[16 + i] += __uint_as_float(s1[i]);
-                            }
-                        }
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            v[i] += __uint_as_float(t0[i]);
-                            if (two) v[16 + i] += __uint_as_float(t1[i]);
-                        }
-                    }
-                    const int jn = two ? 16 : 8;
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int jl = (c0 >> 1) + i;
-                        const int j = jbase + jl;
-                        if (i < jn && j < a.e.Nw)
-                            epi_element_wb(a.e, row, j, v[2 * i], v[2 * i + 1], sh->W[jl], sh->bose[jl]);
-                    }
-                }
-                __syncwarp();   // the next round's tcgen05.ld needs the whole warp converged
+            switch (epi_kind(a.e)) {
+                case EPI_FINAL: tc_epilogue<EPI_FINAL>(a, sh, row, lane_base, jbase, n_big_used); break;
+                case EPI_FINAL_KAHAN: tc_epilogue<EPI_FINAL_KAHAN>(a, sh, row, lane_base, jbase, n_big_used); break;
+                case EPI_FINAL_FP64: tc_epilogue<EPI_FINAL_FP64>(a, sh, row, lane_base, jbase, n_big_used); break;
+                case EPI_STORE_KAHAN: tc_epilogue<EPI_STORE_KAHAN>(a, sh, row, lane_base, jbase, n_big_used); break;
+                case EPI_STORE_FP64: tc_epilogue<EPI_STORE_FP64>(a, sh, row, lane_base, jbase, n_big_used); break;
+                case EPI_ADD_KAHAN: tc_epilogue<EPI_ADD_KAHAN>(a, sh, row, lane_base, jbase, n_big_used); break;
+                default: tc_epilogue<EPI_ADD_FP64>(a, sh, row, lane_base, jbase, n_big_used); break;
             }
         }
     }

@@ -141,6 +141,66 @@ __device__ __forceinline__ void epi_element(const EpiArgs &a, const RowCtx &r, i
     epi_element_wb(a, r, j, re, im, __ldg(a.Wc + j), __ldg(a.bose + j));
 }
 
+// The same update with the flush mode fixed at compile time, so that an unrolled loop over
+// many energies carries only one path (keeps the loop body small).
+enum EpiKind : int {
+    EPI_FINAL = 0,          // last flush, no earlier flushes
+    EPI_FINAL_KAHAN = 1,    // last flush on top of compensated FP32 accumulators
+    EPI_FINAL_FP64 = 2,     // last flush on top of FP64 accumulators
+    EPI_STORE_KAHAN = 3,
+    EPI_STORE_FP64 = 4,
+    EPI_ADD_KAHAN = 5,
+    EPI_ADD_FP64 = 6,
+};
+
+__host__ __device__ inline int epi_kind(const EpiArgs &a) {
+    if (a.mode == FLUSH_STORE) return a.accum ? EPI_STORE_FP64 : EPI_STORE_KAHAN;
+    if (a.mode == FLUSH_ADD) return a.accum ? EPI_ADD_FP64 : EPI_ADD_KAHAN;
+    if (!a.has_prev) return EPI_FINAL;
+    return a.accum ? EPI_FINAL_FP64 : EPI_FINAL_KAHAN;
+}
+
+template <int K>
+__device__ __forceinline__ void epi_apply(const EpiArgs &a, const RowCtx &r, int j, float re, float im, float2 W,
+                                          float bj) {
+    const size_t ai = (size_t)j * (size_t)a.M_pad + (size_t)r.m;
+    if (K == EPI_STORE_KAHAN) {
+        a.acc_s[ai] = make_float2(re, im);
+        a.acc_c[ai] = make_float2(0.f, 0.f);
+    } else if (K == EPI_STORE_FP64) {
+        a.acc_d[ai] = make_double2(re, im);
+    } else if (K == EPI_ADD_KAHAN) {
+        float2 s = a.acc_s[ai], c = a.acc_c[ai];
+        float yr = re - c.x, yi = im - c.y;
+        float tr = s.x + yr, ti = s.y + yi;
+        c.x = (tr - s.x) - yr;
+        c.y = (ti - s.y) - yi;
+        a.acc_s[ai] = make_float2(tr, ti);
+        a.acc_c[ai] = c;
+    } else if (K == EPI_ADD_FP64) {
+        double2 s = a.acc_d[ai];
+        s.x += re;
+        s.y += im;
+        a.acc_d[ai] = s;
+    } else {
+        float pr = re, pi = im;
+        if (K == EPI_FINAL_KAHAN) {
+            float2 s = a.acc_s[ai], c = a.acc_c[ai];
+            pr = s.x + (re - c.x);
+            pi = s.y + (im - c.y);
+        } else if (K == EPI_FINAL_FP64) {
+            double2 s = a.acc_d[ai];
+            pr = (float)(s.x + (double)re);
+            pi = (float)(s.y + (double)im);
+        }
+        pr -= r.dmu.x * W.x - r.dmu.y * W.y;
+        pi -= r.dmu.x * W.y + r.dmu.y * W.x;
+        const int64_t o = r.out_base + (int64_t)j * a.npix;
+        if (a.I_out) a.I_out[o] = (pr * pr + pi * pi) * bj;
+        if (a.Psi_out) a.Psi_out[o] = make_float2(pr, pi);
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // Launchers (each defined in its own translation unit); all enqueue on `st`.
 // ---------------------------------------------------------------------------------------
