@@ -31,7 +31,11 @@ UNIT = "CMAC/s"
 
 # DRAM bytes per launch of the contraction kernel from an ncu capture, keyed by the hash of
 # the kernel's source file at capture time (reported only while the source is unchanged).
-KERNEL_TRAFFIC = {}
+KERNEL_TRAFFIC = {
+    # ncu --set full of flush_tc_kernel on `bench.py --small` (P=2, T=2048, 400 energies, default tiling):
+    # dram__bytes_read.sum 2.275640 GB + dram__bytes_write.sum 0.204266 GB per launch of 1.07e11 CMAC
+    "0f1f317175bb73aa": 2.309592e-02,
+}
 
 
 def parse():
@@ -45,6 +49,12 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2, help="end-to-end steps from pinned host memory (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU oracle baseline")
     ap.add_argument("--small", action="store_true", help="small workload (profiling captures)")
+    ap.add_argument("--tc-accumulators", type=int, default=0, help="tensor-core tiling override (0: plan default)")
+    ap.add_argument("--tc-omega-tile", type=int, default=0)
+    ap.add_argument("--tc-cluster", type=int, default=0)
+    ap.add_argument("--tc-block-frames", type=int, default=0)
+    ap.add_argument("--trace", action="store_true",
+                    help="add the per-CTA phase breakdown of one traced contraction (tacaw_flush_trace)")
     ap.add_argument("--fast-steps", type=int, default=2,
                     help="steps with one TMEM accumulator per tile (faster, larger error; 0: skip)")
     return ap.parse_args()
@@ -120,6 +130,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest value over all ranks (the slowest replica sets the job's time)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest time."""
+    return world * units_per_rank / seconds_max
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -143,20 +168,16 @@ def oracle_rate(series, spec, seconds: float):
     kw = dict(window_kind=spec.window, E_meV=spec.energies_meV(), dt_fs=spec.dt_fs,
               subtract_mean=spec.subtract_mean)
     T, n = series.shape
-    t0 = time.perf_counter()
-    oracle.forward_pixels(series[:, :min(n, 32)], **kw)
-    dt = time.perf_counter() - t0
-    per_px = dt / min(n, 32)
-    m = int(max(32, seconds / max(per_px, 1e-9)))
+    oracle.forward_pixels(series[:, :min(n, 64)], **kw)      # warm-up
+    k = min(1024, n)
     t0 = time.perf_counter()
     done = 0
-    while done < m:
-        k = min(1024, m - done, n)
-        s0 = done % max(1, n - k + 1)
+    while time.perf_counter() - t0 < seconds:
+        s0 = (done // k) * k % max(1, n - k + 1)
         oracle.forward_pixels(series[:, s0:s0 + k], **kw)
         done += k
     dt = time.perf_counter() - t0
-    return m * T * spec.Nw / dt, m, dt
+    return done * T * spec.Nw / dt, done, dt
 
 
 def reference_arm(args):
@@ -270,17 +291,34 @@ def main():
         kms, kn = plan.kernel_time_ms(reset=True)
         plan.set_timing(False)
         launches = (plan.info()["kernel_launches"] - l0) // steps
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
         return ms / steps, kms / max(kn, 1), kn // max(steps, 1), launches, clocks
 
-    plan = TacawPlan([stream_config(spec)], precision=args.precision)
+    tiling = dict(tc_accumulators=args.tc_accumulators, tc_omega_tile=args.tc_omega_tile,
+                  tc_cluster=args.tc_cluster, tc_block_frames=args.tc_block_frames)
+    plan = TacawPlan([stream_config(spec)], precision=args.precision, **tiling)
     info = plan.info()
     ms_step, k_ms, k_per_step, launches, clocks = timed(plan, args.steps, args.warmup, sample_clocks=True)
-    value = world * cmac_step / (ms_step * 1e-3)
+    value = job_rate(cmac_step, world, ms_step * 1e-3)
     spectra_per_s = world * P * D / (ms_step * 1e-3)
+
+    phases = None
+    if args.trace and args.precision == "split_bf16":
+        plan.set_timing(2)
+        run_step(plan)
+        torch.cuda.synchronize()
+        tr = plan.flush_trace().astype(np.int64)
+        plan.set_timing(0)
+        names = ["setup", "fill", "main_loop", "drain", "epilogue", "exit"]
+        phases = {n: round(float(np.median(tr[:, i + 1] - tr[:, i])) / 1e3, 3) for i, n in enumerate(names)}
+        gaps = []
+        for sm in np.unique(tr[:, 7]):
+            r = tr[tr[:, 7] == sm]
+            r = r[np.argsort(r[:, 0])]
+            gaps.extend((r[1:, 0] - r[:-1, 6]).tolist())
+        phases["gap_between_ctas"] = round(float(np.median(gaps)) / 1e3, 3) if gaps else None
+        phases["ctas"] = int(len(tr))
+        phases["unit"] = "us (median per CTA)"
 
     # stated error vs FP64 at sampled pixels (all energies), incl. the bright centre
     import oracle
@@ -333,11 +371,7 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             e2e_step()
-        el = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         e2e = {"value": world * cmac_step * args.e2e_steps / el, "unit": UNIT,
                "h2d_bytes_per_step": T * frame_elems * 8, "d2h_bytes_per_step": S.numel() * 4,
                "ms_per_step": 1e3 * el / args.e2e_steps,
@@ -422,6 +456,8 @@ def main():
                 "max_rel_err_I_vs_fp64": err, "error_sample": "24 (probe, pixel) series, all energies",
                 "spectra_per_s": spectra_per_s, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
                 "roofline": roof, "cpu_baseline": cpu, "fp32_path": fp32, "one_accumulator_mode": fast}
+        if phases:
+            line["flush_phases"] = phases
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -101,6 +101,53 @@ def test_streaming_flushes_match_single_flush(precision, accum):
     assert out["info"]["flushes"] == 5
 
 
+@pytest.mark.parametrize("precision", ["fp32", "split_bf16"])
+def test_elastic_only_input_gives_zero(precision):
+    """Frames constant in time (pure elastic part): nothing is left after the mean removal."""
+    spec = StreamSpec(P=2, Kx=24, Ky=16, T=72, Tc=24, n_omega=40, E_max_meV=120.0, window="hann",
+                      detectors=(Detector("circular", 0, 0, -1, 5.0),))
+    rng = np.random.default_rng(4)
+    c = (rng.standard_normal((2, 1, 16, 24)) + 1j * rng.standard_normal((2, 1, 16, 24))).astype(np.complex64)
+    fr = np.repeat(c, spec.T, axis=1)
+    out = run_gpu(spec, fr, precision)
+    scale = (np.abs(fr) ** 2).sum(axis=(1, 2, 3)).max() * spec.T
+    assert np.abs(out["I"]).max() <= 1e-12 * scale ** 2 / spec.T, np.abs(out["I"]).max()
+    assert np.abs(out["S"]).max() <= 1e-12 * scale ** 2 / spec.T
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split_bf16"])
+def test_signed_energies_bose_and_custom_mask(precision):
+    """Energy-gain and -loss sides (a signed +-60 meV grid) with the Bose factor of Eq. 1, and a
+    caller-supplied weighted mask detector next to circular and annular ones."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan, DetectorConfig
+    from tests.helpers import stream_config
+    P, K, T, Nw = 2, 20, 64, 41
+    rng = np.random.default_rng(12)
+    fr = random_frames(P, T, K, K, seed=12)
+    E = np.linspace(-60.0, 60.0, Nw)
+    mask = (rng.random((K, K)) * (rng.random((K, K)) < 0.3)).astype(np.float32)
+    d_mask = torch.from_numpy(mask).cuda()
+    spec = StreamSpec(P=P, Kx=K, Ky=K, T=T, Tc=T, n_omega=Nw, window="hann", bose_T_K=300.0)
+    cfg = stream_config(spec)
+    cfg.E_meV = [float(e) for e in E]
+    cfg.detectors = [DetectorConfig("circular", 0, 0, -1, 4.0), DetectorConfig("annular", 1, 0, 2.0, 6.0),
+                     DetectorConfig("mask", 0, 0, 0, 0, mask_ptr=d_mask.data_ptr())]
+    buf = torch.from_numpy(np.ascontiguousarray(fr.transpose(1, 0, 2, 3))).cuda()
+    I = torch.empty(P * Nw * K * K, device="cuda")
+    S = torch.empty(P * 3 * Nw, device="cuda")
+    with TacawPlan([cfg], precision=precision) as plan:
+        plan.push(0, buf, T)
+        plan.finalize(I, S)
+    ref = oracle.forward(fr, window_kind="hann", E_meV=E, dt_fs=5.0, subtract_mean=True, bose_T_K=300.0,
+                         detectors=[Detector("circular", 0, 0, -1, 4.0), Detector("annular", 1, 0, 2.0, 6.0)])
+    got_I = I.cpu().numpy().reshape(P, Nw, K, K)
+    assert rel_err_peak(got_I, ref.I) <= TOL[precision]
+    S_mask = np.einsum("pjyx,yx->pj", ref.I, mask.astype(np.float64))
+    S_ref = np.concatenate([ref.S, S_mask[:, None, :]], axis=1)
+    assert rel_err_peak(S.cpu().numpy().reshape(P, 3, Nw), S_ref) <= TOL[precision]
+
+
 def test_errors_overflow_and_state():
     import torch
     from paper_2607_02236_gb300 import TacawPlan, TacawError
