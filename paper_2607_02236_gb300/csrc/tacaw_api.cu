@@ -563,9 +563,9 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         maxN = std::max(maxN, 2 * s.wt);
     }
     if (p->prec == TACAW_PREC_SPLIT_BF16) {
-        // keep at least 3 stages: narrow the block when the widest one leaves fewer
+        // widest rows that still leave two stages (wider rows beat deeper rings in measurements)
         if (!desc->tc_block_frames)
-            while (p->bf > 8 && tc_stages_for(maxN, p->bf) < 3) p->bf /= 2;
+            while (p->bf > 8 && tc_stages_for(maxN, p->bf) < 2) p->bf /= 2;
         p->stages = tc_stages_for(maxN, p->bf);
         for (auto &s : p->s) s.n_kb_T = s.T_pad / p->bf;
         p->tc_prefetch = desc->tc_prefetch > 0 ? desc->tc_prefetch : 0;
