@@ -34,7 +34,7 @@ UNIT = "CMAC/s"
 KERNEL_TRAFFIC = {
     # ncu --set full of flush_tc_kernel on `bench.py --small` (P=2, T=2048, 400 energies, default tiling):
     # dram__bytes_read.sum 2.275640 GB + dram__bytes_write.sum 0.204266 GB per launch of 1.07e11 CMAC
-    "0f1f317175bb73aa": 2.309592e-02,
+    ("0f1f317175bb73aa", "flush_tc_kernel"): 2.309592e-02,
 }
 
 
@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2, help="end-to-end steps from pinned host memory (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU oracle baseline")
     ap.add_argument("--small", action="store_true", help="small workload (profiling captures)")
+    ap.add_argument("--in-place", dest="in_place", action="store_true", default=True,
+                    help="the contraction reads pushed frames in place (default)")
+    ap.add_argument("--staging", dest="in_place", action="store_false",
+                    help="convert pushed frames into the library's staging area at push time")
     ap.add_argument("--tc-accumulators", type=int, default=0, help="tensor-core tiling override (0: plan default)")
     ap.add_argument("--tc-omega-tile", type=int, default=0)
     ap.add_argument("--tc-cluster", type=int, default=0)
@@ -295,7 +299,8 @@ def main():
         return ms / steps, kms / max(kn, 1), kn // max(steps, 1), launches, clocks
 
     tiling = dict(tc_accumulators=args.tc_accumulators, tc_omega_tile=args.tc_omega_tile,
-                  tc_cluster=args.tc_cluster, tc_block_frames=args.tc_block_frames)
+                  tc_cluster=args.tc_cluster, tc_block_frames=args.tc_block_frames,
+                  frames_in_place=bool(args.in_place and args.precision == "split_bf16"))
     plan = TacawPlan([stream_config(spec)], precision=args.precision, **tiling)
     info = plan.info()
     ms_step, k_ms, k_per_step, launches, clocks = timed(plan, args.steps, args.warmup, sample_clocks=True)
@@ -334,55 +339,12 @@ def main():
                                    subtract_mean=spec.subtract_mean)
     err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
 
-    # end to end through the public API from pinned host memory (host ring of pushes, cycled)
-    e2e = None
-    if args.e2e_steps > 0:
-        ring = min(16, n_push)
-        push_elems = Tc * frame_elems
-        host = torch.empty(ring * push_elems, dtype=torch.complex64, pin_memory=True)
-        host.copy_(x[: ring * push_elems])
-        dev = [torch.empty(push_elems, dtype=torch.complex64, device="cuda") for _ in range(2)]
-        S_host = torch.empty(S.numel(), dtype=torch.float32, pin_memory=True)
-        cs = torch.cuda.Stream()
-        done_ev = [torch.cuda.Event() for _ in range(2)]
-        ready_ev = [torch.cuda.Event() for _ in range(2)]
-
-        def e2e_step():
-            plan.reset(st)
-            for i in range(n_push):
-                b = i % 2
-                n = min(Tc, T - i * Tc)
-                with torch.cuda.stream(cs):
-                    cs.wait_event(done_ev[b])
-                    dev[b][: n * frame_elems].copy_(host[(i % ring) * push_elems:(i % ring) * push_elems
-                                                        + n * frame_elems], non_blocking=True)
-                    ready_ev[b].record(cs)
-                stream.wait_event(ready_ev[b])
-                plan.push(0, dev[b].data_ptr(), n, st)
-                done_ev[b].record(stream)
-            plan.finalize(I, S, None, st)
-            S_host.copy_(S, non_blocking=True)
-            torch.cuda.synchronize()
-
-        for b in range(2):
-            done_ev[b].record(stream)
-        e2e_step()
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            e2e_step()
-        el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
-        e2e = {"value": world * cmac_step * args.e2e_steps / el, "unit": UNIT,
-               "h2d_bytes_per_step": T * frame_elems * 8, "d2h_bytes_per_step": S.numel() * 4,
-               "ms_per_step": 1e3 * el / args.e2e_steps,
-               "input": f"pinned host ring of {ring} pushes ({ring * push_elems * 8 / 1e9:.1f} GB) cycled"}
-        del host, dev
-    plan.close()
 
     # tensor-core tiling with a single accumulator per tile: faster, larger accumulation error
     fast = None
     if args.fast_steps > 0 and args.precision == "split_bf16":
-        with TacawPlan([stream_config(spec)], precision="split_bf16", tc_accumulators=1) as pf:
+        with TacawPlan([stream_config(spec)], precision="split_bf16", tc_accumulators=1,
+                       frames_in_place=bool(args.in_place)) as pf:
             msf, kf, _, _, _ = timed(pf, args.fast_steps, 1)
             fi = pf.info()
         gotf = Iv[torch.as_tensor(probes, device="cuda"), :, torch.as_tensor(pix, device="cuda")].cpu().numpy().T
@@ -402,6 +364,48 @@ def main():
         fp32 = {"value": world * cmac_step / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32,
                 "flush_ms": k32, "max_rel_err_I_vs_fp64": err32}
 
+    # end to end through the public API from pinned host memory (host ring of pushes, cycled);
+    # last, because it overwrites the device input with the cycled ring
+    e2e = None
+    if args.e2e_steps > 0:
+        ring = min(16, n_push)
+        push_elems = Tc * frame_elems
+        host = torch.empty(ring * push_elems, dtype=torch.complex64, pin_memory=True)
+        host.copy_(x[: ring * push_elems])
+        S_host = torch.empty(S.numel(), dtype=torch.float32, pin_memory=True)
+        cs = torch.cuda.Stream()
+        ready_ev = [torch.cuda.Event() for _ in range(n_push)]
+
+        def e2e_step():
+            # every push: pinned host -> its slice of the device input (copy stream), then the push;
+            # the slices stay untouched until finalize, so in-place plans may read them directly
+            plan.reset(st)
+            cs.wait_stream(stream)
+            for i in range(n_push):
+                n = min(Tc, T - i * Tc)
+                with torch.cuda.stream(cs):
+                    x[i * push_elems:i * push_elems + n * frame_elems].copy_(
+                        host[(i % ring) * push_elems:(i % ring) * push_elems + n * frame_elems], non_blocking=True)
+                    ready_ev[i].record(cs)
+                stream.wait_event(ready_ev[i])
+                plan.push(0, base + i * push_elems * 8, n, st)
+            plan.finalize(I, S, None, st)
+            S_host.copy_(S, non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": world * cmac_step * args.e2e_steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": T * frame_elems * 8, "d2h_bytes_per_step": S.numel() * 4,
+               "ms_per_step": 1e3 * el / args.e2e_steps,
+               "input": f"pinned host ring of {ring} pushes ({ring * push_elems * 8 / 1e9:.1f} GB) cycled"}
+        del host
+    plan.close()
+
     # roofline of the dominant kernel (the contraction) from its live CUDA-event duration
     peaks, peak_src = measured_peaks()
     cmac_launch = cmac_step / max(k_per_step, 1)
@@ -410,10 +414,11 @@ def main():
         achieved = cmac_launch * 24 / (k_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         src = os.path.join(ROOT, "paper_2607_02236_gb300", "csrc", "k_tc_gemm.cu")
-        tr = KERNEL_TRAFFIC.get(file_hash(src))
+        kname = "flush_tc_direct_kernel" if info["frames_in_place"] else "flush_tc_kernel"
+        tr = KERNEL_TRAFFIC.get((file_hash(src), kname))
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": (tr * cmac_launch if tr else None),
-                "kernel": "flush_tc_kernel", "flop_per_cmac": 24,
+                "kernel": kname, "flop_per_cmac": 24,
                 "peak_source": f"{peak_src} bf16 sustained (MEASURED_PEAKS.json)",
                 "kernel_ms": k_ms, "launches_per_step": k_per_step}
     else:
@@ -449,7 +454,7 @@ def main():
                                                           if args.precision == "split_bf16" else ""),
                            "k_stage": info["k_stage"], "omega_tile": info["omega_tile"],
                            "tc_accumulators": info["tc_accumulators"], "tc_block_frames": info["tc_block_frames"],
-                           "tc_cluster": info["tc_cluster"],
+                           "tc_cluster": info["tc_cluster"], "frames_in_place": bool(info["frames_in_place"]),
                            "smem_stages": info["stages"], "plan_device_GB": round(info["device_bytes"] / 1e9, 2),
                            "l2": "inputs (%.1f GB) larger than L2, no flush" % (T * frame_elems * 8 / 1e9),
                            "parallelism": f"replicas x{world}"},

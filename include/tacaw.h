@@ -130,6 +130,11 @@ typedef struct {
     int tc_cluster;
     int tc_block_frames;
     int tc_prefetch;
+    /* != 0 (split path only): pushed buffers are read in place by the contraction instead of
+     * being converted into a staging area at push time.  Each pushed buffer must then stay
+     * valid and unchanged until the flush that covers its frames has completed on the stream:
+     * with the default K_stage (the whole segment) that is until tacaw_finalize returns. */
+    int frames_in_place;
 } tacaw_plan_desc;
 
 typedef struct tacaw_plan_s *tacaw_plan_t;
@@ -148,6 +153,7 @@ typedef struct {
     int tc_accumulators;       /* TMEM accumulators per tile (split path) */
     int tc_cluster;            /* cluster size of the contraction (split path, first stream) */
     int tc_block_frames;       /* frames per staged operand row (split path) */
+    int frames_in_place;       /* pushed frames are read in place by the contraction */
 } tacaw_plan_info;
 
 /* Creates a plan: validates the descriptor, sizes and allocates device memory

@@ -54,6 +54,8 @@ struct TcShared {
     int abort_flag;
     float2 W[256];      // window transform W(E_j) of this CTA's energies
     float bose[256];    // Bose factors of this CTA's energies
+    double2 rowsum[kMTile];   // in-place kernel: sum over this flush of (psi - mu_hat) per row
+    uint64_t sums_ready;      // in-place kernel: producers -> epilogue
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -259,6 +261,79 @@ __device__ __forceinline__ void tc_epilogue(const TcPlanArgs &a, const TcShared 
     }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void split2_bf16(float2 r, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat16 hr = __float2bfloat16_rn(r.x), hi_ = __float2bfloat16_rn(r.y);
+    const __nv_bfloat16 lr = __float2bfloat16_rn(r.x - __bfloat162float(hr));
+    const __nv_bfloat16 li = __float2bfloat16_rn(r.y - __bfloat162float(hi_));
+    hi = (uint32_t)__bfloat16_as_ushort(hr) | ((uint32_t)__bfloat16_as_ushort(hi_) << 16);
+    lo = (uint32_t)__bfloat16_as_ushort(lr) | ((uint32_t)__bfloat16_as_ushort(li) << 16);
+}
+
+// MMA issue loop (one thread): per stage, bf/8 K-steps of 3 products into the accumulators;
+// tcgen05.commit releases the stage (to every CTA of the cluster when multicast) and, at the
+// end, signals the epilogue.
+__device__ __forceinline__ void tc_mma_loop(const TcPlanArgs &a, TcShared *sh, uint32_t base_s, uint32_t stage_bytes,
+                                            uint32_t kABytes, uint32_t b_pad, uint32_t RB, uint32_t tmem,
+                                            volatile int *abort_flag, unsigned long long *trace, bool multicast) {
+    const uint16_t cmask = (uint16_t)((1u << a.cluster) - 1u);
+    const int n0 = a.N < 256 ? a.N : 256;
+    const int n1 = a.N - n0;
+    const uint32_t id0 = idesc_bf16_f32(kMTile, n0);
+    const uint32_t id1 = n1 > 0 ? idesc_bf16_f32(kMTile, n1) : 0u;
+    const uint64_t b_half_off = (uint64_t)((n0 * RB) >> 4);
+    const uint32_t acc_small = tmem + (uint32_t)(a.n_big * a.N);
+    const int ksteps = a.bf / 8;
+    for (int kb = 0; kb < a.n_kb; ++kb) {
+        const int s = kb % a.stages;
+        const uint32_t use = (uint32_t)(kb / a.stages);
+        if (!mbar_wait(smem_u32(&sh->full[s]), use & 1u, abort_flag)) {
+            if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
+            *abort_flag = 1;
+            break;
+        }
+        tc_fence_after();
+        if (trace && kb == 0) trace[2] = globaltimer();
+        const uint32_t st = base_s + (uint32_t)s * stage_bytes;
+        const uint64_t dAhi0 = sdesc_k(st, RB);
+        const uint64_t dAlo0 = sdesc_k(st + kABytes, RB);
+        const uint64_t dBhi0 = sdesc_k(st + 2 * kABytes, RB);
+        const uint64_t dBlo0 = sdesc_k(st + 2 * kABytes + b_pad, RB);
+        for (int ks = 0; ks < ksteps; ++ks) {
+            // K-step ks starts 32*ks bytes into the swizzled rows (start address in 16 B units)
+            const uint64_t adv = (uint64_t)(2 * ks);
+            const uint64_t dAhi = dAhi0 + adv, dAlo = dAlo0 + adv, dBhi = dBhi0 + adv, dBlo = dBlo0 + adv;
+            const int g = kb * ksteps + ks;       // global K-step index
+            if (a.split) {
+                // N <= 256: one MMA per product
+                const int big = a.n_big == 2 ? (g & 1) : 0;
+                mma_bf16_ss(tmem + (uint32_t)(big * a.N), dAhi, dBhi, id0, g >= a.n_big ? 1u : 0u);
+                mma_bf16_ss(acc_small, dAhi, dBlo, id0, g > 0 ? 1u : 0u);
+                mma_bf16_ss(acc_small, dAlo, dBhi, id0, 1u);
+            } else {
+#pragma unroll
+                for (int pass = 0; pass < 3; ++pass) {
+                    const uint64_t dA = pass == 2 ? dAlo : dAhi;
+                    const uint64_t dB = pass == 1 ? dBlo : dBhi;
+                    const uint32_t acc = (g > 0 || pass > 0) ? 1u : 0u;
+                    mma_bf16_ss(tmem, dA, dB, id0, acc);
+                    if (n1 > 0) mma_bf16_ss(tmem + (uint32_t)n0, dA, dB + b_half_off, id1, acc);
+                }
+            }
+        }
+        if (multicast)
+            mma_commit_mc(smem_u32(&sh->empty[s]), cmask);
+        else
+            mma_commit(smem_u32(&sh->empty[s]));
+    }
+    // always signal: the epilogue (and TMEM release) wait for every issued MMA
+    mma_commit(smem_u32(&sh->tmem_full));
+    if (trace) trace[3] = globaltimer();
+}
+
 __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant__ TcMaps maps, const TcPlanArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -359,60 +434,7 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            const int n0 = a.N < 256 ? a.N : 256;
-            const int n1 = a.N - n0;
-            const uint32_t id0 = idesc_bf16_f32(kMTile, n0);
-            const uint32_t id1 = n1 > 0 ? idesc_bf16_f32(kMTile, n1) : 0u;
-            const uint64_t b_half_off = (uint64_t)((n0 * RB) >> 4);
-            const uint32_t acc_small = tmem + (uint32_t)(a.n_big * a.N);
-            const int ksteps = a.bf / 8;
-            for (int kb = 0; kb < a.n_kb; ++kb) {
-                const int s = kb % a.stages;
-                const uint32_t use = (uint32_t)(kb / a.stages);
-                if (!mbar_wait(smem_u32(&sh->full[s]), use & 1u, abort_flag)) {
-                    if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
-                    *abort_flag = 1;
-                    break;
-                }
-                tc_fence_after();
-                if (trace && kb == 0) trace[2] = globaltimer();
-                const uint32_t st = base_s + (uint32_t)s * stage_bytes;
-                const uint64_t dAhi0 = sdesc_k(st, RB);
-                const uint64_t dAlo0 = sdesc_k(st + kABytes, RB);
-                const uint64_t dBhi0 = sdesc_k(st + 2 * kABytes, RB);
-                const uint64_t dBlo0 = sdesc_k(st + 2 * kABytes + b_pad, RB);
-                for (int ks = 0; ks < ksteps; ++ks) {
-                    // K-step ks starts 32*ks bytes into the swizzled rows (start address in 16 B units)
-                    const uint64_t adv = (uint64_t)(2 * ks);
-                    const uint64_t dAhi = dAhi0 + adv, dAlo = dAlo0 + adv, dBhi = dBhi0 + adv, dBlo = dBlo0 + adv;
-                    const int g = kb * ksteps + ks;       // global K-step index
-                    if (a.split) {
-                        // N <= 256: one MMA per product
-                        const int big = a.n_big == 2 ? (g & 1) : 0;
-                        mma_bf16_ss(tmem + (uint32_t)(big * a.N), dAhi, dBhi, id0, g >= a.n_big ? 1u : 0u);
-                        mma_bf16_ss(acc_small, dAhi, dBlo, id0, g > 0 ? 1u : 0u);
-                        mma_bf16_ss(acc_small, dAlo, dBhi, id0, 1u);
-                    } else {
-#pragma unroll
-                        for (int pass = 0; pass < 3; ++pass) {
-                            const uint64_t dA = pass == 2 ? dAlo : dAhi;
-                            const uint64_t dB = pass == 1 ? dBlo : dBhi;
-                            const uint32_t acc = (g > 0 || pass > 0) ? 1u : 0u;
-                            mma_bf16_ss(tmem, dA, dB, id0, acc);
-                            if (n1 > 0) mma_bf16_ss(tmem + (uint32_t)n0, dA, dB + b_half_off, id1, acc);
-                        }
-                    }
-                }
-                if (C > 1)
-                    mma_commit_mc(smem_u32(&sh->empty[s]), cmask);
-                else
-                    mma_commit(smem_u32(&sh->empty[s]));
-            }
-            // always signal: the epilogue (and TMEM release) wait for every issued MMA
-            mma_commit(smem_u32(&sh->tmem_full));
-            if (trace) trace[3] = globaltimer();
-        }
+        if (lane == 0) tc_mma_loop(a, sh, base_s, stage_bytes, kABytes, b_pad, RB, tmem, abort_flag, trace, C > 1);
     } else {
         // epilogue warps 2..5 -> TMEM lane quarter q = warp % 4
         const int q = warp & 3;
@@ -456,6 +478,215 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
     __syncthreads();
     if (C > 1) cluster_sync();   // no CTA leaves while a peer may still signal its barriers
     if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, ncols);
+    }
+    if (trace && threadIdx.x == 0) trace[6] = globaltimer();
+}
+
+// --------------------------------------------------------------------------------------
+// In-place variant: operand A is read from the caller's pushed complex64 frames.
+//
+//   warps 0-3   A producers: thread r owns tile row r; per staging block it loads the row's bf
+//               frames (coalesced 8-byte loads across the warp, through a per-frame pointer
+//               table), subtracts the provisional mean, splits into bf16 hi/lo and writes the
+//               16-byte chunks of the swizzled K-major rows (128/64/32-byte swizzle pattern of
+//               the row width); fence.proxy.async makes them visible to the tensor core before
+//               the thread arrives on the stage barrier.  Each row's residual sum is kept: the
+//               CTA's epilogue derives the exact mean correction from it (and earlier flushes'
+//               sums), and the first energy tile adds it to the running sums for later flushes.
+//   warp 4      B producer (TMA of this CTA's twiddle rows)
+//   warp 5      TMEM allocator + MMA issuer
+//   warps 6..9  epilogue
+// --------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(320, 1) flush_tc_direct_kernel(const __grid_constant__ TcMaps maps,
+                                                                 const TcPlanArgs a, const TcDirectArgs d) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t RB = 4u * (uint32_t)a.bf;
+    const uint32_t kABytes = tc_a_bytes(a.bf);
+    const uint32_t b_pad = tc_b_bytes_padded(a.N, a.bf);
+    const uint32_t stage_bytes = tc_stage_bytes(a.N, a.bf);
+    TcShared *sh = reinterpret_cast<TcShared *>(base + (size_t)a.stages * stage_bytes);
+    const uint32_t base_s = smem_u32(base);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wtile = (int)(blockIdx.x % (unsigned)a.n_wt);
+    const int m0 = (int)(blockIdx.x / (unsigned)a.n_wt) * kMTile;
+    const int n_acc = a.split ? a.n_big + 1 : 1;
+    const uint32_t ncols = tc_tmem_cols(n_acc * a.N);
+    const uint32_t tx_bytes_b = 2u * (uint32_t)a.N * RB;
+    unsigned long long *trace = a.trace ? a.trace + (size_t)blockIdx.x * kTraceWords : nullptr;
+    if (trace && threadIdx.x == 0) {
+        trace[0] = globaltimer();
+        trace[7] = smid();
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(smem_u32(&sh->full[s]), kMTile + 1);   // 128 A rows + the B producer
+            mbar_init(smem_u32(&sh->empty[s]), 1);
+        }
+        mbar_init(smem_u32(&sh->tmem_full), 1);
+        mbar_init(smem_u32(&sh->sums_ready), kMTile);
+        sh->abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 5) {
+        tmem_alloc(smem_u32(&sh->tmem_addr), ncols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_addr;
+    volatile int *abort_flag = &sh->abort_flag;
+    if (trace && threadIdx.x == 0) trace[1] = globaltimer();
+
+    if (warp < 4) {
+        // ---------------- A producers ----------------
+        const int r = threadIdx.x;
+        const int64_t m = (int64_t)m0 + r;
+        const bool valid = m < d.M;
+        int64_t off = 0;
+        float2 mu = make_float2(0.f, 0.f);
+        if (valid) {
+            const int64_t p = m / d.npix, pix = m - (m / d.npix) * d.npix;
+            const int64_t y = pix / d.kx, x = pix - (pix / d.kx) * d.kx;
+            off = p * d.pitch_probe + (d.roi_y0 + y) * d.pitch_row + (d.roi_x0 + x);
+            mu = d.mu_hat[m];
+        }
+        const int cpr = a.bf / 4;                                   // 16-byte chunks per row
+        const uint32_t row_byte = (uint32_t)r * RB;
+        const uint32_t sw = (row_byte >> 7) & (uint32_t)(cpr - 1);  // swizzle phase of this row
+        double sr = 0.0, si = 0.0;
+        bool ok = true;
+        for (int kb = 0; kb < a.n_kb && ok; ++kb) {
+            const int s = kb % a.stages;
+            const uint32_t use = (uint32_t)(kb / a.stages);
+            if (!mbar_wait(smem_u32(&sh->empty[s]), (use & 1u) ^ 1u, abort_flag)) {
+                if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
+                *abort_flag = 1;
+                ok = false;
+                break;
+            }
+            uint8_t *st = base + (size_t)s * stage_bytes;
+            const int f0 = kb * a.bf;
+            for (int c = 0; c < cpr; ++c) {
+                float2 v[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int f = f0 + 4 * c + i;
+                    v[i] = (valid && f < d.n_frames) ? __ldcs(d.frame_ptr[f] + off) : mu;
+                }
+                uint32_t h[4], l[4];
+                float br = 0.f, bi = 0.f;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float2 q = make_float2(v[i].x - mu.x, v[i].y - mu.y);
+                    br += q.x;
+                    bi += q.y;
+                    split2_bf16(q, h[i], l[i]);
+                }
+                sr += br;
+                si += bi;
+                const uint32_t chunk = ((uint32_t)c ^ sw) * 16u;
+                *reinterpret_cast<uint4 *>(st + row_byte + chunk) = make_uint4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<uint4 *>(st + kABytes + row_byte + chunk) = make_uint4(l[0], l[1], l[2], l[3]);
+            }
+            // generic-proxy writes -> visible to the tensor core (async proxy) before the arrive
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(smem_u32(&sh->full[s]));
+        }
+        // this flush's residual sums: to the epilogue, and (first energy tile) to the running sums
+        sh->rowsum[r] = make_double2(sr, si);
+        if (valid && wtile == 0 && d.accumulate_sums) {
+            double2 t = d.sum_res[m];
+            t.x += sr;
+            t.y += si;
+            d.sum_res[m] = t;
+        }
+        mbar_arrive(smem_u32(&sh->sums_ready));
+    } else if (warp == 4) {
+        // ---------------- B producer ----------------
+        if (lane == 0) {
+            for (int kb = 0; kb < a.n_kb; ++kb) {
+                const int s = kb % a.stages;
+                const uint32_t use = (uint32_t)(kb / a.stages);
+                if (!mbar_wait(smem_u32(&sh->empty[s]), (use & 1u) ^ 1u, abort_flag)) {
+                    if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
+                    *abort_flag = 1;
+                    break;
+                }
+                const uint32_t full = smem_u32(&sh->full[s]);
+                const uint32_t st = base_s + (uint32_t)s * stage_bytes;
+                mbar_arrive_expect_tx(full, tx_bytes_b);
+                for (int b = 0; b < maps.nbox_b; ++b) {
+                    const int r0 = b * maps.box_b_rows;
+                    const uint32_t off = (uint32_t)r0 * RB;
+                    tma_load_3d(st + 2 * kABytes + off, &maps.b_hi, 0, wtile * a.N + r0, a.kbB0 + kb, full);
+                    tma_load_3d(st + 2 * kABytes + b_pad + off, &maps.b_lo, 0, wtile * a.N + r0, a.kbB0 + kb, full);
+                }
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) tc_mma_loop(a, sh, base_s, stage_bytes, kABytes, b_pad, RB, tmem, abort_flag, trace, false);
+    } else {
+        // ---------------- epilogue: warps 6..9 ----------------
+        const int q = warp & 3;
+        {
+            const int jb = wtile * a.wt;
+            for (int i = threadIdx.x - 192; i < a.wt; i += 128) {
+                const int j = jb + i;
+                sh->W[i] = j < a.e.Nw ? __ldg(a.e.Wc + j) : make_float2(0.f, 0.f);
+                sh->bose[i] = j < a.e.Nw ? __ldg(a.e.bose + j) : 0.f;
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+        }
+        const bool ok = mbar_wait(smem_u32(&sh->tmem_full), 0u, nullptr);
+        if (!ok) {
+            atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
+            *abort_flag = 1;
+        }
+        const bool ok2 = ok && mbar_wait(smem_u32(&sh->sums_ready), 0u, abort_flag);
+        tc_fence_after();
+        if (trace && warp == 6 && lane == 0) trace[4] = globaltimer();
+        if (ok2 && !*abort_flag) {
+            const int rr = q * 32 + lane;
+            const int64_t m = (int64_t)m0 + rr;
+            RowCtx row;
+            row.m = m;
+            row.valid = m < d.M;
+            const int64_t p = row.valid ? m / d.npix : 0;
+            row.out_base = p * (int64_t)a.e.Nw * d.npix + (m - p * d.npix);
+            row.dmu = make_float2(0.f, 0.f);
+            if (row.valid && d.subtract_mean && a.e.mode == FLUSH_FINAL) {
+                double2 t = sh->rowsum[rr];
+                if (d.prev_sums) {
+                    const double2 pv = d.sum_res[m];
+                    t.x += pv.x;
+                    t.y += pv.y;
+                }
+                row.dmu = make_float2((float)(t.x / d.T), (float)(t.y / d.T));
+            }
+            const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+            const int total_steps = a.n_kb * (a.bf / 8);
+            const int n_big_used = a.split ? (total_steps < a.n_big ? total_steps : a.n_big) : 0;
+            const int jbase = wtile * a.wt;
+            switch (epi_kind(a.e)) {
+                case EPI_FINAL: tc_epilogue<EPI_FINAL>(a, sh, row, lane_base, jbase, n_big_used); break;
+                case EPI_FINAL_KAHAN: tc_epilogue<EPI_FINAL_KAHAN>(a, sh, row, lane_base, jbase, n_big_used); break;
+                case EPI_FINAL_FP64: tc_epilogue<EPI_FINAL_FP64>(a, sh, row, lane_base, jbase, n_big_used); break;
+                case EPI_STORE_KAHAN: tc_epilogue<EPI_STORE_KAHAN>(a, sh, row, lane_base, jbase, n_big_used); break;
+                case EPI_STORE_FP64: tc_epilogue<EPI_STORE_FP64>(a, sh, row, lane_base, jbase, n_big_used); break;
+                case EPI_ADD_KAHAN: tc_epilogue<EPI_ADD_KAHAN>(a, sh, row, lane_base, jbase, n_big_used); break;
+                default: tc_epilogue<EPI_ADD_FP64>(a, sh, row, lane_base, jbase, n_big_used); break;
+            }
+        }
+        if (trace && warp == 6 && lane == 0) trace[5] = globaltimer();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 5) {
         tc_fence_after();
         tmem_dealloc(tmem, ncols);
     }
@@ -551,6 +782,34 @@ bool tc_make_maps(void *maps_out, const __nv_bfloat16 *A_hi, const __nv_bfloat16
                   "B_lo"))
         return false;
     return true;
+}
+
+bool tc_make_maps_b(void *maps_out, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
+                    int N, int bf, char *errbuf, size_t errlen) {
+    TcMaps *m = reinterpret_cast<TcMaps *>(maps_out);
+    memset(m, 0, sizeof(TcMaps));
+    if (!tc_b_boxes(N, 1, &m->box_b_rows, &m->nbox_b)) {
+        snprintf(errbuf, errlen, "tile of %d columns has no valid twiddle box split", N);
+        return false;
+    }
+    const uint64_t d0 = 2 * (uint64_t)bf;
+    if (!encode3d(&m->b_hi, B_hi, d0, 2 * (uint64_t)Nw_pad, (uint64_t)n_kb_T, (uint32_t)m->box_b_rows, errbuf, errlen,
+                  "B_hi"))
+        return false;
+    return encode3d(&m->b_lo, B_lo, d0, 2 * (uint64_t)Nw_pad, (uint64_t)n_kb_T, (uint32_t)m->box_b_rows, errbuf, errlen,
+                    "B_lo");
+}
+
+size_t tc_smem_bytes_direct(int N, int bf, int stages) { return tc_smem_bytes(N, bf, stages); }
+
+cudaError_t launch_flush_tc_direct(const TcPlanArgs &a, const TcDirectArgs &d, const void *maps, cudaStream_t st) {
+    const size_t smem = tc_smem_bytes(a.N, a.bf, a.stages);
+    cudaError_t e = cudaFuncSetAttribute(flush_tc_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (a.e.M_pad / kMTile) * a.n_wt;
+    if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    flush_tc_direct_kernel<<<(unsigned)blocks, 320, smem, st>>>(*reinterpret_cast<const TcMaps *>(maps), a, d);
+    return cudaGetLastError();
 }
 
 // Co-resident CTAs of the contraction kernel for a cluster size (0 on error).

@@ -76,6 +76,9 @@ struct Stream {
     int n_adj = 0;
     std::vector<unsigned char> tc_maps;
     int tc_cluster = 1;
+    // in-place frames: per staged frame, a pointer into the pushed buffer
+    std::vector<const float2 *> h_frame_ptr;
+    const float2 **d_frame_ptr = nullptr;
     // segment state
     int pushed = 0, staged = 0, stage_start = 0, flushes = 0;
     int64_t I_off = 0, S_off = 0;
@@ -90,6 +93,7 @@ struct tacaw_plan_s {
     int tc_acc = 3;
     int bf = 8;                // frames per staged operand row (split path)
     int tc_prefetch = 0;       // L2 prefetch distance of operand A in staging blocks
+    bool in_place = false;     // the contraction reads pushed frames directly
     int64_t bytes = 0;
     int64_t I_elems = 0, S_elems = 0;
     int64_t flushes_total = 0;
@@ -239,7 +243,55 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         CU_CHECK(p, cudaEventCreate(&e1), "cudaEventCreate");
         CU_CHECK(p, cudaEventRecord(e0, st), "cudaEventRecord");
     }
-    if (p->prec == TACAW_PREC_SPLIT_BF16) {
+    if (p->prec == TACAW_PREC_SPLIT_BF16 && p->in_place) {
+        TcPlanArgs a{};
+        a.e = e;
+        a.wt = s.wt;
+        a.n_wt = s.n_wt;
+        a.N = 2 * s.wt;
+        a.n_kb = (n + p->bf - 1) / p->bf;
+        a.kbB0 = s.stage_start / p->bf;
+        a.bf = p->bf;
+        a.stages = p->stages;
+        a.split = p->tc_acc > 1 ? 1 : 0;
+        a.n_big = p->tc_acc == 3 ? 2 : 1;
+        a.cluster = 1;
+        a.prefetch = 0;
+        a.err = p->d_err;
+        a.trace = nullptr;
+        if (p->trace) {
+            const int64_t nc = (s.M_pad / kMTile) * s.n_wt;
+            if (nc > p->trace_cap) {
+                if (p->d_trace) cudaFree(p->d_trace);
+                p->d_trace = nullptr;
+                p->trace_cap = 0;
+                CU_CHECK(p, cudaMalloc(&p->d_trace, sizeof(unsigned long long) * kTraceWords * nc), "trace buffer");
+                p->trace_cap = nc;
+            }
+            p->trace_ctas = nc;
+            a.trace = p->d_trace;
+        }
+        CU_CHECK(p, cudaMemcpyAsync(s.d_frame_ptr, s.h_frame_ptr.data(), sizeof(const float2 *) * n,
+                                    cudaMemcpyHostToDevice, st), "frame table");
+        TcDirectArgs d{};
+        d.frame_ptr = s.d_frame_ptr;
+        d.n_frames = n;
+        d.M = s.M;
+        d.npix = s.npix;
+        d.kx = s.d.kx;
+        d.pitch_row = s.d.pitch_row;
+        d.pitch_probe = s.d.pitch_probe;
+        d.roi_x0 = s.d.roi_x0;
+        d.roi_y0 = s.d.roi_y0;
+        d.mu_hat = s.mu_hat;
+        d.sum_res = s.sum_res;
+        d.accumulate_sums = mode != FLUSH_FINAL ? 1 : 0;
+        d.prev_sums = s.flushes > 0 ? 1 : 0;
+        d.subtract_mean = s.d.subtract_mean;
+        d.T = s.T;
+        CU_CHECK(p, launch_flush_tc_direct(a, d, s.tc_maps.data(), st), "flush (tensor cores, in place)");
+        p->launches++;
+    } else if (p->prec == TACAW_PREC_SPLIT_BF16) {
         if (n % p->bf) {
             CU_CHECK(p, launch_zero_tail_split(s.M_pad, n, p->bf, s.A_hi, s.A_lo, st), "zero_tail");
             p->launches++;
@@ -334,16 +386,24 @@ tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
         const size_t nb = (size_t)s.n_kb_T * 2 * s.Nw_pad * 2 * p->bf;
         if (!dev_alloc(p, &s.B_hi, nb) || !dev_alloc(p, &s.B_lo, nb)) return fail(TACAW_ERR_OOM, "cudaMalloc(B split)");
         CU_CHECK(p, launch_twiddles_split(ta, s.B_hi, s.B_lo, st), "twiddles split");
-        const size_t na = (size_t)(s.ring / p->bf) * s.M_pad * 2 * p->bf;
-        if (!dev_alloc(p, &s.A_hi, na) || !dev_alloc(p, &s.A_lo, na)) return fail(TACAW_ERR_OOM, "cudaMalloc(staging)");
-        // rows >= M and never-written slots must read as zeros
-        CU_CHECK(p, cudaMemsetAsync(s.A_hi, 0, na * sizeof(__nv_bfloat16), st), "memset staging");
-        CU_CHECK(p, cudaMemsetAsync(s.A_lo, 0, na * sizeof(__nv_bfloat16), st), "memset staging");
         s.tc_maps.resize(tc_maps_size());
         char eb[256];
-        if (!tc_make_maps(s.tc_maps.data(), s.A_hi, s.A_lo, s.M_pad, s.ring / p->bf, s.B_hi, s.B_lo, s.Nw_pad,
-                          s.n_kb_T, 2 * s.wt, s.tc_cluster, p->bf, eb, sizeof(eb)))
-            return fail(TACAW_ERR_CUDA, "%s", eb);
+        if (p->in_place) {
+            s.h_frame_ptr.assign(s.ring, nullptr);
+            if (!dev_alloc(p, &s.d_frame_ptr, s.ring)) return fail(TACAW_ERR_OOM, "cudaMalloc(frame table)");
+            if (!tc_make_maps_b(s.tc_maps.data(), s.B_hi, s.B_lo, s.Nw_pad, s.n_kb_T, 2 * s.wt, p->bf, eb, sizeof(eb)))
+                return fail(TACAW_ERR_CUDA, "%s", eb);
+        } else {
+            const size_t na = (size_t)(s.ring / p->bf) * s.M_pad * 2 * p->bf;
+            if (!dev_alloc(p, &s.A_hi, na) || !dev_alloc(p, &s.A_lo, na))
+                return fail(TACAW_ERR_OOM, "cudaMalloc(staging)");
+            // rows >= M and never-written slots must read as zeros
+            CU_CHECK(p, cudaMemsetAsync(s.A_hi, 0, na * sizeof(__nv_bfloat16), st), "memset staging");
+            CU_CHECK(p, cudaMemsetAsync(s.A_lo, 0, na * sizeof(__nv_bfloat16), st), "memset staging");
+            if (!tc_make_maps(s.tc_maps.data(), s.A_hi, s.A_lo, s.M_pad, s.ring / p->bf, s.B_hi, s.B_lo, s.Nw_pad,
+                              s.n_kb_T, 2 * s.wt, s.tc_cluster, p->bf, eb, sizeof(eb)))
+                return fail(TACAW_ERR_CUDA, "%s", eb);
+        }
     } else {
         const size_t na = (size_t)s.ring * s.M_pad;
         if (!dev_alloc(p, &s.A32, na)) return fail(TACAW_ERR_OOM, "cudaMalloc(staging)");
@@ -477,6 +537,11 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     tacaw_plan_s *p = new (std::nothrow) tacaw_plan_s();
     if (!p) return fail(TACAW_ERR_OOM, "host allocation failed");
     p->tc_acc = desc->tc_accumulators ? desc->tc_accumulators : 3;
+    if (desc->frames_in_place && desc->precision != TACAW_PREC_SPLIT_BF16) {
+        delete p;
+        return fail(TACAW_ERR_UNSUPPORTED, "frames_in_place needs the split-BF16 path");
+    }
+    p->in_place = desc->frames_in_place != 0;
     if (desc->precision == TACAW_PREC_SPLIT_BF16) {
         // widest rows first: fewer, larger TMA requests per MMA K-step
         if (desc->tc_block_frames) {
@@ -529,7 +594,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         int64_t b = fixed;
         for (auto &s : p->s) {
             const int ring = std::min(K, s.T_pad);
-            b += stream_stage_bytes(s, ring);
+            b += p->in_place ? (int64_t)ring * 8 : stream_stage_bytes(s, ring);
             if (s.T > ring) b += stream_acc_bytes(s);
         }
         return b;
@@ -667,12 +732,18 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
         const int chunk = std::min(n_frames - done, s.ring - s.staged);
         FrameGeom gc = g;
         gc.base = g.base + (int64_t)done * g.pitch_frame;
-        if (p->prec == TACAW_PREC_SPLIT_BF16)
-            CU_CHECK(p, launch_convert_split(gc, chunk, s.staged, p->bf, s.M_pad, s.mu_hat, s.sum_res, s.A_hi, s.A_lo, st),
-                     "convert");
-        else
-            CU_CHECK(p, launch_convert_fp32(gc, chunk, s.staged, s.M_pad, s.mu_hat, s.sum_res, s.A32, st), "convert");
-        p->launches++;
+        if (p->in_place) {
+            for (int t = 0; t < chunk; ++t) s.h_frame_ptr[s.staged + t] = gc.base + (int64_t)t * g.pitch_frame;
+        } else {
+            if (p->prec == TACAW_PREC_SPLIT_BF16)
+                CU_CHECK(p, launch_convert_split(gc, chunk, s.staged, p->bf, s.M_pad, s.mu_hat, s.sum_res, s.A_hi,
+                                                 s.A_lo, st),
+                         "convert");
+            else
+                CU_CHECK(p, launch_convert_fp32(gc, chunk, s.staged, s.M_pad, s.mu_hat, s.sum_res, s.A32, st),
+                         "convert");
+            p->launches++;
+        }
         s.staged += chunk;
         s.pushed += chunk;
         done += chunk;
@@ -694,8 +765,10 @@ tacaw_status tacaw_finalize(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi,
     if (d_S && !d_I) return fail(TACAW_ERR_INVALID_ARG, "d_S requires d_I");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     for (auto &s : p->s) {
-        CU_CHECK(p, launch_mean_residual(s.M, s.T, s.d.subtract_mean, s.sum_res, s.dmu, st), "mean residual");
-        p->launches++;
+        if (!p->in_place) {
+            CU_CHECK(p, launch_mean_residual(s.M, s.T, s.d.subtract_mean, s.sum_res, s.dmu, st), "mean residual");
+            p->launches++;
+        }
         float *I = d_I ? d_I + s.I_off : nullptr;
         float2 *Psi = d_Psi ? static_cast<float2 *>(d_Psi) + s.I_off : nullptr;
         tacaw_status r = run_flush(p, s, FLUSH_FINAL, I, Psi, st);
@@ -755,6 +828,7 @@ tacaw_status tacaw_plan_get_info(tacaw_plan_t p, tacaw_plan_info *info) {
     info->tc_accumulators = p->prec == TACAW_PREC_SPLIT_BF16 ? p->tc_acc : 0;
     info->tc_cluster = (p->prec == TACAW_PREC_SPLIT_BF16 && !p->s.empty()) ? p->s[0].tc_cluster : 0;
     info->tc_block_frames = p->prec == TACAW_PREC_SPLIT_BF16 ? p->bf : 0;
+    info->frames_in_place = p->in_place ? 1 : 0;
     return TACAW_OK;
 }
 

@@ -252,9 +252,28 @@ struct TcPlanArgs {
     unsigned long long *trace; // null, or kTraceWords globaltimer stamps per CTA (phase boundaries)
     uint32_t *err;
 };
+// In-place operand A: the contraction reads the pushed frames of this flush directly.
+struct TcDirectArgs {
+    const float2 *const *frame_ptr;   // [n_frames] device pointers to each staged frame (pushed layout)
+    int n_frames;                     // frames in this flush
+    int64_t M, npix;
+    int kx;
+    int64_t pitch_row, pitch_probe;
+    int roi_x0, roi_y0;
+    const float2 *mu_hat;             // [M] provisional mean
+    double2 *sum_res;                 // [M] residual sums of earlier flushes
+    int accumulate_sums;              // add this flush's sums to sum_res (non-final flushes)
+    int prev_sums;                    // final flush: sum_res holds earlier flushes
+    int subtract_mean;
+    int T;
+};
 struct TcMaps;                 // tensor maps (defined in k_tc_gemm.cu)
 cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps /* TcMaps */, cudaStream_t st);
 int64_t tc_grid_ctas(const TcPlanArgs &a);
+cudaError_t launch_flush_tc_direct(const TcPlanArgs &a, const TcDirectArgs &d, const void *maps, cudaStream_t st);
+bool tc_make_maps_b(void *maps_out, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
+                    int N, int bf, char *errbuf, size_t errlen);
+size_t tc_smem_bytes_direct(int N, int bf, int stages);
 int tc_stages_for(int N, int bf);
 size_t tc_smem_bytes(int N, int bf, int stages);
 size_t tc_maps_size();

@@ -55,14 +55,15 @@ class CPlanDesc(ctypes.Structure):
     _fields_ = [("n_streams", c_int), ("streams", POINTER(CStreamDesc)), ("precision", c_int),
                 ("accum", c_int), ("hbm_budget_bytes", c_int64), ("k_stage", c_int),
                 ("tune_cache_path", c_char_p), ("tc_omega_tile", c_int), ("tc_accumulators", c_int),
-                ("tc_cluster", c_int), ("tc_block_frames", c_int), ("tc_prefetch", c_int)]
+                ("tc_cluster", c_int), ("tc_block_frames", c_int), ("tc_prefetch", c_int),
+                ("frames_in_place", c_int)]
 
 
 class CPlanInfo(ctypes.Structure):
     _fields_ = [("device_bytes", c_int64), ("k_stage", c_int), ("n_streams", c_int), ("precision", c_int),
                 ("I_elems", c_int64), ("S_elems", c_int64), ("flushes", c_int64), ("omega_tile", c_int),
                 ("stages", c_int), ("kernel_launches", c_int64), ("tc_accumulators", c_int),
-                ("tc_cluster", c_int), ("tc_block_frames", c_int)]
+                ("tc_cluster", c_int), ("tc_block_frames", c_int), ("frames_in_place", c_int)]
 
 
 _lib = None
@@ -159,7 +160,8 @@ class TacawPlan:
 
     def __init__(self, streams: Sequence[StreamConfig], precision: str = "split_bf16", accum: str = "kahan",
                  hbm_budget_bytes: int = 0, k_stage: int = 0, tc_omega_tile: int = 0,
-                 tc_accumulators: int = 0, tc_cluster: int = 0, tc_block_frames: int = 0, tc_prefetch: int = 0):
+                 tc_accumulators: int = 0, tc_cluster: int = 0, tc_block_frames: int = 0, tc_prefetch: int = 0,
+                 frames_in_place: bool = False):
         L = lib()
         self._keep = []
         descs = (CStreamDesc * len(streams))()
@@ -187,7 +189,8 @@ class TacawPlan:
             d.detectors = ctypes.cast(dets, POINTER(CDetector))
         pd = CPlanDesc(len(streams), ctypes.cast(descs, POINTER(CStreamDesc)), PRECISIONS[precision],
                        ACCUMS[accum], int(hbm_budget_bytes), int(k_stage), None, int(tc_omega_tile),
-                       int(tc_accumulators), int(tc_cluster), int(tc_block_frames), int(tc_prefetch))
+                       int(tc_accumulators), int(tc_cluster), int(tc_block_frames), int(tc_prefetch),
+                       int(bool(frames_in_place)))
         h = c_void_p()
         _check(L.tacaw_plan_create(ctypes.byref(pd), ctypes.byref(h)))
         self._h = h

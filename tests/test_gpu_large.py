@@ -20,7 +20,7 @@ from tests.helpers import oracle_kw, stream_config
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "split_bf16": 3e-5}
+TOL = {"fp32": 1e-5, "split_bf16": 3e-5, "split_inplace": 3e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -42,7 +42,7 @@ def sample_pixels(spec, n, rng):
     return np.concatenate([near, rng.integers(0, spec.Kx * spec.Ky, n - len(near))])
 
 
-@pytest.mark.parametrize("precision", ["split_bf16", "fp32"])
+@pytest.mark.parametrize("precision", ["split_bf16", "fp32", "split_inplace"])
 def test_realistic_full_size(precision):
     import torch
     import synth.gpu as sg
@@ -56,7 +56,9 @@ def test_realistic_full_size(precision):
         sg.generate(spec, 21, x.data_ptr() + t0 * fe * 8, t0, 128, pitch_row=K, pitch_frame=fe, pitch_probe=npix)
     I = torch.empty(P * Nw * npix, dtype=torch.float32, device="cuda")
     S = torch.empty(P * Nw, dtype=torch.float32, device="cuda")
-    with TacawPlan([stream_config(spec)], precision=precision) as plan:
+    kw = dict(precision="split_bf16", frames_in_place=True) if precision == "split_inplace" else dict(
+        precision=precision)
+    with TacawPlan([stream_config(spec)], **kw) as plan:
         for i in range(T // Tc):
             plan.push(0, x.data_ptr() + i * Tc * fe * 8, Tc)
         plan.finalize(I, S)

@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 TOL_FP32 = 1e-5
 TOL_SPLIT = 3e-5
-TOL = {"fp32": TOL_FP32, "split_bf16": TOL_SPLIT}
+TOL = {"fp32": TOL_FP32, "split_bf16": TOL_SPLIT, "split_inplace": TOL_SPLIT}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -37,7 +37,10 @@ def random_frames(P, T, Ky, Kx, seed=0, elastic=1.0, signal=1e-2):
 
 
 def check(spec, fr, precision, **kw):
-    out = run_gpu(spec, fr, precision, **kw)
+    if precision == "split_inplace":      # pushed frames read in place by the contraction
+        out = run_gpu(spec, fr, "split_bf16", frames_in_place=True, **kw)
+    else:
+        out = run_gpu(spec, fr, precision, **kw)
     ref = oracle.forward(fr, **oracle_kw(spec))
     eI = rel_err_peak(out["I"], ref.I)
     tol = TOL[precision]
@@ -51,7 +54,7 @@ def check(spec, fr, precision, **kw):
     return out, ref, eI
 
 
-@pytest.mark.parametrize("precision", ["fp32", "split_bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "split_bf16", "split_inplace"])
 def test_tiny_config_whole(precision):
     """4 probes, 64x64, T=256 in one push, first 128 FFT bins, Hann, mean removed, r=20 aperture."""
     s = synth.tiny().streams[0]
@@ -80,7 +83,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("precision", ["fp32", "split_bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "split_bf16", "split_inplace"])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_edge_cases(name, precision):
     spec, pushes, k_stage = CASES[name]
@@ -91,7 +94,7 @@ def test_edge_cases(name, precision):
 
 
 @pytest.mark.parametrize("accum", ["kahan", "fp64"])
-@pytest.mark.parametrize("precision", ["fp32", "split_bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "split_bf16", "split_inplace"])
 def test_streaming_flushes_match_single_flush(precision, accum):
     """K_stage < T (accumulators in HBM) gives the oracle's result too."""
     spec = StreamSpec(P=2, Kx=32, Ky=16, T=200, Tc=24, n_omega=70, E_max_meV=120.0, window="hann",
@@ -174,18 +177,20 @@ def test_errors_overflow_and_state():
         plan.finalize(I)
 
 
-TILINGS = [(1, 1, 0, 8), (1, 2, 0, 16), (2, 1, 0, 32), (2, 2, 0, 16), (3, 1, 0, 8), (3, 2, 0, 32),
-           (3, 4, 0, 32), (3, 4, 16, 16), (3, 2, 24, 8), (1, 2, 200, 16), (2, 4, 128, 32)]
+TILINGS = [(1, 1, 0, 8, ""), (1, 2, 0, 16, ""), (2, 1, 0, 32, ""), (2, 2, 0, 16, ""), (3, 1, 0, 8, ""),
+           (3, 2, 0, 32, ""), (3, 4, 0, 32, ""), (3, 4, 16, 16, ""), (3, 2, 24, 8, ""), (1, 2, 200, 16, ""),
+           (2, 4, 128, 32, "")]
 
 
-@pytest.mark.parametrize("acc,cluster,wt,bf", TILINGS)
-def test_tensor_core_tilings(acc, cluster, wt, bf):
+@pytest.mark.parametrize("acc,cluster,wt,bf,mode", TILINGS + [(3, 1, 0, 32, "in_place"), (2, 1, 0, 16, "in_place"),
+                                                             (1, 1, 0, 8, "in_place"), (1, 1, 200, 16, "in_place")])
+def test_tensor_core_tilings(acc, cluster, wt, bf, mode):
     """Every accumulator split / multicast cluster / energy-tile width / staging row width gives
     the oracle's result (T=168 is not a multiple of 32: the last block has a zeroed tail)."""
     spec = StreamSpec(P=2, Kx=64, Ky=48, T=168, Tc=40, n_omega=150, E_max_meV=120.0, window="hann", n_modes=6,
                       noise=1e-3, detectors=(Detector("circular", 0, 0, -1, 6.0),))
     fr = frames.frames(spec, 8, 0, spec.T)
-    out, ref, e = check(spec, fr, "split_bf16", tc_accumulators=acc, tc_cluster=cluster, tc_omega_tile=wt,
-                        tc_block_frames=bf)
+    out, ref, e = check(spec, fr, "split_inplace" if mode else "split_bf16", tc_accumulators=acc,
+                        tc_cluster=cluster, tc_omega_tile=wt, tc_block_frames=bf)
     info = out["info"]
     assert (info["tc_accumulators"], info["tc_cluster"], info["tc_block_frames"]) == (acc, cluster, bf)
