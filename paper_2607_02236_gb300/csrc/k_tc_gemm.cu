@@ -273,9 +273,10 @@ __device__ __forceinline__ void split2_bf16(float2 r, uint32_t &hi, uint32_t &lo
     lo = (uint32_t)__bfloat16_as_ushort(lr) | ((uint32_t)__bfloat16_as_ushort(li) << 16);
 }
 
-// MMA issue loop (one thread): per stage, bf/8 K-steps of 3 products into the accumulators;
-// tcgen05.commit releases the stage (to every CTA of the cluster when multicast) and, at the
-// end, signals the epilogue.
+// MMA issue loop of the in-place kernel (one thread): per stage, bf/8 K-steps of 3 products
+// into the accumulators; tcgen05.commit releases the stage and, at the end, signals the
+// epilogue.  (The staged kernel keeps its own copy of this loop inline, with the cluster
+// multicast release.)
 __device__ __forceinline__ void tc_mma_loop(const TcPlanArgs &a, TcShared *sh, uint32_t base_s, uint32_t stage_bytes,
                                             uint32_t kABytes, uint32_t b_pad, uint32_t RB, uint32_t tmem,
                                             volatile int *abort_flag, unsigned long long *trace, bool multicast) {
@@ -431,10 +432,72 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
                     if (!mbar_wait(smem_u32(&sh->full[s]), (uint32_t)(kb / a.stages) & 1u, nullptr))
                         atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
                 }
+            } else if (C > 1) {
+                // every CTA of the cluster releases every slot of this CTA's ring by a remote
+                // arrive; wait until the releases of the last use of each slot have landed, so
+                // that none can reach this shared memory after the CTA has exited
+                for (int s = 0; s < a.stages && s < a.n_kb; ++s) {
+                    const int last = (a.n_kb - 1 - s) / a.stages;
+                    if (!mbar_wait(smem_u32(&sh->empty[s]), (uint32_t)last & 1u, nullptr))
+                        atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+                }
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) tc_mma_loop(a, sh, base_s, stage_bytes, kABytes, b_pad, RB, tmem, abort_flag, trace, C > 1);
+        if (lane == 0) {
+            const int n0 = a.N < 256 ? a.N : 256;
+            const int n1 = a.N - n0;
+            const uint32_t id0 = idesc_bf16_f32(kMTile, n0);
+            const uint32_t id1 = n1 > 0 ? idesc_bf16_f32(kMTile, n1) : 0u;
+            const uint64_t b_half_off = (uint64_t)((n0 * RB) >> 4);
+            const uint32_t acc_small = tmem + (uint32_t)(a.n_big * a.N);
+            const int ksteps = a.bf / 8;
+            for (int kb = 0; kb < a.n_kb; ++kb) {
+                const int s = kb % a.stages;
+                const uint32_t use = (uint32_t)(kb / a.stages);
+                if (!mbar_wait(smem_u32(&sh->full[s]), use & 1u, abort_flag)) {
+                    if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                if (trace && kb == 0) trace[2] = globaltimer();
+                const uint32_t st = base_s + (uint32_t)s * stage_bytes;
+                const uint64_t dAhi0 = sdesc_k(st, RB);
+                const uint64_t dAlo0 = sdesc_k(st + kABytes, RB);
+                const uint64_t dBhi0 = sdesc_k(st + 2 * kABytes, RB);
+                const uint64_t dBlo0 = sdesc_k(st + 2 * kABytes + b_pad, RB);
+                for (int ks = 0; ks < ksteps; ++ks) {
+                    // K-step ks starts 32*ks bytes into the swizzled rows (start address in 16 B units)
+                    const uint64_t adv = (uint64_t)(2 * ks);
+                    const uint64_t dAhi = dAhi0 + adv, dAlo = dAlo0 + adv, dBhi = dBhi0 + adv, dBlo = dBlo0 + adv;
+                    const int g = kb * ksteps + ks;       // global K-step index
+                    if (a.split) {
+                        // N <= 256: one MMA per product
+                        const int big = a.n_big == 2 ? (g & 1) : 0;
+                        mma_bf16_ss(tmem + (uint32_t)(big * a.N), dAhi, dBhi, id0, g >= a.n_big ? 1u : 0u);
+                        mma_bf16_ss(acc_small, dAhi, dBlo, id0, g > 0 ? 1u : 0u);
+                        mma_bf16_ss(acc_small, dAlo, dBhi, id0, 1u);
+                    } else {
+#pragma unroll
+                        for (int pass = 0; pass < 3; ++pass) {
+                            const uint64_t dA = pass == 2 ? dAlo : dAhi;
+                            const uint64_t dB = pass == 1 ? dBlo : dBhi;
+                            const uint32_t acc = (g > 0 || pass > 0) ? 1u : 0u;
+                            mma_bf16_ss(tmem, dA, dB, id0, acc);
+                            if (n1 > 0) mma_bf16_ss(tmem + (uint32_t)n0, dA, dB + b_half_off, id1, acc);
+                        }
+                    }
+                }
+                if (C > 1)
+                    mma_commit_mc(smem_u32(&sh->empty[s]), cmask);
+                else
+                    mma_commit(smem_u32(&sh->empty[s]));
+            }
+            // always signal: the epilogue (and TMEM release) wait for every issued MMA
+            mma_commit(smem_u32(&sh->tmem_full));
+            if (trace) trace[3] = globaltimer();
+        }
     } else {
         // epilogue warps 2..5 -> TMEM lane quarter q = warp % 4
         const int q = warp & 3;
