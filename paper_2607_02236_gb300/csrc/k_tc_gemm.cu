@@ -634,27 +634,31 @@ __global__ void __launch_bounds__(320, 1) flush_tc_direct_kernel(const __grid_co
             }
             uint8_t *st = base + (size_t)s * stage_bytes;
             const int f0 = kb * a.bf;
-            for (int c = 0; c < cpr; ++c) {
-                float2 v[4];
+            // all of the block's loads in flight at once (independent pointer + data loads)
+            float2 v[32];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int f = f0 + 4 * c + i;
-                    v[i] = (valid && f < d.n_frames) ? __ldcs(d.frame_ptr[f] + off) : mu;
-                }
-                uint32_t h[4], l[4];
-                float br = 0.f, bi = 0.f;
+            for (int i = 0; i < 32; ++i) {
+                const int f = f0 + i;
+                v[i] = (i < a.bf && valid && f < d.n_frames) ? __ldcs(d.frame_ptr[f] + off) : mu;
+            }
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float2 q = make_float2(v[i].x - mu.x, v[i].y - mu.y);
-                    br += q.x;
-                    bi += q.y;
-                    split2_bf16(q, h[i], l[i]);
+            for (int c = 0; c < 8; ++c) {
+                if (c < cpr) {
+                    uint32_t h[4], l[4];
+                    float br = 0.f, bi = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 q = make_float2(v[4 * c + i].x - mu.x, v[4 * c + i].y - mu.y);
+                        br += q.x;
+                        bi += q.y;
+                        split2_bf16(q, h[i], l[i]);
+                    }
+                    sr += br;
+                    si += bi;
+                    const uint32_t chunk = ((uint32_t)c ^ sw) * 16u;
+                    *reinterpret_cast<uint4 *>(st + row_byte + chunk) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4 *>(st + kABytes + row_byte + chunk) = make_uint4(l[0], l[1], l[2], l[3]);
                 }
-                sr += br;
-                si += bi;
-                const uint32_t chunk = ((uint32_t)c ^ sw) * 16u;
-                *reinterpret_cast<uint4 *>(st + row_byte + chunk) = make_uint4(h[0], h[1], h[2], h[3]);
-                *reinterpret_cast<uint4 *>(st + kABytes + row_byte + chunk) = make_uint4(l[0], l[1], l[2], l[3]);
             }
             // generic-proxy writes -> visible to the tensor core (async proxy) before the arrive
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
