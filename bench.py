@@ -49,10 +49,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2, help="end-to-end steps from pinned host memory (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU oracle baseline")
     ap.add_argument("--small", action="store_true", help="small workload (profiling captures)")
-    ap.add_argument("--in-place", dest="in_place", action="store_true", default=True,
-                    help="the contraction reads pushed frames in place (default)")
+    ap.add_argument("--in-place", dest="in_place", action="store_true", default=False,
+                    help="the contraction reads pushed frames in place (no staging pass)")
     ap.add_argument("--staging", dest="in_place", action="store_false",
-                    help="convert pushed frames into the library's staging area at push time")
+                    help="convert pushed frames into the library's staging area at push time (default)")
     ap.add_argument("--tc-accumulators", type=int, default=0, help="tensor-core tiling override (0: plan default)")
     ap.add_argument("--tc-omega-tile", type=int, default=0)
     ap.add_argument("--tc-cluster", type=int, default=0)
