@@ -180,8 +180,21 @@ tacaw_status tacaw_push_frames(tacaw_plan_t plan, int stream_id, const void *d_f
  *   d_S   float32 [s][p][d][j]        (may be NULL)
  *   d_Psi complex64 [s][p][j][ky][kx] (may be NULL)
  * Spectra are summed in a fixed order (deterministic).  d_S requires d_I.  Waits for the
- * work on `stream`.  Errors: STATE unless every stream has received exactly T frames.  */
+ * work on `stream`.  Errors: STATE unless every stream has received exactly T frames.
+ * The last flush of every stream on the split path goes out as one tensor-core launch over
+ * all streams (supercell partitions of uneven size; groups of up to 16 streams with the
+ * same cluster size), its tiles ordered longest first.                                  */
 tacaw_status tacaw_finalize(tacaw_plan_t plan, float *d_I, float *d_S, void *d_Psi, void *stream);
+
+/* tacaw_finalize without the wait: enqueues the same work and returns.  With
+ * tacaw_reset and tacaw_push_frames (which never wait) a whole segment can then be
+ * captured into a CUDA graph on `stream` and replayed; a replay reads the frame
+ * addresses given at capture time.  The device error flag is read by tacaw_check_errors. */
+tacaw_status tacaw_finalize_async(tacaw_plan_t plan, float *d_I, float *d_S, void *d_Psi, void *stream);
+
+/* Waits for the work on `stream` and reads the device error flag (TACAW_ERR_TIMEOUT, and
+ * the plan poisoned, if a bounded device wait ran out since the flag was last cleared).  */
+tacaw_status tacaw_check_errors(tacaw_plan_t plan, void *stream);
 
 /* Element offsets of stream stream_id's block inside d_I / d_Psi and d_S.              */
 tacaw_status tacaw_output_offsets(tacaw_plan_t plan, int stream_id, int64_t *I_offset,

@@ -29,8 +29,10 @@
 // bit, lets in-flight copies land, frees TMEM and returns.
 #include <cuda.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <new>
 
 #include "tacaw_internal.cuh"
 
@@ -40,6 +42,19 @@ struct TcMaps {
     CUtensorMap a_hi, a_lo, b_hi, b_lo;
     int box_b_rows;
     int nbox_b;
+};
+
+// One launch over the tiles of several streams (supercell partitions): entry i owns CTAs
+// [cta_begin, cta_begin + ctas) (a multiple of the cluster size).
+struct TcGroupEntry {
+    TcMaps maps;
+    TcPlanArgs args;
+    int cta_begin;
+    int ctas;
+};
+struct TcGroup {
+    TcGroupEntry e[kMaxGroupStreams];
+    int n;
 };
 
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s per wait
@@ -335,7 +350,12 @@ __device__ __forceinline__ void tc_mma_loop(const TcPlanArgs &a, TcShared *sh, u
     if (trace) trace[3] = globaltimer();
 }
 
-__global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant__ TcMaps maps, const TcPlanArgs a) {
+__global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant__ TcGroup g) {
+    int gi = 0;
+    while (gi + 1 < g.n && (int)blockIdx.x >= g.e[gi + 1].cta_begin) ++gi;
+    const TcMaps &maps = g.e[gi].maps;
+    const TcPlanArgs a = g.e[gi].args;
+    const unsigned bid = blockIdx.x - (unsigned)g.e[gi].cta_begin;   // CTA index inside its stream
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t RB = 4u * (uint32_t)a.bf;           // bytes per operand row
@@ -348,7 +368,7 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int C = a.cluster;
     const uint32_t crank = C > 1 ? cluster_ctarank() : 0u;
-    const unsigned cid = blockIdx.x / (unsigned)C;
+    const unsigned cid = bid / (unsigned)C;
     const int wtile = (int)(cid % (unsigned)a.n_wt);
     const int m0 = ((int)(cid / (unsigned)a.n_wt) * C + (int)crank) * kMTile;
     const int n_acc = a.split ? a.n_big + 1 : 1;
@@ -356,7 +376,7 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
     const uint32_t tx_bytes = 2u * kABytes + 2u * (uint32_t)a.N * RB;
     const int rows_cta = a.N / C;                 // B rows this CTA loads (for the whole cluster)
     const uint16_t cmask = (uint16_t)((1u << C) - 1u);
-    unsigned long long *trace = a.trace ? a.trace + (size_t)blockIdx.x * kTraceWords : nullptr;
+    unsigned long long *trace = a.trace ? a.trace + (size_t)bid * kTraceWords : nullptr;
     if (trace && threadIdx.x == 0) {
         trace[0] = globaltimer();
         trace[7] = smid();
@@ -910,27 +930,54 @@ int64_t tc_grid_ctas(const TcPlanArgs &a) {
     return (n_mt + a.cluster - 1) / a.cluster * a.cluster * a.n_wt;
 }
 
-cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps, cudaStream_t st) {
-    const size_t smem = tc_smem_bytes(a.N, a.bf, a.stages);
+cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *maps, int n, cudaStream_t st) {
+    if (n < 1 || n > kMaxGroupStreams) return cudaErrorInvalidValue;
+    TcGroup *g = new (std::nothrow) TcGroup();
+    if (!g) return cudaErrorMemoryAllocation;
+    const int C = args[0].cluster;
+    size_t smem = 0;
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        if (args[i].cluster != C || args[i].stages != args[0].stages || args[i].bf != args[0].bf) {
+            delete g;
+            return cudaErrorInvalidValue;
+        }
+        g->e[i].maps = *reinterpret_cast<const TcMaps *>(maps[i]);
+        g->e[i].args = args[i];
+        g->e[i].cta_begin = (int)total;
+        if (args[i].trace) g->e[i].args.trace = args[i].trace + (size_t)total * kTraceWords;
+        const int64_t c = tc_grid_ctas(args[i]);
+        g->e[i].ctas = (int)c;
+        total += c;
+        smem = std::max(smem, tc_smem_bytes(args[i].N, args[i].bf, args[i].stages));
+    }
+    g->n = n;
+    if (total <= 0 || total > 0x7fffffffLL) {
+        delete g;
+        return cudaErrorInvalidConfiguration;
+    }
     cudaError_t e = cudaFuncSetAttribute(flush_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int64_t n_mt = a.e.M_pad / kMTile;
-    const int64_t n_mt_pad = (n_mt + a.cluster - 1) / a.cluster * a.cluster;
-    const int64_t blocks = n_mt_pad * a.n_wt;
-    if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)blocks, 1, 1);
-    cfg.blockDim = dim3(192, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = a.cluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, flush_tc_kernel, *reinterpret_cast<const TcMaps *>(maps), a);
+    if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)total, 1, 1);
+        cfg.blockDim = dim3(192, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, flush_tc_kernel, *g);
+    }
+    delete g;
+    return e;
+}
+
+cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps, cudaStream_t st) {
+    return launch_flush_tc_group(&a, &maps, 1, st);
 }
 
 }  // namespace tacaw

@@ -77,7 +77,7 @@ struct Stream {
     std::vector<unsigned char> tc_maps;
     int tc_cluster = 1;
     // in-place frames: per staged frame, a pointer into the pushed buffer
-    std::vector<const float2 *> h_frame_ptr;
+    const float2 **h_frame_ptr = nullptr;       // pinned, one slot per frame of the segment
     const float2 **d_frame_ptr = nullptr;
     // segment state
     int pushed = 0, staged = 0, stage_start = 0, flushes = 0;
@@ -129,6 +129,11 @@ bool dev_alloc(tacaw_plan_s *p, T **ptr, size_t count) {
 }
 
 void free_all(tacaw_plan_s *p) {
+    for (auto &s : p->s)
+        if (s.h_frame_ptr) {
+            cudaFreeHost(s.h_frame_ptr);
+            s.h_frame_ptr = nullptr;
+        }
     if (p->d_trace) cudaFree(p->d_trace);
     p->d_trace = nullptr;
     for (auto &e : p->ev) {
@@ -216,10 +221,7 @@ void choose_omega_tile(Stream &s, int n_acc, int requested) {
 int64_t stream_stage_bytes(const Stream &s, int ring) { return s.M_pad * 8 * (int64_t)ring; }
 int64_t stream_acc_bytes(const Stream &s) { return (int64_t)s.Nw_pad * s.M_pad * 16; }
 
-tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float2 *Psi_out, cudaStream_t st) {
-    const int n = s.staged;
-    if (n <= 0) return TACAW_OK;
-    if (mode != FLUSH_FINAL && !s.needs_acc) return fail(TACAW_ERR_STATE, "internal: accumulator missing");
+EpiArgs epi_args(tacaw_plan_s *p, const Stream &s, int mode, float *I_out, float2 *Psi_out) {
     EpiArgs e{};
     e.M = s.M;
     e.M_pad = s.M_pad;
@@ -236,45 +238,87 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
     e.bose = s.bose;
     e.I_out = I_out;
     e.Psi_out = Psi_out;
+    return e;
+}
 
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (p->timing) {
-        CU_CHECK(p, cudaEventCreate(&e0), "cudaEventCreate");
-        CU_CHECK(p, cudaEventCreate(&e1), "cudaEventCreate");
-        CU_CHECK(p, cudaEventRecord(e0, st), "cudaEventRecord");
+// Tensor-core arguments of one flush of the s.staged frames of stream s.
+TcPlanArgs tc_args(tacaw_plan_s *p, const Stream &s, const EpiArgs &e) {
+    const int n = s.staged;
+    TcPlanArgs a{};
+    a.e = e;
+    a.wt = s.wt;
+    a.n_wt = s.n_wt;
+    a.N = 2 * s.wt;
+    a.n_kb = (n + p->bf - 1) / p->bf;
+    a.kbB0 = s.stage_start / p->bf;
+    a.bf = p->bf;
+    a.stages = p->stages;
+    a.split = p->tc_acc > 1 ? 1 : 0;
+    a.n_big = p->tc_acc == 3 ? 2 : 1;
+    a.cluster = p->in_place ? 1 : s.tc_cluster;
+    a.prefetch = p->in_place ? 0 : p->tc_prefetch;
+    a.err = p->d_err;
+    a.trace = nullptr;
+    return a;
+}
+
+// Per-CTA phase trace of the next flush launch (nc CTAs).
+tacaw_status trace_buffer(tacaw_plan_s *p, int64_t nc, unsigned long long **out) {
+    *out = nullptr;
+    if (!p->trace) return TACAW_OK;
+    if (nc > p->trace_cap) {
+        if (p->d_trace) cudaFree(p->d_trace);
+        p->d_trace = nullptr;
+        p->trace_cap = 0;
+        CU_CHECK(p, cudaMalloc(&p->d_trace, sizeof(unsigned long long) * kTraceWords * nc), "trace buffer");
+        p->trace_cap = nc;
     }
+    p->trace_ctas = nc;
+    *out = p->d_trace;
+    return TACAW_OK;
+}
+
+tacaw_status timing_begin(tacaw_plan_s *p, cudaEvent_t *e0, cudaEvent_t *e1, cudaStream_t st) {
+    *e0 = *e1 = nullptr;
+    if (!p->timing) return TACAW_OK;
+    CU_CHECK(p, cudaEventCreate(e0), "cudaEventCreate");
+    CU_CHECK(p, cudaEventCreate(e1), "cudaEventCreate");
+    CU_CHECK(p, cudaEventRecord(*e0, st), "cudaEventRecord");
+    return TACAW_OK;
+}
+
+tacaw_status timing_end(tacaw_plan_s *p, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st) {
+    if (!p->timing) return TACAW_OK;
+    CU_CHECK(p, cudaEventRecord(e1, st), "cudaEventRecord");
+    p->ev.emplace_back(e0, e1);
+    return TACAW_OK;
+}
+
+void flush_done(tacaw_plan_s *p, Stream &s) {
+    s.flushes++;
+    p->flushes_total++;
+    s.stage_start += s.staged;
+    s.staged = 0;
+}
+
+tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float2 *Psi_out, cudaStream_t st) {
+    const int n = s.staged;
+    if (n <= 0) return TACAW_OK;
+    if (mode != FLUSH_FINAL && !s.needs_acc) return fail(TACAW_ERR_STATE, "internal: accumulator missing");
+    const EpiArgs e = epi_args(p, s, mode, I_out, Psi_out);
+    cudaEvent_t e0, e1;
+    tacaw_status r = timing_begin(p, &e0, &e1, st);
+    if (r != TACAW_OK) return r;
     if (p->prec == TACAW_PREC_SPLIT_BF16 && p->in_place) {
-        TcPlanArgs a{};
-        a.e = e;
-        a.wt = s.wt;
-        a.n_wt = s.n_wt;
-        a.N = 2 * s.wt;
-        a.n_kb = (n + p->bf - 1) / p->bf;
-        a.kbB0 = s.stage_start / p->bf;
-        a.bf = p->bf;
-        a.stages = p->stages;
-        a.split = p->tc_acc > 1 ? 1 : 0;
-        a.n_big = p->tc_acc == 3 ? 2 : 1;
-        a.cluster = 1;
-        a.prefetch = 0;
-        a.err = p->d_err;
-        a.trace = nullptr;
-        if (p->trace) {
-            const int64_t nc = (s.M_pad / kMTile) * s.n_wt;
-            if (nc > p->trace_cap) {
-                if (p->d_trace) cudaFree(p->d_trace);
-                p->d_trace = nullptr;
-                p->trace_cap = 0;
-                CU_CHECK(p, cudaMalloc(&p->d_trace, sizeof(unsigned long long) * kTraceWords * nc), "trace buffer");
-                p->trace_cap = nc;
-            }
-            p->trace_ctas = nc;
-            a.trace = p->d_trace;
-        }
-        CU_CHECK(p, cudaMemcpyAsync(s.d_frame_ptr, s.h_frame_ptr.data(), sizeof(const float2 *) * n,
-                                    cudaMemcpyHostToDevice, st), "frame table");
+        TcPlanArgs a = tc_args(p, s, e);
+        r = trace_buffer(p, (s.M_pad / kMTile) * s.n_wt, &a.trace);
+        if (r != TACAW_OK) return r;
+        // the pointer table holds one slot per frame of the segment, so every flush of a
+        // captured segment reads its own slots when the graph is replayed
+        CU_CHECK(p, cudaMemcpyAsync(s.d_frame_ptr + s.stage_start, s.h_frame_ptr + s.stage_start,
+                                    sizeof(const float2 *) * n, cudaMemcpyHostToDevice, st), "frame table");
         TcDirectArgs d{};
-        d.frame_ptr = s.d_frame_ptr;
+        d.frame_ptr = s.d_frame_ptr + s.stage_start;
         d.n_frames = n;
         d.M = s.M;
         d.npix = s.npix;
@@ -296,33 +340,9 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
             CU_CHECK(p, launch_zero_tail_split(s.M_pad, n, p->bf, s.A_hi, s.A_lo, st), "zero_tail");
             p->launches++;
         }
-        TcPlanArgs a{};
-        a.e = e;
-        a.wt = s.wt;
-        a.n_wt = s.n_wt;
-        a.N = 2 * s.wt;
-        a.n_kb = (n + p->bf - 1) / p->bf;
-        a.kbB0 = s.stage_start / p->bf;
-        a.bf = p->bf;
-        a.stages = p->stages;
-        a.split = p->tc_acc > 1 ? 1 : 0;
-        a.n_big = p->tc_acc == 3 ? 2 : 1;
-        a.cluster = s.tc_cluster;
-        a.prefetch = p->tc_prefetch;
-        a.err = p->d_err;
-        a.trace = nullptr;
-        if (p->trace) {
-            const int64_t n = tc_grid_ctas(a);
-            if (n > p->trace_cap) {
-                if (p->d_trace) cudaFree(p->d_trace);
-                p->d_trace = nullptr;
-                p->trace_cap = 0;
-                CU_CHECK(p, cudaMalloc(&p->d_trace, sizeof(unsigned long long) * kTraceWords * n), "trace buffer");
-                p->trace_cap = n;
-            }
-            p->trace_ctas = n;
-            a.trace = p->d_trace;
-        }
+        TcPlanArgs a = tc_args(p, s, e);
+        r = trace_buffer(p, tc_grid_ctas(a), &a.trace);
+        if (r != TACAW_OK) return r;
         CU_CHECK(p, launch_flush_tc(a, s.tc_maps.data(), st), "flush (tensor cores)");
         p->launches++;
     } else {
@@ -336,14 +356,60 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         CU_CHECK(p, launch_flush_simt(a, st), "flush (fp32)");
         p->launches++;
     }
-    if (p->timing) {
-        CU_CHECK(p, cudaEventRecord(e1, st), "cudaEventRecord");
-        p->ev.emplace_back(e0, e1);
+    r = timing_end(p, e0, e1, st);
+    if (r != TACAW_OK) return r;
+    flush_done(p, s);
+    return TACAW_OK;
+}
+
+// Final flushes of all staged tensor-core streams as few launches as possible: streams with
+// the same cluster size share one launch (up to kMaxGroupStreams each), their CTAs ordered by
+// decreasing per-CTA work so that the longest tiles start first.
+tacaw_status final_flush_grouped(tacaw_plan_s *p, float *d_I, float2 *d_Psi, cudaStream_t st) {
+    std::vector<int> todo;
+    for (int i = 0; i < (int)p->s.size(); ++i)
+        if (p->s[i].staged > 0) todo.push_back(i);
+    auto work = [&](int i) {
+        const Stream &s = p->s[i];
+        return (int64_t)((s.staged + p->bf - 1) / p->bf) * (2 * s.wt + 48);
+    };
+    std::stable_sort(todo.begin(), todo.end(), [&](int a, int b) { return work(a) > work(b); });
+    for (int C : {1, 2, 4}) {
+        std::vector<int> grp;
+        for (int i : todo)
+            if (p->s[i].tc_cluster == C) grp.push_back(i);
+        for (size_t g0 = 0; g0 < grp.size(); g0 += kMaxGroupStreams) {
+            const size_t g1 = std::min(grp.size(), g0 + (size_t)kMaxGroupStreams);
+            std::vector<TcPlanArgs> args;
+            std::vector<const void *> maps;
+            int64_t nc = 0;
+            for (size_t k = g0; k < g1; ++k) {
+                Stream &s = p->s[grp[k]];
+                if (s.staged % p->bf) {
+                    CU_CHECK(p, launch_zero_tail_split(s.M_pad, s.staged, p->bf, s.A_hi, s.A_lo, st), "zero_tail");
+                    p->launches++;
+                }
+                float *I = d_I ? d_I + s.I_off : nullptr;
+                float2 *Psi = d_Psi ? d_Psi + s.I_off : nullptr;
+                args.push_back(tc_args(p, s, epi_args(p, s, FLUSH_FINAL, I, Psi)));
+                maps.push_back(s.tc_maps.data());
+                nc += tc_grid_ctas(args.back());
+            }
+            unsigned long long *tr = nullptr;
+            tacaw_status r = trace_buffer(p, nc, &tr);
+            if (r != TACAW_OK) return r;
+            for (auto &a : args) a.trace = tr;     // offset per stream by the launcher
+            cudaEvent_t e0, e1;
+            r = timing_begin(p, &e0, &e1, st);
+            if (r != TACAW_OK) return r;
+            CU_CHECK(p, launch_flush_tc_group(args.data(), maps.data(), (int)args.size(), st),
+                     "flush (tensor cores, grouped)");
+            p->launches++;
+            r = timing_end(p, e0, e1, st);
+            if (r != TACAW_OK) return r;
+            for (size_t k = g0; k < g1; ++k) flush_done(p, p->s[grp[k]]);
+        }
     }
-    s.flushes++;
-    p->flushes_total++;
-    s.stage_start += n;
-    s.staged = 0;
     return TACAW_OK;
 }
 
@@ -389,8 +455,13 @@ tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
         s.tc_maps.resize(tc_maps_size());
         char eb[256];
         if (p->in_place) {
-            s.h_frame_ptr.assign(s.ring, nullptr);
-            if (!dev_alloc(p, &s.d_frame_ptr, s.ring)) return fail(TACAW_ERR_OOM, "cudaMalloc(frame table)");
+            void *hp = nullptr;
+            if (cudaMallocHost(&hp, sizeof(const float2 *) * s.T) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(TACAW_ERR_OOM, "cudaMallocHost(frame table)");
+            }
+            s.h_frame_ptr = static_cast<const float2 **>(hp);
+            if (!dev_alloc(p, &s.d_frame_ptr, s.T)) return fail(TACAW_ERR_OOM, "cudaMalloc(frame table)");
             if (!tc_make_maps_b(s.tc_maps.data(), s.B_hi, s.B_lo, s.Nw_pad, s.n_kb_T, 2 * s.wt, p->bf, eb, sizeof(eb)))
                 return fail(TACAW_ERR_CUDA, "%s", eb);
         } else {
@@ -498,6 +569,50 @@ tacaw_status read_device_error(tacaw_plan_s *p, cudaStream_t st) {
         p->poisoned = true;
         return fail(TACAW_ERR_TIMEOUT, "device wait timed out (error bits 0x%x)", h);
     }
+    return TACAW_OK;
+}
+
+tacaw_status finalize_impl(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, cudaStream_t st) {
+    tacaw_status c = check_plan(p);
+    if (c != TACAW_OK) return c;
+    if (p->finalized) return fail(TACAW_ERR_STATE, "segment already finalized");
+    for (size_t i = 0; i < p->s.size(); ++i)
+        if (p->s[i].pushed != p->s[i].T)
+            return fail(TACAW_ERR_STATE, "stream %zu has %d of %d frames", i, p->s[i].pushed, p->s[i].T);
+    if (d_S && !d_I) return fail(TACAW_ERR_INVALID_ARG, "d_S requires d_I");
+    if (!p->in_place)
+        for (auto &s : p->s) {
+            CU_CHECK(p, launch_mean_residual(s.M, s.T, s.d.subtract_mean, s.sum_res, s.dmu, st), "mean residual");
+            p->launches++;
+        }
+    float2 *Psi_all = static_cast<float2 *>(d_Psi);
+    if (p->prec == TACAW_PREC_SPLIT_BF16 && !p->in_place) {
+        tacaw_status r = final_flush_grouped(p, d_I, Psi_all, st);
+        if (r != TACAW_OK) return r;
+    } else {
+        for (auto &s : p->s) {
+            tacaw_status r = run_flush(p, s, FLUSH_FINAL, d_I ? d_I + s.I_off : nullptr,
+                                       Psi_all ? Psi_all + s.I_off : nullptr, st);
+            if (r != TACAW_OK) return r;
+        }
+    }
+    if (d_S)
+        for (auto &s : p->s) {
+            if (s.D <= 0) continue;
+            ApertureArgs a{};
+            a.I = d_I + s.I_off;
+            a.S = d_S + s.S_off;
+            a.P = s.d.n_probes;
+            a.D = s.D;
+            a.Nw = s.Nw;
+            a.npix = s.npix;
+            a.idx = s.det_idx;
+            a.wts = s.det_w;
+            a.off = s.det_off;
+            CU_CHECK(p, launch_aperture(a, st), "aperture");
+            p->launches++;
+        }
+    p->finalized = true;
     return TACAW_OK;
 }
 
@@ -733,7 +848,7 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
         FrameGeom gc = g;
         gc.base = g.base + (int64_t)done * g.pitch_frame;
         if (p->in_place) {
-            for (int t = 0; t < chunk; ++t) s.h_frame_ptr[s.staged + t] = gc.base + (int64_t)t * g.pitch_frame;
+            for (int t = 0; t < chunk; ++t) s.h_frame_ptr[s.pushed + t] = gc.base + (int64_t)t * g.pitch_frame;
         } else {
             if (p->prec == TACAW_PREC_SPLIT_BF16)
                 CU_CHECK(p, launch_convert_split(gc, chunk, s.staged, p->bf, s.M_pad, s.mu_hat, s.sum_res, s.A_hi,
@@ -756,40 +871,20 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
 }
 
 tacaw_status tacaw_finalize(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    tacaw_status r = finalize_impl(p, d_I, d_S, d_Psi, st);
+    if (r != TACAW_OK) return r;
+    return read_device_error(p, st);
+}
+
+tacaw_status tacaw_finalize_async(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, void *stream) {
+    return finalize_impl(p, d_I, d_S, d_Psi, static_cast<cudaStream_t>(stream));
+}
+
+tacaw_status tacaw_check_errors(tacaw_plan_t p, void *stream) {
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
-    if (p->finalized) return fail(TACAW_ERR_STATE, "segment already finalized");
-    for (size_t i = 0; i < p->s.size(); ++i)
-        if (p->s[i].pushed != p->s[i].T)
-            return fail(TACAW_ERR_STATE, "stream %zu has %d of %d frames", i, p->s[i].pushed, p->s[i].T);
-    if (d_S && !d_I) return fail(TACAW_ERR_INVALID_ARG, "d_S requires d_I");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    for (auto &s : p->s) {
-        if (!p->in_place) {
-            CU_CHECK(p, launch_mean_residual(s.M, s.T, s.d.subtract_mean, s.sum_res, s.dmu, st), "mean residual");
-            p->launches++;
-        }
-        float *I = d_I ? d_I + s.I_off : nullptr;
-        float2 *Psi = d_Psi ? static_cast<float2 *>(d_Psi) + s.I_off : nullptr;
-        tacaw_status r = run_flush(p, s, FLUSH_FINAL, I, Psi, st);
-        if (r != TACAW_OK) return r;
-        if (d_S && s.D > 0) {
-            ApertureArgs a{};
-            a.I = I;
-            a.S = d_S + s.S_off;
-            a.P = s.d.n_probes;
-            a.D = s.D;
-            a.Nw = s.Nw;
-            a.npix = s.npix;
-            a.idx = s.det_idx;
-            a.wts = s.det_w;
-            a.off = s.det_off;
-            CU_CHECK(p, launch_aperture(a, st), "aperture");
-            p->launches++;
-        }
-    }
-    p->finalized = true;
-    return read_device_error(p, st);
+    return read_device_error(p, static_cast<cudaStream_t>(stream));
 }
 
 tacaw_status tacaw_output_offsets(tacaw_plan_t p, int sid, int64_t *I_offset, int64_t *S_offset) {

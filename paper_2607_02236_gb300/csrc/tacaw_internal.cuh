@@ -270,6 +270,9 @@ struct TcDirectArgs {
 struct TcMaps;                 // tensor maps (defined in k_tc_gemm.cu)
 cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps /* TcMaps */, cudaStream_t st);
 int64_t tc_grid_ctas(const TcPlanArgs &a);
+constexpr int kMaxGroupStreams = 16;
+// one launch over up to kMaxGroupStreams streams' flushes (same cluster size, stage count and block frames)
+cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *maps, int n, cudaStream_t st);
 cudaError_t launch_flush_tc_direct(const TcPlanArgs &a, const TcDirectArgs &d, const void *maps, cudaStream_t st);
 bool tc_make_maps_b(void *maps_out, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
                     int N, int bf, char *errbuf, size_t errlen);

@@ -27,7 +27,8 @@ DET_KINDS = {"circular": 0, "annular": 1, "mask": 2}
 EXPORTS = ["tacaw_plan_create", "tacaw_push_frames", "tacaw_finalize", "tacaw_output_offsets",
            "tacaw_backward", "tacaw_reset", "tacaw_plan_get_info", "tacaw_set_timing",
            "tacaw_kernel_time_ms", "tacaw_destroy", "tacaw_last_error", "tacaw_version",
-           "tacaw_detector_spectra_noalloc", "tacaw_flush_trace"]
+           "tacaw_detector_spectra_noalloc", "tacaw_flush_trace", "tacaw_finalize_async",
+           "tacaw_check_errors"]
 
 
 class TacawError(RuntimeError):
@@ -80,6 +81,8 @@ def lib():
     L.tacaw_plan_create.argtypes = [POINTER(CPlanDesc), POINTER(c_void_p)]
     L.tacaw_push_frames.argtypes = [c_void_p, c_int, c_void_p, c_int, c_void_p]
     L.tacaw_finalize.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    L.tacaw_finalize_async.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    L.tacaw_check_errors.argtypes = [c_void_p, c_void_p]
     L.tacaw_output_offsets.argtypes = [c_void_p, c_int, POINTER(c_int64), POINTER(c_int64)]
     L.tacaw_backward.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]
     L.tacaw_reset.argtypes = [c_void_p, c_void_p]
@@ -203,6 +206,13 @@ class TacawPlan:
 
     def finalize(self, I=None, S=None, Psi=None, cuda_stream=None):
         _check(lib().tacaw_finalize(self._h, _ptr(I), _ptr(S), _ptr(Psi), _stream(cuda_stream)))
+
+    def finalize_async(self, I=None, S=None, Psi=None, cuda_stream=None):
+        """Enqueues the finalize work without waiting (capturable into a CUDA graph)."""
+        _check(lib().tacaw_finalize_async(self._h, _ptr(I), _ptr(S), _ptr(Psi), _stream(cuda_stream)))
+
+    def check_errors(self, cuda_stream=None):
+        _check(lib().tacaw_check_errors(self._h, _stream(cuda_stream)))
 
     def backward(self, stream_id: int, dL_dS, frames, grad, cuda_stream=None):
         _check(lib().tacaw_backward(self._h, int(stream_id), _ptr(dL_dS), _ptr(frames), _ptr(grad),

@@ -1,0 +1,155 @@
+"""Several supercell partitions in one plan (the batched layout of Sec. IV: independent
+partitions of uneven size), checked element by element against the FP64 oracle.
+
+  grouped  the last flush of every stream goes out as one tensor-core launch over all
+           streams (tiles ordered longest first); parity per stream and the launch count
+  graph    reset + pushes + finalize_async of a whole segment captured into a CUDA graph;
+           two replays over two different frame sets, each against the oracle
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import Detector, StreamSpec
+from tests.helpers import oracle_kw, rel_err_peak, stream_config
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "split_bf16": 3e-5}
+
+# uneven probes, ROIs (one rectangular), segment lengths (ragged against every block size),
+# energy grids and windows; every omega tile fits one 128-column MMA (cluster size 1)
+SPECS = [
+    StreamSpec(P=3, Kx=48, Ky=48, T=200, Tc=40, n_omega=70, E_max_meV=120.0, window="hann",
+               detectors=(Detector(r_out=10.0),)),
+    StreamSpec(P=2, Kx=40, Ky=24, T=96, Tc=32, fft_bins=48, window="gauss",
+               detectors=(Detector(r_out=6.0), Detector("annular", 2.0, -1.0, 3.0, 9.0))),
+    StreamSpec(P=5, Kx=32, Ky=32, T=333, Tc=50, n_omega=120, E_max_meV=150.0, window="rect",
+               detectors=()),
+    StreamSpec(P=1, Kx=64, Ky=64, T=64, Tc=64, n_omega=9, E_max_meV=90.0, window="tukey",
+               window_param=0.3, subtract_mean=False, bose_T_K=300.0),
+]
+
+MODES = {"split_bf16": dict(precision="split_bf16"),
+         "split_cluster2": dict(precision="split_bf16", tc_cluster=2),
+         "split_inplace": dict(precision="split_bf16", frames_in_place=True),
+         "fp32": dict(precision="fp32")}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2607_02236_gb300 import build
+    build.build_all()
+
+
+def make_frames(spec, seed):
+    rng = np.random.default_rng(seed)
+    P, T, K, L = spec.P, spec.T, spec.Ky, spec.Kx
+    e = rng.standard_normal((P, 1, K, L)) + 1j * rng.standard_normal((P, 1, K, L))
+    s = 1e-2 * (rng.standard_normal((P, T, K, L)) + 1j * rng.standard_normal((P, T, K, L)))
+    return (e + s).astype(np.complex64)
+
+
+def device_frames(fr):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(fr.transpose(1, 0, 2, 3))).to("cuda")  # [T][P][Ky][Kx]
+
+
+def push_all(plan, bufs, stream=None):
+    """Round-robin pushes of Tc frames, as partitions arrive interleaved."""
+    pushed = [0] * len(SPECS)
+    while any(pushed[i] < s.T for i, s in enumerate(SPECS)):
+        for i, s in enumerate(SPECS):
+            if pushed[i] < s.T:
+                n = min(s.Tc, s.T - pushed[i])
+                fb = s.P * s.Kx * s.Ky * 8
+                plan.push(i, bufs[i].data_ptr() + pushed[i] * fb, n, cuda_stream=stream)
+                pushed[i] += n
+
+
+def check_all(plan, I, S, frames, tol):
+    worst = 0.0
+    for i, s in enumerate(SPECS):
+        ref = oracle.forward(frames[i], **oracle_kw(s))
+        io, so = plan.offsets(i)
+        n = s.P * s.Nw * s.Ky * s.Kx
+        got = I[io:io + n].cpu().numpy().reshape(s.P, s.Nw, s.Ky, s.Kx)
+        e = rel_err_peak(got, ref.I)
+        assert e <= tol, (i, e)
+        worst = max(worst, e)
+        D = len(s.detectors)
+        if D:
+            gs = S[so:so + s.P * D * s.Nw].cpu().numpy().reshape(s.P, D, s.Nw)
+            es = rel_err_peak(gs, ref.S)
+            assert es <= tol, (i, es)
+    return worst
+
+
+@pytest.mark.parametrize("mode", sorted(MODES))
+def test_grouped_final_flush(mode):
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    kw = MODES[mode]
+    frames = [make_frames(s, 100 + i) for i, s in enumerate(SPECS)]
+    bufs = [device_frames(f) for f in frames]
+    with TacawPlan([stream_config(s) for s in SPECS], **kw) as plan:
+        info = plan.info()
+        I = torch.zeros(info["I_elems"], dtype=torch.float32, device="cuda")
+        S = torch.zeros(max(1, info["S_elems"]), dtype=torch.float32, device="cuda")
+        push_all(plan, bufs)
+        before = plan.info()["kernel_launches"]
+        plan.finalize(I, S)
+        after = plan.info()
+        worst = check_all(plan, I, S, frames, TOL[kw["precision"]])
+    n_det = sum(1 for s in SPECS if len(s.detectors))
+    if mode in ("split_bf16", "split_cluster2"):
+        bf = after["tc_block_frames"]
+        tails = sum(1 for s in SPECS if s.T % bf)
+        # mean residual per stream, zero tails, ONE contraction launch, one aperture launch per stream
+        assert after["kernel_launches"] - before == len(SPECS) + tails + 1 + n_det
+    assert after["flushes"] == len(SPECS)
+    print(f"{mode}: worst max rel I error {worst:.3g}")
+
+
+@pytest.mark.parametrize("mode", ["split_bf16", "split_inplace", "fp32"])
+def test_graph_capture_and_replay(mode):
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    kw = MODES[mode]
+    tol = TOL[kw["precision"]]
+    frames = [make_frames(s, 200 + i) for i, s in enumerate(SPECS)]
+    bufs = [device_frames(f) for f in frames]
+    st = torch.cuda.Stream()
+    with TacawPlan([stream_config(s) for s in SPECS], **kw) as plan:
+        info = plan.info()
+        I = torch.zeros(info["I_elems"], dtype=torch.float32, device="cuda")
+        S = torch.zeros(max(1, info["S_elems"]), dtype=torch.float32, device="cuda")
+        # one eager segment on the capture stream first (kernel attributes set outside capture)
+        with torch.cuda.stream(st):
+            plan.reset(st)
+            push_all(plan, bufs, st)
+            plan.finalize_async(I, S, cuda_stream=st)
+            plan.check_errors(st)
+        check_all(plan, I, S, frames, tol)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            cur = torch.cuda.current_stream()
+            plan.reset(cur)
+            push_all(plan, bufs, cur)
+            plan.finalize_async(I, S, cuda_stream=cur)
+        launches = plan.info()["kernel_launches"]
+        for rep, seed in enumerate((300, 400)):
+            frames = [make_frames(s, seed + i) for i, s in enumerate(SPECS)]
+            for b, f in zip(bufs, frames):
+                b.copy_(device_frames(f))
+            I.zero_()
+            S.zero_()
+            torch.cuda.synchronize()
+            g.replay()
+            torch.cuda.synchronize()
+            plan.check_errors(torch.cuda.current_stream())
+            worst = check_all(plan, I, S, frames, tol)
+            print(f"{mode} replay {rep}: worst max rel I error {worst:.3g}")
+        # replays launch from the graph, not through the library
+        assert plan.info()["kernel_launches"] == launches
+        del g
