@@ -115,7 +115,13 @@ typedef struct {
     int accum;                         /* tacaw_accum */
     int64_t hbm_budget_bytes;          /* device bytes the plan may hold; 0: 90% of free memory */
     int k_stage;                       /* frames staged per flush (multiple of 8); 0: from budget */
-    const char *tune_cache_path;       /* reserved, may be NULL */
+    /* Tile autotuner of the split path (staged operands).  NULL: tiles from the built-in
+     * cost rule.  Non-NULL: at plan creation every stream shape times its candidate tiles
+     * (energies per tile, cluster size) on scratch operands and keeps the fastest
+     * predicted one; "" keeps nothing, a file path reads and appends a text cache keyed by
+     * GPU and shape, so later plans of the same shapes skip the timing.  A fixed
+     * tc_omega_tile or tc_cluster is honoured and only the other dimension is tuned.     */
+    const char *tune_cache_path;
     /* Tensor-core tiling (split path); 0 selects automatically.
      *   tc_omega_tile     complex energies per tile (multiple of 8)
      *   tc_accumulators   TMEM accumulators per tile: 1 (all products in one), 2 (hi*hi | small
@@ -154,6 +160,9 @@ typedef struct {
     int tc_cluster;            /* cluster size of the contraction (split path, first stream) */
     int tc_block_frames;       /* frames per staged operand row (split path) */
     int frames_in_place;       /* pushed frames are read in place by the contraction */
+    int tuned_streams;         /* streams whose tile the autotuner picked */
+    int tune_candidates;       /* candidate tiles timed at creation (0: none, or all cached) */
+    double tune_ms;            /* host time spent in the autotuner at creation */
 } tacaw_plan_info;
 
 /* Creates a plan: validates the descriptor, sizes and allocates device memory

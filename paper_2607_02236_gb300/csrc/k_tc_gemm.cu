@@ -938,7 +938,7 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *map
     size_t smem = 0;
     int64_t total = 0;
     for (int i = 0; i < n; ++i) {
-        if (args[i].cluster != C || args[i].stages != args[0].stages || args[i].bf != args[0].bf) {
+        if (args[i].cluster != C || args[i].bf != args[0].bf) {
             delete g;
             return cudaErrorInvalidValue;
         }

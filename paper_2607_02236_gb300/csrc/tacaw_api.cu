@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -76,6 +77,8 @@ struct Stream {
     int n_adj = 0;
     std::vector<unsigned char> tc_maps;
     int tc_cluster = 1;
+    int stages = 0;            // shared-memory pipeline stages of this stream's tiles
+    bool tuned = false;        // tile picked by the autotuner
     // in-place frames: per staged frame, a pointer into the pushed buffer
     const float2 **h_frame_ptr = nullptr;       // pinned, one slot per frame of the segment
     const float2 **d_frame_ptr = nullptr;
@@ -109,6 +112,8 @@ struct tacaw_plan_s {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
     double timed_ms = 0.0;
     int64_t timed_launches = 0;
+    int tuned_streams = 0, tune_timed = 0;
+    double tune_ms = 0.0;
 };
 
 namespace {
@@ -195,9 +200,13 @@ double bose_factor(double E, double TK) {
 // of them must fit the 512 TMEM columns (one accumulator may span two 256-column MMAs).
 // Among multiples of 8 the width with the least padded work plus a fixed per-tile cost
 // (operand A is re-read once per energy tile) wins; a requested width is clamped.
-void choose_omega_tile(Stream &s, int n_acc, int requested) {
+int omega_tile_max(int n_acc) {
     const int max_cols = n_acc > 1 ? 512 / n_acc : 512;
-    const int wt_max = std::max(8, (max_cols / 2) / 8 * 8);
+    return std::max(8, (max_cols / 2) / 8 * 8);
+}
+
+void choose_omega_tile(Stream &s, int n_acc, int requested) {
+    const int wt_max = omega_tile_max(n_acc);
     int best = 8;
     if (requested > 0) {
         best = std::min(requested, wt_max);
@@ -252,7 +261,7 @@ TcPlanArgs tc_args(tacaw_plan_s *p, const Stream &s, const EpiArgs &e) {
     a.n_kb = (n + p->bf - 1) / p->bf;
     a.kbB0 = s.stage_start / p->bf;
     a.bf = p->bf;
-    a.stages = p->stages;
+    a.stages = s.stages;
     a.split = p->tc_acc > 1 ? 1 : 0;
     a.n_big = p->tc_acc == 3 ? 2 : 1;
     a.cluster = p->in_place ? 1 : s.tc_cluster;
@@ -668,6 +677,17 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     }
     p->prec = desc->precision;
     p->accum = desc->accum;
+    if (!dev_alloc(p, &p->d_err, 1) || cudaMemset(p->d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        free_all(p);
+        delete p;
+        return fail(TACAW_ERR_OOM, "cudaMalloc(error word)");
+    }
+    auto bail = [&](tacaw_status st) {
+        free_all(p);
+        delete p;
+        return st;
+    };
     int T_pad_max = 0;
     for (int i = 0; i < desc->n_streams; ++i) {
         Stream s;
@@ -692,12 +712,53 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     for (int i = 0; i < desc->n_streams; ++i)
         if (!desc->streams[i].fft_bins) Es[i].assign(desc->streams[i].E_meV, desc->streams[i].E_meV + desc->streams[i].n_omega);
 
+    auto max_cols = [&]() {
+        int n = 0;
+        for (auto &s : p->s) n = std::max(n, 2 * s.wt);
+        return n;
+    };
+    if (p->prec == TACAW_PREC_SPLIT_BF16) {
+        // widest rows that still leave two stages (wider rows beat deeper rings in measurements)
+        if (!desc->tc_block_frames)
+            while (p->bf > 8 && tc_stages_for(max_cols(), p->bf) < 2) p->bf /= 2;
+        for (auto &s : p->s) s.n_kb_T = s.T_pad / p->bf;
+        p->tc_prefetch = desc->tc_prefetch > 0 ? desc->tc_prefetch : 0;
+        // autotuner: time the candidate tiles of every stream shape (staged operands only)
+        if (desc->tune_cache_path && !p->in_place) {
+            const auto t0 = std::chrono::steady_clock::now();
+            for (auto &s : p->s) {
+                TuneShape sh{};
+                sh.M = s.M;
+                sh.Nw = s.Nw;
+                sh.T = s.T;
+                sh.ring = desc->k_stage ? std::min(desc->k_stage, s.T_pad) : s.T_pad;
+                sh.bf = p->bf;
+                sh.n_acc = p->tc_acc;
+                sh.wt_max = omega_tile_max(p->tc_acc);
+                sh.fixed_wt = desc->tc_omega_tile ? s.wt : 0;
+                sh.fixed_cluster = desc->tc_cluster;
+                sh.multi = desc->n_streams > 1;
+                TuneResult r;
+                char eb[256];
+                if (!tc_autotune(sh, desc->tune_cache_path, p->d_err, nullptr, &r, eb, sizeof(eb)))
+                    return bail(fail(TACAW_ERR_CUDA, "%s", eb));
+                s.wt = r.wt;
+                s.n_wt = (s.Nw + r.wt - 1) / r.wt;
+                s.Nw_pad = s.wt * s.n_wt;
+                s.tc_cluster = r.cluster;
+                s.tuned = true;
+                p->tuned_streams++;
+                p->tune_timed += r.candidates;
+            }
+            p->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
+    }
+
     // budget and K_stage
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
         cudaError_t e = cudaGetLastError();
-        delete p;
-        return fail(TACAW_ERR_CUDA, "cudaMemGetInfo: %s", cudaGetErrorString(e));
+        return bail(fail(TACAW_ERR_CUDA, "cudaMemGetInfo: %s", cudaGetErrorString(e)));
     }
     const int64_t budget = desc->hbm_budget_bytes > 0 ? desc->hbm_budget_bytes : (int64_t)(0.9 * (double)free_b);
     int64_t fixed = 0;
@@ -725,53 +786,45 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
                     K = k;
                     break;
                 }
-            if (K == 0) {
-                delete p;
-                return fail(TACAW_ERR_OOM, "HBM budget of %lld bytes is too small (needs %lld at K_stage=64)",
-                            (long long)budget, (long long)need(64));
-            }
+            if (K == 0)
+                return bail(fail(TACAW_ERR_OOM, "HBM budget of %lld bytes is too small (needs %lld at K_stage=64)",
+                                 (long long)budget, (long long)need(64)));
         }
     } else if (need(K) > budget) {
-        delete p;
-        return fail(TACAW_ERR_OOM, "k_stage=%d needs %lld bytes, budget %lld", K, (long long)need(K), (long long)budget);
+        return bail(fail(TACAW_ERR_OOM, "k_stage=%d needs %lld bytes, budget %lld", K, (long long)need(K),
+                         (long long)budget));
     }
     p->k_stage = K;
-    int maxN = 0;
     for (auto &s : p->s) {
         s.ring = std::min(K, s.T_pad);
         s.needs_acc = s.T > s.ring;
-        maxN = std::max(maxN, 2 * s.wt);
     }
     if (p->prec == TACAW_PREC_SPLIT_BF16) {
-        // widest rows that still leave two stages (wider rows beat deeper rings in measurements)
-        if (!desc->tc_block_frames)
-            while (p->bf > 8 && tc_stages_for(maxN, p->bf) < 2) p->bf /= 2;
-        p->stages = tc_stages_for(maxN, p->bf);
-        for (auto &s : p->s) s.n_kb_T = s.T_pad / p->bf;
-        p->tc_prefetch = desc->tc_prefetch > 0 ? desc->tc_prefetch : 0;
-        if (p->stages < 2) {
-            delete p;
-            return fail(TACAW_ERR_UNSUPPORTED, "tensor-core tile of %d columns does not fit shared memory", maxN);
-        }
         for (auto &s : p->s) {
+            s.stages = tc_stages_for(2 * s.wt, p->bf);
+            if (s.stages < 2)
+                return bail(fail(TACAW_ERR_UNSUPPORTED, "tensor-core tile of %d columns does not fit shared memory",
+                                 2 * s.wt));
+        }
+        p->stages = p->s[0].stages;
+        for (auto &s : p->s) {
+            if (s.tuned) continue;
             const int N = 2 * s.wt;
             int br, nb;
             const int64_t n_mt = s.M_pad / kMTile;
             if (desc->tc_cluster) {
                 s.tc_cluster = desc->tc_cluster;
-                if (!tc_b_boxes(N, s.tc_cluster, &br, &nb)) {
-                    delete p;
-                    return fail(TACAW_ERR_INVALID_ARG, "tile of %d columns cannot be split over a cluster of %d", N,
-                                s.tc_cluster);
-                }
+                if (!tc_b_boxes(N, s.tc_cluster, &br, &nb))
+                    return bail(fail(TACAW_ERR_INVALID_ARG, "tile of %d columns cannot be split over a cluster of %d",
+                                     N, s.tc_cluster));
             } else {
                 // largest cluster that keeps (almost) every SM busy
-                const int r1 = tc_resident_ctas(N, p->bf, p->stages, 1);
+                const int r1 = tc_resident_ctas(N, p->bf, s.stages, 1);
                 s.tc_cluster = 1;
                 for (int c : {4, 2}) {
                     // multicast pays off for wide tiles (one accumulator); narrow tiles run best alone
                     if (N <= 256 || !tc_b_boxes(N, c, &br, &nb) || n_mt < 2 * c) continue;
-                    const int rc = tc_resident_ctas(N, p->bf, p->stages, c);
+                    const int rc = tc_resident_ctas(N, p->bf, s.stages, c);
                     if (r1 > 0 && rc >= (int)(0.97 * r1)) {
                         s.tc_cluster = c;
                         break;
@@ -780,14 +833,8 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
             }
         }
     }
-    if (!dev_alloc(p, &p->d_err, 1)) {
-        free_all(p);
-        delete p;
-        return fail(TACAW_ERR_OOM, "cudaMalloc(error word)");
-    }
     cudaStream_t st = nullptr;
     tacaw_status rc = TACAW_OK;
-    if (cudaMemsetAsync(p->d_err, 0, sizeof(uint32_t), st) != cudaSuccess) rc = fail(TACAW_ERR_CUDA, "memset");
     int64_t I_off = 0, S_off = 0;
     for (size_t i = 0; i < p->s.size() && rc == TACAW_OK; ++i) {
         Stream &s = p->s[i];
@@ -923,6 +970,9 @@ tacaw_status tacaw_plan_get_info(tacaw_plan_t p, tacaw_plan_info *info) {
     info->tc_accumulators = p->prec == TACAW_PREC_SPLIT_BF16 ? p->tc_acc : 0;
     info->tc_cluster = (p->prec == TACAW_PREC_SPLIT_BF16 && !p->s.empty()) ? p->s[0].tc_cluster : 0;
     info->tc_block_frames = p->prec == TACAW_PREC_SPLIT_BF16 ? p->bf : 0;
+    info->tuned_streams = p->tuned_streams;
+    info->tune_candidates = p->tune_timed;
+    info->tune_ms = p->tune_ms;
     info->frames_in_place = p->in_place ? 1 : 0;
     return TACAW_OK;
 }

@@ -271,7 +271,7 @@ struct TcMaps;                 // tensor maps (defined in k_tc_gemm.cu)
 cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps /* TcMaps */, cudaStream_t st);
 int64_t tc_grid_ctas(const TcPlanArgs &a);
 constexpr int kMaxGroupStreams = 16;
-// one launch over up to kMaxGroupStreams streams' flushes (same cluster size, stage count and block frames)
+// one launch over up to kMaxGroupStreams streams' flushes (same cluster size and block frames)
 cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *maps, int n, cudaStream_t st);
 cudaError_t launch_flush_tc_direct(const TcPlanArgs &a, const TcDirectArgs &d, const void *maps, cudaStream_t st);
 bool tc_make_maps_b(void *maps_out, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
@@ -285,6 +285,23 @@ bool tc_make_maps(void *maps_out, const __nv_bfloat16 *A_hi, const __nv_bfloat16
                   int N, int cluster, int bf, char *errbuf, size_t errlen);
 bool tc_b_boxes(int N, int cluster, int *box_rows, int *nbox);
 int tc_resident_ctas(int N, int bf, int stages, int cluster);
+
+// Tile autotuner (k_tc_tune.cu): picks energies per tile and cluster size for one stream shape.
+struct TuneShape {
+    int64_t M;                 // rows (probes x ROI pixels)
+    int Nw, T, ring;           // energies, frames per segment, frames per flush
+    int bf, n_acc, wt_max;     // block frames, TMEM accumulators, widest tile allowed
+    int fixed_wt, fixed_cluster;   // 0: tuned
+    bool multi;                // several streams share the final launch
+};
+struct TuneResult {
+    int wt = 0, cluster = 0;
+    int candidates = 0;        // candidates timed (0 when taken from the cache)
+    bool from_cache = false;
+    double predicted_ms = 0.0;
+};
+bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, cudaStream_t st, TuneResult *out,
+                 char *err, size_t errlen);
 
 struct ApertureArgs {
     const float *I;            // [P][Nw][npix]

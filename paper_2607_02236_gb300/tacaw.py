@@ -64,7 +64,8 @@ class CPlanInfo(ctypes.Structure):
     _fields_ = [("device_bytes", c_int64), ("k_stage", c_int), ("n_streams", c_int), ("precision", c_int),
                 ("I_elems", c_int64), ("S_elems", c_int64), ("flushes", c_int64), ("omega_tile", c_int),
                 ("stages", c_int), ("kernel_launches", c_int64), ("tc_accumulators", c_int),
-                ("tc_cluster", c_int), ("tc_block_frames", c_int), ("frames_in_place", c_int)]
+                ("tc_cluster", c_int), ("tc_block_frames", c_int), ("frames_in_place", c_int),
+                ("tuned_streams", c_int), ("tune_candidates", c_int), ("tune_ms", c_double)]
 
 
 _lib = None
@@ -164,7 +165,9 @@ class TacawPlan:
     def __init__(self, streams: Sequence[StreamConfig], precision: str = "split_bf16", accum: str = "kahan",
                  hbm_budget_bytes: int = 0, k_stage: int = 0, tc_omega_tile: int = 0,
                  tc_accumulators: int = 0, tc_cluster: int = 0, tc_block_frames: int = 0, tc_prefetch: int = 0,
-                 frames_in_place: bool = False):
+                 frames_in_place: bool = False, tune: Optional[str] = None):
+        """tune: None uses the built-in tile rule; "" autotunes at creation; a file path
+        autotunes through a text cache at that path."""
         L = lib()
         self._keep = []
         descs = (CStreamDesc * len(streams))()
@@ -191,7 +194,8 @@ class TacawPlan:
             d.n_detectors = len(s.detectors)
             d.detectors = ctypes.cast(dets, POINTER(CDetector))
         pd = CPlanDesc(len(streams), ctypes.cast(descs, POINTER(CStreamDesc)), PRECISIONS[precision],
-                       ACCUMS[accum], int(hbm_budget_bytes), int(k_stage), None, int(tc_omega_tile),
+                       ACCUMS[accum], int(hbm_budget_bytes), int(k_stage),
+                       None if tune is None else os.fsencode(tune), int(tc_omega_tile),
                        int(tc_accumulators), int(tc_cluster), int(tc_block_frames), int(tc_prefetch),
                        int(bool(frames_in_place)))
         h = c_void_p()

@@ -5,6 +5,7 @@ partitions of uneven size), checked element by element against the FP64 oracle.
            streams (tiles ordered longest first); parity per stream and the launch count
   graph    reset + pushes + finalize_async of a whole segment captured into a CUDA graph;
            two replays over two different frame sets, each against the oracle
+  tune     tiles picked by the autotuner (timed candidates, then a cache file hit), parity
 """
 import numpy as np
 import pytest
@@ -153,3 +154,33 @@ def test_graph_capture_and_replay(mode):
         # replays launch from the graph, not through the library
         assert plan.info()["kernel_launches"] == launches
         del g
+
+
+def test_autotuned_tiles_and_cache(tmp_path):
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    frames = [make_frames(s, 500 + i) for i, s in enumerate(SPECS)]
+    bufs = [device_frames(f) for f in frames]
+    cache = str(tmp_path / "tiles.txt")
+    infos = []
+    for rep in range(2):
+        with TacawPlan([stream_config(s) for s in SPECS], precision="split_bf16", tune=cache) as plan:
+            info = plan.info()
+            infos.append(info)
+            I = torch.zeros(info["I_elems"], dtype=torch.float32, device="cuda")
+            S = torch.zeros(max(1, info["S_elems"]), dtype=torch.float32, device="cuda")
+            push_all(plan, bufs)
+            plan.finalize(I, S)
+            worst = check_all(plan, I, S, frames, TOL["split_bf16"])
+        print(f"tuned plan {rep}: {info['tune_candidates']} candidates timed in {info['tune_ms']:.1f} ms, "
+              f"worst error {worst:.3g}")
+        assert info["tuned_streams"] == len(SPECS)
+    assert infos[0]["tune_candidates"] > 0
+    assert infos[1]["tune_candidates"] == 0            # every shape came from the cache
+    assert infos[1]["omega_tile"] == infos[0]["omega_tile"]
+    lines = open(cache).read().splitlines()
+    assert len(lines) == len(SPECS) and all(" | wt=" in ln for ln in lines)
+    # a fixed cluster size is honoured; only the energy tile is tuned
+    with TacawPlan([stream_config(s) for s in SPECS], precision="split_bf16", tune="", tc_cluster=1) as plan:
+        info = plan.info()
+    assert info["tc_cluster"] == 1 and info["tuned_streams"] == len(SPECS)

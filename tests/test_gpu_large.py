@@ -9,7 +9,8 @@ aperture spectra of a few probes are checked from all aperture pixels.
              T=8192 in 64-frame pushes, 1000 E over 0-150 meV, K_stage=2048 (four flushes,
              compensated FP32 accumulators), split BF16
   batched    16 partitions with uneven P, K^2, T, windows; 16-frame pushes interleaved
-             round-robin; 300 E; split BF16
+             round-robin; 300 E; split BF16, tiles picked by the autotuner, the final
+             flushes of all partitions in one launch
 """
 import numpy as np
 import pytest
@@ -140,8 +141,10 @@ def test_batched_uneven_partitions():
         px = sample_pixels(s, 4, rng)
         samples.append((pb, px, np.empty((s.T, 4), dtype=np.complex64)))
     with TacawPlan([stream_config(s) for s in specs], precision="split_bf16",
-                   hbm_budget_bytes=200 * 2 ** 30) as plan:
+                   hbm_budget_bytes=200 * 2 ** 30, tune="") as plan:
         info = plan.info()
+        assert info["tuned_streams"] == len(specs)
+        print(f"batched: autotuner timed {info['tune_candidates']} candidates in {info['tune_ms']:.0f} ms")
         I = torch.empty(info["I_elems"], dtype=torch.float32, device="cuda")
         S = torch.empty(info["S_elems"], dtype=torch.float32, device="cuda")
         pushed = [0] * len(specs)
@@ -158,9 +161,13 @@ def test_batched_uneven_partitions():
                 ser[pushed[i]:pushed[i] + n] = bufs[i].view(s.Tc, -1)[:n, rows].cpu().numpy()
                 plan.push(i, bufs[i], n)
                 pushed[i] += n
+        before = plan.info()
         plan.finalize(I, S)
         offs = [plan.offsets(i) for i in range(len(specs))]
         info = plan.info()
+    # one contraction launch for all partitions (plus per-partition prologue/aperture kernels)
+    tails = sum(1 for s in specs if s.T % info["tc_block_frames"])
+    assert info["kernel_launches"] - before["kernel_launches"] == 2 * len(specs) + tails + 1
     worst = 0.0
     for i, s in enumerate(specs):
         pb, px, ser = samples[i]
