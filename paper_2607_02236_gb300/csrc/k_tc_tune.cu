@@ -11,10 +11,11 @@
 //   one stream per plan:  ceil(CTAs / resident) waves x wave time
 //   several streams:      CTAs x wave time / resident   (their tiles share one launch)
 // summed over the segment's flushes.  Operand values do not change the instruction stream,
-// so the scratch operands hold one constant bit pattern.
+// so the scratch operands hold one constant bit pattern.  The caller picks from the table of
+// predictions (several streams share one cluster size, since it is a launch attribute).
 //
-// Results are kept in a text cache (one line per shape: "<key> | wt=<w> cluster=<c>") so a
-// later plan of the same shape on the same kind of GPU skips the timing.
+// Tables are kept in a text cache (one line per shape: "<key> | <wt>:<cluster>:<ms> ...") so
+// a later plan of the same shape on the same kind of GPU skips the timing.
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -58,50 +59,64 @@ std::string shape_key(const TuneShape &s) {
     return b;
 }
 
-bool cache_lookup(const char *path, const std::string &key, int *wt, int *C) {
+bool cache_lookup(const char *path, const std::string &key, std::vector<TuneCand> *tab) {
     if (!path || !*path) return false;
     FILE *f = fopen(path, "r");
     if (!f) return false;
-    char line[512];
+    std::vector<char> line(1 << 16);
     bool found = false;
-    while (fgets(line, sizeof(line), f)) {
-        const char *bar = strstr(line, " | ");
-        if (!bar || (size_t)(bar - line) != key.size() || strncmp(line, key.c_str(), key.size()) != 0) continue;
-        int w = 0, c = 0;
-        if (sscanf(bar + 3, "wt=%d cluster=%d", &w, &c) == 2 && w > 0 && c > 0) {
-            *wt = w;
-            *C = c;
-            found = true;       // the last matching line wins
+    while (fgets(line.data(), (int)line.size(), f)) {
+        const char *bar = strstr(line.data(), " | ");
+        if (!bar || (size_t)(bar - line.data()) != key.size() || strncmp(line.data(), key.c_str(), key.size()) != 0)
+            continue;
+        std::vector<TuneCand> t;
+        const char *q = bar + 3;
+        int w, c, used;
+        double ms;
+        while (sscanf(q, "%d:%d:%lf%n", &w, &c, &ms, &used) == 3) {
+            if (w > 0 && c > 0 && ms >= 0.0) t.push_back(TuneCand{w, c, ms});
+            q += used;
+        }
+        if (!t.empty()) {
+            *tab = t;           // the last matching line wins
+            found = true;
         }
     }
     fclose(f);
     return found;
 }
 
-void cache_store(const char *path, const std::string &key, int wt, int C, double ms) {
+void cache_store(const char *path, const std::string &key, const std::vector<TuneCand> &tab) {
     if (!path || !*path) return;
+    std::string line = key + " |";
+    char b[64];
+    for (const TuneCand &c : tab) {
+        snprintf(b, sizeof(b), " %d:%d:%.6f", c.wt, c.cluster, c.ms);
+        line += b;
+    }
+    line += "\n";
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s | wt=%d cluster=%d predicted_ms=%.4f\n", key.c_str(), wt, C, ms);
+    fputs(line.c_str(), f);     // one write per line: concurrent plans append whole lines
     fclose(f);
 }
 
 }  // namespace
 
-bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, cudaStream_t st, TuneResult *out,
-                 char *err, size_t errlen) {
-    *out = TuneResult{};
+bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, cudaStream_t st,
+                 std::vector<TuneCand> *table, int *timed, char *err, size_t errlen) {
+    table->clear();
+    *timed = 0;
     const std::string key = shape_key(sh);
-    int wt_c = 0, C_c = 0;
-    if (cache_lookup(cache_path, key, &wt_c, &C_c)) {
-        int br, nb;
-        if (wt_c % 8 == 0 && wt_c <= sh.wt_max && tc_b_boxes(2 * wt_c, C_c, &br, &nb) &&
-            tc_stages_for(2 * wt_c, sh.bf) >= 2) {
-            out->wt = wt_c;
-            out->cluster = C_c;
-            out->from_cache = true;
-            return true;
+    std::vector<TuneCand> cached;
+    if (cache_lookup(cache_path, key, &cached)) {
+        for (const TuneCand &c : cached) {
+            int br, nb;
+            if (c.wt % 8 == 0 && c.wt <= sh.wt_max && tc_b_boxes(2 * c.wt, c.cluster, &br, &nb) &&
+                tc_stages_for(2 * c.wt, sh.bf) >= 2)
+                table->push_back(c);
         }
+        if (!table->empty()) return true;
     }
     const int64_t n_mt = (sh.M + kMTile - 1) / kMTile;
     // candidate tiles
@@ -181,7 +196,6 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
         return false;
     }
     std::vector<char> maps(tc_maps_size());
-    double best = 1e300;
     bool ok = true;
     for (const Cand &c : cands) {
         const int N = 2 * c.wt;
@@ -238,7 +252,7 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
         if (!ok) break;
         const double slope = kb2 > kb1 ? (t[1] - t[0]) / (double)(kb2 - kb1) : 0.0;
         const int64_t ctas = (n_mt + c.C - 1) / c.C * c.C * c.n_wt;
-        const int64_t timed = c.n_mt_sub * c.n_wt;
+        const int64_t per_launch = c.n_mt_sub * c.n_wt;
         double pred = 0.0;
         for (int kb : flush_kb) {
             double tw = t[1] + slope * (double)(kb - kb2);
@@ -246,15 +260,10 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
             if (sh.multi)
                 pred += tw * (double)ctas / (double)c.resident;
             else
-                pred += tw * (double)((ctas + timed - 1) / timed);
+                pred += tw * (double)((ctas + per_launch - 1) / per_launch);
         }
-        out->candidates++;
-        if (pred < best) {
-            best = pred;
-            out->wt = c.wt;
-            out->cluster = c.C;
-            out->predicted_ms = pred;
-        }
+        table->push_back(TuneCand{c.wt, c.C, pred});
+        ++*timed;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -265,7 +274,7 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
         snprintf(err, errlen, "autotune: device wait timed out (error bits 0x%x)", h);
         return false;
     }
-    cache_store(cache_path, key, out->wt, out->cluster, out->predicted_ms);
+    cache_store(cache_path, key, *table);
     return true;
 }
 

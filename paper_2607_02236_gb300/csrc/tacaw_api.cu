@@ -726,7 +726,9 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         // autotuner: time the candidate tiles of every stream shape (staged operands only)
         if (desc->tune_cache_path && !p->in_place) {
             const auto t0 = std::chrono::steady_clock::now();
-            for (auto &s : p->s) {
+            std::vector<std::vector<TuneCand>> tabs(p->s.size());
+            for (size_t i = 0; i < p->s.size(); ++i) {
+                Stream &s = p->s[i];
                 TuneShape sh{};
                 sh.M = s.M;
                 sh.Nw = s.Nw;
@@ -738,17 +740,45 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
                 sh.fixed_wt = desc->tc_omega_tile ? s.wt : 0;
                 sh.fixed_cluster = desc->tc_cluster;
                 sh.multi = desc->n_streams > 1;
-                TuneResult r;
+                int timed = 0;
                 char eb[256];
-                if (!tc_autotune(sh, desc->tune_cache_path, p->d_err, nullptr, &r, eb, sizeof(eb)))
+                if (!tc_autotune(sh, desc->tune_cache_path, p->d_err, nullptr, &tabs[i], &timed, eb, sizeof(eb)))
                     return bail(fail(TACAW_ERR_CUDA, "%s", eb));
-                s.wt = r.wt;
-                s.n_wt = (s.Nw + r.wt - 1) / r.wt;
+                p->tune_timed += timed;
+            }
+            // one cluster size for all streams (their last flushes share one launch), the
+            // fastest total; then each stream's fastest energy tile under it
+            int best_C = 0;
+            double best_total = 1e300;
+            for (int C : {1, 2, 4}) {
+                double total = 0.0;
+                bool all = true;
+                for (auto &tab : tabs) {
+                    double b = 1e300;
+                    for (const TuneCand &c : tab)
+                        if (c.cluster == C) b = std::min(b, c.ms);
+                    if (b == 1e300) all = false;
+                    total += b;
+                }
+                if (all && total < best_total) {
+                    best_total = total;
+                    best_C = C;
+                }
+            }
+            if (!best_C) return bail(fail(TACAW_ERR_UNSUPPORTED, "autotune: no cluster size fits every stream"));
+            for (size_t i = 0; i < p->s.size(); ++i) {
+                Stream &s = p->s[i];
+                double b = 1e300;
+                for (const TuneCand &c : tabs[i])
+                    if (c.cluster == best_C && c.ms < b) {
+                        b = c.ms;
+                        s.wt = c.wt;
+                    }
+                s.n_wt = (s.Nw + s.wt - 1) / s.wt;
                 s.Nw_pad = s.wt * s.n_wt;
-                s.tc_cluster = r.cluster;
+                s.tc_cluster = best_C;
                 s.tuned = true;
                 p->tuned_streams++;
-                p->tune_timed += r.candidates;
             }
             p->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         }

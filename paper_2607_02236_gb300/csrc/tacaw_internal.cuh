@@ -13,6 +13,7 @@
 //   accumulators          [Nw_pad][M_pad] (float2 sum + float2 compensation, or double2)
 //   outputs               I float [p][j][ky][kx], Psi float2 [p][j][ky][kx], S float [p][d][j]
 #pragma once
+#include <vector>
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -294,14 +295,14 @@ struct TuneShape {
     int fixed_wt, fixed_cluster;   // 0: tuned
     bool multi;                // several streams share the final launch
 };
-struct TuneResult {
-    int wt = 0, cluster = 0;
-    int candidates = 0;        // candidates timed (0 when taken from the cache)
-    bool from_cache = false;
-    double predicted_ms = 0.0;
+struct TuneCand {
+    int wt, cluster;
+    double ms;                 // predicted contraction time of the stream's segment
 };
-bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, cudaStream_t st, TuneResult *out,
-                 char *err, size_t errlen);
+// Fills `table` with one prediction per candidate tile (from the cache when it holds the
+// shape; *timed = candidates actually timed).  False with a message on a CUDA error.
+bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, cudaStream_t st,
+                 std::vector<TuneCand> *table, int *timed, char *err, size_t errlen);
 
 struct ApertureArgs {
     const float *I;            // [P][Nw][npix]

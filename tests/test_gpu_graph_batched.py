@@ -179,7 +179,11 @@ def test_autotuned_tiles_and_cache(tmp_path):
     assert infos[1]["tune_candidates"] == 0            # every shape came from the cache
     assert infos[1]["omega_tile"] == infos[0]["omega_tile"]
     lines = open(cache).read().splitlines()
-    assert len(lines) == len(SPECS) and all(" | wt=" in ln for ln in lines)
+    assert len(lines) == len(SPECS)
+    for ln in lines:                                   # "<shape key> | <wt>:<cluster>:<ms> ..."
+        key, table = ln.split(" | ")
+        cands = [tuple(map(float, c.split(":"))) for c in table.split()]
+        assert key.startswith("tacaw-tune-v1") and cands and all(c[0] % 8 == 0 and c[2] > 0 for c in cands)
     # a fixed cluster size is honoured; only the energy tile is tuned
     with TacawPlan([stream_config(s) for s in SPECS], precision="split_bf16", tune="", tc_cluster=1) as plan:
         info = plan.info()
