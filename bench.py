@@ -33,8 +33,8 @@ UNIT = "CMAC/s"
 # the kernel's source file at capture time (reported only while the source is unchanged).
 KERNEL_TRAFFIC = {
     # ncu --set full of flush_tc_kernel on `bench.py --small` (P=2, T=2048, 400 energies, default tiling):
-    # dram__bytes_read.sum 2.275640 GB + dram__bytes_write.sum 0.204266 GB per launch of 1.07e11 CMAC
-    ("0f1f317175bb73aa", "flush_tc_kernel"): 2.309592e-02,
+    # dram__bytes_read.sum 2.337876 GB + dram__bytes_write.sum 0.204146 GB per launch of 1.07e11 CMAC
+    ("2b7b887d7e91f125", "flush_tc_kernel"): 2.367443e-02,
 }
 
 
