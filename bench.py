@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32"])
     ap.add_argument("--fp32-steps", type=int, default=2, help="steps of the FP32 path for comparison (0: skip)")
-    ap.add_argument("--e2e-steps", type=int, default=2, help="end-to-end steps from pinned host memory (0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="end-to-end steps from pinned host memory (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU oracle baseline")
     ap.add_argument("--small", action="store_true", help="small workload (profiling captures)")
     ap.add_argument("--in-place", dest="in_place", action="store_true", default=False,
@@ -372,37 +372,62 @@ def main():
         push_elems = Tc * frame_elems
         host = torch.empty(ring * push_elems, dtype=torch.complex64, pin_memory=True)
         host.copy_(x[: ring * push_elems])
-        S_host = torch.empty(S.numel(), dtype=torch.float32, pin_memory=True)
+        S_host = [torch.empty(S.numel(), dtype=torch.float32, pin_memory=True) for _ in range(2)]
         cs = torch.cuda.Stream()
-        ready_ev = [torch.cuda.Event() for _ in range(n_push)]
+        in_place = bool(info["frames_in_place"])
+        # a staged plan converts each push when it is enqueued, so device slices form a ring that
+        # the next copies reuse as soon as that conversion is done (copies of the next step run
+        # under this step's contraction); an in-place plan reads every slice until finalize
+        n_slots = n_push if in_place else ring
+        copied = [torch.cuda.Event() for _ in range(n_slots)]
+        consumed = [None] * n_slots
 
-        def e2e_step():
-            # every push: pinned host -> its slice of the device input (copy stream), then the push;
-            # the slices stay untouched until finalize, so in-place plans may read them directly
+        def e2e_step(k):
             plan.reset(st)
-            cs.wait_stream(stream)
             for i in range(n_push):
+                slot = i % n_slots
                 n = min(Tc, T - i * Tc)
                 with torch.cuda.stream(cs):
-                    x[i * push_elems:i * push_elems + n * frame_elems].copy_(
+                    if consumed[slot] is not None:
+                        cs.wait_event(consumed[slot])
+                    x[slot * push_elems:slot * push_elems + n * frame_elems].copy_(
                         host[(i % ring) * push_elems:(i % ring) * push_elems + n * frame_elems], non_blocking=True)
-                    ready_ev[i].record(cs)
-                stream.wait_event(ready_ev[i])
-                plan.push(0, base + i * push_elems * 8, n, st)
-            plan.finalize(I, S, None, st)
-            S_host.copy_(S, non_blocking=True)
-            torch.cuda.synchronize()
+                    copied[slot].record(cs)
+                stream.wait_event(copied[slot])
+                plan.push(0, base + slot * push_elems * 8, n, st)
+                if not in_place:
+                    consumed[slot] = torch.cuda.Event()
+                    consumed[slot].record(stream)
+            plan.finalize_async(I, S, None, st)
+            S_host[k % 2].copy_(S, non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(stream)
+            if in_place:
+                for slot in range(n_slots):
+                    consumed[slot] = done
+            return done
 
-        e2e_step()
+        e2e_step(0).synchronize()
+        plan.check_errors(st)
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            e2e_step()
+        prev = None
+        checksum = 0.0
+        for k in range(args.e2e_steps):
+            ev = e2e_step(k)
+            if prev is not None:                 # the host reads each step's result, one step behind
+                prev[0].synchronize()
+                checksum += float(S_host[prev[1] % 2][0])
+            prev = (ev, k)
+        prev[0].synchronize()
+        checksum += float(S_host[prev[1] % 2][0])
+        plan.check_errors(st)
         el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         e2e = {"value": world * cmac_step * args.e2e_steps / el, "unit": UNIT,
                "h2d_bytes_per_step": T * frame_elems * 8, "d2h_bytes_per_step": S.numel() * 4,
                "ms_per_step": 1e3 * el / args.e2e_steps,
-               "input": f"pinned host ring of {ring} pushes ({ring * push_elems * 8 / 1e9:.1f} GB) cycled"}
+               "input": f"pinned host ring of {ring} pushes ({ring * push_elems * 8 / 1e9:.1f} GB) cycled",
+               "overlap": "copies of the next step overlap this step's contraction" if not in_place else "none"}
         del host
     plan.close()
 
