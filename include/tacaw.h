@@ -141,6 +141,12 @@ typedef struct {
      * valid and unchanged until the flush that covers its frames has completed on the stream:
      * with the default K_stage (the whole segment) that is until tacaw_finalize returns. */
     int frames_in_place;
+    /* Split path, staged operands: 1 runs each pair of 128-row tiles as 256-row MMAs on a
+     * cluster of two SMs (tcgen05 CTA pair): each SM stages its own rows of A and half of the
+     * tile's twiddle rows, halving the twiddle operand traffic per SM.  Applies to streams whose
+     * tile is at most 256 columns, a multiple of 32 (others keep the single-CTA form); needs
+     * tc_cluster 0 or 2.  0: off.                                                          */
+    int tc_pair;
 } tacaw_plan_desc;
 
 typedef struct tacaw_plan_s *tacaw_plan_t;
@@ -160,6 +166,7 @@ typedef struct {
     int tc_cluster;            /* cluster size of the contraction (split path, first stream) */
     int tc_block_frames;       /* frames per staged operand row (split path) */
     int frames_in_place;       /* pushed frames are read in place by the contraction */
+    int tc_pair;               /* first stream runs CTA-pair MMAs */
     int tuned_streams;         /* streams whose tile the autotuner picked */
     int tune_candidates;       /* candidate tiles timed at creation (0: none, or all cached) */
     double tune_ms;            /* host time spent in the autotuner at creation */

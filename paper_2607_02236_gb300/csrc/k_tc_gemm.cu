@@ -141,6 +141,64 @@ __device__ __forceinline__ void tmem_relinquish() {
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
+// CTA-pair forms (tcgen05 ... cta_group::2): one warp of EACH CTA of the pair performs the
+// allocation, relinquish and deallocation collectively; MMAs and commits are issued by the
+// even CTA only.
+__device__ __forceinline__ void tmem_alloc2(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish2() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc2(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma2_bf16_ss(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma2_commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"(mask)
+        : "memory");
+}
+// shared::cluster address of the same shared-memory offset in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on a barrier that also receives arrivals from the peer CTA.
+__device__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        if (mbar_try_wait_cluster(bar, parity)) return true;
+        if (abort_flag && *abort_flag) return false;
+        if (globaltimer() - t0 > kWaitLimitNs) return false;
+    }
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -213,7 +271,11 @@ __host__ __device__ inline uint32_t tc_a_bytes(int bf) { return (uint32_t)kMTile
 __host__ __device__ inline uint32_t tc_b_bytes_padded(int N, int bf) {
     return ((uint32_t)N * 4u * (uint32_t)bf + 1023u) & ~1023u;
 }
-__host__ __device__ inline uint32_t tc_stage_bytes(int N, int bf) { return 2u * tc_a_bytes(bf) + 2u * tc_b_bytes_padded(N, bf); }
+// B rows held by one CTA: the whole tile, or half of it in the CTA-pair form
+__host__ __device__ inline int tc_b_rows(int N, int pair) { return pair ? N / 2 : N; }
+__host__ __device__ inline uint32_t tc_stage_bytes(int N, int bf, int pair = 0) {
+    return 2u * tc_a_bytes(bf) + 2u * tc_b_bytes_padded(tc_b_rows(N, pair), bf);
+}
 __host__ __device__ inline uint32_t tc_tmem_cols(int N) {
     uint32_t c = 32;
     while (c < (uint32_t)N) c <<= 1;
@@ -350,7 +412,14 @@ __device__ __forceinline__ void tc_mma_loop(const TcPlanArgs &a, TcShared *sh, u
     if (trace) trace[3] = globaltimer();
 }
 
-__global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant__ TcGroup g) {
+// Body of the staged contraction kernel.  PAIR: the CTA-pair form -- clusters of two CTAs run
+// M = 256 MMAs (tcgen05 cta_group::2) issued by the even CTA: each CTA stages its own 128 rows
+// of A and half of the tile's B rows, so each SM reads half the B operand per MMA; both CTAs
+// receive their 128 accumulator rows in their own TMEM.  The odd CTA's warp 1 relays its
+// stage-full events to the even CTA's barrier (remote arrive), so every CTA still waits only
+// on barriers in its own shared memory when it drains its copies.
+template <bool PAIR>
+__device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
     int gi = 0;
     while (gi + 1 < g.n && (int)blockIdx.x >= g.e[gi + 1].cta_begin) ++gi;
     const TcMaps &maps = g.e[gi].maps;
@@ -360,22 +429,25 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t RB = 4u * (uint32_t)a.bf;           // bytes per operand row
     const uint32_t kABytes = tc_a_bytes(a.bf);
-    const uint32_t b_pad = tc_b_bytes_padded(a.N, a.bf);
-    const uint32_t stage_bytes = tc_stage_bytes(a.N, a.bf);
+    const uint32_t b_pad = tc_b_bytes_padded(tc_b_rows(a.N, PAIR), a.bf);
+    const uint32_t stage_bytes = tc_stage_bytes(a.N, a.bf, PAIR);
     TcShared *sh = reinterpret_cast<TcShared *>(base + (size_t)a.stages * stage_bytes);
     const uint32_t base_s = smem_u32(base);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int C = a.cluster;
+    const int C = PAIR ? 2 : a.cluster;
     const uint32_t crank = C > 1 ? cluster_ctarank() : 0u;
     const unsigned cid = bid / (unsigned)C;
     const int wtile = (int)(cid % (unsigned)a.n_wt);
     const int m0 = ((int)(cid / (unsigned)a.n_wt) * C + (int)crank) * kMTile;
     const int n_acc = a.split ? a.n_big + 1 : 1;
     const uint32_t ncols = tc_tmem_cols(n_acc * a.N);
-    const uint32_t tx_bytes = 2u * kABytes + 2u * (uint32_t)a.N * RB;
+    // bytes landing in this CTA's stage: its A rows plus the B rows it holds (the whole tile
+    // when the cluster multicasts B, half of it in the pair form)
+    const uint32_t tx_bytes = 2u * kABytes + 2u * (uint32_t)tc_b_rows(a.N, PAIR) * RB;
     const int rows_cta = a.N / C;                 // B rows this CTA loads (for the whole cluster)
     const uint16_t cmask = (uint16_t)((1u << C) - 1u);
+    const bool leader = !PAIR || crank == 0;      // issues the MMAs
     unsigned long long *trace = a.trace ? a.trace + (size_t)bid * kTraceWords : nullptr;
     if (trace && threadIdx.x == 0) {
         trace[0] = globaltimer();
@@ -384,16 +456,24 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
-            mbar_init(smem_u32(&sh->full[s]), 1);
-            mbar_init(smem_u32(&sh->empty[s]), (uint32_t)C);   // one release per CTA of the cluster
+            // pair form: the even CTA's stage is full after its own copies AND the odd CTA's relay
+            mbar_init(smem_u32(&sh->full[s]), PAIR && leader ? 2u : 1u);
+            // one release per CTA of a multicast cluster; the pair's MMAs release both CTAs at once
+            mbar_init(smem_u32(&sh->empty[s]), PAIR ? 1u : (uint32_t)C);
         }
         mbar_init(smem_u32(&sh->tmem_full), 1);
         sh->abort_flag = 0;
         fence_mbar_init();
     }
+    if (PAIR) cluster_sync();   // the peer's barriers exist before the collective allocation
     if (warp == 1) {
-        tmem_alloc(smem_u32(&sh->tmem_addr), ncols);
-        tmem_relinquish();
+        if (PAIR) {
+            tmem_alloc2(smem_u32(&sh->tmem_addr), ncols);
+            tmem_relinquish2();
+        } else {
+            tmem_alloc(smem_u32(&sh->tmem_addr), ncols);
+            tmem_relinquish();
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -429,8 +509,12 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
                 for (int b = 0; b < maps.nbox_b; ++b) {
                     const int r0 = (int)crank * rows_cta + b * maps.box_b_rows;
                     const int row = wtile * a.N + r0;
-                    const uint32_t off = (uint32_t)r0 * RB;
-                    if (C > 1) {
+                    // multicast pieces sit at their row in every CTA; a pair CTA keeps its half at 0
+                    const uint32_t off = (uint32_t)(PAIR ? b * maps.box_b_rows : r0) * RB;
+                    if (PAIR) {
+                        tma_load_3d(st + 2 * kABytes + off, &maps.b_hi, 0, row, a.kbB0 + kb, full);
+                        tma_load_3d(st + 2 * kABytes + b_pad + off, &maps.b_lo, 0, row, a.kbB0 + kb, full);
+                    } else if (C > 1) {
                         tma_load_3d_mc(st + 2 * kABytes + off, &maps.b_hi, 0, row, a.kbB0 + kb, full, cmask);
                         tma_load_3d_mc(st + 2 * kABytes + b_pad + off, &maps.b_lo, 0, row, a.kbB0 + kb, full, cmask);
                     } else {
@@ -463,19 +547,37 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
                 }
             }
         }
+    } else if (warp == 1 && PAIR && !leader) {
+        if (lane == 0) {
+            // relay: each stage of this CTA is complete -> one arrival on the even CTA's barrier
+            for (int kb = 0; kb < a.n_kb; ++kb) {
+                const int s = kb % a.stages;
+                if (!mbar_wait(smem_u32(&sh->full[s]), (uint32_t)(kb / a.stages) & 1u, abort_flag)) {
+                    if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
+                    *abort_flag = 1;
+                    break;
+                }
+                if (trace && kb == 0) trace[2] = globaltimer();
+                mbar_arrive_remote(mapa_shared(smem_u32(&sh->full[s]), 0u));
+            }
+            if (trace) trace[3] = globaltimer();
+        }
     } else if (warp == 1) {
         if (lane == 0) {
             const int n0 = a.N < 256 ? a.N : 256;
             const int n1 = a.N - n0;
-            const uint32_t id0 = idesc_bf16_f32(kMTile, n0);
-            const uint32_t id1 = n1 > 0 ? idesc_bf16_f32(kMTile, n1) : 0u;
+            const int m_mma = PAIR ? 2 * kMTile : kMTile;
+            const uint32_t id0 = idesc_bf16_f32(m_mma, n0);
+            const uint32_t id1 = n1 > 0 ? idesc_bf16_f32(m_mma, n1) : 0u;
             const uint64_t b_half_off = (uint64_t)((n0 * RB) >> 4);
             const uint32_t acc_small = tmem + (uint32_t)(a.n_big * a.N);
             const int ksteps = a.bf / 8;
             for (int kb = 0; kb < a.n_kb; ++kb) {
                 const int s = kb % a.stages;
                 const uint32_t use = (uint32_t)(kb / a.stages);
-                if (!mbar_wait(smem_u32(&sh->full[s]), use & 1u, abort_flag)) {
+                const bool got = PAIR ? mbar_wait_cluster(smem_u32(&sh->full[s]), use & 1u, abort_flag)
+                                      : mbar_wait(smem_u32(&sh->full[s]), use & 1u, abort_flag);
+                if (!got) {
                     if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
                     *abort_flag = 1;
                     break;
@@ -492,7 +594,19 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
                     const uint64_t adv = (uint64_t)(2 * ks);
                     const uint64_t dAhi = dAhi0 + adv, dAlo = dAlo0 + adv, dBhi = dBhi0 + adv, dBlo = dBlo0 + adv;
                     const int g = kb * ksteps + ks;       // global K-step index
-                    if (a.split) {
+                    if (PAIR) {
+                        // N <= 256 (host-checked); the even CTA's descriptors address both CTAs
+                        if (a.split) {
+                            const int big = a.n_big == 2 ? (g & 1) : 0;
+                            mma2_bf16_ss(tmem + (uint32_t)(big * a.N), dAhi, dBhi, id0, g >= a.n_big ? 1u : 0u);
+                            mma2_bf16_ss(acc_small, dAhi, dBlo, id0, g > 0 ? 1u : 0u);
+                            mma2_bf16_ss(acc_small, dAlo, dBhi, id0, 1u);
+                        } else {
+                            mma2_bf16_ss(tmem, dAhi, dBhi, id0, g > 0 ? 1u : 0u);
+                            mma2_bf16_ss(tmem, dAhi, dBlo, id0, 1u);
+                            mma2_bf16_ss(tmem, dAlo, dBhi, id0, 1u);
+                        }
+                    } else if (a.split) {
                         // N <= 256: one MMA per product
                         const int big = a.n_big == 2 ? (g & 1) : 0;
                         mma_bf16_ss(tmem + (uint32_t)(big * a.N), dAhi, dBhi, id0, g >= a.n_big ? 1u : 0u);
@@ -509,13 +623,18 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
                         }
                     }
                 }
-                if (C > 1)
+                if (PAIR)
+                    mma2_commit_mc(smem_u32(&sh->empty[s]), cmask);
+                else if (C > 1)
                     mma_commit_mc(smem_u32(&sh->empty[s]), cmask);
                 else
                     mma_commit(smem_u32(&sh->empty[s]));
             }
             // always signal: the epilogue (and TMEM release) wait for every issued MMA
-            mma_commit(smem_u32(&sh->tmem_full));
+            if (PAIR)
+                mma2_commit_mc(smem_u32(&sh->tmem_full), cmask);
+            else
+                mma_commit(smem_u32(&sh->tmem_full));
             if (trace) trace[3] = globaltimer();
         }
     } else {
@@ -562,9 +681,17 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
     if (C > 1) cluster_sync();   // no CTA leaves while a peer may still signal its barriers
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, ncols);
+        if (PAIR)
+            tmem_dealloc2(tmem, ncols);
+        else
+            tmem_dealloc(tmem, ncols);
     }
     if (trace && threadIdx.x == 0) trace[6] = globaltimer();
+}
+
+__global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant__ TcGroup g) { flush_tc_body<false>(g); }
+__global__ void __launch_bounds__(192, 1) flush_tc_pair_kernel(const __grid_constant__ TcGroup g) {
+    flush_tc_body<true>(g);
 }
 
 // --------------------------------------------------------------------------------------
@@ -783,15 +910,15 @@ __global__ void __launch_bounds__(320, 1) flush_tc_direct_kernel(const __grid_co
 // --------------------------------------------------------------------------------------
 // host side
 // --------------------------------------------------------------------------------------
-int tc_stages_for(int N, int bf) {
+int tc_stages_for(int N, int bf, int pair) {
     const int budget = kSmemLimit - 1024 - (int)sizeof(TcShared);
-    int s = budget / (int)tc_stage_bytes(N, bf);
+    int s = budget / (int)tc_stage_bytes(N, bf, pair);
     if (s > kMaxStages) s = kMaxStages;
     return s;
 }
 
-size_t tc_smem_bytes(int N, int bf, int stages) {
-    return (size_t)stages * tc_stage_bytes(N, bf) + sizeof(TcShared) + 1024;
+size_t tc_smem_bytes(int N, int bf, int stages, int pair) {
+    return (size_t)stages * tc_stage_bytes(N, bf, pair) + sizeof(TcShared) + 1024;
 }
 
 size_t tc_maps_size() { return sizeof(TcMaps); }
@@ -900,9 +1027,11 @@ cudaError_t launch_flush_tc_direct(const TcPlanArgs &a, const TcDirectArgs &d, c
 }
 
 // Co-resident CTAs of the contraction kernel for a cluster size (0 on error).
-int tc_resident_ctas(int N, int bf, int stages, int cluster) {
-    const size_t smem = tc_smem_bytes(N, bf, stages);
-    if (cudaFuncSetAttribute(flush_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+int tc_resident_ctas(int N, int bf, int stages, int cluster, int pair) {
+    const size_t smem = tc_smem_bytes(N, bf, stages, pair);
+    auto kern = pair ? flush_tc_pair_kernel : flush_tc_kernel;
+    if (pair) cluster = 2;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -918,7 +1047,7 @@ int tc_resident_ctas(int N, int bf, int stages, int cluster) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, flush_tc_kernel, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -935,10 +1064,13 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *map
     TcGroup *g = new (std::nothrow) TcGroup();
     if (!g) return cudaErrorMemoryAllocation;
     const int C = args[0].cluster;
+    const int pair = args[0].pair;
     size_t smem = 0;
     int64_t total = 0;
     for (int i = 0; i < n; ++i) {
-        if (args[i].cluster != C || args[i].bf != args[0].bf) {
+        // the pair form needs clusters of 2 and tiles of at most 256 columns (one MMA each)
+        if (args[i].cluster != C || args[i].bf != args[0].bf || args[i].pair != pair ||
+            (pair && (C != 2 || args[i].N > 256 || args[i].N % 32))) {
             delete g;
             return cudaErrorInvalidValue;
         }
@@ -949,14 +1081,15 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *map
         const int64_t c = tc_grid_ctas(args[i]);
         g->e[i].ctas = (int)c;
         total += c;
-        smem = std::max(smem, tc_smem_bytes(args[i].N, args[i].bf, args[i].stages));
+        smem = std::max(smem, tc_smem_bytes(args[i].N, args[i].bf, args[i].stages, pair));
     }
     g->n = n;
     if (total <= 0 || total > 0x7fffffffLL) {
         delete g;
         return cudaErrorInvalidConfiguration;
     }
-    cudaError_t e = cudaFuncSetAttribute(flush_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = pair ? flush_tc_pair_kernel : flush_tc_kernel;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)total, 1, 1);
@@ -970,7 +1103,7 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *map
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, flush_tc_kernel, *g);
+        e = cudaLaunchKernelEx(&cfg, kern, *g);
     }
     delete g;
     return e;

@@ -78,6 +78,7 @@ struct Stream {
     std::vector<unsigned char> tc_maps;
     int tc_cluster = 1;
     int stages = 0;            // shared-memory pipeline stages of this stream's tiles
+    int tc_pair = 0;           // CTA-pair MMAs (cluster of 2, M = 256)
     bool tuned = false;        // tile picked by the autotuner
     // in-place frames: per staged frame, a pointer into the pushed buffer
     const float2 **h_frame_ptr = nullptr;       // pinned, one slot per frame of the segment
@@ -265,6 +266,7 @@ TcPlanArgs tc_args(tacaw_plan_s *p, const Stream &s, const EpiArgs &e) {
     a.split = p->tc_acc > 1 ? 1 : 0;
     a.n_big = p->tc_acc == 3 ? 2 : 1;
     a.cluster = p->in_place ? 1 : s.tc_cluster;
+    a.pair = p->in_place ? 0 : s.tc_pair;
     a.prefetch = p->in_place ? 0 : p->tc_prefetch;
     a.err = p->d_err;
     a.trace = nullptr;
@@ -383,10 +385,12 @@ tacaw_status final_flush_grouped(tacaw_plan_s *p, float *d_I, float2 *d_Psi, cud
         return (int64_t)((s.staged + p->bf - 1) / p->bf) * (2 * s.wt + 48);
     };
     std::stable_sort(todo.begin(), todo.end(), [&](int a, int b) { return work(a) > work(b); });
-    for (int C : {1, 2, 4}) {
+    for (int key = 0; key < 8; ++key) {
+        const int C = 1 << (key & 3), pr = key >> 2;   // (cluster, pair): a kernel and a launch attribute
+        if (C > 4) continue;
         std::vector<int> grp;
         for (int i : todo)
-            if (p->s[i].tc_cluster == C) grp.push_back(i);
+            if (p->s[i].tc_cluster == C && p->s[i].tc_pair == pr) grp.push_back(i);
         for (size_t g0 = 0; g0 < grp.size(); g0 += kMaxGroupStreams) {
             const size_t g1 = std::min(grp.size(), g0 + (size_t)kMaxGroupStreams);
             std::vector<TcPlanArgs> args;
@@ -831,14 +835,22 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     }
     if (p->prec == TACAW_PREC_SPLIT_BF16) {
         for (auto &s : p->s) {
-            s.stages = tc_stages_for(2 * s.wt, p->bf);
+            // CTA pairs: 128-row MMAs become 256-row MMAs over a cluster of two, each CTA holding
+            // half of the tile's twiddle rows (tiles of at most 256 columns, a multiple of 32)
+            const int N = 2 * s.wt;
+            if (desc->tc_pair && !p->in_place && N <= 256 && N % 32 == 0 && s.M_pad / kMTile >= 2 &&
+                (desc->tc_cluster == 0 || desc->tc_cluster == 2)) {
+                s.tc_pair = 1;
+                s.tc_cluster = 2;
+            }
+            s.stages = tc_stages_for(N, p->bf, s.tc_pair);
             if (s.stages < 2)
                 return bail(fail(TACAW_ERR_UNSUPPORTED, "tensor-core tile of %d columns does not fit shared memory",
                                  2 * s.wt));
         }
         p->stages = p->s[0].stages;
         for (auto &s : p->s) {
-            if (s.tuned) continue;
+            if (s.tuned || s.tc_pair) continue;
             const int N = 2 * s.wt;
             int br, nb;
             const int64_t n_mt = s.M_pad / kMTile;
@@ -1004,6 +1016,7 @@ tacaw_status tacaw_plan_get_info(tacaw_plan_t p, tacaw_plan_info *info) {
     info->tune_candidates = p->tune_timed;
     info->tune_ms = p->tune_ms;
     info->frames_in_place = p->in_place ? 1 : 0;
+    info->tc_pair = (p->prec == TACAW_PREC_SPLIT_BF16 && !p->s.empty()) ? p->s[0].tc_pair : 0;
     return TACAW_OK;
 }
 

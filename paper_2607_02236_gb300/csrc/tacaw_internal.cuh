@@ -249,6 +249,7 @@ struct TcPlanArgs {
     int split;                 // 1: separate TMEM accumulators for hi*hi and hi*lo + lo*hi (N <= 256)
     int n_big;                 // hi*hi accumulators (1 or 2, alternating by block parity)
     int cluster;               // CTAs sharing (multicasting) one energy tile's B rows: 1, 2 or 4
+    int pair;                  // 1: CTA-pair MMAs (M = 256 over a cluster of 2, B rows split); N <= 256
     int prefetch;              // staging blocks of A prefetched into L2 ahead of the current one (0: off)
     unsigned long long *trace; // null, or kTraceWords globaltimer stamps per CTA (phase boundaries)
     uint32_t *err;
@@ -278,14 +279,14 @@ cudaError_t launch_flush_tc_direct(const TcPlanArgs &a, const TcDirectArgs &d, c
 bool tc_make_maps_b(void *maps_out, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
                     int N, int bf, char *errbuf, size_t errlen);
 size_t tc_smem_bytes_direct(int N, int bf, int stages);
-int tc_stages_for(int N, int bf);
-size_t tc_smem_bytes(int N, int bf, int stages);
+int tc_stages_for(int N, int bf, int pair = 0);
+size_t tc_smem_bytes(int N, int bf, int stages, int pair = 0);
 size_t tc_maps_size();
 bool tc_make_maps(void *maps_out, const __nv_bfloat16 *A_hi, const __nv_bfloat16 *A_lo, int64_t M_pad,
                   int n_kb_stage, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
                   int N, int cluster, int bf, char *errbuf, size_t errlen);
 bool tc_b_boxes(int N, int cluster, int *box_rows, int *nbox);
-int tc_resident_ctas(int N, int bf, int stages, int cluster);
+int tc_resident_ctas(int N, int bf, int stages, int cluster, int pair = 0);
 
 // Tile autotuner (k_tc_tune.cu): picks energies per tile and cluster size for one stream shape.
 struct TuneShape {
