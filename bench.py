@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--tc-omega-tile", type=int, default=0)
     ap.add_argument("--tc-cluster", type=int, default=0)
     ap.add_argument("--tc-block-frames", type=int, default=0)
+    ap.add_argument("--tc-pair", type=int, default=0, choices=[0, 1, 2],
+                    help="CTA-pair MMAs (256 rows over a cluster of two SMs): 1 relayed, 2 direct stage barriers")
     ap.add_argument("--trace", action="store_true",
                     help="add the per-CTA phase breakdown of one traced contraction (tacaw_flush_trace)")
     ap.add_argument("--fast-steps", type=int, default=2,
@@ -299,7 +301,7 @@ def main():
         return ms / steps, kms / max(kn, 1), kn // max(steps, 1), launches, clocks
 
     tiling = dict(tc_accumulators=args.tc_accumulators, tc_omega_tile=args.tc_omega_tile,
-                  tc_cluster=args.tc_cluster, tc_block_frames=args.tc_block_frames,
+                  tc_cluster=args.tc_cluster, tc_block_frames=args.tc_block_frames, tc_pair=args.tc_pair,
                   frames_in_place=bool(args.in_place and args.precision == "split_bf16"))
     plan = TacawPlan([stream_config(spec)], precision=args.precision, **tiling)
     info = plan.info()
@@ -479,7 +481,8 @@ def main():
                                                           if args.precision == "split_bf16" else ""),
                            "k_stage": info["k_stage"], "omega_tile": info["omega_tile"],
                            "tc_accumulators": info["tc_accumulators"], "tc_block_frames": info["tc_block_frames"],
-                           "tc_cluster": info["tc_cluster"], "frames_in_place": bool(info["frames_in_place"]),
+                           "tc_cluster": info["tc_cluster"], "tc_pair": info["tc_pair"],
+                           "frames_in_place": bool(info["frames_in_place"]),
                            "smem_stages": info["stages"], "plan_device_GB": round(info["device_bytes"] / 1e9, 2),
                            "l2": "inputs (%.1f GB) larger than L2, no flush" % (T * frame_elems * 8 / 1e9),
                            "parallelism": f"replicas x{world}"},

@@ -145,7 +145,8 @@ typedef struct {
      * cluster of two SMs (tcgen05 CTA pair): each SM stages its own rows of A and half of the
      * tile's twiddle rows, halving the twiddle operand traffic per SM.  Applies to streams whose
      * tile is at most 256 columns, a multiple of 32 (others keep the single-CTA form); needs
-     * tc_cluster 0 or 2.  0: off.                                                          */
+     * tc_cluster 0 or 2.  2: the same, with the odd CTA's copies completing directly on the
+     * even CTA's stage barriers instead of being relayed by one of its threads.  0: off.   */
     int tc_pair;
 } tacaw_plan_desc;
 

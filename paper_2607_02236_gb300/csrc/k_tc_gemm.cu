@@ -169,6 +169,16 @@ __device__ __forceinline__ void mma2_commit_mc(uint32_t bar, uint16_t mask) {
         "h"(mask)
         : "memory");
 }
+// Copy into this CTA's shared memory whose completion is counted on a barrier of the pair's
+// even CTA (bar: shared::cluster address).
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                                 uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+        "%4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
 // shared::cluster address of the same shared-memory offset in CTA `rank` of the cluster
 __device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
     uint32_t r;
@@ -456,8 +466,9 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
-            // pair form: the even CTA's stage is full after its own copies AND the odd CTA's relay
-            mbar_init(smem_u32(&sh->full[s]), PAIR && leader ? 2u : 1u);
+            // pair form, relay: the even CTA's stage is full after its own copies AND the odd
+            // CTA's relay; direct: after the copies of both CTAs (one arrival, both byte counts)
+            mbar_init(smem_u32(&sh->full[s]), PAIR && leader && a.pair == 1 ? 2u : 1u);
             // one release per CTA of a multicast cluster; the pair's MMAs release both CTAs at once
             mbar_init(smem_u32(&sh->empty[s]), PAIR ? 1u : (uint32_t)C);
         }
@@ -503,6 +514,21 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
                 }
                 const uint32_t full = smem_u32(&sh->full[s]);
                 const uint32_t st = base_s + (uint32_t)s * stage_bytes;
+                if (PAIR && a.pair == 2) {
+                    // direct form: every copy of the pair completes on the even CTA's barrier
+                    const uint32_t fb = mapa_shared(full, 0u);
+                    if (leader) mbar_arrive_expect_tx(full, 2u * tx_bytes);
+                    tma_load_3d_pair(st, &maps.a_hi, 0, m0, kb, fb);
+                    tma_load_3d_pair(st + kABytes, &maps.a_lo, 0, m0, kb, fb);
+                    for (int b = 0; b < maps.nbox_b; ++b) {
+                        const int row = wtile * a.N + (int)crank * rows_cta + b * maps.box_b_rows;
+                        const uint32_t off = (uint32_t)(b * maps.box_b_rows) * RB;
+                        tma_load_3d_pair(st + 2 * kABytes + off, &maps.b_hi, 0, row, a.kbB0 + kb, fb);
+                        tma_load_3d_pair(st + 2 * kABytes + b_pad + off, &maps.b_lo, 0, row, a.kbB0 + kb, fb);
+                    }
+                    issued = kb + 1;
+                    continue;
+                }
                 mbar_arrive_expect_tx(full, tx_bytes);
                 tma_load_3d(st, &maps.a_hi, 0, m0, kb, full);
                 tma_load_3d(st + kABytes, &maps.a_lo, 0, m0, kb, full);
@@ -528,7 +554,13 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
                     tma_prefetch_3d(&maps.a_lo, 0, m0, kb + pf_dist);
                 }
             }
-            if (*abort_flag) {
+            if (*abort_flag && PAIR && a.pair == 2 && !leader) {
+                // this CTA's copies complete on the peer's barriers: give those in flight time
+                // to land before the CTA can exit
+                const uint64_t t0 = globaltimer();
+                while (globaltimer() - t0 < 50000ull) {
+                }
+            } else if (*abort_flag) {
                 // let every copy into this CTA's ring land before it can exit
                 const int first = issued > a.stages ? issued - a.stages : 0;
                 for (int kb = first; kb < issued; ++kb) {
@@ -548,7 +580,7 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
             }
         }
     } else if (warp == 1 && PAIR && !leader) {
-        if (lane == 0) {
+        if (lane == 0 && a.pair == 1) {
             // relay: each stage of this CTA is complete -> one arrival on the even CTA's barrier
             for (int kb = 0; kb < a.n_kb; ++kb) {
                 const int s = kb % a.stages;

@@ -390,7 +390,7 @@ tacaw_status final_flush_grouped(tacaw_plan_s *p, float *d_I, float2 *d_Psi, cud
         if (C > 4) continue;
         std::vector<int> grp;
         for (int i : todo)
-            if (p->s[i].tc_cluster == C && p->s[i].tc_pair == pr) grp.push_back(i);
+            if (p->s[i].tc_cluster == C && (p->s[i].tc_pair != 0) == (pr != 0)) grp.push_back(i);
         for (size_t g0 = 0; g0 < grp.size(); g0 += kMaxGroupStreams) {
             const size_t g1 = std::min(grp.size(), g0 + (size_t)kMaxGroupStreams);
             std::vector<TcPlanArgs> args;
@@ -655,6 +655,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         return fail(TACAW_ERR_INVALID_ARG, "tc_accumulators must be 0 (auto), 1, 2 or 3");
     if (desc->tc_cluster != 0 && desc->tc_cluster != 1 && desc->tc_cluster != 2 && desc->tc_cluster != 4)
         return fail(TACAW_ERR_INVALID_ARG, "tc_cluster must be 0 (auto), 1, 2 or 4");
+    if (desc->tc_pair < 0 || desc->tc_pair > 2) return fail(TACAW_ERR_INVALID_ARG, "tc_pair must be 0, 1 or 2");
     if (desc->tc_omega_tile < 0 || desc->tc_omega_tile % 8)
         return fail(TACAW_ERR_INVALID_ARG, "tc_omega_tile must be a multiple of 8");
     if (desc->tc_block_frames != 0 && desc->tc_block_frames != 8 && desc->tc_block_frames != 16 &&
@@ -840,7 +841,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
             const int N = 2 * s.wt;
             if (desc->tc_pair && !p->in_place && N <= 256 && N % 32 == 0 && s.M_pad / kMTile >= 2 &&
                 (desc->tc_cluster == 0 || desc->tc_cluster == 2)) {
-                s.tc_pair = 1;
+                s.tc_pair = desc->tc_pair;
                 s.tc_cluster = 2;
             }
             s.stages = tc_stages_for(N, p->bf, s.tc_pair);

@@ -249,7 +249,9 @@ struct TcPlanArgs {
     int split;                 // 1: separate TMEM accumulators for hi*hi and hi*lo + lo*hi (N <= 256)
     int n_big;                 // hi*hi accumulators (1 or 2, alternating by block parity)
     int cluster;               // CTAs sharing (multicasting) one energy tile's B rows: 1, 2 or 4
-    int pair;                  // 1: CTA-pair MMAs (M = 256 over a cluster of 2, B rows split); N <= 256
+    int pair;                  // CTA-pair MMAs (M = 256 over a cluster of 2, B rows split; N <= 256):
+                               // 1 = the odd CTA relays its stage-full events, 2 = its copies
+                               // complete directly on the even CTA's barriers; 0 = off
     int prefetch;              // staging blocks of A prefetched into L2 ahead of the current one (0: off)
     unsigned long long *trace; // null, or kTraceWords globaltimer stamps per CTA (phase boundaries)
     uint32_t *err;

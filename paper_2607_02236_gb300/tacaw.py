@@ -165,7 +165,7 @@ class TacawPlan:
     def __init__(self, streams: Sequence[StreamConfig], precision: str = "split_bf16", accum: str = "kahan",
                  hbm_budget_bytes: int = 0, k_stage: int = 0, tc_omega_tile: int = 0,
                  tc_accumulators: int = 0, tc_cluster: int = 0, tc_block_frames: int = 0, tc_prefetch: int = 0,
-                 frames_in_place: bool = False, tune: Optional[str] = None, tc_pair: bool = False):
+                 frames_in_place: bool = False, tune: Optional[str] = None, tc_pair: int = 0):
         """tune: None uses the built-in tile rule; "" autotunes at creation; a file path
         autotunes through a text cache at that path."""
         L = lib()
@@ -197,7 +197,7 @@ class TacawPlan:
                        ACCUMS[accum], int(hbm_budget_bytes), int(k_stage),
                        None if tune is None else os.fsencode(tune), int(tc_omega_tile),
                        int(tc_accumulators), int(tc_cluster), int(tc_block_frames), int(tc_prefetch),
-                       int(bool(frames_in_place)), int(bool(tc_pair)))
+                       int(bool(frames_in_place)), int(tc_pair))
         h = c_void_p()
         _check(L.tacaw_plan_create(ctypes.byref(pd), ctypes.byref(h)))
         self._h = h

@@ -196,14 +196,16 @@ def test_tensor_core_tilings(acc, cluster, wt, bf, mode):
     assert (info["tc_accumulators"], info["tc_cluster"], info["tc_block_frames"]) == (acc, cluster, bf)
 
 
-@pytest.mark.parametrize("acc,wt,bf", [(3, 0, 32), (3, 0, 16), (2, 128, 16), (1, 64, 8), (3, 48, 32), (2, 0, 8)])
-def test_cta_pair_tilings(acc, wt, bf):
+@pytest.mark.parametrize("acc,wt,bf,pair", [(3, 0, 32, 1), (3, 0, 16, 1), (2, 128, 16, 1), (1, 64, 8, 1),
+                                             (3, 48, 32, 1), (2, 0, 8, 1), (3, 0, 32, 2), (2, 128, 16, 2),
+                                             (1, 64, 8, 2), (3, 48, 32, 2)])
+def test_cta_pair_tilings(acc, wt, bf, pair):
     """CTA-pair MMAs (256 rows over a cluster of two SMs, twiddle rows split between them): 31
     row tiles (odd: the last pair has an all-padding tile), ragged rows, ragged frames."""
     spec = StreamSpec(P=3, Kx=36, Ky=36, T=168, Tc=40, n_omega=150, E_max_meV=120.0, window="hann", n_modes=6,
                       noise=1e-3, detectors=(Detector("circular", 0, 0, -1, 6.0),))
     fr = frames.frames(spec, 9, 0, spec.T)
     out, ref, e = check(spec, fr, "split_bf16", tc_accumulators=acc, tc_omega_tile=wt, tc_block_frames=bf,
-                        tc_pair=True)
+                        tc_pair=pair)
     info = out["info"]
-    assert (info["tc_accumulators"], info["tc_pair"], info["tc_cluster"], info["tc_block_frames"]) == (acc, 1, 2, bf)
+    assert (info["tc_accumulators"], info["tc_pair"], info["tc_cluster"], info["tc_block_frames"]) == (acc, pair, 2, bf)
