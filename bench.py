@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--tc-omega-tile", type=int, default=0)
     ap.add_argument("--tc-cluster", type=int, default=0)
     ap.add_argument("--tc-block-frames", type=int, default=0)
+    ap.add_argument("--tc-drain-frames", type=int, default=0,
+                    help="drained accumulator form: chunk length in frames (0: off)")
     ap.add_argument("--tc-pair", type=int, default=0, choices=[0, 1, 2],
                     help="CTA-pair MMAs (256 rows over a cluster of two SMs): 1 relayed, 2 direct stage barriers")
     ap.add_argument("--trace", action="store_true",
@@ -302,6 +304,7 @@ def main():
 
     tiling = dict(tc_accumulators=args.tc_accumulators, tc_omega_tile=args.tc_omega_tile,
                   tc_cluster=args.tc_cluster, tc_block_frames=args.tc_block_frames, tc_pair=args.tc_pair,
+                  tc_drain_frames=args.tc_drain_frames,
                   frames_in_place=bool(args.in_place and args.precision == "split_bf16"))
     plan = TacawPlan([stream_config(spec)], precision=args.precision, **tiling)
     info = plan.info()
@@ -481,7 +484,7 @@ def main():
                                                           if args.precision == "split_bf16" else ""),
                            "k_stage": info["k_stage"], "omega_tile": info["omega_tile"],
                            "tc_accumulators": info["tc_accumulators"], "tc_block_frames": info["tc_block_frames"],
-                           "tc_cluster": info["tc_cluster"], "tc_pair": info["tc_pair"],
+                           "tc_cluster": info["tc_cluster"], "tc_pair": info["tc_pair"], "tc_drain_frames": info["tc_drain_frames"],
                            "frames_in_place": bool(info["frames_in_place"]),
                            "smem_stages": info["stages"], "plan_device_GB": round(info["device_bytes"] / 1e9, 2),
                            "l2": "inputs (%.1f GB) larger than L2, no flush" % (T * frame_elems * 8 / 1e9),

@@ -148,6 +148,14 @@ typedef struct {
      * tc_cluster 0 or 2.  2: the same, with the odd CTA's copies completing directly on the
      * even CTA's stage barriers instead of being relayed by one of its threads.  0: off.   */
     int tc_pair;
+    /* Split path, staged operands: > 0 selects the drained accumulator form.  All three
+     * products of a tile go to one TMEM accumulator, double-buffered: every tc_drain_frames
+     * frames the finished buffer is added into FP32 registers (round to nearest) by the
+     * epilogue warps while the other buffer accumulates.  The tensor core's truncating FP32
+     * accumulation then spans one chunk instead of the segment, at the MMA width of a single
+     * accumulator (tiles up to 128 complex energies).  Multiple of 8; excludes tc_pair,
+     * tc_cluster > 1 and tc_accumulators > 1.  0: off.                                    */
+    int tc_drain_frames;
 } tacaw_plan_desc;
 
 typedef struct tacaw_plan_s *tacaw_plan_t;
@@ -168,6 +176,7 @@ typedef struct {
     int tc_block_frames;       /* frames per staged operand row (split path) */
     int frames_in_place;       /* pushed frames are read in place by the contraction */
     int tc_pair;               /* first stream runs CTA-pair MMAs */
+    int tc_drain_frames;       /* frames per drained accumulator chunk (0: not drained) */
     int tuned_streams;         /* streams whose tile the autotuner picked */
     int tune_candidates;       /* candidate tiles timed at creation (0: none, or all cached) */
     double tune_ms;            /* host time spent in the autotuner at creation */

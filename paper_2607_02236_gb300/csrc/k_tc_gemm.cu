@@ -71,6 +71,8 @@ struct TcShared {
     float bose[256];    // Bose factors of this CTA's energies
     double2 rowsum[kMTile];   // in-place kernel: sum over this flush of (psi - mu_hat) per row
     uint64_t sums_ready;      // in-place kernel: producers -> epilogue
+    uint64_t chunk_full[2];   // drained kernel: a chunk's accumulator buffer is complete
+    uint64_t chunk_free[2];   // drained kernel: the epilogue warps have drained it
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -422,13 +424,68 @@ __device__ __forceinline__ void tc_mma_loop(const TcPlanArgs &a, TcShared *sh, u
     if (trace) trace[3] = globaltimer();
 }
 
+
+// Drained form: per-thread FP32 running sums of up to 128 accumulator columns (one TMEM lane,
+// a contiguous column range).  Loads are warp-uniform; columns past `cols` (up to 15 of them,
+// inside the allocation) are loaded and ignored.
+constexpr int kDrainCols = 128;
+__device__ __forceinline__ void drain_add(float (&sum)[kDrainCols], uint32_t taddr, int cols) {
+#pragma unroll
+    for (int r = 0; r < kDrainCols / 16; ++r) {
+        if (r * 16 < cols) {
+            uint32_t x[16];
+            tmem_ld_x16(taddr + (uint32_t)(r * 16), x);
+            tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (r * 16 + i < cols) sum[r * 16 + i] += __uint_as_float(x[i]);
+        }
+        __syncwarp();
+    }
+}
+
+// Final epilogue of the drained form: the last chunk's accumulator plus the running sums, for
+// the thread's columns [col0, col0 + cols) (energies col0/2 ...).
+template <int KIND>
+__device__ __forceinline__ void tc_epilogue_drained(const TcPlanArgs &a, const TcShared *sh, const RowCtx &row,
+                                                    uint32_t taddr, int col0, int cols, int jbase,
+                                                    const float (&sum)[kDrainCols]) {
+#pragma unroll
+    for (int r = 0; r < kDrainCols / 16; ++r) {
+        if (r * 16 < cols) {
+            uint32_t x[16];
+            tmem_ld_x16(taddr + (uint32_t)(r * 16), x);
+            tmem_ld_wait();
+            if (row.valid) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int c = r * 16 + 2 * i;          // column of the thread's range (even)
+                    const int jl = (col0 + c) >> 1;        // energy inside the tile
+                    const int j = jbase + jl;
+                    if (c < cols && j < a.e.Nw)
+                        epi_apply<KIND>(a.e, row, j, sum[c] + __uint_as_float(x[2 * i]),
+                                        sum[c + 1] + __uint_as_float(x[2 * i + 1]), sh->W[jl], sh->bose[jl]);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Body of the staged contraction kernel.  PAIR: the CTA-pair form -- clusters of two CTAs run
 // M = 256 MMAs (tcgen05 cta_group::2) issued by the even CTA: each CTA stages its own 128 rows
 // of A and half of the tile's B rows, so each SM reads half the B operand per MMA; both CTAs
 // receive their 128 accumulator rows in their own TMEM.  The odd CTA's warp 1 relays its
 // stage-full events to the even CTA's barrier (remote arrive), so every CTA still waits only
 // on barriers in its own shared memory when it drains its copies.
-template <bool PAIR>
+//
+// DRAIN: one accumulator per tile (all three products), double-buffered in TMEM: the K range is
+// cut into chunks of a.drain_kb staging blocks that alternate between the two buffers, and
+// eight epilogue warps (two per TMEM lane quarter, each half of the columns) add every
+// finished chunk into FP32 registers (round to nearest) while the next chunk accumulates.  The
+// tensor core's truncating FP32 accumulation then runs over one chunk instead of the whole
+// segment, and the tile keeps the full width of one accumulator (up to 256 columns).
+template <bool PAIR, bool DRAIN>
 __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
     int gi = 0;
     while (gi + 1 < g.n && (int)blockIdx.x >= g.e[gi + 1].cta_begin) ++gi;
@@ -450,7 +507,7 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
     const unsigned cid = bid / (unsigned)C;
     const int wtile = (int)(cid % (unsigned)a.n_wt);
     const int m0 = ((int)(cid / (unsigned)a.n_wt) * C + (int)crank) * kMTile;
-    const int n_acc = a.split ? a.n_big + 1 : 1;
+    const int n_acc = DRAIN ? 2 : (a.split ? a.n_big + 1 : 1);
     const uint32_t ncols = tc_tmem_cols(n_acc * a.N);
     // bytes landing in this CTA's stage: its A rows plus the B rows it holds (the whole tile
     // when the cluster multicasts B, half of it in the pair form)
@@ -473,6 +530,12 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
             mbar_init(smem_u32(&sh->empty[s]), PAIR ? 1u : (uint32_t)C);
         }
         mbar_init(smem_u32(&sh->tmem_full), 1);
+        if (DRAIN) {
+            for (int b = 0; b < 2; ++b) {
+                mbar_init(smem_u32(&sh->chunk_full[b]), 1);
+                mbar_init(smem_u32(&sh->chunk_free[b]), 8);   // one arrival per epilogue warp
+            }
+        }
         sh->abort_flag = 0;
         fence_mbar_init();
     }
@@ -593,6 +656,104 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
                 mbar_arrive_remote(mapa_shared(smem_u32(&sh->full[s]), 0u));
             }
             if (trace) trace[3] = globaltimer();
+        }
+    } else if (warp == 1 && DRAIN) {
+        if (lane == 0) {
+            const uint32_t id = idesc_bf16_f32(kMTile, a.N);     // N <= 256 (host-checked)
+            const int ksteps = a.bf / 8;
+            const int cb = a.drain_kb;
+            for (int kb = 0; kb < a.n_kb; ++kb) {
+                const int c = kb / cb, buf = c & 1, kc = kb - c * cb;
+                if (kc == 0 && c >= 2) {
+                    // the buffer's previous chunk must be drained before it is overwritten
+                    if (!mbar_wait(smem_u32(&sh->chunk_free[buf]), (uint32_t)((c - 2) >> 1) & 1u, abort_flag)) {
+                        if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                }
+                const int s = kb % a.stages;
+                if (!mbar_wait(smem_u32(&sh->full[s]), (uint32_t)(kb / a.stages) & 1u, abort_flag)) {
+                    if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                if (trace && kb == 0) trace[2] = globaltimer();
+                const uint32_t st = base_s + (uint32_t)s * stage_bytes;
+                const uint64_t dAhi0 = sdesc_k(st, RB);
+                const uint64_t dAlo0 = sdesc_k(st + kABytes, RB);
+                const uint64_t dBhi0 = sdesc_k(st + 2 * kABytes, RB);
+                const uint64_t dBlo0 = sdesc_k(st + 2 * kABytes + b_pad, RB);
+                const uint32_t acc = tmem + (uint32_t)(buf * a.N);
+                for (int ks = 0; ks < ksteps; ++ks) {
+                    const uint64_t adv = (uint64_t)(2 * ks);
+                    const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;   // a chunk starts from zero
+                    mma_bf16_ss(acc, dAhi0 + adv, dBhi0 + adv, id, first);
+                    mma_bf16_ss(acc, dAhi0 + adv, dBlo0 + adv, id, 1u);
+                    mma_bf16_ss(acc, dAlo0 + adv, dBhi0 + adv, id, 1u);
+                }
+                mma_commit(smem_u32(&sh->empty[s]));
+                if (kc == cb - 1 && kb != a.n_kb - 1) mma_commit(smem_u32(&sh->chunk_full[buf]));
+            }
+            mma_commit(smem_u32(&sh->tmem_full));   // always: the last chunk, and TMEM release
+            if (trace) trace[3] = globaltimer();
+        }
+    } else if (DRAIN) {
+        // epilogue warps 2..9: TMEM lane quarter q = warp % 4, column half h
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        {
+            const int jb = wtile * a.wt;
+            for (int i = threadIdx.x - 64; i < a.wt; i += 256) {
+                const int j = jb + i;
+                sh->W[i] = j < a.e.Nw ? __ldg(a.e.Wc + j) : make_float2(0.f, 0.f);
+                sh->bose[i] = j < a.e.Nw ? __ldg(a.e.bose + j) : 0.f;
+            }
+            asm volatile("bar.sync 1, 256;" ::: "memory");   // the eight epilogue warps only
+        }
+        float sum[kDrainCols];
+#pragma unroll
+        for (int i = 0; i < kDrainCols; ++i) sum[i] = 0.f;
+        const int cols = a.wt;                       // N / 2 columns per thread
+        const int col0 = h * cols;
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
+        const int n_chunks = (a.n_kb + a.drain_kb - 1) / a.drain_kb;
+        bool ok = true;
+        for (int c = 0; c + 1 < n_chunks; ++c) {
+            if (!mbar_wait(smem_u32(&sh->chunk_full[c & 1]), (uint32_t)(c >> 1) & 1u, abort_flag)) {
+                if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
+                *abort_flag = 1;
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            drain_add(sum, lane_base + (uint32_t)((c & 1) * a.N), cols);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&sh->chunk_free[c & 1]));
+        }
+        if (ok && !mbar_wait(smem_u32(&sh->tmem_full), 0u, nullptr)) {
+            atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
+            *abort_flag = 1;
+            ok = false;
+        }
+        tc_fence_after();
+        if (trace && warp == 2 && lane == 0) trace[4] = globaltimer();
+        if (ok && !*abort_flag) {
+            const int64_t m = (int64_t)m0 + q * 32 + lane;
+            const RowCtx row = make_row(a.e, m);
+            const int jbase = wtile * a.wt;
+            const uint32_t tl = lane_base + (uint32_t)(((n_chunks - 1) & 1) * a.N);
+            switch (epi_kind(a.e)) {
+                case EPI_FINAL: tc_epilogue_drained<EPI_FINAL>(a, sh, row, tl, col0, cols, jbase, sum); break;
+                case EPI_FINAL_KAHAN: tc_epilogue_drained<EPI_FINAL_KAHAN>(a, sh, row, tl, col0, cols, jbase, sum); break;
+                case EPI_FINAL_FP64: tc_epilogue_drained<EPI_FINAL_FP64>(a, sh, row, tl, col0, cols, jbase, sum); break;
+                case EPI_STORE_KAHAN: tc_epilogue_drained<EPI_STORE_KAHAN>(a, sh, row, tl, col0, cols, jbase, sum); break;
+                case EPI_STORE_FP64: tc_epilogue_drained<EPI_STORE_FP64>(a, sh, row, tl, col0, cols, jbase, sum); break;
+                case EPI_ADD_KAHAN: tc_epilogue_drained<EPI_ADD_KAHAN>(a, sh, row, tl, col0, cols, jbase, sum); break;
+                default: tc_epilogue_drained<EPI_ADD_FP64>(a, sh, row, tl, col0, cols, jbase, sum); break;
+            }
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -721,9 +882,14 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
     if (trace && threadIdx.x == 0) trace[6] = globaltimer();
 }
 
-__global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant__ TcGroup g) { flush_tc_body<false>(g); }
+__global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant__ TcGroup g) {
+    flush_tc_body<false, false>(g);
+}
 __global__ void __launch_bounds__(192, 1) flush_tc_pair_kernel(const __grid_constant__ TcGroup g) {
-    flush_tc_body<true>(g);
+    flush_tc_body<true, false>(g);
+}
+__global__ void __maxnreg__(200) flush_tc_drain_kernel(const __grid_constant__ TcGroup g) {
+    flush_tc_body<false, true>(g);
 }
 
 // --------------------------------------------------------------------------------------
@@ -1059,9 +1225,9 @@ cudaError_t launch_flush_tc_direct(const TcPlanArgs &a, const TcDirectArgs &d, c
 }
 
 // Co-resident CTAs of the contraction kernel for a cluster size (0 on error).
-int tc_resident_ctas(int N, int bf, int stages, int cluster, int pair) {
+int tc_resident_ctas(int N, int bf, int stages, int cluster, int pair, int drain) {
     const size_t smem = tc_smem_bytes(N, bf, stages, pair);
-    auto kern = pair ? flush_tc_pair_kernel : flush_tc_kernel;
+    auto kern = drain ? flush_tc_drain_kernel : (pair ? flush_tc_pair_kernel : flush_tc_kernel);
     if (pair) cluster = 2;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
@@ -1069,7 +1235,7 @@ int tc_resident_ctas(int N, int bf, int stages, int cluster, int pair) {
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cluster * 1024, 1, 1);
-    cfg.blockDim = dim3(192, 1, 1);
+    cfg.blockDim = dim3(drain ? 320 : 192, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1097,12 +1263,15 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *map
     if (!g) return cudaErrorMemoryAllocation;
     const int C = args[0].cluster;
     const int pair = args[0].pair;
+    const bool drain = args[0].drain_kb > 0;
     size_t smem = 0;
     int64_t total = 0;
     for (int i = 0; i < n; ++i) {
-        // the pair form needs clusters of 2 and tiles of at most 256 columns (one MMA each)
+        // the pair form needs clusters of 2 and tiles of at most 256 columns (one MMA each);
+        // the drained form one CTA per tile and two buffers of at most 256 columns
         if (args[i].cluster != C || args[i].bf != args[0].bf || args[i].pair != pair ||
-            (pair && (C != 2 || args[i].N > 256 || args[i].N % 32))) {
+            (args[i].drain_kb > 0) != drain || (pair && (C != 2 || args[i].N > 256 || args[i].N % 32)) ||
+            (drain && (C != 1 || pair || args[i].N > 256 || args[i].wt > 128))) {
             delete g;
             return cudaErrorInvalidValue;
         }
@@ -1120,12 +1289,12 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *map
         delete g;
         return cudaErrorInvalidConfiguration;
     }
-    auto kern = pair ? flush_tc_pair_kernel : flush_tc_kernel;
+    auto kern = drain ? flush_tc_drain_kernel : (pair ? flush_tc_pair_kernel : flush_tc_kernel);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)total, 1, 1);
-        cfg.blockDim = dim3(192, 1, 1);
+        cfg.blockDim = dim3(drain ? 320 : 192, 1, 1);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];

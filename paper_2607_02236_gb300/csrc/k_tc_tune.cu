@@ -54,8 +54,9 @@ std::string shape_key(const TuneShape &s) {
     cudaDeviceGetAttribute(&mnr, cudaDevAttrComputeCapabilityMinor, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     char b[320];
-    snprintf(b, sizeof(b), "tacaw-tune-v1 sm%d%dx%d acc=%d bf=%d M=%lld Nw=%d T=%d ring=%d multi=%d wt=%d c=%d", maj,
-             mnr, sms, s.n_acc, s.bf, (long long)s.M, s.Nw, s.T, s.ring, s.multi ? 1 : 0, s.fixed_wt, s.fixed_cluster);
+    snprintf(b, sizeof(b), "tacaw-tune-v1 sm%d%dx%d acc=%d drain=%d bf=%d M=%lld Nw=%d T=%d ring=%d multi=%d wt=%d c=%d",
+             maj, mnr, sms, s.n_acc, s.drain_kb, s.bf, (long long)s.M, s.Nw, s.T, s.ring, s.multi ? 1 : 0, s.fixed_wt,
+             s.fixed_cluster);
     return b;
 }
 
@@ -138,9 +139,10 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
         const int n_wt = (sh.Nw + w - 1) / w;
         for (int C : {1, 2, 4}) {
             if (sh.fixed_cluster && C != sh.fixed_cluster) continue;
+            if (sh.drain_kb && C != 1) continue;
             int br, nb;
             if (!tc_b_boxes(N, C, &br, &nb) || (C > 1 && n_mt < 2 * C)) continue;
-            const int R = tc_resident_ctas(N, sh.bf, stages, C);
+            const int R = tc_resident_ctas(N, sh.bf, stages, C, 0, sh.drain_kb > 0);
             if (R <= 0) continue;
             Cand c{w, n_wt, C, stages, R, 0};
             // one wave: at most R CTAs, whole clusters, no more M tiles than the stream has
@@ -225,6 +227,7 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
         a.split = sh.n_acc > 1 ? 1 : 0;
         a.n_big = sh.n_acc == 3 ? 2 : 1;
         a.cluster = c.C;
+        a.drain_kb = sh.drain_kb;
         a.err = d_err;
         double t[2] = {0.0, 0.0};
         const int kbs[2] = {kb1, kb2};

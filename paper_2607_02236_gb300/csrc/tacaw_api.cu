@@ -95,6 +95,7 @@ struct tacaw_plan_s {
     int prec = 0, accum = 0, k_stage = 0;
     int stages = 0;
     int tc_acc = 3;
+    int drain_kb = 0;          // drained form: staging blocks per accumulator chunk (0: off)
     int bf = 8;                // frames per staged operand row (split path)
     int tc_prefetch = 0;       // L2 prefetch distance of operand A in staging blocks
     bool in_place = false;     // the contraction reads pushed frames directly
@@ -265,6 +266,7 @@ TcPlanArgs tc_args(tacaw_plan_s *p, const Stream &s, const EpiArgs &e) {
     a.stages = s.stages;
     a.split = p->tc_acc > 1 ? 1 : 0;
     a.n_big = p->tc_acc == 3 ? 2 : 1;
+    a.drain_kb = p->in_place ? 0 : p->drain_kb;
     a.cluster = p->in_place ? 1 : s.tc_cluster;
     a.pair = p->in_place ? 0 : s.tc_pair;
     a.prefetch = p->in_place ? 0 : p->tc_prefetch;
@@ -656,6 +658,11 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     if (desc->tc_cluster != 0 && desc->tc_cluster != 1 && desc->tc_cluster != 2 && desc->tc_cluster != 4)
         return fail(TACAW_ERR_INVALID_ARG, "tc_cluster must be 0 (auto), 1, 2 or 4");
     if (desc->tc_pair < 0 || desc->tc_pair > 2) return fail(TACAW_ERR_INVALID_ARG, "tc_pair must be 0, 1 or 2");
+    if (desc->tc_drain_frames < 0 || desc->tc_drain_frames % 8)
+        return fail(TACAW_ERR_INVALID_ARG, "tc_drain_frames must be a non-negative multiple of 8");
+    if (desc->tc_drain_frames && (desc->tc_pair || desc->tc_cluster > 1 || desc->tc_accumulators > 1))
+        return fail(TACAW_ERR_INVALID_ARG, "tc_drain_frames runs one accumulator on single CTAs "
+                    "(tc_pair 0, tc_cluster 0/1, tc_accumulators 0/1)");
     if (desc->tc_omega_tile < 0 || desc->tc_omega_tile % 8)
         return fail(TACAW_ERR_INVALID_ARG, "tc_omega_tile must be a multiple of 8");
     if (desc->tc_block_frames != 0 && desc->tc_block_frames != 8 && desc->tc_block_frames != 16 &&
@@ -666,6 +673,10 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     tacaw_plan_s *p = new (std::nothrow) tacaw_plan_s();
     if (!p) return fail(TACAW_ERR_OOM, "host allocation failed");
     p->tc_acc = desc->tc_accumulators ? desc->tc_accumulators : 3;
+    const bool drained = desc->tc_drain_frames > 0 && desc->precision == TACAW_PREC_SPLIT_BF16 && !desc->frames_in_place;
+    if (drained) p->tc_acc = 1;
+    // TMEM columns per tile: accumulators side by side (the drained form holds two buffers)
+    const int tile_acc = drained ? 2 : p->tc_acc;
     if (desc->frames_in_place && desc->precision != TACAW_PREC_SPLIT_BF16) {
         delete p;
         return fail(TACAW_ERR_UNSUPPORTED, "frames_in_place needs the split-BF16 path");
@@ -707,7 +718,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         s.T_pad = (int)round_up(s.T, p->prec == TACAW_PREC_SPLIT_BF16 ? p->bf : 8);
         s.n_kb_T = s.T_pad / (p->prec == TACAW_PREC_SPLIT_BF16 ? p->bf : 8);
         s.Nw = s.d.n_omega;
-        choose_omega_tile(s, p->tc_acc, desc->tc_omega_tile);
+        choose_omega_tile(s, tile_acc, desc->tc_omega_tile);
         if (p->prec == TACAW_PREC_FP32) s.Nw_pad = (int)round_up(s.Nw, 64);
         T_pad_max = std::max(T_pad_max, s.T_pad);
         p->s.push_back(s);
@@ -728,6 +739,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
             while (p->bf > 8 && tc_stages_for(max_cols(), p->bf) < 2) p->bf /= 2;
         for (auto &s : p->s) s.n_kb_T = s.T_pad / p->bf;
         p->tc_prefetch = desc->tc_prefetch > 0 ? desc->tc_prefetch : 0;
+        if (drained) p->drain_kb = std::max(1, desc->tc_drain_frames / p->bf);
         // autotuner: time the candidate tiles of every stream shape (staged operands only)
         if (desc->tune_cache_path && !p->in_place) {
             const auto t0 = std::chrono::steady_clock::now();
@@ -741,7 +753,8 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
                 sh.ring = desc->k_stage ? std::min(desc->k_stage, s.T_pad) : s.T_pad;
                 sh.bf = p->bf;
                 sh.n_acc = p->tc_acc;
-                sh.wt_max = omega_tile_max(p->tc_acc);
+                sh.wt_max = omega_tile_max(tile_acc);
+                sh.drain_kb = drained ? std::max(1, desc->tc_drain_frames / p->bf) : 0;
                 sh.fixed_wt = desc->tc_omega_tile ? s.wt : 0;
                 sh.fixed_cluster = desc->tc_cluster;
                 sh.multi = desc->n_streams > 1;
@@ -852,6 +865,10 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         p->stages = p->s[0].stages;
         for (auto &s : p->s) {
             if (s.tuned || s.tc_pair) continue;
+            if (drained) {
+                s.tc_cluster = 1;
+                continue;
+            }
             const int N = 2 * s.wt;
             int br, nb;
             const int64_t n_mt = s.M_pad / kMTile;
@@ -1018,6 +1035,7 @@ tacaw_status tacaw_plan_get_info(tacaw_plan_t p, tacaw_plan_info *info) {
     info->tune_ms = p->tune_ms;
     info->frames_in_place = p->in_place ? 1 : 0;
     info->tc_pair = (p->prec == TACAW_PREC_SPLIT_BF16 && !p->s.empty()) ? p->s[0].tc_pair : 0;
+    info->tc_drain_frames = p->drain_kb * p->bf;
     return TACAW_OK;
 }
 

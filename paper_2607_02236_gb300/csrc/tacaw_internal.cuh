@@ -252,6 +252,8 @@ struct TcPlanArgs {
     int pair;                  // CTA-pair MMAs (M = 256 over a cluster of 2, B rows split; N <= 256):
                                // 1 = the odd CTA relays its stage-full events, 2 = its copies
                                // complete directly on the even CTA's barriers; 0 = off
+    int drain_kb;              // > 0: one double-buffered accumulator drained into FP32
+                               // registers every drain_kb staging blocks (N <= 256, wt <= 128)
     int prefetch;              // staging blocks of A prefetched into L2 ahead of the current one (0: off)
     unsigned long long *trace; // null, or kTraceWords globaltimer stamps per CTA (phase boundaries)
     uint32_t *err;
@@ -288,7 +290,7 @@ bool tc_make_maps(void *maps_out, const __nv_bfloat16 *A_hi, const __nv_bfloat16
                   int n_kb_stage, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
                   int N, int cluster, int bf, char *errbuf, size_t errlen);
 bool tc_b_boxes(int N, int cluster, int *box_rows, int *nbox);
-int tc_resident_ctas(int N, int bf, int stages, int cluster, int pair = 0);
+int tc_resident_ctas(int N, int bf, int stages, int cluster, int pair = 0, int drain = 0);
 
 // Tile autotuner (k_tc_tune.cu): picks energies per tile and cluster size for one stream shape.
 struct TuneShape {
@@ -297,6 +299,7 @@ struct TuneShape {
     int bf, n_acc, wt_max;     // block frames, TMEM accumulators, widest tile allowed
     int fixed_wt, fixed_cluster;   // 0: tuned
     bool multi;                // several streams share the final launch
+    int drain_kb;              // drained form (single CTAs, one double-buffered accumulator)
 };
 struct TuneCand {
     int wt, cluster;
