@@ -733,7 +733,8 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&sh->chunk_free[c & 1]));
         }
-        if (ok && !mbar_wait(smem_u32(&sh->tmem_full), 0u, nullptr)) {
+        // always wait (bounded) for the last commit: no MMA may still write TMEM at release
+        if (!mbar_wait(smem_u32(&sh->tmem_full), 0u, nullptr)) {
             atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
             *abort_flag = 1;
             ok = false;
