@@ -889,7 +889,9 @@ __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant_
 __global__ void __launch_bounds__(192, 1) flush_tc_pair_kernel(const __grid_constant__ TcGroup g) {
     flush_tc_body<true, false>(g);
 }
-__global__ void __maxnreg__(200) flush_tc_drain_kernel(const __grid_constant__ TcGroup g) {
+// 320 threads: warps are spread over the SM's four register files, three on two of them, so a
+// thread may hold at most 16384 / (3 * 32) = 170 registers (168 allocatable).
+__global__ void __maxnreg__(168) flush_tc_drain_kernel(const __grid_constant__ TcGroup g) {
     flush_tc_body<false, true>(g);
 }
 
