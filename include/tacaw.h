@@ -125,7 +125,9 @@ typedef struct {
     /* Tensor-core tiling (split path); 0 selects automatically.
      *   tc_omega_tile     complex energies per tile (multiple of 8)
      *   tc_accumulators   TMEM accumulators per tile: 1 (all products in one), 2 (hi*hi | small
-     *                     terms), 3 (hi*hi alternating over two | small terms; default)
+     *                     terms), 3 (hi*hi alternating over two | small terms; the in-place
+     *                     and CTA-pair default).  Left at 0 on staged operands, the drained
+     *                     one-accumulator form below is used.
      *   tc_cluster        CTAs per cluster sharing the twiddle rows by TMA multicast: 1, 2, 4
      *   tc_block_frames   frames per staged operand row: 8, 16 or 32 (32-, 64-, 128-byte rows);
      *                     k_stage must be a multiple of it
@@ -154,7 +156,8 @@ typedef struct {
      * epilogue warps while the other buffer accumulates.  The tensor core's truncating FP32
      * accumulation then spans one chunk instead of the segment, at the MMA width of a single
      * accumulator (tiles up to 128 complex energies).  Multiple of 8; excludes tc_pair,
-     * tc_cluster > 1 and tc_accumulators > 1.  0: off.                                    */
+     * tc_cluster > 1 and tc_accumulators > 1.  0: the default -- 256 frames when
+     * tc_accumulators, tc_pair and tc_cluster (> 1) are all left unset, otherwise off.     */
     int tc_drain_frames;
 } tacaw_plan_desc;
 

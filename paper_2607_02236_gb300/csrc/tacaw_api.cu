@@ -673,7 +673,12 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     tacaw_plan_s *p = new (std::nothrow) tacaw_plan_s();
     if (!p) return fail(TACAW_ERR_OOM, "host allocation failed");
     p->tc_acc = desc->tc_accumulators ? desc->tc_accumulators : 3;
-    const bool drained = desc->tc_drain_frames > 0 && desc->precision == TACAW_PREC_SPLIT_BF16 && !desc->frames_in_place;
+    // default accumulation of the staged split path: the drained form, chunks of 256 frames
+    // (faster and more accurate than three side-by-side accumulators in measurements)
+    const int drain_frames =
+        desc->tc_drain_frames ? desc->tc_drain_frames
+                              : (desc->tc_accumulators == 0 && !desc->tc_pair && desc->tc_cluster <= 1 ? 256 : 0);
+    const bool drained = drain_frames > 0 && desc->precision == TACAW_PREC_SPLIT_BF16 && !desc->frames_in_place;
     if (drained) p->tc_acc = 1;
     // TMEM columns per tile: accumulators side by side (the drained form holds two buffers)
     const int tile_acc = drained ? 2 : p->tc_acc;
@@ -739,7 +744,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
             while (p->bf > 8 && tc_stages_for(max_cols(), p->bf) < 2) p->bf /= 2;
         for (auto &s : p->s) s.n_kb_T = s.T_pad / p->bf;
         p->tc_prefetch = desc->tc_prefetch > 0 ? desc->tc_prefetch : 0;
-        if (drained) p->drain_kb = std::max(1, desc->tc_drain_frames / p->bf);
+        if (drained) p->drain_kb = std::max(1, drain_frames / p->bf);
         // autotuner: time the candidate tiles of every stream shape (staged operands only)
         if (desc->tune_cache_path && !p->in_place) {
             const auto t0 = std::chrono::steady_clock::now();
@@ -754,7 +759,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
                 sh.bf = p->bf;
                 sh.n_acc = p->tc_acc;
                 sh.wt_max = omega_tile_max(tile_acc);
-                sh.drain_kb = drained ? std::max(1, desc->tc_drain_frames / p->bf) : 0;
+                sh.drain_kb = drained ? std::max(1, drain_frames / p->bf) : 0;
                 sh.fixed_wt = desc->tc_omega_tile ? s.wt : 0;
                 sh.fixed_cluster = desc->tc_cluster;
                 sh.multi = desc->n_streams > 1;
