@@ -444,7 +444,14 @@ def main():
         achieved = cmac_launch * 24 / (k_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         src = os.path.join(ROOT, "paper_2607_02236_gb300", "csrc", "k_tc_gemm.cu")
-        kname = "flush_tc_direct_kernel" if info["frames_in_place"] else "flush_tc_kernel"
+        if info["frames_in_place"]:
+            kname = "flush_tc_direct_kernel"
+        elif info["tc_drain_frames"]:
+            kname = "flush_tc_drain_kernel"
+        elif info["tc_pair"]:
+            kname = "flush_tc_pair_kernel"
+        else:
+            kname = "flush_tc_kernel"
         tr = KERNEL_TRAFFIC.get((file_hash(src), kname))
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": (tr * cmac_launch if tr else None),

@@ -155,7 +155,7 @@ typedef struct {
      * frames the finished buffer is added into FP32 registers (round to nearest) by the
      * epilogue warps while the other buffer accumulates.  The tensor core's truncating FP32
      * accumulation then spans one chunk instead of the segment, at the MMA width of a single
-     * accumulator (tiles up to 128 complex energies).  Multiple of 8; excludes tc_pair,
+     * accumulator (tiles up to 112 complex energies).  Multiple of 8; excludes tc_pair,
      * tc_cluster > 1 and tc_accumulators > 1.  0: the default -- 256 frames when
      * tc_accumulators, tc_pair and tc_cluster (> 1) are all left unset, otherwise off.     */
     int tc_drain_frames;

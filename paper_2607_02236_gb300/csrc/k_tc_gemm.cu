@@ -55,6 +55,8 @@ struct TcGroupEntry {
 struct TcGroup {
     TcGroupEntry e[kMaxGroupStreams];
     int n;
+    int stages, n_max;         // drained kernel: ring stages and ring/TMEM width (widest tile)
+    int64_t tiles;             // drained kernel: tiles of all entries
 };
 
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s per wait
@@ -425,10 +427,11 @@ __device__ __forceinline__ void tc_mma_loop(const TcPlanArgs &a, TcShared *sh, u
 }
 
 
-// Drained form: per-thread FP32 running sums of up to 128 accumulator columns (one TMEM lane,
-// a contiguous column range).  Loads are warp-uniform; columns past `cols` (up to 15 of them,
-// inside the allocation) are loaded and ignored.
-constexpr int kDrainCols = 128;
+// Drained form: per-thread FP32 running sums of up to kDrainCols accumulator columns (one TMEM
+// lane, a contiguous column range: tiles of at most 112 complex energies).  Loads are
+// warp-uniform; columns past `cols` (up to 15 of them, inside the allocation) are loaded and
+// ignored.
+constexpr int kDrainCols = 112;
 __device__ __forceinline__ void drain_add(float (&sum)[kDrainCols], uint32_t taddr, int cols) {
 #pragma unroll
     for (int r = 0; r < kDrainCols / 16; ++r) {
@@ -447,8 +450,8 @@ __device__ __forceinline__ void drain_add(float (&sum)[kDrainCols], uint32_t tad
 // Final epilogue of the drained form: the last chunk's accumulator plus the running sums, for
 // the thread's columns [col0, col0 + cols) (energies col0/2 ...).
 template <int KIND>
-__device__ __forceinline__ void tc_epilogue_drained(const TcPlanArgs &a, const TcShared *sh, const RowCtx &row,
-                                                    uint32_t taddr, int col0, int cols, int jbase,
+__device__ __forceinline__ void tc_epilogue_drained(const TcPlanArgs &a, const RowCtx &row, uint32_t taddr,
+                                                    int col0, int cols, int jbase,
                                                     const float (&sum)[kDrainCols]) {
 #pragma unroll
     for (int r = 0; r < kDrainCols / 16; ++r) {
@@ -460,11 +463,12 @@ __device__ __forceinline__ void tc_epilogue_drained(const TcPlanArgs &a, const T
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int c = r * 16 + 2 * i;          // column of the thread's range (even)
-                    const int jl = (col0 + c) >> 1;        // energy inside the tile
-                    const int j = jbase + jl;
+                    const int j = jbase + ((col0 + c) >> 1);
+                    // W(E_j), B(E_j): the same address across the warp (broadcast loads)
                     if (c < cols && j < a.e.Nw)
                         epi_apply<KIND>(a.e, row, j, sum[c] + __uint_as_float(x[2 * i]),
-                                        sum[c + 1] + __uint_as_float(x[2 * i + 1]), sh->W[jl], sh->bose[jl]);
+                                        sum[c + 1] + __uint_as_float(x[2 * i + 1]), __ldg(a.e.Wc + j),
+                                        __ldg(a.e.bose + j));
                 }
             }
         }
@@ -478,14 +482,7 @@ __device__ __forceinline__ void tc_epilogue_drained(const TcPlanArgs &a, const T
 // receive their 128 accumulator rows in their own TMEM.  The odd CTA's warp 1 relays its
 // stage-full events to the even CTA's barrier (remote arrive), so every CTA still waits only
 // on barriers in its own shared memory when it drains its copies.
-//
-// DRAIN: one accumulator per tile (all three products), double-buffered in TMEM: the K range is
-// cut into chunks of a.drain_kb staging blocks that alternate between the two buffers, and
-// eight epilogue warps (two per TMEM lane quarter, each half of the columns) add every
-// finished chunk into FP32 registers (round to nearest) while the next chunk accumulates.  The
-// tensor core's truncating FP32 accumulation then runs over one chunk instead of the whole
-// segment, and the tile keeps the full width of one accumulator (up to 256 columns).
-template <bool PAIR, bool DRAIN>
+template <bool PAIR>
 __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
     int gi = 0;
     while (gi + 1 < g.n && (int)blockIdx.x >= g.e[gi + 1].cta_begin) ++gi;
@@ -507,7 +504,7 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
     const unsigned cid = bid / (unsigned)C;
     const int wtile = (int)(cid % (unsigned)a.n_wt);
     const int m0 = ((int)(cid / (unsigned)a.n_wt) * C + (int)crank) * kMTile;
-    const int n_acc = DRAIN ? 2 : (a.split ? a.n_big + 1 : 1);
+    const int n_acc = a.split ? a.n_big + 1 : 1;
     const uint32_t ncols = tc_tmem_cols(n_acc * a.N);
     // bytes landing in this CTA's stage: its A rows plus the B rows it holds (the whole tile
     // when the cluster multicasts B, half of it in the pair form)
@@ -530,12 +527,6 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
             mbar_init(smem_u32(&sh->empty[s]), PAIR ? 1u : (uint32_t)C);
         }
         mbar_init(smem_u32(&sh->tmem_full), 1);
-        if (DRAIN) {
-            for (int b = 0; b < 2; ++b) {
-                mbar_init(smem_u32(&sh->chunk_full[b]), 1);
-                mbar_init(smem_u32(&sh->chunk_free[b]), 8);   // one arrival per epilogue warp
-            }
-        }
         sh->abort_flag = 0;
         fence_mbar_init();
     }
@@ -656,105 +647,6 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
                 mbar_arrive_remote(mapa_shared(smem_u32(&sh->full[s]), 0u));
             }
             if (trace) trace[3] = globaltimer();
-        }
-    } else if (warp == 1 && DRAIN) {
-        if (lane == 0) {
-            const uint32_t id = idesc_bf16_f32(kMTile, a.N);     // N <= 256 (host-checked)
-            const int ksteps = a.bf / 8;
-            const int cb = a.drain_kb;
-            for (int kb = 0; kb < a.n_kb; ++kb) {
-                const int c = kb / cb, buf = c & 1, kc = kb - c * cb;
-                if (kc == 0 && c >= 2) {
-                    // the buffer's previous chunk must be drained before it is overwritten
-                    if (!mbar_wait(smem_u32(&sh->chunk_free[buf]), (uint32_t)((c - 2) >> 1) & 1u, abort_flag)) {
-                        if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
-                        *abort_flag = 1;
-                        break;
-                    }
-                    tc_fence_after();
-                }
-                const int s = kb % a.stages;
-                if (!mbar_wait(smem_u32(&sh->full[s]), (uint32_t)(kb / a.stages) & 1u, abort_flag)) {
-                    if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
-                    *abort_flag = 1;
-                    break;
-                }
-                tc_fence_after();
-                if (trace && kb == 0) trace[2] = globaltimer();
-                const uint32_t st = base_s + (uint32_t)s * stage_bytes;
-                const uint64_t dAhi0 = sdesc_k(st, RB);
-                const uint64_t dAlo0 = sdesc_k(st + kABytes, RB);
-                const uint64_t dBhi0 = sdesc_k(st + 2 * kABytes, RB);
-                const uint64_t dBlo0 = sdesc_k(st + 2 * kABytes + b_pad, RB);
-                const uint32_t acc = tmem + (uint32_t)(buf * a.N);
-                for (int ks = 0; ks < ksteps; ++ks) {
-                    const uint64_t adv = (uint64_t)(2 * ks);
-                    const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;   // a chunk starts from zero
-                    mma_bf16_ss(acc, dAhi0 + adv, dBhi0 + adv, id, first);
-                    mma_bf16_ss(acc, dAhi0 + adv, dBlo0 + adv, id, 1u);
-                    mma_bf16_ss(acc, dAlo0 + adv, dBhi0 + adv, id, 1u);
-                }
-                mma_commit(smem_u32(&sh->empty[s]));
-                if (kc == cb - 1 && kb != a.n_kb - 1) mma_commit(smem_u32(&sh->chunk_full[buf]));
-            }
-            mma_commit(smem_u32(&sh->tmem_full));   // always: the last chunk, and TMEM release
-            if (trace) trace[3] = globaltimer();
-        }
-    } else if (DRAIN) {
-        // epilogue warps 2..9: TMEM lane quarter q = warp % 4, column half h
-        const int q = warp & 3, h = (warp - 2) >> 2;
-        {
-            const int jb = wtile * a.wt;
-            for (int i = threadIdx.x - 64; i < a.wt; i += 256) {
-                const int j = jb + i;
-                sh->W[i] = j < a.e.Nw ? __ldg(a.e.Wc + j) : make_float2(0.f, 0.f);
-                sh->bose[i] = j < a.e.Nw ? __ldg(a.e.bose + j) : 0.f;
-            }
-            asm volatile("bar.sync 1, 256;" ::: "memory");   // the eight epilogue warps only
-        }
-        float sum[kDrainCols];
-#pragma unroll
-        for (int i = 0; i < kDrainCols; ++i) sum[i] = 0.f;
-        const int cols = a.wt;                       // N / 2 columns per thread
-        const int col0 = h * cols;
-        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
-        const int n_chunks = (a.n_kb + a.drain_kb - 1) / a.drain_kb;
-        bool ok = true;
-        for (int c = 0; c + 1 < n_chunks; ++c) {
-            if (!mbar_wait(smem_u32(&sh->chunk_full[c & 1]), (uint32_t)(c >> 1) & 1u, abort_flag)) {
-                if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
-                *abort_flag = 1;
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            drain_add(sum, lane_base + (uint32_t)((c & 1) * a.N), cols);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&sh->chunk_free[c & 1]));
-        }
-        // always wait (bounded) for the last commit: no MMA may still write TMEM at release
-        if (!mbar_wait(smem_u32(&sh->tmem_full), 0u, nullptr)) {
-            atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
-            *abort_flag = 1;
-            ok = false;
-        }
-        tc_fence_after();
-        if (trace && warp == 2 && lane == 0) trace[4] = globaltimer();
-        if (ok && !*abort_flag) {
-            const int64_t m = (int64_t)m0 + q * 32 + lane;
-            const RowCtx row = make_row(a.e, m);
-            const int jbase = wtile * a.wt;
-            const uint32_t tl = lane_base + (uint32_t)(((n_chunks - 1) & 1) * a.N);
-            switch (epi_kind(a.e)) {
-                case EPI_FINAL: tc_epilogue_drained<EPI_FINAL>(a, sh, row, tl, col0, cols, jbase, sum); break;
-                case EPI_FINAL_KAHAN: tc_epilogue_drained<EPI_FINAL_KAHAN>(a, sh, row, tl, col0, cols, jbase, sum); break;
-                case EPI_FINAL_FP64: tc_epilogue_drained<EPI_FINAL_FP64>(a, sh, row, tl, col0, cols, jbase, sum); break;
-                case EPI_STORE_KAHAN: tc_epilogue_drained<EPI_STORE_KAHAN>(a, sh, row, tl, col0, cols, jbase, sum); break;
-                case EPI_STORE_FP64: tc_epilogue_drained<EPI_STORE_FP64>(a, sh, row, tl, col0, cols, jbase, sum); break;
-                case EPI_ADD_KAHAN: tc_epilogue_drained<EPI_ADD_KAHAN>(a, sh, row, tl, col0, cols, jbase, sum); break;
-                default: tc_epilogue_drained<EPI_ADD_FP64>(a, sh, row, tl, col0, cols, jbase, sum); break;
-            }
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -884,15 +776,236 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
 }
 
 __global__ void __launch_bounds__(192, 1) flush_tc_kernel(const __grid_constant__ TcGroup g) {
-    flush_tc_body<false, false>(g);
+    flush_tc_body<false>(g);
 }
 __global__ void __launch_bounds__(192, 1) flush_tc_pair_kernel(const __grid_constant__ TcGroup g) {
-    flush_tc_body<true, false>(g);
+    flush_tc_body<true>(g);
 }
+
+// --------------------------------------------------------------------------------------
+// Drained form, persistent: one CTA per SM walks the tiles of all streams of the group
+// (tile t of the concatenated tile lists, t = blockIdx.x, blockIdx.x + gridDim.x, ...).
+//
+// All three products of a tile go to one TMEM accumulator, double-buffered: the tile's K range
+// is cut into chunks of drain_kb staging blocks that alternate between the two buffers (a
+// buffer parity that runs on across tiles), and eight epilogue warps (two per TMEM lane
+// quarter, each half of the columns) add every finished chunk into FP32 registers (round to
+// nearest) while the next chunk accumulates; the last chunk of a tile goes, with the sums,
+// through the flush epilogue while the next tile's first chunk accumulates.  The tensor
+// core's truncating FP32 accumulation thus spans one chunk instead of the segment, tiles keep
+// the full width of one accumulator (up to 256 columns), and neither the operand fill nor the
+// epilogue of a tile is exposed.
+//
+//   warp 0     TMA producer over the ring (a stage counter running across tiles)
+//   warp 1     TMEM allocation and MMA issue (one thread); commits release stages and mark
+//              finished chunks
+//   warps 2-9  drains and epilogues
+// The shared-memory ring and the two TMEM buffers are laid out for the widest tile of the group.
 // 320 threads: warps are spread over the SM's four register files, three on two of them, so a
 // thread may hold at most 16384 / (3 * 32) = 170 registers (168 allocatable).
+__device__ __forceinline__ int group_entry(const TcGroup &g, int64_t tile) {
+    int gi = 0;
+    while (gi + 1 < g.n && tile >= (int64_t)g.e[gi + 1].cta_begin) ++gi;
+    return gi;
+}
+
 __global__ void __maxnreg__(168) flush_tc_drain_kernel(const __grid_constant__ TcGroup g) {
-    flush_tc_body<false, true>(g);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int bf = g.e[0].args.bf, stages = g.stages, n_max = g.n_max;
+    const uint32_t RB = 4u * (uint32_t)bf;
+    const uint32_t kABytes = tc_a_bytes(bf);
+    const uint32_t b_pad = tc_b_bytes_padded(n_max, bf);
+    const uint32_t stage_bytes = tc_stage_bytes(n_max, bf);
+    TcShared *sh = reinterpret_cast<TcShared *>(base + (size_t)stages * stage_bytes);
+    const uint32_t base_s = smem_u32(base);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t ncols = tc_tmem_cols(2 * n_max);
+    const int64_t n_tiles = g.tiles;
+    uint32_t *err = g.e[0].args.err;
+    unsigned long long *trace = g.e[0].args.trace ? g.e[0].args.trace + (size_t)blockIdx.x * kTraceWords : nullptr;
+    if (trace && threadIdx.x == 0) {
+        trace[0] = globaltimer();
+        trace[7] = smid();
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(smem_u32(&sh->full[s]), 1);
+            mbar_init(smem_u32(&sh->empty[s]), 1);
+        }
+        mbar_init(smem_u32(&sh->tmem_full), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&sh->chunk_full[b]), 1);
+            mbar_init(smem_u32(&sh->chunk_free[b]), 8);   // one arrival per epilogue warp
+        }
+        sh->abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(&sh->tmem_addr), ncols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_addr;
+    volatile int *abort_flag = &sh->abort_flag;
+    if (trace && threadIdx.x == 0) trace[1] = globaltimer();
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int64_t q = 0;                            // stages issued by this CTA
+            for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
+                const int gi = group_entry(g, t);
+                const TcGroupEntry &en = g.e[gi];
+                const int64_t lt = t - en.cta_begin;
+                const int wtile = (int)(lt % en.args.n_wt);
+                const int m0 = (int)(lt / en.args.n_wt) * kMTile;
+                const int N = en.args.N;
+                const uint32_t tx_bytes = 2u * kABytes + 2u * (uint32_t)N * RB;
+                for (int kb = 0; kb < en.args.n_kb; ++kb, ++q) {
+                    const int s = (int)(q % stages);
+                    const uint32_t use = (uint32_t)(q / stages);
+                    if (!mbar_wait(smem_u32(&sh->empty[s]), (use & 1u) ^ 1u, abort_flag)) {
+                        if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_EMPTY);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    const uint32_t full = smem_u32(&sh->full[s]);
+                    const uint32_t st = base_s + (uint32_t)s * stage_bytes;
+                    mbar_arrive_expect_tx(full, tx_bytes);
+                    tma_load_3d(st, &en.maps.a_hi, 0, m0, kb, full);
+                    tma_load_3d(st + kABytes, &en.maps.a_lo, 0, m0, kb, full);
+                    for (int b = 0; b < en.maps.nbox_b; ++b) {
+                        const int r0 = b * en.maps.box_b_rows;
+                        const uint32_t off = (uint32_t)r0 * RB;
+                        tma_load_3d(st + 2 * kABytes + off, &en.maps.b_hi, 0, wtile * N + r0, en.args.kbB0 + kb, full);
+                        tma_load_3d(st + 2 * kABytes + b_pad + off, &en.maps.b_lo, 0, wtile * N + r0,
+                                    en.args.kbB0 + kb, full);
+                    }
+                }
+            }
+            if (*abort_flag) {
+                // let every copy into this CTA's ring land before it can exit
+                for (int64_t k = q > stages ? q - stages : 0; k < q; ++k)
+                    if (!mbar_wait(smem_u32(&sh->full[k % stages]), (uint32_t)(k / stages) & 1u, nullptr))
+                        atomicOr(err, DEVERR_TIMEOUT_DRAIN);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const int ksteps = bf / 8;
+            int64_t q = 0, c = 0;                     // stages consumed, chunks started
+            bool stop = false;
+            for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x) {
+                const TcGroupEntry &en = g.e[group_entry(g, t)];
+                const int N = en.args.N, n_kb = en.args.n_kb, cb = en.args.drain_kb;
+                const uint32_t id = idesc_bf16_f32(kMTile, N);
+                for (int kb = 0; kb < n_kb; ++kb, ++q) {
+                    const int kc = kb % cb;
+                    const int64_t gc = c + kb / cb;   // chunk of this CTA
+                    const int buf = (int)(gc & 1);
+                    if (kc == 0 && gc >= 2) {
+                        // the buffer's previous chunk must be drained before it is overwritten
+                        if (!mbar_wait(smem_u32(&sh->chunk_free[buf]), (uint32_t)((gc - 2) >> 1) & 1u, abort_flag)) {
+                            if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
+                            *abort_flag = 1;
+                            stop = true;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    const int s = (int)(q % stages);
+                    if (!mbar_wait(smem_u32(&sh->full[s]), (uint32_t)(q / stages) & 1u, abort_flag)) {
+                        if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_FULL);
+                        *abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    if (trace && q == 0) trace[2] = globaltimer();
+                    const uint32_t st = base_s + (uint32_t)s * stage_bytes;
+                    const uint64_t dAhi0 = sdesc_k(st, RB);
+                    const uint64_t dAlo0 = sdesc_k(st + kABytes, RB);
+                    const uint64_t dBhi0 = sdesc_k(st + 2 * kABytes, RB);
+                    const uint64_t dBlo0 = sdesc_k(st + 2 * kABytes + b_pad, RB);
+                    const uint32_t acc = tmem + (uint32_t)(buf * n_max);
+                    for (int ks = 0; ks < ksteps; ++ks) {
+                        const uint64_t adv = (uint64_t)(2 * ks);
+                        const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;   // a chunk starts from zero
+                        mma_bf16_ss(acc, dAhi0 + adv, dBhi0 + adv, id, first);
+                        mma_bf16_ss(acc, dAhi0 + adv, dBlo0 + adv, id, 1u);
+                        mma_bf16_ss(acc, dAlo0 + adv, dBhi0 + adv, id, 1u);
+                    }
+                    mma_commit(smem_u32(&sh->empty[s]));
+                    if (kc == cb - 1 || kb == n_kb - 1) mma_commit(smem_u32(&sh->chunk_full[buf]));
+                }
+                c += (n_kb + cb - 1) / cb;
+            }
+            mma_commit(smem_u32(&sh->tmem_full));   // always: nothing writes TMEM after this
+            if (trace) trace[3] = globaltimer();
+        }
+    } else {
+        // epilogue warps 2..9: TMEM lane quarter q4 = warp % 4, column half h
+        const int q4 = warp & 3, h = (warp - 2) >> 2;
+        float sum[kDrainCols];
+        int64_t c = 0;                                // chunks consumed
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+            const TcGroupEntry &en = g.e[group_entry(g, t)];
+            const TcPlanArgs &a = en.args;
+            const int64_t lt = t - en.cta_begin;
+            const int wtile = (int)(lt % a.n_wt);
+            const int m0 = (int)(lt / a.n_wt) * kMTile;
+            const int cols = a.wt;                    // N / 2 columns per thread
+            const int col0 = h * cols;
+            const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)col0;
+            const int n_chunks = (a.n_kb + a.drain_kb - 1) / a.drain_kb;
+#pragma unroll
+            for (int i = 0; i < kDrainCols; ++i) sum[i] = 0.f;
+            for (int lc = 0; lc < n_chunks; ++lc, ++c) {
+                const int buf = (int)(c & 1);
+                if (!mbar_wait(smem_u32(&sh->chunk_full[buf]), (uint32_t)(c >> 1) & 1u, abort_flag)) {
+                    if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tl = lane_base + (uint32_t)(buf * n_max);
+                if (lc + 1 < n_chunks) {
+                    drain_add(sum, tl, cols);
+                } else {
+                    if (trace && warp == 2 && lane == 0 && t == blockIdx.x) trace[4] = globaltimer();
+                    const RowCtx row = make_row(a.e, (int64_t)m0 + q4 * 32 + lane);
+                    const int jbase = wtile * a.wt;
+                    switch (epi_kind(a.e)) {
+                        case EPI_FINAL: tc_epilogue_drained<EPI_FINAL>(a, row, tl, col0, cols, jbase, sum); break;
+                        case EPI_FINAL_KAHAN: tc_epilogue_drained<EPI_FINAL_KAHAN>(a, row, tl, col0, cols, jbase, sum); break;
+                        case EPI_FINAL_FP64: tc_epilogue_drained<EPI_FINAL_FP64>(a, row, tl, col0, cols, jbase, sum); break;
+                        case EPI_STORE_KAHAN: tc_epilogue_drained<EPI_STORE_KAHAN>(a, row, tl, col0, cols, jbase, sum); break;
+                        case EPI_STORE_FP64: tc_epilogue_drained<EPI_STORE_FP64>(a, row, tl, col0, cols, jbase, sum); break;
+                        case EPI_ADD_KAHAN: tc_epilogue_drained<EPI_ADD_KAHAN>(a, row, tl, col0, cols, jbase, sum); break;
+                        default: tc_epilogue_drained<EPI_ADD_FP64>(a, row, tl, col0, cols, jbase, sum); break;
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&sh->chunk_free[buf]));
+            }
+        }
+        // always wait (bounded) for the last commit: no MMA may still write TMEM at release
+        if (!mbar_wait(smem_u32(&sh->tmem_full), 0u, nullptr)) atomicOr(err, DEVERR_TIMEOUT_TMEM);
+        tc_fence_after();
+    }
+    if (trace && warp == 2 && lane == 0) trace[5] = globaltimer();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, ncols);
+    }
+    if (trace && threadIdx.x == 0) trace[6] = globaltimer();
 }
 
 // --------------------------------------------------------------------------------------
@@ -1274,14 +1387,14 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *map
         // the drained form one CTA per tile and two buffers of at most 256 columns
         if (args[i].cluster != C || args[i].bf != args[0].bf || args[i].pair != pair ||
             (args[i].drain_kb > 0) != drain || (pair && (C != 2 || args[i].N > 256 || args[i].N % 32)) ||
-            (drain && (C != 1 || pair || args[i].N > 256 || args[i].wt > 128))) {
+            (drain && (C != 1 || pair || args[i].wt > kDrainCols))) {
             delete g;
             return cudaErrorInvalidValue;
         }
         g->e[i].maps = *reinterpret_cast<const TcMaps *>(maps[i]);
         g->e[i].args = args[i];
         g->e[i].cta_begin = (int)total;
-        if (args[i].trace) g->e[i].args.trace = args[i].trace + (size_t)total * kTraceWords;
+        if (args[i].trace && !drain) g->e[i].args.trace = args[i].trace + (size_t)total * kTraceWords;
         const int64_t c = tc_grid_ctas(args[i]);
         g->e[i].ctas = (int)c;
         total += c;
@@ -1292,11 +1405,34 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *map
         delete g;
         return cudaErrorInvalidConfiguration;
     }
+    unsigned grid = (unsigned)total;
+    if (drain) {
+        // persistent: the ring and the two TMEM buffers are sized for the widest tile; one wave
+        // of CTAs walks all tiles
+        int n_max = 0;
+        for (int i = 0; i < n; ++i) n_max = std::max(n_max, args[i].N);
+        g->n_max = n_max;
+        g->stages = tc_stages_for(n_max, args[0].bf);
+        g->tiles = total;
+        smem = tc_smem_bytes(n_max, args[0].bf, g->stages);
+        int dev = 0, sms = 0, occ = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(flush_tc_drain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, flush_tc_drain_kernel, 320, smem);
+        if (e != cudaSuccess || g->stages < 2 || n_max > 2 * kDrainCols || occ < 1) {
+            delete g;
+            return e != cudaSuccess ? e : cudaErrorInvalidConfiguration;
+        }
+        if ((int64_t)occ * sms < total) grid = (unsigned)(occ * sms);
+    }
     auto kern = drain ? flush_tc_drain_kernel : (pair ? flush_tc_pair_kernel : flush_tc_kernel);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)total, 1, 1);
+        cfg.gridDim = dim3(grid, 1, 1);
         cfg.blockDim = dim3(drain ? 320 : 192, 1, 1);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = st;

@@ -207,8 +207,8 @@ int omega_tile_max(int n_acc) {
     return std::max(8, (max_cols / 2) / 8 * 8);
 }
 
-void choose_omega_tile(Stream &s, int n_acc, int requested) {
-    const int wt_max = omega_tile_max(n_acc);
+void choose_omega_tile(Stream &s, int n_acc, int requested, int cap = 0) {
+    const int wt_max = cap ? std::min(cap, omega_tile_max(n_acc)) : omega_tile_max(n_acc);
     int best = 8;
     if (requested > 0) {
         best = std::min(requested, wt_max);
@@ -723,7 +723,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         s.T_pad = (int)round_up(s.T, p->prec == TACAW_PREC_SPLIT_BF16 ? p->bf : 8);
         s.n_kb_T = s.T_pad / (p->prec == TACAW_PREC_SPLIT_BF16 ? p->bf : 8);
         s.Nw = s.d.n_omega;
-        choose_omega_tile(s, tile_acc, desc->tc_omega_tile);
+        choose_omega_tile(s, tile_acc, desc->tc_omega_tile, drained ? kDrainMaxOmegaTile : 0);
         if (p->prec == TACAW_PREC_FP32) s.Nw_pad = (int)round_up(s.Nw, 64);
         T_pad_max = std::max(T_pad_max, s.T_pad);
         p->s.push_back(s);
@@ -758,7 +758,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
                 sh.ring = desc->k_stage ? std::min(desc->k_stage, s.T_pad) : s.T_pad;
                 sh.bf = p->bf;
                 sh.n_acc = p->tc_acc;
-                sh.wt_max = omega_tile_max(tile_acc);
+                sh.wt_max = drained ? std::min(kDrainMaxOmegaTile, omega_tile_max(tile_acc)) : omega_tile_max(tile_acc);
                 sh.drain_kb = drained ? std::max(1, drain_frames / p->bf) : 0;
                 sh.fixed_wt = desc->tc_omega_tile ? s.wt : 0;
                 sh.fixed_cluster = desc->tc_cluster;

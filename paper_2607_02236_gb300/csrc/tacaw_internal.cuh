@@ -277,6 +277,7 @@ struct TcMaps;                 // tensor maps (defined in k_tc_gemm.cu)
 cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps /* TcMaps */, cudaStream_t st);
 int64_t tc_grid_ctas(const TcPlanArgs &a);
 constexpr int kMaxGroupStreams = 16;
+constexpr int kDrainMaxOmegaTile = 112;   // drained form: complex energies per tile at most
 // one launch over up to kMaxGroupStreams streams' flushes (same cluster size and block frames)
 cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *maps, int n, cudaStream_t st);
 cudaError_t launch_flush_tc_direct(const TcPlanArgs &a, const TcDirectArgs &d, const void *maps, cudaStream_t st);
