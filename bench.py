@@ -313,12 +313,27 @@ def main():
     spectra_per_s = world * P * D / (ms_step * 1e-3)
 
     phases = None
+    tr = None
     if args.trace and args.precision == "split_bf16":
         plan.set_timing(2)
         run_step(plan)
         torch.cuda.synchronize()
         tr = plan.flush_trace().astype(np.int64)
         plan.set_timing(0)
+        if info["tc_drain_frames"]:
+            # persistent drained kernel: one row per launched CTA (see tacaw_set_timing)
+            tr = tr[tr[:, 0] != 0]
+            life = tr[:, 6] - tr[:, 0]
+            phases = {"ctas": int(len(tr)), "lifetime_us": round(float(np.median(life)) / 1e3, 1),
+                      "setup_us": round(float(np.median(tr[:, 1] - tr[:, 0])) / 1e3, 2),
+                      "first_operands_us": round(float(np.median(tr[:, 2] - tr[:, 1])) / 1e3, 2),
+                      "mma_span_us": round(float(np.median(tr[:, 3] - tr[:, 2])) / 1e3, 1),
+                      "mma_wait_drained_buffer_us": round(float(np.median(tr[:, 4])) / 1e3, 1),
+                      "mma_wait_operands_us": round(float(np.median(tr[:, 5])) / 1e3, 1),
+                      "tail_after_last_mma_us": round(float(np.median(tr[:, 6] - tr[:, 3])) / 1e3, 2),
+                      "unit": "median per CTA"}
+            tr = None
+    if tr is not None and args.trace and args.precision == "split_bf16":
         names = ["setup", "fill", "main_loop", "drain", "epilogue", "exit"]
         phases = {n: round(float(np.median(tr[:, i + 1] - tr[:, i])) / 1e3, 3) for i, n in enumerate(names)}
         gaps = []

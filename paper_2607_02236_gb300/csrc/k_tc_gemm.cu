@@ -897,6 +897,7 @@ __global__ void __maxnreg__(168) flush_tc_drain_kernel(const __grid_constant__ T
             const int ksteps = bf / 8;
             int64_t q = 0, c = 0;                     // stages consumed, chunks started
             bool stop = false;
+            uint64_t wait_drain = 0, wait_full = 0;   // traced: ns spent waiting
             for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x) {
                 const TcGroupEntry &en = g.e[group_entry(g, t)];
                 const int N = en.args.N, n_kb = en.args.n_kb, cb = en.args.drain_kb;
@@ -907,21 +908,25 @@ __global__ void __maxnreg__(168) flush_tc_drain_kernel(const __grid_constant__ T
                     const int buf = (int)(gc & 1);
                     if (kc == 0 && gc >= 2) {
                         // the buffer's previous chunk must be drained before it is overwritten
+                        const uint64_t w0 = trace ? globaltimer() : 0;
                         if (!mbar_wait(smem_u32(&sh->chunk_free[buf]), (uint32_t)((gc - 2) >> 1) & 1u, abort_flag)) {
                             if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
                             *abort_flag = 1;
                             stop = true;
                             break;
                         }
+                        if (trace) wait_drain += globaltimer() - w0;
                         tc_fence_after();
                     }
                     const int s = (int)(q % stages);
+                    const uint64_t w1 = trace ? globaltimer() : 0;
                     if (!mbar_wait(smem_u32(&sh->full[s]), (uint32_t)(q / stages) & 1u, abort_flag)) {
                         if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_FULL);
                         *abort_flag = 1;
                         stop = true;
                         break;
                     }
+                    if (trace && q > 0) wait_full += globaltimer() - w1;
                     tc_fence_after();
                     if (trace && q == 0) trace[2] = globaltimer();
                     const uint32_t st = base_s + (uint32_t)s * stage_bytes;
@@ -943,7 +948,11 @@ __global__ void __maxnreg__(168) flush_tc_drain_kernel(const __grid_constant__ T
                 c += (n_kb + cb - 1) / cb;
             }
             mma_commit(smem_u32(&sh->tmem_full));   // always: nothing writes TMEM after this
-            if (trace) trace[3] = globaltimer();
+            if (trace) {
+                trace[3] = globaltimer();
+                trace[4] = wait_drain;
+                trace[5] = wait_full;
+            }
         }
     } else {
         // epilogue warps 2..9: TMEM lane quarter q4 = warp % 4, column half h
@@ -976,7 +985,6 @@ __global__ void __maxnreg__(168) flush_tc_drain_kernel(const __grid_constant__ T
                 if (lc + 1 < n_chunks) {
                     drain_add(sum, tl, cols);
                 } else {
-                    if (trace && warp == 2 && lane == 0 && t == blockIdx.x) trace[4] = globaltimer();
                     const RowCtx row = make_row(a.e, (int64_t)m0 + q4 * 32 + lane);
                     const int jbase = wtile * a.wt;
                     switch (epi_kind(a.e)) {
@@ -998,7 +1006,6 @@ __global__ void __maxnreg__(168) flush_tc_drain_kernel(const __grid_constant__ T
         if (!mbar_wait(smem_u32(&sh->tmem_full), 0u, nullptr)) atomicOr(err, DEVERR_TIMEOUT_TMEM);
         tc_fence_after();
     }
-    if (trace && warp == 2 && lane == 0) trace[5] = globaltimer();
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {

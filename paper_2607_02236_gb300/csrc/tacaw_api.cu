@@ -287,6 +287,8 @@ tacaw_status trace_buffer(tacaw_plan_s *p, int64_t nc, unsigned long long **out)
         p->trace_cap = nc;
     }
     p->trace_ctas = nc;
+    // a persistent launch writes fewer CTAs than tiles: the rest stays zero
+    CU_CHECK(p, cudaMemsetAsync(p->d_trace, 0, sizeof(unsigned long long) * kTraceWords * nc, nullptr), "trace reset");
     *out = p->d_trace;
     return TACAW_OK;
 }
