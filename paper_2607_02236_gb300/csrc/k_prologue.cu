@@ -57,10 +57,22 @@ __device__ __forceinline__ void split2(float2 r, uint32_t &hi, uint32_t &lo) {
     lo = pack_bf16x2(lr, li);
 }
 
+// Pre-swizzled staging (swz != 0): the 16-byte chunks of row m are stored in the order the
+// tensor core's shared-memory swizzle of the row width expects (chunk c at c ^ sw(m), sw(m) =
+// (m * chunks_per_row / 8) mod chunks_per_row: 128-, 64- and 32-byte swizzle), so that a plain
+// contiguous copy of a block of rows into 1024-byte-aligned shared memory gives the swizzled
+// operand layout.  Word w (bf16 pair) of the row -> its stored position:
+__host__ __device__ __forceinline__ int swz_word(int w, int64_t m, int bf, int swz) {
+    if (!swz) return w;
+    const int cpr = bf >> 2;
+    const int sw = (int)(((m * cpr) >> 3) & (cpr - 1));
+    return ((((w >> 2) ^ sw)) << 2) | (w & 3);
+}
+
 // Staged frame slot s (s0 + t) goes to block s/bf, elements 2(s%bf), 2(s%bf)+1 of row m
 // (rows of 2*bf bf16 = 4*bf bytes; bf is 8, 16 or 32).
 __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t M_pad, const float2 *mu_hat,
-                                     double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo) {
+                                     double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= g.M) return;
     const float2 *src = row_src(g, m);
@@ -78,7 +90,7 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t
         si += r.y;
         uint32_t h, l;
         split2(r, h, l);
-        size_t o = ((size_t)(s / bf) * M_pad + m) * bf + (s % bf);   // in bf16x2 units
+        size_t o = ((size_t)(s / bf) * M_pad + m) * bf + swz_word(s % bf, m, bf, swz);   // in bf16x2 units
         Hi[o] = h;
         Lo[o] = l;
         ++t;
@@ -100,13 +112,12 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t
         sr += br;
         si += bi;
         const int s = s0 + t;
-        size_t o = ((size_t)(s / bf) * M_pad + m) * bf + (s % bf);
-        uint4 *ph = reinterpret_cast<uint4 *>(Hi + o);
-        uint4 *pl = reinterpret_cast<uint4 *>(Lo + o);
-        ph[0] = make_uint4(h[0], h[1], h[2], h[3]);
-        ph[1] = make_uint4(h[4], h[5], h[6], h[7]);
-        pl[0] = make_uint4(l[0], l[1], l[2], l[3]);
-        pl[1] = make_uint4(l[4], l[5], l[6], l[7]);
+        const size_t row = ((size_t)(s / bf) * M_pad + m) * bf;
+        const size_t o0 = row + swz_word(s % bf, m, bf, swz), o1 = row + swz_word(s % bf + 4, m, bf, swz);
+        *reinterpret_cast<uint4 *>(Hi + o0) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4 *>(Hi + o1) = make_uint4(h[4], h[5], h[6], h[7]);
+        *reinterpret_cast<uint4 *>(Lo + o0) = make_uint4(l[0], l[1], l[2], l[3]);
+        *reinterpret_cast<uint4 *>(Lo + o1) = make_uint4(l[4], l[5], l[6], l[7]);
     }
     // trailing frames
     for (; t < n; ++t) {
@@ -117,7 +128,7 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t
         si += r.y;
         uint32_t h, l;
         split2(r, h, l);
-        size_t o = ((size_t)(s / bf) * M_pad + m) * bf + (s % bf);
+        size_t o = ((size_t)(s / bf) * M_pad + m) * bf + swz_word(s % bf, m, bf, swz);
         Hi[o] = h;
         Lo[o] = l;
     }
@@ -134,7 +145,7 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t
 template <int BF>
 __global__ void __launch_bounds__(128) convert_split_tiled_kernel(FrameGeom g, int n, int s0, int64_t M_pad,
                                                                   const float2 *mu_hat, double2 *sum_res,
-                                                                  __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo) {
+                                                                  __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz) {
     constexpr int bf = BF;
     constexpr int cpr = BF / 4;             // 16-byte chunks per row
     __shared__ uint4 tile_h[128 * cpr], tile_l[128 * cpr];
@@ -174,8 +185,10 @@ __global__ void __launch_bounds__(128) convert_split_tiled_kernel(FrameGeom g, i
         for (int q = r; q < 128 * cpr; q += 128) {
             const int rr = q / cpr, c = q - (q / cpr) * cpr;
             const int slot = rr * cpr + (c ^ (rr & (cpr - 1)));
-            Hi[base + q] = tile_h[slot];
-            Lo[base + q] = tile_l[slot];
+            // stored chunk position of chunk c (m0 is a multiple of 128: row rr's pattern)
+            const int cs = swz ? (c ^ (((rr * cpr) >> 3) & (cpr - 1))) : c;
+            Hi[base + rr * cpr + cs] = tile_h[slot];
+            Lo[base + rr * cpr + cs] = tile_l[slot];
         }
         __syncthreads();
     }
@@ -224,12 +237,12 @@ __global__ void convert_fp32_kernel(FrameGeom g, int n, int s0, int64_t M_pad, c
 }
 
 // Zeroes staged slots [staged, next multiple of bf) of the last block, all M_pad rows.
-__global__ void zero_tail_split_kernel(int64_t M_pad, int staged, int bf, uint32_t *Hi, uint32_t *Lo) {
+__global__ void zero_tail_split_kernel(int64_t M_pad, int staged, int bf, uint32_t *Hi, uint32_t *Lo, int swz) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M_pad) return;
     const int blk = staged / bf;
     for (int tt = staged % bf; tt < bf; ++tt) {
-        size_t o = ((size_t)blk * M_pad + m) * bf + tt;
+        size_t o = ((size_t)blk * M_pad + m) * bf + swz_word(tt, m, bf, swz);
         Hi[o] = 0u;
         Lo[o] = 0u;
     }
@@ -250,16 +263,17 @@ cudaError_t launch_mean(const FrameGeom &g, int n, float2 *mu_hat, cudaStream_t 
 }
 
 cudaError_t launch_convert_split(const FrameGeom &g, int n, int s0, int bf, int64_t M_pad, const float2 *mu_hat,
-                                 double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, cudaStream_t st) {
+                                 double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz,
+                                 cudaStream_t st) {
     if (bf >= 16 && s0 % bf == 0 && n % bf == 0) {
         const unsigned grid = (unsigned)(M_pad / 128);
         if (bf == 32)
-            convert_split_tiled_kernel<32><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo);
+            convert_split_tiled_kernel<32><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo, swz);
         else
-            convert_split_tiled_kernel<16><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo);
+            convert_split_tiled_kernel<16><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo, swz);
         return cudaGetLastError();
     }
-    convert_split_kernel<<<blocks_for(g.M, 256), 256, 0, st>>>(g, n, s0, bf, M_pad, mu_hat, sum_res, A_hi, A_lo);
+    convert_split_kernel<<<blocks_for(g.M, 256), 256, 0, st>>>(g, n, s0, bf, M_pad, mu_hat, sum_res, A_hi, A_lo, swz);
     return cudaGetLastError();
 }
 
@@ -270,9 +284,9 @@ cudaError_t launch_convert_fp32(const FrameGeom &g, int n, int s0, int64_t M_pad
 }
 
 cudaError_t launch_zero_tail_split(int64_t M_pad, int staged, int bf, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo,
-                                   cudaStream_t st) {
+                                   int swz, cudaStream_t st) {
     zero_tail_split_kernel<<<blocks_for(M_pad, 256), 256, 0, st>>>(
-        M_pad, staged, bf, reinterpret_cast<uint32_t *>(A_hi), reinterpret_cast<uint32_t *>(A_lo));
+        M_pad, staged, bf, reinterpret_cast<uint32_t *>(A_hi), reinterpret_cast<uint32_t *>(A_lo), swz);
     return cudaGetLastError();
 }
 

@@ -74,8 +74,14 @@ __global__ void twiddles_split_kernel(TableArgs a, __nv_bfloat16 *B_hi, __nv_bfl
     const int bf = a.block_frames;
     const int kb = t / bf, tt = t % bf;
     const size_t rows = 2 * (size_t)a.Nw_pad;
-    const size_t r0 = ((size_t)kb * rows + 2 * (size_t)j) * (2 * bf) + 2 * tt;
-    const size_t r1 = r0 + 2 * bf;
+    // word tt (a bf16 pair) of rows 2j and 2j+1; pre-swizzled rows keep their 16-byte chunks
+    // where the tensor core's shared-memory swizzle of the row width expects them
+    const int cpr = bf >> 2;
+    const int sw0 = a.swz ? (int)(((2 * j * cpr) >> 3) & (cpr - 1)) : 0;
+    const int sw1 = a.swz ? (int)((((2 * j + 1) * cpr) >> 3) & (cpr - 1)) : 0;
+    const int w0 = (((tt >> 2) ^ sw0) << 2) | (tt & 3), w1 = (((tt >> 2) ^ sw1) << 2) | (tt & 3);
+    const size_t r0 = ((size_t)kb * rows + 2 * (size_t)j) * (2 * bf) + 2 * w0;
+    const size_t r1 = ((size_t)kb * rows + 2 * (size_t)j + 1) * (2 * bf) + 2 * w1;
     float v0[2] = {(float)br, (float)(-bi)};
     float v1[2] = {(float)bi, (float)br};
     for (int e = 0; e < 2; ++e) {

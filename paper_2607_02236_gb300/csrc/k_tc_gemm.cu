@@ -128,6 +128,12 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
         : "memory");
 }
+// Contiguous copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+                 : "memory");
+}
 // L2 prefetch of a tensor box (no shared-memory destination, no completion)
 __device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *map, int c0, int c1, int c2) {
     asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
@@ -874,15 +880,14 @@ __global__ void __maxnreg__(168) flush_tc_drain_kernel(const __grid_constant__ T
                     const uint32_t full = smem_u32(&sh->full[s]);
                     const uint32_t st = base_s + (uint32_t)s * stage_bytes;
                     mbar_arrive_expect_tx(full, tx_bytes);
-                    tma_load_3d(st, &en.maps.a_hi, 0, m0, kb, full);
-                    tma_load_3d(st + kABytes, &en.maps.a_lo, 0, m0, kb, full);
-                    for (int b = 0; b < en.maps.nbox_b; ++b) {
-                        const int r0 = b * en.maps.box_b_rows;
-                        const uint32_t off = (uint32_t)r0 * RB;
-                        tma_load_3d(st + 2 * kABytes + off, &en.maps.b_hi, 0, wtile * N + r0, en.args.kbB0 + kb, full);
-                        tma_load_3d(st + 2 * kABytes + b_pad + off, &en.maps.b_lo, 0, wtile * N + r0,
-                                    en.args.kbB0 + kb, full);
-                    }
+                    // the tables are pre-swizzled: each operand block is one contiguous copy
+                    const size_t ao = ((size_t)kb * (size_t)en.args.a_rows + (size_t)m0) * RB;
+                    const size_t bo = ((size_t)(en.args.kbB0 + kb) * (size_t)en.args.b_rows + (size_t)wtile * N) * RB;
+                    bulk_load(st, static_cast<const uint8_t *>(en.args.A_hi) + ao, kABytes, full);
+                    bulk_load(st + kABytes, static_cast<const uint8_t *>(en.args.A_lo) + ao, kABytes, full);
+                    bulk_load(st + 2 * kABytes, static_cast<const uint8_t *>(en.args.B_hi) + bo, (uint32_t)N * RB, full);
+                    bulk_load(st + 2 * kABytes + b_pad, static_cast<const uint8_t *>(en.args.B_lo) + bo,
+                              (uint32_t)N * RB, full);
                 }
             }
             if (*abort_flag) {

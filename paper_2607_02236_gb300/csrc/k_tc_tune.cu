@@ -228,6 +228,12 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
         a.n_big = sh.n_acc == 3 ? 2 : 1;
         a.cluster = c.C;
         a.drain_kb = sh.drain_kb;
+        a.A_hi = a_hi.p;
+        a.A_lo = a_lo.p;
+        a.B_hi = b_hi.p;
+        a.B_lo = b_lo.p;
+        a.a_rows = rows;
+        a.b_rows = 2 * c.wt * c.n_wt;
         a.err = d_err;
         double t[2] = {0.0, 0.0};
         const int kbs[2] = {kb1, kb2};

@@ -267,6 +267,12 @@ TcPlanArgs tc_args(tacaw_plan_s *p, const Stream &s, const EpiArgs &e) {
     a.split = p->tc_acc > 1 ? 1 : 0;
     a.n_big = p->tc_acc == 3 ? 2 : 1;
     a.drain_kb = p->in_place ? 0 : p->drain_kb;
+    a.A_hi = s.A_hi;
+    a.A_lo = s.A_lo;
+    a.B_hi = s.B_hi;
+    a.B_lo = s.B_lo;
+    a.a_rows = s.M_pad;
+    a.b_rows = 2 * s.Nw_pad;
     a.cluster = p->in_place ? 1 : s.tc_cluster;
     a.pair = p->in_place ? 0 : s.tc_pair;
     a.prefetch = p->in_place ? 0 : p->tc_prefetch;
@@ -352,7 +358,7 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         p->launches++;
     } else if (p->prec == TACAW_PREC_SPLIT_BF16) {
         if (n % p->bf) {
-            CU_CHECK(p, launch_zero_tail_split(s.M_pad, n, p->bf, s.A_hi, s.A_lo, st), "zero_tail");
+            CU_CHECK(p, launch_zero_tail_split(s.M_pad, n, p->bf, s.A_hi, s.A_lo, p->drain_kb > 0, st), "zero_tail");
             p->launches++;
         }
         TcPlanArgs a = tc_args(p, s, e);
@@ -403,7 +409,7 @@ tacaw_status final_flush_grouped(tacaw_plan_s *p, float *d_I, float2 *d_Psi, cud
             for (size_t k = g0; k < g1; ++k) {
                 Stream &s = p->s[grp[k]];
                 if (s.staged % p->bf) {
-                    CU_CHECK(p, launch_zero_tail_split(s.M_pad, s.staged, p->bf, s.A_hi, s.A_lo, st), "zero_tail");
+                    CU_CHECK(p, launch_zero_tail_split(s.M_pad, s.staged, p->bf, s.A_hi, s.A_lo, p->drain_kb > 0, st), "zero_tail");
                     p->launches++;
                 }
                 float *I = d_I ? d_I + s.I_off : nullptr;
@@ -441,6 +447,7 @@ tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
     ta.window_param = d.window_param;
     ta.fft_bins = d.fft_bins;
     ta.block_frames = p->bf;
+    ta.swz = p->drain_kb > 0 ? 1 : 0;   // the drained kernel copies pre-swizzled blocks
     // cycles per frame c_j = E_j dt / h (FP64)
     std::vector<double> cj(s.Nw), E(s.Nw);
     for (int j = 0; j < s.Nw; ++j) {
@@ -966,7 +973,7 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
         } else {
             if (p->prec == TACAW_PREC_SPLIT_BF16)
                 CU_CHECK(p, launch_convert_split(gc, chunk, s.staged, p->bf, s.M_pad, s.mu_hat, s.sum_res, s.A_hi,
-                                                 s.A_lo, st),
+                                                 s.A_lo, p->drain_kb > 0, st),
                          "convert");
             else
                 CU_CHECK(p, launch_convert_fp32(gc, chunk, s.staged, s.M_pad, s.mu_hat, s.sum_res, s.A32, st),

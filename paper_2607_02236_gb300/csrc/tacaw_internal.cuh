@@ -212,6 +212,7 @@ struct TableArgs {
     int fft_bins;
     const double *cj;          // device, cycles per frame per energy (explicit grid)
     int block_frames;          // split-path staging block (8, 16 or 32 frames)
+    int swz;                   // split path: rows stored pre-swizzled (see convert_split_kernel)
 };
 
 cudaError_t launch_twiddles_split(const TableArgs &t, __nv_bfloat16 *B_hi, __nv_bfloat16 *B_lo, cudaStream_t st);
@@ -221,11 +222,12 @@ cudaError_t launch_window_values(const TableArgs &t, float *w, cudaStream_t st);
 
 cudaError_t launch_mean(const FrameGeom &g, int n, float2 *mu_hat, cudaStream_t st);
 cudaError_t launch_convert_split(const FrameGeom &g, int n, int s0, int bf, int64_t M_pad, const float2 *mu_hat,
-                                 double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, cudaStream_t st);
+                                 double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz,
+                                 cudaStream_t st);
 cudaError_t launch_convert_fp32(const FrameGeom &g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
                                 double2 *sum_res, float2 *A32, cudaStream_t st);
 cudaError_t launch_zero_tail_split(int64_t M_pad, int staged, int bf, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo,
-                                   cudaStream_t st);
+                                   int swz, cudaStream_t st);
 cudaError_t launch_mean_residual(int64_t M, int T, int subtract_mean, const double2 *sum_res, float2 *dmu,
                                  cudaStream_t st);
 
@@ -253,7 +255,11 @@ struct TcPlanArgs {
                                // 1 = the odd CTA relays its stage-full events, 2 = its copies
                                // complete directly on the even CTA's barriers; 0 = off
     int drain_kb;              // > 0: one double-buffered accumulator drained into FP32
-                               // registers every drain_kb staging blocks (N <= 256, wt <= 128)
+                               // registers every drain_kb staging blocks (wt <= 112); the
+                               // operands are pre-swizzled and copied as contiguous blocks:
+    const void *A_hi, *A_lo, *B_hi, *B_lo;   //   staging and twiddle tables
+    int64_t a_rows;            //   rows per staging block of A (M_pad)
+    int b_rows;                //   rows per twiddle block of B (2 * Nw_pad)
     int prefetch;              // staging blocks of A prefetched into L2 ahead of the current one (0: off)
     unsigned long long *trace; // null, or kTraceWords globaltimer stamps per CTA (phase boundaries)
     uint32_t *err;
