@@ -16,6 +16,14 @@ What is computed (per stream, probe p, ROI pixel k), all in float64:
   I[k,j]    = B(E_j) * |Psi[k,j]|^2,  B(E) = beta E / (1 - exp(-beta E))   (Eq. 1)
   S[d,j]    = sum_k M_d(k) * I[k,j]                  (DetectorSet apertures, Sec. II.B)
 
+Welch averaging (Sec. II.B, "Welch method: trajectory chunk overlap & windowing" and the
+1/N average of "Processing of a batch"): segments of L frames start at s_0 = 0 and
+s_{n+1} = s_n + stride (stride = L // nu for the overlap nu), N = (n_frames - L) // stride + 1
+of them; each is a segment of the definition above (its own mean, the window over its L
+frames, phases counted from its first frame) and
+
+  I_welch = (1/N) sum_n I_n,   S_welch = (1/N) sum_n S_n
+
 and, for a real loss L = sum_{p,d,j} (dL/dS)[p,d,j] * S[p,d,j], the gradient in
 PyTorch's convention for real losses of complex inputs, g = dL/dRe(psi) +
 i dL/dIm(psi) = 2 dL/dconj(psi):
@@ -182,6 +190,34 @@ def forward(psi, *, window_kind="hann", window_param=0.0, E_meV=None, dt_fs=5.0,
     M = detector_masks(Kx, Ky, detectors).reshape(len(detectors), Ky * Kx)
     S = np.einsum("pjk,dk->pdj", I, M) if len(detectors) else np.zeros((P, 0, len(E)))
     return Result(mu.reshape(P, Ky, Kx), Psi.reshape(P, -1, Ky, Kx), I.reshape(P, -1, Ky, Kx), S)
+
+
+def welch_segments(n_frames: int, L: int, stride: int) -> np.ndarray:
+    """Start frames of the Welch segments: 0, stride, 2*stride, ... while a whole segment fits."""
+    if L < 1 or stride < 1 or n_frames < L:
+        return np.zeros(0, dtype=np.int64)
+    return np.arange((n_frames - L) // stride + 1, dtype=np.int64) * stride
+
+
+def welch_stride(L: int, nu: float) -> int:
+    """Frames between segment starts for the overlap parameter nu (remainder-less division)."""
+    return int(L // nu)
+
+
+def welch_forward(psi, L: int, stride: int, **kw) -> Result:
+    """Welch average of the segments of psi [P, n_frames, Ky, Kx] (see the module header).
+    Result.I and Result.S are the averages; mu and Psi are those of the last segment."""
+    psi = np.asarray(psi)
+    starts = welch_segments(psi.shape[1], L, stride)
+    if len(starts) == 0:
+        raise ValueError("no whole segment of L frames")
+    I = S = None
+    for s0 in starts:
+        r = forward(psi[:, s0:s0 + L], **kw)
+        I = r.I if I is None else I + r.I
+        S = r.S if S is None else S + r.S
+    N = float(len(starts))
+    return Result(r.mu, r.Psi, I / N, S / N)
 
 
 def gradient(psi, dLdS, *, window_kind="hann", window_param=0.0, E_meV=None, dt_fs=5.0,

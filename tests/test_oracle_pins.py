@@ -376,3 +376,44 @@ def test_pixel_gradient_equals_full_gradient_on_pixels():
         Lp = oracle.loss_pixels(series, dLdS[p], M.T, **kw2)
         Lfull = float(np.sum(dLdS[p] * oracle.forward(psi[p:p + 1], **kw).S[0]))
         assert abs(Lp - Lfull) <= 1e-10 * abs(Lfull)
+
+
+# ------------------------------------------------------------------------------------ Welch
+def test_welch_segment_starts_and_stride():
+    """s_{n+1} = s_n + L // nu (remainder-less); whole segments only."""
+    assert oracle.welch_stride(200, 2.0) == 100 and oracle.welch_stride(200, 3.0) == 66
+    st = oracle.welch_segments(3200, 200, 100)
+    assert len(st) == 31 and st[0] == 0 and np.all(np.diff(st) == 100) and st[-1] + 200 == 3200
+    assert len(oracle.welch_segments(3299, 200, 100)) == 31
+    assert len(oracle.welch_segments(199, 200, 100)) == 0
+
+
+def test_welch_single_segment_is_the_plain_definition():
+    rng = np.random.default_rng(71)
+    psi = rand_psi(2, 40, 3, 4, rng)
+    kw = dict(window_kind="hann", E_meV=np.linspace(0, 90, 9) + 0.3, dt_fs=5.0, subtract_mean=True,
+              detectors=[Detector("circular", 0, 0, -1, 1.5)])
+    a = oracle.welch_forward(psi, 40, 13, **kw)
+    b = oracle.forward(psi, **kw)
+    np.testing.assert_allclose(a.I, b.I, rtol=0, atol=0)
+    np.testing.assert_allclose(a.S, b.S, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("L,stride,win", [(64, 32, "hann"), (60, 20, "hann"), (50, 50, "rect"),
+                                          (64, 21, "tukey"), (48, 16, "rect")])
+def test_welch_matches_scipy_welch(L, stride, win):
+    """On the FFT grid, I_welch = scipy.signal.welch(..., detrend='constant', scaling='spectrum',
+    two-sided) * (sum of the window)^2: per-segment mean removal, window, |DFT|^2, 1/N average."""
+    rng = np.random.default_rng(72)
+    n = 5 * L + 7
+    t = np.arange(n)
+    x = (0.7 + 0.2j + np.exp(2j * np.pi * 0.137 * t) + 0.4 * np.exp(-2j * np.pi * 0.31 * t)
+         + 0.3 * (rng.standard_normal(n) + 1j * rng.standard_normal(n)))
+    psi = np.broadcast_to(x[None, :, None, None], (1, n, 1, 1)).copy()
+    param = 0.3 if win == "tukey" else 0.0
+    r = oracle.welch_forward(psi, L, stride, window_kind=win, window_param=param, fft_bins=L, dt_fs=5.0)
+    sw = {"hann": "hann", "rect": "boxcar", "tukey": ("tukey", 0.3)}[win]
+    _, pxx = scipy.signal.welch(x, window=sw, nperseg=L, noverlap=L - stride, detrend="constant",
+                                return_onesided=False, scaling="spectrum", average="mean")
+    wsum = oracle.window(win, L, param).sum()
+    np.testing.assert_allclose(r.I[0, :, 0, 0], pxx * wsum ** 2, rtol=1e-9, atol=1e-9 * np.max(pxx) * wsum ** 2)
