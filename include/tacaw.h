@@ -106,6 +106,14 @@ typedef struct {
     double bose_T_K;           /* > 0: multiply I by B(E) at this temperature; 0: B = 1 */
     int n_detectors;           /* D >= 0 */
     const tacaw_detector *detectors; /* host array of D detectors */
+    /* Welch averaging (Sec. II.B): welch_segments N > 1 splits the pushed frames into N
+     * segments of T frames starting welch_stride frames apart (stride = L // nu for the
+     * overlap nu; 0 means T), each a segment of the definition above (its own mean, window and
+     * phase origin), and the outputs are the averages I = (1/N) sum_n I_n, S likewise.  The
+     * stream then takes (N - 1) * stride + T frames; each frame feeds every segment covering
+     * it (up to ceil(T / stride) at once, each with its own staging).  0 or 1: one segment.  */
+    int welch_segments;
+    int welch_stride;
 } tacaw_stream_desc;
 
 typedef struct {

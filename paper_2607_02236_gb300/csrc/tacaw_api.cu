@@ -78,6 +78,12 @@ struct Stream {
     std::vector<unsigned char> tc_maps;
     int tc_cluster = 1;
     int stages = 0;            // shared-memory pipeline stages of this stream's tiles
+    // Welch lanes: internal stream `lane` of user stream `user` runs segments lane, lane +
+    // lanes, ... one after another; its last flush adds out_scale * I into the user's average
+    int user = 0, lane = 0;
+    int64_t seg = 0;           // current segment of this lane
+    float out_scale = 1.f;
+    int out_add = 0;
     int tc_pair = 0;           // CTA-pair MMAs (cluster of 2, M = 256)
     bool tuned = false;        // tile picked by the autotuner
     // in-place frames: per staged frame, a pointer into the pushed buffer
@@ -90,8 +96,20 @@ struct Stream {
 
 }  // namespace
 
+// A stream as the caller sees it: one internal stream, or the lanes of a Welch average.
+struct UserStream {
+    int first = 0, lanes = 1;  // internal streams [first, first + lanes)
+    int N = 1, stride = 0, L = 0;
+    int64_t total = 0;         // frames of the whole push sequence: (N - 1) * stride + L
+    int64_t pushed = 0;
+    float *I_acc = nullptr;    // Welch: plan-owned running average of the segments' I
+    int64_t I_elems = 0;
+    int64_t I_off = 0, S_off = 0;
+};
+
 struct tacaw_plan_s {
-    std::vector<Stream> s;
+    std::vector<Stream> s;     // internal streams (Welch lanes expanded)
+    std::vector<UserStream> us;
     int prec = 0, accum = 0, k_stage = 0;
     int stages = 0;
     int tc_acc = 3;
@@ -179,6 +197,11 @@ tacaw_status validate_stream(const tacaw_stream_desc &d, int i) {
     if (d.n_detectors < 0 || (d.n_detectors > 0 && !d.detectors))
         return fail(TACAW_ERR_INVALID_ARG, "stream %d: bad detector array", i);
     if (d.bose_T_K < 0) return fail(TACAW_ERR_INVALID_ARG, "stream %d: bose_T_K must be >= 0", i);
+    if (d.welch_segments < 0 || d.welch_stride < 0)
+        return fail(TACAW_ERR_INVALID_ARG, "stream %d: welch_segments and welch_stride must be >= 0", i);
+    if (d.welch_segments > 1 && (int64_t)(d.welch_segments - 1) * (d.welch_stride ? d.welch_stride : d.T) + d.T >
+                                    (int64_t)INT32_MAX)
+        return fail(TACAW_ERR_INVALID_ARG, "stream %d: Welch push sequence longer than 2^31 frames", i);
     for (int k = 0; k < d.n_detectors; ++k) {
         const tacaw_detector &t = d.detectors[k];
         if (t.kind < TACAW_DET_CIRCULAR || t.kind > TACAW_DET_MASK)
@@ -249,6 +272,8 @@ EpiArgs epi_args(tacaw_plan_s *p, const Stream &s, int mode, float *I_out, float
     e.bose = s.bose;
     e.I_out = I_out;
     e.Psi_out = Psi_out;
+    e.out_scale = s.out_scale;
+    e.out_add = s.out_add;
     return e;
 }
 
@@ -600,12 +625,17 @@ tacaw_status finalize_impl(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, 
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
     if (p->finalized) return fail(TACAW_ERR_STATE, "segment already finalized");
-    for (size_t i = 0; i < p->s.size(); ++i)
-        if (p->s[i].pushed != p->s[i].T)
-            return fail(TACAW_ERR_STATE, "stream %zu has %d of %d frames", i, p->s[i].pushed, p->s[i].T);
+    for (size_t i = 0; i < p->us.size(); ++i)
+        if (p->us[i].pushed != p->us[i].total)
+            return fail(TACAW_ERR_STATE, "stream %zu has %lld of %lld frames", i, (long long)p->us[i].pushed,
+                        (long long)p->us[i].total);
     if (d_S && !d_I) return fail(TACAW_ERR_INVALID_ARG, "d_S requires d_I");
+    for (auto &u : p->us)
+        if (d_Psi && u.N > 1) return fail(TACAW_ERR_INVALID_ARG, "d_Psi is not available for Welch-averaged streams");
+    // single-segment streams: their last flush (Welch lanes finished theirs during the pushes)
     if (!p->in_place)
         for (auto &s : p->s) {
+            if (p->us[s.user].N > 1) continue;
             CU_CHECK(p, launch_mean_residual(s.M, s.T, s.d.subtract_mean, s.sum_res, s.dmu, st), "mean residual");
             p->launches++;
         }
@@ -615,17 +645,23 @@ tacaw_status finalize_impl(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, 
         if (r != TACAW_OK) return r;
     } else {
         for (auto &s : p->s) {
+            if (p->us[s.user].N > 1) continue;
             tacaw_status r = run_flush(p, s, FLUSH_FINAL, d_I ? d_I + s.I_off : nullptr,
                                        Psi_all ? Psi_all + s.I_off : nullptr, st);
             if (r != TACAW_OK) return r;
         }
     }
+    for (auto &u : p->us)
+        if (u.N > 1 && d_I)
+            CU_CHECK(p, cudaMemcpyAsync(d_I + u.I_off, u.I_acc, sizeof(float) * u.I_elems, cudaMemcpyDeviceToDevice, st),
+                     "Welch average");
     if (d_S)
-        for (auto &s : p->s) {
+        for (auto &u : p->us) {
+            const Stream &s = p->s[u.first];
             if (s.D <= 0) continue;
             ApertureArgs a{};
-            a.I = d_I + s.I_off;
-            a.S = d_S + s.S_off;
+            a.I = d_I + u.I_off;
+            a.S = d_S + u.S_off;
             a.P = s.d.n_probes;
             a.D = s.D;
             a.Nw = s.Nw;
@@ -637,6 +673,66 @@ tacaw_status finalize_impl(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, 
             p->launches++;
         }
     p->finalized = true;
+    return TACAW_OK;
+}
+
+// Pushes n frames (device pointer, the stream's layout) into internal stream s.
+tacaw_status push_internal(tacaw_plan_s *p, Stream &s, const float2 *frames, int n_frames, cudaStream_t st) {
+    FrameGeom g{};
+    g.pitch_row = s.d.pitch_row;
+    g.pitch_frame = s.d.pitch_frame;
+    g.pitch_probe = s.d.pitch_probe;
+    g.roi_x0 = s.d.roi_x0;
+    g.roi_y0 = s.d.roi_y0;
+    g.kx = s.d.kx;
+    g.ky = s.d.ky;
+    g.npix = s.npix;
+    g.M = s.M;
+    g.base = frames;
+    if (s.pushed == 0 && s.d.subtract_mean) {
+        CU_CHECK(p, launch_mean(g, n_frames, s.mu_hat, st), "provisional mean");
+        p->launches++;
+    }
+    int done = 0;
+    while (done < n_frames) {
+        const int chunk = std::min(n_frames - done, s.ring - s.staged);
+        FrameGeom gc = g;
+        gc.base = g.base + (int64_t)done * g.pitch_frame;
+        if (p->in_place) {
+            for (int t = 0; t < chunk; ++t) s.h_frame_ptr[s.pushed + t] = gc.base + (int64_t)t * g.pitch_frame;
+        } else {
+            if (p->prec == TACAW_PREC_SPLIT_BF16)
+                CU_CHECK(p, launch_convert_split(gc, chunk, s.staged, p->bf, s.M_pad, s.mu_hat, s.sum_res, s.A_hi,
+                                                 s.A_lo, p->drain_kb > 0, st),
+                         "convert");
+            else
+                CU_CHECK(p, launch_convert_fp32(gc, chunk, s.staged, s.M_pad, s.mu_hat, s.sum_res, s.A32, st),
+                         "convert");
+            p->launches++;
+        }
+        s.staged += chunk;
+        s.pushed += chunk;
+        done += chunk;
+        if (s.staged == s.ring && s.pushed < s.T) {
+            tacaw_status r = run_flush(p, s, s.flushes == 0 ? FLUSH_STORE : FLUSH_ADD, nullptr, nullptr, st);
+            if (r != TACAW_OK) return r;
+        }
+    }
+    return TACAW_OK;
+}
+
+// A Welch lane has all T frames of its segment: finish the segment into the user's average
+// and make the lane ready for its next segment.
+tacaw_status finish_segment(tacaw_plan_s *p, UserStream &u, Stream &s, cudaStream_t st) {
+    if (!p->in_place) {
+        CU_CHECK(p, launch_mean_residual(s.M, s.T, s.d.subtract_mean, s.sum_res, s.dmu, st), "mean residual");
+        p->launches++;
+    }
+    tacaw_status r = run_flush(p, s, FLUSH_FINAL, u.I_acc, nullptr, st);
+    if (r != TACAW_OK) return r;
+    CU_CHECK(p, cudaMemsetAsync(s.sum_res, 0, sizeof(double2) * s.M, st), "reset sums");
+    s.pushed = s.staged = s.stage_start = s.flushes = 0;
+    s.seg += u.lanes;
     return TACAW_OK;
 }
 
@@ -735,7 +831,25 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         choose_omega_tile(s, tile_acc, desc->tc_omega_tile, drained ? kDrainMaxOmegaTile : 0);
         if (p->prec == TACAW_PREC_FP32) s.Nw_pad = (int)round_up(s.Nw, 64);
         T_pad_max = std::max(T_pad_max, s.T_pad);
-        p->s.push_back(s);
+        // Welch: ceil(T / stride) lanes (segments that overlap in time), each an internal stream
+        UserStream u;
+        u.N = std::max(1, s.d.welch_segments);
+        u.L = s.T;
+        u.stride = s.d.welch_stride ? s.d.welch_stride : s.T;
+        u.lanes = u.N > 1 ? (int)std::min<int64_t>(u.N, (s.T + u.stride - 1) / u.stride) : 1;
+        u.total = (int64_t)(u.N - 1) * u.stride + u.L;
+        u.first = (int)p->s.size();
+        s.user = i;
+        if (u.N > 1) {
+            s.out_scale = (float)(1.0 / (double)u.N);
+            s.out_add = 1;
+        }
+        for (int l = 0; l < u.lanes; ++l) {
+            s.lane = l;
+            s.seg = l;
+            p->s.push_back(s);
+        }
+        p->us.push_back(u);
     }
     // keep the energies (host) for the tables
     std::vector<std::vector<double>> Es(desc->n_streams);
@@ -824,6 +938,8 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     }
     const int64_t budget = desc->hbm_budget_bytes > 0 ? desc->hbm_budget_bytes : (int64_t)(0.9 * (double)free_b);
     int64_t fixed = 0;
+    for (auto &u : p->us)   // Welch averages
+        if (u.N > 1) fixed += 4 * (int64_t)p->s[u.first].d.n_probes * p->s[u.first].Nw * p->s[u.first].npix;
     for (auto &s : p->s) {
         fixed += s.M * (8 + 8 + 16) + (int64_t)s.T_pad * s.Nw_pad * 8 + (int64_t)s.n_kb_T * 2 * s.Nw_pad * 16 * 4 +
                  (int64_t)s.npix * 16 + (1 << 20);
@@ -912,13 +1028,30 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     int64_t I_off = 0, S_off = 0;
     for (size_t i = 0; i < p->s.size() && rc == TACAW_OK; ++i) {
         Stream &s = p->s[i];
-        s.d.E_meV = Es[i].empty() ? nullptr : Es[i].data();
+        s.d.E_meV = Es[s.user].empty() ? nullptr : Es[s.user].data();
         rc = build_stream(p, s, st);
         s.d.E_meV = nullptr;
-        s.I_off = I_off;
-        s.S_off = S_off;
-        I_off += (int64_t)s.d.n_probes * s.Nw * s.npix;
-        S_off += (int64_t)s.d.n_probes * s.D * s.Nw;
+    }
+    for (auto &u : p->us) {
+        if (rc != TACAW_OK) break;
+        Stream &s0 = p->s[u.first];
+        u.I_elems = (int64_t)s0.d.n_probes * s0.Nw * s0.npix;
+        u.I_off = I_off;
+        u.S_off = S_off;
+        for (int l = 0; l < u.lanes; ++l) {
+            p->s[u.first + l].I_off = I_off;
+            p->s[u.first + l].S_off = S_off;
+        }
+        I_off += u.I_elems;
+        S_off += (int64_t)s0.d.n_probes * s0.D * s0.Nw;
+        if (u.N > 1) {
+            if (!dev_alloc(p, &u.I_acc, (size_t)u.I_elems)) {
+                rc = fail(TACAW_ERR_OOM, "cudaMalloc(Welch average)");
+                break;
+            }
+            if (cudaMemsetAsync(u.I_acc, 0, sizeof(float) * u.I_elems, st) != cudaSuccess)
+                rc = fail(TACAW_ERR_CUDA, "memset");
+        }
     }
     p->I_elems = I_off;
     p->S_elems = S_off;
@@ -939,55 +1072,39 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
 tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, int n_frames, void *stream) {
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
-    if (sid < 0 || sid >= (int)p->s.size()) return fail(TACAW_ERR_INVALID_ARG, "stream_id %d out of range", sid);
+    if (sid < 0 || sid >= (int)p->us.size()) return fail(TACAW_ERR_INVALID_ARG, "stream_id %d out of range", sid);
     if (!d_frames) return fail(TACAW_ERR_INVALID_ARG, "d_frames is NULL");
     if (n_frames < 1) return fail(TACAW_ERR_INVALID_ARG, "n_frames must be >= 1");
     if (p->finalized) return fail(TACAW_ERR_STATE, "segment finalized; call tacaw_reset first");
     if ((reinterpret_cast<uintptr_t>(d_frames) & 7) != 0) return fail(TACAW_ERR_INVALID_ARG, "d_frames must be 8-byte aligned");
-    Stream &s = p->s[sid];
-    if ((int64_t)s.pushed + n_frames > s.T)
-        return fail(TACAW_ERR_OVERFLOW, "push of %d frames exceeds T=%d (already %d)", n_frames, s.T, s.pushed);
+    UserStream &u = p->us[sid];
+    if (u.pushed + n_frames > u.total)
+        return fail(TACAW_ERR_OVERFLOW, "push of %d frames exceeds %lld (already %lld)", n_frames, (long long)u.total,
+                    (long long)u.pushed);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    FrameGeom g{};
-    g.pitch_row = s.d.pitch_row;
-    g.pitch_frame = s.d.pitch_frame;
-    g.pitch_probe = s.d.pitch_probe;
-    g.roi_x0 = s.d.roi_x0;
-    g.roi_y0 = s.d.roi_y0;
-    g.kx = s.d.kx;
-    g.ky = s.d.ky;
-    g.npix = s.npix;
-    g.M = s.M;
-    g.base = static_cast<const float2 *>(d_frames);
-    if (s.pushed == 0 && s.d.subtract_mean) {
-        CU_CHECK(p, launch_mean(g, n_frames, s.mu_hat, st), "provisional mean");
-        p->launches++;
+    const float2 *base = static_cast<const float2 *>(d_frames);
+    if (u.N <= 1) {
+        tacaw_status r = push_internal(p, p->s[u.first], base, n_frames, st);
+        if (r == TACAW_OK) u.pushed += n_frames;
+        return r;
     }
-    int done = 0;
-    while (done < n_frames) {
-        const int chunk = std::min(n_frames - done, s.ring - s.staged);
-        FrameGeom gc = g;
-        gc.base = g.base + (int64_t)done * g.pitch_frame;
-        if (p->in_place) {
-            for (int t = 0; t < chunk; ++t) s.h_frame_ptr[s.pushed + t] = gc.base + (int64_t)t * g.pitch_frame;
-        } else {
-            if (p->prec == TACAW_PREC_SPLIT_BF16)
-                CU_CHECK(p, launch_convert_split(gc, chunk, s.staged, p->bf, s.M_pad, s.mu_hat, s.sum_res, s.A_hi,
-                                                 s.A_lo, p->drain_kb > 0, st),
-                         "convert");
-            else
-                CU_CHECK(p, launch_convert_fp32(gc, chunk, s.staged, s.M_pad, s.mu_hat, s.sum_res, s.A32, st),
-                         "convert");
-            p->launches++;
-        }
-        s.staged += chunk;
-        s.pushed += chunk;
-        done += chunk;
-        if (s.staged == s.ring && s.pushed < s.T) {
-            tacaw_status r = run_flush(p, s, s.flushes == 0 ? FLUSH_STORE : FLUSH_ADD, nullptr, nullptr, st);
+    // Welch: every lane takes the part of this push inside its current segment, finishing
+    // segments (and starting the next ones of the lane) as their last frames arrive
+    const int64_t a = u.pushed, b = u.pushed + n_frames;
+    for (int l = 0; l < u.lanes; ++l) {
+        Stream &s = p->s[u.first + l];
+        while (s.seg < u.N) {
+            const int64_t s0 = s.seg * (int64_t)u.stride;
+            const int64_t lo = std::max(a, s0 + s.pushed), hi = std::min(b, s0 + u.L);
+            if (lo >= hi) break;
+            tacaw_status r = push_internal(p, s, base + (lo - a) * s.d.pitch_frame, (int)(hi - lo), st);
+            if (r != TACAW_OK) return r;
+            if (s.pushed < s.T) break;
+            r = finish_segment(p, u, s, st);
             if (r != TACAW_OK) return r;
         }
     }
+    u.pushed = b;
     return TACAW_OK;
 }
 
@@ -1010,9 +1127,9 @@ tacaw_status tacaw_check_errors(tacaw_plan_t p, void *stream) {
 
 tacaw_status tacaw_output_offsets(tacaw_plan_t p, int sid, int64_t *I_offset, int64_t *S_offset) {
     if (!p) return fail(TACAW_ERR_INVALID_ARG, "plan is NULL");
-    if (sid < 0 || sid >= (int)p->s.size()) return fail(TACAW_ERR_INVALID_ARG, "stream_id out of range");
-    if (I_offset) *I_offset = p->s[sid].I_off;
-    if (S_offset) *S_offset = p->s[sid].S_off;
+    if (sid < 0 || sid >= (int)p->us.size()) return fail(TACAW_ERR_INVALID_ARG, "stream_id out of range");
+    if (I_offset) *I_offset = p->us[sid].I_off;
+    if (S_offset) *S_offset = p->us[sid].S_off;
     return TACAW_OK;
 }
 
@@ -1024,6 +1141,11 @@ tacaw_status tacaw_reset(tacaw_plan_t p, void *stream) {
         CU_CHECK(p, cudaMemsetAsync(s.sum_res, 0, sizeof(double2) * s.M, st), "reset sums");
         CU_CHECK(p, cudaMemsetAsync(s.mu_hat, 0, sizeof(float2) * s.M, st), "reset mean");
         s.pushed = s.staged = s.stage_start = s.flushes = 0;
+        s.seg = s.lane;
+    }
+    for (auto &u : p->us) {
+        u.pushed = 0;
+        if (u.I_acc) CU_CHECK(p, cudaMemsetAsync(u.I_acc, 0, sizeof(float) * u.I_elems, st), "reset Welch average");
     }
     p->finalized = false;
     return TACAW_OK;
@@ -1033,7 +1155,7 @@ tacaw_status tacaw_plan_get_info(tacaw_plan_t p, tacaw_plan_info *info) {
     if (!p || !info) return fail(TACAW_ERR_INVALID_ARG, "NULL argument");
     info->device_bytes = p->bytes;
     info->k_stage = p->k_stage;
-    info->n_streams = (int)p->s.size();
+    info->n_streams = (int)p->us.size();
     info->precision = p->prec;
     info->I_elems = p->I_elems;
     info->S_elems = p->S_elems;
@@ -1099,9 +1221,10 @@ tacaw_status tacaw_backward(tacaw_plan_t p, int sid, const float *d_dL_dS, const
                             void *stream) {
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
-    if (sid < 0 || sid >= (int)p->s.size()) return fail(TACAW_ERR_INVALID_ARG, "stream_id %d out of range", sid);
+    if (sid < 0 || sid >= (int)p->us.size()) return fail(TACAW_ERR_INVALID_ARG, "stream_id %d out of range", sid);
     if (!d_dL_dS || !d_frames || !d_grad) return fail(TACAW_ERR_INVALID_ARG, "NULL device pointer");
-    Stream &s = p->s[sid];
+    if (p->us[sid].N > 1) return fail(TACAW_ERR_UNSUPPORTED, "the adjoint of a Welch-averaged stream is not built");
+    Stream &s = p->s[p->us[sid].first];
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     AdjointArgs a{};
     a.frames = static_cast<const float2 *>(d_frames);

@@ -63,6 +63,8 @@ struct EpiArgs {
     const float2 *dmu;         // [M] mean residual mu - mu_hat (null: none)
     const float2 *Wc;          // [Nw] window transform W(E_j) (FP64-derived)
     const float *bose;         // [Nw]
+    float out_scale;           // FINAL: I = out_scale * B(E) |Psi|^2 (Welch: 1/N per segment)
+    int out_add;               // FINAL: add into I_out instead of storing (Welch segments)
 };
 
 struct RowCtx {
@@ -134,7 +136,10 @@ __device__ __forceinline__ void epi_element_wb(const EpiArgs &a, const RowCtx &r
     pr -= r.dmu.x * W.x - r.dmu.y * W.y;
     pi -= r.dmu.x * W.y + r.dmu.y * W.x;
     const int64_t o = r.out_base + (int64_t)j * a.npix;
-    if (a.I_out) a.I_out[o] = (pr * pr + pi * pi) * bj;
+    if (a.I_out) {
+        const float v = (pr * pr + pi * pi) * bj * a.out_scale;
+        a.I_out[o] = a.out_add ? a.I_out[o] + v : v;
+    }
     if (a.Psi_out) a.Psi_out[o] = make_float2(pr, pi);
 }
 
@@ -197,7 +202,10 @@ __device__ __forceinline__ void epi_apply(const EpiArgs &a, const RowCtx &r, int
         pr -= r.dmu.x * W.x - r.dmu.y * W.y;
         pi -= r.dmu.x * W.y + r.dmu.y * W.x;
         const int64_t o = r.out_base + (int64_t)j * a.npix;
-        if (a.I_out) a.I_out[o] = (pr * pr + pi * pi) * bj;
+        if (a.I_out) {
+            const float v = (pr * pr + pi * pi) * bj * a.out_scale;
+            a.I_out[o] = a.out_add ? a.I_out[o] + v : v;
+        }
         if (a.Psi_out) a.Psi_out[o] = make_float2(pr, pi);
     }
 }

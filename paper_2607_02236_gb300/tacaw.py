@@ -49,7 +49,8 @@ class CStreamDesc(ctypes.Structure):
                 ("roi_x0", c_int), ("roi_y0", c_int), ("T", c_int), ("dt_fs", c_double),
                 ("n_omega", c_int), ("E_meV", POINTER(c_double)), ("fft_bins", c_int),
                 ("window", c_int), ("window_param", c_double), ("subtract_mean", c_int),
-                ("bose_T_K", c_double), ("n_detectors", c_int), ("detectors", POINTER(CDetector))]
+                ("bose_T_K", c_double), ("n_detectors", c_int), ("detectors", POINTER(CDetector)),
+                ("welch_segments", c_int), ("welch_stride", c_int)]
 
 
 class CPlanDesc(ctypes.Structure):
@@ -157,6 +158,9 @@ class StreamConfig:
     subtract_mean: bool = True
     bose_T_K: float = 0.0
     detectors: List[DetectorConfig] = field(default_factory=list)
+    # Welch averaging: N segments of T frames, `welch_stride` frames apart (0: T); 0/1: off
+    welch_segments: int = 0
+    welch_stride: int = 0
 
 
 class TacawPlan:
@@ -194,6 +198,7 @@ class TacawPlan:
             self._keep.append(dets)
             d.n_detectors = len(s.detectors)
             d.detectors = ctypes.cast(dets, POINTER(CDetector))
+            d.welch_segments, d.welch_stride = int(s.welch_segments), int(s.welch_stride)
         pd = CPlanDesc(len(streams), ctypes.cast(descs, POINTER(CStreamDesc)), PRECISIONS[precision],
                        ACCUMS[accum], int(hbm_budget_bytes), int(k_stage),
                        None if tune is None else os.fsencode(tune), int(tc_omega_tile),
