@@ -257,6 +257,17 @@ __global__ void mean_residual_kernel(int64_t M, int T, int sub, const double2 *s
 
 static inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// In-place frames: slot t of the table <- base + t * pitch_frame (t < n)
+__global__ void frame_table_kernel(const float2 **table, const float2 *base, int64_t pitch_frame, int n) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) table[t] = base + (int64_t)t * pitch_frame;
+}
+
+cudaError_t launch_frame_table(const float2 **table, const float2 *base, int64_t pitch_frame, int n, cudaStream_t st) {
+    frame_table_kernel<<<blocks_for(n, 128), 128, 0, st>>>(table, base, pitch_frame, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mean(const FrameGeom &g, int n, float2 *mu_hat, cudaStream_t st) {
     mean_kernel<<<blocks_for(g.M, 256), 256, 0, st>>>(g, n, mu_hat);
     return cudaGetLastError();

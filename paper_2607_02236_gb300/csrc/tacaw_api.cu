@@ -87,8 +87,8 @@ struct Stream {
     int tc_pair = 0;           // CTA-pair MMAs (cluster of 2, M = 256)
     bool tuned = false;        // tile picked by the autotuner
     // in-place frames: per staged frame, a pointer into the pushed buffer
-    const float2 **h_frame_ptr = nullptr;       // pinned, one slot per frame of the segment
-    const float2 **d_frame_ptr = nullptr;
+    const float2 **d_frame_ptr = nullptr;       // one slot per frame of the segment, written on
+                                                // the stream at push time (no host copy)
     // segment state
     int pushed = 0, staged = 0, stage_start = 0, flushes = 0;
     int64_t I_off = 0, S_off = 0;
@@ -155,10 +155,6 @@ bool dev_alloc(tacaw_plan_s *p, T **ptr, size_t count) {
 
 void free_all(tacaw_plan_s *p) {
     for (auto &s : p->s)
-        if (s.h_frame_ptr) {
-            cudaFreeHost(s.h_frame_ptr);
-            s.h_frame_ptr = nullptr;
-        }
     if (p->d_trace) cudaFree(p->d_trace);
     p->d_trace = nullptr;
     for (auto &e : p->ev) {
@@ -359,10 +355,6 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         TcPlanArgs a = tc_args(p, s, e);
         r = trace_buffer(p, (s.M_pad / kMTile) * s.n_wt, &a.trace);
         if (r != TACAW_OK) return r;
-        // the pointer table holds one slot per frame of the segment, so every flush of a
-        // captured segment reads its own slots when the graph is replayed
-        CU_CHECK(p, cudaMemcpyAsync(s.d_frame_ptr + s.stage_start, s.h_frame_ptr + s.stage_start,
-                                    sizeof(const float2 *) * n, cudaMemcpyHostToDevice, st), "frame table");
         TcDirectArgs d{};
         d.frame_ptr = s.d_frame_ptr + s.stage_start;
         d.n_frames = n;
@@ -504,12 +496,6 @@ tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
         s.tc_maps.resize(tc_maps_size());
         char eb[256];
         if (p->in_place) {
-            void *hp = nullptr;
-            if (cudaMallocHost(&hp, sizeof(const float2 *) * s.T) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(TACAW_ERR_OOM, "cudaMallocHost(frame table)");
-            }
-            s.h_frame_ptr = static_cast<const float2 **>(hp);
             if (!dev_alloc(p, &s.d_frame_ptr, s.T)) return fail(TACAW_ERR_OOM, "cudaMalloc(frame table)");
             if (!tc_make_maps_b(s.tc_maps.data(), s.B_hi, s.B_lo, s.Nw_pad, s.n_kb_T, 2 * s.wt, p->bf, eb, sizeof(eb)))
                 return fail(TACAW_ERR_CUDA, "%s", eb);
@@ -699,7 +685,10 @@ tacaw_status push_internal(tacaw_plan_s *p, Stream &s, const float2 *frames, int
         FrameGeom gc = g;
         gc.base = g.base + (int64_t)done * g.pitch_frame;
         if (p->in_place) {
-            for (int t = 0; t < chunk; ++t) s.h_frame_ptr[s.pushed + t] = gc.base + (int64_t)t * g.pitch_frame;
+            // the frames' addresses go to the device table by a kernel on the stream: ordered
+            // with the flushes that read them, and fixed inside a captured graph
+            CU_CHECK(p, launch_frame_table(s.d_frame_ptr + s.pushed, gc.base, g.pitch_frame, chunk, st), "frame table");
+            p->launches++;
         } else {
             if (p->prec == TACAW_PREC_SPLIT_BF16)
                 CU_CHECK(p, launch_convert_split(gc, chunk, s.staged, p->bf, s.M_pad, s.mu_hat, s.sum_res, s.A_hi,

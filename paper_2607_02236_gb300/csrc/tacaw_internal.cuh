@@ -234,6 +234,7 @@ cudaError_t launch_convert_split(const FrameGeom &g, int n, int s0, int bf, int6
                                  cudaStream_t st);
 cudaError_t launch_convert_fp32(const FrameGeom &g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
                                 double2 *sum_res, float2 *A32, cudaStream_t st);
+cudaError_t launch_frame_table(const float2 **table, const float2 *base, int64_t pitch_frame, int n, cudaStream_t st);
 cudaError_t launch_zero_tail_split(int64_t M_pad, int staged, int bf, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo,
                                    int swz, cudaStream_t st);
 cudaError_t launch_mean_residual(int64_t M, int T, int subtract_mean, const double2 *sum_res, float2 *dmu,
