@@ -69,6 +69,11 @@ def window(kind: str, T: int, param: float = 0.0) -> np.ndarray:
     gauss: w_n = exp(-1/2 ((n - T/2)/sigma)^2), sigma = param (default T/6)
     tukey: cosine tapers of total fractional width alpha = param on a flat top
            (periodic form: the symmetric window of length T+1 with its last sample dropped)
+    blackmanharris: 4-term cosine sum (Harris 1978), a = 0.35875, 0.48829, 0.14128, 0.01168
+    kaiser: I0(beta sqrt(1 - (2n/T - 1)^2)) / I0(beta), beta = param (App. A: 3 pi, 5 pi)
+    chebwin: Dolph-Chebyshev with side lobes param dB down (App. A: 100 dB)
+    The last three are App. A's "more aggressive" windows, in scipy's periodic forms (the
+    symmetric window of length T+1 without its last sample).
     T = 1 gives [1] for every kind (scipy's convention for length-1 windows).
     """
     n = np.arange(T, dtype=np.float64)
@@ -96,7 +101,59 @@ def window(kind: str, T: int, param: float = 0.0) -> np.ndarray:
             elif i > L - edge:
                 w[i] = 0.5 * (1 - np.cos(np.pi * (L - i) / edge))
         return w
+    if kind == "blackmanharris":
+        a = (0.35875, 0.48829, 0.14128, 0.01168)
+        x = 2.0 * np.pi * n / T
+        return a[0] - a[1] * np.cos(x) + a[2] * np.cos(2 * x) - a[3] * np.cos(3 * x)
+    if kind == "kaiser":
+        beta = float(param)
+        r = np.clip(1.0 - (2.0 * n / T - 1.0) ** 2, 0.0, None)
+        return _bessel_i0(beta * np.sqrt(r)) / _bessel_i0(np.array([beta]))[0]
+    if kind == "chebwin":
+        return _dolph_chebyshev(T + 1, float(param))[:T]
     raise ValueError(f"unknown window {kind!r}")
+
+
+def _bessel_i0(x) -> np.ndarray:
+    """Modified Bessel function I0 by its power series sum_k ((x/2)^k / k!)^2 (x <= ~50)."""
+    x = np.asarray(x, dtype=np.float64)
+    term = np.ones_like(x)
+    total = np.ones_like(x)
+    q = (x / 2.0) ** 2
+    for k in range(1, 200):
+        term = term * q / (k * k)
+        total = total + term
+        if np.all(term <= 1e-18 * total):
+            break
+    return total
+
+
+def _chebyshev_t(order: int, x) -> np.ndarray:
+    """Chebyshev polynomial T_order(x) for real x (cos / cosh forms)."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    inside = np.abs(x) <= 1.0
+    out[inside] = np.cos(order * np.arccos(x[inside]))
+    big = x > 1.0
+    out[big] = np.cosh(order * np.arccosh(x[big]))
+    neg = x < -1.0
+    out[neg] = (-1.0) ** order * np.cosh(order * np.arccosh(-x[neg]))
+    return out
+
+
+def _dolph_chebyshev(M: int, at_db: float) -> np.ndarray:
+    """Symmetric Dolph-Chebyshev window of M taps, side lobes at_db below the main lobe: its
+    frequency response is T_{M-1}(x0 cos(theta/2)) with T_{M-1}(x0) = 10^(at/20); the taps are
+    the inverse DFT of M samples of that response about the window's centre, scaled to max 1."""
+    if M == 1:
+        return np.ones(1)
+    r = 10.0 ** (at_db / 20.0)
+    x0 = np.cosh(np.arccosh(r) / (M - 1))
+    k = np.arange(M)
+    W = _chebyshev_t(M - 1, x0 * np.cos(np.pi * k / M))
+    n = np.arange(M)[:, None]
+    w = np.real(np.exp(2j * np.pi * k[None, :] * (n - (M - 1) / 2.0) / M) @ W) / M
+    return w / np.max(w)
 
 
 # ----------------------------------------------------------------------------------------------

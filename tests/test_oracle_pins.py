@@ -38,6 +38,31 @@ def test_windows_match_scipy_periodic(T):
         np.testing.assert_allclose(ours, ref, rtol=0, atol=1e-14, err_msg=f"{kind} T={T}")
 
 
+@pytest.mark.parametrize("T", [1, 2, 7, 8, 64, 65, 257, 2048])
+def test_appendix_windows_match_scipy_periodic(T):
+    """App. A's high-dynamic-range windows, which the paper defines by scipy's forms."""
+    pairs = [(("blackmanharris", 0.0), "blackmanharris"), (("kaiser", 3 * np.pi), ("kaiser", 3 * np.pi)),
+             (("kaiser", 5 * np.pi), ("kaiser", 5 * np.pi)), (("chebwin", 100.0), ("chebwin", 100.0)),
+             (("chebwin", 60.0), ("chebwin", 60.0))]
+    for (kind, p), sp in pairs:
+        ours = oracle.window(kind, T, p)
+        ref = scipy.signal.get_window(sp, T, fftbins=True)
+        np.testing.assert_allclose(ours, ref, rtol=0, atol=1e-12, err_msg=f"{kind} T={T}")
+
+
+def test_chebwin_sidelobes_at_the_stated_attenuation():
+    """Dolph-Chebyshev: every side lobe of the symmetric window's response is at_db down."""
+    M, at = 129, 100.0
+    w = oracle.tacaw_oracle._dolph_chebyshev(M, at)
+    H = np.abs(np.fft.fft(w, 64 * M))
+    H /= H[0]
+    # beyond the first null the response stays at -100 dB (equiripple), within rounding
+    k0 = np.argmax(H < 10 ** (-at / 20) * 1.001)
+    side = H[k0:len(H) // 2]
+    assert np.max(side) <= 10 ** (-at / 20) * (1 + 1e-6)
+    assert np.max(side) >= 10 ** (-at / 20) * (1 - 1e-3)
+
+
 def test_tukey_limits_are_rect_and_hann():
     # Sec. III.A: rectangular = Tukey alpha 0, Hann = Tukey alpha 1
     np.testing.assert_array_equal(oracle.window("tukey", 100, 0.0), oracle.window("rect", 100))
