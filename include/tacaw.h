@@ -55,8 +55,19 @@ typedef enum {
  *   RECT   w_t = 1
  *   HANN   w_t = 1/2 - 1/2 cos(2 pi t / T)
  *   GAUSS  w_t = exp(-1/2 ((t - T/2)/sigma)^2), sigma = window_param frames (<= 0: T/6)
- *   TUKEY  cosine tapers of total fractional width alpha = window_param               */
-typedef enum { TACAW_WIN_RECT = 0, TACAW_WIN_HANN = 1, TACAW_WIN_GAUSS = 2, TACAW_WIN_TUKEY = 3 } tacaw_window;
+ *   TUKEY  cosine tapers of total fractional width alpha = window_param
+ *   BLACKMANHARRIS  4-term cosine sum 0.35875, 0.48829, 0.14128, 0.01168 (Harris)
+ *   KAISER I0(beta sqrt(1 - (2t/T - 1)^2)) / I0(beta), beta = window_param (>= 0)
+ *   CHEBWIN Dolph-Chebyshev, side lobes window_param dB (> 0) below the main lobe      */
+typedef enum {
+    TACAW_WIN_RECT = 0,
+    TACAW_WIN_HANN = 1,
+    TACAW_WIN_GAUSS = 2,
+    TACAW_WIN_TUKEY = 3,
+    TACAW_WIN_BLACKMANHARRIS = 4,
+    TACAW_WIN_KAISER = 5,
+    TACAW_WIN_CHEBWIN = 6
+} tacaw_window;
 
 /* Arithmetic of the time->energy contraction.
  *   FP32        CUDA-core FFMA, FP32 accumulate.
@@ -101,7 +112,7 @@ typedef struct {
     const double *E_meV;       /* host array of Nw energies in meV (ignored when fft_bins) */
     int fft_bins;              /* != 0: E_j = j h / (T dt), j < Nw, exact integer phase */
     int window;                /* tacaw_window */
-    double window_param;       /* GAUSS sigma (frames), TUKEY alpha */
+    double window_param;       /* GAUSS sigma (frames), TUKEY alpha, KAISER beta, CHEBWIN dB */
     int subtract_mean;         /* != 0: remove the segment's time mean mu[k] */
     double bose_T_K;           /* > 0: multiply I by B(E) at this temperature; 0: B = 1 */
     int n_detectors;           /* D >= 0 */

@@ -9,9 +9,24 @@
 
 namespace tacaw {
 
-enum { WIN_RECT = 0, WIN_HANN = 1, WIN_GAUSS = 2, WIN_TUKEY = 3 };
+enum { WIN_RECT = 0, WIN_HANN = 1, WIN_GAUSS = 2, WIN_TUKEY = 3, WIN_BLACKMANHARRIS = 4, WIN_KAISER = 5,
+       WIN_CHEBWIN = 6 };
 
-__device__ double window_value(int kind, int T, double param, int t) {
+// Modified Bessel function I0 by its power series sum_k ((x/2)^k / k!)^2, FP64 (x <= 60)
+__device__ double bessel_i0(double x) {
+    const double q = 0.25 * x * x;
+    double term = 1.0, total = 1.0;
+    for (int k = 1; k < 200; ++k) {
+        term *= q / ((double)k * (double)k);
+        total += term;
+        if (term <= 1e-18 * total) break;
+    }
+    return total;
+}
+
+__device__ double window_value(const TableArgs &a, int t) {
+    const int kind = a.window, T = a.T;
+    const double param = a.window_param;
     if (T == 1) return 1.0;
     switch (kind) {
         case WIN_RECT:
@@ -32,6 +47,17 @@ __device__ double window_value(int kind, int T, double param, int t) {
             if ((double)t > (double)T - edge) return 0.5 * (1.0 - cospi((double)(T - t) / edge));
             return 1.0;
         }
+        case WIN_BLACKMANHARRIS: {
+            const double x = 2.0 * (double)t / (double)T;   // in units of pi
+            return 0.35875 - 0.48829 * cospi(x) + 0.14128 * cospi(2.0 * x) - 0.01168 * cospi(3.0 * x);
+        }
+        case WIN_KAISER: {
+            const double u = 2.0 * (double)t / (double)T - 1.0;
+            const double r = 1.0 - u * u;
+            return bessel_i0(param * sqrt(r > 0.0 ? r : 0.0)) / bessel_i0(param);
+        }
+        case WIN_CHEBWIN:
+            return a.win_table ? a.win_table[t] : 1.0;
     }
     return 1.0;
 }
@@ -67,7 +93,7 @@ __global__ void twiddles_split_kernel(TableArgs a, __nv_bfloat16 *B_hi, __nv_bfl
     if (j < a.Nw && t < a.T) {
         double c, s;
         twiddle(a, j, t, c, s);
-        double w = window_value(a.window, a.T, a.window_param, t);
+        double w = window_value(a, t);
         br = w * c;
         bi = -w * s;
     }
@@ -103,7 +129,7 @@ __global__ void twiddles_fp32_kernel(TableArgs a, float2 *B32) {
     if (j < a.Nw && t < a.T) {
         double c, s;
         twiddle(a, j, t, c, s);
-        double w = window_value(a.window, a.T, a.window_param, t);
+        double w = window_value(a, t);
         v = make_float2((float)(w * c), (float)(-w * s));
     }
     B32[(size_t)t * a.Nw_pad + j] = v;
@@ -116,7 +142,7 @@ __global__ void window_transform_kernel(TableArgs a, float2 *Wc) {
     for (int t = threadIdx.x; t < a.T; t += blockDim.x) {
         double c, s;
         twiddle(a, j, t, c, s);
-        double w = window_value(a.window, a.T, a.window_param, t);
+        double w = window_value(a, t);
         sr += w * c;
         si -= w * s;
     }
@@ -136,7 +162,7 @@ __global__ void window_transform_kernel(TableArgs a, float2 *Wc) {
 
 __global__ void window_values_kernel(TableArgs a, float *w) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < a.T) w[t] = (float)window_value(a.window, a.T, a.window_param, t);
+    if (t < a.T) w[t] = (float)window_value(a, t);
 }
 
 cudaError_t launch_twiddles_split(const TableArgs &t, __nv_bfloat16 *B_hi, __nv_bfloat16 *B_lo, cudaStream_t st) {

@@ -78,6 +78,7 @@ struct Stream {
     std::vector<unsigned char> tc_maps;
     int tc_cluster = 1;
     int stages = 0;            // shared-memory pipeline stages of this stream's tiles
+    double *win_table = nullptr;   // table-driven windows (Dolph-Chebyshev)
     // Welch lanes: internal stream `lane` of user stream `user` runs segments lane, lane +
     // lanes, ... one after another; its last flush adds out_scale * I into the user's average
     int user = 0, lane = 0;
@@ -184,7 +185,11 @@ tacaw_status validate_stream(const tacaw_stream_desc &d, int i) {
     if (d.n_omega < 1) return fail(TACAW_ERR_INVALID_ARG, "stream %d: n_omega must be >= 1", i);
     if (!d.fft_bins && !d.E_meV) return fail(TACAW_ERR_INVALID_ARG, "stream %d: E_meV is NULL", i);
     if (d.fft_bins && d.n_omega > d.T) return fail(TACAW_ERR_INVALID_ARG, "stream %d: fft_bins needs n_omega <= T", i);
-    if (d.window < TACAW_WIN_RECT || d.window > TACAW_WIN_TUKEY) return fail(TACAW_ERR_INVALID_ARG, "stream %d: bad window", i);
+    if (d.window < TACAW_WIN_RECT || d.window > TACAW_WIN_CHEBWIN) return fail(TACAW_ERR_INVALID_ARG, "stream %d: bad window", i);
+    if (d.window == TACAW_WIN_KAISER && !(d.window_param >= 0.0 && d.window_param <= 60.0))
+        return fail(TACAW_ERR_INVALID_ARG, "stream %d: Kaiser beta must be in [0, 60]", i);
+    if (d.window == TACAW_WIN_CHEBWIN && !(d.window_param > 0.0 && d.window_param <= 300.0))
+        return fail(TACAW_ERR_INVALID_ARG, "stream %d: Chebyshev attenuation must be in (0, 300] dB", i);
     if (d.roi_x0 < 0 || d.roi_y0 < 0) return fail(TACAW_ERR_INVALID_ARG, "stream %d: negative ROI origin", i);
     if (d.pitch_row < (int64_t)d.roi_x0 + d.kx) return fail(TACAW_ERR_INVALID_ARG, "stream %d: pitch_row < roi_x0 + kx", i);
     if (d.pitch_frame < d.pitch_row * (int64_t)(d.roi_y0 + d.ky) && d.T > 1)
@@ -453,6 +458,43 @@ tacaw_status final_flush_grouped(tacaw_plan_s *p, float *d_I, float2 *d_Psi, cud
     return TACAW_OK;
 }
 
+// Periodic Dolph-Chebyshev window of length T: the symmetric window of M = T + 1 taps without
+// its last tap.  The symmetric taps are the inverse DFT of M samples of the response
+// T_{M-1}(x0 cos(pi k / M)), T_{M-1}(x0) = 10^(at/20), taken about the window's centre and
+// scaled to a maximum of 1.  The phase pi k (2n - M + 1) / M is reduced exactly on a table of
+// 2M cosines.
+double chebyshev_t(int order, double x) {
+    if (std::fabs(x) <= 1.0) return std::cos(order * std::acos(x));
+    if (x > 1.0) return std::cosh(order * std::acosh(x));
+    return ((order & 1) ? -1.0 : 1.0) * std::cosh(order * std::acosh(-x));
+}
+
+std::vector<double> chebwin_periodic(int T, double at_db) {
+    const int M = T + 1;
+    std::vector<double> w(T, 1.0);
+    if (T <= 1) return w;
+    const double x0 = std::cosh(std::acosh(std::pow(10.0, at_db / 20.0)) / (M - 1));
+    std::vector<double> W(M), cs(2 * (size_t)M);
+    for (int k = 0; k < M; ++k) W[k] = chebyshev_t(M - 1, x0 * std::cos(M_PI * k / M));
+    for (int j = 0; j < 2 * M; ++j) cs[j] = std::cos(M_PI * j / M);
+    double mx = 0.0;
+    std::vector<double> full(M);
+    for (int n = 0; n < M; ++n) {
+        const int64_t step = (((int64_t)2 * n - M + 1) % (2 * M) + 2 * M) % (2 * M);
+        int64_t idx = 0;
+        double acc = 0.0;
+        for (int k = 0; k < M; ++k) {
+            acc += W[k] * cs[idx];
+            idx += step;
+            if (idx >= 2 * M) idx -= 2 * M;
+        }
+        full[n] = acc / M;
+        mx = std::max(mx, full[n]);
+    }
+    for (int n = 0; n < T; ++n) w[n] = full[n] / mx;
+    return w;
+}
+
 tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
     const tacaw_stream_desc &d = s.d;
     TableArgs ta{};
@@ -464,6 +506,13 @@ tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
     ta.window_param = d.window_param;
     ta.fft_bins = d.fft_bins;
     ta.block_frames = p->bf;
+    if (d.window == TACAW_WIN_CHEBWIN) {
+        // Dolph-Chebyshev taps (a transform over the whole window): computed here in FP64
+        const std::vector<double> w = chebwin_periodic(s.T, d.window_param);
+        if (!dev_alloc(p, &s.win_table, (size_t)s.T)) return fail(TACAW_ERR_OOM, "cudaMalloc(window table)");
+        CU_CHECK(p, cudaMemcpy(s.win_table, w.data(), sizeof(double) * s.T, cudaMemcpyHostToDevice), "copy window");
+        ta.win_table = s.win_table;
+    }
     ta.swz = p->drain_kb > 0 ? 1 : 0;   // the drained kernel copies pre-swizzled blocks
     // cycles per frame c_j = E_j dt / h (FP64)
     std::vector<double> cj(s.Nw), E(s.Nw);

@@ -221,6 +221,7 @@ struct TableArgs {
     const double *cj;          // device, cycles per frame per energy (explicit grid)
     int block_frames;          // split-path staging block (8, 16 or 32 frames)
     int swz;                   // split path: rows stored pre-swizzled (see convert_split_kernel)
+    const double *win_table;   // table-driven windows (Dolph-Chebyshev): w_t, t < T
 };
 
 cudaError_t launch_twiddles_split(const TableArgs &t, __nv_bfloat16 *B_hi, __nv_bfloat16 *B_lo, cudaStream_t st);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libtacaw.so")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_OVERFLOW, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = ["OK", "INVALID_ARG", "OOM", "CUDA", "STATE", "OVERFLOW", "TIMEOUT", "UNSUPPORTED"]
-WINDOWS = {"rect": 0, "hann": 1, "gauss": 2, "tukey": 3}
+WINDOWS = {"rect": 0, "hann": 1, "gauss": 2, "tukey": 3, "blackmanharris": 4, "kaiser": 5, "chebwin": 6}
 PRECISIONS = {"fp32": 0, "split_bf16": 1}
 ACCUMS = {"kahan": 0, "fp64": 1}
 DET_KINDS = {"circular": 0, "annular": 1, "mask": 2}

@@ -50,8 +50,9 @@ class StreamSpec:
     fft_bins: int = 0
     n_omega: int = 0
     E_max_meV: float = 120.0
-    window: str = "hann"          # rect | hann | gauss | tukey
-    window_param: float = 0.0     # gauss: sigma in frames (0 -> T/6); tukey: alpha
+    window: str = "hann"          # rect | hann | gauss | tukey | blackmanharris | kaiser | chebwin
+    window_param: float = 0.0     # gauss: sigma in frames (0 -> T/6); tukey: alpha; kaiser: beta;
+                                  # chebwin: side-lobe attenuation in dB
     subtract_mean: bool = True
     bose_T_K: float = 0.0
     detectors: Tuple[Detector, ...] = (Detector(),)

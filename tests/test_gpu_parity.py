@@ -225,3 +225,16 @@ def test_drained_accumulator_tilings(drain, wt, bf, k_stage):
     info = out["info"]
     assert info["tc_drain_frames"] == max(bf, drain // bf * bf) and info["tc_accumulators"] == 1
     assert info["tc_cluster"] == 1 and info["tc_block_frames"] == bf
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split_bf16"])
+@pytest.mark.parametrize("win,param", [("blackmanharris", 0.0), ("kaiser", 3 * np.pi), ("kaiser", 5 * np.pi),
+                                       ("chebwin", 100.0)])
+def test_appendix_windows(win, param, precision):
+    """App. A's windows (Blackman-Harris, Kaiser beta = 3 pi / 5 pi, Dolph-Chebyshev 100 dB) on a
+    ragged segment (T = 150) and an off-grid energy list."""
+    spec = StreamSpec(P=2, Kx=20, Ky=24, T=150, Tc=48, n_omega=60, E_max_meV=120.0, window=win, window_param=param,
+                      detectors=(Detector("circular", 0, 0, -1, 5.0),))
+    fr = random_frames(2, 150, 24, 20, seed=31)
+    out, ref, e = check(spec, fr, precision)
+    print(f"{win} {param:.3g} {precision}: {e:.3g}")
