@@ -482,6 +482,20 @@ __device__ __forceinline__ void tc_epilogue_drained(const TcPlanArgs &a, const R
     }
 }
 
+// Flush epilogue of the split drained form: the tile's result is all in the running sums.
+template <int KIND>
+__device__ __forceinline__ void tc_epilogue_regs(const TcPlanArgs &a, const RowCtx &row, int col0, int cols,
+                                                 int jbase, const float (&sum)[kDrainCols]) {
+    if (!row.valid) return;
+#pragma unroll
+    for (int i = 0; i < kDrainCols / 2; ++i) {
+        const int c = 2 * i;
+        const int j = jbase + ((col0 + c) >> 1);
+        if (c < cols && j < a.e.Nw)
+            epi_apply<KIND>(a.e, row, j, sum[c], sum[c + 1], __ldg(a.e.Wc + j), __ldg(a.e.bose + j));
+    }
+}
+
 // Body of the staged contraction kernel.  PAIR: the CTA-pair form -- clusters of two CTAs run
 // M = 256 MMAs (tcgen05 cta_group::2) issued by the even CTA: each CTA stages its own 128 rows
 // of A and half of the tile's B rows, so each SM reads half the B operand per MMA; both CTAs
@@ -815,7 +829,15 @@ __device__ __forceinline__ int group_entry(const TcGroup &g, int64_t tile) {
     return gi;
 }
 
-__global__ void __maxnreg__(168) flush_tc_drain_kernel(const __grid_constant__ TcGroup g) {
+// FORM 2 (split): hi*hi goes to accumulator H, the small products hi*lo + lo*hi to S (TMEM
+// columns 256 on).  Only H is drained, every chunk, into the FP32 registers (the small terms
+// carry ~2^-8 of the magnitude, so their truncation stays far below the bound); at the end of
+// a tile the last chunk of H and all of S are added to the registers and both accumulators
+// are released at once, the flush epilogue then runs from registers while the next tile
+// accumulates.  The MMA thread issues a stage's small products before it waits for H to be
+// drained, so the tensor core has work while the epilogue warps empty H.
+template <int FORM>
+__device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int bf = g.e[0].args.bf, stages = g.stages, n_max = g.n_max;
@@ -826,7 +848,7 @@ __global__ void __maxnreg__(168) flush_tc_drain_kernel(const __grid_constant__ T
     TcShared *sh = reinterpret_cast<TcShared *>(base + (size_t)stages * stage_bytes);
     const uint32_t base_s = smem_u32(base);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t ncols = tc_tmem_cols(2 * n_max);
+    const uint32_t ncols = FORM == 2 ? 512u : tc_tmem_cols(2 * n_max);
     const int64_t n_tiles = g.tiles;
     uint32_t *err = g.e[0].args.err;
     unsigned long long *trace = g.e[0].args.trace ? g.e[0].args.trace + (size_t)blockIdx.x * kTraceWords : nullptr;
@@ -897,6 +919,84 @@ __global__ void __maxnreg__(168) flush_tc_drain_kernel(const __grid_constant__ T
                         atomicOr(err, DEVERR_TIMEOUT_DRAIN);
             }
         }
+    } else if (warp == 1 && FORM == 2) {
+        if (lane == 0) {
+            const int ksteps = bf / 8;
+            int64_t q = 0, hc = 0, tiles = 0;         // stages consumed, H drains requested, tiles
+            bool stop = false;
+            uint64_t wait_drain = 0, wait_full = 0;
+            const uint32_t accH = tmem, accS = tmem + 256u;
+            for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x, ++tiles) {
+                const TcGroupEntry &en = g.e[group_entry(g, t)];
+                const int N = en.args.N, n_kb = en.args.n_kb, cb = en.args.drain_kb;
+                const uint32_t id = idesc_bf16_f32(kMTile, N);
+                if (tiles > 0) {
+                    // the previous tile's H and S must be in registers before they are reused
+                    const uint64_t w0 = trace ? globaltimer() : 0;
+                    if (!mbar_wait(smem_u32(&sh->chunk_free[1]), (uint32_t)((tiles - 1) & 1), abort_flag)) {
+                        if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    if (trace) wait_drain += globaltimer() - w0;
+                    tc_fence_after();
+                }
+                for (int kb = 0; kb < n_kb; ++kb, ++q) {
+                    const int kc = kb % cb;
+                    const int s = (int)(q % stages);
+                    const uint64_t w1 = trace ? globaltimer() : 0;
+                    if (!mbar_wait(smem_u32(&sh->full[s]), (uint32_t)(q / stages) & 1u, abort_flag)) {
+                        if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_FULL);
+                        *abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    if (trace && q > 0) wait_full += globaltimer() - w1;
+                    tc_fence_after();
+                    if (trace && q == 0) trace[2] = globaltimer();
+                    const uint32_t st = base_s + (uint32_t)s * stage_bytes;
+                    const uint64_t dAhi0 = sdesc_k(st, RB);
+                    const uint64_t dAlo0 = sdesc_k(st + kABytes, RB);
+                    const uint64_t dBhi0 = sdesc_k(st + 2 * kABytes, RB);
+                    const uint64_t dBlo0 = sdesc_k(st + 2 * kABytes + b_pad, RB);
+                    // small products of the whole stage first (S never waits inside a tile)
+                    for (int ks = 0; ks < ksteps; ++ks) {
+                        const uint64_t adv = (uint64_t)(2 * ks);
+                        mma_bf16_ss(accS, dAhi0 + adv, dBlo0 + adv, id, (kb == 0 && ks == 0) ? 0u : 1u);
+                        mma_bf16_ss(accS, dAlo0 + adv, dBhi0 + adv, id, 1u);
+                    }
+                    if (kc == 0 && kb > 0) {
+                        // the previous chunk of H must be drained before this chunk overwrites it
+                        const uint64_t w0 = trace ? globaltimer() : 0;
+                        if (!mbar_wait(smem_u32(&sh->chunk_free[0]), (uint32_t)((hc - 1) & 1), abort_flag)) {
+                            if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
+                            *abort_flag = 1;
+                            stop = true;
+                            break;
+                        }
+                        if (trace) wait_drain += globaltimer() - w0;
+                        tc_fence_after();
+                    }
+                    for (int ks = 0; ks < ksteps; ++ks) {
+                        const uint64_t adv = (uint64_t)(2 * ks);
+                        mma_bf16_ss(accH, dAhi0 + adv, dBhi0 + adv, id, (kc == 0 && ks == 0) ? 0u : 1u);
+                    }
+                    mma_commit(smem_u32(&sh->empty[s]));
+                    if (kc == cb - 1 && kb != n_kb - 1) {
+                        mma_commit(smem_u32(&sh->chunk_full[0]));   // a finished chunk of H
+                        ++hc;
+                    }
+                }
+                if (stop) break;
+                mma_commit(smem_u32(&sh->chunk_full[1]));           // the tile's last H and S
+            }
+            mma_commit(smem_u32(&sh->tmem_full));   // always: nothing writes TMEM after this
+            if (trace) {
+                trace[3] = globaltimer();
+                trace[4] = wait_drain;
+                trace[5] = wait_full;
+            }
+        }
     } else if (warp == 1) {
         if (lane == 0) {
             const int ksteps = bf / 8;
@@ -959,6 +1059,65 @@ __global__ void __maxnreg__(168) flush_tc_drain_kernel(const __grid_constant__ T
                 trace[5] = wait_full;
             }
         }
+    } else if (FORM == 2) {
+        // epilogue warps 2..9: TMEM lane quarter q4 = warp % 4, column half h
+        const int q4 = warp & 3, h = (warp - 2) >> 2;
+        float sum[kDrainCols];
+        int64_t hc = 0, tiles = 0;                    // H drains done, tiles done
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tiles) {
+            const TcGroupEntry &en = g.e[group_entry(g, t)];
+            const TcPlanArgs &a = en.args;
+            const int64_t lt = t - en.cta_begin;
+            const int wtile = (int)(lt % a.n_wt);
+            const int m0 = (int)(lt / a.n_wt) * kMTile;
+            const int cols = a.wt;                    // N / 2 columns per thread
+            const int col0 = h * cols;
+            const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)col0;
+            const int n_chunks = (a.n_kb + a.drain_kb - 1) / a.drain_kb;
+#pragma unroll
+            for (int i = 0; i < kDrainCols; ++i) sum[i] = 0.f;
+            for (int lc = 0; lc + 1 < n_chunks; ++lc, ++hc) {
+                if (!mbar_wait(smem_u32(&sh->chunk_full[0]), (uint32_t)(hc & 1), abort_flag)) {
+                    if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                drain_add(sum, lane_base, cols);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&sh->chunk_free[0]));
+            }
+            if (!ok) break;
+            if (!mbar_wait(smem_u32(&sh->chunk_full[1]), (uint32_t)(tiles & 1), abort_flag)) {
+                if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
+                *abort_flag = 1;
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            drain_add(sum, lane_base, cols);          // the last chunk of H
+            drain_add(sum, lane_base + 256u, cols);   // S
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&sh->chunk_free[1]));
+            const RowCtx row = make_row(a.e, (int64_t)m0 + q4 * 32 + lane);
+            const int jbase = wtile * a.wt;
+            switch (epi_kind(a.e)) {
+                case EPI_FINAL: tc_epilogue_regs<EPI_FINAL>(a, row, col0, cols, jbase, sum); break;
+                case EPI_FINAL_KAHAN: tc_epilogue_regs<EPI_FINAL_KAHAN>(a, row, col0, cols, jbase, sum); break;
+                case EPI_FINAL_FP64: tc_epilogue_regs<EPI_FINAL_FP64>(a, row, col0, cols, jbase, sum); break;
+                case EPI_STORE_KAHAN: tc_epilogue_regs<EPI_STORE_KAHAN>(a, row, col0, cols, jbase, sum); break;
+                case EPI_STORE_FP64: tc_epilogue_regs<EPI_STORE_FP64>(a, row, col0, cols, jbase, sum); break;
+                case EPI_ADD_KAHAN: tc_epilogue_regs<EPI_ADD_KAHAN>(a, row, col0, cols, jbase, sum); break;
+                default: tc_epilogue_regs<EPI_ADD_FP64>(a, row, col0, cols, jbase, sum); break;
+            }
+        }
+        // always wait (bounded) for the last commit: no MMA may still write TMEM at release
+        if (!mbar_wait(smem_u32(&sh->tmem_full), 0u, nullptr)) atomicOr(err, DEVERR_TIMEOUT_TMEM);
+        tc_fence_after();
     } else {
         // epilogue warps 2..9: TMEM lane quarter q4 = warp % 4, column half h
         const int q4 = warp & 3, h = (warp - 2) >> 2;
@@ -1018,6 +1177,13 @@ __global__ void __maxnreg__(168) flush_tc_drain_kernel(const __grid_constant__ T
         tmem_dealloc(tmem, ncols);
     }
     if (trace && threadIdx.x == 0) trace[6] = globaltimer();
+}
+
+__global__ void __maxnreg__(168) flush_tc_drain_kernel(const __grid_constant__ TcGroup g) {
+    flush_tc_drain_body<1>(g);
+}
+__global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ TcGroup g) {
+    flush_tc_drain_body<2>(g);
 }
 
 // --------------------------------------------------------------------------------------
@@ -1355,7 +1521,8 @@ cudaError_t launch_flush_tc_direct(const TcPlanArgs &a, const TcDirectArgs &d, c
 // Co-resident CTAs of the contraction kernel for a cluster size (0 on error).
 int tc_resident_ctas(int N, int bf, int stages, int cluster, int pair, int drain) {
     const size_t smem = tc_smem_bytes(N, bf, stages, pair);
-    auto kern = drain ? flush_tc_drain_kernel : (pair ? flush_tc_pair_kernel : flush_tc_kernel);
+    auto kern = drain ? (drain == 2 ? flush_tc_drain2_kernel : flush_tc_drain_kernel)
+                      : (pair ? flush_tc_pair_kernel : flush_tc_kernel);
     if (pair) cluster = 2;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
@@ -1392,13 +1559,15 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *map
     const int C = args[0].cluster;
     const int pair = args[0].pair;
     const bool drain = args[0].drain_kb > 0;
+    const int form = args[0].drain_form == 2 ? 2 : 1;
     size_t smem = 0;
     int64_t total = 0;
     for (int i = 0; i < n; ++i) {
         // the pair form needs clusters of 2 and tiles of at most 256 columns (one MMA each);
         // the drained form one CTA per tile and two buffers of at most 256 columns
         if (args[i].cluster != C || args[i].bf != args[0].bf || args[i].pair != pair ||
-            (args[i].drain_kb > 0) != drain || (pair && (C != 2 || args[i].N > 256 || args[i].N % 32)) ||
+            (args[i].drain_kb > 0) != drain || (drain && (args[i].drain_form == 2 ? 2 : 1) != form) ||
+            (pair && (C != 2 || args[i].N > 256 || args[i].N % 32)) ||
             (drain && (C != 1 || pair || args[i].wt > kDrainCols))) {
             delete g;
             return cudaErrorInvalidValue;
@@ -1430,17 +1599,17 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *map
         int dev = 0, sms = 0, occ = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(flush_tc_drain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, flush_tc_drain_kernel, 320, smem);
+        auto dk = form == 2 ? flush_tc_drain2_kernel : flush_tc_drain_kernel;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(dk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dk, 320, smem);
         if (e != cudaSuccess || g->stages < 2 || n_max > 2 * kDrainCols || occ < 1) {
             delete g;
             return e != cudaSuccess ? e : cudaErrorInvalidConfiguration;
         }
         if ((int64_t)occ * sms < total) grid = (unsigned)(occ * sms);
     }
-    auto kern = drain ? flush_tc_drain_kernel : (pair ? flush_tc_pair_kernel : flush_tc_kernel);
+    auto kern = drain ? (form == 2 ? flush_tc_drain2_kernel : flush_tc_drain_kernel)
+                      : (pair ? flush_tc_pair_kernel : flush_tc_kernel);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
         cudaLaunchConfig_t cfg = {};

@@ -142,7 +142,7 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
             if (sh.drain_kb && C != 1) continue;
             int br, nb;
             if (!tc_b_boxes(N, C, &br, &nb) || (C > 1 && n_mt < 2 * C)) continue;
-            const int R = tc_resident_ctas(N, sh.bf, stages, C, 0, sh.drain_kb > 0);
+            const int R = tc_resident_ctas(N, sh.bf, stages, C, 0, sh.drain_kb > 0 ? sh.drain_form : 0);
             if (R <= 0) continue;
             Cand c{w, n_wt, C, stages, R, 0};
             // one wave: at most R CTAs, whole clusters, no more M tiles than the stream has
@@ -229,6 +229,7 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
         a.n_big = sh.n_acc == 3 ? 2 : 1;
         a.cluster = c.C;
         a.drain_kb = sh.drain_kb;
+        a.drain_form = sh.drain_form;
         a.A_hi = a_hi.p;
         a.A_lo = a_lo.p;
         a.B_hi = b_hi.p;

@@ -115,6 +115,7 @@ struct tacaw_plan_s {
     int stages = 0;
     int tc_acc = 3;
     int drain_kb = 0;          // drained form: staging blocks per accumulator chunk (0: off)
+    int drain_form = 1;
     int bf = 8;                // frames per staged operand row (split path)
     int tc_prefetch = 0;       // L2 prefetch distance of operand A in staging blocks
     bool in_place = false;     // the contraction reads pushed frames directly
@@ -293,6 +294,7 @@ TcPlanArgs tc_args(tacaw_plan_s *p, const Stream &s, const EpiArgs &e) {
     a.split = p->tc_acc > 1 ? 1 : 0;
     a.n_big = p->tc_acc == 3 ? 2 : 1;
     a.drain_kb = p->in_place ? 0 : p->drain_kb;
+    a.drain_form = p->drain_form;
     a.A_hi = s.A_hi;
     a.A_lo = s.A_lo;
     a.B_hi = s.B_hi;
@@ -803,9 +805,9 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     if (desc->tc_pair < 0 || desc->tc_pair > 2) return fail(TACAW_ERR_INVALID_ARG, "tc_pair must be 0, 1 or 2");
     if (desc->tc_drain_frames < 0 || desc->tc_drain_frames % 8)
         return fail(TACAW_ERR_INVALID_ARG, "tc_drain_frames must be a non-negative multiple of 8");
-    if (desc->tc_drain_frames && (desc->tc_pair || desc->tc_cluster > 1 || desc->tc_accumulators > 1))
-        return fail(TACAW_ERR_INVALID_ARG, "tc_drain_frames runs one accumulator on single CTAs "
-                    "(tc_pair 0, tc_cluster 0/1, tc_accumulators 0/1)");
+    if (desc->tc_drain_frames && (desc->tc_pair || desc->tc_cluster > 1 || desc->tc_accumulators > 2))
+        return fail(TACAW_ERR_INVALID_ARG, "tc_drain_frames runs on single CTAs with one or two accumulators "
+                    "(tc_pair 0, tc_cluster 0/1, tc_accumulators 0/1/2)");
     if (desc->tc_omega_tile < 0 || desc->tc_omega_tile % 8)
         return fail(TACAW_ERR_INVALID_ARG, "tc_omega_tile must be a multiple of 8");
     if (desc->tc_block_frames != 0 && desc->tc_block_frames != 8 && desc->tc_block_frames != 16 &&
@@ -822,7 +824,10 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         desc->tc_drain_frames ? desc->tc_drain_frames
                               : (desc->tc_accumulators == 0 && !desc->tc_pair && desc->tc_cluster <= 1 ? 256 : 0);
     const bool drained = drain_frames > 0 && desc->precision == TACAW_PREC_SPLIT_BF16 && !desc->frames_in_place;
-    if (drained) p->tc_acc = 1;
+    // drained forms: 1 = all products in one double-buffered accumulator, 2 = hi*hi drained, the
+    // small products in a second accumulator
+    if (drained) p->drain_form = desc->tc_accumulators == 2 ? 2 : 1;
+    if (drained) p->tc_acc = p->drain_form;
     // TMEM columns per tile: accumulators side by side (the drained form holds two buffers)
     const int tile_acc = drained ? 2 : p->tc_acc;
     if (desc->frames_in_place && desc->precision != TACAW_PREC_SPLIT_BF16) {
@@ -921,6 +926,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
                 sh.n_acc = p->tc_acc;
                 sh.wt_max = drained ? std::min(kDrainMaxOmegaTile, omega_tile_max(tile_acc)) : omega_tile_max(tile_acc);
                 sh.drain_kb = drained ? std::max(1, drain_frames / p->bf) : 0;
+                sh.drain_form = p->drain_form;
                 sh.fixed_wt = desc->tc_omega_tile ? s.wt : 0;
                 sh.fixed_cluster = desc->tc_cluster;
                 sh.multi = desc->n_streams > 1;

@@ -264,6 +264,8 @@ struct TcPlanArgs {
     int pair;                  // CTA-pair MMAs (M = 256 over a cluster of 2, B rows split; N <= 256):
                                // 1 = the odd CTA relays its stage-full events, 2 = its copies
                                // complete directly on the even CTA's barriers; 0 = off
+    int drain_form;            // drained kernel: 1 one accumulator, double-buffered; 2 hi*hi drained,
+                               // small products in a second accumulator for the whole tile
     int drain_kb;              // > 0: one double-buffered accumulator drained into FP32
                                // registers every drain_kb staging blocks (wt <= 112); the
                                // operands are pre-swizzled and copied as contiguous blocks:
@@ -317,6 +319,7 @@ struct TuneShape {
     int fixed_wt, fixed_cluster;   // 0: tuned
     bool multi;                // several streams share the final launch
     int drain_kb;              // drained form (single CTAs, one double-buffered accumulator)
+    int drain_form;            // 1 or 2 (see TcPlanArgs::drain_form)
 };
 struct TuneCand {
     int wt, cluster;

@@ -211,19 +211,21 @@ def test_cta_pair_tilings(acc, wt, bf, pair):
     assert (info["tc_accumulators"], info["tc_pair"], info["tc_cluster"], info["tc_block_frames"]) == (acc, pair, 2, bf)
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("drain,wt,bf,k_stage", [(32, 0, 8, 0), (64, 0, 32, 0), (1024, 0, 16, 0), (16, 112, 16, 0),
                                                  (24, 40, 8, 0), (32, 0, 32, 64), (64, 72, 16, 96)])
-def test_drained_accumulator_tilings(drain, wt, bf, k_stage):
+def test_drained_accumulator_tilings(drain, wt, bf, k_stage, form):
     """Drained form: one double-buffered accumulator emptied into FP32 registers every `drain`
     frames (chunks that do not divide the flush, a single chunk, the widest 112-energy tile,
-    several flushes on top of the cross-flush accumulators); 31 ragged row tiles, T=168."""
+    several flushes on top of the cross-flush accumulators); 31 ragged row tiles, T=168.
+    form 2: only hi*hi is drained, the small products accumulate apart for the whole tile."""
     spec = StreamSpec(P=3, Kx=36, Ky=36, T=168, Tc=40, n_omega=150, E_max_meV=120.0, window="hann", n_modes=6,
                       noise=1e-3, detectors=(Detector("circular", 0, 0, -1, 6.0),))
     fr = frames.frames(spec, 10, 0, spec.T)
     out, ref, e = check(spec, fr, "split_bf16", tc_drain_frames=drain, tc_omega_tile=wt, tc_block_frames=bf,
-                        k_stage=k_stage)
+                        k_stage=k_stage, tc_accumulators=form)
     info = out["info"]
-    assert info["tc_drain_frames"] == max(bf, drain // bf * bf) and info["tc_accumulators"] == 1
+    assert info["tc_drain_frames"] == max(bf, drain // bf * bf) and info["tc_accumulators"] == form
     assert info["tc_cluster"] == 1 and info["tc_block_frames"] == bf
 
 
