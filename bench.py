@@ -484,8 +484,8 @@ def main():
                       "setup_us": round(float(np.median(tr[:, 1] - tr[:, 0])) / 1e3, 2),
                       "first_operands_us": round(float(np.median(tr[:, 2] - tr[:, 1])) / 1e3, 2),
                       "mma_span_us": round(float(np.median(tr[:, 3] - tr[:, 2])) / 1e3, 1),
-                      "mma_wait_drained_buffer_us": round(float(np.median(tr[:, 4])) / 1e3, 1),
-                      "mma_wait_operands_us": round(float(np.median(tr[:, 5])) / 1e3, 1),
+                      "tiles_per_cta": int(np.median(tr[:, 4])), "chunks_per_cta": int(np.median(tr[:, 5])),
+                      "mma_us_per_tile": round(float(np.median((tr[:, 3] - tr[:, 2]) / np.maximum(tr[:, 4], 1))) / 1e3, 2),
                       "tail_after_last_mma_us": round(float(np.median(tr[:, 6] - tr[:, 3])) / 1e3, 2),
                       "unit": "median per CTA"}
             tr = None

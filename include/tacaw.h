@@ -277,8 +277,8 @@ tacaw_status tacaw_plan_get_info(tacaw_plan_t plan, tacaw_plan_info *info);
  * the SM id; tacaw_flush_trace copies the last flush's words (n_ctas x 8, CTA-major) to
  * host_out (at most max_ctas CTAs) and reports the CTA count.  The drained (persistent)
  * form writes one row per launched CTA (rows of tiles it did not launch stay zero): entry,
- * set-up done, first operands landed, last MMA issued, ns the MMA thread waited for
- * drained accumulator buffers, ns it waited for operands, exit, SM id.                    */
+ * set-up done, first operands landed, last MMA issued, tiles processed, accumulator chunks
+ * started, exit, SM id.                                                                   */
 tacaw_status tacaw_set_timing(tacaw_plan_t plan, int enable);
 tacaw_status tacaw_kernel_time_ms(tacaw_plan_t plan, double *flush_ms, int64_t *flush_launches,
                                   int reset);

@@ -880,9 +880,13 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
     volatile int *abort_flag = &sh->abort_flag;
     if (trace && threadIdx.x == 0) trace[1] = globaltimer();
 
+    // Ring position: slot s and its use parity advance by one per staging block, across tiles
+    // (no divisions in the issue loops: the single MMA thread's loop sits on the critical path).
     if (warp == 0) {
         if (lane == 0) {
-            int64_t q = 0;                            // stages issued by this CTA
+            int s = 0;
+            uint32_t ph = 0;                          // parity of the current use of slot s
+            int issued = 0;                           // copies in flight that may still land
             for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
                 const int gi = group_entry(g, t);
                 const TcGroupEntry &en = g.e[gi];
@@ -891,10 +895,14 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
                 const int m0 = (int)(lt / en.args.n_wt) * kMTile;
                 const int N = en.args.N;
                 const uint32_t tx_bytes = 2u * kABytes + 2u * (uint32_t)N * RB;
-                for (int kb = 0; kb < en.args.n_kb; ++kb, ++q) {
-                    const int s = (int)(q % stages);
-                    const uint32_t use = (uint32_t)(q / stages);
-                    if (!mbar_wait(smem_u32(&sh->empty[s]), (use & 1u) ^ 1u, abort_flag)) {
+                const uint8_t *pAhi = static_cast<const uint8_t *>(en.args.A_hi) + (size_t)m0 * RB;
+                const uint8_t *pAlo = static_cast<const uint8_t *>(en.args.A_lo) + (size_t)m0 * RB;
+                const size_t b0 = ((size_t)en.args.kbB0 * (size_t)en.args.b_rows + (size_t)wtile * N) * RB;
+                const uint8_t *pBhi = static_cast<const uint8_t *>(en.args.B_hi) + b0;
+                const uint8_t *pBlo = static_cast<const uint8_t *>(en.args.B_lo) + b0;
+                const size_t a_step = (size_t)en.args.a_rows * RB, b_step = (size_t)en.args.b_rows * RB;
+                for (int kb = 0; kb < en.args.n_kb; ++kb) {
+                    if (!mbar_wait(smem_u32(&sh->empty[s]), ph ^ 1u, abort_flag)) {
                         if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_EMPTY);
                         *abort_flag = 1;
                         break;
@@ -903,28 +911,43 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
                     const uint32_t st = base_s + (uint32_t)s * stage_bytes;
                     mbar_arrive_expect_tx(full, tx_bytes);
                     // the tables are pre-swizzled: each operand block is one contiguous copy
-                    const size_t ao = ((size_t)kb * (size_t)en.args.a_rows + (size_t)m0) * RB;
-                    const size_t bo = ((size_t)(en.args.kbB0 + kb) * (size_t)en.args.b_rows + (size_t)wtile * N) * RB;
-                    bulk_load(st, static_cast<const uint8_t *>(en.args.A_hi) + ao, kABytes, full);
-                    bulk_load(st + kABytes, static_cast<const uint8_t *>(en.args.A_lo) + ao, kABytes, full);
-                    bulk_load(st + 2 * kABytes, static_cast<const uint8_t *>(en.args.B_hi) + bo, (uint32_t)N * RB, full);
-                    bulk_load(st + 2 * kABytes + b_pad, static_cast<const uint8_t *>(en.args.B_lo) + bo,
-                              (uint32_t)N * RB, full);
+                    bulk_load(st, pAhi, kABytes, full);
+                    bulk_load(st + kABytes, pAlo, kABytes, full);
+                    bulk_load(st + 2 * kABytes, pBhi, (uint32_t)N * RB, full);
+                    bulk_load(st + 2 * kABytes + b_pad, pBlo, (uint32_t)N * RB, full);
+                    pAhi += a_step;
+                    pAlo += a_step;
+                    pBhi += b_step;
+                    pBlo += b_step;
+                    issued = issued < stages ? issued + 1 : stages;
+                    if (++s == stages) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                 }
             }
             if (*abort_flag) {
-                // let every copy into this CTA's ring land before it can exit
-                for (int64_t k = q > stages ? q - stages : 0; k < q; ++k)
-                    if (!mbar_wait(smem_u32(&sh->full[k % stages]), (uint32_t)(k / stages) & 1u, nullptr))
-                        atomicOr(err, DEVERR_TIMEOUT_DRAIN);
+                // let every copy into this CTA's ring land before it can exit: the last `issued`
+                // slots before the current position
+                int ks = s;
+                uint32_t kp = ph;
+                for (int i = 0; i < issued; ++i) {
+                    if (--ks < 0) {
+                        ks = stages - 1;
+                        kp ^= 1u;
+                    }
+                    if (!mbar_wait(smem_u32(&sh->full[ks]), kp, nullptr)) atomicOr(err, DEVERR_TIMEOUT_DRAIN);
+                }
             }
         }
     } else if (warp == 1 && FORM == 2) {
         if (lane == 0) {
             const int ksteps = bf / 8;
-            int64_t q = 0, hc = 0, tiles = 0;         // stages consumed, H drains requested, tiles
+            int s = 0;
+            uint32_t ph = 0;
+            uint32_t hph = 0, tph = 0;                // parities of the H drain and tile release
+            int64_t tiles = 0, chunks = 0;
             bool stop = false;
-            uint64_t wait_drain = 0, wait_full = 0;
             const uint32_t accH = tmem, accS = tmem + 256u;
             for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x, ++tiles) {
                 const TcGroupEntry &en = g.e[group_entry(g, t)];
@@ -932,28 +955,24 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
                 const uint32_t id = idesc_bf16_f32(kMTile, N);
                 if (tiles > 0) {
                     // the previous tile's H and S must be in registers before they are reused
-                    const uint64_t w0 = trace ? globaltimer() : 0;
-                    if (!mbar_wait(smem_u32(&sh->chunk_free[1]), (uint32_t)((tiles - 1) & 1), abort_flag)) {
+                    if (!mbar_wait(smem_u32(&sh->chunk_free[1]), tph, abort_flag)) {
                         if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
                         *abort_flag = 1;
                         break;
                     }
-                    if (trace) wait_drain += globaltimer() - w0;
+                    tph ^= 1u;
                     tc_fence_after();
                 }
-                for (int kb = 0; kb < n_kb; ++kb, ++q) {
-                    const int kc = kb % cb;
-                    const int s = (int)(q % stages);
-                    const uint64_t w1 = trace ? globaltimer() : 0;
-                    if (!mbar_wait(smem_u32(&sh->full[s]), (uint32_t)(q / stages) & 1u, abort_flag)) {
+                int kc = 0;                           // staging block inside the chunk
+                for (int kb = 0; kb < n_kb; ++kb) {
+                    if (!mbar_wait(smem_u32(&sh->full[s]), ph, abort_flag)) {
                         if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_FULL);
                         *abort_flag = 1;
                         stop = true;
                         break;
                     }
-                    if (trace && q > 0) wait_full += globaltimer() - w1;
                     tc_fence_after();
-                    if (trace && q == 0) trace[2] = globaltimer();
+                    if (trace && tiles == 0 && kb == 0) trace[2] = globaltimer();
                     const uint32_t st = base_s + (uint32_t)s * stage_bytes;
                     const uint64_t dAhi0 = sdesc_k(st, RB);
                     const uint64_t dAlo0 = sdesc_k(st + kABytes, RB);
@@ -967,14 +986,13 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
                     }
                     if (kc == 0 && kb > 0) {
                         // the previous chunk of H must be drained before this chunk overwrites it
-                        const uint64_t w0 = trace ? globaltimer() : 0;
-                        if (!mbar_wait(smem_u32(&sh->chunk_free[0]), (uint32_t)((hc - 1) & 1), abort_flag)) {
+                        if (!mbar_wait(smem_u32(&sh->chunk_free[0]), hph, abort_flag)) {
                             if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
                             *abort_flag = 1;
                             stop = true;
                             break;
                         }
-                        if (trace) wait_drain += globaltimer() - w0;
+                        hph ^= 1u;
                         tc_fence_after();
                     }
                     for (int ks = 0; ks < ksteps; ++ks) {
@@ -982,9 +1000,14 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
                         mma_bf16_ss(accH, dAhi0 + adv, dBhi0 + adv, id, (kc == 0 && ks == 0) ? 0u : 1u);
                     }
                     mma_commit(smem_u32(&sh->empty[s]));
-                    if (kc == cb - 1 && kb != n_kb - 1) {
+                    if (++s == stages) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                    if (++kc == cb && kb != n_kb - 1) {
                         mma_commit(smem_u32(&sh->chunk_full[0]));   // a finished chunk of H
-                        ++hc;
+                        kc = 0;
+                        ++chunks;
                     }
                 }
                 if (stop) break;
@@ -993,47 +1016,47 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
             mma_commit(smem_u32(&sh->tmem_full));   // always: nothing writes TMEM after this
             if (trace) {
                 trace[3] = globaltimer();
-                trace[4] = wait_drain;
-                trace[5] = wait_full;
+                trace[4] = (unsigned long long)tiles;
+                trace[5] = (unsigned long long)chunks;
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const int ksteps = bf / 8;
-            int64_t q = 0, c = 0;                     // stages consumed, chunks started
+            int s = 0;
+            uint32_t ph = 0;
+            int buf = 0;                              // accumulator buffer of the current chunk
+            uint32_t fph = 0u;                        // bit b: parity of buffer b's next release
+            int64_t tiles = 0, chunks = 0;            // chunks started by this CTA
             bool stop = false;
-            uint64_t wait_drain = 0, wait_full = 0;   // traced: ns spent waiting
-            for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x) {
+            for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x, ++tiles) {
                 const TcGroupEntry &en = g.e[group_entry(g, t)];
                 const int N = en.args.N, n_kb = en.args.n_kb, cb = en.args.drain_kb;
                 const uint32_t id = idesc_bf16_f32(kMTile, N);
-                for (int kb = 0; kb < n_kb; ++kb, ++q) {
-                    const int kc = kb % cb;
-                    const int64_t gc = c + kb / cb;   // chunk of this CTA
-                    const int buf = (int)(gc & 1);
-                    if (kc == 0 && gc >= 2) {
-                        // the buffer's previous chunk must be drained before it is overwritten
-                        const uint64_t w0 = trace ? globaltimer() : 0;
-                        if (!mbar_wait(smem_u32(&sh->chunk_free[buf]), (uint32_t)((gc - 2) >> 1) & 1u, abort_flag)) {
-                            if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
-                            *abort_flag = 1;
-                            stop = true;
-                            break;
+                int kc = 0;
+                for (int kb = 0; kb < n_kb; ++kb) {
+                    if (kc == 0) {
+                        if (chunks >= 2) {
+                            // the buffer's previous chunk must be drained before it is overwritten
+                            if (!mbar_wait(smem_u32(&sh->chunk_free[buf]), (fph >> buf) & 1u, abort_flag)) {
+                                if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
+                                *abort_flag = 1;
+                                stop = true;
+                                break;
+                            }
+                            fph ^= 1u << buf;
+                            tc_fence_after();
                         }
-                        if (trace) wait_drain += globaltimer() - w0;
-                        tc_fence_after();
+                        ++chunks;
                     }
-                    const int s = (int)(q % stages);
-                    const uint64_t w1 = trace ? globaltimer() : 0;
-                    if (!mbar_wait(smem_u32(&sh->full[s]), (uint32_t)(q / stages) & 1u, abort_flag)) {
+                    if (!mbar_wait(smem_u32(&sh->full[s]), ph, abort_flag)) {
                         if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_FULL);
                         *abort_flag = 1;
                         stop = true;
                         break;
                     }
-                    if (trace && q > 0) wait_full += globaltimer() - w1;
                     tc_fence_after();
-                    if (trace && q == 0) trace[2] = globaltimer();
+                    if (trace && tiles == 0 && kb == 0) trace[2] = globaltimer();
                     const uint32_t st = base_s + (uint32_t)s * stage_bytes;
                     const uint64_t dAhi0 = sdesc_k(st, RB);
                     const uint64_t dAlo0 = sdesc_k(st + kABytes, RB);
@@ -1048,15 +1071,22 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
                         mma_bf16_ss(acc, dAlo0 + adv, dBhi0 + adv, id, 1u);
                     }
                     mma_commit(smem_u32(&sh->empty[s]));
-                    if (kc == cb - 1 || kb == n_kb - 1) mma_commit(smem_u32(&sh->chunk_full[buf]));
+                    if (++s == stages) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                    if (++kc == cb || kb == n_kb - 1) {
+                        mma_commit(smem_u32(&sh->chunk_full[buf]));
+                        kc = 0;
+                        buf ^= 1;
+                    }
                 }
-                c += (n_kb + cb - 1) / cb;
             }
             mma_commit(smem_u32(&sh->tmem_full));   // always: nothing writes TMEM after this
             if (trace) {
                 trace[3] = globaltimer();
-                trace[4] = wait_drain;
-                trace[5] = wait_full;
+                trace[4] = (unsigned long long)tiles;
+                trace[5] = (unsigned long long)chunks;
             }
         }
     } else if (FORM == 2) {
