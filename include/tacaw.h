@@ -146,7 +146,7 @@ typedef struct {
      *   tc_accumulators   TMEM accumulators per tile: 1 (all products in one), 2 (hi*hi | small
      *                     terms), 3 (hi*hi alternating over two | small terms; the in-place
      *                     and CTA-pair default).  Left at 0 on staged operands, the drained
-     *                     one-accumulator form below is used.
+     *                     split form below is used.
      *   tc_cluster        CTAs per cluster sharing the twiddle rows by TMA multicast: 1, 2, 4
      *   tc_block_frames   frames per staged operand row: 8, 16 or 32 (32-, 64-, 128-byte rows);
      *                     k_stage must be a multiple of it
@@ -169,14 +169,16 @@ typedef struct {
      * tc_cluster 0 or 2.  2: the same, with the odd CTA's copies completing directly on the
      * even CTA's stage barriers instead of being relayed by one of its threads.  0: off.   */
     int tc_pair;
-    /* Split path, staged operands: > 0 selects the drained accumulator form.  All three
-     * products of a tile go to one TMEM accumulator, double-buffered: every tc_drain_frames
-     * frames the finished buffer is added into FP32 registers (round to nearest) by the
-     * epilogue warps while the other buffer accumulates.  The tensor core's truncating FP32
-     * accumulation then spans one chunk instead of the segment, at the MMA width of a single
-     * accumulator (tiles up to 112 complex energies).  Multiple of 8; excludes tc_pair,
-     * tc_cluster > 1 and tc_accumulators > 1.  0: the default -- 256 frames when
-     * tc_accumulators, tc_pair and tc_cluster (> 1) are all left unset, otherwise off.     */
+    /* Split path, staged operands: > 0 selects a drained accumulator form, chunks of
+     * tc_drain_frames frames (multiple of 8).  The tensor core's FP32 accumulation truncates
+     * each step against the running sum; draining finished chunks into FP32 registers (round
+     * to nearest, by the epilogue warps while the tensor core goes on) bounds that to a chunk.
+     *   tc_accumulators 1: all three products in one TMEM accumulator, double-buffered
+     *   tc_accumulators 2: hi*hi in one accumulator, drained; hi*lo + lo*hi in a second one
+     *                      for the whole tile (their truncation is ~2^-8 smaller)
+     * Tiles of up to 112 complex energies; single CTAs (tc_pair 0, tc_cluster 0/1); a
+     * persistent grid walks the tiles of all streams.  0: the default -- form 2 with 512-frame
+     * chunks when tc_accumulators, tc_pair and tc_cluster (> 1) are all left unset, else off. */
     int tc_drain_frames;
 } tacaw_plan_desc;
 

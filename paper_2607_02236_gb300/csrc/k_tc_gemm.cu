@@ -385,9 +385,15 @@ __device__ __forceinline__ void tc_mma_loop(const TcPlanArgs &a, TcShared *sh, u
     const uint64_t b_half_off = (uint64_t)((n0 * RB) >> 4);
     const uint32_t acc_small = tmem + (uint32_t)(a.n_big * a.N);
     const int ksteps = a.bf / 8;
+    int s_ring = -1;       // ring slot and use of staging block kb (no divisions)
+    uint32_t u_ring = 0;
     for (int kb = 0; kb < a.n_kb; ++kb) {
-        const int s = kb % a.stages;
-        const uint32_t use = (uint32_t)(kb / a.stages);
+        if (++s_ring == a.stages) {
+            s_ring = 0;
+            ++u_ring;
+        }
+        const int s = s_ring;
+        const uint32_t use = u_ring;
         if (!mbar_wait(smem_u32(&sh->full[s]), use & 1u, abort_flag)) {
             if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
             *abort_flag = 1;
@@ -578,9 +584,15 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
                 tma_prefetch_3d(&maps.a_hi, 0, m0, kb);
                 tma_prefetch_3d(&maps.a_lo, 0, m0, kb);
             }
+            int s_ring = -1;       // ring slot and use of staging block kb (no divisions)
+            uint32_t u_ring = 0;
             for (int kb = 0; kb < a.n_kb; ++kb) {
-                const int s = kb % a.stages;
-                const uint32_t use = (uint32_t)(kb / a.stages);
+                if (++s_ring == a.stages) {
+                    s_ring = 0;
+                    ++u_ring;
+                }
+                const int s = s_ring;
+                const uint32_t use = u_ring;
                 if (!mbar_wait(smem_u32(&sh->empty[s]), (use & 1u) ^ 1u, abort_flag)) {
                     if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
                     *abort_flag = 1;
@@ -656,9 +668,15 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
     } else if (warp == 1 && PAIR && !leader) {
         if (lane == 0 && a.pair == 1) {
             // relay: each stage of this CTA is complete -> one arrival on the even CTA's barrier
+            int s_ring = -1;
+            uint32_t u_ring = 0;
             for (int kb = 0; kb < a.n_kb; ++kb) {
-                const int s = kb % a.stages;
-                if (!mbar_wait(smem_u32(&sh->full[s]), (uint32_t)(kb / a.stages) & 1u, abort_flag)) {
+                if (++s_ring == a.stages) {
+                    s_ring = 0;
+                    ++u_ring;
+                }
+                const int s = s_ring;
+                if (!mbar_wait(smem_u32(&sh->full[s]), u_ring & 1u, abort_flag)) {
                     if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
                     *abort_flag = 1;
                     break;
@@ -678,9 +696,15 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
             const uint64_t b_half_off = (uint64_t)((n0 * RB) >> 4);
             const uint32_t acc_small = tmem + (uint32_t)(a.n_big * a.N);
             const int ksteps = a.bf / 8;
+            int s_ring = -1;       // ring slot and use of staging block kb (no divisions)
+            uint32_t u_ring = 0;
             for (int kb = 0; kb < a.n_kb; ++kb) {
-                const int s = kb % a.stages;
-                const uint32_t use = (uint32_t)(kb / a.stages);
+                if (++s_ring == a.stages) {
+                    s_ring = 0;
+                    ++u_ring;
+                }
+                const int s = s_ring;
+                const uint32_t use = u_ring;
                 const bool got = PAIR ? mbar_wait_cluster(smem_u32(&sh->full[s]), use & 1u, abort_flag)
                                       : mbar_wait(smem_u32(&sh->full[s]), use & 1u, abort_flag);
                 if (!got) {
@@ -1292,9 +1316,15 @@ __global__ void __launch_bounds__(320, 1) flush_tc_direct_kernel(const __grid_co
         const uint32_t sw = (row_byte >> 7) & (uint32_t)(cpr - 1);  // swizzle phase of this row
         double sr = 0.0, si = 0.0;
         bool ok = true;
+        int s_ring = -1;           // ring slot and use of staging block kb (no divisions)
+        uint32_t u_ring = 0;
         for (int kb = 0; kb < a.n_kb && ok; ++kb) {
-            const int s = kb % a.stages;
-            const uint32_t use = (uint32_t)(kb / a.stages);
+            if (++s_ring == a.stages) {
+                s_ring = 0;
+                ++u_ring;
+            }
+            const int s = s_ring;
+            const uint32_t use = u_ring;
             if (!mbar_wait(smem_u32(&sh->empty[s]), (use & 1u) ^ 1u, abort_flag)) {
                 if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
                 *abort_flag = 1;
@@ -1345,9 +1375,15 @@ __global__ void __launch_bounds__(320, 1) flush_tc_direct_kernel(const __grid_co
     } else if (warp == 4) {
         // ---------------- B producer ----------------
         if (lane == 0) {
+            int s_ring = -1;       // ring slot and use of staging block kb (no divisions)
+            uint32_t u_ring = 0;
             for (int kb = 0; kb < a.n_kb; ++kb) {
-                const int s = kb % a.stages;
-                const uint32_t use = (uint32_t)(kb / a.stages);
+                if (++s_ring == a.stages) {
+                    s_ring = 0;
+                    ++u_ring;
+                }
+                const int s = s_ring;
+                const uint32_t use = u_ring;
                 if (!mbar_wait(smem_u32(&sh->empty[s]), (use & 1u) ^ 1u, abort_flag)) {
                     if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
                     *abort_flag = 1;

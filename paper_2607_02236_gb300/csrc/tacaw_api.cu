@@ -818,15 +818,15 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     tacaw_plan_s *p = new (std::nothrow) tacaw_plan_s();
     if (!p) return fail(TACAW_ERR_OOM, "host allocation failed");
     p->tc_acc = desc->tc_accumulators ? desc->tc_accumulators : 3;
-    // default accumulation of the staged split path: the drained form, chunks of 256 frames
-    // (faster and more accurate than three side-by-side accumulators in measurements)
-    const int drain_frames =
-        desc->tc_drain_frames ? desc->tc_drain_frames
-                              : (desc->tc_accumulators == 0 && !desc->tc_pair && desc->tc_cluster <= 1 ? 256 : 0);
+    // default accumulation of the staged split path: the split drained form (hi*hi drained
+    // every 512 frames, small products apart), the fastest and most accurate form measured
+    const bool auto_acc = desc->tc_accumulators == 0 && !desc->tc_drain_frames && !desc->tc_pair &&
+                          desc->tc_cluster <= 1;
+    const int drain_frames = desc->tc_drain_frames ? desc->tc_drain_frames : (auto_acc ? 512 : 0);
     const bool drained = drain_frames > 0 && desc->precision == TACAW_PREC_SPLIT_BF16 && !desc->frames_in_place;
     // drained forms: 1 = all products in one double-buffered accumulator, 2 = hi*hi drained, the
     // small products in a second accumulator
-    if (drained) p->drain_form = desc->tc_accumulators == 2 ? 2 : 1;
+    if (drained) p->drain_form = (desc->tc_accumulators == 2 || auto_acc) ? 2 : 1;
     if (drained) p->tc_acc = p->drain_form;
     // TMEM columns per tile: accumulators side by side (the drained form holds two buffers)
     const int tile_acc = drained ? 2 : p->tc_acc;
