@@ -347,7 +347,8 @@ def batched_arm(args):
     peaks, peak_src = measured_peaks()
     peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
     achieved = cmac_step * 24 / (k_ms * 1e-3) / 1e12
-    kname = "flush_tc_drain_kernel" if info["tc_drain_frames"] else "flush_tc_kernel"
+    kname = ("flush_tc_drain2_kernel" if info["tc_accumulators"] == 2 else "flush_tc_drain_kernel") \
+        if info["tc_drain_frames"] else "flush_tc_kernel"
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -618,7 +619,7 @@ def main():
         if info["frames_in_place"]:
             kname = "flush_tc_direct_kernel"
         elif info["tc_drain_frames"]:
-            kname = "flush_tc_drain_kernel"
+            kname = "flush_tc_drain2_kernel" if info["tc_accumulators"] == 2 else "flush_tc_drain_kernel"
         elif info["tc_pair"]:
             kname = "flush_tc_pair_kernel"
         else:
