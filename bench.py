@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3, help="end-to-end steps from pinned host memory (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU oracle baseline")
     ap.add_argument("--small", action="store_true", help="small workload (profiling captures)")
+    ap.add_argument("--pipeline", type=int, default=2,
+                    help="segments in flight: one plan and CUDA stream each, steps alternate between them "
+                         "(a segment's conversions overlap the previous segment's contraction)")
     ap.add_argument("--workload", default="realistic", choices=["realistic", "batched"],
                     help="batched: the 16 uneven partitions, autotuned tiles, one CUDA-graph replay per step")
     ap.add_argument("--in-place", dest="in_place", action="store_true", default=False,
@@ -428,34 +431,54 @@ def main():
     S = torch.empty(max(1, P * D * Nw), dtype=torch.float32, device="cuda")
     n_push = (T + Tc - 1) // Tc
 
-    def run_step(plan):
-        plan.reset(st)
+    def run_step(plan, out=None, sth=None):
+        """One segment through the public API: reset, all pushes, finalize (asynchronous)."""
+        I_, S_ = out if out is not None else (I, S)
+        sth = st if sth is None else sth
+        plan.reset(sth)
         for i in range(n_push):
-            plan.push(0, base + i * Tc * frame_elems * 8, min(Tc, T - i * Tc), st)
-        plan.finalize(I, S, None, st)
+            plan.push(0, base + i * Tc * frame_elems * 8, min(Tc, T - i * Tc), sth)
+        plan.finalize_async(I_, S_, None, sth)
 
-    def timed(plan, steps, warmup, sample_clocks=False):
-        for _ in range(warmup):
-            run_step(plan)
+    def timed(plans, steps, warmup, sample_clocks=False, outs=None, streams=None):
+        """Steps alternate over the plans, each on its own stream (one segment in flight per plan)."""
+        plans = plans if isinstance(plans, list) else [plans]
+        outs = outs or [(I, S)]
+        streams = streams or [stream]
+        n = len(plans)
+        for k in range(warmup):
+            run_step(plans[k % n], outs[k % n], streams[k % n].cuda_stream)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
         clk = ClockSampler(local) if sample_clocks else None
-        plan.set_timing(True)
-        plan.kernel_time_ms(reset=True)
-        l0 = plan.info()["kernel_launches"]
+        for pl in plans:
+            pl.set_timing(True)
+            pl.kernel_time_ms(reset=True)
+        l0 = sum(pl.info()["kernel_launches"] for pl in plans)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(steps):
-            run_step(plan)
+        for sx in streams:
+            sx.wait_event(e0)
+        for k in range(steps):
+            run_step(plans[k % n], outs[k % n], streams[k % n].cuda_stream)
+        for sx in streams:
+            ev = torch.cuda.Event()
+            ev.record(sx)
+            stream.wait_event(ev)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
+        for sx, pl in zip(streams, plans):
+            pl.check_errors(sx.cuda_stream)
         clocks = clk.stop() if clk else None
         ms = e0.elapsed_time(e1)
-        kms, kn = plan.kernel_time_ms(reset=True)
-        plan.set_timing(False)
-        launches = (plan.info()["kernel_launches"] - l0) // steps
+        kms, kn = 0.0, 0
+        for pl in plans:
+            a, b = pl.kernel_time_ms(reset=True)
+            kms, kn = kms + a, kn + b
+            pl.set_timing(False)
+        launches = (sum(pl.info()["kernel_launches"] for pl in plans) - l0) // steps
         ms = max_over_ranks(ms, dist, "cuda")
         return ms / steps, kms / max(kn, 1), kn // max(steps, 1), launches, clocks
 
@@ -463,9 +486,18 @@ def main():
                   tc_cluster=args.tc_cluster, tc_block_frames=args.tc_block_frames, tc_pair=args.tc_pair,
                   tc_drain_frames=args.tc_drain_frames,
                   frames_in_place=bool(args.in_place and args.precision == "split_bf16"))
-    plan = TacawPlan([stream_config(spec)], precision=args.precision, **tiling)
+    # segments in flight: plan k and stream k take steps k, k + n, ...; the first plan writes I, S
+    n_pipe = max(1, args.pipeline)
+    plans = [TacawPlan([stream_config(spec)], precision=args.precision, **tiling) for _ in range(n_pipe)]
+    plan = plans[0]
     info = plan.info()
-    ms_step, k_ms, k_per_step, launches, clocks = timed(plan, args.steps, args.warmup, sample_clocks=True)
+    outs = [(I, S)] + [(torch.empty_like(I), torch.empty_like(S)) for _ in range(n_pipe - 1)]
+    pipe_streams = [torch.cuda.Stream() for _ in range(n_pipe)] if n_pipe > 1 else [stream]
+    ms_step, k_ms, k_per_step, launches, clocks = timed(plans, args.steps, args.warmup, sample_clocks=True,
+                                                        outs=outs, streams=pipe_streams)
+    for pl in plans[1:]:          # free the other segments' staging before the comparison legs
+        pl.close()
+    del outs[1:]
     value = job_rate(cmac_step, world, ms_step * 1e-3)
     spectra_per_s = world * P * D / (ms_step * 1e-3)
 
@@ -667,6 +699,7 @@ def main():
                            "frames_in_place": bool(info["frames_in_place"]),
                            "smem_stages": info["stages"], "plan_device_GB": round(info["device_bytes"] / 1e9, 2),
                            "l2": "inputs (%.1f GB) larger than L2, no flush" % (T * frame_elems * 8 / 1e9),
+                           "segments_in_flight": n_pipe,
                            "parallelism": f"replicas x{world}"},
                 "max_rel_err_I_vs_fp64": err, "error_sample": "24 (probe, pixel) series, all energies",
                 "spectra_per_s": spectra_per_s, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
