@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3, help="end-to-end steps from pinned host memory (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU oracle baseline")
     ap.add_argument("--small", action="store_true", help="small workload (profiling captures)")
-    ap.add_argument("--pipeline", type=int, default=2,
+    ap.add_argument("--pipeline", type=int, default=1,
                     help="segments in flight: one plan and CUDA stream each, steps alternate between them "
                          "(a segment's conversions overlap the previous segment's contraction)")
     ap.add_argument("--workload", default="realistic", choices=["realistic", "batched"],
