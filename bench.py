@@ -32,9 +32,9 @@ UNIT = "CMAC/s"
 # DRAM bytes per launch of the contraction kernel from an ncu capture, keyed by the hash of
 # the kernel's source file at capture time (reported only while the source is unchanged).
 KERNEL_TRAFFIC = {
-    # ncu --set full of flush_tc_drain_kernel on `bench.py --small` (P=2, T=2048, 400 energies, default
-    # tiling): dram__bytes_read.sum 2.448184 GB + dram__bytes_write.sum 0.205258 GB per launch of 1.07e11 CMAC
-    ("f06984492f3a6401", "flush_tc_drain_kernel"): 2.471210e-02,
+    # ncu --set full of flush_tc_drain2_kernel on `bench.py --small` (P=2, T=2048, 400 energies, default
+    # tiling): dram__bytes_read.sum 2.471981 GB + dram__bytes_write.sum 0.204507 GB per launch of 1.07e11 CMAC
+    ("a33f8126ac2c2b08", "flush_tc_drain2_kernel"): 2.492674e-02,
 }
 
 
