@@ -649,7 +649,7 @@ def main():
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         src = os.path.join(ROOT, "paper_2607_02236_gb300", "csrc", "k_tc_gemm.cu")
         if info["frames_in_place"]:
-            kname = "flush_tc_direct_kernel"
+            kname = "flush_tc_inplace_kernel" if info["tc_inplace_form"] == 2 else "flush_tc_direct_kernel"
         elif info["tc_drain_frames"]:
             kname = "flush_tc_drain2_kernel" if info["tc_accumulators"] == 2 else "flush_tc_drain_kernel"
         elif info["tc_pair"]:

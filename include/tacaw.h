@@ -160,7 +160,12 @@ typedef struct {
     /* != 0 (split path only): pushed buffers are read in place by the contraction instead of
      * being converted into a staging area at push time.  Each pushed buffer must then stay
      * valid and unchanged until the flush that covers its frames has completed on the stream:
-     * with the default K_stage (the whole segment) that is until tacaw_finalize returns. */
+     * with the default K_stage (the whole segment) that is until tacaw_finalize returns.
+     * When every stream keeps each 128-row tile contiguous in a frame (kx a multiple of 128, or
+     * unpadded rows with roi_x0 = 0 and probes that are whole tiles or adjacent), all row
+     * offsets and pitches are even, and the tiling is left at (or set to) 32-frame blocks with
+     * one or two accumulators, a persistent drained kernel copies the rows with bulk copies
+     * (pushed buffers must then be 16-byte aligned); otherwise a register-fed kernel runs. */
     int frames_in_place;
     /* Split path, staged operands: 1 runs each pair of 128-row tiles as 256-row MMAs on a
      * cluster of two SMs (tcgen05 CTA pair): each SM stages its own rows of A and half of the
@@ -204,6 +209,9 @@ typedef struct {
     int tuned_streams;         /* streams whose tile the autotuner picked */
     int tune_candidates;       /* candidate tiles timed at creation (0: none, or all cached) */
     double tune_ms;            /* host time spent in the autotuner at creation */
+    int tc_inplace_form;       /* frames_in_place kernel: 0 none, 1 register-fed, 2 persistent drained
+                                  (chosen when every stream's tile rows are contiguous in a frame,
+                                  all row offsets even, 32-frame blocks, one or two accumulators) */
 } tacaw_plan_info;
 
 /* Creates a plan: validates the descriptor, sizes and allocates device memory

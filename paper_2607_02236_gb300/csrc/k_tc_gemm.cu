@@ -75,6 +75,11 @@ struct TcShared {
     uint64_t sums_ready;      // in-place kernel: producers -> epilogue
     uint64_t chunk_full[2];   // drained kernel: a chunk's accumulator buffer is complete
     uint64_t chunk_free[2];   // drained kernel: the epilogue warps have drained it
+    uint64_t raw_full[2];     // in-place drained kernel: raw frame rows landed
+    uint64_t raw_empty[2];    //   converters are done with a raw stage
+    uint64_t sums_full[2];    //   a tile's row sums are in `tsum`
+    uint64_t sums_free[2];    //   the epilogue has read them
+    double2 tsum[2][kMTile];  //   per-tile sums of (psi - mu_hat) over this flush, double-buffered
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -1240,6 +1245,419 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
     flush_tc_drain_body<2>(g);
 }
 
+
+// --------------------------------------------------------------------------------------
+// In-place drained form (persistent): operand A is read from the caller's pushed complex64
+// frames without a staging pass.  For every staging block the producer copies, per frame, the
+// tile's 128 rows (contiguous in the frame: checked by the host) into a raw ring with
+// contiguous bulk copies; two converter warps subtract the provisional mean, split into bf16
+// hi/lo and write the swizzled K-major rows of the stage, keeping each row's residual sum for
+// the exact mean correction.  Accumulation as in the split drained form (H drained every
+// drain_kb blocks, S for the whole tile).
+//
+//   warp 0     producer: twiddle rows (pre-swizzled, bulk) and raw frame rows (lane f: frame f)
+//   warp 1     TMEM allocation and MMA issue
+//   warps 2-3  converters: thread i handles rows i and i + 64 of the tile
+//   warps 4-11 drains and epilogues
+// 384 threads: three warps on each register file, 168 registers a thread.
+struct TcInplaceArgs {
+    TcPlanArgs a;
+    TcDirectArgs d;
+    int stages;                // operand ring stages
+    int64_t tiles;             // (M_pad / 128) * n_wt
+};
+
+__global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__ TcInplaceArgs g) {
+    const TcPlanArgs &a = g.a;
+    const TcDirectArgs &d = g.d;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int bf = a.bf, stages = g.stages, N = a.N;
+    const uint32_t RB = 4u * (uint32_t)bf;
+    const uint32_t kABytes = tc_a_bytes(bf);
+    const uint32_t b_pad = tc_b_bytes_padded(N, bf);
+    const uint32_t stage_bytes = tc_stage_bytes(N, bf);
+    const uint32_t raw_bytes = (uint32_t)bf * (uint32_t)kMTile * 8u;          // one raw stage
+    uint8_t *raw = base + (size_t)stages * stage_bytes;
+    TcShared *sh = reinterpret_cast<TcShared *>(raw + 2 * (size_t)raw_bytes);
+    const uint32_t base_s = smem_u32(base), raw_s = smem_u32(raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n_tiles = g.tiles;
+    unsigned long long *trace = a.trace ? a.trace + (size_t)blockIdx.x * kTraceWords : nullptr;
+    if (trace && threadIdx.x == 0) {
+        trace[0] = globaltimer();
+        trace[7] = smid();
+    }
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < stages; ++st) {
+            mbar_init(smem_u32(&sh->full[st]), 3);   // twiddle copies + two converter warps
+            mbar_init(smem_u32(&sh->empty[st]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&sh->raw_full[b]), 1);
+            mbar_init(smem_u32(&sh->raw_empty[b]), 2);
+            mbar_init(smem_u32(&sh->sums_full[b]), 2);
+            mbar_init(smem_u32(&sh->sums_free[b]), 8);
+            mbar_init(smem_u32(&sh->chunk_full[b]), 1);
+            mbar_init(smem_u32(&sh->chunk_free[b]), 8);
+        }
+        mbar_init(smem_u32(&sh->tmem_full), 1);
+        sh->abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(&sh->tmem_addr), 512u);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_addr;
+    volatile int *abort_flag = &sh->abort_flag;
+    if (trace && threadIdx.x == 0) trace[1] = globaltimer();
+
+    if (warp == 0) {
+        // ---------------- producer ----------------
+        int s = 0, r = 0;
+        uint32_t ph = 0, rph = 0;
+        int op_issued = 0, raw_issued = 0;
+        const uint32_t tx_b = 2u * (uint32_t)N * RB;
+        for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
+            const int wtile = (int)(t % a.n_wt);
+            const int64_t m0 = (t / a.n_wt) * kMTile;
+            const int nrows = (int)(d.M - m0 < kMTile ? d.M - m0 : kMTile);   // even (host-checked)
+            const int64_t p = m0 / d.npix, pix = m0 - p * d.npix;
+            const int64_t y = pix / d.kx, x = pix - y * d.kx;
+            const int64_t off = p * d.pitch_probe + (d.roi_y0 + y) * d.pitch_row + (d.roi_x0 + x);
+            const uint8_t *pBhi = static_cast<const uint8_t *>(a.B_hi) +
+                                  ((size_t)a.kbB0 * (size_t)a.b_rows + (size_t)wtile * N) * RB;
+            const uint8_t *pBlo = static_cast<const uint8_t *>(a.B_lo) +
+                                  ((size_t)a.kbB0 * (size_t)a.b_rows + (size_t)wtile * N) * RB;
+            const size_t b_step = (size_t)a.b_rows * RB;
+            bool stop = false;
+            for (int kb = 0; kb < a.n_kb && !stop; ++kb) {
+                // raw frame rows of this block: lane f copies frame kb*bf + f
+                const int f = kb * bf + lane;
+                const float2 *fp = (lane < bf && f < d.n_frames) ? d.frame_ptr[f] : nullptr;
+                const int nfr = min(bf, d.n_frames - kb * bf);
+                if (!mbar_wait(smem_u32(&sh->raw_empty[r]), rph ^ 1u, abort_flag)) {
+                    if (lane == 0 && !*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
+                    *abort_flag = 1;
+                    break;
+                }
+                const uint32_t rf = smem_u32(&sh->raw_full[r]);
+                if (lane == 0) mbar_arrive_expect_tx(rf, (uint32_t)nfr * (uint32_t)nrows * 8u);
+                __syncwarp();
+                if (fp) bulk_load(raw_s + (uint32_t)r * raw_bytes + (uint32_t)lane * (uint32_t)kMTile * 8u, fp + off,
+                                  (uint32_t)nrows * 8u, rf);
+                raw_issued = raw_issued < 2 ? raw_issued + 1 : 2;
+                if (++r == 2) {
+                    r = 0;
+                    rph ^= 1u;
+                }
+                // twiddle rows of this block
+                if (lane == 0) {
+                    if (!mbar_wait(smem_u32(&sh->empty[s]), ph ^ 1u, abort_flag)) {
+                        if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
+                        *abort_flag = 1;
+                        stop = true;
+                    } else {
+                        const uint32_t full = smem_u32(&sh->full[s]);
+                        const uint32_t st = base_s + (uint32_t)s * stage_bytes;
+                        mbar_arrive_expect_tx(full, tx_b);
+                        bulk_load(st + 2 * kABytes, pBhi + (size_t)kb * b_step, (uint32_t)N * RB, full);
+                        bulk_load(st + 2 * kABytes + b_pad, pBlo + (size_t)kb * b_step, (uint32_t)N * RB, full);
+                    }
+                }
+                stop = __shfl_sync(0xffffffffu, stop ? 1 : 0, 0) != 0;
+                if (!stop) op_issued = op_issued < stages ? op_issued + 1 : stages;
+                if (++s == stages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+            if (stop) break;
+        }
+        if (*abort_flag && lane == 0) {
+            // let every copy into this CTA's rings land before it can exit.  The twiddle copies
+            // share their stage barrier with the converters, which may never arrive: give them
+            // a fixed 20 ms (copies take microseconds); the raw copies have barriers of their own
+            if (op_issued > 0) {
+                const uint64_t t0 = globaltimer();
+                while (globaltimer() - t0 < 20000000ull) {
+                }
+            }
+            int kr = r;
+            uint32_t krp = rph;
+            for (int i = 0; i < raw_issued; ++i) {
+                if (--kr < 0) {
+                    kr = 1;
+                    krp ^= 1u;
+                }
+                if (!mbar_wait(smem_u32(&sh->raw_full[kr]), krp, nullptr)) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA (split drained form) ----------------
+        if (lane == 0) {
+            const int ksteps = bf / 8;
+            int s = 0;
+            uint32_t ph = 0, hph = 0, tph = 0;
+            int64_t tiles = 0;
+            bool stop = false;
+            const uint32_t accH = tmem, accS = tmem + 256u;
+            const uint32_t id = idesc_bf16_f32(kMTile, N);
+            const int cb = a.drain_kb;
+            for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x, ++tiles) {
+                if (tiles > 0) {
+                    if (!mbar_wait(smem_u32(&sh->chunk_free[1]), tph, abort_flag)) {
+                        if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    tph ^= 1u;
+                    tc_fence_after();
+                }
+                int kc = 0;
+                for (int kb = 0; kb < a.n_kb; ++kb) {
+                    if (!mbar_wait(smem_u32(&sh->full[s]), ph, abort_flag)) {
+                        if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
+                        *abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    if (trace && tiles == 0 && kb == 0) trace[2] = globaltimer();
+                    const uint32_t st = base_s + (uint32_t)s * stage_bytes;
+                    const uint64_t dAhi0 = sdesc_k(st, RB);
+                    const uint64_t dAlo0 = sdesc_k(st + kABytes, RB);
+                    const uint64_t dBhi0 = sdesc_k(st + 2 * kABytes, RB);
+                    const uint64_t dBlo0 = sdesc_k(st + 2 * kABytes + b_pad, RB);
+                    for (int ks = 0; ks < ksteps; ++ks) {
+                        const uint64_t adv = (uint64_t)(2 * ks);
+                        mma_bf16_ss(accS, dAhi0 + adv, dBlo0 + adv, id, (kb == 0 && ks == 0) ? 0u : 1u);
+                        mma_bf16_ss(accS, dAlo0 + adv, dBhi0 + adv, id, 1u);
+                    }
+                    if (kc == 0 && kb > 0) {
+                        if (!mbar_wait(smem_u32(&sh->chunk_free[0]), hph, abort_flag)) {
+                            if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
+                            *abort_flag = 1;
+                            stop = true;
+                            break;
+                        }
+                        hph ^= 1u;
+                        tc_fence_after();
+                    }
+                    for (int ks = 0; ks < ksteps; ++ks) {
+                        const uint64_t adv = (uint64_t)(2 * ks);
+                        mma_bf16_ss(accH, dAhi0 + adv, dBhi0 + adv, id, (kc == 0 && ks == 0) ? 0u : 1u);
+                    }
+                    mma_commit(smem_u32(&sh->empty[s]));
+                    if (++s == stages) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                    if (++kc == cb && kb != a.n_kb - 1) {
+                        mma_commit(smem_u32(&sh->chunk_full[0]));
+                        kc = 0;
+                    }
+                }
+                if (stop) break;
+                mma_commit(smem_u32(&sh->chunk_full[1]));
+            }
+            mma_commit(smem_u32(&sh->tmem_full));
+            if (trace) {
+                trace[3] = globaltimer();
+                trace[4] = (unsigned long long)tiles;
+                trace[5] = 0;
+            }
+        }
+    } else if (warp < 4) {
+        // ---------------- converters ----------------
+        const int i = threadIdx.x - 64;               // rows i and i + 64 of the tile
+        const int cpr = bf / 4;
+        int s = 0, r = 0;
+        uint32_t ph = 0, rph = 0;
+        int64_t tiles = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tiles) {
+            const int wtile = (int)(t % a.n_wt);
+            const int64_t m0 = (t / a.n_wt) * kMTile;
+            const int sb = (int)(tiles & 1);
+            float2 mu[2];
+            bool valid[2];
+            double sr[2] = {0.0, 0.0}, si[2] = {0.0, 0.0};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t m = m0 + i + 64 * h;
+                valid[h] = m < d.M;
+                mu[h] = valid[h] ? d.mu_hat[m] : make_float2(0.f, 0.f);
+            }
+            for (int kb = 0; kb < a.n_kb; ++kb) {
+                if (!mbar_wait(smem_u32(&sh->raw_full[r]), rph, abort_flag) ||
+                    !mbar_wait(smem_u32(&sh->empty[s]), ph ^ 1u, abort_flag)) {
+                    if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                const int nfr = min(bf, d.n_frames - kb * bf);
+                const uint8_t *rs = raw + (size_t)r * raw_bytes;
+                uint8_t *st = base + (size_t)s * stage_bytes;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int row = i + 64 * h;
+                    const uint32_t row_byte = (uint32_t)row * RB;
+                    const uint32_t sw = (row_byte >> 7) & (uint32_t)(cpr - 1);
+                    float br = 0.f, bi = 0.f;
+                    for (int c = 0; c < cpr; ++c) {
+                        uint32_t hw[4], lw[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int fr = 4 * c + q;
+                            float2 v = make_float2(0.f, 0.f);
+                            if (valid[h] && fr < nfr) {
+                                const float2 x = *reinterpret_cast<const float2 *>(rs + (size_t)fr * kMTile * 8 + row * 8);
+                                v = make_float2(x.x - mu[h].x, x.y - mu[h].y);
+                            }
+                            br += v.x;
+                            bi += v.y;
+                            split2_bf16(v, hw[q], lw[q]);
+                        }
+                        const uint32_t chunk = ((uint32_t)c ^ sw) * 16u;
+                        *reinterpret_cast<uint4 *>(st + row_byte + chunk) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4 *>(st + kABytes + row_byte + chunk) =
+                            make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+                    sr[h] += br;
+                    si[h] += bi;
+                }
+                // generic-proxy writes -> visible to the tensor core before the arrive
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(smem_u32(&sh->full[s]));
+                    mbar_arrive(smem_u32(&sh->raw_empty[r]));
+                }
+                if (++s == stages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+                if (++r == 2) {
+                    r = 0;
+                    rph ^= 1u;
+                }
+            }
+            if (!ok) break;
+            // this tile's residual sums: to the epilogue, and (first energy tile) to the running
+            // sums; buffer sb was last read by the epilogue for tile `tiles - 2`
+            if (tiles >= 2 &&
+                !mbar_wait(smem_u32(&sh->sums_free[sb]), (uint32_t)(((tiles - 2) >> 1) & 1), abort_flag)) {
+                if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
+                *abort_flag = 1;
+                break;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int row = i + 64 * h;
+                sh->tsum[sb][row] = make_double2(sr[h], si[h]);
+                const int64_t m = m0 + row;
+                if (valid[h] && wtile == 0 && d.accumulate_sums) {
+                    double2 tt = d.sum_res[m];
+                    tt.x += sr[h];
+                    tt.y += si[h];
+                    d.sum_res[m] = tt;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&sh->sums_full[sb]));
+        }
+    } else {
+        // ---------------- drains and epilogues: warps 4..11 ----------------
+        const int q4 = warp & 3, h = (warp - 4) >> 2;
+        float sum[kDrainCols];
+        int64_t hc = 0, tiles = 0;
+        bool ok = true;
+        const int cols = a.wt;
+        const int col0 = h * cols;
+        const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)col0;
+        const int n_chunks = (a.n_kb + a.drain_kb - 1) / a.drain_kb;
+        for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tiles) {
+            const int wtile = (int)(t % a.n_wt);
+            const int64_t m0 = (t / a.n_wt) * kMTile;
+            const int sb = (int)(tiles & 1);
+#pragma unroll
+            for (int k = 0; k < kDrainCols; ++k) sum[k] = 0.f;
+            for (int lc = 0; lc + 1 < n_chunks; ++lc, ++hc) {
+                if (!mbar_wait(smem_u32(&sh->chunk_full[0]), (uint32_t)(hc & 1), abort_flag)) {
+                    if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                drain_add(sum, lane_base, cols);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&sh->chunk_free[0]));
+            }
+            if (!ok) break;
+            if (!mbar_wait(smem_u32(&sh->chunk_full[1]), (uint32_t)(tiles & 1), abort_flag) ||
+                !mbar_wait(smem_u32(&sh->sums_full[sb]), (uint32_t)((tiles >> 1) & 1), abort_flag)) {
+                if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
+                *abort_flag = 1;
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            drain_add(sum, lane_base, cols);
+            drain_add(sum, lane_base + 256u, cols);
+            tc_fence_before();
+            const int rr = q4 * 32 + lane;
+            const int64_t m = m0 + rr;
+            RowCtx row;
+            row.m = m;
+            row.valid = m < d.M;
+            const int64_t p = row.valid ? m / d.npix : 0;
+            row.out_base = p * (int64_t)a.e.Nw * d.npix + (m - p * d.npix);
+            row.dmu = make_float2(0.f, 0.f);
+            if (row.valid && d.subtract_mean && a.e.mode == FLUSH_FINAL) {
+                double2 tt = sh->tsum[sb][rr];
+                if (d.prev_sums) {
+                    const double2 pv = d.sum_res[m];
+                    tt.x += pv.x;
+                    tt.y += pv.y;
+                }
+                row.dmu = make_float2((float)(tt.x / d.T), (float)(tt.y / d.T));
+            }
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(smem_u32(&sh->chunk_free[1]));
+                mbar_arrive(smem_u32(&sh->sums_free[sb]));
+            }
+            const int jbase = wtile * a.wt;
+            switch (epi_kind(a.e)) {
+                case EPI_FINAL: tc_epilogue_regs<EPI_FINAL>(a, row, col0, cols, jbase, sum); break;
+                case EPI_FINAL_KAHAN: tc_epilogue_regs<EPI_FINAL_KAHAN>(a, row, col0, cols, jbase, sum); break;
+                case EPI_FINAL_FP64: tc_epilogue_regs<EPI_FINAL_FP64>(a, row, col0, cols, jbase, sum); break;
+                case EPI_STORE_KAHAN: tc_epilogue_regs<EPI_STORE_KAHAN>(a, row, col0, cols, jbase, sum); break;
+                case EPI_STORE_FP64: tc_epilogue_regs<EPI_STORE_FP64>(a, row, col0, cols, jbase, sum); break;
+                case EPI_ADD_KAHAN: tc_epilogue_regs<EPI_ADD_KAHAN>(a, row, col0, cols, jbase, sum); break;
+                default: tc_epilogue_regs<EPI_ADD_FP64>(a, row, col0, cols, jbase, sum); break;
+            }
+        }
+        if (!mbar_wait(smem_u32(&sh->tmem_full), 0u, nullptr)) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
+        tc_fence_after();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512u);
+    }
+    if (trace && threadIdx.x == 0) trace[6] = globaltimer();
+}
+
 // --------------------------------------------------------------------------------------
 // In-place variant: operand A is read from the caller's pushed complex64 frames.
 //
@@ -1573,6 +1991,37 @@ bool tc_make_maps_b(void *maps_out, const __nv_bfloat16 *B_hi, const __nv_bfloat
 }
 
 size_t tc_smem_bytes_direct(int N, int bf, int stages) { return tc_smem_bytes(N, bf, stages); }
+
+size_t tc_inplace_smem_bytes(int N, int bf, int stages) {
+    return (size_t)stages * tc_stage_bytes(N, bf) + 2 * (size_t)bf * kMTile * 8 + sizeof(TcShared) + 1024;
+}
+
+int tc_inplace_stages(int N, int bf) {
+    int st = 0;
+    while (st < kMaxStages && tc_inplace_smem_bytes(N, bf, st + 1) <= (size_t)kSmemLimit) ++st;
+    return st;
+}
+
+cudaError_t launch_flush_tc_inplace(const TcPlanArgs &a, const TcDirectArgs &d, cudaStream_t st) {
+    TcInplaceArgs g{};
+    g.a = a;
+    g.d = d;
+    g.stages = tc_inplace_stages(a.N, a.bf);
+    g.tiles = (a.e.M_pad / kMTile) * a.n_wt;
+    if (g.stages < 2 || a.N > 2 * kDrainCols || a.drain_kb < 1 || g.tiles <= 0) return cudaErrorInvalidConfiguration;
+    const size_t smem = tc_inplace_smem_bytes(a.N, a.bf, g.stages);
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(flush_tc_inplace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, flush_tc_inplace_kernel, 384, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int64_t grid = g.tiles < (int64_t)occ * sms ? g.tiles : (int64_t)occ * sms;
+    flush_tc_inplace_kernel<<<(unsigned)grid, 384, smem, st>>>(g);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_flush_tc_direct(const TcPlanArgs &a, const TcDirectArgs &d, const void *maps, cudaStream_t st) {
     const size_t smem = tc_smem_bytes(a.N, a.bf, a.stages);

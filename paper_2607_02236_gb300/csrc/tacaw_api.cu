@@ -119,6 +119,7 @@ struct tacaw_plan_s {
     int bf = 8;                // frames per staged operand row (split path)
     int tc_prefetch = 0;       // L2 prefetch distance of operand A in staging blocks
     bool in_place = false;     // the contraction reads pushed frames directly
+    bool ip2 = false;          // ... through the persistent drained in-place kernel
     int64_t bytes = 0;
     int64_t I_elems = 0, S_elems = 0;
     int64_t flushes_total = 0;
@@ -293,7 +294,7 @@ TcPlanArgs tc_args(tacaw_plan_s *p, const Stream &s, const EpiArgs &e) {
     a.stages = s.stages;
     a.split = p->tc_acc > 1 ? 1 : 0;
     a.n_big = p->tc_acc == 3 ? 2 : 1;
-    a.drain_kb = p->in_place ? 0 : p->drain_kb;
+    a.drain_kb = (p->in_place && !p->ip2) ? 0 : p->drain_kb;
     a.drain_form = p->drain_form;
     a.A_hi = s.A_hi;
     a.A_lo = s.A_lo;
@@ -378,7 +379,10 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         d.prev_sums = s.flushes > 0 ? 1 : 0;
         d.subtract_mean = s.d.subtract_mean;
         d.T = s.T;
-        CU_CHECK(p, launch_flush_tc_direct(a, d, s.tc_maps.data(), st), "flush (tensor cores, in place)");
+        if (p->ip2)
+            CU_CHECK(p, launch_flush_tc_inplace(a, d, st), "flush (tensor cores, in place, drained)");
+        else
+            CU_CHECK(p, launch_flush_tc_direct(a, d, s.tc_maps.data(), st), "flush (tensor cores, in place)");
         p->launches++;
     } else if (p->prec == TACAW_PREC_SPLIT_BF16) {
         if (n % p->bf) {
@@ -823,13 +827,33 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     const bool auto_acc = desc->tc_accumulators == 0 && !desc->tc_drain_frames && !desc->tc_pair &&
                           desc->tc_cluster <= 1;
     const int drain_frames = desc->tc_drain_frames ? desc->tc_drain_frames : (auto_acc ? 512 : 0);
-    const bool drained = drain_frames > 0 && desc->precision == TACAW_PREC_SPLIT_BF16 && !desc->frames_in_place;
+    // in-place frames: the persistent drained kernel reads each tile's 128 rows of every frame
+    // with one contiguous copy, which needs (per stream) the rows of a tile contiguous in the
+    // frame and 16-byte aligned copies; otherwise the register-fed in-place kernel runs
+    bool ip2 = desc->frames_in_place && desc->precision == TACAW_PREC_SPLIT_BF16 &&
+               (desc->tc_accumulators == 0 || desc->tc_accumulators == 2) && !desc->tc_pair &&
+               desc->tc_cluster <= 1 && (desc->tc_block_frames == 0 || desc->tc_block_frames == 32) &&
+               desc->k_stage % 32 == 0;
+    for (int i = 0; i < desc->n_streams && ip2; ++i) {
+        const tacaw_stream_desc &d = desc->streams[i];
+        const int64_t npix = (int64_t)d.kx * d.ky, M = npix * d.n_probes;
+        const bool even = M % 2 == 0 && d.kx % 2 == 0 && d.pitch_row % 2 == 0 && d.roi_x0 % 2 == 0 &&
+                          d.pitch_frame % 2 == 0 && (d.n_probes == 1 || d.pitch_probe % 2 == 0);
+        const bool rows_contiguous =
+            d.kx % kMTile == 0 ||
+            (d.pitch_row == d.kx && d.roi_x0 == 0 && (npix % kMTile == 0 || d.n_probes == 1 || d.pitch_probe == npix));
+        ip2 = even && rows_contiguous;
+    }
+    p->ip2 = ip2;
+    const bool drained = (drain_frames > 0 && desc->precision == TACAW_PREC_SPLIT_BF16 && !desc->frames_in_place) || ip2;
     // drained forms: 1 = all products in one double-buffered accumulator, 2 = hi*hi drained, the
     // small products in a second accumulator
-    if (drained) p->drain_form = (desc->tc_accumulators == 2 || auto_acc) ? 2 : 1;
+    if (drained) p->drain_form = (desc->tc_accumulators == 2 || auto_acc || ip2) ? 2 : 1;
     if (drained) p->tc_acc = p->drain_form;
     // TMEM columns per tile: accumulators side by side (the drained form holds two buffers)
     const int tile_acc = drained ? 2 : p->tc_acc;
+    // widest tile: the drained forms' register sums; in place, also the raw frame ring
+    const int tile_cap = ip2 ? kInplaceMaxOmegaTile : (drained ? kDrainMaxOmegaTile : 0);
     if (desc->frames_in_place && desc->precision != TACAW_PREC_SPLIT_BF16) {
         delete p;
         return fail(TACAW_ERR_UNSUPPORTED, "frames_in_place needs the split-BF16 path");
@@ -871,7 +895,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         s.T_pad = (int)round_up(s.T, p->prec == TACAW_PREC_SPLIT_BF16 ? p->bf : 8);
         s.n_kb_T = s.T_pad / (p->prec == TACAW_PREC_SPLIT_BF16 ? p->bf : 8);
         s.Nw = s.d.n_omega;
-        choose_omega_tile(s, tile_acc, desc->tc_omega_tile, drained ? kDrainMaxOmegaTile : 0);
+        choose_omega_tile(s, tile_acc, desc->tc_omega_tile, tile_cap);
         if (p->prec == TACAW_PREC_FP32) s.Nw_pad = (int)round_up(s.Nw, 64);
         T_pad_max = std::max(T_pad_max, s.T_pad);
         // Welch: ceil(T / stride) lanes (segments that overlap in time), each an internal stream
@@ -910,7 +934,8 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
             while (p->bf > 8 && tc_stages_for(max_cols(), p->bf) < 2) p->bf /= 2;
         for (auto &s : p->s) s.n_kb_T = s.T_pad / p->bf;
         p->tc_prefetch = desc->tc_prefetch > 0 ? desc->tc_prefetch : 0;
-        if (drained) p->drain_kb = std::max(1, drain_frames / p->bf);
+        if (drained) p->drain_kb = std::max(1, (ip2 ? (desc->tc_drain_frames ? desc->tc_drain_frames : 512)
+                                                     : drain_frames) / p->bf);
         // autotuner: time the candidate tiles of every stream shape (staged operands only)
         if (desc->tune_cache_path && !p->in_place) {
             const auto t0 = std::chrono::steady_clock::now();
@@ -1031,7 +1056,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
                 s.tc_pair = desc->tc_pair;
                 s.tc_cluster = 2;
             }
-            s.stages = tc_stages_for(N, p->bf, s.tc_pair);
+            s.stages = p->ip2 ? tc_inplace_stages(N, p->bf) : tc_stages_for(N, p->bf, s.tc_pair);
             if (s.stages < 2)
                 return bail(fail(TACAW_ERR_UNSUPPORTED, "tensor-core tile of %d columns does not fit shared memory",
                                  2 * s.wt));
@@ -1121,6 +1146,8 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
     if (n_frames < 1) return fail(TACAW_ERR_INVALID_ARG, "n_frames must be >= 1");
     if (p->finalized) return fail(TACAW_ERR_STATE, "segment finalized; call tacaw_reset first");
     if ((reinterpret_cast<uintptr_t>(d_frames) & 7) != 0) return fail(TACAW_ERR_INVALID_ARG, "d_frames must be 8-byte aligned");
+    if (p->ip2 && (reinterpret_cast<uintptr_t>(d_frames) & 15) != 0)
+        return fail(TACAW_ERR_INVALID_ARG, "in-place frames must be 16-byte aligned (contiguous row copies)");
     UserStream &u = p->us[sid];
     if (u.pushed + n_frames > u.total)
         return fail(TACAW_ERR_OVERFLOW, "push of %d frames exceeds %lld (already %lld)", n_frames, (long long)u.total,
@@ -1216,6 +1243,7 @@ tacaw_status tacaw_plan_get_info(tacaw_plan_t p, tacaw_plan_info *info) {
     info->frames_in_place = p->in_place ? 1 : 0;
     info->tc_pair = (p->prec == TACAW_PREC_SPLIT_BF16 && !p->s.empty()) ? p->s[0].tc_pair : 0;
     info->tc_drain_frames = p->drain_kb * p->bf;
+    info->tc_inplace_form = p->in_place ? (p->ip2 ? 2 : 1) : 0;
     return TACAW_OK;
 }
 

@@ -296,9 +296,14 @@ cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps /* TcMaps */, 
 int64_t tc_grid_ctas(const TcPlanArgs &a);
 constexpr int kMaxGroupStreams = 16;
 constexpr int kDrainMaxOmegaTile = 112;   // drained form: complex energies per tile at most
+constexpr int kInplaceMaxOmegaTile = 88;  // in-place drained form (the raw frame ring shares smem)
 // one launch over up to kMaxGroupStreams streams' flushes (same cluster size and block frames)
 cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *maps, int n, cudaStream_t st);
 cudaError_t launch_flush_tc_direct(const TcPlanArgs &a, const TcDirectArgs &d, const void *maps, cudaStream_t st);
+// persistent in-place drained form: tile rows contiguous and 16-byte aligned in every frame
+// (host-checked), 128-byte staging rows, tiles of at most kDrainMaxOmegaTile energies
+cudaError_t launch_flush_tc_inplace(const TcPlanArgs &a, const TcDirectArgs &d, cudaStream_t st);
+int tc_inplace_stages(int N, int bf);
 bool tc_make_maps_b(void *maps_out, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
                     int N, int bf, char *errbuf, size_t errlen);
 size_t tc_smem_bytes_direct(int N, int bf, int stages);

@@ -66,7 +66,8 @@ class CPlanInfo(ctypes.Structure):
                 ("I_elems", c_int64), ("S_elems", c_int64), ("flushes", c_int64), ("omega_tile", c_int),
                 ("stages", c_int), ("kernel_launches", c_int64), ("tc_accumulators", c_int),
                 ("tc_cluster", c_int), ("tc_block_frames", c_int), ("frames_in_place", c_int),
-                ("tc_pair", c_int), ("tc_drain_frames", c_int), ("tuned_streams", c_int), ("tune_candidates", c_int), ("tune_ms", c_double)]
+                ("tc_pair", c_int), ("tc_drain_frames", c_int), ("tuned_streams", c_int), ("tune_candidates", c_int), ("tune_ms", c_double),
+                ("tc_inplace_form", c_int)]
 
 
 _lib = None
