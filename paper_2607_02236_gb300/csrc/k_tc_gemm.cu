@@ -125,6 +125,22 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_fla
         if (globaltimer() - t0 > kWaitLimitNs) return false;
     }
 }
+// Warp-uniform bounded wait: lane 0 waits, every lane gets its verdict (so no lane of the warp
+// can leave a loop that the others stay in), and the warp synchronises for memory ordering.
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
                                             uint32_t bar) {
     asm volatile(
@@ -132,6 +148,24 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
             dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
         : "memory");
+}
+// 16-byte asynchronous copy global -> shared through L2 (LSU path), and the arrive on an
+// mbarrier once all of this thread's earlier such copies have landed (counted as one of the
+// barrier's expected arrivals)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(reinterpret_cast<uint64_t>(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Running FP32 sum with a compensation term (Kahan)
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
 }
 // Contiguous copy global -> shared (16-byte aligned addresses, size a multiple of 16)
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
@@ -367,12 +401,16 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// (re, im) -> packed bf16x2 hi = RN(re, im) and lo = RN(residuals), re in the low half: one
+// paired conversion each (the unpacking of hi back to FP32 is two bit operations).
 __device__ __forceinline__ void split2_bf16(float2 r, uint32_t &hi, uint32_t &lo) {
-    const __nv_bfloat16 hr = __float2bfloat16_rn(r.x), hi_ = __float2bfloat16_rn(r.y);
-    const __nv_bfloat16 lr = __float2bfloat16_rn(r.x - __bfloat162float(hr));
-    const __nv_bfloat16 li = __float2bfloat16_rn(r.y - __bfloat162float(hi_));
-    hi = (uint32_t)__bfloat16_as_ushort(hr) | ((uint32_t)__bfloat16_as_ushort(hi_) << 16);
-    lo = (uint32_t)__bfloat16_as_ushort(lr) | ((uint32_t)__bfloat16_as_ushort(li) << 16);
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(r.x, r.y);
+    uint32_t hb;
+    memcpy(&hb, &h2, sizeof(hb));
+    const float hr = __uint_as_float(hb << 16), him = __uint_as_float(hb & 0xffff0000u);
+    const __nv_bfloat162 l2 = __floats2bfloat162_rn(r.x - hr, r.y - him);
+    hi = hb;
+    memcpy(&lo, &l2, sizeof(lo));
 }
 
 // MMA issue loop of the in-place kernel (one thread): per stage, bf/8 K-steps of 3 products
@@ -449,16 +487,17 @@ __device__ __forceinline__ void tc_mma_loop(const TcPlanArgs &a, TcShared *sh, u
 // warp-uniform; columns past `cols` (up to 15 of them, inside the allocation) are loaded and
 // ignored.
 constexpr int kDrainCols = 112;
-__device__ __forceinline__ void drain_add(float (&sum)[kDrainCols], uint32_t taddr, int cols) {
+template <int C>
+__device__ __forceinline__ void drain_add(float (&sum)[C], uint32_t taddr, int cols) {
 #pragma unroll
-    for (int r = 0; r < kDrainCols / 16; ++r) {
+    for (int r = 0; r < (C + 15) / 16; ++r) {
         if (r * 16 < cols) {
             uint32_t x[16];
             tmem_ld_x16(taddr + (uint32_t)(r * 16), x);
             tmem_ld_wait();
 #pragma unroll
             for (int i = 0; i < 16; ++i)
-                if (r * 16 + i < cols) sum[r * 16 + i] += __uint_as_float(x[i]);
+                if (r * 16 + i < C && r * 16 + i < cols) sum[r * 16 + i] += __uint_as_float(x[i]);
         }
         __syncwarp();
     }
@@ -494,12 +533,12 @@ __device__ __forceinline__ void tc_epilogue_drained(const TcPlanArgs &a, const R
 }
 
 // Flush epilogue of the split drained form: the tile's result is all in the running sums.
-template <int KIND>
+template <int KIND, int C>
 __device__ __forceinline__ void tc_epilogue_regs(const TcPlanArgs &a, const RowCtx &row, int col0, int cols,
-                                                 int jbase, const float (&sum)[kDrainCols]) {
+                                                 int jbase, const float (&sum)[C]) {
     if (!row.valid) return;
 #pragma unroll
-    for (int i = 0; i < kDrainCols / 2; ++i) {
+    for (int i = 0; i < C / 2; ++i) {
         const int c = 2 * i;
         const int j = jbase + ((col0 + c) >> 1);
         if (c < cols && j < a.e.Nw)
@@ -1247,39 +1286,141 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
 
 
 // --------------------------------------------------------------------------------------
-// In-place drained form (persistent): operand A is read from the caller's pushed complex64
-// frames without a staging pass.  For every staging block the producer copies, per frame, the
-// tile's 128 rows (contiguous in the frame: checked by the host) into a raw ring with
-// contiguous bulk copies; two converter warps subtract the provisional mean, split into bf16
-// hi/lo and write the swizzled K-major rows of the stage, keeping each row's residual sum for
-// the exact mean correction.  Accumulation as in the split drained form (H drained every
-// drain_kb blocks, S for the whole tile).
+// In-place drained form (persistent), operand A in tensor memory.  The pushed complex64 frames
+// are read without a staging pass: for every 32-frame block of a tile the producer copies, per
+// frame, the tile's 128 rows (contiguous in the frame: checked by the host) into a ring of raw
+// stages with contiguous bulk copies.  Eight worker warps subtract the provisional mean, split
+// each value into bf16 hi/lo and write them to tensor memory with tcgen05.st, one TMEM column
+// per frame (the packed (re, im) pair is one 32-bit column, two K elements): the MMAs take A
+// from tensor memory and only the twiddle rows from shared memory, so neither the swizzled
+// A layout nor its shared-memory bandwidth is needed.  Accumulation as in the split drained
+// form: H = hi*hi drained into FP32 registers every drain_kb blocks, S = the small products
+// for the whole tile.  The same warps drain and run the epilogues; a tile's final epilogue
+// waits until the first `defer` blocks of the next tile are converted, so the tensor pipe has
+// work while it runs.
 //
-//   warp 0     producer: twiddle rows (pre-swizzled, bulk) and raw frame rows (lane f: frame f)
+//   warp 0     raw frame producer (16-byte asynchronous copies, 512 contiguous bytes a warp
+//              instruction), up to raw_stages blocks ahead
 //   warp 1     TMEM allocation and MMA issue
-//   warps 2-3  converters: thread i handles rows i and i + 64 of the tile
-//   warps 4-11 drains and epilogues
-// 384 threads: three warps on each register file, 168 registers a thread.
+//   warp 10    twiddle producer (pre-swizzled rows, one bulk copy for hi and one for lo)
+//   warps 2-9  workers: warp w owns TMEM lanes / tile rows 32 (w % 4) .. + 31; h = (w - 2) / 4
+//              selects frames 16 h .. 16 h + 15 of each block and accumulator columns
+//              [h wt, (h + 1) wt) of the drains and epilogue
+// TMEM columns: H [0, N), S [acc_s, acc_s + N), A stage s [a_col + 64 s, + 64): hi 32 | lo 32.
+// 352 threads put three warps on three of the four register files: at most 168 registers a
+// thread, which bounds the drained columns a worker holds (kIpCols).
+constexpr int kIpRawMax = 4;
+constexpr int kIpBlockFrames = 32;
+constexpr int kIpCols = 56;          // accumulator columns a worker drains (tiles of <= 56 energies)
 struct TcInplaceArgs {
+    CUtensorMap fmap;          // frames of the flush as [n_frames][pitch_frame] complex64 (fmap_ok)
+    int fmap_ok;               // evenly spaced frames: one 2-D box of 32 frames x 128 rows a block
     TcPlanArgs a;
     TcDirectArgs d;
-    int stages;                // operand ring stages
+    int stages;                // A (tensor memory) + B (shared memory) stages
+    int raw_stages;            // raw frame stages
+    int defer;                 // blocks of the next tile converted before a tile's final epilogue
+    uint32_t acc_s;            // TMEM column of the small-product accumulator
+    uint32_t a_col;            // TMEM column of A stage 0
     int64_t tiles;             // (M_pad / 128) * n_wt
 };
+struct IpShared {
+    uint64_t full[kMaxStages];      // twiddle copies landed + the 8 workers stored A
+    uint64_t empty[kMaxStages];     // the stage's MMAs completed
+    uint64_t raw_full[kIpRawMax];   // raw frame rows landed
+    uint64_t raw_empty[kIpRawMax];  // the 8 workers read them
+    uint64_t chunk_full[2];         // [0] an H chunk is complete, [1] the tile's H and S are
+    uint64_t chunk_free[2];         // the workers drained them
+    uint64_t sums_full[2];          // a tile's residual row sums are in `part` (by tile parity)
+    uint64_t tmem_full;
+    uint32_t tmem_addr;
+    int abort_flag;
+    double2 part[2][2][kMTile];     // [tile parity][frame half][row] sums of (psi - mu_hat)
+};
 
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st_x8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Final of one tile in a worker thread: the last H chunk and S added to the running sums, the
+// mean correction from the tile's residual sums, the epilogue.  Returns false on a timeout.
+template <int KIND>
+__device__ __forceinline__ bool ip_final(const TcInplaceArgs &g, IpShared *sh, float (&sum)[kIpCols], int t,
+                                         int cnt, int h, int rr, uint32_t hbase, uint32_t sbase,
+                                         volatile int *abort_flag) {
+    const TcPlanArgs &a = g.a;
+    const TcDirectArgs &d = g.d;
+    const int lane = threadIdx.x & 31;
+    if (!mbar_wait_warp(smem_u32(&sh->sums_full[cnt & 1]), (uint32_t)((cnt >> 1) & 1), abort_flag) ||
+        !mbar_wait_warp(smem_u32(&sh->chunk_full[1]), (uint32_t)(cnt & 1), abort_flag)) {
+        if (lane == 0 && !*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
+        *abort_flag = 1;
+        return false;
+    }
+    tc_fence_after();
+    const int cols = a.wt;
+    drain_add(sum, hbase, cols);
+    drain_add(sum, sbase, cols);
+    tc_fence_before();
+    const double2 p0 = sh->part[cnt & 1][0][rr], p1 = sh->part[cnt & 1][1][rr];
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_u32(&sh->chunk_free[1]));
+    const int wtile = t % a.n_wt;
+    const int64_t m0 = (int64_t)(t / a.n_wt) * kMTile;
+    RowCtx row;
+    row.m = m0 + rr;
+    row.valid = row.m < d.M;
+    const int64_t p = row.valid ? row.m / d.npix : 0;
+    row.out_base = p * (int64_t)a.e.Nw * d.npix + (row.m - p * d.npix);
+    row.dmu = make_float2(0.f, 0.f);
+    double2 tt = make_double2(p0.x + p1.x, p0.y + p1.y);
+    if (row.valid && h == 0 && wtile == 0 && d.accumulate_sums) {
+        double2 s = d.sum_res[row.m];
+        s.x += tt.x;
+        s.y += tt.y;
+        d.sum_res[row.m] = s;
+    }
+    if (row.valid && d.subtract_mean && a.e.mode == FLUSH_FINAL) {
+        if (d.prev_sums) {
+            const double2 pv = d.sum_res[row.m];
+            tt.x += pv.x;
+            tt.y += pv.y;
+        }
+        row.dmu = make_float2((float)(tt.x / d.T), (float)(tt.y / d.T));
+    }
+    const int col0 = h * cols, jbase = wtile * a.wt;
+    tc_epilogue_regs<KIND>(a, row, col0, cols, jbase, sum);
+#pragma unroll
+    for (int k = 0; k < kIpCols; ++k) sum[k] = 0.f;
+    return true;
+}
+
+template <int KIND>
 __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__ TcInplaceArgs g) {
     const TcPlanArgs &a = g.a;
     const TcDirectArgs &d = g.d;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int bf = a.bf, stages = g.stages, N = a.N;
-    const uint32_t RB = 4u * (uint32_t)bf;
-    const uint32_t kABytes = tc_a_bytes(bf);
-    const uint32_t b_pad = tc_b_bytes_padded(N, bf);
-    const uint32_t stage_bytes = tc_stage_bytes(N, bf);
-    const uint32_t raw_bytes = (uint32_t)bf * (uint32_t)kMTile * 8u;          // one raw stage
-    uint8_t *raw = base + (size_t)stages * stage_bytes;
-    TcShared *sh = reinterpret_cast<TcShared *>(raw + 2 * (size_t)raw_bytes);
+    constexpr int BF = kIpBlockFrames;
+    const int stages = g.stages, R = g.raw_stages, N = a.N;
+    constexpr uint32_t RB = 4u * BF;                                   // bytes per twiddle row
+    const uint32_t b_pad = tc_b_bytes_padded(N, BF);
+    const uint32_t b_stage = 2u * b_pad;                               // twiddle rows hi | lo
+    constexpr uint32_t raw_bytes = (uint32_t)BF * kMTile * 8u;         // one raw stage
+    uint8_t *raw = base + (size_t)stages * b_stage;
+    IpShared *sh = reinterpret_cast<IpShared *>(raw + (size_t)R * raw_bytes);
     const uint32_t base_s = smem_u32(base), raw_s = smem_u32(raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n_tiles = g.tiles;
@@ -1290,16 +1431,18 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
     }
     if (threadIdx.x == 0) {
         for (int st = 0; st < stages; ++st) {
-            mbar_init(smem_u32(&sh->full[st]), 3);   // twiddle copies + two converter warps
+            mbar_init(smem_u32(&sh->full[st]), 9);   // twiddle copies + eight worker warps
             mbar_init(smem_u32(&sh->empty[st]), 1);
         }
+        for (int r = 0; r < R; ++r) {
+            // one tensor copy (arrive with its bytes), or the producer warp's 32 lanes' copies
+            mbar_init(smem_u32(&sh->raw_full[r]), g.fmap_ok ? 1 : 32);
+            mbar_init(smem_u32(&sh->raw_empty[r]), 8);
+        }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&sh->raw_full[b]), 1);
-            mbar_init(smem_u32(&sh->raw_empty[b]), 2);
-            mbar_init(smem_u32(&sh->sums_full[b]), 2);
-            mbar_init(smem_u32(&sh->sums_free[b]), 8);
             mbar_init(smem_u32(&sh->chunk_full[b]), 1);
             mbar_init(smem_u32(&sh->chunk_free[b]), 8);
+            mbar_init(smem_u32(&sh->sums_full[b]), 8);
         }
         mbar_init(smem_u32(&sh->tmem_full), 1);
         sh->abort_flag = 0;
@@ -1317,95 +1460,120 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
     if (trace && threadIdx.x == 0) trace[1] = globaltimer();
 
     if (warp == 0) {
-        // ---------------- producer ----------------
-        int s = 0, r = 0;
-        uint32_t ph = 0, rph = 0;
-        int op_issued = 0, raw_issued = 0;
-        const uint32_t tx_b = 2u * (uint32_t)N * RB;
+        // ---------------- raw frame producer: runs up to raw_stages blocks ahead ----------------
+        int r = 0, tma_issued = 0;
+        uint32_t rph = 0;
         for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
-            const int wtile = (int)(t % a.n_wt);
             const int64_t m0 = (t / a.n_wt) * kMTile;
             const int nrows = (int)(d.M - m0 < kMTile ? d.M - m0 : kMTile);   // even (host-checked)
             const int64_t p = m0 / d.npix, pix = m0 - p * d.npix;
             const int64_t y = pix / d.kx, x = pix - y * d.kx;
             const int64_t off = p * d.pitch_probe + (d.roi_y0 + y) * d.pitch_row + (d.roi_x0 + x);
-            const uint8_t *pBhi = static_cast<const uint8_t *>(a.B_hi) +
-                                  ((size_t)a.kbB0 * (size_t)a.b_rows + (size_t)wtile * N) * RB;
-            const uint8_t *pBlo = static_cast<const uint8_t *>(a.B_lo) +
-                                  ((size_t)a.kbB0 * (size_t)a.b_rows + (size_t)wtile * N) * RB;
-            const size_t b_step = (size_t)a.b_rows * RB;
+            const int nchunk = nrows / 2;                 // 16-byte chunks of a frame's rows
             bool stop = false;
-            for (int kb = 0; kb < a.n_kb && !stop; ++kb) {
-                // raw frame rows of this block: lane f copies frame kb*bf + f
-                const int f = kb * bf + lane;
-                const float2 *fp = (lane < bf && f < d.n_frames) ? d.frame_ptr[f] : nullptr;
-                const int nfr = min(bf, d.n_frames - kb * bf);
-                if (!mbar_wait(smem_u32(&sh->raw_empty[r]), rph ^ 1u, abort_flag)) {
+            for (int kb = 0; kb < a.n_kb; ++kb) {
+                const int f = kb * BF + lane;
+                const float2 *fp = f < d.n_frames ? d.frame_ptr[f] + off : nullptr;
+                const int nfr = min(BF, d.n_frames - kb * BF);
+                if (!mbar_wait_warp(smem_u32(&sh->raw_empty[r]), rph ^ 1u, abort_flag)) {
                     if (lane == 0 && !*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
                     *abort_flag = 1;
+                    stop = true;
                     break;
                 }
-                const uint32_t rf = smem_u32(&sh->raw_full[r]);
-                if (lane == 0) mbar_arrive_expect_tx(rf, (uint32_t)nfr * (uint32_t)nrows * 8u);
-                __syncwarp();
-                if (fp) bulk_load(raw_s + (uint32_t)r * raw_bytes + (uint32_t)lane * (uint32_t)kMTile * 8u, fp + off,
-                                  (uint32_t)nrows * 8u, rf);
-                raw_issued = raw_issued < 2 ? raw_issued + 1 : 2;
-                if (++r == 2) {
+                if (g.fmap_ok) {
+                    // one box: 32 frames x 128 rows (frames past the flush and rows past the
+                    // frame read as zeros; the full box's bytes arrive)
+                    if (lane == 0) {
+                        const uint32_t rf = smem_u32(&sh->raw_full[r]);
+                        mbar_arrive_expect_tx(rf, raw_bytes);
+                        tma_load_2d(raw_s + (uint32_t)r * raw_bytes, &g.fmap, (int)off, kb * BF, rf);
+                    }
+                    tma_issued = tma_issued < R ? tma_issued + 1 : R;
+                } else {
+                    // frame j's rows: 16-byte chunks lane, lane + 32 (512 contiguous bytes a warp
+                    // instruction); rows past M and frames past the flush stay stale (masked)
+                    const uint32_t dst = raw_s + (uint32_t)r * raw_bytes + (uint32_t)lane * 16u;
+                    for (int j = 0; j < nfr; ++j) {
+                        const char *src =
+                            reinterpret_cast<const char *>(__shfl_sync(0xffffffffu, (unsigned long long)fp, j));
+                        if (lane < nchunk) cp_async16(dst + (uint32_t)j * kMTile * 8u, src + lane * 16);
+                        if (lane + 32 < nchunk)
+                            cp_async16(dst + (uint32_t)j * kMTile * 8u + 512u, src + lane * 16 + 512);
+                    }
+                    cp_async_arrive(smem_u32(&sh->raw_full[r]));
+                }
+                if (++r == R) {
                     r = 0;
                     rph ^= 1u;
-                }
-                // twiddle rows of this block
-                if (lane == 0) {
-                    if (!mbar_wait(smem_u32(&sh->empty[s]), ph ^ 1u, abort_flag)) {
-                        if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
-                        *abort_flag = 1;
-                        stop = true;
-                    } else {
-                        const uint32_t full = smem_u32(&sh->full[s]);
-                        const uint32_t st = base_s + (uint32_t)s * stage_bytes;
-                        mbar_arrive_expect_tx(full, tx_b);
-                        bulk_load(st + 2 * kABytes, pBhi + (size_t)kb * b_step, (uint32_t)N * RB, full);
-                        bulk_load(st + 2 * kABytes + b_pad, pBlo + (size_t)kb * b_step, (uint32_t)N * RB, full);
-                    }
-                }
-                stop = __shfl_sync(0xffffffffu, stop ? 1 : 0, 0) != 0;
-                if (!stop) op_issued = op_issued < stages ? op_issued + 1 : stages;
-                if (++s == stages) {
-                    s = 0;
-                    ph ^= 1u;
                 }
             }
             if (stop) break;
         }
+        // no copy may still be landing in this CTA's shared memory when it exits
+        cp_async_wait_all();
         if (*abort_flag && lane == 0) {
-            // let every copy into this CTA's rings land before it can exit.  The twiddle copies
-            // share their stage barrier with the converters, which may never arrive: give them
-            // a fixed 20 ms (copies take microseconds); the raw copies have barriers of their own
-            if (op_issued > 0) {
-                const uint64_t t0 = globaltimer();
-                while (globaltimer() - t0 < 20000000ull) {
-                }
-            }
+            // tensor copies in flight land on their raw stage's barrier
             int kr = r;
             uint32_t krp = rph;
-            for (int i = 0; i < raw_issued; ++i) {
+            for (int i = 0; i < tma_issued; ++i) {
                 if (--kr < 0) {
-                    kr = 1;
+                    kr = R - 1;
                     krp ^= 1u;
                 }
                 if (!mbar_wait(smem_u32(&sh->raw_full[kr]), krp, nullptr)) atomicOr(a.err, DEVERR_TIMEOUT_DRAIN);
             }
         }
-    } else if (warp == 1) {
-        // ---------------- MMA (split drained form) ----------------
+    } else if (warp == 10) {
+        // ---------------- twiddle producer ----------------
         if (lane == 0) {
-            const int ksteps = bf / 8;
+            int s = 0;
+            uint32_t ph = 0;
+            int op_issued = 0;
+            const uint32_t tx_b = 2u * (uint32_t)N * RB;
+            const size_t b_step = (size_t)a.b_rows * RB;
+            bool stop = false;
+            for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x) {
+                const int wtile = (int)(t % a.n_wt);
+                const uint8_t *pBhi = static_cast<const uint8_t *>(a.B_hi) +
+                                      ((size_t)a.kbB0 * (size_t)a.b_rows + (size_t)wtile * N) * RB;
+                const uint8_t *pBlo = static_cast<const uint8_t *>(a.B_lo) +
+                                      ((size_t)a.kbB0 * (size_t)a.b_rows + (size_t)wtile * N) * RB;
+                for (int kb = 0; kb < a.n_kb; ++kb) {
+                    if (!mbar_wait(smem_u32(&sh->empty[s]), ph ^ 1u, abort_flag)) {
+                        if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
+                        *abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    const uint32_t full = smem_u32(&sh->full[s]);
+                    const uint32_t st = base_s + (uint32_t)s * b_stage;
+                    mbar_arrive_expect_tx(full, tx_b);
+                    bulk_load(st, pBhi + (size_t)kb * b_step, (uint32_t)N * RB, full);
+                    bulk_load(st + b_pad, pBlo + (size_t)kb * b_step, (uint32_t)N * RB, full);
+                    op_issued = op_issued < stages ? op_issued + 1 : stages;
+                    if (++s == stages) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            if (*abort_flag && op_issued > 0) {
+                // the twiddle copies share their stage barrier with the workers, which may never
+                // arrive: give them a fixed 20 ms to land (copies take microseconds)
+                const uint64_t t0 = globaltimer();
+                while (globaltimer() - t0 < 20000000ull) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA: A from tensor memory, B from shared memory ----------------
+        if (lane == 0) {
             int s = 0;
             uint32_t ph = 0, hph = 0, tph = 0;
             int64_t tiles = 0;
             bool stop = false;
-            const uint32_t accH = tmem, accS = tmem + 256u;
+            const uint32_t accH = tmem, accS = tmem + g.acc_s;
             const uint32_t id = idesc_bf16_f32(kMTile, N);
             const int cb = a.drain_kb;
             for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x, ++tiles) {
@@ -1428,15 +1596,15 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
                     }
                     tc_fence_after();
                     if (trace && tiles == 0 && kb == 0) trace[2] = globaltimer();
-                    const uint32_t st = base_s + (uint32_t)s * stage_bytes;
-                    const uint64_t dAhi0 = sdesc_k(st, RB);
-                    const uint64_t dAlo0 = sdesc_k(st + kABytes, RB);
-                    const uint64_t dBhi0 = sdesc_k(st + 2 * kABytes, RB);
-                    const uint64_t dBlo0 = sdesc_k(st + 2 * kABytes + b_pad, RB);
-                    for (int ks = 0; ks < ksteps; ++ks) {
+                    const uint32_t aH = tmem + g.a_col + 64u * (uint32_t)s, aL = aH + 32u;
+                    const uint32_t st = base_s + (uint32_t)s * b_stage;
+                    const uint64_t dBhi0 = sdesc_k(st, RB);
+                    const uint64_t dBlo0 = sdesc_k(st + b_pad, RB);
+#pragma unroll
+                    for (int ks = 0; ks < BF / 8; ++ks) {
                         const uint64_t adv = (uint64_t)(2 * ks);
-                        mma_bf16_ss(accS, dAhi0 + adv, dBlo0 + adv, id, (kb == 0 && ks == 0) ? 0u : 1u);
-                        mma_bf16_ss(accS, dAlo0 + adv, dBhi0 + adv, id, 1u);
+                        mma_bf16_ts(accS, aH + 8u * ks, dBlo0 + adv, id, (kb == 0 && ks == 0) ? 0u : 1u);
+                        mma_bf16_ts(accS, aL + 8u * ks, dBhi0 + adv, id, 1u);
                     }
                     if (kc == 0 && kb > 0) {
                         if (!mbar_wait(smem_u32(&sh->chunk_free[0]), hph, abort_flag)) {
@@ -1448,9 +1616,10 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
                         hph ^= 1u;
                         tc_fence_after();
                     }
-                    for (int ks = 0; ks < ksteps; ++ks) {
+#pragma unroll
+                    for (int ks = 0; ks < BF / 8; ++ks) {
                         const uint64_t adv = (uint64_t)(2 * ks);
-                        mma_bf16_ss(accH, dAhi0 + adv, dBhi0 + adv, id, (kc == 0 && ks == 0) ? 0u : 1u);
+                        mma_bf16_ts(accH, aH + 8u * ks, dBhi0 + adv, id, (kc == 0 && ks == 0) ? 0u : 1u);
                     }
                     mma_commit(smem_u32(&sh->empty[s]));
                     if (++s == stages) {
@@ -1472,181 +1641,128 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
                 trace[5] = 0;
             }
         }
-    } else if (warp < 4) {
-        // ---------------- converters ----------------
-        const int i = threadIdx.x - 64;               // rows i and i + 64 of the tile
-        const int cpr = bf / 4;
+    } else {
+        // ---------------- workers: conversion into TMEM, drains, epilogues ----------------
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int rr = q * 32 + lane;                                   // tile row = TMEM lane
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        const int cols = a.wt;
+        const uint32_t hbase = tmem + lane_off + (uint32_t)(h * cols);
+        const uint32_t sbase = tmem + lane_off + g.acc_s + (uint32_t)(h * cols);
+        const uint32_t abase = tmem + lane_off + g.a_col + 16u * (uint32_t)h;
+        const int cb = a.drain_kb, D = g.defer;
+        float sum[kIpCols];
+#pragma unroll
+        for (int k = 0; k < kIpCols; ++k) sum[k] = 0.f;
         int s = 0, r = 0;
         uint32_t ph = 0, rph = 0;
-        int64_t tiles = 0;
-        bool ok = true;
-        for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tiles) {
-            const int wtile = (int)(t % a.n_wt);
-            const int64_t m0 = (t / a.n_wt) * kMTile;
-            const int sb = (int)(tiles & 1);
-            float2 mu[2];
-            bool valid[2];
-            double sr[2] = {0.0, 0.0}, si[2] = {0.0, 0.0};
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t m = m0 + i + 64 * h;
-                valid[h] = m < d.M;
-                mu[h] = valid[h] ? d.mu_hat[m] : make_float2(0.f, 0.f);
-            }
-            for (int kb = 0; kb < a.n_kb; ++kb) {
-                if (!mbar_wait(smem_u32(&sh->raw_full[r]), rph, abort_flag) ||
-                    !mbar_wait(smem_u32(&sh->empty[s]), ph ^ 1u, abort_flag)) {
-                    if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
+        uint32_t hc = 0;
+        int tiles = 0, fin_t = -1, fin_cnt = 0;   // tile indices fit 31 bits (host-checked)
+        int t = (int)blockIdx.x;
+        int kb = 0;
+        bool valid = false;
+        float2 mu = make_float2(0.f, 0.f);
+        // per-tile residual sums in FP32 with compensation (FP64 arithmetic is slow on this part)
+        float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
+        // one pass per block of this CTA's tiles, plus a last pass for the last tile's final
+        for (;;) {
+            const bool have = t < n_tiles;
+            if (have) {
+                if (kb == 0) {
+                    const int64_t m = (t / a.n_wt) * kMTile + rr;
+                    valid = m < d.M;
+                    mu = valid ? d.mu_hat[m] : make_float2(0.f, 0.f);
+                    sr = si = cr = ci = 0.f;
+                }
+                if (!mbar_wait_warp(smem_u32(&sh->raw_full[r]), rph, abort_flag) ||
+                    !mbar_wait_warp(smem_u32(&sh->empty[s]), ph ^ 1u, abort_flag)) {
+                    if (lane == 0 && !*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
                     *abort_flag = 1;
-                    ok = false;
                     break;
                 }
-                const int nfr = min(bf, d.n_frames - kb * bf);
-                const uint8_t *rs = raw + (size_t)r * raw_bytes;
-                uint8_t *st = base + (size_t)s * stage_bytes;
+                tc_fence_after();
+                const int nfr = min(BF, d.n_frames - kb * BF);
+                const uint8_t *rs = raw + (size_t)r * raw_bytes + (size_t)rr * 8u;
+                const uint32_t ac = abase + 64u * (uint32_t)s;
+                // all 16 of this warp's frames in flight at once.  The raw stage is always
+                // readable; rows past M and frames past the flush hold stale data and are
+                // replaced by the mean (a zero residual) on the rare partial blocks
+                float2 x[16];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int row = i + 64 * h;
-                    const uint32_t row_byte = (uint32_t)row * RB;
-                    const uint32_t sw = (row_byte >> 7) & (uint32_t)(cpr - 1);
-                    float br = 0.f, bi = 0.f;
-                    for (int c = 0; c < cpr; ++c) {
-                        uint32_t hw[4], lw[4];
+                for (int f = 0; f < 16; ++f)
+                    x[f] = *reinterpret_cast<const float2 *>(rs + (size_t)(16 * h + f) * kMTile * 8u);
+                if (!valid || nfr < BF) {
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int fr = 4 * c + q;
-                            float2 v = make_float2(0.f, 0.f);
-                            if (valid[h] && fr < nfr) {
-                                const float2 x = *reinterpret_cast<const float2 *>(rs + (size_t)fr * kMTile * 8 + row * 8);
-                                v = make_float2(x.x - mu[h].x, x.y - mu[h].y);
-                            }
-                            br += v.x;
-                            bi += v.y;
-                            split2_bf16(v, hw[q], lw[q]);
-                        }
-                        const uint32_t chunk = ((uint32_t)c ^ sw) * 16u;
-                        *reinterpret_cast<uint4 *>(st + row_byte + chunk) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                        *reinterpret_cast<uint4 *>(st + kABytes + row_byte + chunk) =
-                            make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    for (int f = 0; f < 16; ++f)
+                        if (!valid || 16 * h + f >= nfr) x[f] = mu;
+                }
+                float br = 0.f, bi = 0.f;
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    uint32_t hw[8], lw[8];
+#pragma unroll
+                    for (int f = 0; f < 8; ++f) {
+                        const float2 v = make_float2(x[8 * half + f].x - mu.x, x[8 * half + f].y - mu.y);
+                        br += v.x;
+                        bi += v.y;
+                        split2_bf16(v, hw[f], lw[f]);
                     }
-                    sr[h] += br;
-                    si[h] += bi;
+                    __syncwarp();
+                    tmem_st_x8(ac + 8u * (uint32_t)half, hw);
+                    tmem_st_x8(ac + 32u + 8u * (uint32_t)half, lw);
                 }
-                // generic-proxy writes -> visible to the tensor core before the arrive
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                kahan_add(sr, cr, br);
+                kahan_add(si, ci, bi);
+                tmem_st_wait();
                 __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(smem_u32(&sh->full[s]));
-                    mbar_arrive(smem_u32(&sh->raw_empty[r]));
-                }
+                if (lane == 0) mbar_arrive(smem_u32(&sh->raw_empty[r]));
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&sh->full[s]));
                 if (++s == stages) {
                     s = 0;
                     ph ^= 1u;
                 }
-                if (++r == 2) {
+                if (++r == R) {
                     r = 0;
                     rph ^= 1u;
                 }
             }
-            if (!ok) break;
-            // this tile's residual sums: to the epilogue, and (first energy tile) to the running
-            // sums; buffer sb was last read by the epilogue for tile `tiles - 2`
-            if (tiles >= 2 &&
-                !mbar_wait(smem_u32(&sh->sums_free[sb]), (uint32_t)(((tiles - 2) >> 1) & 1), abort_flag)) {
-                if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
-                *abort_flag = 1;
-                break;
+            // the previous tile's final, once this tile's first `defer` blocks keep the MMAs
+            // busy (or after the last tile)
+            if (fin_t >= 0 && (!have || kb + 1 == D)) {
+                if (!ip_final<KIND>(g, sh, sum, fin_t, fin_cnt, h, rr, hbase, sbase, abort_flag)) break;
+                fin_t = -1;
             }
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int row = i + 64 * h;
-                sh->tsum[sb][row] = make_double2(sr[h], si[h]);
-                const int64_t m = m0 + row;
-                if (valid[h] && wtile == 0 && d.accumulate_sums) {
-                    double2 tt = d.sum_res[m];
-                    tt.x += sr[h];
-                    tt.y += si[h];
-                    d.sum_res[m] = tt;
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&sh->sums_full[sb]));
-        }
-    } else {
-        // ---------------- drains and epilogues: warps 4..11 ----------------
-        const int q4 = warp & 3, h = (warp - 4) >> 2;
-        float sum[kDrainCols];
-        int64_t hc = 0, tiles = 0;
-        bool ok = true;
-        const int cols = a.wt;
-        const int col0 = h * cols;
-        const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)col0;
-        const int n_chunks = (a.n_kb + a.drain_kb - 1) / a.drain_kb;
-        for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tiles) {
-            const int wtile = (int)(t % a.n_wt);
-            const int64_t m0 = (t / a.n_wt) * kMTile;
-            const int sb = (int)(tiles & 1);
-#pragma unroll
-            for (int k = 0; k < kDrainCols; ++k) sum[k] = 0.f;
-            for (int lc = 0; lc + 1 < n_chunks; ++lc, ++hc) {
-                if (!mbar_wait(smem_u32(&sh->chunk_full[0]), (uint32_t)(hc & 1), abort_flag)) {
-                    if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
+            if (!have) break;
+            // the H chunk that ended with block kb - 1 (drained one block late, so this block's
+            // small products run on the tensor pipe meanwhile)
+            if (kb >= 1 && kb % cb == 0) {
+                if (!mbar_wait_warp(smem_u32(&sh->chunk_full[0]), (uint32_t)(hc & 1), abort_flag)) {
+                    if (lane == 0 && !*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
                     *abort_flag = 1;
-                    ok = false;
                     break;
                 }
                 tc_fence_after();
-                drain_add(sum, lane_base, cols);
+                drain_add(sum, hbase, cols);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&sh->chunk_free[0]));
+                ++hc;
             }
-            if (!ok) break;
-            if (!mbar_wait(smem_u32(&sh->chunk_full[1]), (uint32_t)(tiles & 1), abort_flag) ||
-                !mbar_wait(smem_u32(&sh->sums_full[sb]), (uint32_t)((tiles >> 1) & 1), abort_flag)) {
-                if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
-                *abort_flag = 1;
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            drain_add(sum, lane_base, cols);
-            drain_add(sum, lane_base + 256u, cols);
-            tc_fence_before();
-            const int rr = q4 * 32 + lane;
-            const int64_t m = m0 + rr;
-            RowCtx row;
-            row.m = m;
-            row.valid = m < d.M;
-            const int64_t p = row.valid ? m / d.npix : 0;
-            row.out_base = p * (int64_t)a.e.Nw * d.npix + (m - p * d.npix);
-            row.dmu = make_float2(0.f, 0.f);
-            if (row.valid && d.subtract_mean && a.e.mode == FLUSH_FINAL) {
-                double2 tt = sh->tsum[sb][rr];
-                if (d.prev_sums) {
-                    const double2 pv = d.sum_res[m];
-                    tt.x += pv.x;
-                    tt.y += pv.y;
-                }
-                row.dmu = make_float2((float)(tt.x / d.T), (float)(tt.y / d.T));
-            }
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(smem_u32(&sh->chunk_free[1]));
-                mbar_arrive(smem_u32(&sh->sums_free[sb]));
-            }
-            const int jbase = wtile * a.wt;
-            switch (epi_kind(a.e)) {
-                case EPI_FINAL: tc_epilogue_regs<EPI_FINAL>(a, row, col0, cols, jbase, sum); break;
-                case EPI_FINAL_KAHAN: tc_epilogue_regs<EPI_FINAL_KAHAN>(a, row, col0, cols, jbase, sum); break;
-                case EPI_FINAL_FP64: tc_epilogue_regs<EPI_FINAL_FP64>(a, row, col0, cols, jbase, sum); break;
-                case EPI_STORE_KAHAN: tc_epilogue_regs<EPI_STORE_KAHAN>(a, row, col0, cols, jbase, sum); break;
-                case EPI_STORE_FP64: tc_epilogue_regs<EPI_STORE_FP64>(a, row, col0, cols, jbase, sum); break;
-                case EPI_ADD_KAHAN: tc_epilogue_regs<EPI_ADD_KAHAN>(a, row, col0, cols, jbase, sum); break;
-                default: tc_epilogue_regs<EPI_ADD_FP64>(a, row, col0, cols, jbase, sum); break;
+            if (++kb == a.n_kb) {
+                // this tile's residual sums (frame half h) for its final
+                sh->part[tiles & 1][h][rr] = make_double2((double)sr - (double)cr, (double)si - (double)ci);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&sh->sums_full[tiles & 1]));
+                fin_t = t;
+                fin_cnt = tiles;
+                ++tiles;
+                t += (int)gridDim.x;
+                kb = 0;
             }
         }
-        if (!mbar_wait(smem_u32(&sh->tmem_full), 0u, nullptr)) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
+        if (!mbar_wait_warp(smem_u32(&sh->tmem_full), 0u, nullptr) && lane == 0) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
         tc_fence_after();
     }
     tc_fence_before();
@@ -1992,34 +2108,87 @@ bool tc_make_maps_b(void *maps_out, const __nv_bfloat16 *B_hi, const __nv_bfloat
 
 size_t tc_smem_bytes_direct(int N, int bf, int stages) { return tc_smem_bytes(N, bf, stages); }
 
-size_t tc_inplace_smem_bytes(int N, int bf, int stages) {
-    return (size_t)stages * tc_stage_bytes(N, bf) + 2 * (size_t)bf * kMTile * 8 + sizeof(TcShared) + 1024;
+// In-place drained kernel: shared memory of `stages` twiddle stages and `raw` raw frame stages.
+static size_t tc_inplace_smem_bytes(int N, int stages, int raw) {
+    return (size_t)stages * 2 * tc_b_bytes_padded(N, kIpBlockFrames) +
+           (size_t)raw * kIpBlockFrames * kMTile * 8 + sizeof(IpShared) + 1024;
 }
 
-int tc_inplace_stages(int N, int bf) {
-    int st = 0;
-    while (st < kMaxStages && tc_inplace_smem_bytes(N, bf, st + 1) <= (size_t)kSmemLimit) ++st;
-    return st;
+// Stage counts of the in-place drained kernel for an N-column tile: TMEM holds H, S (at a
+// 32-column boundary) and 64 columns per A stage; two stages with as many raw stages as shared
+// memory allows (up to four).  Returns the A/B stages (0: the tile does not fit).
+int tc_inplace_stages(int N, int bf, int *raw_out, uint32_t *acc_s, uint32_t *a_col) {
+    if (bf != kIpBlockFrames || N <= 0 || N % 16) return 0;
+    const int s_col = (N + 31) & ~31;
+    const int stages = 2;
+    if (s_col + N + 64 * stages > 512) return 0;
+    int raw = kIpRawMax;
+    while (raw >= 2 && tc_inplace_smem_bytes(N, stages, raw) > (size_t)kSmemLimit) --raw;
+    if (raw < 2) return 0;
+    if (raw_out) *raw_out = raw;
+    if (acc_s) *acc_s = (uint32_t)s_col;
+    if (a_col) *a_col = (uint32_t)(512 - 64 * stages);
+    return stages;
 }
 
-cudaError_t launch_flush_tc_inplace(const TcPlanArgs &a, const TcDirectArgs &d, cudaStream_t st) {
+bool tc_make_frame_map(void *map_out, const void *first_frame, int64_t pitch_frame, int n_frames, char *errbuf,
+                       size_t errlen) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) {
+        snprintf(errbuf, errlen, "cuTensorMapEncodeTiled is not available from the driver");
+        return false;
+    }
+    // complex64 elements as 8-byte words: [n_frames][pitch_frame], box 32 frames x 128 rows
+    cuuint64_t dims[2] = {(cuuint64_t)pitch_frame, (cuuint64_t)n_frames};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch_frame * 8};
+    cuuint32_t box[2] = {(cuuint32_t)kMTile, (cuuint32_t)kIpBlockFrames};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(reinterpret_cast<CUtensorMap *>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                    const_cast<void *>(first_frame), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        snprintf(errbuf, errlen, "cuTensorMapEncodeTiled(frames) failed with %d", (int)r);
+        return false;
+    }
+    return true;
+}
+size_t tc_frame_map_size() { return sizeof(CUtensorMap); }
+
+cudaError_t launch_flush_tc_inplace(const TcPlanArgs &a, const TcDirectArgs &d, const void *frame_map, cudaStream_t st) {
     TcInplaceArgs g{};
     g.a = a;
     g.d = d;
-    g.stages = tc_inplace_stages(a.N, a.bf);
+    g.fmap_ok = frame_map != nullptr;
+    if (frame_map) memcpy(&g.fmap, frame_map, sizeof(CUtensorMap));
+    g.stages = tc_inplace_stages(a.N, a.bf, &g.raw_stages, &g.acc_s, &g.a_col);
     g.tiles = (a.e.M_pad / kMTile) * a.n_wt;
-    if (g.stages < 2 || a.N > 2 * kDrainCols || a.drain_kb < 1 || g.tiles <= 0) return cudaErrorInvalidConfiguration;
-    const size_t smem = tc_inplace_smem_bytes(a.N, a.bf, g.stages);
+    if (g.stages < 2 || a.wt > kIpCols || a.drain_kb < 1 || a.n_kb < 1 || g.tiles <= 0 || g.tiles > 0x7fffffffLL)
+        return cudaErrorInvalidConfiguration;
+    // the next tile's first blocks converted before a tile's final: at most stages - 1 (their
+    // stages must be free while the final's tile still holds the others), and not past the
+    // first H chunk drain
+    g.defer = std::min(std::min(g.stages - 1, a.drain_kb), a.n_kb);
+    const size_t smem = tc_inplace_smem_bytes(a.N, g.stages, g.raw_stages);
+    // one instantiation per flush mode: a single epilogue path keeps the workers' registers
+    void (*kern)(TcInplaceArgs) = nullptr;
+    switch (epi_kind(a.e)) {
+        case EPI_FINAL: kern = flush_tc_inplace_kernel<EPI_FINAL>; break;
+        case EPI_FINAL_KAHAN: kern = flush_tc_inplace_kernel<EPI_FINAL_KAHAN>; break;
+        case EPI_FINAL_FP64: kern = flush_tc_inplace_kernel<EPI_FINAL_FP64>; break;
+        case EPI_STORE_KAHAN: kern = flush_tc_inplace_kernel<EPI_STORE_KAHAN>; break;
+        case EPI_STORE_FP64: kern = flush_tc_inplace_kernel<EPI_STORE_FP64>; break;
+        case EPI_ADD_KAHAN: kern = flush_tc_inplace_kernel<EPI_ADD_KAHAN>; break;
+        default: kern = flush_tc_inplace_kernel<EPI_ADD_FP64>; break;
+    }
     int dev = 0, sms = 0, occ = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(flush_tc_inplace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, flush_tc_inplace_kernel, 384, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 352, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int64_t grid = g.tiles < (int64_t)occ * sms ? g.tiles : (int64_t)occ * sms;
-    flush_tc_inplace_kernel<<<(unsigned)grid, 384, smem, st>>>(g);
+    kern<<<(unsigned)grid, 352, smem, st>>>(g);
     return cudaGetLastError();
 }
 

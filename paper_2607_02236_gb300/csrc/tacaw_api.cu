@@ -88,6 +88,9 @@ struct Stream {
     int tc_pair = 0;           // CTA-pair MMAs (cluster of 2, M = 256)
     bool tuned = false;        // tile picked by the autotuner
     // in-place frames: per staged frame, a pointer into the pushed buffer
+    // host record of the segment's pushes (first frame, address): a flush whose frames are
+    // evenly spaced reads them through one 2-D tensor map
+    std::vector<std::pair<int, const float2 *>> h_pushes;
     const float2 **d_frame_ptr = nullptr;       // one slot per frame of the segment, written on
                                                 // the stream at push time (no host copy)
     // segment state
@@ -351,6 +354,25 @@ void flush_done(tacaw_plan_s *p, Stream &s) {
     s.staged = 0;
 }
 
+// Address of frame `a` when frames [a, a + n) of the segment are evenly spaced (pitch_frame
+// apart) across the pushes that hold them, else null.
+const float2 *inplace_first_frame(const Stream &s, int a, int n) {
+    const float2 *first = nullptr;
+    for (size_t i = 0; i < s.h_pushes.size(); ++i) {
+        const int b0 = s.h_pushes[i].first;
+        const int b1 = i + 1 < s.h_pushes.size() ? s.h_pushes[i + 1].first : s.pushed;
+        if (b1 <= a || b0 >= a + n) continue;
+        const float2 *base = s.h_pushes[i].second;
+        if (!first) {
+            if (b0 > a) return nullptr;
+            first = base + (int64_t)(a - b0) * s.d.pitch_frame;
+        } else if (base != first + (int64_t)(b0 - a) * s.d.pitch_frame) {
+            return nullptr;
+        }
+    }
+    return first;
+}
+
 tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float2 *Psi_out, cudaStream_t st) {
     const int n = s.staged;
     if (n <= 0) return TACAW_OK;
@@ -379,8 +401,17 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         d.prev_sums = s.flushes > 0 ? 1 : 0;
         d.subtract_mean = s.d.subtract_mean;
         d.T = s.T;
-        if (p->ip2)
-            CU_CHECK(p, launch_flush_tc_inplace(a, d, st), "flush (tensor cores, in place, drained)");
+        if (p->ip2) {
+            // evenly spaced frames (one buffer, or pushes that continue each other): tensor map
+            alignas(64) unsigned char fmap[128];
+            const void *fm = nullptr;
+            const float2 *first = inplace_first_frame(s, s.stage_start, n);
+            char eb[256];
+            if (first && (size_t)tc_frame_map_size() <= sizeof(fmap) && s.d.pitch_frame < (int64_t)1 << 31 &&
+                tc_make_frame_map(fmap, first, s.d.pitch_frame, n, eb, sizeof(eb)))
+                fm = fmap;
+            CU_CHECK(p, launch_flush_tc_inplace(a, d, fm, st), "flush (tensor cores, in place, drained)");
+        }
         else
             CU_CHECK(p, launch_flush_tc_direct(a, d, s.tc_maps.data(), st), "flush (tensor cores, in place)");
         p->launches++;
@@ -740,6 +771,8 @@ tacaw_status push_internal(tacaw_plan_s *p, Stream &s, const float2 *frames, int
         FrameGeom gc = g;
         gc.base = g.base + (int64_t)done * g.pitch_frame;
         if (p->in_place) {
+            if (s.pushed == 0) s.h_pushes.clear();
+            s.h_pushes.emplace_back((int)s.pushed, gc.base);
             // the frames' addresses go to the device table by a kernel on the stream: ordered
             // with the flushes that read them, and fixed inside a captured graph
             CU_CHECK(p, launch_frame_table(s.d_frame_ptr + s.pushed, gc.base, g.pitch_frame, chunk, st), "frame table");

@@ -296,14 +296,21 @@ cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps /* TcMaps */, 
 int64_t tc_grid_ctas(const TcPlanArgs &a);
 constexpr int kMaxGroupStreams = 16;
 constexpr int kDrainMaxOmegaTile = 112;   // drained form: complex energies per tile at most
-constexpr int kInplaceMaxOmegaTile = 88;  // in-place drained form (the raw frame ring shares smem)
+constexpr int kInplaceMaxOmegaTile = 56;  // in-place drained form (worker registers at 168 a thread)
 // one launch over up to kMaxGroupStreams streams' flushes (same cluster size and block frames)
 cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *maps, int n, cudaStream_t st);
 cudaError_t launch_flush_tc_direct(const TcPlanArgs &a, const TcDirectArgs &d, const void *maps, cudaStream_t st);
-// persistent in-place drained form: tile rows contiguous and 16-byte aligned in every frame
-// (host-checked), 128-byte staging rows, tiles of at most kDrainMaxOmegaTile energies
-cudaError_t launch_flush_tc_inplace(const TcPlanArgs &a, const TcDirectArgs &d, cudaStream_t st);
-int tc_inplace_stages(int N, int bf);
+// persistent in-place drained form (A in tensor memory): tile rows contiguous and 16-byte
+// aligned in every frame (host-checked), 32-frame blocks, tiles of at most
+// kInplaceMaxOmegaTile energies.  tc_inplace_stages: its A/B stages for an N-column tile (0 if
+// it does not fit), the raw frame stages and TMEM columns through the optional pointers.
+// frame_map (optional, tc_make_frame_map): the flush's frames evenly spaced from the first
+cudaError_t launch_flush_tc_inplace(const TcPlanArgs &a, const TcDirectArgs &d, const void *frame_map,
+                                    cudaStream_t st);
+bool tc_make_frame_map(void *map_out, const void *first_frame, int64_t pitch_frame, int n_frames, char *errbuf,
+                       size_t errlen);
+size_t tc_frame_map_size();
+int tc_inplace_stages(int N, int bf, int *raw = nullptr, uint32_t *acc_s = nullptr, uint32_t *a_col = nullptr);
 bool tc_make_maps_b(void *maps_out, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
                     int N, int bf, char *errbuf, size_t errlen);
 size_t tc_smem_bytes_direct(int N, int bf, int stages);

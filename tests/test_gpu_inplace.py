@@ -1,8 +1,9 @@
 """Frames read in place by the contraction (no staging pass), against the FP64 oracle element by
-element.  Two kernels serve this mode: the persistent drained kernel (bulk copies of each
-tile's 128 contiguous rows of every frame into a raw ring, converted in shared memory) when the
-layout allows it, else the register-fed kernel.  Both are exercised, with the selection checked
-through tc_inplace_form (2: persistent drained, 1: register-fed)."""
+element.  Two kernels serve this mode: the persistent drained kernel (each tile's 128 contiguous
+rows of every frame copied into a raw ring, converted into tensor memory) when the layout allows
+it, else the register-fed kernel.  Both are exercised, with the selection checked through
+tc_inplace_form (2: persistent drained, 1: register-fed); the drained kernel's two copy paths
+(one 2-D tensor box a block for evenly spaced frames, per-frame copies otherwise) as well."""
 import numpy as np
 import pytest
 
@@ -102,6 +103,17 @@ DRAINED = {
     "wide_bose": (StreamSpec(P=1, Kx=16, Ky=16, T=64, Tc=64, n_omega=300, E_max_meV=400.0, window="tukey",
                              window_param=0.2, subtract_mean=False, bose_T_K=300.0,
                              detectors=(Detector("circular", 0, 0, -1, 3.0),)), {}),
+    # H drained every 64 frames: chunks end inside the tile (after blocks 1, 3, .., 9 of 11)
+    "long_drains": (StreamSpec(P=1, Kx=16, Ky=24, T=330, Tc=64, n_omega=70, E_max_meV=120.0, window="hann",
+                               detectors=(Detector("circular", 0, 0, -1, 5.0),)), {"tc_drain_frames": 64}),
+    # 256 tiles on at most 152 CTAs: each tile's final runs after the next tile's first block;
+    # H drained after every block
+    "many_tiles": (StreamSpec(P=4, Kx=64, Ky=64, T=96, Tc=32, n_omega=100, E_max_meV=120.0, window="hann",
+                              detectors=(Detector("circular", 0, 0, -1, 8.0),)), {"tc_drain_frames": 32}),
+    # the same over four flushes with the HBM accumulators, three energy tiles
+    "many_tiles_streaming": (StreamSpec(P=4, Kx=64, Ky=64, T=200, Tc=40, n_omega=150, E_max_meV=120.0,
+                                        window="hann", detectors=(Detector("circular", 0, 0, -1, 8.0),)),
+                             {"k_stage": 64, "tc_drain_frames": 32}),
     # the caller's tiling: two accumulators, 40 energies a tile, 32-frame blocks, one chunk
     "fixed_tile": (StreamSpec(P=2, Kx=64, Ky=48, T=168, Tc=40, n_omega=150, E_max_meV=120.0, window="hann",
                               detectors=(Detector("circular", 0, 0, -1, 6.0),)),
@@ -133,6 +145,35 @@ REGISTER_FED = {
 def test_register_fed_in_place(name):
     spec, kw = REGISTER_FED[name]
     check(spec, 60 + sorted(REGISTER_FED).index(name), 1, **kw)
+
+
+def test_scattered_pushes():
+    """Pushes from separate allocations (frames not evenly spaced across them): the persistent
+    kernel copies each frame's rows on its own instead of one 2-D tensor box per block."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    spec = StreamSpec(P=2, Kx=32, Ky=16, T=150, Tc=40, n_omega=60, E_max_meV=120.0, window="hann",
+                      detectors=(Detector("circular", 0, 0, -1, 5.0),))
+    full = full_frames(spec, 71)
+    fr = full.transpose(1, 0, 2, 3)                              # [T][P][Ky][Kx]
+    cuts = [0, 13, 40, 41, 100, 150]
+    # each push a gap of 3 frames after the previous one inside one allocation
+    big = torch.zeros((spec.T + 3 * len(cuts),) + fr.shape[1:], dtype=torch.complex64, device="cuda")
+    bufs = []
+    for i, (a, b) in enumerate(zip(cuts[:-1], cuts[1:])):
+        big[a + 3 * i:b + 3 * i] = torch.from_numpy(np.ascontiguousarray(fr[a:b])).to("cuda")
+        bufs.append(big[a + 3 * i:b + 3 * i])
+    I = torch.empty(spec.P * spec.Nw * spec.Kx * spec.Ky, device="cuda")
+    S = torch.empty(spec.P * spec.Nw, device="cuda")
+    with TacawPlan([stream_config(spec)], precision="split_bf16", frames_in_place=True) as plan:
+        assert plan.info()["tc_inplace_form"] == 2
+        for b in bufs:
+            plan.push(0, b, b.shape[0])
+        plan.finalize(I, S)
+    torch.cuda.synchronize()
+    ref = oracle.forward(full, **oracle_kw(spec))
+    assert rel_err_peak(I.cpu().numpy().reshape(ref.I.shape), ref.I) <= TOL
+    assert rel_err_peak(S.cpu().numpy().reshape(ref.S.shape), ref.S) <= TOL
 
 
 def test_unaligned_push_is_refused():
