@@ -125,6 +125,11 @@ typedef struct {
      * it (up to ceil(T / stride) at once, each with its own staging).  0 or 1: one segment.  */
     int welch_segments;
     int welch_stride;
+    /* Frames dropped at the start of the stream before its first segment (the trajectory's
+     * initial, unequilibrated part; App. configuration `trajectory_chunks_skip_init`, read as a
+     * frame count).  The stream then takes skip_init + (N - 1) * stride + T frames; the skipped
+     * ones are never read.  >= 0. */
+    int skip_init;
 } tacaw_stream_desc;
 
 typedef struct {

@@ -261,10 +261,12 @@ def welch_stride(L: int, nu: float) -> int:
     return int(L // nu)
 
 
-def welch_forward(psi, L: int, stride: int, **kw) -> Result:
+def welch_forward(psi, L: int, stride: int, skip_init: int = 0, **kw) -> Result:
     """Welch average of the segments of psi [P, n_frames, Ky, Kx] (see the module header).
+    The first `skip_init` frames are dropped before the first segment (the configuration's
+    `trajectory_chunks_skip_init`, App. listing, read as a frame count).
     Result.I and Result.S are the averages; mu and Psi are those of the last segment."""
-    psi = np.asarray(psi)
+    psi = np.asarray(psi)[:, skip_init:]
     starts = welch_segments(psi.shape[1], L, stride)
     if len(starts) == 0:
         raise ValueError("no whole segment of L frames")

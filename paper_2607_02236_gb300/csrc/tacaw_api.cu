@@ -104,7 +104,8 @@ struct Stream {
 struct UserStream {
     int first = 0, lanes = 1;  // internal streams [first, first + lanes)
     int N = 1, stride = 0, L = 0;
-    int64_t total = 0;         // frames of the whole push sequence: (N - 1) * stride + L
+    int64_t total = 0;         // frames of the whole push sequence: skip + (N - 1) * stride + L
+    int64_t skip = 0;          // leading frames dropped before the first segment
     int64_t pushed = 0;
     float *I_acc = nullptr;    // Welch: plan-owned running average of the segments' I
     int64_t I_elems = 0;
@@ -205,9 +206,12 @@ tacaw_status validate_stream(const tacaw_stream_desc &d, int i) {
     if (d.bose_T_K < 0) return fail(TACAW_ERR_INVALID_ARG, "stream %d: bose_T_K must be >= 0", i);
     if (d.welch_segments < 0 || d.welch_stride < 0)
         return fail(TACAW_ERR_INVALID_ARG, "stream %d: welch_segments and welch_stride must be >= 0", i);
-    if (d.welch_segments > 1 && (int64_t)(d.welch_segments - 1) * (d.welch_stride ? d.welch_stride : d.T) + d.T >
-                                    (int64_t)INT32_MAX)
-        return fail(TACAW_ERR_INVALID_ARG, "stream %d: Welch push sequence longer than 2^31 frames", i);
+    if (d.skip_init < 0) return fail(TACAW_ERR_INVALID_ARG, "stream %d: skip_init must be >= 0", i);
+    if ((int64_t)d.skip_init +
+            (d.welch_segments > 1 ? (int64_t)(d.welch_segments - 1) * (d.welch_stride ? d.welch_stride : d.T) : 0) +
+            d.T >
+        (int64_t)INT32_MAX)
+        return fail(TACAW_ERR_INVALID_ARG, "stream %d: push sequence longer than 2^31 frames", i);
     for (int k = 0; k < d.n_detectors; ++k) {
         const tacaw_detector &t = d.detectors[k];
         if (t.kind < TACAW_DET_CIRCULAR || t.kind > TACAW_DET_MASK)
@@ -937,7 +941,8 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         u.L = s.T;
         u.stride = s.d.welch_stride ? s.d.welch_stride : s.T;
         u.lanes = u.N > 1 ? (int)std::min<int64_t>(u.N, (s.T + u.stride - 1) / u.stride) : 1;
-        u.total = (int64_t)(u.N - 1) * u.stride + u.L;
+        u.skip = desc->streams[i].skip_init;
+        u.total = u.skip + (int64_t)(u.N - 1) * u.stride + u.L;
         u.first = (int)p->s.size();
         s.user = i;
         if (u.N > 1) {
@@ -1187,14 +1192,26 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
                     (long long)u.pushed);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const float2 *base = static_cast<const float2 *>(d_frames);
+    // leading frames of the stream that precede its first segment are dropped unread
+    if (u.pushed + n_frames <= u.skip) {
+        u.pushed += n_frames;
+        return TACAW_OK;
+    }
+    if (u.pushed < u.skip) {
+        const int64_t drop = u.skip - u.pushed;
+        base += drop * p->s[u.first].d.pitch_frame;
+        n_frames -= (int)drop;
+        u.pushed = u.skip;
+    }
     if (u.N <= 1) {
         tacaw_status r = push_internal(p, p->s[u.first], base, n_frames, st);
         if (r == TACAW_OK) u.pushed += n_frames;
         return r;
     }
     // Welch: every lane takes the part of this push inside its current segment, finishing
-    // segments (and starting the next ones of the lane) as their last frames arrive
-    const int64_t a = u.pushed, b = u.pushed + n_frames;
+    // segments (and starting the next ones of the lane) as their last frames arrive; frame
+    // positions count from the first frame after the skipped ones
+    const int64_t a = u.pushed - u.skip, b = a + n_frames;
     for (int l = 0; l < u.lanes; ++l) {
         Stream &s = p->s[u.first + l];
         while (s.seg < u.N) {
@@ -1208,7 +1225,7 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
             if (r != TACAW_OK) return r;
         }
     }
-    u.pushed = b;
+    u.pushed = u.skip + b;
     return TACAW_OK;
 }
 

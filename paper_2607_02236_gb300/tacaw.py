@@ -50,7 +50,7 @@ class CStreamDesc(ctypes.Structure):
                 ("n_omega", c_int), ("E_meV", POINTER(c_double)), ("fft_bins", c_int),
                 ("window", c_int), ("window_param", c_double), ("subtract_mean", c_int),
                 ("bose_T_K", c_double), ("n_detectors", c_int), ("detectors", POINTER(CDetector)),
-                ("welch_segments", c_int), ("welch_stride", c_int)]
+                ("welch_segments", c_int), ("welch_stride", c_int), ("skip_init", c_int)]
 
 
 class CPlanDesc(ctypes.Structure):
@@ -162,6 +162,8 @@ class StreamConfig:
     # Welch averaging: N segments of T frames, `welch_stride` frames apart (0: T); 0/1: off
     welch_segments: int = 0
     welch_stride: int = 0
+    # leading frames dropped before the first segment (the trajectory's initial part)
+    skip_init: int = 0
 
 
 class TacawPlan:
@@ -200,6 +202,7 @@ class TacawPlan:
             d.n_detectors = len(s.detectors)
             d.detectors = ctypes.cast(dets, POINTER(CDetector))
             d.welch_segments, d.welch_stride = int(s.welch_segments), int(s.welch_stride)
+            d.skip_init = int(s.skip_init)
         pd = CPlanDesc(len(streams), ctypes.cast(descs, POINTER(CStreamDesc)), PRECISIONS[precision],
                        ACCUMS[accum], int(hbm_budget_bytes), int(k_stage),
                        None if tune is None else os.fsencode(tune), int(tc_omega_tile),

@@ -28,9 +28,9 @@ def make_frames(P, n, Ky, Kx, seed):
     return (e + tone + s).astype(np.complex64)
 
 
-def welch_config(spec, N, stride):
+def welch_config(spec, N, stride, skip=0):
     c = stream_config(spec)
-    c.welch_segments, c.welch_stride = N, stride
+    c.welch_segments, c.welch_stride, c.skip_init = N, stride, skip
     return c
 
 
@@ -111,6 +111,35 @@ def test_welch_stream_beside_a_plain_stream():
     assert rel_err_peak(outs[1][0], rb.I) <= TOL["split_bf16"]
     assert rel_err_peak(outs[1][1], rb.S) <= TOL["split_bf16"]
     assert info["n_streams"] == 2
+
+
+@pytest.mark.parametrize("N,stride,skip,push,kw", [(4, 32, 45, 40, {}), (1, 0, 70, 33, {}), (3, 20, 96, 96, {}),
+                                                    (4, 32, 45, 40, {"frames_in_place": True}),
+                                                    (1, 0, 64, 32, {"frames_in_place": True})])
+def test_skip_init(N, stride, skip, push, kw):
+    """Leading frames dropped before the first segment (one segment or Welch; pushes that end
+    inside, at and after the skipped part; in place)."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    spec = SPEC
+    n = skip + (N - 1) * (stride or spec.T) + spec.T
+    fr = make_frames(spec.P, n, spec.Ky, spec.Kx, 9)
+    fr[:, :skip] += 30.0                                            # a transient that must not leak in
+    buf = torch.from_numpy(np.ascontiguousarray(fr.transpose(1, 0, 2, 3))).to("cuda")
+    with TacawPlan([welch_config(spec, N, stride, skip)], precision="split_bf16", **kw) as plan:
+        I = torch.zeros(plan.info()["I_elems"], device="cuda")
+        S = torch.zeros(max(1, plan.info()["S_elems"]), device="cuda")
+        fb = spec.P * spec.Kx * spec.Ky * 8
+        t = 0
+        while t < n:
+            k = min(push, n - t)
+            plan.push(0, buf.data_ptr() + t * fb, k)
+            t += k
+        plan.finalize(I, S)
+    ref = oracle.welch_forward(fr, spec.T, stride or spec.T, skip_init=skip, **oracle_kw(spec))
+    got = I.cpu().numpy().reshape(ref.I.shape)
+    assert rel_err_peak(got, ref.I) <= TOL["split_bf16"]
+    assert rel_err_peak(S.cpu().numpy()[:ref.S.size].reshape(ref.S.shape), ref.S) <= TOL["split_bf16"]
 
 
 def test_welch_errors():

@@ -442,3 +442,22 @@ def test_welch_matches_scipy_welch(L, stride, win):
                                 return_onesided=False, scaling="spectrum", average="mean")
     wsum = oracle.window(win, L, param).sum()
     np.testing.assert_allclose(r.I[0, :, 0, 0], pxx * wsum ** 2, rtol=1e-9, atol=1e-9 * np.max(pxx) * wsum ** 2)
+
+
+@pytest.mark.parametrize("skip", [1, 37, 64])
+def test_welch_skip_init_matches_scipy_on_the_remaining_frames(skip):
+    """skip_init drops the leading frames (an initial transient here) before the first segment:
+    the result is scipy's Welch estimate of the frames after them."""
+    rng = np.random.default_rng(73)
+    L, stride = 64, 32
+    n = skip + 4 * stride + L
+    t = np.arange(n)
+    x = (0.5 - 0.1j + np.exp(2j * np.pi * 0.21 * t) + 0.2 * (rng.standard_normal(n) + 1j * rng.standard_normal(n)))
+    x[:skip] += 50.0 * np.exp(-t[:skip] / 7.0)                       # transient that must not leak in
+    psi = x[None, :, None, None].copy()
+    r = oracle.welch_forward(psi, L, stride, skip_init=skip, window_kind="hann", fft_bins=L, dt_fs=5.0)
+    _, pxx = scipy.signal.welch(x[skip:], window="hann", nperseg=L, noverlap=L - stride, detrend="constant",
+                                return_onesided=False, scaling="spectrum", average="mean")
+    wsum = oracle.window("hann", L).sum()
+    np.testing.assert_allclose(r.I[0, :, 0, 0], pxx * wsum ** 2, rtol=1e-9, atol=1e-9 * np.max(pxx) * wsum ** 2)
+    assert len(oracle.welch_segments(n - skip, L, stride)) == 5
