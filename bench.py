@@ -67,6 +67,9 @@ def parse():
                     help="drained accumulator form: chunk length in frames (0: off)")
     ap.add_argument("--tc-pair", type=int, default=0, choices=[0, 1, 2],
                     help="CTA-pair MMAs (256 rows over a cluster of two SMs): 1 relayed, 2 direct stage barriers")
+    ap.add_argument("--tc-max-ctas", type=int, default=0,
+                    help="persistent contraction grid cap (0: every SM); with --pipeline 2 the free SMs "
+                         "convert the next segment's pushes beside the current contraction")
     ap.add_argument("--trace", action="store_true",
                     help="add the per-CTA phase breakdown of one traced contraction (tacaw_flush_trace)")
     ap.add_argument("--fast-steps", type=int, default=2,
@@ -495,7 +498,7 @@ def main():
 
     tiling = dict(tc_accumulators=args.tc_accumulators, tc_omega_tile=args.tc_omega_tile,
                   tc_cluster=args.tc_cluster, tc_block_frames=args.tc_block_frames, tc_pair=args.tc_pair,
-                  tc_drain_frames=args.tc_drain_frames,
+                  tc_drain_frames=args.tc_drain_frames, tc_max_ctas=args.tc_max_ctas,
                   frames_in_place=bool(args.in_place and args.precision == "split_bf16"))
     # segments in flight: plan k and stream k take steps k, k + n, ...; the first plan writes I, S
     n_pipe = max(1, args.pipeline)
@@ -710,7 +713,7 @@ def main():
                            "frames_in_place": bool(info["frames_in_place"]),
                            "smem_stages": info["stages"], "plan_device_GB": round(info["device_bytes"] / 1e9, 2),
                            "l2": "inputs (%.1f GB) larger than L2, no flush" % (T * frame_elems * 8 / 1e9),
-                           "segments_in_flight": n_pipe,
+                           "segments_in_flight": n_pipe, "contraction_ctas_max": args.tc_max_ctas or None,
                            "parallelism": f"replicas x{world}"},
                 "max_rel_err_I_vs_fp64": err, "error_sample": "24 (probe, pixel) series, all energies",
                 "spectra_per_s": spectra_per_s, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,

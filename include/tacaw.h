@@ -190,6 +190,10 @@ typedef struct {
      * persistent grid walks the tiles of all streams.  0: the default -- form 2 with 512-frame
      * chunks when tc_accumulators, tc_pair and tc_cluster (> 1) are all left unset, else off. */
     int tc_drain_frames;
+    /* Persistent contraction grids (drained forms, in-place drained kernel) take at most this
+     * many CTAs, one per SM (0: every SM).  SMs left free run other work beside the
+     * contraction, e.g. the conversions of another plan's segment pushed on another stream. */
+    int tc_max_ctas;
 } tacaw_plan_desc;
 
 typedef struct tacaw_plan_s *tacaw_plan_t;

@@ -2187,7 +2187,9 @@ cudaError_t launch_flush_tc_inplace(const TcPlanArgs &a, const TcDirectArgs &d, 
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 352, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    const int64_t grid = g.tiles < (int64_t)occ * sms ? g.tiles : (int64_t)occ * sms;
+    int64_t cap = (int64_t)occ * sms;
+    if (a.max_ctas > 0 && a.max_ctas < cap) cap = a.max_ctas;
+    const int64_t grid = g.tiles < cap ? g.tiles : cap;
     kern<<<(unsigned)grid, 352, smem, st>>>(g);
     return cudaGetLastError();
 }
@@ -2290,7 +2292,9 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *map
             delete g;
             return e != cudaSuccess ? e : cudaErrorInvalidConfiguration;
         }
-        if ((int64_t)occ * sms < total) grid = (unsigned)(occ * sms);
+        int64_t cap = (int64_t)occ * sms;
+        if (args[0].max_ctas > 0 && args[0].max_ctas < cap) cap = args[0].max_ctas;
+        if (cap < total) grid = (unsigned)cap;
     }
     auto kern = drain ? (form == 2 ? flush_tc_drain2_kernel : flush_tc_drain_kernel)
                       : (pair ? flush_tc_pair_kernel : flush_tc_kernel);

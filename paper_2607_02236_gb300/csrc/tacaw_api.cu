@@ -124,6 +124,12 @@ struct tacaw_plan_s {
     int tc_prefetch = 0;       // L2 prefetch distance of operand A in staging blocks
     bool in_place = false;     // the contraction reads pushed frames directly
     bool ip2 = false;          // ... through the persistent drained in-place kernel
+    int tc_max_ctas = 0;       // persistent contraction grids: at most this many CTAs (0: all SMs)
+    // with a capped grid the last flush runs on a highest-priority stream of the plan, forked
+    // from and joined back to the caller's stream, so that its CTAs take SMs ahead of other
+    // streams' queued work
+    cudaStream_t hp_stream = nullptr;
+    cudaEvent_t hp_in = nullptr, hp_out = nullptr;
     int64_t bytes = 0;
     int64_t I_elems = 0, S_elems = 0;
     int64_t flushes_total = 0;
@@ -161,7 +167,11 @@ bool dev_alloc(tacaw_plan_s *p, T **ptr, size_t count) {
 }
 
 void free_all(tacaw_plan_s *p) {
-    for (auto &s : p->s)
+    if (p->hp_stream) cudaStreamDestroy(p->hp_stream);
+    if (p->hp_in) cudaEventDestroy(p->hp_in);
+    if (p->hp_out) cudaEventDestroy(p->hp_out);
+    p->hp_stream = nullptr;
+    p->hp_in = p->hp_out = nullptr;
     if (p->d_trace) cudaFree(p->d_trace);
     p->d_trace = nullptr;
     for (auto &e : p->ev) {
@@ -312,6 +322,7 @@ TcPlanArgs tc_args(tacaw_plan_s *p, const Stream &s, const EpiArgs &e) {
     a.cluster = p->in_place ? 1 : s.tc_cluster;
     a.pair = p->in_place ? 0 : s.tc_pair;
     a.prefetch = p->in_place ? 0 : p->tc_prefetch;
+    a.max_ctas = p->tc_max_ctas;
     a.err = p->d_err;
     a.trace = nullptr;
     return a;
@@ -717,8 +728,25 @@ tacaw_status finalize_impl(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, 
         }
     float2 *Psi_all = static_cast<float2 *>(d_Psi);
     if (p->prec == TACAW_PREC_SPLIT_BF16 && !p->in_place) {
-        tacaw_status r = final_flush_grouped(p, d_I, Psi_all, st);
+        cudaStream_t fs = st;
+        if (p->tc_max_ctas > 0) {
+            if (!p->hp_stream) {
+                int lo = 0, hi = 0;
+                CU_CHECK(p, cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
+                CU_CHECK(p, cudaStreamCreateWithPriority(&p->hp_stream, cudaStreamNonBlocking, hi), "flush stream");
+                CU_CHECK(p, cudaEventCreateWithFlags(&p->hp_in, cudaEventDisableTiming), "cudaEventCreate");
+                CU_CHECK(p, cudaEventCreateWithFlags(&p->hp_out, cudaEventDisableTiming), "cudaEventCreate");
+            }
+            CU_CHECK(p, cudaEventRecord(p->hp_in, st), "cudaEventRecord");
+            CU_CHECK(p, cudaStreamWaitEvent(p->hp_stream, p->hp_in, 0), "cudaStreamWaitEvent");
+            fs = p->hp_stream;
+        }
+        tacaw_status r = final_flush_grouped(p, d_I, Psi_all, fs);
         if (r != TACAW_OK) return r;
+        if (fs != st) {
+            CU_CHECK(p, cudaEventRecord(p->hp_out, fs), "cudaEventRecord");
+            CU_CHECK(p, cudaStreamWaitEvent(st, p->hp_out, 0), "cudaStreamWaitEvent");
+        }
     } else {
         for (auto &s : p->s) {
             if (p->us[s.user].N > 1) continue;
@@ -972,6 +1000,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
             while (p->bf > 8 && tc_stages_for(max_cols(), p->bf) < 2) p->bf /= 2;
         for (auto &s : p->s) s.n_kb_T = s.T_pad / p->bf;
         p->tc_prefetch = desc->tc_prefetch > 0 ? desc->tc_prefetch : 0;
+        p->tc_max_ctas = desc->tc_max_ctas > 0 ? desc->tc_max_ctas : 0;
         if (drained) p->drain_kb = std::max(1, (ip2 ? (desc->tc_drain_frames ? desc->tc_drain_frames : 512)
                                                      : drain_frames) / p->bf);
         // autotuner: time the candidate tiles of every stream shape (staged operands only)

@@ -58,7 +58,8 @@ class CPlanDesc(ctypes.Structure):
                 ("accum", c_int), ("hbm_budget_bytes", c_int64), ("k_stage", c_int),
                 ("tune_cache_path", c_char_p), ("tc_omega_tile", c_int), ("tc_accumulators", c_int),
                 ("tc_cluster", c_int), ("tc_block_frames", c_int), ("tc_prefetch", c_int),
-                ("frames_in_place", c_int), ("tc_pair", c_int), ("tc_drain_frames", c_int)]
+                ("frames_in_place", c_int), ("tc_pair", c_int), ("tc_drain_frames", c_int),
+                ("tc_max_ctas", c_int)]
 
 
 class CPlanInfo(ctypes.Structure):
@@ -173,7 +174,7 @@ class TacawPlan:
                  hbm_budget_bytes: int = 0, k_stage: int = 0, tc_omega_tile: int = 0,
                  tc_accumulators: int = 0, tc_cluster: int = 0, tc_block_frames: int = 0, tc_prefetch: int = 0,
                  frames_in_place: bool = False, tune: Optional[str] = None, tc_pair: int = 0,
-                 tc_drain_frames: int = 0):
+                 tc_drain_frames: int = 0, tc_max_ctas: int = 0):
         """tune: None uses the built-in tile rule; "" autotunes at creation; a file path
         autotunes through a text cache at that path."""
         L = lib()
@@ -208,7 +209,7 @@ class TacawPlan:
                        None if tune is None else os.fsencode(tune), int(tc_omega_tile),
                        int(tc_accumulators), int(tc_cluster), int(tc_block_frames), int(tc_prefetch),
                        int(bool(frames_in_place)), int(tc_pair),
-                       int(tc_drain_frames))
+                       int(tc_drain_frames), int(tc_max_ctas))
         h = c_void_p()
         _check(L.tacaw_plan_create(ctypes.byref(pd), ctypes.byref(h)))
         self._h = h

@@ -156,6 +156,28 @@ def test_graph_capture_and_replay(mode):
         del g
 
 
+@pytest.mark.parametrize("kw", [dict(precision="split_bf16", tc_max_ctas=7),
+                                dict(precision="split_bf16", tc_max_ctas=3, frames_in_place=True)])
+def test_capped_persistent_grid(kw):
+    """Persistent contraction grids capped at a few CTAs (each walks many tiles of several
+    streams; the capped last flush runs on the plan's forked high-priority stream)."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    frames = [make_frames(s, 700 + i) for i, s in enumerate(SPECS)]
+    bufs = [device_frames(f) for f in frames]
+    st = torch.cuda.Stream()
+    with TacawPlan([stream_config(s) for s in SPECS], **kw) as plan:
+        info = plan.info()
+        I = torch.zeros(info["I_elems"], dtype=torch.float32, device="cuda")
+        S = torch.zeros(max(1, info["S_elems"]), dtype=torch.float32, device="cuda")
+        with torch.cuda.stream(st):
+            push_all(plan, bufs, st)
+            plan.finalize(I, S, cuda_stream=st)
+        torch.cuda.synchronize()
+        worst = check_all(plan, I, S, frames, TOL["split_bf16"])
+    print(f"capped grid {kw}: worst max rel I error {worst:.3g}")
+
+
 def test_autotuned_tiles_and_cache(tmp_path):
     import torch
     from paper_2607_02236_gb300 import TacawPlan
