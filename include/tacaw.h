@@ -276,6 +276,10 @@ tacaw_status tacaw_output_offsets(tacaw_plan_t plan, int stream_id, int64_t *I_o
  * descriptor; d_grad (complex64) has the same layout: every ROI element is written (zero
  * outside the apertures), elements outside the ROI are not touched.  Psi is recomputed
  * from the frames, not stored.  Independent of the push/finalize state of the plan.
+ * Streams with skip_init or Welch averaging: d_frames / d_grad hold the whole push sequence
+ * (skip_init + (N - 1) * stride + T frames); S is the segments' average, so the gradient is
+ * (1/N) sum_n g_n with segment n's g_n placed at its frames (added where segments overlap)
+ * and zero on the skipped frames.
  * d_dL_dS: float32 [p][d][j] on the device.  Waits for the work on `stream`.             */
 tacaw_status tacaw_backward(tacaw_plan_t plan, int stream_id, const float *d_dL_dS,
                             const void *d_frames, void *d_grad, void *stream);

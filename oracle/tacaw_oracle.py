@@ -279,6 +279,20 @@ def welch_forward(psi, L: int, stride: int, skip_init: int = 0, **kw) -> Result:
     return Result(r.mu, r.Psi, I / N, S / N)
 
 
+def welch_gradient(psi, dLdS, L: int, stride: int, skip_init: int = 0, **kw) -> np.ndarray:
+    """Gradient of sum dLdS * S_welch, S_welch = (1/N) sum_n S_n (welch_forward), with respect
+    to the whole push sequence psi [P, n_frames, Ky, Kx]: each segment's gradient (gradient())
+    weighted 1/N at its frames, summed where segments overlap, zero on dropped frames."""
+    psi = np.asarray(psi)
+    starts = welch_segments(psi.shape[1] - skip_init, L, stride) + skip_init
+    if len(starts) == 0:
+        raise ValueError("no whole segment of L frames")
+    g = np.zeros(psi.shape, dtype=np.complex128)
+    for s0 in starts:
+        g[:, s0:s0 + L] += gradient(psi[:, s0:s0 + L], dLdS, **kw) / len(starts)
+    return g
+
+
 def gradient(psi, dLdS, *, window_kind="hann", window_param=0.0, E_meV=None, dt_fs=5.0,
              fft_bins=0, subtract_mean=True, bose_T_K=0.0, detectors=()) -> np.ndarray:
     """g = 2 dL/dconj(psi) for L = sum dLdS * S.  psi [P,T,Ky,Kx], dLdS [P,D,Nw]. Returns [P,T,Ky,Kx]."""

@@ -20,8 +20,9 @@ def _dims(plan: TacawPlan, sid: int):
 class TacawSpectrum(torch.autograd.Function):
     """S = TacawSpectrum.apply(frames, plan, stream_id, frames_per_push).
 
-    frames: complex64 CUDA tensor holding one whole segment of `stream_id` in the pushed
-    layout of the plan's stream descriptor (pitches).  The plan must have a single stream
+    frames: complex64 CUDA tensor holding the whole push sequence of `stream_id` in the
+    pushed layout of the plan's stream descriptor (pitches): one segment, or with skip_init /
+    Welch averaging skip_init + (N - 1) * stride + T frames.  The plan must have a single stream
     (finalize completes every stream).  Returns S as a float32 tensor [P, D, Nw].
     """
 
@@ -32,10 +33,12 @@ class TacawSpectrum(torch.autograd.Function):
         s, nw, D = _dims(plan, stream_id)
         cs = torch.cuda.current_stream()
         plan.reset(cs)
-        chunk = frames_per_push or s.T
+        n_seg = max(1, int(s.welch_segments))
+        total = int(s.skip_init) + (n_seg - 1) * (int(s.welch_stride) or s.T) + s.T
+        chunk = frames_per_push or total
         base = frames.data_ptr()
-        for t0 in range(0, s.T, chunk):
-            plan.push(stream_id, base + t0 * s.pitch_frame * 8, min(chunk, s.T - t0), cs)
+        for t0 in range(0, total, chunk):
+            plan.push(stream_id, base + t0 * s.pitch_frame * 8, min(chunk, total - t0), cs)
         info = plan.info()
         I = torch.empty(info["I_elems"], dtype=torch.float32, device=frames.device)
         S = torch.empty(max(1, info["S_elems"]), dtype=torch.float32, device=frames.device)

@@ -5,6 +5,8 @@
 //   C[p,k,t] = sum_j conj(w_t e^{-i theta_jt}) G[p,k,j] = w_t sum_j e^{+i theta_jt} G[p,k,j]
 //   grad[p,t,k] = 2 (C[p,k,t] - (1/T) sum_t' C[p,k,t'])            (mean term with subtract_mean)
 // and (1/T) sum_t C = (1/T) sum_j conj(W_j) G_j with W_j = sum_t w_t e^{-i theta_jt}.
+// A Welch-averaged stream (S = (1/N) sum_n S_n, Sec. II.B) runs this per segment with
+// scale 1/N, adding into the gradient of the frames the segments share.
 // Only pixels inside an aperture have G != 0, so both contractions run over that compact
 // pixel list; Psi is recomputed from the frames (the window and twiddles come from the
 // plan's table), never stored between forward and backward.
@@ -170,8 +172,15 @@ __global__ void __launch_bounds__(256) adj_backward_kernel(AdjointArgs a) {
                 const int pix = a.mpix[g0 + i];
                 const int y = pix / a.kx, x = pix - (pix / a.kx) * a.kx;
                 const float2 K = Kc[(size_t)p * a.n_mpix + g0 + i];
-                a.grad[(int64_t)p * a.pitch_probe + (int64_t)t * a.pitch_frame + (int64_t)(a.roi_y0 + y) * a.pitch_row +
-                       (a.roi_x0 + x)] = make_float2(2.f * (cr[i] - K.x), 2.f * (ci[i] - K.y));
+                float2 *gp = a.grad + (int64_t)p * a.pitch_probe + (int64_t)t * a.pitch_frame +
+                             (int64_t)(a.roi_y0 + y) * a.pitch_row + (a.roi_x0 + x);
+                const float2 v = make_float2(2.f * a.scale * (cr[i] - K.x), 2.f * a.scale * (ci[i] - K.y));
+                if (a.accumulate) {
+                    const float2 o = *gp;
+                    *gp = make_float2(o.x + v.x, o.y + v.y);
+                } else {
+                    *gp = v;
+                }
             }
         }
     }

@@ -1374,8 +1374,8 @@ tacaw_status tacaw_backward(tacaw_plan_t p, int sid, const float *d_dL_dS, const
     if (c != TACAW_OK) return c;
     if (sid < 0 || sid >= (int)p->us.size()) return fail(TACAW_ERR_INVALID_ARG, "stream_id %d out of range", sid);
     if (!d_dL_dS || !d_frames || !d_grad) return fail(TACAW_ERR_INVALID_ARG, "NULL device pointer");
-    if (p->us[sid].N > 1) return fail(TACAW_ERR_UNSUPPORTED, "the adjoint of a Welch-averaged stream is not built");
-    Stream &s = p->s[p->us[sid].first];
+    const UserStream &u = p->us[sid];
+    Stream &s = p->s[u.first];
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     AdjointArgs a{};
     a.frames = static_cast<const float2 *>(d_frames);
@@ -1401,15 +1401,32 @@ tacaw_status tacaw_backward(tacaw_plan_t p, int sid, const float *d_dL_dS, const
     a.mwts = s.adj_w;
     a.n_mpix = s.n_adj;
     a.grad = static_cast<float2 *>(d_grad);
-    CU_CHECK(p, launch_zero_roi(a, st), "zero gradient");
+    a.scale = 1.f;
+    a.accumulate = 0;
+    // the whole push sequence's gradient: skipped frames and frames of no segment get zero
+    AdjointArgs z = a;
+    z.T = (int)u.total;
+    CU_CHECK(p, launch_zero_roi(z, st), "zero gradient");
     p->launches++;
     if (s.n_adj > 0 && s.D > 0) {
         float2 *scratch = nullptr;
         const size_t n_scr = (size_t)s.d.n_probes * s.n_adj * (s.Nw + 2);
         CU_CHECK(p, cudaMallocAsync(reinterpret_cast<void **>(&scratch), n_scr * sizeof(float2), st), "scratch");
         a.scratch = scratch;
-        cudaError_t e = launch_adjoint(a, st);
-        p->launches += 2;
+        // one segment, or each Welch segment at its start frame with weight 1/N, its gradient
+        // added where segments overlap
+        const int nseg = u.N > 1 ? u.N : 1;
+        cudaError_t e = cudaSuccess;
+        for (int n = 0; n < nseg && e == cudaSuccess; ++n) {
+            const int64_t f0 = u.skip + (int64_t)n * u.stride;
+            AdjointArgs an = a;
+            an.frames = a.frames + f0 * s.d.pitch_frame;
+            an.grad = a.grad + f0 * s.d.pitch_frame;
+            an.scale = 1.f / (float)nseg;
+            an.accumulate = 1;
+            e = launch_adjoint(an, st);
+            p->launches += 2;
+        }
         cudaFreeAsync(scratch, st);
         if (e != cudaSuccess) return cuda_fail(p, e, "adjoint");
     }

@@ -374,6 +374,8 @@ struct AdjointArgs {
     int n_mpix;
     float2 *grad;              // same layout as frames (pitches above)
     float2 *scratch;           // [P][n_mpix][Nw] complex (G), plus [P][n_mpix] means
+    float scale;               // the gradient is scale * 2 (C - K) ...
+    int accumulate;            // ... added to grad (1) or stored (0)
 };
 cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t st);
 cudaError_t launch_zero_roi(const AdjointArgs &a, cudaStream_t st);

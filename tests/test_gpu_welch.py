@@ -156,7 +156,31 @@ def test_welch_errors():
         with pytest.raises(TacawError, match="INVALID_ARG"):
             plan.finalize(I, None, Psi)
         plan.finalize(I)
-        g = torch.zeros_like(buf)
-        dLdS = torch.zeros(SPEC.P * SPEC.Nw, device="cuda")
-        with pytest.raises(TacawError, match="UNSUPPORTED"):
-            plan.backward(0, dLdS, buf, g)
+
+
+@pytest.mark.parametrize("N,stride,skip", [(4, 24, 10), (3, 64, 0), (1, 0, 17)])
+def test_welch_gradient_through_autograd(N, stride, skip):
+    """The adjoint of the averaged spectrum (segments weighted 1/N, overlaps summed, skipped
+    frames zero) through torch.autograd, against the FP64 oracle's Welch gradient."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    from paper_2607_02236_gb300.autograd import spectrum
+    spec = StreamSpec(P=2, Kx=16, Ky=12, T=64, Tc=32, n_omega=24, E_max_meV=120.0, window="hann",
+                      detectors=(Detector("circular", 0, 0, -1, 3.5), Detector("annular", 1.0, 0.0, 2.0, 5.0)))
+    n = skip + (N - 1) * (stride or spec.T) + spec.T
+    fr = make_frames(spec.P, n, spec.Ky, spec.Kx, 21)
+    rng = np.random.default_rng(5)
+    c = rng.standard_normal((spec.P, len(spec.detectors), spec.Nw))
+    x = torch.from_numpy(np.ascontiguousarray(fr.transpose(1, 0, 2, 3))).to("cuda").requires_grad_(True)
+    with TacawPlan([welch_config(spec, N, stride, skip)], precision="fp32") as plan:
+        S = spectrum(x, plan, 0, 20)
+        L = (S * torch.tensor(c, dtype=torch.float32, device="cuda")).sum()
+        L.backward()
+        torch.cuda.synchronize()
+    g = x.grad.cpu().numpy().transpose(1, 0, 2, 3)               # [P, n, Ky, Kx]
+    ref = oracle.welch_gradient(fr, c, spec.T, stride or spec.T, skip_init=skip, **oracle_kw(spec))
+    rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    assert rel <= 1e-4, rel
+    assert np.all(g[:, :skip] == 0)
+    refS = oracle.welch_forward(fr, spec.T, stride or spec.T, skip_init=skip, **oracle_kw(spec)).S
+    assert rel_err_peak(S.detach().cpu().numpy(), refS) <= TOL["fp32"]

@@ -365,6 +365,36 @@ def test_gradient_central_differences():
             assert abs(fd - an) <= 1e-7 * max(1.0, abs(an)) + floor, (idx, comp, fd, an, floor)
 
 
+def test_welch_gradient_central_differences():
+    """welch_gradient against central differences of the Welch loss sum dLdS * S_welch
+    (overlapping segments, skipped leading frames), probed on frames of one, two and no segments."""
+    psi, dLdS, kw = _grad_case()
+    P, T, Ky, Kx = psi.shape
+    L, stride, skip = 12, 5, 3
+    rng = np.random.default_rng(11)
+    n = skip + 3 * stride + L
+    seq = (rng.standard_normal((P, n, Ky, Kx)) + 1j * rng.standard_normal((P, n, Ky, Kx)))
+    g = oracle.welch_gradient(seq, dLdS, L, stride, skip_init=skip, **kw)
+
+    def welch_loss(x):
+        return float(np.sum(dLdS * oracle.welch_forward(x, L, stride, skip_init=skip, **kw).S))
+
+    h = 1e-6
+    floor = 16 * np.finfo(np.float64).eps * abs(welch_loss(seq)) / h + 1e-9
+    assert np.all(g[:, :skip] == 0)
+    for t in (0, skip, skip + 2, skip + 6, skip + 11, skip + 13, n - 1):
+        for _ in range(4):
+            idx = (int(rng.integers(0, P)), t, int(rng.integers(0, Ky)), int(rng.integers(0, Kx)))
+            for comp, unit in (("re", 1.0), ("im", 1j)):
+                a = seq.copy()
+                b = seq.copy()
+                a[idx] += h * unit
+                b[idx] -= h * unit
+                fd = (welch_loss(a) - welch_loss(b)) / (2 * h)
+                an = g[idx].real if comp == "re" else g[idx].imag
+                assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)) + floor, (idx, comp, fd, an, floor)
+
+
 def test_gradient_matches_torch_autograd():
     torch = pytest.importorskip("torch")
     psi, dLdS, kw = _grad_case(9)
