@@ -1311,7 +1311,7 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
 // thread, which bounds the drained columns a worker holds (kIpCols).
 constexpr int kIpRawMax = 4;
 constexpr int kIpBlockFrames = 32;
-constexpr int kIpCols = 56;          // accumulator columns a worker drains (tiles of <= 56 energies)
+constexpr int kIpCols = 80;          // accumulator columns a worker drains (tiles of <= 80 energies)
 struct TcInplaceArgs {
     CUtensorMap fmap;          // frames of the flush as [n_frames][pitch_frame] complex64 (fmap_ok)
     int fmap_ok;               // evenly spaced frames: one 2-D box of 32 frames x 128 rows a block

@@ -297,7 +297,7 @@ cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps /* TcMaps */, 
 int64_t tc_grid_ctas(const TcPlanArgs &a);
 constexpr int kMaxGroupStreams = 16;
 constexpr int kDrainMaxOmegaTile = 112;   // drained form: complex energies per tile at most
-constexpr int kInplaceMaxOmegaTile = 56;  // in-place drained form (worker registers at 168 a thread)
+constexpr int kInplaceMaxOmegaTile = 80;  // in-place drained form (worker registers at 168 a thread)
 // one launch over up to kMaxGroupStreams streams' flushes (same cluster size and block frames)
 cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *maps, int n, cudaStream_t st);
 cudaError_t launch_flush_tc_direct(const TcPlanArgs &a, const TcDirectArgs &d, const void *maps, cudaStream_t st);
