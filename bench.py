@@ -67,6 +67,8 @@ def parse():
                     help="drained accumulator form: chunk length in frames (0: off)")
     ap.add_argument("--tc-pair", type=int, default=0, choices=[0, 1, 2],
                     help="CTA-pair MMAs (256 rows over a cluster of two SMs): 1 relayed, 2 direct stage barriers")
+    ap.add_argument("--accum", default="auto", choices=["auto", "kahan", "fp64", "fp32"],
+                    help="Psi accumulators across flushes (only used when a segment needs several flushes)")
     ap.add_argument("--tc-max-ctas", type=int, default=0,
                     help="persistent contraction grid cap (0: every SM); with --pipeline 2 the free SMs "
                          "convert the next segment's pushes beside the current contraction")
@@ -285,7 +287,7 @@ def batched_arm(args):
     S = torch.empty(max(1, sum(s.P * len(s.detectors) * s.Nw for s in specs)), dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plan = TacawPlan([stream_config(s) for s in specs], precision="split_bf16", tune="")
+    plan = TacawPlan([stream_config(s) for s in specs], precision="split_bf16", tune="", accum=args.accum)
     plan_s = time.perf_counter() - t0
     info = plan.info()
     assert info["I_elems"] == I.numel() and info["S_elems"] <= S.numel()
@@ -374,6 +376,7 @@ def batched_arm(args):
                            "probes": [s.P for s in specs], "k_roi": [s.Kx for s in specs], "T": [s.T for s in specs],
                            "n_omega": specs[0].Nw, "frames_per_push": specs[0].Tc,
                            "k_stage": info["k_stage"], "tc_drain_frames": info["tc_drain_frames"],
+                           "accumulators": ["kahan", "fp64", "fp32"][info["accum"]],
                            "tuned_streams": info["tuned_streams"], "tune_candidates": info["tune_candidates"],
                            "tune_ms": round(info["tune_ms"], 1), "plan_create_s": round(plan_s, 2),
                            "plan_device_GB": round(info["device_bytes"] / 1e9, 1),
@@ -502,7 +505,8 @@ def main():
                   frames_in_place=bool(args.in_place and args.precision == "split_bf16"))
     # segments in flight: plan k and stream k take steps k, k + n, ...; the first plan writes I, S
     n_pipe = max(1, args.pipeline)
-    plans = [TacawPlan([stream_config(spec)], precision=args.precision, **tiling) for _ in range(n_pipe)]
+    plans = [TacawPlan([stream_config(spec)], precision=args.precision, accum=args.accum, **tiling)
+             for _ in range(n_pipe)]
     plan = plans[0]
     info = plan.info()
     outs = [(I, S)] + [(torch.empty_like(I), torch.empty_like(S)) for _ in range(n_pipe - 1)]

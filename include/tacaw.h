@@ -77,8 +77,17 @@ typedef enum {
 typedef enum { TACAW_PREC_FP32 = 0, TACAW_PREC_SPLIT_BF16 = 1 } tacaw_precision;
 
 /* Accumulation of Psi across flushes (used only when a segment needs more than one
- * flush): compensated FP32 (sum + Kahan compensation) or FP64.                         */
-typedef enum { TACAW_ACC_KAHAN_FP32 = 0, TACAW_ACC_FP64 = 1 } tacaw_accum;
+ * flush): compensated FP32 (sum + Kahan compensation), FP64, or plain FP32 (half the
+ * accumulator memory and traffic; each flush adds one FP32 rounding, ~6e-8 relative, so it
+ * suits segments of up to tens of flushes).                                            */
+typedef enum {
+    TACAW_ACC_KAHAN_FP32 = 0,
+    TACAW_ACC_FP64 = 1,
+    TACAW_ACC_FP32 = 2,
+    TACAW_ACC_AUTO = 3 /* plain FP32 when no segment needs more than 16 flushes at the K_stage
+                          that fits the budget with it (half-size accumulators leave more room
+                          for staging), else compensated FP32 */
+} tacaw_accum;
 
 /* Apertures (Sec. II.B DetectorSet).  Centres are offsets in pixels from the DC pixel
  * (kx/2, ky/2) of the ROI.  Pixel (ix, iy) with squared distance d2 to the centre is in
@@ -221,6 +230,7 @@ typedef struct {
     int tc_inplace_form;       /* frames_in_place kernel: 0 none, 1 register-fed, 2 persistent drained
                                   (chosen when every stream's tile rows are contiguous in a frame,
                                   all row offsets even, 32-frame blocks, one or two accumulators) */
+    int accum;                 /* tacaw_accum in use (TACAW_ACC_AUTO resolved at creation) */
 } tacaw_plan_info;
 
 /* Creates a plan: validates the descriptor, sizes and allocates device memory

@@ -271,9 +271,14 @@ void choose_omega_tile(Stream &s, int n_acc, int requested, int cap = 0) {
     s.Nw_pad = s.wt * s.n_wt;
 }
 
+// Automatic accumulators choose plain FP32 up to this many flushes per segment.
+constexpr int kAutoFp32Flushes = 16;
+
 // Staging + accumulator bytes of one stream for a given ring length.
 int64_t stream_stage_bytes(const Stream &s, int ring) { return s.M_pad * 8 * (int64_t)ring; }
-int64_t stream_acc_bytes(const Stream &s) { return (int64_t)s.Nw_pad * s.M_pad * 16; }
+int64_t stream_acc_bytes(const Stream &s, int accum) {
+    return (int64_t)s.Nw_pad * s.M_pad * (accum == TACAW_ACC_FP32 ? 8 : 16);
+}
 
 EpiArgs epi_args(tacaw_plan_s *p, const Stream &s, int mode, float *I_out, float2 *Psi_out) {
     EpiArgs e{};
@@ -283,7 +288,7 @@ EpiArgs epi_args(tacaw_plan_s *p, const Stream &s, int mode, float *I_out, float
     e.Nw = s.Nw;
     e.mode = mode;
     e.has_prev = s.flushes > 0 ? 1 : 0;
-    e.accum = p->accum;
+    e.accum = p->accum == TACAW_ACC_FP64 ? 1 : 0;   // FP64 accumulators; else FP32 (acc_c: compensation)
     e.acc_s = s.acc_s;
     e.acc_c = s.acc_c;
     e.acc_d = s.acc_d;
@@ -621,7 +626,7 @@ tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
         if (p->accum == TACAW_ACC_FP64) {
             if (!dev_alloc(p, &s.acc_d, n)) return fail(TACAW_ERR_OOM, "cudaMalloc(accumulators)");
         } else {
-            if (!dev_alloc(p, &s.acc_s, n) || !dev_alloc(p, &s.acc_c, n))
+            if (!dev_alloc(p, &s.acc_s, n) || (p->accum == TACAW_ACC_KAHAN_FP32 && !dev_alloc(p, &s.acc_c, n)))
                 return fail(TACAW_ERR_OOM, "cudaMalloc(accumulators)");
         }
     }
@@ -860,7 +865,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     if (desc->n_streams < 1 || !desc->streams) return fail(TACAW_ERR_INVALID_ARG, "n_streams must be >= 1");
     if (desc->precision != TACAW_PREC_FP32 && desc->precision != TACAW_PREC_SPLIT_BF16)
         return fail(TACAW_ERR_INVALID_ARG, "bad precision");
-    if (desc->accum != TACAW_ACC_KAHAN_FP32 && desc->accum != TACAW_ACC_FP64)
+    if (desc->accum < TACAW_ACC_KAHAN_FP32 || desc->accum > TACAW_ACC_AUTO)
         return fail(TACAW_ERR_INVALID_ARG, "bad accum");
     if (desc->k_stage < 0 || (desc->k_stage % 8) != 0) return fail(TACAW_ERR_INVALID_ARG, "k_stage must be a multiple of 8");
     for (int i = 0; i < desc->n_streams; ++i) {
@@ -934,7 +939,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         }
     }
     p->prec = desc->precision;
-    p->accum = desc->accum;
+    p->accum = desc->accum == TACAW_ACC_AUTO ? TACAW_ACC_KAHAN_FP32 : desc->accum;   // resolved with K_stage
     if (!dev_alloc(p, &p->d_err, 1) || cudaMemset(p->d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         free_all(p);
@@ -1080,16 +1085,35 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         fixed += s.M * (8 + 8 + 16) + (int64_t)s.T_pad * s.Nw_pad * 8 + (int64_t)s.n_kb_T * 2 * s.Nw_pad * 16 * 4 +
                  (int64_t)s.npix * 16 + (1 << 20);
     }
+    int accum = desc->accum == TACAW_ACC_AUTO ? TACAW_ACC_FP32 : desc->accum;
     auto need = [&](int K) {
         int64_t b = fixed;
         for (auto &s : p->s) {
             const int ring = std::min(K, s.T_pad);
             b += p->in_place ? (int64_t)ring * 8 : stream_stage_bytes(s, ring);
-            if (s.T > ring) b += stream_acc_bytes(s);
+            if (s.T > ring) b += stream_acc_bytes(s, accum);
         }
         return b;
     };
+    // automatic accumulators: plain FP32 while no segment takes more than kAutoFp32Flushes
+    // flushes at the K_stage they allow, else compensated FP32
+    auto max_flushes = [&](int K) {
+        int f = 1;
+        for (auto &s : p->s) f = std::max(f, (s.T + std::min(K, s.T_pad) - 1) / std::min(K, s.T_pad));
+        return f;
+    };
+    auto pick_k = [&]() {
+        if (need(T_pad_max) <= budget) return T_pad_max;
+        for (int k = (T_pad_max / 64) * 64; k >= 64; k -= 64)  // multiples of 64: any block size divides
+            if (need(k) <= budget) return k;
+        return 0;
+    };
     int K = desc->k_stage;
+    if (desc->accum == TACAW_ACC_AUTO) {
+        const int k32 = K ? K : pick_k();
+        if (k32 == 0 || max_flushes(k32) > kAutoFp32Flushes) accum = TACAW_ACC_KAHAN_FP32;
+    }
+    p->accum = accum;
     if (K == 0) {
         if (need(T_pad_max) <= budget) {
             K = T_pad_max;
@@ -1323,6 +1347,7 @@ tacaw_status tacaw_plan_get_info(tacaw_plan_t p, tacaw_plan_info *info) {
     info->tc_pair = (p->prec == TACAW_PREC_SPLIT_BF16 && !p->s.empty()) ? p->s[0].tc_pair : 0;
     info->tc_drain_frames = p->drain_kb * p->bf;
     info->tc_inplace_form = p->in_place ? (p->ip2 ? 2 : 1) : 0;
+    info->accum = p->accum;
     return TACAW_OK;
 }
 

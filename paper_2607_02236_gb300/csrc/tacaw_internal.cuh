@@ -94,7 +94,7 @@ __device__ __forceinline__ void epi_element_wb(const EpiArgs &a, const RowCtx &r
             a.acc_d[ai] = make_double2(re, im);
         } else {
             a.acc_s[ai] = make_float2(re, im);
-            a.acc_c[ai] = make_float2(0.f, 0.f);
+            if (a.acc_c) a.acc_c[ai] = make_float2(0.f, 0.f);
         }
         return;
     }
@@ -104,7 +104,7 @@ __device__ __forceinline__ void epi_element_wb(const EpiArgs &a, const RowCtx &r
             s.x += re;
             s.y += im;
             a.acc_d[ai] = s;
-        } else {
+        } else if (a.acc_c) {
             // Kahan (compensated) summation per component
             float2 s = a.acc_s[ai], c = a.acc_c[ai];
             float yr = re - c.x, yi = im - c.y;
@@ -113,6 +113,10 @@ __device__ __forceinline__ void epi_element_wb(const EpiArgs &a, const RowCtx &r
             c.y = (ti - s.y) - yi;
             a.acc_s[ai] = make_float2(tr, ti);
             a.acc_c[ai] = c;
+        } else {
+            // plain FP32 sums (one rounding per flush)
+            const float2 s = a.acc_s[ai];
+            a.acc_s[ai] = make_float2(s.x + re, s.y + im);
         }
         return;
     }
@@ -124,7 +128,7 @@ __device__ __forceinline__ void epi_element_wb(const EpiArgs &a, const RowCtx &r
             pr = (float)(s.x + (double)re);
             pi = (float)(s.y + (double)im);
         } else {
-            float2 s = a.acc_s[ai], c = a.acc_c[ai];
+            const float2 s = a.acc_s[ai], c = a.acc_c ? a.acc_c[ai] : make_float2(0.f, 0.f);
             pr = s.x + (re - c.x);
             pi = s.y + (im - c.y);
         }
@@ -172,17 +176,22 @@ __device__ __forceinline__ void epi_apply(const EpiArgs &a, const RowCtx &r, int
     const size_t ai = (size_t)j * (size_t)a.M_pad + (size_t)r.m;
     if (K == EPI_STORE_KAHAN) {
         a.acc_s[ai] = make_float2(re, im);
-        a.acc_c[ai] = make_float2(0.f, 0.f);
+        if (a.acc_c) a.acc_c[ai] = make_float2(0.f, 0.f);
     } else if (K == EPI_STORE_FP64) {
         a.acc_d[ai] = make_double2(re, im);
     } else if (K == EPI_ADD_KAHAN) {
-        float2 s = a.acc_s[ai], c = a.acc_c[ai];
-        float yr = re - c.x, yi = im - c.y;
-        float tr = s.x + yr, ti = s.y + yi;
-        c.x = (tr - s.x) - yr;
-        c.y = (ti - s.y) - yi;
-        a.acc_s[ai] = make_float2(tr, ti);
-        a.acc_c[ai] = c;
+        if (a.acc_c) {
+            float2 s = a.acc_s[ai], c = a.acc_c[ai];
+            float yr = re - c.x, yi = im - c.y;
+            float tr = s.x + yr, ti = s.y + yi;
+            c.x = (tr - s.x) - yr;
+            c.y = (ti - s.y) - yi;
+            a.acc_s[ai] = make_float2(tr, ti);
+            a.acc_c[ai] = c;
+        } else {
+            const float2 s = a.acc_s[ai];   // plain FP32 accumulators
+            a.acc_s[ai] = make_float2(s.x + re, s.y + im);
+        }
     } else if (K == EPI_ADD_FP64) {
         double2 s = a.acc_d[ai];
         s.x += re;
@@ -191,7 +200,7 @@ __device__ __forceinline__ void epi_apply(const EpiArgs &a, const RowCtx &r, int
     } else {
         float pr = re, pi = im;
         if (K == EPI_FINAL_KAHAN) {
-            float2 s = a.acc_s[ai], c = a.acc_c[ai];
+            const float2 s = a.acc_s[ai], c = a.acc_c ? a.acc_c[ai] : make_float2(0.f, 0.f);
             pr = s.x + (re - c.x);
             pi = s.y + (im - c.y);
         } else if (K == EPI_FINAL_FP64) {

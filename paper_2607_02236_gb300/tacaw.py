@@ -20,7 +20,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_OVERFLOW, ERR_TIMEOUT, ER
 STATUS_NAMES = ["OK", "INVALID_ARG", "OOM", "CUDA", "STATE", "OVERFLOW", "TIMEOUT", "UNSUPPORTED"]
 WINDOWS = {"rect": 0, "hann": 1, "gauss": 2, "tukey": 3, "blackmanharris": 4, "kaiser": 5, "chebwin": 6}
 PRECISIONS = {"fp32": 0, "split_bf16": 1}
-ACCUMS = {"kahan": 0, "fp64": 1}
+ACCUMS = {"kahan": 0, "fp64": 1, "fp32": 2, "auto": 3}
 DET_KINDS = {"circular": 0, "annular": 1, "mask": 2}
 
 # Every symbol include/tacaw.h declares (checked by the CPU test that loads the library).
@@ -68,7 +68,7 @@ class CPlanInfo(ctypes.Structure):
                 ("stages", c_int), ("kernel_launches", c_int64), ("tc_accumulators", c_int),
                 ("tc_cluster", c_int), ("tc_block_frames", c_int), ("frames_in_place", c_int),
                 ("tc_pair", c_int), ("tc_drain_frames", c_int), ("tuned_streams", c_int), ("tune_candidates", c_int), ("tune_ms", c_double),
-                ("tc_inplace_form", c_int)]
+                ("tc_inplace_form", c_int), ("accum", c_int)]
 
 
 _lib = None
@@ -170,7 +170,7 @@ class StreamConfig:
 class TacawPlan:
     """A streaming plan over one or more streams (see include/tacaw.h)."""
 
-    def __init__(self, streams: Sequence[StreamConfig], precision: str = "split_bf16", accum: str = "kahan",
+    def __init__(self, streams: Sequence[StreamConfig], precision: str = "split_bf16", accum: str = "auto",
                  hbm_budget_bytes: int = 0, k_stage: int = 0, tc_omega_tile: int = 0,
                  tc_accumulators: int = 0, tc_cluster: int = 0, tc_block_frames: int = 0, tc_prefetch: int = 0,
                  frames_in_place: bool = False, tune: Optional[str] = None, tc_pair: int = 0,

@@ -93,7 +93,7 @@ def test_edge_cases(name, precision):
         assert out["info"]["flushes"] > 1
 
 
-@pytest.mark.parametrize("accum", ["kahan", "fp64"])
+@pytest.mark.parametrize("accum", ["kahan", "fp64", "fp32"])
 @pytest.mark.parametrize("precision", ["fp32", "split_bf16", "split_inplace"])
 def test_streaming_flushes_match_single_flush(precision, accum):
     """K_stage < T (accumulators in HBM) gives the oracle's result too."""
@@ -102,6 +102,17 @@ def test_streaming_flushes_match_single_flush(precision, accum):
     fr = frames.frames(spec, 3, 0, spec.T)
     out, ref, e = check(spec, fr, precision, k_stage=48, accum=accum)
     assert out["info"]["flushes"] == 5
+
+
+@pytest.mark.parametrize("k_stage,expect", [(16, 2), (8, 0), (0, 2)])
+def test_auto_accumulators(k_stage, expect):
+    """accum="auto": plain FP32 cross-flush sums up to 16 flushes a segment (13 here at
+    K_stage = 16), compensated beyond (25 at K_stage = 8); irrelevant for one flush."""
+    spec = StreamSpec(P=2, Kx=16, Ky=16, T=200, Tc=24, n_omega=40, E_max_meV=120.0, window="hann",
+                      detectors=(Detector("circular", 0, 0, -1, 4.0),))
+    fr = frames.frames(spec, 5, 0, spec.T)
+    out, ref, e = check(spec, fr, "split_bf16", k_stage=k_stage, accum="auto")
+    assert out["info"]["accum"] == expect, out["info"]["accum"]
 
 
 @pytest.mark.parametrize("precision", ["fp32", "split_bf16"])
