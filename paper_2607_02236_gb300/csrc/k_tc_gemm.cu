@@ -57,7 +57,19 @@ struct TcGroup {
     int n;
     int stages, n_max;         // drained kernel: ring stages and ring/TMEM width (widest tile)
     int64_t tiles;             // drained kernel: tiles of all entries
+    int rot;                   // drained kernel: rotate energy tiles across a CTA's passes (see wtile_of)
 };
+
+// Energy tile of local tile lt on a CTA's k-th pass.  Tiles go out in row-major order (the
+// energy tiles of a row tile run side by side and share its operand rows in L2).  When the
+// grid is a multiple of the tile count per row (one stream), every pass hands each CTA the
+// same energy slot; rotating the slot by the pass number keeps each row tile's set of energy
+// tiles intact while cycling every CTA through all of them (a narrower last tile then shortens
+// every CTA's work alike).
+__device__ __forceinline__ int wtile_of(int64_t lt, int n_wt, int rot, int64_t pass) {
+    const int w = (int)(lt % n_wt);
+    return rot ? (int)((w + pass) % n_wt) : w;
+}
 
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s per wait
 constexpr int kMaxStages = 12;
@@ -955,14 +967,17 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
             int s = 0;
             uint32_t ph = 0;                          // parity of the current use of slot s
             int issued = 0;                           // copies in flight that may still land
-            for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
+            int64_t pass = 0;
+            for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x, ++pass) {
                 const int gi = group_entry(g, t);
                 const TcGroupEntry &en = g.e[gi];
                 const int64_t lt = t - en.cta_begin;
-                const int wtile = (int)(lt % en.args.n_wt);
+                const int wtile = wtile_of(lt, en.args.n_wt, g.rot, pass);
                 const int m0 = (int)(lt / en.args.n_wt) * kMTile;
                 const int N = en.args.N;
-                const uint32_t tx_bytes = 2u * kABytes + 2u * (uint32_t)N * RB;
+                // columns of this tile (N_last: a narrower last energy tile; 0 = full width)
+                const int Nt = (wtile == en.args.n_wt - 1 && en.args.N_last > 0) ? en.args.N_last : N;
+                const uint32_t tx_bytes = 2u * kABytes + 2u * (uint32_t)Nt * RB;
                 const uint8_t *pAhi = static_cast<const uint8_t *>(en.args.A_hi) + (size_t)m0 * RB;
                 const uint8_t *pAlo = static_cast<const uint8_t *>(en.args.A_lo) + (size_t)m0 * RB;
                 const size_t b0 = ((size_t)en.args.kbB0 * (size_t)en.args.b_rows + (size_t)wtile * N) * RB;
@@ -981,8 +996,8 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
                     // the tables are pre-swizzled: each operand block is one contiguous copy
                     bulk_load(st, pAhi, kABytes, full);
                     bulk_load(st + kABytes, pAlo, kABytes, full);
-                    bulk_load(st + 2 * kABytes, pBhi, (uint32_t)N * RB, full);
-                    bulk_load(st + 2 * kABytes + b_pad, pBlo, (uint32_t)N * RB, full);
+                    bulk_load(st + 2 * kABytes, pBhi, (uint32_t)Nt * RB, full);
+                    bulk_load(st + 2 * kABytes + b_pad, pBlo, (uint32_t)Nt * RB, full);
                     pAhi += a_step;
                     pAlo += a_step;
                     pBhi += b_step;
@@ -1019,7 +1034,9 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
             const uint32_t accH = tmem, accS = tmem + 256u;
             for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x, ++tiles) {
                 const TcGroupEntry &en = g.e[group_entry(g, t)];
-                const int N = en.args.N, n_kb = en.args.n_kb, cb = en.args.drain_kb;
+                const bool last_w = en.args.N_last > 0 &&
+                                    wtile_of(t - en.cta_begin, en.args.n_wt, g.rot, tiles) == en.args.n_wt - 1;
+                const int N = last_w ? en.args.N_last : en.args.N, n_kb = en.args.n_kb, cb = en.args.drain_kb;
                 const uint32_t id = idesc_bf16_f32(kMTile, N);
                 if (tiles > 0) {
                     // the previous tile's H and S must be in registers before they are reused
@@ -1099,7 +1116,7 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
             bool stop = false;
             for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x, ++tiles) {
                 const TcGroupEntry &en = g.e[group_entry(g, t)];
-                const int N = en.args.N, n_kb = en.args.n_kb, cb = en.args.drain_kb;
+                const int N = en.args.N, n_kb = en.args.n_kb, cb = en.args.drain_kb;   // form 1: full tiles
                 const uint32_t id = idesc_bf16_f32(kMTile, N);
                 int kc = 0;
                 for (int kb = 0; kb < n_kb; ++kb) {
@@ -1167,9 +1184,10 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
             const TcGroupEntry &en = g.e[group_entry(g, t)];
             const TcPlanArgs &a = en.args;
             const int64_t lt = t - en.cta_begin;
-            const int wtile = (int)(lt % a.n_wt);
+            const int wtile = wtile_of(lt, a.n_wt, g.rot, tiles);
             const int m0 = (int)(lt / a.n_wt) * kMTile;
-            const int cols = a.wt;                    // N / 2 columns per thread
+            // N / 2 columns per thread (the last energy tile may be narrower)
+            const int cols = ((wtile == a.n_wt - 1 && a.N_last > 0) ? a.N_last : a.N) / 2;
             const int col0 = h * cols;
             const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)col0;
             const int n_chunks = (a.n_kb + a.drain_kb - 1) / a.drain_kb;
@@ -1222,13 +1240,14 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
         float sum[kDrainCols];
         int64_t c = 0;                                // chunks consumed
         bool ok = true;
-        for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        int64_t pass = 0;
+        for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++pass) {
             const TcGroupEntry &en = g.e[group_entry(g, t)];
             const TcPlanArgs &a = en.args;
             const int64_t lt = t - en.cta_begin;
-            const int wtile = (int)(lt % a.n_wt);
+            const int wtile = wtile_of(lt, a.n_wt, g.rot, pass);
             const int m0 = (int)(lt / a.n_wt) * kMTile;
-            const int cols = a.wt;                    // N / 2 columns per thread
+            const int cols = a.wt;                    // N / 2 columns per thread (form 1: full tiles)
             const int col0 = h * cols;
             const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)col0;
             const int n_chunks = (a.n_kb + a.drain_kb - 1) / a.drain_kb;
@@ -2295,6 +2314,8 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *map
         int64_t cap = (int64_t)occ * sms;
         if (args[0].max_ctas > 0 && args[0].max_ctas < cap) cap = args[0].max_ctas;
         if (cap < total) grid = (unsigned)cap;
+        // one stream whose row of energy tiles divides the grid: rotate the energy slots
+        g->rot = (n == 1 && args[0].n_wt > 1 && grid % (unsigned)args[0].n_wt == 0) ? 1 : 0;
     }
     auto kern = drain ? (form == 2 ? flush_tc_drain2_kernel : flush_tc_drain_kernel)
                       : (pair ? flush_tc_pair_kernel : flush_tc_kernel);

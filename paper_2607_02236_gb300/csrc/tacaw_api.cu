@@ -310,6 +310,12 @@ TcPlanArgs tc_args(tacaw_plan_s *p, const Stream &s, const EpiArgs &e) {
     a.wt = s.wt;
     a.n_wt = s.n_wt;
     a.N = 2 * s.wt;
+    // split drained form: the last energy tile computes only the columns that hold energies
+    a.N_last = a.N;
+    if (p->drain_kb > 0 && p->drain_form == 2 && !p->in_place) {
+        const int last = s.Nw - (s.n_wt - 1) * s.wt;
+        a.N_last = std::min(a.N, (2 * last + 15) / 16 * 16);
+    }
     a.n_kb = (n + p->bf - 1) / p->bf;
     a.kbB0 = s.stage_start / p->bf;
     a.bf = p->bf;

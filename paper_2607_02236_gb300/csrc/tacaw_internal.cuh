@@ -283,6 +283,7 @@ struct TcPlanArgs {
     int b_rows;                //   rows per twiddle block of B (2 * Nw_pad)
     int prefetch;              // staging blocks of A prefetched into L2 ahead of the current one (0: off)
     int max_ctas;              // persistent grids: at most this many CTAs (0: one per SM)
+    int N_last;                // split drained form: columns of the last energy tile (<= N, multiple of 16)
     unsigned long long *trace; // null, or kTraceWords globaltimer stamps per CTA (phase boundaries)
     uint32_t *err;
 };
