@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -34,8 +35,8 @@ UNIT = "CMAC/s"
 KERNEL_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum of flush_tc_drain2_kernel on `bench.py
     # --small` (P=2, T=2048, 400 energies, default tiling): 2.460228 GB read + 0.203510 GB written per
-    # launch of 1.0737e11 CMAC; key = hash of k_tc_gemm.cu without its in-place section
-    ("2b4050ab697da14a", "flush_tc_drain2_kernel"): 2.480799e-02,
+    # launch of 1.0737e11 CMAC; key = hash of the code of k_tc_gemm.cu without its in-place section
+    ("13254f331f0f22cb", "flush_tc_drain2_kernel"): 2.480799e-02,
 }
 
 
@@ -178,12 +179,16 @@ INPLACE_SECTION = (b"// In-place drained form (persistent)", b"// In-place varia
 
 
 def file_hash(path, skip=None):
+    """Hash of a source file's code: `//` comments and whitespace are left out, so that only
+    code changes invalidate a capture."""
     with open(path, "rb") as f:
         data = f.read()
     if skip:
         a, b = data.find(skip[0]), data.find(skip[1])
         if 0 <= a < b:
             data = data[:a] + data[b:]
+    data = re.sub(rb"//[^\n]*", b"", data)
+    data = re.sub(rb"\s+", b"", data)
     return hashlib.sha256(data).hexdigest()[:16]
 
 

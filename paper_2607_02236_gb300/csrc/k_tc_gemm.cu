@@ -27,6 +27,15 @@
 //               and the per-element flush update (store / compensated add / finalize)
 // Every mbarrier wait is bounded (globaltimer); on timeout the kernel records an error
 // bit, lets in-flight copies land, frees TMEM and returns.
+//
+// Kernels of this file:
+//   flush_tc_kernel          the layout above (1, 2 or 3 accumulators, optional multicast)
+//   flush_tc_pair_kernel     CTA pairs (cta_group::2, 256-row MMAs over two SMs)
+//   flush_tc_drain_kernel    persistent, one double-buffered accumulator drained into FP32
+//   flush_tc_drain2_kernel   persistent, hi*hi drained, small products apart (the default)
+//   flush_tc_inplace_kernel  persistent, pushed frames read in place, operand A converted into
+//                            tensor memory (no staging pass)
+//   flush_tc_direct_kernel   pushed frames read in place, converted in shared memory
 #include <cuda.h>
 
 #include <algorithm>
