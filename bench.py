@@ -34,9 +34,9 @@ UNIT = "CMAC/s"
 # the kernel's source file at capture time (reported only while the source is unchanged).
 KERNEL_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum of flush_tc_drain2_kernel on `bench.py
-    # --small` (P=2, T=2048, 400 energies, default tiling): 2.460228 GB read + 0.203510 GB written per
+    # --small` (P=2, T=2048, 400 energies, default tiling): 2.461281 GB read + 0.203440 GB written per
     # launch of 1.0737e11 CMAC; key = hash of the code of k_tc_gemm.cu without its in-place section
-    ("13254f331f0f22cb", "flush_tc_drain2_kernel"): 2.480799e-02,
+    ("c496d2cc510ed277", "flush_tc_drain2_kernel"): 2.481715e-02,
 }
 
 
@@ -46,7 +46,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32"])
+    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "split_fp16", "fp32"])
+    ap.add_argument("--fp16-steps", type=int, default=2,
+                    help="steps of the split-FP16 path for comparison (0: skip)")
     ap.add_argument("--fp32-steps", type=int, default=2, help="steps of the FP32 path for comparison (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="end-to-end steps from pinned host memory (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU oracle baseline")
@@ -54,8 +56,9 @@ def parse():
     ap.add_argument("--pipeline", type=int, default=1,
                     help="segments in flight: one plan and CUDA stream each, steps alternate between them "
                          "(a segment's conversions overlap the previous segment's contraction)")
-    ap.add_argument("--workload", default="realistic", choices=["realistic", "batched"],
-                    help="batched: the 16 uneven partitions, autotuned tiles, one CUDA-graph replay per step")
+    ap.add_argument("--workload", default="realistic", choices=["realistic", "batched", "diff"],
+                    help="batched: the 16 uneven partitions, autotuned tiles, one CUDA-graph replay per step; "
+                         "diff: the differentiation workload, forward + adjoint per step")
     ap.add_argument("--in-place", dest="in_place", action="store_true", default=False,
                     help="the contraction reads pushed frames in place (no staging pass)")
     ap.add_argument("--staging", dest="in_place", action="store_false",
@@ -405,12 +408,154 @@ def batched_arm(args):
 
 
 # ----------------------------------------------------------------------------------------------
+# Differentiation: forward spectrum and the hand-written adjoint (tacaw_backward) per step
+# ----------------------------------------------------------------------------------------------
+def diff_arm(args):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import synth
+    import synth.gpu as sg
+    from paper_2607_02236_gb300 import TacawPlan
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = synth.diff()
+    spec = w.streams[0]
+    P, K, T, Nw = spec.P, spec.Kx, spec.T, spec.Nw
+    D = len(spec.detectors)
+    npix = K * K
+    mask = oracle.detector_masks(K, K, spec.detectors)          # [D, K*K] (host geometry only)
+    n_ap = int(np.count_nonzero(mask.reshape(D, -1).any(axis=0)))
+    # forward: the dense DFT of every ROI pixel; adjoint: Psi recomputed on the aperture pixels
+    # (not stored) and projected back onto every frame (G = 0 outside the apertures)
+    cmac_fwd = P * npix * T * Nw
+    cmac_adj = 2 * P * n_ap * T * Nw
+    st_t = torch.cuda.current_stream()
+    st = st_t.cuda_stream
+    x = torch.empty(T * P * npix, dtype=torch.complex64, device="cuda")
+    sg.generate(spec, 4 + rank, x.data_ptr(), 0, T, pitch_row=K, pitch_frame=P * npix, pitch_probe=npix, stream=st)
+    grad = torch.empty_like(x)
+    c = torch.tensor(synth.loss_weights(Nw, seed=0), dtype=torch.float32, device="cuda")
+    dLdS = c[None, None, :].expand(P, D, Nw).contiguous()
+    I = torch.empty(P * Nw * npix, dtype=torch.float32, device="cuda")
+    S = torch.empty(max(1, P * D * Nw), dtype=torch.float32, device="cuda")
+    plan = TacawPlan([stream_config(spec)], precision=w.precision)
+    info = plan.info()
+    n_push = (T + spec.Tc - 1) // spec.Tc
+
+    def step(ev=None):
+        plan.reset(st)
+        for i in range(n_push):
+            plan.push(0, x.data_ptr() + i * spec.Tc * P * npix * 8, min(spec.Tc, T - i * spec.Tc), st)
+        plan.finalize_async(I, S, None, st)
+        if ev is not None:
+            ev[0].record(st_t)
+        plan.backward(0, dLdS, x, grad, st)
+        if ev is not None:
+            ev[1].record(st_t)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.check_errors(st)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    plan.set_timing(True)
+    plan.kernel_time_ms(reset=True)
+    l0 = plan.info()["kernel_launches"]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st_t)
+    for k in range(args.steps):
+        step(evs[k])
+    e1.record(st_t)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = clk.stop()
+    plan.check_errors(st)
+    launches = (plan.info()["kernel_launches"] - l0) // args.steps
+    k_ms, k_n = plan.kernel_time_ms(reset=True)
+    plan.set_timing(False)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda") / args.steps
+    adj_ms = statistics.median(a.elapsed_time(b) for a, b in evs)
+    value = job_rate(cmac_fwd + cmac_adj, world, ms * 1e-3)
+
+    # stated error: spectra of two probes and the gradient at 16 aperture pixels of two probes
+    rng = np.random.default_rng(rank)
+    kw = dict(window_kind=spec.window, E_meV=spec.energies_meV(), dt_fs=spec.dt_fs,
+              subtract_mean=spec.subtract_mean)
+    ap = np.nonzero(mask[0].reshape(-1))[0]
+    xv = x.view(T, P, npix)
+    gv = grad.view(T, P, npix)
+    err_s, err_g = 0.0, 0.0
+    for p in rng.choice(P, 2, replace=False):
+        series = xv[:, int(p)][:, torch.as_tensor(ap, device="cuda")].cpu().numpy()
+        _, Iref = oracle.forward_pixels(series, **kw)
+        sref = Iref.sum(axis=1)
+        sgot = S.view(P, D, Nw)[int(p), 0].cpu().numpy()
+        err_s = max(err_s, float(np.max(np.abs(sgot - sref)) / np.max(np.abs(sref))))
+        sel = rng.choice(len(ap), 16, replace=False)
+        gref = oracle.gradient_pixels(series[:, sel], c.cpu().numpy().astype(np.float64)[None, :],
+                                      np.ones((len(sel), 1)), **kw)
+        ggot = gv[:, int(p)][:, torch.as_tensor(ap[sel], device="cuda")].cpu().numpy()
+        err_g = max(err_g, float(np.linalg.norm(ggot - gref) / np.linalg.norm(gref)))
+
+    mhz = clocks.get("sm_max_mhz") or 2070.0
+    ffma_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    # kernel_time_ms: total over the timed launches and their count
+    fwd_launch_ms = k_ms / max(k_n, 1)
+    fwd_tflops = (cmac_fwd * args.steps / max(k_n, 1)) * 8 / (fwd_launch_ms * 1e-3) / 1e12
+    adj_tflops = cmac_adj * 8 / (adj_ms * 1e-3) / 1e12
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name, "probes": P, "k_roi": f"{K}x{K}", "T": T, "n_omega": Nw,
+                           "window": spec.window, "aperture_pixels": n_ap,
+                           "cmac_per_step": {"forward": cmac_fwd, "adjoint": cmac_adj},
+                           "step": "reset + push + finalize_async (FP32 path) + tacaw_backward (dL/dS = c(E))",
+                           "l2": "frames (%.2f GB) and gradient re-read every step, no flush" % (T * P * npix * 8 / 1e9),
+                           "parallelism": f"replicas x{world}"},
+                "max_rel_err_S_vs_fp64": err_s, "rel_l2_err_grad_vs_fp64": err_g,
+                "error_sample": "spectra of 2 probes; gradient at 16 aperture pixels of 2 probes",
+                "clocks": clocks, "gpu_launches": launches, "e2e": None, "cpu_baseline": None,
+                "roofline": {"bound": "alu", "achieved": fwd_tflops, "peak": ffma_peak, "unit": "TFLOP/s",
+                             "frac": fwd_tflops / ffma_peak, "traffic": None, "kernel": "flush_simt_kernel",
+                             "flop_per_cmac": 8, "kernel_ms": fwd_launch_ms,
+                             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"},
+                "adjoint": {"ms": adj_ms, "cmac": cmac_adj, "achieved": adj_tflops, "peak": ffma_peak,
+                            "unit": "TFLOP/s", "frac": adj_tflops / ffma_peak, "bound": "alu",
+                            "kernels": "zero_roi_kernel, adj_forward_kernel, adj_backward_kernel",
+                            "timed": "CUDA events around the tacaw_backward call (median per step; includes "
+                                     "its closing wait for the device error word)"}}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+# ----------------------------------------------------------------------------------------------
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
     if args.workload == "batched":
         return batched_arm(args)
+    if args.workload == "diff":
+        return diff_arm(args)
 
     import numpy as np
     import torch
@@ -508,6 +653,7 @@ def main():
                   tc_cluster=args.tc_cluster, tc_block_frames=args.tc_block_frames, tc_pair=args.tc_pair,
                   tc_drain_frames=args.tc_drain_frames, tc_max_ctas=args.tc_max_ctas,
                   frames_in_place=bool(args.in_place and args.precision == "split_bf16"))
+    split = args.precision.startswith("split")
     # segments in flight: plan k and stream k take steps k, k + n, ...; the first plan writes I, S
     n_pipe = max(1, args.pipeline)
     plans = [TacawPlan([stream_config(spec)], precision=args.precision, accum=args.accum, **tiling)
@@ -526,7 +672,7 @@ def main():
 
     phases = None
     tr = None
-    if args.trace and args.precision == "split_bf16":
+    if args.trace and split:
         plan.set_timing(2)
         run_step(plan)
         torch.cuda.synchronize()
@@ -545,7 +691,7 @@ def main():
                       "tail_after_last_mma_us": round(float(np.median(tr[:, 6] - tr[:, 3])) / 1e3, 2),
                       "unit": "median per CTA"}
             tr = None
-    if tr is not None and args.trace and args.precision == "split_bf16":
+    if tr is not None and args.trace and split:
         names = ["setup", "fill", "main_loop", "drain", "epilogue", "exit"]
         phases = {n: round(float(np.median(tr[:, i + 1] - tr[:, i])) / 1e3, 3) for i, n in enumerate(names)}
         gaps = []
@@ -585,6 +731,17 @@ def main():
                 "max_rel_err_I_vs_fp64": errf, "tc_accumulators": 1, "omega_tile": fi["omega_tile"],
                 "block_frames": fi["tc_block_frames"], "cluster": fi["tc_cluster"],
                 "flush_tflops": cmac_step * 24 / (kf * 1e-3) / 1e12}
+
+    # split-FP16 pieces (scaled frames) on the same input: same kernels and tiling, other operand type
+    fp16 = None
+    if args.fp16_steps > 0 and args.precision == "split_bf16":
+        with TacawPlan([stream_config(spec)], precision="split_fp16", accum=args.accum, **tiling) as p16:
+            ms16, k16, _, _, _ = timed(p16, args.fp16_steps, 1)
+        got16 = Iv[torch.as_tensor(probes, device="cuda"), :, torch.as_tensor(pix, device="cuda")].cpu().numpy().T
+        err16 = float(np.max(np.abs(got16 - ref)) / np.max(np.abs(ref)))
+        fp16 = {"value": world * cmac_step / (ms16 * 1e-3), "unit": UNIT, "ms_per_step": ms16, "flush_ms": k16,
+                "max_rel_err_I_vs_fp64": err16, "fp16_scale": 4096,
+                "flush_tflops": cmac_step * 24 / (k16 * 1e-3) / 1e12}
 
     # FP32 CUDA-core path on the same input, for comparison at equal stated accuracy
     fp32 = None
@@ -666,8 +823,8 @@ def main():
     # roofline of the dominant kernel (the contraction) from its live CUDA-event duration
     peaks, peak_src = measured_peaks()
     cmac_launch = cmac_step / max(k_per_step, 1)
-    if args.precision == "split_bf16":
-        # 3 bf16 products (hi*hi, hi*lo, lo*hi) x 4 real MAC per complex MAC = 24 flop per CMAC
+    if split:
+        # 3 bf16 (or fp16) products (hi*hi, hi*lo, lo*hi) x 4 real MAC per complex MAC = 24 flop per CMAC
         achieved = cmac_launch * 24 / (k_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         src = os.path.join(ROOT, "paper_2607_02236_gb300", "csrc", "k_tc_gemm.cu")
@@ -683,7 +840,8 @@ def main():
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": (tr * cmac_launch if tr else None),
                 "kernel": kname, "flop_per_cmac": 24,
-                "peak_source": f"{peak_src} bf16 sustained (MEASURED_PEAKS.json)",
+                "peak_source": f"{peak_src} bf16 sustained (MEASURED_PEAKS.json)" +
+                               (" x 1 (fp16 and bf16 have the same dense tensor rate)" if args.precision == "split_fp16" else ""),
                 "kernel_ms": k_ms, "launches_per_step": k_per_step}
     else:
         achieved = cmac_launch * 8 / (k_ms * 1e-3) / 1e12
@@ -710,12 +868,12 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "bf16" if args.precision == "split_bf16" else "f32",
+                "vs_baseline": None, "dtype": {"split_bf16": "bf16", "split_fp16": "f16"}.get(args.precision, "f32"),
                 "data": "synthetic",
                 "config": {"workload": name, "probes": P, "k_roi": f"{K}x{K}", "T": T, "frames_per_push": Tc,
                            "n_omega": Nw, "E_range_meV": [0, spec.E_max_meV], "window": spec.window,
                            "precision": args.precision + (" (hi*hi+hi*lo+lo*hi, fp32 accumulate, fp64 phase)"
-                                                          if args.precision == "split_bf16" else ""),
+                                                          if split else ""),
                            "k_stage": info["k_stage"], "omega_tile": info["omega_tile"],
                            "tc_accumulators": info["tc_accumulators"], "tc_block_frames": info["tc_block_frames"],
                            "tc_cluster": info["tc_cluster"], "tc_pair": info["tc_pair"], "tc_drain_frames": info["tc_drain_frames"],
@@ -726,7 +884,8 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "max_rel_err_I_vs_fp64": err, "error_sample": "24 (probe, pixel) series, all energies",
                 "spectra_per_s": spectra_per_s, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
-                "roofline": roof, "cpu_baseline": cpu, "fp32_path": fp32, "one_accumulator_mode": fast}
+                "roofline": roof, "cpu_baseline": cpu, "fp32_path": fp32, "split_fp16_path": fp16,
+                "one_accumulator_mode": fast}
         if phases:
             line["flush_phases"] = phases
         print(json.dumps(line), flush=True)

@@ -73,8 +73,16 @@ typedef enum {
  *   FP32        CUDA-core FFMA, FP32 accumulate.
  *   SPLIT_BF16  tcgen05 tensor cores: each operand x = hi + lo with hi, lo bf16; the
  *               product is hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory.
+ *   SPLIT_FP16  the same with fp16 pieces (11-bit significands: hi + lo carries 22 bits
+ *               against 16 for bf16).  fp16 has a narrow exponent range, so the frames'
+ *               residual psi - mu_hat is multiplied by tacaw_plan_desc.fp16_scale (a power
+ *               of two, undone exactly in the epilogue) before the split; the twiddles
+ *               (|w e^{-i theta}| <= 1) are split unscaled.  A scaled component beyond the
+ *               fp16 range (65504) is detected: finalize / tacaw_check_errors then return
+ *               TACAW_ERR_OVERFLOW and the plan is poisoned.  Staged operands only
+ *               (frames_in_place must be 0).
  * Twiddle phases are always reduced in FP64; the exact mean correction is FP64-derived. */
-typedef enum { TACAW_PREC_FP32 = 0, TACAW_PREC_SPLIT_BF16 = 1 } tacaw_precision;
+typedef enum { TACAW_PREC_FP32 = 0, TACAW_PREC_SPLIT_BF16 = 1, TACAW_PREC_SPLIT_FP16 = 2 } tacaw_precision;
 
 /* Accumulation of Psi across flushes (used only when a segment needs more than one
  * flush): compensated FP32 (sum + Kahan compensation), FP64, or plain FP32 (half the
@@ -203,6 +211,12 @@ typedef struct {
      * many CTAs, one per SM (0: every SM).  SMs left free run other work beside the
      * contraction, e.g. the conversions of another plan's segment pushed on another stream. */
     int tc_max_ctas;
+    /* TACAW_PREC_SPLIT_FP16 only: power of two multiplying psi - mu_hat before the fp16 split,
+     * in [2^-60, 2^60]; 0 selects 2^12, which suits exit waves of unit norm (|psi| <= 1, so
+     * |psi - mu_hat| <= 2 becomes <= 8192, eight times inside the fp16 range, while residual
+     * pieces of components down to ~1e-4 stay in fp16's normal range).  Scale data with
+     * larger components down (e.g. 2^12 / max|psi|).  Ignored by the other precisions.   */
+    double fp16_scale;
 } tacaw_plan_desc;
 
 typedef struct tacaw_plan_s *tacaw_plan_t;

@@ -49,13 +49,34 @@ __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 a, __nv_bfloat16 b
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-__device__ __forceinline__ void split2(float2 r, uint32_t &hi, uint32_t &lo) {
-    __nv_bfloat16 hr = __float2bfloat16_rn(r.x), hi_ = __float2bfloat16_rn(r.y);
-    __nv_bfloat16 lr = __float2bfloat16_rn(r.x - __bfloat162float(hr));
-    __nv_bfloat16 li = __float2bfloat16_rn(r.y - __bfloat162float(hi_));
-    hi = pack_bf16x2(hr, hi_);
-    lo = pack_bf16x2(lr, li);
+__device__ __forceinline__ uint32_t pack_f16x2(__half a, __half b) {
+    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
+
+// (re, im) -> hi = RN(re, im), lo = RN(residuals), packed pairs with re in the low half:
+// bf16 pieces, or on the split-FP16 path fp16 pieces of the scaled value sc * r (sc = 2^e;
+// amax tracks the largest scaled component for the range check).
+template <bool F16>
+__device__ __forceinline__ void split2(float2 r, float sc, float &amax, uint32_t &hi, uint32_t &lo) {
+    if (F16) {
+        const float qr = r.x * sc, qi = r.y * sc;
+        amax = fmaxf(amax, fmaxf(fabsf(qr), fabsf(qi)));
+        __half hr = __float2half_rn(qr), hi_ = __float2half_rn(qi);
+        __half lr = __float2half_rn(qr - __half2float(hr));
+        __half li = __float2half_rn(qi - __half2float(hi_));
+        hi = pack_f16x2(hr, hi_);
+        lo = pack_f16x2(lr, li);
+    } else {
+        __nv_bfloat16 hr = __float2bfloat16_rn(r.x), hi_ = __float2bfloat16_rn(r.y);
+        __nv_bfloat16 lr = __float2bfloat16_rn(r.x - __bfloat162float(hr));
+        __nv_bfloat16 li = __float2bfloat16_rn(r.y - __bfloat162float(hi_));
+        hi = pack_bf16x2(hr, hi_);
+        lo = pack_bf16x2(lr, li);
+    }
+}
+
+// largest finite fp16 value: a scaled component above it does not survive the split
+constexpr float kF16Max = 65504.f;
 
 // Pre-swizzled staging (swz != 0): the 16-byte chunks of row m are stored in the order the
 // tensor core's shared-memory swizzle of the row width expects (chunk c at c ^ sw(m), sw(m) =
@@ -71,8 +92,10 @@ __host__ __device__ __forceinline__ int swz_word(int w, int64_t m, int bf, int s
 
 // Staged frame slot s (s0 + t) goes to block s/bf, elements 2(s%bf), 2(s%bf)+1 of row m
 // (rows of 2*bf bf16 = 4*bf bytes; bf is 8, 16 or 32).
+template <bool F16>
 __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t M_pad, const float2 *mu_hat,
-                                     double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz) {
+                                     double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz,
+                                     float sc, uint32_t *err) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= g.M) return;
     const float2 *src = row_src(g, m);
@@ -80,6 +103,7 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t
     uint32_t *Hi = reinterpret_cast<uint32_t *>(A_hi);
     uint32_t *Lo = reinterpret_cast<uint32_t *>(A_lo);
     double sr = 0.0, si = 0.0;
+    float amax = 0.f;
     int t = 0;
     // leading frames up to the next block boundary
     while (t < n && ((s0 + t) & 7)) {
@@ -89,7 +113,7 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t
         sr += r.x;
         si += r.y;
         uint32_t h, l;
-        split2(r, h, l);
+        split2<F16>(r, sc, amax, h, l);
         size_t o = ((size_t)(s / bf) * M_pad + m) * bf + swz_word(s % bf, m, bf, swz);   // in bf16x2 units
         Hi[o] = h;
         Lo[o] = l;
@@ -107,7 +131,7 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t
             float2 r = make_float2(v[i].x - mu.x, v[i].y - mu.y);
             br += r.x;
             bi += r.y;
-            split2(r, h[i], l[i]);
+            split2<F16>(r, sc, amax, h[i], l[i]);
         }
         sr += br;
         si += bi;
@@ -127,7 +151,7 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t
         sr += r.x;
         si += r.y;
         uint32_t h, l;
-        split2(r, h, l);
+        split2<F16>(r, sc, amax, h, l);
         size_t o = ((size_t)(s / bf) * M_pad + m) * bf + swz_word(s % bf, m, bf, swz);
         Hi[o] = h;
         Lo[o] = l;
@@ -136,16 +160,18 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t
     a.x += sr;
     a.y += si;
     sum_res[m] = a;
+    if (F16 && amax > kF16Max) atomicOr(err, DEVERR_FP16_RANGE);
 }
 
 // Whole staging blocks (s0 and n multiples of bf): 128 rows per CTA.  Each thread converts
 // its row's bf frames into a shared tile (16-byte chunks XOR-swizzled by row to spread the
 // banks); the CTA then writes the 128 contiguous rows of the block with consecutive
 // threads on consecutive 16-byte chunks, so every warp store is one contiguous 512 bytes.
-template <int BF>
+template <int BF, bool F16>
 __global__ void __launch_bounds__(128) convert_split_tiled_kernel(FrameGeom g, int n, int s0, int64_t M_pad,
                                                                   const float2 *mu_hat, double2 *sum_res,
-                                                                  __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz) {
+                                                                  __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz,
+                                                                  float sc, uint32_t *err) {
     constexpr int bf = BF;
     constexpr int cpr = BF / 4;             // 16-byte chunks per row
     __shared__ uint4 tile_h[128 * cpr], tile_l[128 * cpr];
@@ -158,6 +184,7 @@ __global__ void __launch_bounds__(128) convert_split_tiled_kernel(FrameGeom g, i
     uint4 *Hi = reinterpret_cast<uint4 *>(A_hi);
     uint4 *Lo = reinterpret_cast<uint4 *>(A_lo);
     double sr = 0.0, si = 0.0;
+    float amax = 0.f;
     for (int t0 = 0; t0 < n; t0 += bf) {
         float2 v[BF];
 #pragma unroll
@@ -172,7 +199,7 @@ __global__ void __launch_bounds__(128) convert_split_tiled_kernel(FrameGeom g, i
                 float2 q = valid ? make_float2(v[4 * c + i].x - mu.x, v[4 * c + i].y - mu.y) : make_float2(0.f, 0.f);
                 br += q.x;
                 bi += q.y;
-                split2(q, h[i], l[i]);
+                split2<F16>(q, sc, amax, h[i], l[i]);
             }
             const int slot = r * cpr + (c ^ (r & (cpr - 1)));
             tile_h[slot] = make_uint4(h[0], h[1], h[2], h[3]);
@@ -198,6 +225,7 @@ __global__ void __launch_bounds__(128) convert_split_tiled_kernel(FrameGeom g, i
         a.y += si;
         sum_res[m] = a;
     }
+    if (F16 && amax > kF16Max) atomicOr(err, DEVERR_FP16_RANGE);
 }
 
 __global__ void convert_fp32_kernel(FrameGeom g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
@@ -248,11 +276,11 @@ __global__ void zero_tail_split_kernel(int64_t M_pad, int staged, int bf, uint32
     }
 }
 
-__global__ void mean_residual_kernel(int64_t M, int T, int sub, const double2 *sum_res, float2 *dmu) {
+__global__ void mean_residual_kernel(int64_t M, int T, int sub, const double2 *sum_res, float2 *dmu, double sc) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     double2 s = sum_res[m];
-    dmu[m] = sub ? make_float2((float)(s.x / T), (float)(s.y / T)) : make_float2(0.f, 0.f);
+    dmu[m] = sub ? make_float2((float)(sc * s.x / T), (float)(sc * s.y / T)) : make_float2(0.f, 0.f);
 }
 
 static inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -273,19 +301,30 @@ cudaError_t launch_mean(const FrameGeom &g, int n, float2 *mu_hat, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_convert_split(const FrameGeom &g, int n, int s0, int bf, int64_t M_pad, const float2 *mu_hat,
-                                 double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz,
-                                 cudaStream_t st) {
+template <bool F16>
+static cudaError_t convert_split(const FrameGeom &g, int n, int s0, int bf, int64_t M_pad, const float2 *mu_hat,
+                                 double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz, float sc,
+                                 uint32_t *err, cudaStream_t st) {
     if (bf >= 16 && s0 % bf == 0 && n % bf == 0) {
         const unsigned grid = (unsigned)(M_pad / 128);
         if (bf == 32)
-            convert_split_tiled_kernel<32><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo, swz);
+            convert_split_tiled_kernel<32, F16><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo,
+                                                                      swz, sc, err);
         else
-            convert_split_tiled_kernel<16><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo, swz);
+            convert_split_tiled_kernel<16, F16><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo,
+                                                                      swz, sc, err);
         return cudaGetLastError();
     }
-    convert_split_kernel<<<blocks_for(g.M, 256), 256, 0, st>>>(g, n, s0, bf, M_pad, mu_hat, sum_res, A_hi, A_lo, swz);
+    convert_split_kernel<F16><<<blocks_for(g.M, 256), 256, 0, st>>>(g, n, s0, bf, M_pad, mu_hat, sum_res, A_hi,
+                                                                    A_lo, swz, sc, err);
     return cudaGetLastError();
+}
+
+cudaError_t launch_convert_split(const FrameGeom &g, int n, int s0, int bf, int64_t M_pad, const float2 *mu_hat,
+                                 double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz, int f16,
+                                 float f16_scale, uint32_t *err, cudaStream_t st) {
+    if (f16) return convert_split<true>(g, n, s0, bf, M_pad, mu_hat, sum_res, A_hi, A_lo, swz, f16_scale, err, st);
+    return convert_split<false>(g, n, s0, bf, M_pad, mu_hat, sum_res, A_hi, A_lo, swz, 1.f, err, st);
 }
 
 cudaError_t launch_convert_fp32(const FrameGeom &g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
@@ -302,8 +341,8 @@ cudaError_t launch_zero_tail_split(int64_t M_pad, int staged, int bf, __nv_bfloa
 }
 
 cudaError_t launch_mean_residual(int64_t M, int T, int subtract_mean, const double2 *sum_res, float2 *dmu,
-                                 cudaStream_t st) {
-    mean_residual_kernel<<<blocks_for(M, 256), 256, 0, st>>>(M, T, subtract_mean, sum_res, dmu);
+                                 float scale, cudaStream_t st) {
+    mean_residual_kernel<<<blocks_for(M, 256), 256, 0, st>>>(M, T, subtract_mean, sum_res, dmu, (double)scale);
     return cudaGetLastError();
 }
 

@@ -80,11 +80,22 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
+// fp16 pieces (split-FP16 path), stored in the bf16-typed table as raw 16-bit patterns;
+// |B| <= 1, so no scaling: residuals below the fp16 normal range keep an absolute
+// resolution of 2^-24, far below the 2^-22 relative resolution of the largest twiddles
+__device__ __forceinline__ void split_f16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    const __half h = __float2half_rn(x);
+    const __half l = __float2half_rn(x - __half2float(h));
+    hi = __ushort_as_bfloat16(__half_as_ushort(h));
+    lo = __ushort_as_bfloat16(__half_as_ushort(l));
+}
+
 // One thread per (energy j < Nw_pad, frame t < T_pad).  Rows 2j and 2j+1 of block t/bf
 // (rows of 2*bf bf16) receive, at elements 2(t%bf) and 2(t%bf)+1, the real embedding of
 // B = w_t exp(-i theta):
 //   row 2j   : ( Re B, -Im B)  ->  Re Psi_j = Re psi Re B - Im psi Im B
 //   row 2j+1 : ( Im B,  Re B)  ->  Im Psi_j = Re psi Im B + Im psi Re B
+template <bool F16>
 __global__ void twiddles_split_kernel(TableArgs a, __nv_bfloat16 *B_hi, __nv_bfloat16 *B_lo) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     int t = blockIdx.y * blockDim.y + threadIdx.y;
@@ -112,10 +123,12 @@ __global__ void twiddles_split_kernel(TableArgs a, __nv_bfloat16 *B_hi, __nv_bfl
     float v1[2] = {(float)bi, (float)br};
     for (int e = 0; e < 2; ++e) {
         __nv_bfloat16 h, l;
-        split_bf16(v0[e], h, l);
+        if (F16) split_f16(v0[e], h, l);
+        else split_bf16(v0[e], h, l);
         B_hi[r0 + e] = h;
         B_lo[r0 + e] = l;
-        split_bf16(v1[e], h, l);
+        if (F16) split_f16(v1[e], h, l);
+        else split_bf16(v1[e], h, l);
         B_hi[r1 + e] = h;
         B_lo[r1 + e] = l;
     }
@@ -165,10 +178,14 @@ __global__ void window_values_kernel(TableArgs a, float *w) {
     if (t < a.T) w[t] = (float)window_value(a, t);
 }
 
-cudaError_t launch_twiddles_split(const TableArgs &t, __nv_bfloat16 *B_hi, __nv_bfloat16 *B_lo, cudaStream_t st) {
+cudaError_t launch_twiddles_split(const TableArgs &t, __nv_bfloat16 *B_hi, __nv_bfloat16 *B_lo, int f16,
+                                  cudaStream_t st) {
     dim3 blk(32, 8);
     dim3 grd((t.Nw_pad + 31) / 32, (t.T_pad + 7) / 8);
-    twiddles_split_kernel<<<grd, blk, 0, st>>>(t, B_hi, B_lo);
+    if (f16)
+        twiddles_split_kernel<true><<<grd, blk, 0, st>>>(t, B_hi, B_lo);
+    else
+        twiddles_split_kernel<false><<<grd, blk, 0, st>>>(t, B_hi, B_lo);
     return cudaGetLastError();
 }
 

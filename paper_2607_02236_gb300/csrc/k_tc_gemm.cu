@@ -346,6 +346,11 @@ __device__ __forceinline__ uint64_t sdesc_k(uint32_t saddr, uint32_t row_bytes) 
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// The same with A = B = F16 (format fields 0) when f16 is set: both operands always share
+// one type (the split-FP16 path stages fp16 pieces of A and of B alike).
+__host__ __device__ constexpr uint32_t idesc_f32acc(int M, int N, int f16) {
+    return f16 ? (idesc_bf16_f32(M, N) & ~((1u << 7) | (1u << 10))) : idesc_bf16_f32(M, N);
+}
 
 __host__ __device__ inline uint32_t tc_a_bytes(int bf) { return (uint32_t)kMTile * 4u * (uint32_t)bf; }
 __host__ __device__ inline uint32_t tc_b_bytes_padded(int N, int bf) {
@@ -444,8 +449,8 @@ __device__ __forceinline__ void tc_mma_loop(const TcPlanArgs &a, TcShared *sh, u
     const uint16_t cmask = (uint16_t)((1u << a.cluster) - 1u);
     const int n0 = a.N < 256 ? a.N : 256;
     const int n1 = a.N - n0;
-    const uint32_t id0 = idesc_bf16_f32(kMTile, n0);
-    const uint32_t id1 = n1 > 0 ? idesc_bf16_f32(kMTile, n1) : 0u;
+    const uint32_t id0 = idesc_f32acc(kMTile, n0, a.f16);
+    const uint32_t id1 = n1 > 0 ? idesc_f32acc(kMTile, n1, a.f16) : 0u;
     const uint64_t b_half_off = (uint64_t)((n0 * RB) >> 4);
     const uint32_t acc_small = tmem + (uint32_t)(a.n_big * a.N);
     const int ksteps = a.bf / 8;
@@ -756,8 +761,8 @@ __device__ __forceinline__ void flush_tc_body(const TcGroup &g) {
             const int n0 = a.N < 256 ? a.N : 256;
             const int n1 = a.N - n0;
             const int m_mma = PAIR ? 2 * kMTile : kMTile;
-            const uint32_t id0 = idesc_bf16_f32(m_mma, n0);
-            const uint32_t id1 = n1 > 0 ? idesc_bf16_f32(m_mma, n1) : 0u;
+            const uint32_t id0 = idesc_f32acc(m_mma, n0, a.f16);
+            const uint32_t id1 = n1 > 0 ? idesc_f32acc(m_mma, n1, a.f16) : 0u;
             const uint64_t b_half_off = (uint64_t)((n0 * RB) >> 4);
             const uint32_t acc_small = tmem + (uint32_t)(a.n_big * a.N);
             const int ksteps = a.bf / 8;
@@ -1046,7 +1051,7 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
                 const bool last_w = en.args.N_last > 0 &&
                                     wtile_of(t - en.cta_begin, en.args.n_wt, g.rot, tiles) == en.args.n_wt - 1;
                 const int N = last_w ? en.args.N_last : en.args.N, n_kb = en.args.n_kb, cb = en.args.drain_kb;
-                const uint32_t id = idesc_bf16_f32(kMTile, N);
+                const uint32_t id = idesc_f32acc(kMTile, N, en.args.f16);
                 if (tiles > 0) {
                     // the previous tile's H and S must be in registers before they are reused
                     if (!mbar_wait(smem_u32(&sh->chunk_free[1]), tph, abort_flag)) {
@@ -1126,7 +1131,7 @@ __device__ __forceinline__ void flush_tc_drain_body(const TcGroup &g) {
             for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x, ++tiles) {
                 const TcGroupEntry &en = g.e[group_entry(g, t)];
                 const int N = en.args.N, n_kb = en.args.n_kb, cb = en.args.drain_kb;   // form 1: full tiles
-                const uint32_t id = idesc_bf16_f32(kMTile, N);
+                const uint32_t id = idesc_f32acc(kMTile, N, en.args.f16);
                 int kc = 0;
                 for (int kb = 0; kb < n_kb; ++kb) {
                     if (kc == 0) {

@@ -216,6 +216,7 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
         a.e.Nw = sh.Nw;
         a.e.mode = FLUSH_FINAL;
         a.e.out_scale = 1.f;
+        a.e.psi_scale = 1.f;
         a.e.I_out = static_cast<float *>(iout.p);
         a.e.Wc = static_cast<const float2 *>(wc.p);
         a.e.bose = static_cast<const float *>(bose.p);

@@ -115,7 +115,10 @@ struct UserStream {
 struct tacaw_plan_s {
     std::vector<Stream> s;     // internal streams (Welch lanes expanded)
     std::vector<UserStream> us;
-    int prec = 0, accum = 0, k_stage = 0;
+    int prec = 0, accum = 0, k_stage = 0;   // prec: TACAW_PREC_SPLIT_BF16 for both split paths
+    int prec_user = 0;         // the precision asked for (tacaw_plan_info)
+    int f16 = 0;               // split path with fp16 pieces of the scaled operands
+    float f16_scale = 1.f;     // split FP16: operand A is f16_scale * (psi - mu_hat), a power of two
     int stages = 0;
     int tc_acc = 3;
     int drain_kb = 0;          // drained form: staging blocks per accumulator chunk (0: off)
@@ -297,7 +300,10 @@ EpiArgs epi_args(tacaw_plan_s *p, const Stream &s, int mode, float *I_out, float
     e.bose = s.bose;
     e.I_out = I_out;
     e.Psi_out = Psi_out;
-    e.out_scale = s.out_scale;
+    // split FP16: the accumulators hold f16_scale * Psi (powers of two: exact rescaling)
+    const float inv = 1.f / p->f16_scale;
+    e.out_scale = p->f16 ? s.out_scale * inv * inv : s.out_scale;
+    e.psi_scale = p->f16 ? inv : 1.f;
     e.out_add = s.out_add;
     return e;
 }
@@ -334,6 +340,7 @@ TcPlanArgs tc_args(tacaw_plan_s *p, const Stream &s, const EpiArgs &e) {
     a.pair = p->in_place ? 0 : s.tc_pair;
     a.prefetch = p->in_place ? 0 : p->tc_prefetch;
     a.max_ctas = p->tc_max_ctas;
+    a.f16 = p->f16;
     a.err = p->d_err;
     a.trace = nullptr;
     return a;
@@ -604,7 +611,7 @@ tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
     if (p->prec == TACAW_PREC_SPLIT_BF16) {
         const size_t nb = (size_t)s.n_kb_T * 2 * s.Nw_pad * 2 * p->bf;
         if (!dev_alloc(p, &s.B_hi, nb) || !dev_alloc(p, &s.B_lo, nb)) return fail(TACAW_ERR_OOM, "cudaMalloc(B split)");
-        CU_CHECK(p, launch_twiddles_split(ta, s.B_hi, s.B_lo, st), "twiddles split");
+        CU_CHECK(p, launch_twiddles_split(ta, s.B_hi, s.B_lo, p->f16, st), "twiddles split");
         s.tc_maps.resize(tc_maps_size());
         char eb[256];
         if (p->in_place) {
@@ -714,6 +721,9 @@ tacaw_status read_device_error(tacaw_plan_s *p, cudaStream_t st) {
     CU_CHECK(p, cudaMemcpy(&h, p->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost), "read error word");
     if (h) {
         p->poisoned = true;
+        if (h == DEVERR_FP16_RANGE)
+            return fail(TACAW_ERR_OVERFLOW, "split FP16: a frame value times the operand scale %g exceeds the fp16 "
+                        "range (65504); create the plan with a smaller fp16_scale", (double)p->f16_scale);
         return fail(TACAW_ERR_TIMEOUT, "device wait timed out (error bits 0x%x)", h);
     }
     return TACAW_OK;
@@ -734,7 +744,8 @@ tacaw_status finalize_impl(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, 
     if (!p->in_place)
         for (auto &s : p->s) {
             if (p->us[s.user].N > 1) continue;
-            CU_CHECK(p, launch_mean_residual(s.M, s.T, s.d.subtract_mean, s.sum_res, s.dmu, st), "mean residual");
+            CU_CHECK(p, launch_mean_residual(s.M, s.T, s.d.subtract_mean, s.sum_res, s.dmu, p->f16_scale, st),
+                     "mean residual");
             p->launches++;
         }
     float2 *Psi_all = static_cast<float2 *>(d_Psi);
@@ -823,7 +834,7 @@ tacaw_status push_internal(tacaw_plan_s *p, Stream &s, const float2 *frames, int
         } else {
             if (p->prec == TACAW_PREC_SPLIT_BF16)
                 CU_CHECK(p, launch_convert_split(gc, chunk, s.staged, p->bf, s.M_pad, s.mu_hat, s.sum_res, s.A_hi,
-                                                 s.A_lo, p->drain_kb > 0, st),
+                                                 s.A_lo, p->drain_kb > 0, p->f16, p->f16_scale, p->d_err, st),
                          "convert");
             else
                 CU_CHECK(p, launch_convert_fp32(gc, chunk, s.staged, s.M_pad, s.mu_hat, s.sum_res, s.A32, st),
@@ -845,7 +856,8 @@ tacaw_status push_internal(tacaw_plan_s *p, Stream &s, const float2 *frames, int
 // and make the lane ready for its next segment.
 tacaw_status finish_segment(tacaw_plan_s *p, UserStream &u, Stream &s, cudaStream_t st) {
     if (!p->in_place) {
-        CU_CHECK(p, launch_mean_residual(s.M, s.T, s.d.subtract_mean, s.sum_res, s.dmu, st), "mean residual");
+        CU_CHECK(p, launch_mean_residual(s.M, s.T, s.d.subtract_mean, s.sum_res, s.dmu, p->f16_scale, st),
+                 "mean residual");
         p->launches++;
     }
     tacaw_status r = run_flush(p, s, FLUSH_FINAL, u.I_acc, nullptr, st);
@@ -869,8 +881,23 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     if (!desc || !out) return fail(TACAW_ERR_INVALID_ARG, "desc and out must not be NULL");
     *out = nullptr;
     if (desc->n_streams < 1 || !desc->streams) return fail(TACAW_ERR_INVALID_ARG, "n_streams must be >= 1");
-    if (desc->precision != TACAW_PREC_FP32 && desc->precision != TACAW_PREC_SPLIT_BF16)
+    if (desc->precision != TACAW_PREC_FP32 && desc->precision != TACAW_PREC_SPLIT_BF16 &&
+        desc->precision != TACAW_PREC_SPLIT_FP16)
         return fail(TACAW_ERR_INVALID_ARG, "bad precision");
+    // both split paths share the staged tensor-core machinery; they differ in the 16-bit type
+    // of the pieces (and the operand scale the fp16 range needs)
+    const bool f16 = desc->precision == TACAW_PREC_SPLIT_FP16;
+    const int prec = f16 ? (int)TACAW_PREC_SPLIT_BF16 : desc->precision;
+    double f16_scale = 1.0;
+    if (f16) {
+        f16_scale = desc->fp16_scale == 0.0 ? 4096.0 : desc->fp16_scale;
+        int ex = 0;
+        if (!(f16_scale > 0.0) || std::frexp(f16_scale, &ex) != 0.5 || ex - 1 < -60 || ex - 1 > 60)
+            return fail(TACAW_ERR_INVALID_ARG, "fp16_scale must be 0 or a power of two in [2^-60, 2^60]");
+        if (desc->frames_in_place)
+            return fail(TACAW_ERR_UNSUPPORTED, "frames_in_place converts frames to bf16 inside the contraction; "
+                        "the split-FP16 path stages its operands (frames_in_place 0)");
+    }
     if (desc->accum < TACAW_ACC_KAHAN_FP32 || desc->accum > TACAW_ACC_AUTO)
         return fail(TACAW_ERR_INVALID_ARG, "bad accum");
     if (desc->k_stage < 0 || (desc->k_stage % 8) != 0) return fail(TACAW_ERR_INVALID_ARG, "k_stage must be a multiple of 8");
@@ -893,7 +920,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     if (desc->tc_block_frames != 0 && desc->tc_block_frames != 8 && desc->tc_block_frames != 16 &&
         desc->tc_block_frames != 32)
         return fail(TACAW_ERR_INVALID_ARG, "tc_block_frames must be 0 (auto), 8, 16 or 32");
-    if (desc->precision == TACAW_PREC_SPLIT_BF16 && desc->tc_block_frames && desc->k_stage % desc->tc_block_frames)
+    if (prec == TACAW_PREC_SPLIT_BF16 && desc->tc_block_frames && desc->k_stage % desc->tc_block_frames)
         return fail(TACAW_ERR_INVALID_ARG, "k_stage must be a multiple of tc_block_frames");
     tacaw_plan_s *p = new (std::nothrow) tacaw_plan_s();
     if (!p) return fail(TACAW_ERR_OOM, "host allocation failed");
@@ -906,7 +933,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     // in-place frames: the persistent drained kernel reads each tile's 128 rows of every frame
     // with one contiguous copy, which needs (per stream) the rows of a tile contiguous in the
     // frame and 16-byte aligned copies; otherwise the register-fed in-place kernel runs
-    bool ip2 = desc->frames_in_place && desc->precision == TACAW_PREC_SPLIT_BF16 &&
+    bool ip2 = desc->frames_in_place && prec == TACAW_PREC_SPLIT_BF16 &&
                (desc->tc_accumulators == 0 || desc->tc_accumulators == 2) && !desc->tc_pair &&
                desc->tc_cluster <= 1 && (desc->tc_block_frames == 0 || desc->tc_block_frames == 32) &&
                desc->k_stage % 32 == 0;
@@ -921,7 +948,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         ip2 = even && rows_contiguous;
     }
     p->ip2 = ip2;
-    const bool drained = (drain_frames > 0 && desc->precision == TACAW_PREC_SPLIT_BF16 && !desc->frames_in_place) || ip2;
+    const bool drained = (drain_frames > 0 && prec == TACAW_PREC_SPLIT_BF16 && !desc->frames_in_place) || ip2;
     // drained forms: 1 = all products in one double-buffered accumulator, 2 = hi*hi drained, the
     // small products in a second accumulator
     if (drained) p->drain_form = (desc->tc_accumulators == 2 || auto_acc || ip2) ? 2 : 1;
@@ -930,12 +957,12 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     const int tile_acc = drained ? 2 : p->tc_acc;
     // widest tile: the drained forms' register sums; in place, also the raw frame ring
     const int tile_cap = ip2 ? kInplaceMaxOmegaTile : (drained ? kDrainMaxOmegaTile : 0);
-    if (desc->frames_in_place && desc->precision != TACAW_PREC_SPLIT_BF16) {
+    if (desc->frames_in_place && prec != TACAW_PREC_SPLIT_BF16) {
         delete p;
         return fail(TACAW_ERR_UNSUPPORTED, "frames_in_place needs the split-BF16 path");
     }
     p->in_place = desc->frames_in_place != 0;
-    if (desc->precision == TACAW_PREC_SPLIT_BF16) {
+    if (prec == TACAW_PREC_SPLIT_BF16) {
         // widest rows first: fewer, larger TMA requests per MMA K-step
         if (desc->tc_block_frames) {
             p->bf = desc->tc_block_frames;
@@ -944,7 +971,10 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
             while (p->bf > 8 && desc->k_stage % p->bf) p->bf /= 2;
         }
     }
-    p->prec = desc->precision;
+    p->prec = prec;
+    p->prec_user = desc->precision;
+    p->f16 = f16 ? 1 : 0;
+    p->f16_scale = (float)f16_scale;
     p->accum = desc->accum == TACAW_ACC_AUTO ? TACAW_ACC_KAHAN_FP32 : desc->accum;   // resolved with K_stage
     if (!dev_alloc(p, &p->d_err, 1) || cudaMemset(p->d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
@@ -1336,7 +1366,7 @@ tacaw_status tacaw_plan_get_info(tacaw_plan_t p, tacaw_plan_info *info) {
     info->device_bytes = p->bytes;
     info->k_stage = p->k_stage;
     info->n_streams = (int)p->us.size();
-    info->precision = p->prec;
+    info->precision = p->prec_user;
     info->I_elems = p->I_elems;
     info->S_elems = p->S_elems;
     info->flushes = p->flushes_total;

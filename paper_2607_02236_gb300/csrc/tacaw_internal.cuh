@@ -4,7 +4,8 @@
 // M_pad = M rounded up to 128; Nw_pad = n_wt * wt energies):
 //   staging, split path   A_hi, A_lo  bf16 [kb][M_pad][2*bf] kb = staged frame / bf (bf = 8, 16
 //                         or 32 frames per block: 32-, 64- or 128-byte rows);
-//                         element 2*(f%bf)+0 = Re(psi - mu_hat), +1 = Im(...)
+//                         element 2*(f%bf)+0 = Re(psi - mu_hat), +1 = Im(...); the split-FP16
+//                         path stores fp16 pieces of 2^e (psi - mu_hat) in the same layout
 //   staging, FP32 path    A32        float2 [K_stage][M_pad]
 //   twiddles, split path  B_hi, B_lo  bf16 [kbT][2*Nw_pad][2*bf] kbT = t / bf; rows 2j, 2j+1
 //                         hold the real embedding of w_t exp(-i theta_jt) so that
@@ -17,6 +18,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 namespace tacaw {
@@ -37,6 +39,7 @@ enum : uint32_t {
     DEVERR_TIMEOUT_EMPTY = 2u,
     DEVERR_TIMEOUT_TMEM = 4u,
     DEVERR_TIMEOUT_DRAIN = 8u,
+    DEVERR_FP16_RANGE = 16u,   // split-FP16 conversion: a scaled value beyond the fp16 range
 };
 
 struct FrameGeom {
@@ -65,6 +68,8 @@ struct EpiArgs {
     const float *bose;         // [Nw]
     float out_scale;           // FINAL: I = out_scale * B(E) |Psi|^2 (Welch: 1/N per segment)
     int out_add;               // FINAL: add into I_out instead of storing (Welch segments)
+    float psi_scale;           // FINAL: Psi_out = psi_scale * Psi (split FP16: the accumulators hold
+                               // 2^e Psi, dmu is 2^e (mu - mu_hat), out_scale carries 2^-2e)
 };
 
 struct RowCtx {
@@ -144,7 +149,7 @@ __device__ __forceinline__ void epi_element_wb(const EpiArgs &a, const RowCtx &r
         const float v = (pr * pr + pi * pi) * bj * a.out_scale;
         a.I_out[o] = a.out_add ? a.I_out[o] + v : v;
     }
-    if (a.Psi_out) a.Psi_out[o] = make_float2(pr, pi);
+    if (a.Psi_out) a.Psi_out[o] = make_float2(pr * a.psi_scale, pi * a.psi_scale);
 }
 
 __device__ __forceinline__ void epi_element(const EpiArgs &a, const RowCtx &r, int j, float re, float im) {
@@ -215,7 +220,7 @@ __device__ __forceinline__ void epi_apply(const EpiArgs &a, const RowCtx &r, int
             const float v = (pr * pr + pi * pi) * bj * a.out_scale;
             a.I_out[o] = a.out_add ? a.I_out[o] + v : v;
         }
-        if (a.Psi_out) a.Psi_out[o] = make_float2(pr, pi);
+        if (a.Psi_out) a.Psi_out[o] = make_float2(pr * a.psi_scale, pi * a.psi_scale);
     }
 }
 
@@ -233,22 +238,27 @@ struct TableArgs {
     const double *win_table;   // table-driven windows (Dolph-Chebyshev): w_t, t < T
 };
 
-cudaError_t launch_twiddles_split(const TableArgs &t, __nv_bfloat16 *B_hi, __nv_bfloat16 *B_lo, cudaStream_t st);
+// f16 != 0: fp16 hi/lo pieces (the split-FP16 path) instead of bf16, same layout
+cudaError_t launch_twiddles_split(const TableArgs &t, __nv_bfloat16 *B_hi, __nv_bfloat16 *B_lo, int f16,
+                                  cudaStream_t st);
 cudaError_t launch_twiddles_fp32(const TableArgs &t, float2 *B32, cudaStream_t st);
 cudaError_t launch_window_transform(const TableArgs &t, float2 *Wc, cudaStream_t st);
 cudaError_t launch_window_values(const TableArgs &t, float *w, cudaStream_t st);
 
 cudaError_t launch_mean(const FrameGeom &g, int n, float2 *mu_hat, cudaStream_t st);
+// f16 != 0: fp16 hi/lo pieces of f16_scale * (psi - mu_hat); a scaled component beyond the
+// fp16 range sets DEVERR_FP16_RANGE in *err
 cudaError_t launch_convert_split(const FrameGeom &g, int n, int s0, int bf, int64_t M_pad, const float2 *mu_hat,
-                                 double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz,
-                                 cudaStream_t st);
+                                 double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz, int f16,
+                                 float f16_scale, uint32_t *err, cudaStream_t st);
 cudaError_t launch_convert_fp32(const FrameGeom &g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
                                 double2 *sum_res, float2 *A32, cudaStream_t st);
 cudaError_t launch_frame_table(const float2 **table, const float2 *base, int64_t pitch_frame, int n, cudaStream_t st);
 cudaError_t launch_zero_tail_split(int64_t M_pad, int staged, int bf, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo,
                                    int swz, cudaStream_t st);
+// dmu = scale * (mu - mu_hat) (scale: the split-FP16 operand scale, else 1)
 cudaError_t launch_mean_residual(int64_t M, int T, int subtract_mean, const double2 *sum_res, float2 *dmu,
-                                 cudaStream_t st);
+                                 float scale, cudaStream_t st);
 
 struct SimtArgs {
     EpiArgs e;
@@ -284,6 +294,7 @@ struct TcPlanArgs {
     int prefetch;              // staging blocks of A prefetched into L2 ahead of the current one (0: off)
     int max_ctas;              // persistent grids: at most this many CTAs (0: one per SM)
     int N_last;                // split drained form: columns of the last energy tile (<= N, multiple of 16)
+    int f16;                   // operands are fp16 pieces (split-FP16 path) instead of bf16
     unsigned long long *trace; // null, or kTraceWords globaltimer stamps per CTA (phase boundaries)
     uint32_t *err;
 };

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libtacaw.so")
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_OVERFLOW, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = ["OK", "INVALID_ARG", "OOM", "CUDA", "STATE", "OVERFLOW", "TIMEOUT", "UNSUPPORTED"]
 WINDOWS = {"rect": 0, "hann": 1, "gauss": 2, "tukey": 3, "blackmanharris": 4, "kaiser": 5, "chebwin": 6}
-PRECISIONS = {"fp32": 0, "split_bf16": 1}
+PRECISIONS = {"fp32": 0, "split_bf16": 1, "split_fp16": 2}
 ACCUMS = {"kahan": 0, "fp64": 1, "fp32": 2, "auto": 3}
 DET_KINDS = {"circular": 0, "annular": 1, "mask": 2}
 
@@ -59,7 +59,7 @@ class CPlanDesc(ctypes.Structure):
                 ("tune_cache_path", c_char_p), ("tc_omega_tile", c_int), ("tc_accumulators", c_int),
                 ("tc_cluster", c_int), ("tc_block_frames", c_int), ("tc_prefetch", c_int),
                 ("frames_in_place", c_int), ("tc_pair", c_int), ("tc_drain_frames", c_int),
-                ("tc_max_ctas", c_int)]
+                ("tc_max_ctas", c_int), ("fp16_scale", c_double)]
 
 
 class CPlanInfo(ctypes.Structure):
@@ -174,9 +174,10 @@ class TacawPlan:
                  hbm_budget_bytes: int = 0, k_stage: int = 0, tc_omega_tile: int = 0,
                  tc_accumulators: int = 0, tc_cluster: int = 0, tc_block_frames: int = 0, tc_prefetch: int = 0,
                  frames_in_place: bool = False, tune: Optional[str] = None, tc_pair: int = 0,
-                 tc_drain_frames: int = 0, tc_max_ctas: int = 0):
+                 tc_drain_frames: int = 0, tc_max_ctas: int = 0, fp16_scale: float = 0.0):
         """tune: None uses the built-in tile rule; "" autotunes at creation; a file path
-        autotunes through a text cache at that path."""
+        autotunes through a text cache at that path.  fp16_scale: operand scale of the
+        split_fp16 precision (a power of two; 0 selects 2^12)."""
         L = lib()
         self._keep = []
         descs = (CStreamDesc * len(streams))()
@@ -209,7 +210,7 @@ class TacawPlan:
                        None if tune is None else os.fsencode(tune), int(tc_omega_tile),
                        int(tc_accumulators), int(tc_cluster), int(tc_block_frames), int(tc_prefetch),
                        int(bool(frames_in_place)), int(tc_pair),
-                       int(tc_drain_frames), int(tc_max_ctas))
+                       int(tc_drain_frames), int(tc_max_ctas), float(fp16_scale))
         h = c_void_p()
         _check(L.tacaw_plan_create(ctypes.byref(pd), ctypes.byref(h)))
         self._h = h

@@ -70,3 +70,17 @@ def test_null_plan_calls_are_errors(L):
     assert L.tacaw_push_frames(None, 0, None, 1, None) == t.ERR_INVALID_ARG
     assert L.tacaw_finalize(None, None, None, None, None) == t.ERR_INVALID_ARG
     assert L.tacaw_destroy(None) == t.OK
+
+
+def test_split_fp16_options_rejected_without_device_work(L):
+    import paper_2607_02236_gb300.tacaw as t
+    cfg = t.StreamConfig(n_probes=2, kx=8, ky=8, T=16, dt_fs=5.0, pitch_row=8, pitch_frame=128, pitch_probe=64,
+                         fft_bins=8)
+    for bad in (3.0, -4.0, 2.0 ** 61, float("nan")):
+        with pytest.raises(t.TacawError) as ei:
+            t.TacawPlan([cfg], precision="split_fp16", fp16_scale=bad)
+        assert ei.value.status == t.ERR_INVALID_ARG, bad
+        assert "power of two" in L.tacaw_last_error().decode()
+    with pytest.raises(t.TacawError) as ei:
+        t.TacawPlan([cfg], precision="split_fp16", frames_in_place=True)
+    assert ei.value.status == t.ERR_UNSUPPORTED
