@@ -537,7 +537,7 @@ def diff_arm(args):
                              "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"},
                 "adjoint": {"ms": adj_ms, "cmac": cmac_adj, "achieved": adj_tflops, "peak": ffma_peak,
                             "unit": "TFLOP/s", "frac": adj_tflops / ffma_peak, "bound": "alu",
-                            "kernels": "zero_roi_kernel, adj_forward_kernel, adj_backward_kernel",
+                            "kernels": "zero_roi_kernel, adj_psi_kernel, adj_grad_kernel",
                             "timed": "CUDA events around the tacaw_backward call (median per step; includes "
                                      "its closing wait for the device error word)"}}
         print(json.dumps(line), flush=True)

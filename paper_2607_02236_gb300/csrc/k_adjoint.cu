@@ -8,210 +8,254 @@
 // A Welch-averaged stream (S = (1/N) sum_n S_n, Sec. II.B) runs this per segment with
 // scale 1/N, adding into the gradient of the frames the segments share.
 // Only pixels inside an aperture have G != 0, so both contractions run over that compact
-// pixel list; Psi is recomputed from the frames (the window and twiddles come from the
-// plan's table), never stored between forward and backward.
+// pixel list: rows m = p * n_mpix + i (probe p, aperture pixel i).  Psi is recomputed from
+// the frames (the window and twiddles come from the plan's table), never stored between
+// forward and backward.
+//
+// Both contractions are complex GEMMs tiled for the CUDA cores: a 256-thread block owns a
+// 64-row x 64-column tile, each thread a 4 x 4 tile of complex accumulators (rows tx + 16a,
+// columns ty + 16b), with 16-deep slices of both operands staged in shared memory by
+// coalesced loads.
+//   forward  Psi'[m][j] = sum_t (psi[t,m] - psi[0,m]) B[t][j]      (K = T, N = Nw)
+//            Psi = Psi' - (mu - psi_0) W_j  (the first frame as provisional mean keeps the
+//            elastic part out of the FP32 sums; the row sums ride along in the tile loads);
+//            G is written transposed, Gt[j][m], for the backward's coalesced loads
+//   backward C[m][t] = sum_j Gt[j][m] conj(B[t][j])                 (K = Nw, N = T)
+//            with K[m] = (1/T) sum_j conj(W_j) Gt[j][m] summed by the same tile loads
 #include "tacaw_internal.cuh"
 
 namespace tacaw {
 
-constexpr int ADJ_PIX = 8;    // pixels per block
-constexpr int ADJ_TCH = 64;   // frames staged per step
+constexpr int ADJ_TM = 64;     // rows per block tile
+constexpr int ADJ_TN = 64;     // columns (energies or frames) per block tile
+constexpr int ADJ_TK = 16;     // contraction depth per staged slice
 
-__device__ __forceinline__ const float2 *adj_src(const AdjointArgs &a, int p, int pix) {
+// complex64 offset of row m's pixel in frame 0 of the pushed layout
+__device__ __forceinline__ int64_t adj_row_offset(const AdjointArgs &a, int64_t m) {
+    const int p = (int)(m / a.n_mpix);
+    const int pix = a.mpix[m - (int64_t)p * a.n_mpix];
     const int y = pix / a.kx, x = pix - (pix / a.kx) * a.kx;
-    return a.frames + (int64_t)p * a.pitch_probe + (int64_t)(a.roi_y0 + y) * a.pitch_row + (a.roi_x0 + x);
+    return (int64_t)p * a.pitch_probe + (int64_t)(a.roi_y0 + y) * a.pitch_row + (a.roi_x0 + x);
 }
 
-// block (pixel group, probe): mean, Psi over all energies, G, and the constant K
-__global__ void __launch_bounds__(256) adj_forward_kernel(AdjointArgs a) {
-    const int g0 = blockIdx.x * ADJ_PIX;
-    const int p = blockIdx.y;
-    const int npx = min(ADJ_PIX, a.n_mpix - g0);
-    __shared__ float2 xs[ADJ_TCH][ADJ_PIX];
-    __shared__ float2 mu[ADJ_PIX];
-    __shared__ float2 red[ADJ_PIX][8];
-    const int tid = threadIdx.x;
-    // exact mean of each pixel's series
-    if (tid < 32 * ADJ_PIX) {
-        const int i = tid >> 5, lane = tid & 31;
-        float sr = 0.f, si = 0.f;
-        if (i < npx && a.subtract_mean) {
-            const float2 *src = adj_src(a, p, a.mpix[g0 + i]);
-            for (int t = lane; t < a.T; t += 32) {
-                float2 v = src[(int64_t)t * a.pitch_frame];
+__device__ __forceinline__ void cmac(float2 &acc, float2 x, float2 b) {
+    acc.x = fmaf(x.x, b.x, fmaf(-x.y, b.y, acc.x));
+    acc.y = fmaf(x.x, b.y, fmaf(x.y, b.x, acc.y));
+}
+
+// One 16-deep step of the 4 x 4 complex register tile.
+__device__ __forceinline__ void tile_step(const float2 (*As)[ADJ_TM], const float2 (*Bs)[ADJ_TN + 1], int tx, int ty,
+                                          float2 (&acc)[4][4]) {
+#pragma unroll
+    for (int kk = 0; kk < ADJ_TK; ++kk) {
+        float2 x[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = As[kk][tx + 16 * i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] = Bs[kk][ty + 16 * i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) cmac(acc[i][jj], x[i], b[jj]);
+    }
+}
+
+// grid (row tiles, energy tiles): G^T[j][m] for all aperture rows
+__global__ void __launch_bounds__(256) adj_psi_kernel(AdjointArgs a) {
+    __shared__ float2 As[ADJ_TK][ADJ_TM];
+    __shared__ float2 Bs[ADJ_TK][ADJ_TN + 1];
+    __shared__ float2 rsum[4][ADJ_TM];
+    __shared__ float2 ref[ADJ_TM];
+    __shared__ int64_t roff[ADJ_TM];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t M = (int64_t)a.P * a.n_mpix;
+    const int64_t m0 = (int64_t)blockIdx.x * ADJ_TM;
+    const int n0 = blockIdx.y * ADJ_TN;
+    // this thread's load slot: row lr of every slice, frames lk and lk + 4, 8, 12
+    const int lr = tid & (ADJ_TM - 1), lk = tid >> 6;
+    if (tid < ADJ_TM) {
+        const int64_t m = m0 + tid;
+        float2 v = make_float2(0.f, 0.f);
+        int64_t o = 0;
+        if (m < M) {
+            o = adj_row_offset(a, m);
+            if (a.subtract_mean) v = a.frames[o];      // provisional mean: the first frame
+        }
+        roff[tid] = o;
+        ref[tid] = v;
+    }
+    __syncthreads();
+    const bool row_ok = m0 + lr < M;
+    const int64_t my_off = roff[lr];
+    const float2 my_ref = ref[lr];
+    float sr = 0.f, si = 0.f;
+    float2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = make_float2(0.f, 0.f);
+    for (int t0 = 0; t0 < a.T; t0 += ADJ_TK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int kk = lk + 4 * q, t = t0 + kk;
+            float2 v = make_float2(0.f, 0.f);
+            if (row_ok && t < a.T) {
+                v = a.frames[my_off + (int64_t)t * a.pitch_frame];
+                v.x -= my_ref.x;
+                v.y -= my_ref.y;
                 sr += v.x;
                 si += v.y;
             }
+            As[kk][lr] = v;
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sr += __shfl_xor_sync(0xffffffffu, sr, o);
-            si += __shfl_xor_sync(0xffffffffu, si, o);
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q, kk = e >> 6, nn = e & 63, t = t0 + kk, j = n0 + nn;
+            Bs[kk][nn] = (t < a.T && j < a.Nw) ? a.B32[(size_t)t * a.Nw_pad + j] : make_float2(0.f, 0.f);
         }
-        if (lane == 0) mu[i] = make_float2(sr / a.T, si / a.T);
+        __syncthreads();
+        tile_step(As, Bs, tx, ty, acc);
+        __syncthreads();
     }
+    rsum[lk][lr] = make_float2(sr, si);
     __syncthreads();
-    float2 *G = a.scratch;                                   // [P][n_mpix][Nw]
-    float2 *Kc = a.scratch + (size_t)a.P * a.n_mpix * a.Nw;  // [P][n_mpix]
-    float kr[ADJ_PIX], ki[ADJ_PIX];
+    float2 *Gt = a.scratch;                                   // [Nw][M]
 #pragma unroll
-    for (int i = 0; i < ADJ_PIX; ++i) kr[i] = ki[i] = 0.f;
-    for (int jb = 0; jb < a.Nw; jb += 256) {
-        const int j = jb + tid;
-        float pr[ADJ_PIX], pi[ADJ_PIX];
-#pragma unroll
-        for (int i = 0; i < ADJ_PIX; ++i) pr[i] = pi[i] = 0.f;
-        for (int t0 = 0; t0 < a.T; t0 += ADJ_TCH) {
-            __syncthreads();
-            for (int e = tid; e < ADJ_TCH * ADJ_PIX; e += 256) {
-                const int tt = e / ADJ_PIX, i = e % ADJ_PIX;
-                float2 v = make_float2(0.f, 0.f);
-                if (i < npx && t0 + tt < a.T) {
-                    v = adj_src(a, p, a.mpix[g0 + i])[(int64_t)(t0 + tt) * a.pitch_frame];
-                    v.x -= mu[i].x;
-                    v.y -= mu[i].y;
-                }
-                xs[tt][i] = v;
-            }
-            __syncthreads();
-            if (j < a.Nw) {
-                const int tn = min(ADJ_TCH, a.T - t0);
-                for (int tt = 0; tt < tn; ++tt) {
-                    const float2 b = a.B32[(size_t)(t0 + tt) * a.Nw_pad + j];
-#pragma unroll
-                    for (int i = 0; i < ADJ_PIX; ++i) {
-                        const float2 x = xs[tt][i];
-                        pr[i] = fmaf(x.x, b.x, fmaf(-x.y, b.y, pr[i]));
-                        pi[i] = fmaf(x.x, b.y, fmaf(x.y, b.x, pi[i]));
-                    }
-                }
-            }
+    for (int i = 0; i < 4; ++i) {
+        const int r = tx + 16 * i;
+        const int64_t m = m0 + r;
+        if (m >= M) continue;
+        // Psi = Psi' - (mu - psi_0) W  (subtract_mean), else Psi' itself (psi_0 = 0)
+        float2 dmu = make_float2(0.f, 0.f);
+        if (a.subtract_mean) {
+            const float xr = ((rsum[0][r].x + rsum[1][r].x) + rsum[2][r].x) + rsum[3][r].x;
+            const float xi = ((rsum[0][r].y + rsum[1][r].y) + rsum[2][r].y) + rsum[3][r].y;
+            dmu = make_float2(xr / a.T, xi / a.T);
         }
-        if (j < a.Nw) {
+        const int p = (int)(m / a.n_mpix);
+        const int64_t ip = m - (int64_t)p * a.n_mpix;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int j = n0 + ty + 16 * jj;
+            if (j >= a.Nw) continue;
             const float2 W = a.Wc[j];
-            const float bj = a.bose[j];
+            float c = 0.f;
+            for (int d = 0; d < a.D; ++d) c += a.dLdS[((size_t)p * a.D + d) * a.Nw + j] * a.mwts[ip * a.D + d];
+            c *= a.bose[j];
+            const float pr = acc[i][jj].x - (dmu.x * W.x - dmu.y * W.y);
+            const float pi = acc[i][jj].y - (dmu.x * W.y + dmu.y * W.x);
+            Gt[(size_t)j * M + m] = make_float2(c * pr, c * pi);
+        }
+    }
+}
+
+// grid (row tiles, frame tiles): C[m][t] = sum_j Gt[j][m] conj(B[t][j]); grad = 2 scale (C - K)
+__global__ void __launch_bounds__(256) adj_grad_kernel(AdjointArgs a) {
+    __shared__ float2 As[ADJ_TK][ADJ_TM];
+    __shared__ float2 Bs[ADJ_TK][ADJ_TN + 1];
+    __shared__ float2 ksum[4][ADJ_TM];
+    __shared__ int64_t roff[ADJ_TM];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t M = (int64_t)a.P * a.n_mpix;
+    const int64_t m0 = (int64_t)blockIdx.x * ADJ_TM;
+    const int tb0 = blockIdx.y * ADJ_TN;
+    const int lr = tid & (ADJ_TM - 1), lk = tid >> 6;
+    if (tid < ADJ_TM) roff[tid] = (m0 + tid < M) ? adj_row_offset(a, m0 + tid) : 0;
+    const float2 *Gt = a.scratch;
+    const bool row_ok = m0 + lr < M;
+    float kr = 0.f, ki = 0.f;
+    float2 acc[4][4];
 #pragma unroll
-            for (int i = 0; i < ADJ_PIX; ++i) {
-                if (i >= npx) break;
-                float c = 0.f;
-                for (int d = 0; d < a.D; ++d)
-                    c += a.dLdS[((size_t)p * a.D + d) * a.Nw + j] * a.mwts[(size_t)(g0 + i) * a.D + d];
-                c *= bj;
-                const float gr = c * pr[i], gi = c * pi[i];
-                G[((size_t)p * a.n_mpix + g0 + i) * a.Nw + j] = make_float2(gr, gi);
-                // conj(W) G
-                kr[i] += W.x * gr + W.y * gi;
-                ki[i] += W.x * gi - W.y * gr;
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = make_float2(0.f, 0.f);
+    for (int j0 = 0; j0 < a.Nw; j0 += ADJ_TK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int kk = lk + 4 * q, j = j0 + kk;
+            float2 g = make_float2(0.f, 0.f);
+            if (row_ok && j < a.Nw) {
+                g = Gt[(size_t)j * M + m0 + lr];
+                const float2 W = a.Wc[j];
+                kr += W.x * g.x + W.y * g.y;               // conj(W) G
+                ki += W.x * g.y - W.y * g.x;
             }
+            As[kk][lr] = g;
         }
-    }
-    // block reduction of K over energies: warp shuffles, then fixed-order sum of 8 warps
-    const int lane = tid & 31, warp = tid >> 5;
+        // conj(B[t][j]) for 64 frames x 16 energies: 16 consecutive energies of a frame per
+        // 16 threads (128-byte rows of the table)
 #pragma unroll
-    for (int i = 0; i < ADJ_PIX; ++i) {
-        float vr = kr[i], vi = ki[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            vr += __shfl_xor_sync(0xffffffffu, vr, o);
-            vi += __shfl_xor_sync(0xffffffffu, vi, o);
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q, kk = e & 15, nn = e >> 4, t = tb0 + nn, j = j0 + kk;
+            float2 b = make_float2(0.f, 0.f);
+            if (t < a.T && j < a.Nw) {
+                b = a.B32[(size_t)t * a.Nw_pad + j];
+                b.y = -b.y;
+            }
+            Bs[kk][nn] = b;
         }
-        if (lane == 0) red[i][warp] = make_float2(vr, vi);
+        __syncthreads();
+        tile_step(As, Bs, tx, ty, acc);
+        __syncthreads();
     }
+    ksum[lk][lr] = make_float2(kr, ki);
     __syncthreads();
-    if (tid < npx) {
-        float sr = 0.f, si = 0.f;
-        for (int w = 0; w < 8; ++w) {
-            sr += red[tid][w].x;
-            si += red[tid][w].y;
-        }
-        Kc[(size_t)p * a.n_mpix + g0 + tid] =
-            a.subtract_mean ? make_float2(sr / a.T, si / a.T) : make_float2(0.f, 0.f);
-    }
-}
-
-// block (pixel group, probe): C_t = sum_j G_j conj(B[t][j]) for every frame; grad = 2 (C - K)
-__global__ void __launch_bounds__(256) adj_backward_kernel(AdjointArgs a) {
-    const int g0 = blockIdx.x * ADJ_PIX;
-    const int p = blockIdx.y;
-    const int npx = min(ADJ_PIX, a.n_mpix - g0);
-    constexpr int JCH = 128;
-    __shared__ float2 gs[JCH][ADJ_PIX];
-    const float2 *G = a.scratch;
-    const float2 *Kc = a.scratch + (size_t)a.P * a.n_mpix * a.Nw;
-    const int tid = threadIdx.x;
-    for (int tb = 0; tb < a.T; tb += 256) {
-        const int t = tb + tid;
-        float cr[ADJ_PIX], ci[ADJ_PIX];
+    const float s2 = 2.f * a.scale;
 #pragma unroll
-        for (int i = 0; i < ADJ_PIX; ++i) cr[i] = ci[i] = 0.f;
-        for (int j0 = 0; j0 < a.Nw; j0 += JCH) {
-            __syncthreads();
-            for (int e = tid; e < JCH * ADJ_PIX; e += 256) {
-                const int jj = e / ADJ_PIX, i = e % ADJ_PIX;
-                float2 v = make_float2(0.f, 0.f);
-                if (i < npx && j0 + jj < a.Nw) v = G[((size_t)p * a.n_mpix + g0 + i) * a.Nw + j0 + jj];
-                gs[jj][i] = v;
-            }
-            __syncthreads();
-            if (t < a.T) {
-                const int jn = min(JCH, a.Nw - j0);
-                for (int jj = 0; jj < jn; ++jj) {
-                    const float2 b = a.B32[(size_t)t * a.Nw_pad + j0 + jj];   // w_t e^{-i theta}
-#pragma unroll
-                    for (int i = 0; i < ADJ_PIX; ++i) {
-                        const float2 g = gs[jj][i];
-                        // g * conj(b)
-                        cr[i] = fmaf(g.x, b.x, fmaf(g.y, b.y, cr[i]));
-                        ci[i] = fmaf(g.y, b.x, fmaf(-g.x, b.y, ci[i]));
-                    }
-                }
-            }
+    for (int i = 0; i < 4; ++i) {
+        const int r = tx + 16 * i;
+        if (m0 + r >= M) continue;
+        float2 K = make_float2(0.f, 0.f);
+        if (a.subtract_mean) {
+            K.x = (((ksum[0][r].x + ksum[1][r].x) + ksum[2][r].x) + ksum[3][r].x) / a.T;
+            K.y = (((ksum[0][r].y + ksum[1][r].y) + ksum[2][r].y) + ksum[3][r].y) / a.T;
         }
-        if (t < a.T) {
-            for (int i = 0; i < npx; ++i) {
-                const int pix = a.mpix[g0 + i];
-                const int y = pix / a.kx, x = pix - (pix / a.kx) * a.kx;
-                const float2 K = Kc[(size_t)p * a.n_mpix + g0 + i];
-                float2 *gp = a.grad + (int64_t)p * a.pitch_probe + (int64_t)t * a.pitch_frame +
-                             (int64_t)(a.roi_y0 + y) * a.pitch_row + (a.roi_x0 + x);
-                const float2 v = make_float2(2.f * a.scale * (cr[i] - K.x), 2.f * a.scale * (ci[i] - K.y));
-                if (a.accumulate) {
-                    const float2 o = *gp;
-                    *gp = make_float2(o.x + v.x, o.y + v.y);
-                } else {
-                    *gp = v;
-                }
+        const int64_t o = roff[r];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int t = tb0 + ty + 16 * jj;
+            if (t >= a.T) continue;
+            float2 *gp = a.grad + o + (int64_t)t * a.pitch_frame;
+            const float2 v = make_float2(s2 * (acc[i][jj].x - K.x), s2 * (acc[i][jj].y - K.y));
+            if (a.accumulate) {
+                const float2 old = *gp;
+                *gp = make_float2(old.x + v.x, old.y + v.y);
+            } else {
+                *gp = v;
             }
         }
     }
 }
 
-// zero every ROI element of the gradient (layout of the frames)
-__global__ void zero_roi_kernel(AdjointArgs a) {
-    const int64_t npix = (int64_t)a.kx * a.ky;
-    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= (int64_t)a.P * a.T * npix) return;
-    const int64_t pix = id % npix;
-    const int64_t pt = id / npix;
+// zero every ROI element of the gradient (layout of the frames): one warp per frame row
+// (p, t, y) of the ROI, consecutive lanes on consecutive pixels
+__global__ void __launch_bounds__(256) zero_roi_kernel(AdjointArgs a, int64_t rows) {
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    const int y = (int)(r % a.ky);
+    const int64_t pt = r / a.ky;
     const int t = (int)(pt % a.T), p = (int)(pt / a.T);
-    const int64_t y = pix / a.kx, x = pix - (pix / a.kx) * a.kx;
-    a.grad[(int64_t)p * a.pitch_probe + (int64_t)t * a.pitch_frame + (a.roi_y0 + y) * a.pitch_row + (a.roi_x0 + x)] =
-        make_float2(0.f, 0.f);
+    float2 *row = a.grad + (int64_t)p * a.pitch_probe + (int64_t)t * a.pitch_frame +
+                  (int64_t)(a.roi_y0 + y) * a.pitch_row + a.roi_x0;
+    for (int x = threadIdx.x & 31; x < a.kx; x += 32) row[x] = make_float2(0.f, 0.f);
 }
 
 cudaError_t launch_zero_roi(const AdjointArgs &a, cudaStream_t st) {
-    const int64_t n = (int64_t)a.P * a.T * a.kx * a.ky;
-    zero_roi_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
+    const int64_t rows = (int64_t)a.P * a.T * a.ky;
+    if (rows == 0) return cudaSuccess;
+    zero_roi_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(a, rows);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t st) {
-    if (a.n_mpix == 0 || a.P == 0) return cudaSuccess;
-    dim3 grd((a.n_mpix + ADJ_PIX - 1) / ADJ_PIX, a.P);
-    adj_forward_kernel<<<grd, 256, 0, st>>>(a);
+    const int64_t M = (int64_t)a.P * a.n_mpix;
+    if (M == 0 || a.T == 0) return cudaSuccess;
+    const unsigned mt = (unsigned)((M + ADJ_TM - 1) / ADJ_TM);
+    if ((a.T + ADJ_TN - 1) / ADJ_TN > 65535 || (a.Nw + ADJ_TN - 1) / ADJ_TN > 65535) return cudaErrorInvalidValue;
+    adj_psi_kernel<<<dim3(mt, (a.Nw + ADJ_TN - 1) / ADJ_TN), 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    adj_backward_kernel<<<grd, 256, 0, st>>>(a);
+    adj_grad_kernel<<<dim3(mt, (a.T + ADJ_TN - 1) / ADJ_TN), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -20,29 +20,43 @@ __device__ __forceinline__ const float2 *row_src(const FrameGeom &g, int64_t m) 
     return g.base + p * g.pitch_probe + (g.roi_y0 + y) * g.pitch_row + (g.roi_x0 + x);
 }
 
-__global__ void mean_kernel(FrameGeom g, int n, float2 *mu_hat) {
-    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= g.M) return;
-    const float2 *src = row_src(g, m);
+// Provisional mean of each row over the n frames of the first push.  Block = 32 rows x 8
+// frame lanes: lane f sums frames f, f + 8, ... of its row (a warp reads 32 consecutive
+// pixels of one frame), the eight partial sums are added in a fixed order.  Any rounding of
+// mu_hat is harmless: the exact mean correction uses the FP64 residual sums of the pushes.
+__global__ void __launch_bounds__(256) mean_kernel(FrameGeom g, int n, float2 *mu_hat) {
+    __shared__ float2 part[8][32];
+    const int r = threadIdx.x & 31, f = threadIdx.x >> 5;
+    const int64_t m = (int64_t)blockIdx.x * 32 + r;
     double sr = 0.0, si = 0.0;
-    int t = 0;
-    for (; t + 8 <= n; t += 8) {
-        float br = 0.f, bi = 0.f;
+    if (m < g.M) {
+        const float2 *src = row_src(g, m);
+        for (int t0 = f; t0 < n; t0 += 64) {
+            float br = 0.f, bi = 0.f;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            float2 v = __ldcs(src + (int64_t)(t + i) * g.pitch_frame);
-            br += v.x;
-            bi += v.y;
+            for (int i = 0; i < 8; ++i) {
+                const int t = t0 + 8 * i;
+                if (t < n) {
+                    const float2 v = __ldcs(src + (int64_t)t * g.pitch_frame);
+                    br += v.x;
+                    bi += v.y;
+                }
+            }
+            sr += br;
+            si += bi;
         }
-        sr += br;
-        si += bi;
     }
-    for (; t < n; ++t) {
-        float2 v = __ldcs(src + (int64_t)t * g.pitch_frame);
-        sr += v.x;
-        si += v.y;
+    part[f][r] = make_float2((float)sr, (float)si);
+    __syncthreads();
+    if (f == 0 && m < g.M) {
+        float ar = 0.f, ai = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            ar += part[k][r].x;
+            ai += part[k][r].y;
+        }
+        mu_hat[m] = make_float2(ar / n, ai / n);
     }
-    mu_hat[m] = make_float2((float)(sr / n), (float)(si / n));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 a, __nv_bfloat16 b) {
@@ -297,7 +311,7 @@ cudaError_t launch_frame_table(const float2 **table, const float2 *base, int64_t
 }
 
 cudaError_t launch_mean(const FrameGeom &g, int n, float2 *mu_hat, cudaStream_t st) {
-    mean_kernel<<<blocks_for(g.M, 256), 256, 0, st>>>(g, n, mu_hat);
+    mean_kernel<<<blocks_for(g.M, 32), 256, 0, st>>>(g, n, mu_hat);
     return cudaGetLastError();
 }
 
