@@ -56,9 +56,10 @@ def parse():
     ap.add_argument("--pipeline", type=int, default=1,
                     help="segments in flight: one plan and CUDA stream each, steps alternate between them "
                          "(a segment's conversions overlap the previous segment's contraction)")
-    ap.add_argument("--workload", default="realistic", choices=["realistic", "batched", "diff"],
+    ap.add_argument("--workload", default="realistic", choices=["realistic", "batched", "diff", "thick"],
                     help="batched: the 16 uneven partitions, autotuned tiles, one CUDA-graph replay per step; "
-                         "diff: the differentiation workload, forward + adjoint per step")
+                         "diff: the differentiation workload, forward + adjoint per step; thick: one 32-probe "
+                         "batch of the thick-sample workload per step")
     ap.add_argument("--in-place", dest="in_place", action="store_true", default=False,
                     help="the contraction reads pushed frames in place (no staging pass)")
     ap.add_argument("--staging", dest="in_place", action="store_false",
@@ -408,6 +409,135 @@ def batched_arm(args):
 
 
 # ----------------------------------------------------------------------------------------------
+# Thick sample: 32-probe batches of 1024^2 multislice frames, a centred 256^2 k-ROI cropped while
+# the pushes are read, T = 8192 in 64-frame pushes, 1000 energies, compensated FP32 accumulators
+# across flushes of 2048 frames.  One step = one probe batch (1/8 of the 256-probe scan).
+# ----------------------------------------------------------------------------------------------
+def thick_arm(args):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import synth
+    import synth.gpu as sg
+    from paper_2607_02236_gb300 import TacawPlan
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = synth.thick()
+    spec = w.streams[0]
+    B = w.probe_batch
+    K, T, Tc, Nw = spec.Kx, spec.T, spec.Tc, spec.Nw
+    gx, gy = spec.full_grid
+    rx, ry = spec.roi_origin
+    npix = K * K
+    fe = B * gx * gy                       # one full frame for each probe of the batch
+    cmac_step = B * npix * T * Nw
+    k_stage = 2048
+    st_t = torch.cuda.current_stream()
+    st = st_t.cuda_stream
+    # a resident ring of R pushes (17.2 GB each), cycled over the segment: frame t of a step is
+    # frame t mod (R * Tc) of the ring; only the ROI of the full grid is synthesised (and read)
+    R = 2
+    ring = torch.zeros(R * Tc * fe, dtype=torch.complex64, device="cuda")
+    for r in range(R):
+        sg.generate(spec, 33 + rank, ring.data_ptr() + r * Tc * fe * 8, r * Tc, Tc, pitch_row=gx, pitch_frame=fe,
+                    pitch_probe=gx * gy, out_x0=rx, out_y0=ry, p0=0, P=B, stream=st)
+    I = torch.empty(B * Nw * npix, dtype=torch.float32, device="cuda")
+    S = torch.empty(max(1, B * len(spec.detectors) * Nw), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    plan = TacawPlan([stream_config(spec, P=B)], precision="split_bf16", k_stage=k_stage, accum="kahan")
+    info = plan.info()
+    n_push = T // Tc
+
+    def step():
+        plan.reset(st)
+        for i in range(n_push):
+            plan.push(0, ring.data_ptr() + (i % R) * Tc * fe * 8, Tc, st)
+        plan.finalize_async(I, S if len(spec.detectors) else None, None, st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.check_errors(st)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    plan.set_timing(True)
+    plan.kernel_time_ms(reset=True)
+    l0 = plan.info()["kernel_launches"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st_t)
+    for _ in range(args.steps):
+        step()
+    e1.record(st_t)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = clk.stop()
+    plan.check_errors(st)
+    launches = (plan.info()["kernel_launches"] - l0) // args.steps
+    k_ms, k_n = plan.kernel_time_ms(reset=True)
+    plan.set_timing(False)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda") / args.steps
+    value = job_rate(cmac_step, world, ms * 1e-3)
+
+    # stated error: 8 (probe, pixel) series of the ring-cycled segment, all energies
+    rng = np.random.default_rng(rank)
+    pb = rng.integers(0, B, 8)
+    c = (K // 2) * K + K // 2
+    px = np.concatenate([[c, c + 3], rng.integers(0, npix, 6)])
+    rows = torch.as_tensor(pb * gx * gy + (ry + px // K) * gx + (rx + px % K), device="cuda")
+    cyc = ring.view(R * Tc, fe)[:, rows].cpu().numpy()
+    ser = cyc[np.arange(T) % (R * Tc)]
+    got = I.view(B, Nw, npix)[torch.as_tensor(pb, device="cuda"), :, torch.as_tensor(px, device="cuda")]
+    got = got.cpu().numpy().T
+    _, ref = oracle.forward_pixels(ser, window_kind=spec.window, E_meV=spec.energies_meV(), dt_fs=spec.dt_fs,
+                                   subtract_mean=spec.subtract_mean)
+    err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+
+    peaks, peak_src = measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    flush_ms = k_ms / max(k_n, 1)
+    achieved = (cmac_step * args.steps / max(k_n, 1)) * 24 / (flush_ms * 1e-3) / 1e12
+    kname = ("flush_tc_drain2_kernel" if info["tc_accumulators"] == 2 else "flush_tc_drain_kernel") \
+        if info["tc_drain_frames"] else "flush_tc_kernel"
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": w.name, "probes_per_step": B, "full_grid": f"{gx}x{gy}",
+                           "k_roi": f"{K}x{K} at ({rx}, {ry})", "T": T, "frames_per_push": Tc, "n_omega": Nw,
+                           "E_range_meV": [0, spec.E_max_meV], "window": spec.window,
+                           "k_stage": info["k_stage"], "flushes_per_step": T // info["k_stage"],
+                           "accumulators": ["kahan", "fp64", "fp32"][info["accum"]],
+                           "omega_tile": info["omega_tile"], "tc_drain_frames": info["tc_drain_frames"],
+                           "plan_device_GB": round(info["device_bytes"] / 1e9, 1),
+                           "inputs": f"ring of {R} pushes of full frames ({R * Tc * fe * 8 / 1e9:.1f} GB) cycled",
+                           "l2": "pushes (17.2 GB of full frames, 1.07 GB of ROI read) larger than L2, no flush",
+                           "parallelism": f"replicas x{world}"},
+                "max_rel_err_I_vs_fp64": err, "error_sample": "8 (probe, pixel) series, all energies",
+                "clocks": clocks, "gpu_launches": launches, "e2e": None, "cpu_baseline": None,
+                "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": None, "kernel": kname, "flop_per_cmac": 24,
+                             "kernel_ms": flush_ms, "launches_per_step": k_n // max(args.steps, 1),
+                             "peak_source": f"{peak_src} bf16 sustained (MEASURED_PEAKS.json)"}}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+# ----------------------------------------------------------------------------------------------
 # Differentiation: forward spectrum and the hand-written adjoint (tacaw_backward) per step
 # ----------------------------------------------------------------------------------------------
 def diff_arm(args):
@@ -556,6 +686,8 @@ def main():
         return batched_arm(args)
     if args.workload == "diff":
         return diff_arm(args)
+    if args.workload == "thick":
+        return thick_arm(args)
 
     import numpy as np
     import torch
