@@ -948,7 +948,48 @@ def main():
                "h2d_bytes_per_step": T * frame_elems * 8, "d2h_bytes_per_step": S.numel() * 4,
                "ms_per_step": 1e3 * el / args.e2e_steps,
                "input": f"pinned host ring of {ring} pushes ({ring * push_elems * 8 / 1e9:.1f} GB) cycled",
+               "ingest": "copy engines: cudaMemcpyAsync of each push into a device ring, then the push",
                "overlap": "copies of the next step overlap this step's contraction" if not in_place else "none"}
+
+        # zero-copy ingest (staged plans): each push passes its pinned host address and the push
+        # kernels read the frames over the host link, no separate copy
+        if not in_place:
+            def zc_step(k):
+                plan.reset(st)
+                for i in range(n_push):
+                    n = min(Tc, T - i * Tc)
+                    plan.push(0, host.data_ptr() + (i % ring) * push_elems * 8, n, st)
+                plan.finalize_async(I, S, None, st)
+                S_host[k % 2].copy_(S, non_blocking=True)
+                done = torch.cuda.Event()
+                done.record(stream)
+                return done
+
+            zc_step(0).synchronize()
+            plan.check_errors(st)
+            barrier()
+            t0 = time.perf_counter()
+            prev = None
+            for k in range(args.e2e_steps):
+                ev = zc_step(k)
+                if prev is not None:
+                    prev[0].synchronize()
+                    checksum += float(S_host[prev[1] % 2][0])
+                prev = (ev, k)
+            prev[0].synchronize()
+            checksum += float(S_host[prev[1] % 2][0])
+            plan.check_errors(st)
+            el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+            zc = {"value": world * cmac_step * args.e2e_steps / el, "unit": UNIT,
+                  "h2d_bytes_per_step": T * frame_elems * 8, "d2h_bytes_per_step": S.numel() * 4,
+                  "ms_per_step": 1e3 * el / args.e2e_steps, "input": e2e["input"],
+                  "ingest": "zero-copy: the push kernels read each push from pinned host memory",
+                  "overlap": "none (reads happen inside the conversions)"}
+            # the faster ingest is the end-to-end figure; the other one is kept beside it
+            if zc["value"] > e2e["value"]:
+                zc["other_ingest"], e2e = e2e, zc
+            else:
+                e2e["other_ingest"] = zc
         del host
     plan.close()
 

@@ -253,13 +253,19 @@ typedef struct {
  * tables on the GPU (phase reduced in FP64).  Synchronous.  *out is written on success. */
 tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out);
 
-/* Pushes n_frames frames of stream stream_id (layout: tacaw_stream_desc) from device
- * memory.  The library reads them, removes the provisional mean (the mean of the first
- * push of the segment), splits/converts them into its staging area and, when K_stage
- * frames are staged and the segment is not complete, runs a flush (the contraction of the
- * staged frames into Psi).  d_frames may be reused once the work enqueued on `stream`
- * has completed.  Errors: OVERFLOW if the segment would exceed T frames (nothing is
- * pushed), STATE after finalize without reset, INVALID_ARG for n_frames < 1.           */
+/* Pushes n_frames frames of stream stream_id (layout: tacaw_stream_desc).  The library
+ * reads them, removes the provisional mean (the mean of the first push of the segment),
+ * splits/converts them into its staging area and, when K_stage frames are staged and the
+ * segment is not complete, runs a flush (the contraction of the staged frames into Psi).
+ * d_frames may be reused once the work enqueued on `stream` has completed.
+ * d_frames is device (or managed) memory, or -- staged plans only -- pinned host memory
+ * (cudaHostAlloc, or cudaHostRegister'ed and mapped at the same address): the push kernels
+ * then read the frames straight from host memory over the host link (NVLink-C2C on Grace
+ * systems), with no separate host-to-device copy.  Outside stream capture the address is
+ * checked with cudaPointerGetAttributes; pageable host memory and unknown addresses are
+ * refused (INVALID_ARG) before any work is enqueued.
+ * Errors: OVERFLOW if the segment would exceed T frames (nothing is pushed), STATE after
+ * finalize without reset, INVALID_ARG for n_frames < 1 or frames the device cannot read. */
 tacaw_status tacaw_push_frames(tacaw_plan_t plan, int stream_id, const void *d_frames,
                                int n_frames, void *stream);
 

@@ -1265,6 +1265,37 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     return TACAW_OK;
 }
 
+// The frames of a push are read by kernels: device or managed memory, or pinned host memory
+// that the device reads at the same address (a zero-copy ingest over the host link; staged
+// plans only, since the in-place contraction copies frames with tensor copies).  Anything else
+// (pageable host memory, an address CUDA does not know) is refused before any work is
+// enqueued.  Skipped while `st` is capturing a graph (the attribute query is not a stream
+// operation; pointers of a captured segment are the caller's to keep valid).
+static tacaw_status check_frames_memory(tacaw_plan_t p, const void *d_frames, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return TACAW_OK;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return TACAW_OK;
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, d_frames) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TACAW_ERR_INVALID_ARG, "d_frames is not an address CUDA knows");
+    }
+    if (pa.type == cudaMemoryTypeUnregistered)
+        return fail(TACAW_ERR_INVALID_ARG, "d_frames is neither device memory nor pinned host memory");
+    if (pa.type == cudaMemoryTypeHost) {
+        if (pa.devicePointer != d_frames)
+            return fail(TACAW_ERR_INVALID_ARG, "pinned host frames are mapped at another device address; "
+                        "pass the address from cudaHostGetDevicePointer");
+        if (p->in_place)
+            return fail(TACAW_ERR_INVALID_ARG, "frames_in_place plans read device memory only; push pinned "
+                        "host frames into a staged plan");
+    }
+    return TACAW_OK;
+}
+
 tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, int n_frames, void *stream) {
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
@@ -1275,6 +1306,8 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
     if ((reinterpret_cast<uintptr_t>(d_frames) & 7) != 0) return fail(TACAW_ERR_INVALID_ARG, "d_frames must be 8-byte aligned");
     if (p->ip2 && (reinterpret_cast<uintptr_t>(d_frames) & 15) != 0)
         return fail(TACAW_ERR_INVALID_ARG, "in-place frames must be 16-byte aligned (contiguous row copies)");
+    tacaw_status pk = check_frames_memory(p, d_frames, static_cast<cudaStream_t>(stream));
+    if (pk != TACAW_OK) return pk;
     UserStream &u = p->us[sid];
     if (u.pushed + n_frames > u.total)
         return fail(TACAW_ERR_OVERFLOW, "push of %d frames exceeds %lld (already %lld)", n_frames, (long long)u.total,
