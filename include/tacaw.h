@@ -277,7 +277,9 @@ tacaw_status tacaw_push_frames(tacaw_plan_t plan, int stream_id, const void *d_f
  *   d_S   float32 [s][p][d][j]        (may be NULL)
  *   d_Psi complex64 [s][p][j][ky][kx] (may be NULL)
  * Spectra are summed in a fixed order (deterministic).  d_S requires d_I.  Waits for the
- * work on `stream`.  Errors: STATE unless every stream has received exactly T frames.
+ * work on `stream`.  Outputs may be device, managed or pinned host memory; outside stream
+ * capture any other address is refused (INVALID_ARG) before work is enqueued.
+ * Errors: STATE unless every stream has received exactly T frames.
  * The last flush of every stream on the split path goes out as one tensor-core launch over
  * all streams (supercell partitions of uneven size; groups of up to 16 streams with the
  * same cluster size), its tiles ordered longest first.                                  */
@@ -310,7 +312,9 @@ tacaw_status tacaw_output_offsets(tacaw_plan_t plan, int stream_id, int64_t *I_o
  * (skip_init + (N - 1) * stride + T frames); S is the segments' average, so the gradient is
  * (1/N) sum_n g_n with segment n's g_n placed at its frames (added where segments overlap)
  * and zero on the skipped frames.
- * d_dL_dS: float32 [p][d][j] on the device.  Waits for the work on `stream`.             */
+ * d_dL_dS: float32 [p][d][j] on the device.  d_frames, d_grad and d_dL_dS may be device,
+ * managed or pinned host memory; outside stream capture any other address is refused
+ * (INVALID_ARG) before work is enqueued.  Waits for the work on `stream`.                */
 tacaw_status tacaw_backward(tacaw_plan_t plan, int stream_id, const float *d_dL_dS,
                             const void *d_frames, void *d_grad, void *stream);
 

@@ -715,6 +715,38 @@ tacaw_status check_plan(tacaw_plan_s *p) {
     return TACAW_OK;
 }
 
+// Buffers that kernels read or write: device or managed memory, or pinned host memory that the
+// device reaches at the same address (for pushes a zero-copy ingest over the host link, on
+// staged plans only: the in-place contraction copies frames with tensor copies, so
+// allow_host is false there).  Anything else (pageable host memory, an address CUDA does not
+// know) is refused before any work is enqueued.  Skipped while `st` is capturing a graph (the
+// attribute query is not a stream operation; pointers of a captured segment are the caller's to
+// keep valid).
+tacaw_status check_kernel_memory(const void *ptr, const char *what, bool allow_host, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return TACAW_OK;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return TACAW_OK;
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TACAW_ERR_INVALID_ARG, "%s is not an address CUDA knows", what);
+    }
+    if (pa.type == cudaMemoryTypeUnregistered)
+        return fail(TACAW_ERR_INVALID_ARG, "%s is neither device memory nor pinned host memory", what);
+    if (pa.type == cudaMemoryTypeHost) {
+        if (pa.devicePointer != ptr)
+            return fail(TACAW_ERR_INVALID_ARG, "pinned host %s is mapped at another device address; "
+                        "pass the address from cudaHostGetDevicePointer", what);
+        if (!allow_host)
+            return fail(TACAW_ERR_INVALID_ARG, "frames_in_place plans read device memory only; push pinned "
+                        "host frames into a staged plan");
+    }
+    return TACAW_OK;
+}
+
 tacaw_status read_device_error(tacaw_plan_s *p, cudaStream_t st) {
     CU_CHECK(p, cudaStreamSynchronize(st), "cudaStreamSynchronize");
     uint32_t h = 0;
@@ -732,6 +764,13 @@ tacaw_status read_device_error(tacaw_plan_s *p, cudaStream_t st) {
 tacaw_status finalize_impl(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, cudaStream_t st) {
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
+    const void *outs[3] = {d_I, d_S, d_Psi};
+    const char *names[3] = {"d_I", "d_S", "d_Psi"};
+    for (int i = 0; i < 3; ++i) {
+        if (!outs[i]) continue;
+        c = check_kernel_memory(outs[i], names[i], true, st);
+        if (c != TACAW_OK) return c;
+    }
     if (p->finalized) return fail(TACAW_ERR_STATE, "segment already finalized");
     for (size_t i = 0; i < p->us.size(); ++i)
         if (p->us[i].pushed != p->us[i].total)
@@ -1265,37 +1304,6 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     return TACAW_OK;
 }
 
-// The frames of a push are read by kernels: device or managed memory, or pinned host memory
-// that the device reads at the same address (a zero-copy ingest over the host link; staged
-// plans only, since the in-place contraction copies frames with tensor copies).  Anything else
-// (pageable host memory, an address CUDA does not know) is refused before any work is
-// enqueued.  Skipped while `st` is capturing a graph (the attribute query is not a stream
-// operation; pointers of a captured segment are the caller's to keep valid).
-static tacaw_status check_frames_memory(tacaw_plan_t p, const void *d_frames, cudaStream_t st) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
-        cudaGetLastError();
-        return TACAW_OK;
-    }
-    if (cs != cudaStreamCaptureStatusNone) return TACAW_OK;
-    cudaPointerAttributes pa{};
-    if (cudaPointerGetAttributes(&pa, d_frames) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(TACAW_ERR_INVALID_ARG, "d_frames is not an address CUDA knows");
-    }
-    if (pa.type == cudaMemoryTypeUnregistered)
-        return fail(TACAW_ERR_INVALID_ARG, "d_frames is neither device memory nor pinned host memory");
-    if (pa.type == cudaMemoryTypeHost) {
-        if (pa.devicePointer != d_frames)
-            return fail(TACAW_ERR_INVALID_ARG, "pinned host frames are mapped at another device address; "
-                        "pass the address from cudaHostGetDevicePointer");
-        if (p->in_place)
-            return fail(TACAW_ERR_INVALID_ARG, "frames_in_place plans read device memory only; push pinned "
-                        "host frames into a staged plan");
-    }
-    return TACAW_OK;
-}
-
 tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, int n_frames, void *stream) {
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
@@ -1306,7 +1314,7 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
     if ((reinterpret_cast<uintptr_t>(d_frames) & 7) != 0) return fail(TACAW_ERR_INVALID_ARG, "d_frames must be 8-byte aligned");
     if (p->ip2 && (reinterpret_cast<uintptr_t>(d_frames) & 15) != 0)
         return fail(TACAW_ERR_INVALID_ARG, "in-place frames must be 16-byte aligned (contiguous row copies)");
-    tacaw_status pk = check_frames_memory(p, d_frames, static_cast<cudaStream_t>(stream));
+    tacaw_status pk = check_kernel_memory(d_frames, "d_frames", !p->in_place, static_cast<cudaStream_t>(stream));
     if (pk != TACAW_OK) return pk;
     UserStream &u = p->us[sid];
     if (u.pushed + n_frames > u.total)
@@ -1468,6 +1476,13 @@ tacaw_status tacaw_backward(tacaw_plan_t p, int sid, const float *d_dL_dS, const
     if (c != TACAW_OK) return c;
     if (sid < 0 || sid >= (int)p->us.size()) return fail(TACAW_ERR_INVALID_ARG, "stream_id %d out of range", sid);
     if (!d_dL_dS || !d_frames || !d_grad) return fail(TACAW_ERR_INVALID_ARG, "NULL device pointer");
+    {
+        cudaStream_t cs = static_cast<cudaStream_t>(stream);
+        tacaw_status k = check_kernel_memory(d_frames, "d_frames", true, cs);
+        if (k == TACAW_OK) k = check_kernel_memory(d_grad, "d_grad", true, cs);
+        if (k == TACAW_OK) k = check_kernel_memory(d_dL_dS, "d_dL_dS", true, cs);
+        if (k != TACAW_OK) return k;
+    }
     const UserStream &u = p->us[sid];
     Stream &s = p->s[u.first];
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -66,3 +66,28 @@ def test_unreadable_or_in_place_host_frames_are_refused():
     with TacawPlan([stream_config(SPEC)], precision="split_bf16", frames_in_place=True) as plan:
         with pytest.raises(TacawError, match="INVALID_ARG"):
             plan.push(0, pinned.data_ptr(), 8)
+
+
+def test_pageable_outputs_and_gradient_buffers_are_refused():
+    """finalize's outputs and backward's buffers are written by kernels: pageable host memory
+    is refused before any work is enqueued, device memory then completes the same calls."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan, TacawError
+    s = SPEC
+    n = s.P * s.Kx * s.Ky
+    fr = torch.zeros(s.T * n, dtype=torch.complex64, device="cuda")
+    I_host = np.zeros(s.P * s.Nw * s.Kx * s.Ky, dtype=np.float32)
+    grad_host = np.zeros(s.T * n, dtype=np.complex64)
+    dLdS = torch.ones(s.P * s.Nw, dtype=torch.float32, device="cuda")
+    with TacawPlan([stream_config(s)], precision="fp32") as plan:
+        plan.push(0, fr, s.T)
+        with pytest.raises(TacawError, match="INVALID_ARG"):
+            plan.finalize(I_host.ctypes.data)
+        I = torch.empty(I_host.size, dtype=torch.float32, device="cuda")
+        plan.finalize(I)
+        with pytest.raises(TacawError, match="INVALID_ARG"):
+            plan.backward(0, dLdS, fr, grad_host.ctypes.data)
+        grad = torch.empty_like(fr)
+        plan.backward(0, dLdS, fr, grad)
+    torch.cuda.synchronize()
+    assert float(I.abs().max()) == 0.0 and float(grad.abs().max()) == 0.0
