@@ -730,13 +730,18 @@ def main():
     S = torch.empty(max(1, P * D * Nw), dtype=torch.float32, device="cuda")
     n_push = (T + Tc - 1) // Tc
 
-    def run_step(plan, out=None, sth=None):
-        """One segment through the public API: reset, all pushes, finalize (asynchronous)."""
+    def run_step(plan, out=None, sth=None, ev=None, sobj=None):
+        """One segment through the public API: reset, all pushes, finalize (asynchronous).
+        ev: a pair of CUDA events recorded on sobj around the reset and pushes (the conversions)."""
         I_, S_ = out if out is not None else (I, S)
         sth = st if sth is None else sth
+        if ev is not None:
+            ev[0].record(sobj)
         plan.reset(sth)
         for i in range(n_push):
             plan.push(0, base + i * Tc * frame_elems * 8, min(Tc, T - i * Tc), sth)
+        if ev is not None:
+            ev[1].record(sobj)
         plan.finalize_async(I_, S_, None, sth)
 
     def timed(plans, steps, warmup, sample_clocks=False, outs=None, streams=None):
@@ -759,8 +764,12 @@ def main():
         e0.record(stream)
         for sx in streams:
             sx.wait_event(e0)
+        # one segment in flight: the pushes' span (reset, provisional mean, conversions) per step
+        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)] if n == 1 else None
         for k in range(steps):
-            run_step(plans[k % n], outs[k % n], streams[k % n].cuda_stream)
+            run_step(plans[k % n], outs[k % n], streams[k % n].cuda_stream,
+                     ev=pev[k] if pev else None, sobj=streams[k % n])
         for sx in streams:
             ev = torch.cuda.Event()
             ev.record(sx)
@@ -772,6 +781,7 @@ def main():
             pl.check_errors(sx.cuda_stream)
         clocks = clk.stop() if clk else None
         ms = e0.elapsed_time(e1)
+        timed.push_ms = statistics.median(a.elapsed_time(b) for a, b in pev) if pev else None
         kms, kn = 0.0, 0
         for pl in plans:
             a, b = pl.kernel_time_ms(reset=True)
@@ -796,6 +806,7 @@ def main():
     pipe_streams = [torch.cuda.Stream() for _ in range(n_pipe)] if n_pipe > 1 else [stream]
     ms_step, k_ms, k_per_step, launches, clocks = timed(plans, args.steps, args.warmup, sample_clocks=True,
                                                         outs=outs, streams=pipe_streams)
+    push_ms = timed.push_ms
     for pl in plans[1:]:          # free the other segments' staging before the comparison legs
         pl.close()
     del outs[1:]
@@ -1026,6 +1037,21 @@ def main():
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock", "kernel_ms": k_ms,
                 "launches_per_step": k_per_step}
 
+    # HBM roofline of the pushes (staged plans): each conversion reads a complex64 sample (8 B)
+    # and writes its two 16-bit pieces of Re and Im (or a float2 on the FP32 path, 8 B)
+    conv = None
+    if push_ms and not info["frames_in_place"]:
+        conv_bytes = 16.0 * P * npix * T
+        hbm = peaks.get("hbm_gbs")
+        conv = {"bound": "hbm", "achieved": conv_bytes / (push_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": conv_bytes / (push_ms * 1e-3) / 1e9 / hbm if hbm else None, "traffic": None,
+                "kernel": "convert_split_tiled_kernel" if split else "convert_fp32_kernel",
+                "bytes_per_step": conv_bytes, "ms_per_step": push_ms,
+                "timed": "CUDA events around reset + all pushes of each timed step (median); the span also "
+                         "holds the provisional-mean kernel of the first push, whose 8 B per sample of "
+                         "that push are not counted",
+                "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json)"}
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         n_cpu = 4096
@@ -1057,7 +1083,8 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "max_rel_err_I_vs_fp64": err, "error_sample": "24 (probe, pixel) series, all energies",
                 "spectra_per_s": spectra_per_s, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
-                "roofline": roof, "cpu_baseline": cpu, "fp32_path": fp32, "split_fp16_path": fp16,
+                "roofline": roof, "conversion_roofline": conv, "cpu_baseline": cpu, "fp32_path": fp32,
+                "split_fp16_path": fp16,
                 "one_accumulator_mode": fast}
         if phases:
             line["flush_phases"] = phases
