@@ -14,7 +14,7 @@ import pytest
 import oracle
 import synth
 from synth import Detector, StreamSpec, frames
-from tests.helpers import oracle_kw, rel_err_peak, run_gpu
+from tests.helpers import oracle_kw, rel_err_peak, run_gpu, stream_config
 from tests.test_gpu_parity import CASES, TOL_SPLIT, random_frames
 
 pytestmark = pytest.mark.gpu
@@ -96,3 +96,67 @@ def test_fp16_range_is_checked_and_scale_is_honoured():
         run_gpu(spec, fr, "split_fp16")
     assert ei.value.status == ERR_OVERFLOW
     check(spec, fr, fp16_scale=16.0, want_psi=True)
+
+
+@pytest.mark.parametrize("N,stride,skip", [(5, 32, 0), (3, 20, 45)])
+def test_welch_and_skip_init_fp16(N, stride, skip):
+    """Welch lanes (each segment's mean residual at the operand scale, its last flush adding
+    (1/N) 2^-2e B |Psi|^2 into the average) and skipped leading frames on fp16 pieces."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    from tests.test_gpu_welch import SPEC as WSPEC, make_frames, welch_config
+    s = WSPEC
+    n = skip + (N - 1) * stride + s.T
+    fr = make_frames(s.P, n, s.Ky, s.Kx, seed=50 + N)
+    buf = torch.from_numpy(np.ascontiguousarray(fr.transpose(1, 0, 2, 3))).to("cuda")
+    fb = s.P * s.Kx * s.Ky * 8
+    with TacawPlan([welch_config(s, N, stride, skip)], precision="split_fp16") as plan:
+        info = plan.info()
+        I = torch.zeros(info["I_elems"], dtype=torch.float32, device="cuda")
+        S = torch.zeros(max(1, info["S_elems"]), dtype=torch.float32, device="cuda")
+        for t0 in range(0, n, 40):
+            plan.push(0, buf.data_ptr() + t0 * fb, min(40, n - t0))
+        plan.finalize(I, S)
+    ref = oracle.welch_forward(fr, s.T, stride, skip_init=skip, **oracle_kw(s))
+    got = I.cpu().numpy().reshape(s.P, s.Nw, s.Ky, s.Kx)
+    assert rel_err_peak(got, ref.I) <= TOL_SPLIT
+    assert rel_err_peak(S.cpu().numpy().reshape(s.P, 1, s.Nw), ref.S) <= TOL_SPLIT
+
+
+def test_grouped_launch_and_graph_replay_fp16():
+    """Uneven partitions in one plan: the last flushes of all streams in one grouped launch of
+    fp16 operands, then the whole segment captured into a CUDA graph and replayed over new
+    frames, each time against the oracle."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    from tests.test_gpu_graph_batched import SPECS, check_all, device_frames, make_frames, push_all
+    frames_ = [make_frames(s, 500 + i) for i, s in enumerate(SPECS)]
+    bufs = [device_frames(f) for f in frames_]
+    st = torch.cuda.Stream()
+    with TacawPlan([stream_config(s) for s in SPECS], precision="split_fp16") as plan:
+        info = plan.info()
+        I = torch.zeros(info["I_elems"], dtype=torch.float32, device="cuda")
+        S = torch.zeros(max(1, info["S_elems"]), dtype=torch.float32, device="cuda")
+        with torch.cuda.stream(st):
+            plan.reset(st)
+            push_all(plan, bufs, st)
+            plan.finalize_async(I, S, cuda_stream=st)
+            plan.check_errors(st)
+        check_all(plan, I, S, frames_, TOL_SPLIT)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            cur = torch.cuda.current_stream()
+            plan.reset(cur)
+            push_all(plan, bufs, cur)
+            plan.finalize_async(I, S, cuda_stream=cur)
+        frames_ = [make_frames(s, 600 + i) for i, s in enumerate(SPECS)]
+        for b, f in zip(bufs, frames_):
+            b.copy_(device_frames(f))
+        I.zero_()
+        S.zero_()
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        plan.check_errors(torch.cuda.current_stream())
+        check_all(plan, I, S, frames_, TOL_SPLIT)
+        del g
