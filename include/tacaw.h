@@ -291,8 +291,10 @@ tacaw_status tacaw_finalize(tacaw_plan_t plan, float *d_I, float *d_S, void *d_P
  * addresses given at capture time.  The device error flag is read by tacaw_check_errors. */
 tacaw_status tacaw_finalize_async(tacaw_plan_t plan, float *d_I, float *d_S, void *d_Psi, void *stream);
 
-/* Waits for the work on `stream` and reads the device error flag (TACAW_ERR_TIMEOUT, and
- * the plan poisoned, if a bounded device wait ran out since the flag was last cleared).  */
+/* Waits for the work on `stream` and reads the device error flag: TACAW_ERR_TIMEOUT if a
+ * bounded device wait ran out, TACAW_ERR_OVERFLOW if a split-FP16 push met a value beyond
+ * the fp16 range at the plan's fp16_scale; either poisons the plan.  tacaw_finalize and
+ * tacaw_backward read the same flag when they wait.                                      */
 tacaw_status tacaw_check_errors(tacaw_plan_t plan, void *stream);
 
 /* Element offsets of stream stream_id's block inside d_I / d_Psi and d_S.              */
