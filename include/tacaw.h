@@ -213,9 +213,9 @@ typedef struct {
     int tc_max_ctas;
     /* TACAW_PREC_SPLIT_FP16 only: power of two multiplying psi - mu_hat before the fp16 split,
      * in [2^-60, 2^60]; 0 selects 2^12, which suits exit waves of unit norm (|psi| <= 1, so
-     * |psi - mu_hat| <= 2 becomes <= 8192, eight times inside the fp16 range, while residual
-     * pieces of components down to ~1e-4 stay in fp16's normal range).  Scale data with
-     * larger components down (e.g. 2^12 / max|psi|).  Ignored by the other precisions.   */
+     * |psi - mu_hat| <= 2 becomes <= 8192, nearly eight times inside the fp16 range, while
+     * residual pieces of components down to ~1e-4 stay in fp16's normal range).  Scale data
+     * with larger components down (e.g. 2^12 / max|psi|).  Ignored by the other precisions. */
     double fp16_scale;
 } tacaw_plan_desc;
 
