@@ -189,6 +189,9 @@ class TacawPlan:
             if s.fft_bins:
                 d.fft_bins, d.n_omega = 1, int(s.fft_bins)
                 d.E_meV = POINTER(c_double)()
+            elif s.E_meV is None:              # no grid: the library reports it
+                d.fft_bins, d.n_omega = 0, int(s.n_omega)
+                d.E_meV = POINTER(c_double)()
             else:
                 E = (c_double * len(s.E_meV))(*[float(e) for e in s.E_meV])
                 self._keep.append(E)

@@ -84,3 +84,55 @@ def test_split_fp16_options_rejected_without_device_work(L):
     with pytest.raises(t.TacawError) as ei:
         t.TacawPlan([cfg], precision="split_fp16", frames_in_place=True)
     assert ei.value.status == t.ERR_UNSUPPORTED
+
+
+_BASE = dict(n_probes=2, kx=8, ky=8, T=16, dt_fs=5.0, pitch_row=8, pitch_frame=128, pitch_probe=64, fft_bins=8)
+
+# (stream fields, plan options, message fragment): each is refused with INVALID_ARG before the
+# plan touches the device
+_REFUSED = [
+    (dict(window="kaiser", window_param=61.0), {}, "Kaiser beta"),
+    (dict(window="chebwin", window_param=0.0), {}, "Chebyshev attenuation"),
+    (dict(roi_x0=-1, pitch_row=9), {}, "negative ROI origin"),
+    (dict(pitch_frame=32), {}, "pitch_frame"),
+    (dict(bose_T_K=-1.0), {}, "bose_T_K"),
+    (dict(welch_segments=-1), {}, "welch_segments"),
+    (dict(skip_init=-3), {}, "skip_init"),
+    (dict(fft_bins=0, E_meV=None, n_omega=4), {}, "E_meV is NULL"),
+    ({}, dict(tc_accumulators=4), "tc_accumulators"),
+    ({}, dict(tc_cluster=3), "tc_cluster"),
+    ({}, dict(tc_pair=3), "tc_pair"),
+    ({}, dict(tc_drain_frames=12), "tc_drain_frames"),
+    ({}, dict(tc_drain_frames=64, tc_pair=1), "tc_drain_frames runs on single CTAs"),
+    ({}, dict(tc_omega_tile=12), "tc_omega_tile"),
+    ({}, dict(tc_block_frames=24), "tc_block_frames"),
+    ({}, dict(k_stage=40, tc_block_frames=32), "multiple of tc_block_frames"),
+]
+
+
+@pytest.mark.parametrize("stream_kw,plan_kw,msg", _REFUSED, ids=[r[2] for r in _REFUSED])
+def test_plan_options_refused_before_device_work(L, stream_kw, plan_kw, msg):
+    import paper_2607_02236_gb300.tacaw as t
+    cfg = dict(_BASE)
+    cfg.update(stream_kw)
+    with pytest.raises(t.TacawError) as ei:
+        t.TacawPlan([t.StreamConfig(**cfg)], precision="split_bf16", **plan_kw)
+    assert ei.value.status == t.ERR_INVALID_ARG, str(ei.value)
+    assert msg in L.tacaw_last_error().decode()
+
+
+def test_bad_enums_refused_before_device_work(L):
+    import ctypes
+    import paper_2607_02236_gb300.tacaw as t
+    s = t.CStreamDesc()
+    s.n_probes, s.kx, s.ky, s.T, s.dt_fs = 1, 8, 8, 16, 5.0
+    s.pitch_row, s.pitch_frame, s.pitch_probe, s.fft_bins, s.n_omega = 8, 64, 64, 1, 8
+    for field_name, value, msg in (("precision", 7, "bad precision"), ("accum", 9, "bad accum")):
+        d = t.CPlanDesc()
+        d.n_streams, d.streams = 1, ctypes.pointer(s)
+        d.precision, d.accum = 1, 3
+        setattr(d, field_name, value)
+        h = ctypes.c_void_p()
+        assert L.tacaw_plan_create(ctypes.byref(d), ctypes.byref(h)) == t.ERR_INVALID_ARG
+        assert msg in L.tacaw_last_error().decode()
+        assert not h.value
