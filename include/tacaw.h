@@ -368,6 +368,16 @@ tacaw_status tacaw_destroy(tacaw_plan_t plan);
 /* Message for the calling thread's last non-OK status ("" if none).                     */
 const char *tacaw_last_error(void);
 
+/* Log sink.  The library reports every error it returns (the message tacaw_last_error
+ * gives, level TACAW_LOG_ERROR) and, at TACAW_LOG_INFO, the configuration each successful
+ * tacaw_plan_create chose (precision, K_stage, accumulators, tiling, device bytes).  The
+ * callback runs on the thread that made the call, synchronously, and must not block for
+ * long; it may call tacaw_set_log_callback.  One sink per process; NULL removes it.  The
+ * message is valid during the callback only.                                            */
+typedef enum { TACAW_LOG_ERROR = 0, TACAW_LOG_INFO = 1 } tacaw_log_level;
+typedef void (*tacaw_log_fn)(int level, const char *message, void *user);
+tacaw_status tacaw_set_log_callback(tacaw_log_fn fn, void *user);
+
 /* Library version string.                                                               */
 const char *tacaw_version(void);
 

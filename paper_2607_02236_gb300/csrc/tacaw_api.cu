@@ -16,6 +16,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -29,6 +30,22 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// process-wide log sink (tacaw_set_log_callback); called outside the lock
+std::mutex g_log_mu;
+tacaw_log_fn g_log_fn = nullptr;
+void *g_log_user = nullptr;
+
+void emit_log(int level, const char *msg) {
+    tacaw_log_fn fn;
+    void *user;
+    {
+        std::lock_guard<std::mutex> lk(g_log_mu);
+        fn = g_log_fn;
+        user = g_log_user;
+    }
+    if (fn) fn(level, msg, user);
+}
+
 tacaw_status fail(tacaw_status st, const char *fmt, ...) {
     char buf[512];
     va_list ap;
@@ -36,6 +53,7 @@ tacaw_status fail(tacaw_status st, const char *fmt, ...) {
     vsnprintf(buf, sizeof(buf), fmt, ap);
     va_end(ap);
     g_last_error = buf;
+    emit_log(TACAW_LOG_ERROR, buf);
     return st;
 }
 
@@ -44,7 +62,10 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 }  // namespace
 
 namespace tacaw {
-void set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+void set_last_error(const char *msg) {
+    g_last_error = msg ? msg : "";
+    emit_log(TACAW_LOG_ERROR, g_last_error.c_str());
+}
 }  // namespace tacaw
 
 namespace {
@@ -913,6 +934,13 @@ extern "C" {
 
 const char *tacaw_last_error(void) { return g_last_error.c_str(); }
 
+tacaw_status tacaw_set_log_callback(tacaw_log_fn fn, void *user) {
+    std::lock_guard<std::mutex> lk(g_log_mu);
+    g_log_fn = fn;
+    g_log_user = fn ? user : nullptr;
+    return TACAW_OK;
+}
+
 const char *tacaw_version(void) { return "tacaw-gb300 0.1 (sm_103a)"; }
 
 tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
@@ -1301,6 +1329,19 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         return rc;
     }
     *out = p;
+    {
+        char buf[512];
+        const Stream &s0 = p->s[0];
+        snprintf(buf, sizeof(buf),
+                 "plan: %d stream(s) (%zu internal), precision %s, K_stage %d frames, accumulators %s, "
+                 "first stream: %d energies in tiles of %d, block frames %d, drained chunks %d frames, "
+                 "in place %d, autotuned streams %d, %.2f GB on the device",
+                 (int)p->us.size(), p->s.size(),
+                 p->prec_user == TACAW_PREC_FP32 ? "fp32" : (p->f16 ? "split_fp16" : "split_bf16"), p->k_stage,
+                 p->accum == TACAW_ACC_FP64 ? "fp64" : (p->accum == TACAW_ACC_FP32 ? "fp32" : "kahan"), s0.Nw,
+                 s0.wt, p->bf, p->drain_kb * p->bf, p->in_place ? 1 : 0, p->tuned_streams, p->bytes / 1e9);
+        emit_log(TACAW_LOG_INFO, buf);
+    }
     return TACAW_OK;
 }
 

@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_int64, c_void_p
+from ctypes import CFUNCTYPE, POINTER, c_char_p, c_double, c_float, c_int, c_int64, c_void_p
 from dataclasses import dataclass, field
 from typing import List, Optional, Sequence
 
@@ -28,7 +28,7 @@ EXPORTS = ["tacaw_plan_create", "tacaw_push_frames", "tacaw_finalize", "tacaw_ou
            "tacaw_backward", "tacaw_reset", "tacaw_plan_get_info", "tacaw_set_timing",
            "tacaw_kernel_time_ms", "tacaw_destroy", "tacaw_last_error", "tacaw_version",
            "tacaw_detector_spectra_noalloc", "tacaw_flush_trace", "tacaw_finalize_async",
-           "tacaw_check_errors"]
+           "tacaw_check_errors", "tacaw_set_log_callback"]
 
 
 class TacawError(RuntimeError):
@@ -97,6 +97,7 @@ def lib():
     L.tacaw_flush_trace.argtypes = [c_void_p, c_void_p, c_int64, POINTER(c_int64)]
     L.tacaw_detector_spectra_noalloc.argtypes = [c_void_p, c_int, c_int, c_int, c_int, POINTER(CDetector), c_int,
                                                  c_void_p, c_void_p]
+    L.tacaw_set_log_callback.argtypes = [c_void_p, c_void_p]
     L.tacaw_last_error.restype = c_char_p
     L.tacaw_version.restype = c_char_p
     for name in EXPORTS:
@@ -307,3 +308,22 @@ def detector_spectra_noalloc(I, n_probes: int, n_omega: int, kx: int, ky: int, d
 
 def version() -> str:
     return lib().tacaw_version().decode()
+
+
+LOG_ERROR, LOG_INFO = 0, 1
+_LOG_FN = CFUNCTYPE(None, c_int, c_char_p, c_void_p)
+_log_keep = None
+
+
+def set_log_callback(fn=None):
+    """Routes the library's log (tacaw_set_log_callback) to fn(level, message); None removes
+    it.  Levels: LOG_ERROR (every error returned, with its message), LOG_INFO (the
+    configuration of each plan created)."""
+    global _log_keep
+    if fn is None:
+        _check(lib().tacaw_set_log_callback(None, None))
+        _log_keep = None
+        return
+    cb = _LOG_FN(lambda level, msg, user: fn(int(level), msg.decode(errors="replace") if msg else ""))
+    _check(lib().tacaw_set_log_callback(ctypes.cast(cb, c_void_p), None))
+    _log_keep = cb

@@ -136,3 +136,22 @@ def test_bad_enums_refused_before_device_work(L):
         assert L.tacaw_plan_create(ctypes.byref(d), ctypes.byref(h)) == t.ERR_INVALID_ARG
         assert msg in L.tacaw_last_error().decode()
         assert not h.value
+
+
+def test_log_callback_receives_errors_and_can_be_removed(L):
+    import paper_2607_02236_gb300.tacaw as t
+    got = []
+    t.set_log_callback(lambda level, msg: got.append((level, msg)))
+    try:
+        with pytest.raises(t.TacawError):
+            t.TacawPlan([t.StreamConfig(**dict(_BASE, T=0))], precision="fp32")
+        assert L.tacaw_push_frames(None, 0, None, 1, None) == t.ERR_INVALID_ARG
+    finally:
+        t.set_log_callback(None)
+    assert [lvl for lvl, _ in got] == [t.LOG_ERROR, t.LOG_ERROR]
+    assert "T must be >= 1" in got[0][1]
+    assert got[1][1] == L.tacaw_last_error().decode()
+    n = len(got)
+    with pytest.raises(t.TacawError):
+        t.TacawPlan([t.StreamConfig(**dict(_BASE, T=0))], precision="fp32")
+    assert len(got) == n                                   # removed: no further calls

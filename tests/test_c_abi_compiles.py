@@ -13,6 +13,11 @@ PROGRAM = r"""
 #include "tacaw.h"
 #include <stdio.h>
 
+static void on_log(int level, const char *message, void *user) {
+    (void)user;
+    fprintf(stderr, "[tacaw %d] %s\n", level, message);
+}
+
 int main(void) {
     tacaw_detector det = {TACAW_DET_CIRCULAR, 0.f, 0.f, -1.f, 20.f, NULL};
     double E[4] = {0.0, 1.0, 2.0, 3.0};
@@ -28,7 +33,8 @@ int main(void) {
     int64_t io = 0, so = 0, nc = 0, nl = 0;
     double ms = 0.0;
     unsigned long long trace[8];
-    tacaw_status st = tacaw_plan_create(&d, &plan);
+    tacaw_status st = tacaw_set_log_callback(on_log, NULL);
+    st = tacaw_plan_create(&d, &plan);
     if (st != TACAW_OK) { printf("%s\n", tacaw_last_error()); return 1; }
     st = tacaw_push_frames(plan, 0, NULL, 16, NULL);
     st = tacaw_finalize(plan, NULL, NULL, NULL, NULL);
