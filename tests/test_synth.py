@@ -51,3 +51,27 @@ def test_noise_std():
                      np.arange(64)[None, None, :])
     assert abs(np.std(n.real) - 1e-3 / np.sqrt(2)) < 0.03e-3
     assert abs(np.std(n.imag) - 1e-3 / np.sqrt(2)) < 0.03e-3
+
+
+def test_workload_shapes_match_their_configurations():
+    """The five workloads carry the stated shapes: complex MAC per segment (P K^2 T Nw), pushes,
+    energy ranges, probe batching and the crop of the thick-sample grid."""
+    from synth import workloads as W
+    cm = lambda w: sum(s.P * s.Kx * s.Ky * s.T * s.Nw for s in w.streams)
+    tiny, real, bat, diff, thick = (W.WORKLOADS[k]() for k in ("tiny", "realistic", "batched", "diff", "thick"))
+    assert cm(tiny) == 4 * 64 * 64 * 256 * 128 and tiny.streams[0].fft_bins == 128
+    assert cm(real) == 64 * 256 * 256 * 2048 * 400 and real.streams[0].Tc == 32
+    assert real.streams[0].E_max_meV == 120.0 and real.streams[0].n_modes == 32
+    assert cm(diff) == 8 * 128 * 128 * 512 * 200 and diff.precision == "fp32"
+    assert cm(thick) == 256 * 256 * 256 * 8192 * 1000 and thick.probe_batch == 32
+    ts = thick.streams[0]
+    assert ts.full_grid == (1024, 1024) and ts.roi_origin == (384, 384) and ts.Tc == 64
+    assert ts.E_max_meV == 150.0 and ts.n_modes == 30
+    # batched: 16 partitions, frame counts in {512, ..., 4096}, ROIs from the four sizes,
+    # 4-32 probes, 300 energies, 16-frame pushes, Hann or Gaussian windows
+    assert len(bat.streams) == 16
+    for s in bat.streams:
+        assert s.T % 512 == 0 and 512 <= s.T <= 4096
+        assert s.Kx == s.Ky and s.Kx in (128, 192, 256, 384)
+        assert 4 <= s.P <= 32 and s.Nw == 300 and s.Tc == 16 and s.window in ("hann", "gauss")
+    assert 0.5e13 < cm(bat) < 3e13
