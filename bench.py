@@ -64,14 +64,10 @@ def parse():
                     help="the contraction reads pushed frames in place (no staging pass)")
     ap.add_argument("--staging", dest="in_place", action="store_false",
                     help="convert pushed frames into the library's staging area at push time (default)")
-    ap.add_argument("--tc-accumulators", type=int, default=0, help="tensor-core tiling override (0: plan default)")
-    ap.add_argument("--tc-omega-tile", type=int, default=0)
-    ap.add_argument("--tc-cluster", type=int, default=0)
+    ap.add_argument("--tc-omega-tile", type=int, default=0, help="tensor-core tiling override (0: plan default)")
     ap.add_argument("--tc-block-frames", type=int, default=0)
     ap.add_argument("--tc-drain-frames", type=int, default=0,
-                    help="drained accumulator form: chunk length in frames (0: off)")
-    ap.add_argument("--tc-pair", type=int, default=0, choices=[0, 1, 2],
-                    help="CTA-pair MMAs (256 rows over a cluster of two SMs): 1 relayed, 2 direct stage barriers")
+                    help="frames per drained hi*hi accumulator chunk (0: 512)")
     ap.add_argument("--accum", default="auto", choices=["auto", "kahan", "fp64", "fp32"],
                     help="Psi accumulators across flushes (only used when a segment needs several flushes)")
     ap.add_argument("--tc-max-ctas", type=int, default=0,
@@ -79,8 +75,6 @@ def parse():
                          "convert the next segment's pushes beside the current contraction")
     ap.add_argument("--trace", action="store_true",
                     help="add the per-CTA phase breakdown of one traced contraction (tacaw_flush_trace)")
-    ap.add_argument("--fast-steps", type=int, default=2,
-                    help="steps with one TMEM accumulator per tile (faster, larger error; 0: skip)")
     return ap.parse_args()
 
 
@@ -375,8 +369,7 @@ def batched_arm(args):
     peaks, peak_src = measured_peaks()
     peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
     achieved = cmac_step * 24 / (k_ms * 1e-3) / 1e12
-    kname = ("flush_tc_drain2_kernel" if info["tc_accumulators"] == 2 else "flush_tc_drain_kernel") \
-        if info["tc_drain_frames"] else "flush_tc_kernel"
+    kname = "flush_tc_drain2_kernel"
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -508,8 +501,7 @@ def thick_arm(args):
     peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
     flush_ms = k_ms / max(k_n, 1)
     achieved = (cmac_step * args.steps / max(k_n, 1)) * 24 / (flush_ms * 1e-3) / 1e12
-    kname = ("flush_tc_drain2_kernel" if info["tc_accumulators"] == 2 else "flush_tc_drain_kernel") \
-        if info["tc_drain_frames"] else "flush_tc_kernel"
+    kname = "flush_tc_drain2_kernel"
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -791,8 +783,7 @@ def main():
         ms = max_over_ranks(ms, dist, "cuda")
         return ms / steps, kms / max(kn, 1), kn // max(steps, 1), launches, clocks
 
-    tiling = dict(tc_accumulators=args.tc_accumulators, tc_omega_tile=args.tc_omega_tile,
-                  tc_cluster=args.tc_cluster, tc_block_frames=args.tc_block_frames, tc_pair=args.tc_pair,
+    tiling = dict(tc_omega_tile=args.tc_omega_tile, tc_block_frames=args.tc_block_frames,
                   tc_drain_frames=args.tc_drain_frames, tc_max_ctas=args.tc_max_ctas,
                   frames_in_place=bool(args.in_place and args.precision == "split_bf16"))
     split = args.precision.startswith("split")
@@ -860,20 +851,6 @@ def main():
                                    subtract_mean=spec.subtract_mean)
     err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
 
-
-    # tensor-core tiling with a single accumulator per tile: faster, larger accumulation error
-    fast = None
-    if args.fast_steps > 0 and args.precision == "split_bf16":
-        with TacawPlan([stream_config(spec)], precision="split_bf16", tc_accumulators=1,
-                       frames_in_place=bool(args.in_place)) as pf:
-            msf, kf, _, _, _ = timed(pf, args.fast_steps, 1)
-            fi = pf.info()
-        gotf = Iv[torch.as_tensor(probes, device="cuda"), :, torch.as_tensor(pix, device="cuda")].cpu().numpy().T
-        errf = float(np.max(np.abs(gotf - ref)) / np.max(np.abs(ref)))
-        fast = {"value": world * cmac_step / (msf * 1e-3), "unit": UNIT, "ms_per_step": msf, "flush_ms": kf,
-                "max_rel_err_I_vs_fp64": errf, "tc_accumulators": 1, "omega_tile": fi["omega_tile"],
-                "block_frames": fi["tc_block_frames"], "cluster": fi["tc_cluster"],
-                "flush_tflops": cmac_step * 24 / (kf * 1e-3) / 1e12}
 
     # split-FP16 pieces (scaled frames) on the same input: same kernels and tiling, other operand type
     fp16 = None
@@ -1012,14 +989,7 @@ def main():
         achieved = cmac_launch * 24 / (k_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         src = os.path.join(ROOT, "paper_2607_02236_gb300", "csrc", "k_tc_gemm.cu")
-        if info["frames_in_place"]:
-            kname = "flush_tc_inplace_kernel" if info["tc_inplace_form"] == 2 else "flush_tc_direct_kernel"
-        elif info["tc_drain_frames"]:
-            kname = "flush_tc_drain2_kernel" if info["tc_accumulators"] == 2 else "flush_tc_drain_kernel"
-        elif info["tc_pair"]:
-            kname = "flush_tc_pair_kernel"
-        else:
-            kname = "flush_tc_kernel"
+        kname = "flush_tc_inplace_kernel" if info["frames_in_place"] else "flush_tc_drain2_kernel"
         tr = KERNEL_TRAFFIC.get((file_hash(src, None if info["frames_in_place"] else INPLACE_SECTION), kname))
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": (tr * cmac_launch if tr else None),
@@ -1074,8 +1044,7 @@ def main():
                            "precision": args.precision + (" (hi*hi+hi*lo+lo*hi, fp32 accumulate, fp64 phase)"
                                                           if split else ""),
                            "k_stage": info["k_stage"], "omega_tile": info["omega_tile"],
-                           "tc_accumulators": info["tc_accumulators"], "tc_block_frames": info["tc_block_frames"],
-                           "tc_cluster": info["tc_cluster"], "tc_pair": info["tc_pair"], "tc_drain_frames": info["tc_drain_frames"],
+                           "tc_block_frames": info["tc_block_frames"], "tc_drain_frames": info["tc_drain_frames"],
                            "frames_in_place": bool(info["frames_in_place"]),
                            "smem_stages": info["stages"], "plan_device_GB": round(info["device_bytes"] / 1e9, 2),
                            "l2": "inputs (%.1f GB) larger than L2, no flush" % (T * frame_elems * 8 / 1e9),
@@ -1084,8 +1053,7 @@ def main():
                 "max_rel_err_I_vs_fp64": err, "error_sample": "24 (probe, pixel) series, all energies",
                 "spectra_per_s": spectra_per_s, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
                 "roofline": roof, "conversion_roofline": conv, "cpu_baseline": cpu, "fp32_path": fp32,
-                "split_fp16_path": fp16,
-                "one_accumulator_mode": fast}
+                "split_fp16_path": fp16}
         if phases:
             line["flush_phases"] = phases
         print(json.dumps(line), flush=True)

@@ -157,57 +157,34 @@ typedef struct {
     int64_t hbm_budget_bytes;          /* device bytes the plan may hold; 0: 90% of free memory */
     int k_stage;                       /* frames staged per flush (multiple of 8); 0: from budget */
     /* Tile autotuner of the split path (staged operands).  NULL: tiles from the built-in
-     * cost rule.  Non-NULL: at plan creation every stream shape times its candidate tiles
-     * (energies per tile, cluster size) on scratch operands and keeps the fastest
-     * predicted one; "" keeps nothing, a file path reads and appends a text cache keyed by
-     * GPU and shape, so later plans of the same shapes skip the timing.  A fixed
-     * tc_omega_tile or tc_cluster is honoured and only the other dimension is tuned.     */
+     * cost rule.  Non-NULL: at plan creation every stream shape times its candidate tile
+     * widths (energies per tile) on scratch operands and keeps the fastest predicted one;
+     * "" keeps nothing, a file path reads and appends a text cache keyed by GPU and shape, so
+     * later plans of the same shapes skip the timing.  A fixed tc_omega_tile is honoured. */
     const char *tune_cache_path;
     /* Tensor-core tiling (split path); 0 selects automatically.
-     *   tc_omega_tile     complex energies per tile (multiple of 8)
-     *   tc_accumulators   TMEM accumulators per tile: 1 (all products in one), 2 (hi*hi | small
-     *                     terms), 3 (hi*hi alternating over two | small terms; the in-place
-     *                     and CTA-pair default).  Left at 0 on staged operands, the drained
-     *                     split form below is used.
-     *   tc_cluster        CTAs per cluster sharing the twiddle rows by TMA multicast: 1, 2, 4
-     *   tc_block_frames   frames per staged operand row: 8, 16 or 32 (32-, 64-, 128-byte rows);
-     *                     k_stage must be a multiple of it
-     *   tc_prefetch       staging blocks of operand A prefetched into L2 ahead of the load ring
-     *                     (<= 0: off) */
+     *   tc_omega_tile     complex energies per tile (multiple of 8; at most 112 on staged
+     *                     operands, 80 in place)
+     *   tc_block_frames   frames per staged operand row: 8, 16 or 32 (32-, 64- or 128-byte rows);
+     *                     k_stage must be a multiple of it                                    */
     int tc_omega_tile;
-    int tc_accumulators;
-    int tc_cluster;
     int tc_block_frames;
-    int tc_prefetch;
-    /* != 0 (split path only): pushed buffers are read in place by the contraction instead of
+    /* != 0 (split-BF16 only): pushed buffers are read in place by the contraction instead of
      * being converted into a staging area at push time.  Each pushed buffer must then stay
      * valid and unchanged until the flush that covers its frames has completed on the stream:
      * with the default K_stage (the whole segment) that is until tacaw_finalize returns.
-     * When every stream keeps each 128-row tile contiguous in a frame (kx a multiple of 128, or
-     * unpadded rows with roi_x0 = 0 and probes that are whole tiles or adjacent), all row
-     * offsets and pitches are even, and the tiling is left at (or set to) 32-frame blocks with
-     * one or two accumulators, a persistent drained kernel copies the rows with bulk copies
-     * (pushed buffers must then be 16-byte aligned); otherwise a register-fed kernel runs. */
+     * Every stream must keep each 128-row tile contiguous in a frame (kx a multiple of 128, or
+     * unpadded rows with roi_x0 = 0 and probes that are whole tiles or adjacent), with even
+     * sizes, row offsets and pitches, 32-frame blocks, and 16-byte aligned pushed buffers;
+     * other layouts are refused with TACAW_ERR_UNSUPPORTED at plan creation.              */
     int frames_in_place;
-    /* Split path, staged operands: 1 runs each pair of 128-row tiles as 256-row MMAs on a
-     * cluster of two SMs (tcgen05 CTA pair): each SM stages its own rows of A and half of the
-     * tile's twiddle rows, halving the twiddle operand traffic per SM.  Applies to streams whose
-     * tile is at most 256 columns, a multiple of 32 (others keep the single-CTA form); needs
-     * tc_cluster 0 or 2.  2: the same, with the odd CTA's copies completing directly on the
-     * even CTA's stage barriers instead of being relayed by one of its threads.  0: off.   */
-    int tc_pair;
-    /* Split path, staged operands: > 0 selects a drained accumulator form, chunks of
-     * tc_drain_frames frames (multiple of 8).  The tensor core's FP32 accumulation truncates
-     * each step against the running sum; draining finished chunks into FP32 registers (round
-     * to nearest, by the epilogue warps while the tensor core goes on) bounds that to a chunk.
-     *   tc_accumulators 1: all three products in one TMEM accumulator, double-buffered
-     *   tc_accumulators 2: hi*hi in one accumulator, drained; hi*lo + lo*hi in a second one
-     *                      for the whole tile (their truncation is ~2^-8 smaller)
-     * Tiles of up to 112 complex energies; single CTAs (tc_pair 0, tc_cluster 0/1); a
-     * persistent grid walks the tiles of all streams.  0: the default -- form 2 with 512-frame
-     * chunks when tc_accumulators, tc_pair and tc_cluster (> 1) are all left unset, else off. */
+    /* Split path: the tensor core's FP32 accumulation truncates each step against the running
+     * sum, so the hi*hi products are accumulated in chunks of tc_drain_frames frames (multiple of
+     * 8; 0: 512) that the epilogue warps drain into FP32 registers (round to nearest) while the
+     * tensor core goes on; hi*lo + lo*hi (~2^-8 of the magnitude) keep one accumulator for the
+     * whole flush.                                                                         */
     int tc_drain_frames;
-    /* Persistent contraction grids (drained forms, in-place drained kernel) take at most this
+    /* Persistent contraction grids (staged and in-place tensor-core kernels) take at most this
      * many CTAs, one per SM (0: every SM).  SMs left free run other work beside the
      * contraction, e.g. the conversions of another plan's segment pushed on another stream. */
     int tc_max_ctas;
@@ -232,19 +209,15 @@ typedef struct {
     int omega_tile;            /* complex energies per tensor-core tile (split path) */
     int stages;                /* shared-memory pipeline stages (split path) */
     int64_t kernel_launches;   /* kernels launched by push/finalize/backward since creation */
-    int tc_accumulators;       /* TMEM accumulators per tile (split path) */
-    int tc_cluster;            /* cluster size of the contraction (split path, first stream) */
     int tc_block_frames;       /* frames per staged operand row (split path) */
     int frames_in_place;       /* pushed frames are read in place by the contraction */
-    int tc_pair;               /* first stream runs CTA-pair MMAs */
-    int tc_drain_frames;       /* frames per drained accumulator chunk (0: not drained) */
+    int tc_drain_frames;       /* frames per drained hi*hi accumulator chunk (split path) */
     int tuned_streams;         /* streams whose tile the autotuner picked */
     int tune_candidates;       /* candidate tiles timed at creation (0: none, or all cached) */
     double tune_ms;            /* host time spent in the autotuner at creation */
-    int tc_inplace_form;       /* frames_in_place kernel: 0 none, 1 register-fed, 2 persistent drained
-                                  (chosen when every stream's tile rows are contiguous in a frame,
-                                  all row offsets even, 32-frame blocks, one or two accumulators) */
     int accum;                 /* tacaw_accum in use (TACAW_ACC_AUTO resolved at creation) */
+    int64_t flush_launches;    /* contraction launches since creation (one grouped launch over
+                                  several streams counts once) */
 } tacaw_plan_info;
 
 /* Creates a plan: validates the descriptor, sizes and allocates device memory
@@ -253,7 +226,10 @@ typedef struct {
  * tables on the GPU (phase reduced in FP64).  Synchronous.  *out is written on success. */
 tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out);
 
-/* Pushes n_frames frames of stream stream_id (layout: tacaw_stream_desc).  The library
+/* Sec. II.B, processing of a batch: the exit waves of a trajectory chunk arrive frame by
+ * frame; here they are folded into the segment's transform as they arrive (streaming form
+ * of the chunk FFT of Eq. 1's phi_MD).
+ * Pushes n_frames frames of stream stream_id (layout: tacaw_stream_desc).  The library
  * reads them, removes the provisional mean (the mean of the first push of the segment),
  * splits/converts them into its staging area and, when K_stage frames are staged and the
  * segment is not complete, runs a flush (the contraction of the staged frames into Psi).
@@ -269,7 +245,8 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out);
 tacaw_status tacaw_push_frames(tacaw_plan_t plan, int stream_id, const void *d_frames,
                                int n_frames, void *stream);
 
-/* Completes the segment of every stream: flushes what is staged, applies the exact
+/* Eq. 1 (I = B(E) |phi_MD|^2) and the DetectorSet sum over apertures (Sec. II.B).
+ * Completes the segment of every stream: flushes what is staged, applies the exact
  * mean correction Psi -= (mu - mu_hat) W(E_j), W the window's transform, forms I and
  * the detector spectra.  Outputs (caller-owned device memory, streams concatenated in
  * order; see tacaw_output_offsets):
@@ -281,8 +258,8 @@ tacaw_status tacaw_push_frames(tacaw_plan_t plan, int stream_id, const void *d_f
  * capture any other address is refused (INVALID_ARG) before work is enqueued.
  * Errors: STATE unless every stream has received exactly T frames.
  * The last flush of every stream on the split path goes out as one tensor-core launch over
- * all streams (supercell partitions of uneven size; groups of up to 16 streams with the
- * same cluster size), its tiles ordered longest first.                                  */
+ * all streams (supercell partitions of uneven size; groups of up to 16 streams), its tiles
+ * ordered longest first.                                                                */
 tacaw_status tacaw_finalize(tacaw_plan_t plan, float *d_I, float *d_S, void *d_Psi, void *stream);
 
 /* tacaw_finalize without the wait: enqueues the same work and returns.  With
@@ -301,7 +278,9 @@ tacaw_status tacaw_check_errors(tacaw_plan_t plan, void *stream);
 tacaw_status tacaw_output_offsets(tacaw_plan_t plan, int stream_id, int64_t *I_offset,
                                   int64_t *S_offset);
 
-/* Gradient of L = sum_{p,d,j} dL_dS[p][d][j] * S[p][d][j] with respect to the frames of one
+/* Adjoint of the path above (no counterpart in the paper, whose spectra are not
+ * differentiated): the chain rule through Eq. 1, the windowed transform and the detector sum.
+ * Gradient of L = sum_{p,d,j} dL_dS[p][d][j] * S[p][d][j] with respect to the frames of one
  * stream's segment, in PyTorch's convention for real losses of complex inputs:
  *   grad = dL/dRe(psi) + i dL/dIm(psi) = 2 dL/dconj(psi)
  *   g[t,k] = 2 ( w_t A[t,k] - (1/T) sum_t' w_t' A[t',k] ),  A[t,k] = sum_j e^{+i theta_jt} G[k,j],

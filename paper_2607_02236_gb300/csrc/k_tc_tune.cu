@@ -1,21 +1,19 @@
 // Tile autotuner of the tensor-core contraction (host code).
 //
 // For one stream shape (rows M, energies Nw, segment length T, frames per flush) it times the
-// contraction kernel itself for each candidate tile -- energies per tile wt and cluster size
-// C -- on scratch operands, and keeps the fastest predicted one.  Candidates: for n_wt energy
-// tiles from the fewest that fit the TMEM columns up to three more, the narrowest multiple of
-// 8 covering Nw in n_wt tiles; C in {1, 2, 4} where the tile splits over the cluster.  Each
-// candidate runs one wave of CTAs (as many as are co-resident) at two flush lengths; the
-// per-CTA time is linear in the staged blocks (fill + main loop + epilogue), so the two points
-// give the time of any flush length.  The prediction for the stream is
-//   one stream per plan:  ceil(CTAs / resident) waves x wave time
-//   several streams:      CTAs x wave time / resident   (their tiles share one launch)
+// staged contraction kernel itself for each candidate tile width -- energies per tile wt -- on
+// scratch operands, and keeps the fastest predicted one.  Candidates: for n_wt energy tiles
+// from the fewest that fit the widest tile up to three more, the narrowest multiple of 8
+// covering Nw in n_wt tiles.  Each candidate runs one wave of tiles (one per co-resident CTA)
+// at two flush lengths; the per-tile time is linear in the staged blocks (fill + main loop +
+// epilogue), so the two points give the time of any flush length.  The prediction is
+//   one stream per plan:  ceil(tiles / resident) waves x wave time
+//   several streams:      tiles x wave time / resident   (their tiles share one launch)
 // summed over the segment's flushes.  Operand values do not change the instruction stream,
-// so the scratch operands hold one constant bit pattern.  The caller picks from the table of
-// predictions (several streams share one cluster size, since it is a launch attribute).
+// so the scratch operands hold one constant bit pattern.
 //
-// Tables are kept in a text cache (one line per shape: "<key> | <wt>:<cluster>:<ms> ...") so
-// a later plan of the same shape on the same kind of GPU skips the timing.
+// Tables are kept in a text cache (one line per shape: "<key> | <wt>:<ms> ...") so a later
+// plan of the same shape on the same kind of GPU skips the timing.
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -43,7 +41,7 @@ struct DevBuf {
 };
 
 struct Cand {
-    int wt, n_wt, C, stages, resident;
+    int wt, n_wt, stages, resident;
     int64_t n_mt_sub;
 };
 
@@ -54,9 +52,8 @@ std::string shape_key(const TuneShape &s) {
     cudaDeviceGetAttribute(&mnr, cudaDevAttrComputeCapabilityMinor, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     char b[320];
-    snprintf(b, sizeof(b), "tacaw-tune-v1 sm%d%dx%d acc=%d drain=%d bf=%d M=%lld Nw=%d T=%d ring=%d multi=%d wt=%d c=%d",
-             maj, mnr, sms, s.n_acc, s.drain_kb, s.bf, (long long)s.M, s.Nw, s.T, s.ring, s.multi ? 1 : 0, s.fixed_wt,
-             s.fixed_cluster);
+    snprintf(b, sizeof(b), "tacaw-tune-v2 sm%d%dx%d drain=%d bf=%d M=%lld Nw=%d T=%d ring=%d multi=%d wt=%d", maj,
+             mnr, sms, s.drain_kb, s.bf, (long long)s.M, s.Nw, s.T, s.ring, s.multi ? 1 : 0, s.fixed_wt);
     return b;
 }
 
@@ -72,10 +69,10 @@ bool cache_lookup(const char *path, const std::string &key, std::vector<TuneCand
             continue;
         std::vector<TuneCand> t;
         const char *q = bar + 3;
-        int w, c, used;
+        int w, used;
         double ms;
-        while (sscanf(q, "%d:%d:%lf%n", &w, &c, &ms, &used) == 3) {
-            if (w > 0 && c > 0 && ms >= 0.0) t.push_back(TuneCand{w, c, ms});
+        while (sscanf(q, "%d:%lf%n", &w, &ms, &used) == 2) {
+            if (w > 0 && ms >= 0.0) t.push_back(TuneCand{w, ms});
             q += used;
         }
         if (!t.empty()) {
@@ -92,7 +89,7 @@ void cache_store(const char *path, const std::string &key, const std::vector<Tun
     std::string line = key + " |";
     char b[64];
     for (const TuneCand &c : tab) {
-        snprintf(b, sizeof(b), " %d:%d:%.6f", c.wt, c.cluster, c.ms);
+        snprintf(b, sizeof(b), " %d:%.6f", c.wt, c.ms);
         line += b;
     }
     line += "\n";
@@ -111,12 +108,8 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
     const std::string key = shape_key(sh);
     std::vector<TuneCand> cached;
     if (cache_lookup(cache_path, key, &cached)) {
-        for (const TuneCand &c : cached) {
-            int br, nb;
-            if (c.wt % 8 == 0 && c.wt <= sh.wt_max && tc_b_boxes(2 * c.wt, c.cluster, &br, &nb) &&
-                tc_stages_for(2 * c.wt, sh.bf) >= 2)
-                table->push_back(c);
-        }
+        for (const TuneCand &c : cached)
+            if (c.wt % 8 == 0 && c.wt <= sh.wt_max && tc_stages_for(2 * c.wt, sh.bf) >= 2) table->push_back(c);
         if (!table->empty()) return true;
     }
     const int64_t n_mt = (sh.M + kMTile - 1) / kMTile;
@@ -137,21 +130,14 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
         const int stages = tc_stages_for(N, sh.bf);
         if (stages < 2) continue;
         const int n_wt = (sh.Nw + w - 1) / w;
-        for (int C : {1, 2, 4}) {
-            if (sh.fixed_cluster && C != sh.fixed_cluster) continue;
-            if (sh.drain_kb && C != 1) continue;
-            int br, nb;
-            if (!tc_b_boxes(N, C, &br, &nb) || (C > 1 && n_mt < 2 * C)) continue;
-            const int R = tc_resident_ctas(N, sh.bf, stages, C, 0, sh.drain_kb > 0 ? sh.drain_form : 0);
-            if (R <= 0) continue;
-            Cand c{w, n_wt, C, stages, R, 0};
-            // one wave: at most R CTAs, whole clusters, no more M tiles than the stream has
-            int64_t m = (int64_t)(R / (n_wt * C)) * C;
-            if (m < C) m = C;
-            const int64_t n_mt_c = (n_mt + C - 1) / C * C;
-            c.n_mt_sub = m < n_mt_c ? m : n_mt_c;
-            cands.push_back(c);
-        }
+        const int R = tc_resident_ctas(N, sh.bf, stages);
+        if (R <= 0) continue;
+        Cand c{w, n_wt, stages, R, 0};
+        // one wave: at most R tiles, no more row tiles than the stream has
+        int64_t m = (int64_t)(R / n_wt);
+        if (m < 1) m = 1;
+        c.n_mt_sub = m < n_mt ? m : n_mt;
+        cands.push_back(c);
     }
     if (cands.empty()) {
         snprintf(err, errlen, "autotune: no tensor-core tile fits (Nw=%d, bf=%d)", sh.Nw, sh.bf);
@@ -197,18 +183,10 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
         snprintf(err, errlen, "autotune: cudaEventCreate failed");
         return false;
     }
-    std::vector<char> maps(tc_maps_size());
     bool ok = true;
     for (const Cand &c : cands) {
         const int N = 2 * c.wt;
         const int64_t m_sub = c.n_mt_sub * kMTile;
-        if (!tc_make_maps(maps.data(), static_cast<const __nv_bfloat16 *>(a_hi.p),
-                          static_cast<const __nv_bfloat16 *>(a_lo.p), rows, kb2,
-                          static_cast<const __nv_bfloat16 *>(b_hi.p), static_cast<const __nv_bfloat16 *>(b_lo.p),
-                          c.wt * c.n_wt, kb2, N, c.C, sh.bf, err, errlen)) {
-            ok = false;
-            break;
-        }
         TcPlanArgs a{};
         a.e.M = m_sub;
         a.e.M_pad = m_sub;
@@ -226,11 +204,8 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
         a.kbB0 = 0;
         a.bf = sh.bf;
         a.stages = c.stages;
-        a.split = sh.n_acc > 1 ? 1 : 0;
-        a.n_big = sh.n_acc == 3 ? 2 : 1;
-        a.cluster = c.C;
         a.drain_kb = sh.drain_kb;
-        a.drain_form = sh.drain_form;
+        a.N_last = N;
         a.A_hi = a_hi.p;
         a.A_lo = a_lo.p;
         a.B_hi = b_hi.p;
@@ -243,9 +218,9 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
         for (int q = 0; q < 2 && ok; ++q) {
             a.n_kb = kbs[q];
             const int reps = 3;
-            cudaError_t e = launch_flush_tc(a, maps.data(), st);       // warm-up
+            cudaError_t e = launch_flush_tc(a, st);       // warm-up
             e = e == cudaSuccess ? cudaEventRecord(e0, st) : e;
-            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_flush_tc(a, maps.data(), st);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_flush_tc(a, st);
             e = e == cudaSuccess ? cudaEventRecord(e1, st) : e;
             e = e == cudaSuccess ? cudaEventSynchronize(e1) : e;
             float ms = 0.f;
@@ -263,7 +238,7 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
         }
         if (!ok) break;
         const double slope = kb2 > kb1 ? (t[1] - t[0]) / (double)(kb2 - kb1) : 0.0;
-        const int64_t ctas = (n_mt + c.C - 1) / c.C * c.C * c.n_wt;
+        const int64_t ctas = n_mt * c.n_wt;
         const int64_t per_launch = c.n_mt_sub * c.n_wt;
         double pred = 0.0;
         for (int kb : flush_kb) {
@@ -274,7 +249,7 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
             else
                 pred += tw * (double)((ctas + per_launch - 1) / per_launch);
         }
-        table->push_back(TuneCand{c.wt, c.C, pred});
+        table->push_back(TuneCand{c.wt, pred});
         ++*timed;
     }
     cudaEventDestroy(e0);

@@ -96,8 +96,6 @@ struct Stream {
     int *adj_pix = nullptr;
     float *adj_w = nullptr;
     int n_adj = 0;
-    std::vector<unsigned char> tc_maps;
-    int tc_cluster = 1;
     int stages = 0;            // shared-memory pipeline stages of this stream's tiles
     double *win_table = nullptr;   // table-driven windows (Dolph-Chebyshev)
     // Welch lanes: internal stream `lane` of user stream `user` runs segments lane, lane +
@@ -106,7 +104,6 @@ struct Stream {
     int64_t seg = 0;           // current segment of this lane
     float out_scale = 1.f;
     int out_add = 0;
-    int tc_pair = 0;           // CTA-pair MMAs (cluster of 2, M = 256)
     bool tuned = false;        // tile picked by the autotuner
     // in-place frames: per staged frame, a pointer into the pushed buffer
     // host record of the segment's pushes (first frame, address): a flush whose frames are
@@ -141,13 +138,9 @@ struct tacaw_plan_s {
     int f16 = 0;               // split path with fp16 pieces of the scaled operands
     float f16_scale = 1.f;     // split FP16: operand A is f16_scale * (psi - mu_hat), a power of two
     int stages = 0;
-    int tc_acc = 3;
-    int drain_kb = 0;          // drained form: staging blocks per accumulator chunk (0: off)
-    int drain_form = 1;
+    int drain_kb = 0;          // split path: staging blocks per drained H chunk
     int bf = 8;                // frames per staged operand row (split path)
-    int tc_prefetch = 0;       // L2 prefetch distance of operand A in staging blocks
-    bool in_place = false;     // the contraction reads pushed frames directly
-    bool ip2 = false;          // ... through the persistent drained in-place kernel
+    bool in_place = false;     // the contraction reads pushed frames directly (in-place kernel)
     int tc_max_ctas = 0;       // persistent contraction grids: at most this many CTAs (0: all SMs)
     // with a capped grid the last flush runs on a highest-priority stream of the plan, forked
     // from and joined back to the caller's stream, so that its CTAs take SMs ahead of other
@@ -158,6 +151,7 @@ struct tacaw_plan_s {
     int64_t I_elems = 0, S_elems = 0;
     int64_t flushes_total = 0;
     int64_t launches = 0;
+    int64_t flush_launches = 0;    // contraction launches (a grouped launch counts once)
     bool poisoned = false;
     bool finalized = false;
     uint32_t *d_err = nullptr;
@@ -265,17 +259,12 @@ double bose_factor(double E, double TK) {
     return x / (-std::expm1(-x));
 }
 
-// Complex energies per tensor-core tile: every accumulator holds 2*wt real columns and all
-// of them must fit the 512 TMEM columns (one accumulator may span two 256-column MMAs).
-// Among multiples of 8 the width with the least padded work plus a fixed per-tile cost
-// (operand A is re-read once per energy tile) wins; a requested width is clamped.
-int omega_tile_max(int n_acc) {
-    const int max_cols = n_acc > 1 ? 512 / n_acc : 512;
-    return std::max(8, (max_cols / 2) / 8 * 8);
-}
-
-void choose_omega_tile(Stream &s, int n_acc, int requested, int cap = 0) {
-    const int wt_max = cap ? std::min(cap, omega_tile_max(n_acc)) : omega_tile_max(n_acc);
+// Complex energies per tile: at most `cap` (the register sums of the tensor-core kernels; the
+// FP32 path pads to 64-wide tiles on its own).  Among multiples of 8 the width with the least
+// padded work plus a fixed per-tile cost (operand A is re-read once per energy tile) wins; a
+// requested width is clamped.
+void choose_omega_tile(Stream &s, int requested, int cap) {
+    const int wt_max = std::max(8, cap / 8 * 8);
     int best = 8;
     if (requested > 0) {
         best = std::min(requested, wt_max);
@@ -337,9 +326,9 @@ TcPlanArgs tc_args(tacaw_plan_s *p, const Stream &s, const EpiArgs &e) {
     a.wt = s.wt;
     a.n_wt = s.n_wt;
     a.N = 2 * s.wt;
-    // split drained form: the last energy tile computes only the columns that hold energies
+    // staged form: the last energy tile computes only the columns that hold energies
     a.N_last = a.N;
-    if (p->drain_kb > 0 && p->drain_form == 2 && !p->in_place) {
+    if (!p->in_place) {
         const int last = s.Nw - (s.n_wt - 1) * s.wt;
         a.N_last = std::min(a.N, (2 * last + 15) / 16 * 16);
     }
@@ -347,19 +336,13 @@ TcPlanArgs tc_args(tacaw_plan_s *p, const Stream &s, const EpiArgs &e) {
     a.kbB0 = s.stage_start / p->bf;
     a.bf = p->bf;
     a.stages = s.stages;
-    a.split = p->tc_acc > 1 ? 1 : 0;
-    a.n_big = p->tc_acc == 3 ? 2 : 1;
-    a.drain_kb = (p->in_place && !p->ip2) ? 0 : p->drain_kb;
-    a.drain_form = p->drain_form;
+    a.drain_kb = p->drain_kb;
     a.A_hi = s.A_hi;
     a.A_lo = s.A_lo;
     a.B_hi = s.B_hi;
     a.B_lo = s.B_lo;
     a.a_rows = s.M_pad;
     a.b_rows = 2 * s.Nw_pad;
-    a.cluster = p->in_place ? 1 : s.tc_cluster;
-    a.pair = p->in_place ? 0 : s.tc_pair;
-    a.prefetch = p->in_place ? 0 : p->tc_prefetch;
     a.max_ctas = p->tc_max_ctas;
     a.f16 = p->f16;
     a.err = p->d_err;
@@ -455,30 +438,28 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         d.prev_sums = s.flushes > 0 ? 1 : 0;
         d.subtract_mean = s.d.subtract_mean;
         d.T = s.T;
-        if (p->ip2) {
-            // evenly spaced frames (one buffer, or pushes that continue each other): tensor map
-            alignas(64) unsigned char fmap[128];
-            const void *fm = nullptr;
-            const float2 *first = inplace_first_frame(s, s.stage_start, n);
-            char eb[256];
-            if (first && (size_t)tc_frame_map_size() <= sizeof(fmap) && s.d.pitch_frame < (int64_t)1 << 31 &&
-                tc_make_frame_map(fmap, first, s.d.pitch_frame, n, eb, sizeof(eb)))
-                fm = fmap;
-            CU_CHECK(p, launch_flush_tc_inplace(a, d, fm, st), "flush (tensor cores, in place, drained)");
-        }
-        else
-            CU_CHECK(p, launch_flush_tc_direct(a, d, s.tc_maps.data(), st), "flush (tensor cores, in place)");
+        // evenly spaced frames (one buffer, or pushes that continue each other): tensor map
+        alignas(64) unsigned char fmap[128];
+        const void *fm = nullptr;
+        const float2 *first = inplace_first_frame(s, s.stage_start, n);
+        char eb[256];
+        if (first && (size_t)tc_frame_map_size() <= sizeof(fmap) && s.d.pitch_frame < (int64_t)1 << 31 &&
+            tc_make_frame_map(fmap, first, s.d.pitch_frame, n, eb, sizeof(eb)))
+            fm = fmap;
+        CU_CHECK(p, launch_flush_tc_inplace(a, d, fm, st), "flush (tensor cores, in place)");
         p->launches++;
+        p->flush_launches++;
     } else if (p->prec == TACAW_PREC_SPLIT_BF16) {
         if (n % p->bf) {
-            CU_CHECK(p, launch_zero_tail_split(s.M_pad, n, p->bf, s.A_hi, s.A_lo, p->drain_kb > 0, st), "zero_tail");
+            CU_CHECK(p, launch_zero_tail_split(s.M_pad, n, p->bf, s.A_hi, s.A_lo, 1, st), "zero_tail");
             p->launches++;
         }
         TcPlanArgs a = tc_args(p, s, e);
         r = trace_buffer(p, tc_grid_ctas(a), &a.trace);
         if (r != TACAW_OK) return r;
-        CU_CHECK(p, launch_flush_tc(a, s.tc_maps.data(), st), "flush (tensor cores)");
+        CU_CHECK(p, launch_flush_tc(a, st), "flush (tensor cores)");
         p->launches++;
+        p->flush_launches++;
     } else {
         SimtArgs a{};
         a.e = e;
@@ -489,6 +470,7 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
         a.t0 = s.stage_start;
         CU_CHECK(p, launch_flush_simt(a, st), "flush (fp32)");
         p->launches++;
+        p->flush_launches++;
     }
     r = timing_end(p, e0, e1, st);
     if (r != TACAW_OK) return r;
@@ -496,57 +478,63 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
     return TACAW_OK;
 }
 
-// Final flushes of all staged tensor-core streams as few launches as possible: streams with
-// the same cluster size share one launch (up to kMaxGroupStreams each), their CTAs ordered by
-// decreasing per-CTA work so that the longest tiles start first.
-tacaw_status final_flush_grouped(tacaw_plan_s *p, float *d_I, float2 *d_Psi, cudaStream_t st) {
-    std::vector<int> todo;
-    for (int i = 0; i < (int)p->s.size(); ++i)
-        if (p->s[i].staged > 0) todo.push_back(i);
-    auto work = [&](int i) {
-        const Stream &s = p->s[i];
+// One flush of a staged tensor-core stream inside a grouped launch.
+struct FlushReq {
+    int s;                     // internal stream
+    int mode;                  // FLUSH_STORE / FLUSH_ADD / FLUSH_FINAL
+    float *I;                  // FINAL: the stream's block of I (or the Welch average), else null
+    float2 *Psi;
+};
+
+// Flushes of several staged tensor-core streams as few launches as possible: up to
+// kMaxGroupStreams streams share one persistent launch, their tiles ordered by decreasing
+// per-tile work so that the longest tiles start first.
+tacaw_status flush_grouped(tacaw_plan_s *p, std::vector<FlushReq> req, cudaStream_t st) {
+    auto work = [&](const FlushReq &q) {
+        const Stream &s = p->s[q.s];
         return (int64_t)((s.staged + p->bf - 1) / p->bf) * (2 * s.wt + 48);
     };
-    std::stable_sort(todo.begin(), todo.end(), [&](int a, int b) { return work(a) > work(b); });
-    for (int key = 0; key < 8; ++key) {
-        const int C = 1 << (key & 3), pr = key >> 2;   // (cluster, pair): a kernel and a launch attribute
-        if (C > 4) continue;
-        std::vector<int> grp;
-        for (int i : todo)
-            if (p->s[i].tc_cluster == C && (p->s[i].tc_pair != 0) == (pr != 0)) grp.push_back(i);
-        for (size_t g0 = 0; g0 < grp.size(); g0 += kMaxGroupStreams) {
-            const size_t g1 = std::min(grp.size(), g0 + (size_t)kMaxGroupStreams);
-            std::vector<TcPlanArgs> args;
-            std::vector<const void *> maps;
-            int64_t nc = 0;
-            for (size_t k = g0; k < g1; ++k) {
-                Stream &s = p->s[grp[k]];
-                if (s.staged % p->bf) {
-                    CU_CHECK(p, launch_zero_tail_split(s.M_pad, s.staged, p->bf, s.A_hi, s.A_lo, p->drain_kb > 0, st), "zero_tail");
-                    p->launches++;
-                }
-                float *I = d_I ? d_I + s.I_off : nullptr;
-                float2 *Psi = d_Psi ? d_Psi + s.I_off : nullptr;
-                args.push_back(tc_args(p, s, epi_args(p, s, FLUSH_FINAL, I, Psi)));
-                maps.push_back(s.tc_maps.data());
-                nc += tc_grid_ctas(args.back());
+    std::stable_sort(req.begin(), req.end(), [&](const FlushReq &a, const FlushReq &b) { return work(a) > work(b); });
+    for (size_t g0 = 0; g0 < req.size(); g0 += kMaxGroupStreams) {
+        const size_t g1 = std::min(req.size(), g0 + (size_t)kMaxGroupStreams);
+        std::vector<TcPlanArgs> args;
+        int64_t nc = 0;
+        for (size_t k = g0; k < g1; ++k) {
+            Stream &s = p->s[req[k].s];
+            if (s.staged % p->bf) {
+                CU_CHECK(p, launch_zero_tail_split(s.M_pad, s.staged, p->bf, s.A_hi, s.A_lo, 1, st), "zero_tail");
+                p->launches++;
             }
-            unsigned long long *tr = nullptr;
-            tacaw_status r = trace_buffer(p, nc, &tr);
-            if (r != TACAW_OK) return r;
-            for (auto &a : args) a.trace = tr;     // offset per stream by the launcher
-            cudaEvent_t e0, e1;
-            r = timing_begin(p, &e0, &e1, st);
-            if (r != TACAW_OK) return r;
-            CU_CHECK(p, launch_flush_tc_group(args.data(), maps.data(), (int)args.size(), st),
-                     "flush (tensor cores, grouped)");
-            p->launches++;
-            r = timing_end(p, e0, e1, st);
-            if (r != TACAW_OK) return r;
-            for (size_t k = g0; k < g1; ++k) flush_done(p, p->s[grp[k]]);
+            args.push_back(tc_args(p, s, epi_args(p, s, req[k].mode, req[k].I, req[k].Psi)));
+            nc += tc_grid_ctas(args.back());
         }
+        unsigned long long *tr = nullptr;
+        tacaw_status r = trace_buffer(p, nc, &tr);
+        if (r != TACAW_OK) return r;
+        for (auto &a : args) a.trace = tr;
+        cudaEvent_t e0, e1;
+        r = timing_begin(p, &e0, &e1, st);
+        if (r != TACAW_OK) return r;
+        CU_CHECK(p, launch_flush_tc_group(args.data(), (int)args.size(), st), "flush (tensor cores, grouped)");
+        p->launches++;
+        p->flush_launches++;
+        r = timing_end(p, e0, e1, st);
+        if (r != TACAW_OK) return r;
+        for (size_t k = g0; k < g1; ++k) flush_done(p, p->s[req[k].s]);
     }
     return TACAW_OK;
+}
+
+// Final flushes of all staged tensor-core single-segment streams (Welch lanes finish their
+// segments during the pushes).
+tacaw_status final_flush_grouped(tacaw_plan_s *p, float *d_I, float2 *d_Psi, cudaStream_t st) {
+    std::vector<FlushReq> req;
+    for (int i = 0; i < (int)p->s.size(); ++i) {
+        const Stream &s = p->s[i];
+        if (s.staged <= 0) continue;
+        req.push_back(FlushReq{i, FLUSH_FINAL, d_I ? d_I + s.I_off : nullptr, d_Psi ? d_Psi + s.I_off : nullptr});
+    }
+    return flush_grouped(p, req, st);
 }
 
 // Periodic Dolph-Chebyshev window of length T: the symmetric window of M = T + 1 taps without
@@ -604,7 +592,7 @@ tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
         CU_CHECK(p, cudaMemcpy(s.win_table, w.data(), sizeof(double) * s.T, cudaMemcpyHostToDevice), "copy window");
         ta.win_table = s.win_table;
     }
-    ta.swz = p->drain_kb > 0 ? 1 : 0;   // the drained kernel copies pre-swizzled blocks
+    ta.swz = 1;   // the staged kernel copies pre-swizzled blocks
     // cycles per frame c_j = E_j dt / h (FP64)
     std::vector<double> cj(s.Nw), E(s.Nw);
     for (int j = 0; j < s.Nw; ++j) {
@@ -633,12 +621,8 @@ tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
         const size_t nb = (size_t)s.n_kb_T * 2 * s.Nw_pad * 2 * p->bf;
         if (!dev_alloc(p, &s.B_hi, nb) || !dev_alloc(p, &s.B_lo, nb)) return fail(TACAW_ERR_OOM, "cudaMalloc(B split)");
         CU_CHECK(p, launch_twiddles_split(ta, s.B_hi, s.B_lo, p->f16, st), "twiddles split");
-        s.tc_maps.resize(tc_maps_size());
-        char eb[256];
         if (p->in_place) {
             if (!dev_alloc(p, &s.d_frame_ptr, s.T)) return fail(TACAW_ERR_OOM, "cudaMalloc(frame table)");
-            if (!tc_make_maps_b(s.tc_maps.data(), s.B_hi, s.B_lo, s.Nw_pad, s.n_kb_T, 2 * s.wt, p->bf, eb, sizeof(eb)))
-                return fail(TACAW_ERR_CUDA, "%s", eb);
         } else {
             const size_t na = (size_t)(s.ring / p->bf) * s.M_pad * 2 * p->bf;
             if (!dev_alloc(p, &s.A_hi, na) || !dev_alloc(p, &s.A_lo, na))
@@ -646,9 +630,6 @@ tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
             // rows >= M and never-written slots must read as zeros
             CU_CHECK(p, cudaMemsetAsync(s.A_hi, 0, na * sizeof(__nv_bfloat16), st), "memset staging");
             CU_CHECK(p, cudaMemsetAsync(s.A_lo, 0, na * sizeof(__nv_bfloat16), st), "memset staging");
-            if (!tc_make_maps(s.tc_maps.data(), s.A_hi, s.A_lo, s.M_pad, s.ring / p->bf, s.B_hi, s.B_lo, s.Nw_pad,
-                              s.n_kb_T, 2 * s.wt, s.tc_cluster, p->bf, eb, sizeof(eb)))
-                return fail(TACAW_ERR_CUDA, "%s", eb);
         }
     } else {
         const size_t na = (size_t)s.ring * s.M_pad;
@@ -894,7 +875,7 @@ tacaw_status push_internal(tacaw_plan_s *p, Stream &s, const float2 *frames, int
         } else {
             if (p->prec == TACAW_PREC_SPLIT_BF16)
                 CU_CHECK(p, launch_convert_split(gc, chunk, s.staged, p->bf, s.M_pad, s.mu_hat, s.sum_res, s.A_hi,
-                                                 s.A_lo, p->drain_kb > 0, p->f16, p->f16_scale, p->d_err, st),
+                                                 s.A_lo, 1, p->f16, p->f16_scale, p->d_err, st),
                          "convert");
             else
                 CU_CHECK(p, launch_convert_fp32(gc, chunk, s.staged, s.M_pad, s.mu_hat, s.sum_res, s.A32, st),
@@ -972,16 +953,8 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         tacaw_status v = validate_stream(desc->streams[i], i);
         if (v != TACAW_OK) return v;
     }
-    if (desc->tc_accumulators < 0 || desc->tc_accumulators > 3)
-        return fail(TACAW_ERR_INVALID_ARG, "tc_accumulators must be 0 (auto), 1, 2 or 3");
-    if (desc->tc_cluster != 0 && desc->tc_cluster != 1 && desc->tc_cluster != 2 && desc->tc_cluster != 4)
-        return fail(TACAW_ERR_INVALID_ARG, "tc_cluster must be 0 (auto), 1, 2 or 4");
-    if (desc->tc_pair < 0 || desc->tc_pair > 2) return fail(TACAW_ERR_INVALID_ARG, "tc_pair must be 0, 1 or 2");
     if (desc->tc_drain_frames < 0 || desc->tc_drain_frames % 8)
         return fail(TACAW_ERR_INVALID_ARG, "tc_drain_frames must be a non-negative multiple of 8");
-    if (desc->tc_drain_frames && (desc->tc_pair || desc->tc_cluster > 1 || desc->tc_accumulators > 2))
-        return fail(TACAW_ERR_INVALID_ARG, "tc_drain_frames runs on single CTAs with one or two accumulators "
-                    "(tc_pair 0, tc_cluster 0/1, tc_accumulators 0/1/2)");
     if (desc->tc_omega_tile < 0 || desc->tc_omega_tile % 8)
         return fail(TACAW_ERR_INVALID_ARG, "tc_omega_tile must be a multiple of 8");
     if (desc->tc_block_frames != 0 && desc->tc_block_frames != 8 && desc->tc_block_frames != 16 &&
@@ -989,45 +962,37 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         return fail(TACAW_ERR_INVALID_ARG, "tc_block_frames must be 0 (auto), 8, 16 or 32");
     if (prec == TACAW_PREC_SPLIT_BF16 && desc->tc_block_frames && desc->k_stage % desc->tc_block_frames)
         return fail(TACAW_ERR_INVALID_ARG, "k_stage must be a multiple of tc_block_frames");
+    if (desc->frames_in_place) {
+        // the in-place kernel reads each tile's 128 rows of every frame with one contiguous copy:
+        // per stream, the rows of a tile contiguous in the frame, even element offsets (16-byte
+        // aligned copies), 32-frame blocks
+        if (prec != TACAW_PREC_SPLIT_BF16)
+            return fail(TACAW_ERR_UNSUPPORTED, "frames_in_place needs the split-BF16 path");
+        if ((desc->tc_block_frames != 0 && desc->tc_block_frames != 32) || desc->k_stage % 32)
+            return fail(TACAW_ERR_UNSUPPORTED, "frames_in_place reads 32-frame blocks: tc_block_frames 0 or 32, "
+                        "k_stage a multiple of 32");
+        for (int i = 0; i < desc->n_streams; ++i) {
+            const tacaw_stream_desc &d = desc->streams[i];
+            const int64_t npix = (int64_t)d.kx * d.ky, M = npix * d.n_probes;
+            const bool even = M % 2 == 0 && d.kx % 2 == 0 && d.pitch_row % 2 == 0 && d.roi_x0 % 2 == 0 &&
+                              d.pitch_frame % 2 == 0 && (d.n_probes == 1 || d.pitch_probe % 2 == 0);
+            const bool rows_contiguous =
+                d.kx % kMTile == 0 ||
+                (d.pitch_row == d.kx && d.roi_x0 == 0 &&
+                 (npix % kMTile == 0 || d.n_probes == 1 || d.pitch_probe == npix));
+            if (!even || !rows_contiguous)
+                return fail(TACAW_ERR_UNSUPPORTED,
+                            "stream %d: frames_in_place needs every 128-row tile contiguous in a frame (kx a "
+                            "multiple of 128, or unpadded rows from roi_x0 = 0 with probes that are whole tiles or "
+                            "adjacent) and even sizes, offsets and pitches; stage the frames instead", i);
+        }
+    }
     tacaw_plan_s *p = new (std::nothrow) tacaw_plan_s();
     if (!p) return fail(TACAW_ERR_OOM, "host allocation failed");
-    p->tc_acc = desc->tc_accumulators ? desc->tc_accumulators : 3;
-    // default accumulation of the staged split path: the split drained form (hi*hi drained
-    // every 512 frames, small products apart), the fastest and most accurate form measured
-    const bool auto_acc = desc->tc_accumulators == 0 && !desc->tc_drain_frames && !desc->tc_pair &&
-                          desc->tc_cluster <= 1;
-    const int drain_frames = desc->tc_drain_frames ? desc->tc_drain_frames : (auto_acc ? 512 : 0);
-    // in-place frames: the persistent drained kernel reads each tile's 128 rows of every frame
-    // with one contiguous copy, which needs (per stream) the rows of a tile contiguous in the
-    // frame and 16-byte aligned copies; otherwise the register-fed in-place kernel runs
-    bool ip2 = desc->frames_in_place && prec == TACAW_PREC_SPLIT_BF16 &&
-               (desc->tc_accumulators == 0 || desc->tc_accumulators == 2) && !desc->tc_pair &&
-               desc->tc_cluster <= 1 && (desc->tc_block_frames == 0 || desc->tc_block_frames == 32) &&
-               desc->k_stage % 32 == 0;
-    for (int i = 0; i < desc->n_streams && ip2; ++i) {
-        const tacaw_stream_desc &d = desc->streams[i];
-        const int64_t npix = (int64_t)d.kx * d.ky, M = npix * d.n_probes;
-        const bool even = M % 2 == 0 && d.kx % 2 == 0 && d.pitch_row % 2 == 0 && d.roi_x0 % 2 == 0 &&
-                          d.pitch_frame % 2 == 0 && (d.n_probes == 1 || d.pitch_probe % 2 == 0);
-        const bool rows_contiguous =
-            d.kx % kMTile == 0 ||
-            (d.pitch_row == d.kx && d.roi_x0 == 0 && (npix % kMTile == 0 || d.n_probes == 1 || d.pitch_probe == npix));
-        ip2 = even && rows_contiguous;
-    }
-    p->ip2 = ip2;
-    const bool drained = (drain_frames > 0 && prec == TACAW_PREC_SPLIT_BF16 && !desc->frames_in_place) || ip2;
-    // drained forms: 1 = all products in one double-buffered accumulator, 2 = hi*hi drained, the
-    // small products in a second accumulator
-    if (drained) p->drain_form = (desc->tc_accumulators == 2 || auto_acc || ip2) ? 2 : 1;
-    if (drained) p->tc_acc = p->drain_form;
-    // TMEM columns per tile: accumulators side by side (the drained form holds two buffers)
-    const int tile_acc = drained ? 2 : p->tc_acc;
-    // widest tile: the drained forms' register sums; in place, also the raw frame ring
-    const int tile_cap = ip2 ? kInplaceMaxOmegaTile : (drained ? kDrainMaxOmegaTile : 0);
-    if (desc->frames_in_place && prec != TACAW_PREC_SPLIT_BF16) {
-        delete p;
-        return fail(TACAW_ERR_UNSUPPORTED, "frames_in_place needs the split-BF16 path");
-    }
+    // split path: hi*hi drained from tensor memory into FP32 registers every 512 frames (default)
+    const int drain_frames = desc->tc_drain_frames ? desc->tc_drain_frames : 512;
+    // widest tile: the staged form's register sums; in place, also the raw frame ring
+    const int tile_cap = desc->frames_in_place ? kInplaceMaxOmegaTile : kDrainMaxOmegaTile;
     p->in_place = desc->frames_in_place != 0;
     if (prec == TACAW_PREC_SPLIT_BF16) {
         // widest rows first: fewer, larger TMA requests per MMA K-step
@@ -1068,7 +1033,7 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         s.T_pad = (int)round_up(s.T, p->prec == TACAW_PREC_SPLIT_BF16 ? p->bf : 8);
         s.n_kb_T = s.T_pad / (p->prec == TACAW_PREC_SPLIT_BF16 ? p->bf : 8);
         s.Nw = s.d.n_omega;
-        choose_omega_tile(s, tile_acc, desc->tc_omega_tile, tile_cap);
+        choose_omega_tile(s, desc->tc_omega_tile, tile_cap);
         if (p->prec == TACAW_PREC_FP32) s.Nw_pad = (int)round_up(s.Nw, 64);
         T_pad_max = std::max(T_pad_max, s.T_pad);
         // Welch: ceil(T / stride) lanes (segments that overlap in time), each an internal stream
@@ -1107,10 +1072,8 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
         if (!desc->tc_block_frames)
             while (p->bf > 8 && tc_stages_for(max_cols(), p->bf) < 2) p->bf /= 2;
         for (auto &s : p->s) s.n_kb_T = s.T_pad / p->bf;
-        p->tc_prefetch = desc->tc_prefetch > 0 ? desc->tc_prefetch : 0;
         p->tc_max_ctas = desc->tc_max_ctas > 0 ? desc->tc_max_ctas : 0;
-        if (drained) p->drain_kb = std::max(1, (ip2 ? (desc->tc_drain_frames ? desc->tc_drain_frames : 512)
-                                                     : drain_frames) / p->bf);
+        p->drain_kb = std::max(1, drain_frames / p->bf);
         // autotuner: time the candidate tiles of every stream shape (staged operands only)
         if (desc->tune_cache_path && !p->in_place) {
             const auto t0 = std::chrono::steady_clock::now();
@@ -1123,12 +1086,9 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
                 sh.T = s.T;
                 sh.ring = desc->k_stage ? std::min(desc->k_stage, s.T_pad) : s.T_pad;
                 sh.bf = p->bf;
-                sh.n_acc = p->tc_acc;
-                sh.wt_max = drained ? std::min(kDrainMaxOmegaTile, omega_tile_max(tile_acc)) : omega_tile_max(tile_acc);
-                sh.drain_kb = drained ? std::max(1, drain_frames / p->bf) : 0;
-                sh.drain_form = p->drain_form;
+                sh.wt_max = kDrainMaxOmegaTile;
+                sh.drain_kb = p->drain_kb;
                 sh.fixed_wt = desc->tc_omega_tile ? s.wt : 0;
-                sh.fixed_cluster = desc->tc_cluster;
                 sh.multi = desc->n_streams > 1;
                 int timed = 0;
                 char eb[256];
@@ -1136,37 +1096,18 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
                     return bail(fail(TACAW_ERR_CUDA, "%s", eb));
                 p->tune_timed += timed;
             }
-            // one cluster size for all streams (their last flushes share one launch), the
-            // fastest total; then each stream's fastest energy tile under it
-            int best_C = 0;
-            double best_total = 1e300;
-            for (int C : {1, 2, 4}) {
-                double total = 0.0;
-                bool all = true;
-                for (auto &tab : tabs) {
-                    double b = 1e300;
-                    for (const TuneCand &c : tab)
-                        if (c.cluster == C) b = std::min(b, c.ms);
-                    if (b == 1e300) all = false;
-                    total += b;
-                }
-                if (all && total < best_total) {
-                    best_total = total;
-                    best_C = C;
-                }
-            }
-            if (!best_C) return bail(fail(TACAW_ERR_UNSUPPORTED, "autotune: no cluster size fits every stream"));
+            // each stream's fastest energy tile
             for (size_t i = 0; i < p->s.size(); ++i) {
                 Stream &s = p->s[i];
                 double b = 1e300;
                 for (const TuneCand &c : tabs[i])
-                    if (c.cluster == best_C && c.ms < b) {
+                    if (c.ms < b) {
                         b = c.ms;
                         s.wt = c.wt;
                     }
+                if (b == 1e300) return bail(fail(TACAW_ERR_UNSUPPORTED, "autotune: no tile fits stream %zu", i));
                 s.n_wt = (s.Nw + s.wt - 1) / s.wt;
                 s.Nw_pad = s.wt * s.n_wt;
-                s.tc_cluster = best_C;
                 s.tuned = true;
                 p->tuned_streams++;
             }
@@ -1242,49 +1183,12 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     }
     if (p->prec == TACAW_PREC_SPLIT_BF16) {
         for (auto &s : p->s) {
-            // CTA pairs: 128-row MMAs become 256-row MMAs over a cluster of two, each CTA holding
-            // half of the tile's twiddle rows (tiles of at most 256 columns, a multiple of 32)
             const int N = 2 * s.wt;
-            if (desc->tc_pair && !p->in_place && N <= 256 && N % 32 == 0 && s.M_pad / kMTile >= 2 &&
-                (desc->tc_cluster == 0 || desc->tc_cluster == 2)) {
-                s.tc_pair = desc->tc_pair;
-                s.tc_cluster = 2;
-            }
-            s.stages = p->ip2 ? tc_inplace_stages(N, p->bf) : tc_stages_for(N, p->bf, s.tc_pair);
+            s.stages = p->in_place ? tc_inplace_stages(N, p->bf) : tc_stages_for(N, p->bf);
             if (s.stages < 2)
-                return bail(fail(TACAW_ERR_UNSUPPORTED, "tensor-core tile of %d columns does not fit shared memory",
-                                 2 * s.wt));
+                return bail(fail(TACAW_ERR_UNSUPPORTED, "tensor-core tile of %d columns does not fit shared memory", N));
         }
         p->stages = p->s[0].stages;
-        for (auto &s : p->s) {
-            if (s.tuned || s.tc_pair) continue;
-            if (drained) {
-                s.tc_cluster = 1;
-                continue;
-            }
-            const int N = 2 * s.wt;
-            int br, nb;
-            const int64_t n_mt = s.M_pad / kMTile;
-            if (desc->tc_cluster) {
-                s.tc_cluster = desc->tc_cluster;
-                if (!tc_b_boxes(N, s.tc_cluster, &br, &nb))
-                    return bail(fail(TACAW_ERR_INVALID_ARG, "tile of %d columns cannot be split over a cluster of %d",
-                                     N, s.tc_cluster));
-            } else {
-                // largest cluster that keeps (almost) every SM busy
-                const int r1 = tc_resident_ctas(N, p->bf, s.stages, 1);
-                s.tc_cluster = 1;
-                for (int c : {4, 2}) {
-                    // multicast pays off for wide tiles (one accumulator); narrow tiles run best alone
-                    if (N <= 256 || !tc_b_boxes(N, c, &br, &nb) || n_mt < 2 * c) continue;
-                    const int rc = tc_resident_ctas(N, p->bf, s.stages, c);
-                    if (r1 > 0 && rc >= (int)(0.97 * r1)) {
-                        s.tc_cluster = c;
-                        break;
-                    }
-                }
-            }
-        }
     }
     cudaStream_t st = nullptr;
     tacaw_status rc = TACAW_OK;
@@ -1353,7 +1257,7 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
     if (n_frames < 1) return fail(TACAW_ERR_INVALID_ARG, "n_frames must be >= 1");
     if (p->finalized) return fail(TACAW_ERR_STATE, "segment finalized; call tacaw_reset first");
     if ((reinterpret_cast<uintptr_t>(d_frames) & 7) != 0) return fail(TACAW_ERR_INVALID_ARG, "d_frames must be 8-byte aligned");
-    if (p->ip2 && (reinterpret_cast<uintptr_t>(d_frames) & 15) != 0)
+    if (p->in_place && (reinterpret_cast<uintptr_t>(d_frames) & 15) != 0)
         return fail(TACAW_ERR_INVALID_ARG, "in-place frames must be 16-byte aligned (contiguous row copies)");
     tacaw_status pk = check_kernel_memory(d_frames, "d_frames", !p->in_place, static_cast<cudaStream_t>(stream));
     if (pk != TACAW_OK) return pk;
@@ -1455,17 +1359,14 @@ tacaw_status tacaw_plan_get_info(tacaw_plan_t p, tacaw_plan_info *info) {
     info->omega_tile = p->s.empty() ? 0 : p->s[0].wt;
     info->stages = p->stages;
     info->kernel_launches = p->launches;
-    info->tc_accumulators = p->prec == TACAW_PREC_SPLIT_BF16 ? p->tc_acc : 0;
-    info->tc_cluster = (p->prec == TACAW_PREC_SPLIT_BF16 && !p->s.empty()) ? p->s[0].tc_cluster : 0;
     info->tc_block_frames = p->prec == TACAW_PREC_SPLIT_BF16 ? p->bf : 0;
     info->tuned_streams = p->tuned_streams;
     info->tune_candidates = p->tune_timed;
     info->tune_ms = p->tune_ms;
     info->frames_in_place = p->in_place ? 1 : 0;
-    info->tc_pair = (p->prec == TACAW_PREC_SPLIT_BF16 && !p->s.empty()) ? p->s[0].tc_pair : 0;
-    info->tc_drain_frames = p->drain_kb * p->bf;
-    info->tc_inplace_form = p->in_place ? (p->ip2 ? 2 : 1) : 0;
+    info->tc_drain_frames = p->prec == TACAW_PREC_SPLIT_BF16 ? p->drain_kb * p->bf : 0;
     info->accum = p->accum;
+    info->flush_launches = p->flush_launches;
     return TACAW_OK;
 }
 

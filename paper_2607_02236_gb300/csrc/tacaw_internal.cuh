@@ -277,23 +277,14 @@ struct TcPlanArgs {
     int kbB0;                  // first global twiddle block
     int bf;                    // frames per staging block (8, 16, 32): rows of 4*bf bytes
     int stages;
-    int split;                 // 1: separate TMEM accumulators for hi*hi and hi*lo + lo*hi (N <= 256)
-    int n_big;                 // hi*hi accumulators (1 or 2, alternating by block parity)
-    int cluster;               // CTAs sharing (multicasting) one energy tile's B rows: 1, 2 or 4
-    int pair;                  // CTA-pair MMAs (M = 256 over a cluster of 2, B rows split; N <= 256):
-                               // 1 = the odd CTA relays its stage-full events, 2 = its copies
-                               // complete directly on the even CTA's barriers; 0 = off
-    int drain_form;            // drained kernel: 1 one accumulator, double-buffered; 2 hi*hi drained,
-                               // small products in a second accumulator for the whole tile
-    int drain_kb;              // > 0: one double-buffered accumulator drained into FP32
-                               // registers every drain_kb staging blocks (wt <= 112); the
+    int drain_kb;              // H (the hi*hi accumulator) is drained into FP32 registers every
+                               // drain_kb staging blocks (wt <= kDrainMaxOmegaTile); the staged
                                // operands are pre-swizzled and copied as contiguous blocks:
     const void *A_hi, *A_lo, *B_hi, *B_lo;   //   staging and twiddle tables
     int64_t a_rows;            //   rows per staging block of A (M_pad)
     int b_rows;                //   rows per twiddle block of B (2 * Nw_pad)
-    int prefetch;              // staging blocks of A prefetched into L2 ahead of the current one (0: off)
     int max_ctas;              // persistent grids: at most this many CTAs (0: one per SM)
-    int N_last;                // split drained form: columns of the last energy tile (<= N, multiple of 16)
+    int N_last;                // staged form: columns of the last energy tile (<= N, multiple of 16)
     int f16;                   // operands are fp16 pieces (split-FP16 path) instead of bf16
     unsigned long long *trace; // null, or kTraceWords globaltimer stamps per CTA (phase boundaries)
     uint32_t *err;
@@ -313,15 +304,13 @@ struct TcDirectArgs {
     int subtract_mean;
     int T;
 };
-struct TcMaps;                 // tensor maps (defined in k_tc_gemm.cu)
-cudaError_t launch_flush_tc(const TcPlanArgs &a, const void *maps /* TcMaps */, cudaStream_t st);
+cudaError_t launch_flush_tc(const TcPlanArgs &a, cudaStream_t st);
 int64_t tc_grid_ctas(const TcPlanArgs &a);
 constexpr int kMaxGroupStreams = 16;
-constexpr int kDrainMaxOmegaTile = 112;   // drained form: complex energies per tile at most
-constexpr int kInplaceMaxOmegaTile = 80;  // in-place drained form (worker registers at 168 a thread)
-// one launch over up to kMaxGroupStreams streams' flushes (same cluster size and block frames)
-cudaError_t launch_flush_tc_group(const TcPlanArgs *args, const void *const *maps, int n, cudaStream_t st);
-cudaError_t launch_flush_tc_direct(const TcPlanArgs &a, const TcDirectArgs &d, const void *maps, cudaStream_t st);
+constexpr int kDrainMaxOmegaTile = 112;   // staged form: complex energies per tile at most
+constexpr int kInplaceMaxOmegaTile = 80;  // in-place form (worker registers at 168 a thread)
+// one persistent launch over the flushes of up to kMaxGroupStreams streams (same block frames)
+cudaError_t launch_flush_tc_group(const TcPlanArgs *args, int n, cudaStream_t st);
 // persistent in-place drained form (A in tensor memory): tile rows contiguous and 16-byte
 // aligned in every frame (host-checked), 32-frame blocks, tiles of at most
 // kInplaceMaxOmegaTile energies.  tc_inplace_stages: its A/B stages for an N-column tile (0 if
@@ -333,30 +322,21 @@ bool tc_make_frame_map(void *map_out, const void *first_frame, int64_t pitch_fra
                        size_t errlen);
 size_t tc_frame_map_size();
 int tc_inplace_stages(int N, int bf, int *raw = nullptr, uint32_t *acc_s = nullptr, uint32_t *a_col = nullptr);
-bool tc_make_maps_b(void *maps_out, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
-                    int N, int bf, char *errbuf, size_t errlen);
-size_t tc_smem_bytes_direct(int N, int bf, int stages);
-int tc_stages_for(int N, int bf, int pair = 0);
-size_t tc_smem_bytes(int N, int bf, int stages, int pair = 0);
-size_t tc_maps_size();
-bool tc_make_maps(void *maps_out, const __nv_bfloat16 *A_hi, const __nv_bfloat16 *A_lo, int64_t M_pad,
-                  int n_kb_stage, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, int Nw_pad, int n_kb_T,
-                  int N, int cluster, int bf, char *errbuf, size_t errlen);
-bool tc_b_boxes(int N, int cluster, int *box_rows, int *nbox);
-int tc_resident_ctas(int N, int bf, int stages, int cluster, int pair = 0, int drain = 0);
+int tc_stages_for(int N, int bf);
+size_t tc_smem_bytes(int N, int bf, int stages);
+int tc_resident_ctas(int N, int bf, int stages);
 
-// Tile autotuner (k_tc_tune.cu): picks energies per tile and cluster size for one stream shape.
+// Tile autotuner (k_tc_tune.cu): picks the energies per tile for one stream shape.
 struct TuneShape {
     int64_t M;                 // rows (probes x ROI pixels)
     int Nw, T, ring;           // energies, frames per segment, frames per flush
-    int bf, n_acc, wt_max;     // block frames, TMEM accumulators, widest tile allowed
-    int fixed_wt, fixed_cluster;   // 0: tuned
+    int bf, wt_max;            // block frames, widest tile allowed
+    int fixed_wt;              // 0: tuned
     bool multi;                // several streams share the final launch
-    int drain_kb;              // drained form (single CTAs, one double-buffered accumulator)
-    int drain_form;            // 1 or 2 (see TcPlanArgs::drain_form)
+    int drain_kb;              // staging blocks per drained H chunk
 };
 struct TuneCand {
-    int wt, cluster;
+    int wt;
     double ms;                 // predicted contraction time of the stream's segment
 };
 // Fills `table` with one prediction per candidate tile (from the cache when it holds the

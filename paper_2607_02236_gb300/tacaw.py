@@ -56,19 +56,17 @@ class CStreamDesc(ctypes.Structure):
 class CPlanDesc(ctypes.Structure):
     _fields_ = [("n_streams", c_int), ("streams", POINTER(CStreamDesc)), ("precision", c_int),
                 ("accum", c_int), ("hbm_budget_bytes", c_int64), ("k_stage", c_int),
-                ("tune_cache_path", c_char_p), ("tc_omega_tile", c_int), ("tc_accumulators", c_int),
-                ("tc_cluster", c_int), ("tc_block_frames", c_int), ("tc_prefetch", c_int),
-                ("frames_in_place", c_int), ("tc_pair", c_int), ("tc_drain_frames", c_int),
-                ("tc_max_ctas", c_int), ("fp16_scale", c_double)]
+                ("tune_cache_path", c_char_p), ("tc_omega_tile", c_int), ("tc_block_frames", c_int),
+                ("frames_in_place", c_int), ("tc_drain_frames", c_int), ("tc_max_ctas", c_int),
+                ("fp16_scale", c_double)]
 
 
 class CPlanInfo(ctypes.Structure):
     _fields_ = [("device_bytes", c_int64), ("k_stage", c_int), ("n_streams", c_int), ("precision", c_int),
                 ("I_elems", c_int64), ("S_elems", c_int64), ("flushes", c_int64), ("omega_tile", c_int),
-                ("stages", c_int), ("kernel_launches", c_int64), ("tc_accumulators", c_int),
-                ("tc_cluster", c_int), ("tc_block_frames", c_int), ("frames_in_place", c_int),
-                ("tc_pair", c_int), ("tc_drain_frames", c_int), ("tuned_streams", c_int), ("tune_candidates", c_int), ("tune_ms", c_double),
-                ("tc_inplace_form", c_int), ("accum", c_int)]
+                ("stages", c_int), ("kernel_launches", c_int64), ("tc_block_frames", c_int),
+                ("frames_in_place", c_int), ("tc_drain_frames", c_int), ("tuned_streams", c_int),
+                ("tune_candidates", c_int), ("tune_ms", c_double), ("accum", c_int), ("flush_launches", c_int64)]
 
 
 _lib = None
@@ -172,10 +170,9 @@ class TacawPlan:
     """A streaming plan over one or more streams (see include/tacaw.h)."""
 
     def __init__(self, streams: Sequence[StreamConfig], precision: str = "split_bf16", accum: str = "auto",
-                 hbm_budget_bytes: int = 0, k_stage: int = 0, tc_omega_tile: int = 0,
-                 tc_accumulators: int = 0, tc_cluster: int = 0, tc_block_frames: int = 0, tc_prefetch: int = 0,
-                 frames_in_place: bool = False, tune: Optional[str] = None, tc_pair: int = 0,
-                 tc_drain_frames: int = 0, tc_max_ctas: int = 0, fp16_scale: float = 0.0):
+                 hbm_budget_bytes: int = 0, k_stage: int = 0, tc_omega_tile: int = 0, tc_block_frames: int = 0,
+                 frames_in_place: bool = False, tune: Optional[str] = None, tc_drain_frames: int = 0,
+                 tc_max_ctas: int = 0, fp16_scale: float = 0.0):
         """tune: None uses the built-in tile rule; "" autotunes at creation; a file path
         autotunes through a text cache at that path.  fp16_scale: operand scale of the
         split_fp16 precision (a power of two; 0 selects 2^12)."""
@@ -211,10 +208,8 @@ class TacawPlan:
             d.skip_init = int(s.skip_init)
         pd = CPlanDesc(len(streams), ctypes.cast(descs, POINTER(CStreamDesc)), PRECISIONS[precision],
                        ACCUMS[accum], int(hbm_budget_bytes), int(k_stage),
-                       None if tune is None else os.fsencode(tune), int(tc_omega_tile),
-                       int(tc_accumulators), int(tc_cluster), int(tc_block_frames), int(tc_prefetch),
-                       int(bool(frames_in_place)), int(tc_pair),
-                       int(tc_drain_frames), int(tc_max_ctas), float(fp16_scale))
+                       None if tune is None else os.fsencode(tune), int(tc_omega_tile), int(tc_block_frames),
+                       int(bool(frames_in_place)), int(tc_drain_frames), int(tc_max_ctas), float(fp16_scale))
         h = c_void_p()
         _check(L.tacaw_plan_create(ctypes.byref(pd), ctypes.byref(h)))
         self._h = h

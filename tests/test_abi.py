@@ -99,11 +99,7 @@ _REFUSED = [
     (dict(welch_segments=-1), {}, "welch_segments"),
     (dict(skip_init=-3), {}, "skip_init"),
     (dict(fft_bins=0, E_meV=None, n_omega=4), {}, "E_meV is NULL"),
-    ({}, dict(tc_accumulators=4), "tc_accumulators"),
-    ({}, dict(tc_cluster=3), "tc_cluster"),
-    ({}, dict(tc_pair=3), "tc_pair"),
     ({}, dict(tc_drain_frames=12), "tc_drain_frames"),
-    ({}, dict(tc_drain_frames=64, tc_pair=1), "tc_drain_frames runs on single CTAs"),
     ({}, dict(tc_omega_tile=12), "tc_omega_tile"),
     ({}, dict(tc_block_frames=24), "tc_block_frames"),
     ({}, dict(k_stage=40, tc_block_frames=32), "multiple of tc_block_frames"),
@@ -155,3 +151,28 @@ def test_log_callback_receives_errors_and_can_be_removed(L):
     with pytest.raises(t.TacawError):
         t.TacawPlan([t.StreamConfig(**dict(_BASE, T=0))], precision="fp32")
     assert len(got) == n                                   # removed: no further calls
+
+
+# in-place layouts the in-place kernel cannot take: refused with UNSUPPORTED before device work
+_INPLACE_REFUSED = [
+    (dict(kx=16, ky=16, pitch_row=20, pitch_frame=640, pitch_probe=320, roi_x0=2), {}, "contiguous"),
+    (dict(kx=8, ky=8, pitch_row=16, pitch_frame=256, pitch_probe=128), {}, "contiguous"),
+    (dict(kx=128, ky=2, pitch_row=129, pitch_frame=1024, pitch_probe=512, roi_x0=1), {}, "contiguous"),
+    (dict(kx=128, ky=2, pitch_row=128, pitch_frame=512, pitch_probe=256), dict(tc_block_frames=16), "32-frame"),
+    (dict(kx=128, ky=2, pitch_row=128, pitch_frame=512, pitch_probe=256), dict(k_stage=48), "32-frame"),
+]
+
+
+@pytest.mark.parametrize("stream_kw,plan_kw,msg", _INPLACE_REFUSED, ids=[f"{i}-{r[2]}" for i, r in
+                                                                            enumerate(_INPLACE_REFUSED)])
+def test_inplace_layouts_refused_before_device_work(L, stream_kw, plan_kw, msg):
+    import paper_2607_02236_gb300.tacaw as t
+    cfg = dict(_BASE, T=64)
+    cfg.update(stream_kw)
+    with pytest.raises(t.TacawError) as ei:
+        t.TacawPlan([t.StreamConfig(**cfg)], precision="split_bf16", frames_in_place=True, **plan_kw)
+    assert ei.value.status == t.ERR_UNSUPPORTED, str(ei.value)
+    assert msg in L.tacaw_last_error().decode()
+    with pytest.raises(t.TacawError) as ei:
+        t.TacawPlan([t.StreamConfig(**cfg)], precision="fp32", frames_in_place=True)
+    assert ei.value.status == t.ERR_UNSUPPORTED

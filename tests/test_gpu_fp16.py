@@ -70,14 +70,14 @@ def test_streaming_flushes_fp16(accum):
     assert out["info"]["flushes"] == 5
 
 
-@pytest.mark.parametrize("kw", [dict(tc_accumulators=3, tc_cluster=2, tc_block_frames=32),
-                                dict(tc_accumulators=1, tc_cluster=2, tc_omega_tile=200, tc_block_frames=16),
-                                dict(tc_accumulators=3, tc_pair=1, tc_block_frames=32),
-                                dict(tc_accumulators=1, tc_drain_frames=64, tc_block_frames=16),
-                                dict(tc_accumulators=2, tc_drain_frames=32, tc_block_frames=8)],
-                         ids=["classic3", "classic1_wide", "pair", "drain1", "drain2_bf8"])
+@pytest.mark.parametrize("kw", [dict(tc_block_frames=32),
+                                dict(tc_omega_tile=112, tc_block_frames=16),
+                                dict(tc_drain_frames=64, tc_block_frames=16),
+                                dict(tc_drain_frames=32, tc_block_frames=8)],
+                         ids=["bf32", "wide_bf16", "drain64_bf16", "drain32_bf8"])
 def test_tilings_fp16(kw):
-    """Every staged tensor-core kernel takes the fp16 operand type (instruction descriptor)."""
+    """The staged tensor-core kernel takes the fp16 operand type (instruction descriptor) at every
+    staging row width and drain length."""
     spec = StreamSpec(P=3, Kx=36, Ky=36, T=168, Tc=40, n_omega=150, E_max_meV=120.0, window="hann", n_modes=6,
                       noise=1e-3, detectors=(Detector("circular", 0, 0, -1, 6.0),))
     fr = frames.frames(spec, 11, 0, spec.T)

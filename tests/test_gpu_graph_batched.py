@@ -16,10 +16,10 @@ from tests.helpers import oracle_kw, rel_err_peak, stream_config
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "split_bf16": 3e-5}
+TOL = {"fp32": 1e-5, "split_bf16": 1e-5}
 
 # uneven probes, ROIs (one rectangular), segment lengths (ragged against every block size),
-# energy grids and windows; every omega tile fits one 128-column MMA (cluster size 1)
+# energy grids and windows
 SPECS = [
     StreamSpec(P=3, Kx=48, Ky=48, T=200, Tc=40, n_omega=70, E_max_meV=120.0, window="hann",
                detectors=(Detector(r_out=10.0),)),
@@ -32,7 +32,6 @@ SPECS = [
 ]
 
 MODES = {"split_bf16": dict(precision="split_bf16"),
-         "split_cluster2": dict(precision="split_bf16", tc_cluster=2),
          "split_inplace": dict(precision="split_bf16", frames_in_place=True),
          "fp32": dict(precision="fp32")}
 
@@ -103,7 +102,7 @@ def test_grouped_final_flush(mode):
         after = plan.info()
         worst = check_all(plan, I, S, frames, TOL[kw["precision"]])
     n_det = sum(1 for s in SPECS if len(s.detectors))
-    if mode in ("split_bf16", "split_cluster2"):
+    if mode == "split_bf16":
         bf = after["tc_block_frames"]
         tails = sum(1 for s in SPECS if s.T % bf)
         # mean residual per stream, zero tails, ONE contraction launch, one aperture launch per stream
@@ -202,11 +201,11 @@ def test_autotuned_tiles_and_cache(tmp_path):
     assert infos[1]["omega_tile"] == infos[0]["omega_tile"]
     lines = open(cache).read().splitlines()
     assert len(lines) == len(SPECS)
-    for ln in lines:                                   # "<shape key> | <wt>:<cluster>:<ms> ..."
+    for ln in lines:                                   # "<shape key> | <wt>:<ms> ..."
         key, table = ln.split(" | ")
         cands = [tuple(map(float, c.split(":"))) for c in table.split()]
-        assert key.startswith("tacaw-tune-v1") and cands and all(c[0] % 8 == 0 and c[2] > 0 for c in cands)
-    # a fixed cluster size is honoured; only the energy tile is tuned
-    with TacawPlan([stream_config(s) for s in SPECS], precision="split_bf16", tune="", tc_cluster=1) as plan:
+        assert key.startswith("tacaw-tune-v2") and cands and all(c[0] % 8 == 0 and c[1] > 0 for c in cands)
+    # a fixed energy tile is honoured
+    with TacawPlan([stream_config(s) for s in SPECS], precision="split_bf16", tune="", tc_omega_tile=48) as plan:
         info = plan.info()
-    assert info["tc_cluster"] == 1 and info["tuned_streams"] == len(SPECS)
+    assert info["omega_tile"] == 48 and info["tuned_streams"] == len(SPECS)

@@ -21,7 +21,7 @@ from tests.helpers import oracle_kw, stream_config
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "split_bf16": 3e-5, "split_inplace": 3e-5}
+TOL = {"fp32": 1e-5, "split_bf16": 1e-5, "split_inplace": 1e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)

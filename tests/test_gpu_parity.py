@@ -1,9 +1,12 @@
 """GPU path vs the FP64 oracle, element by element, through the C ABI.
 
 Tolerances (max |GPU - oracle| / max |oracle|, per output):
-  FP32 CUDA-core path:   1e-5 of peak intensity (and of peak spectrum)
-  split-BF16 tensor path: TOL_SPLIT, the measured bound of hi*hi + hi*lo + lo*hi with FP32
-                          accumulation (each operand carries ~2^-17 relative error).
+  FP32 CUDA-core path:    1e-5 of peak intensity (and of peak spectrum)
+  split tensor-core path: the same 1e-5 (TOL_SPLIT): hi*hi + hi*lo + lo*hi with FP32 accumulation
+                          in tensor memory, hi*hi drained into FP32 registers every 512 frames
+                          (each operand carries ~2^-17 relative error; measured 2-7e-6 on the
+                          realistic, batched and thick workloads), so the split path is held to the
+                          FP32 path's accuracy.
 """
 import zlib
 
@@ -18,7 +21,7 @@ from tests.helpers import oracle_kw, rel_err_peak, run_gpu
 pytestmark = pytest.mark.gpu
 
 TOL_FP32 = 1e-5
-TOL_SPLIT = 3e-5
+TOL_SPLIT = 1e-5
 TOL = {"fp32": TOL_FP32, "split_bf16": TOL_SPLIT, "split_inplace": TOL_SPLIT}
 
 
@@ -88,6 +91,14 @@ CASES = {
 def test_edge_cases(name, precision):
     spec, pushes, k_stage = CASES[name]
     fr = random_frames(spec.P, spec.T, spec.Ky, spec.Kx, seed=zlib.crc32(name.encode()) % 1000)
+    if precision == "split_inplace" and name == "ragged":
+        # 105 rows: an odd row count cannot be read in place (16-byte row copies); the plan is refused
+        from paper_2607_02236_gb300 import TacawError
+        from paper_2607_02236_gb300.tacaw import ERR_UNSUPPORTED
+        with pytest.raises(TacawError) as ei:
+            run_gpu(spec, fr, "split_bf16", frames_in_place=True, pushes=pushes, k_stage=k_stage)
+        assert ei.value.status == ERR_UNSUPPORTED
+        return
     out, ref, e = check(spec, fr, precision, pushes=pushes, k_stage=k_stage)
     if k_stage:
         assert out["info"]["flushes"] > 1
@@ -188,56 +199,37 @@ def test_errors_overflow_and_state():
         plan.finalize(I)
 
 
-TILINGS = [(1, 1, 0, 8, ""), (1, 2, 0, 16, ""), (2, 1, 0, 32, ""), (2, 2, 0, 16, ""), (3, 1, 0, 8, ""),
-           (3, 2, 0, 32, ""), (3, 4, 0, 32, ""), (3, 4, 16, 16, ""), (3, 2, 24, 8, ""), (1, 2, 200, 16, ""),
-           (2, 4, 128, 32, "")]
-
-
-@pytest.mark.parametrize("acc,cluster,wt,bf,mode", TILINGS + [(3, 1, 0, 32, "in_place"), (2, 1, 0, 16, "in_place"),
-                                                             (1, 1, 0, 8, "in_place"), (1, 1, 200, 16, "in_place")])
-def test_tensor_core_tilings(acc, cluster, wt, bf, mode):
-    """Every accumulator split / multicast cluster / energy-tile width / staging row width gives
-    the oracle's result (T=168 is not a multiple of 32: the last block has a zeroed tail)."""
-    spec = StreamSpec(P=2, Kx=64, Ky=48, T=168, Tc=40, n_omega=150, E_max_meV=120.0, window="hann", n_modes=6,
-                      noise=1e-3, detectors=(Detector("circular", 0, 0, -1, 6.0),))
-    fr = frames.frames(spec, 8, 0, spec.T)
-    out, ref, e = check(spec, fr, "split_inplace" if mode else "split_bf16", tc_accumulators=acc,
-                        tc_cluster=cluster, tc_omega_tile=wt, tc_block_frames=bf)
-    info = out["info"]
-    assert (info["tc_accumulators"], info["tc_cluster"], info["tc_block_frames"]) == (acc, cluster, bf)
-
-
-@pytest.mark.parametrize("acc,wt,bf,pair", [(3, 0, 32, 1), (3, 0, 16, 1), (2, 128, 16, 1), (1, 64, 8, 1),
-                                             (3, 48, 32, 1), (2, 0, 8, 1), (3, 0, 32, 2), (2, 128, 16, 2),
-                                             (1, 64, 8, 2), (3, 48, 32, 2)])
-def test_cta_pair_tilings(acc, wt, bf, pair):
-    """CTA-pair MMAs (256 rows over a cluster of two SMs, twiddle rows split between them): 31
-    row tiles (odd: the last pair has an all-padding tile), ragged rows, ragged frames."""
-    spec = StreamSpec(P=3, Kx=36, Ky=36, T=168, Tc=40, n_omega=150, E_max_meV=120.0, window="hann", n_modes=6,
-                      noise=1e-3, detectors=(Detector("circular", 0, 0, -1, 6.0),))
-    fr = frames.frames(spec, 9, 0, spec.T)
-    out, ref, e = check(spec, fr, "split_bf16", tc_accumulators=acc, tc_omega_tile=wt, tc_block_frames=bf,
-                        tc_pair=pair)
-    info = out["info"]
-    assert (info["tc_accumulators"], info["tc_pair"], info["tc_cluster"], info["tc_block_frames"]) == (acc, pair, 2, bf)
-
-
-@pytest.mark.parametrize("form", [1, 2])
-@pytest.mark.parametrize("drain,wt,bf,k_stage", [(32, 0, 8, 0), (64, 0, 32, 0), (1024, 0, 16, 0), (16, 112, 16, 0),
-                                                 (24, 40, 8, 0), (32, 0, 32, 64), (64, 72, 16, 96)])
-def test_drained_accumulator_tilings(drain, wt, bf, k_stage, form):
-    """Drained form: one double-buffered accumulator emptied into FP32 registers every `drain`
-    frames (chunks that do not divide the flush, a single chunk, the widest 112-energy tile,
-    several flushes on top of the cross-flush accumulators); 31 ragged row tiles, T=168.
-    form 2: only hi*hi is drained, the small products accumulate apart for the whole tile."""
+@pytest.mark.parametrize("wt,bf,drain,k_stage", [(0, 8, 0, 0), (0, 16, 0, 0), (0, 32, 0, 0), (16, 16, 0, 0),
+                                                 (24, 8, 0, 0), (112, 16, 0, 0), (40, 32, 0, 0), (0, 8, 32, 0),
+                                                 (0, 32, 64, 0), (0, 16, 1024, 0), (112, 16, 16, 0),
+                                                 (40, 8, 24, 0), (0, 32, 32, 64), (72, 16, 64, 96)])
+def test_staged_tilings(wt, bf, drain, k_stage):
+    """Staged split path at every energy-tile width (16 .. 112 energies, a narrower last tile),
+    staging row width (8, 16, 32 frames) and drain length (chunks that do not divide the flush, a
+    single chunk, several flushes on top of the cross-flush accumulators): 31 ragged row tiles,
+    T = 168 (not a multiple of 32: the last block has a zeroed tail)."""
     spec = StreamSpec(P=3, Kx=36, Ky=36, T=168, Tc=40, n_omega=150, E_max_meV=120.0, window="hann", n_modes=6,
                       noise=1e-3, detectors=(Detector("circular", 0, 0, -1, 6.0),))
     fr = frames.frames(spec, 10, 0, spec.T)
     out, ref, e = check(spec, fr, "split_bf16", tc_drain_frames=drain, tc_omega_tile=wt, tc_block_frames=bf,
-                        k_stage=k_stage, tc_accumulators=form)
+                        k_stage=k_stage)
     info = out["info"]
-    assert info["tc_drain_frames"] == max(bf, drain // bf * bf) and info["tc_accumulators"] == form
-    assert info["tc_cluster"] == 1 and info["tc_block_frames"] == bf
+    assert info["tc_drain_frames"] == max(bf, (drain or 512) // bf * bf)
+    assert info["tc_block_frames"] == bf and info["frames_in_place"] == 0
+    if wt:
+        assert info["omega_tile"] == wt
+
+
+@pytest.mark.parametrize("wt,drain", [(0, 0), (80, 64), (40, 32), (24, 1024)])
+def test_inplace_tilings(wt, drain):
+    """Pushed frames read in place by the contraction (operand A converted into tensor memory):
+    energy-tile widths up to the in-place limit of 80, drain lengths, T = 168."""
+    spec = StreamSpec(P=2, Kx=64, Ky=48, T=168, Tc=40, n_omega=150, E_max_meV=120.0, window="hann", n_modes=6,
+                      noise=1e-3, detectors=(Detector("circular", 0, 0, -1, 6.0),))
+    fr = frames.frames(spec, 8, 0, spec.T)
+    out, ref, e = check(spec, fr, "split_inplace", tc_omega_tile=wt, tc_drain_frames=drain)
+    info = out["info"]
+    assert info["frames_in_place"] == 1 and info["tc_block_frames"] == 32
 
 
 @pytest.mark.parametrize("precision", ["fp32", "split_bf16"])
