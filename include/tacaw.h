@@ -218,6 +218,8 @@ typedef struct {
     int accum;                 /* tacaw_accum in use (TACAW_ACC_AUTO resolved at creation) */
     int64_t flush_launches;    /* contraction launches since creation (one grouped launch over
                                   several streams counts once) */
+    int64_t aperture_pixels;   /* first stream: ROI pixels inside any detector (the rows the
+                                  adjoint recomputes Psi on) */
 } tacaw_plan_info;
 
 /* Creates a plan: validates the descriptor, sizes and allocates device memory
@@ -306,6 +308,16 @@ tacaw_status tacaw_reset(tacaw_plan_t plan, void *stream);
 /* Fills *info.                                                                          */
 tacaw_status tacaw_plan_get_info(tacaw_plan_t plan, tacaw_plan_info *info);
 
+/* Bounded device waits.  Every wait of the tensor-core contraction kernels on a pipeline event
+ * (operands landed, a stage or an accumulator freed) gives up after limit_ns nanoseconds of
+ * the GPU's global timer; the launch then stops early (its copies in flight are waited for and
+ * its tensor memory freed, under the default limit), the error word is set, and the next
+ * waiting call (tacaw_finalize, tacaw_check_errors, tacaw_backward) returns TACAW_ERR_TIMEOUT
+ * and poisons the plan.  0 restores the default of 4 s; other values are raised to at least
+ * 1000 ns.  A limit shorter than a tile's work (tens of microseconds) makes a wait run out on
+ * purpose, which is how the timeout path is tested without a fault.  Applies to later launches. */
+tacaw_status tacaw_set_wait_limit_ns(tacaw_plan_t plan, uint64_t limit_ns);
+
 /* Kernel timing: when enable != 0, CUDA events are recorded around every contraction
  * (flush) launch on the launching stream; tacaw_kernel_time_ms returns the summed
  * milliseconds and the launch count since the last call with reset != 0.  Reading the
@@ -330,12 +342,16 @@ tacaw_status tacaw_flush_trace(tacaw_plan_t plan, unsigned long long *host_out, 
  * device budget, real-time loops where cudaMalloc/cudaFree would synchronise the device,
  * hosts that only hand over raw device pointers.
  * Apertures follow tacaw_detector (MASK weights are read back from the device during the
- * call).  Their (pixel, weight) lists go into one fixed device array that the library holds
- * on every device that loads it, until the process exits: at most 2^20 pixel entries summed
- * over all detectors and at most 1024 detectors; a larger request returns
- * TACAW_ERR_INVALID_ARG before any device work.  The first call on a device looks up that
- * array's address, so make it before any stream capture.  Every call reuses the same array:
- * calls whose work overlaps on the GPU (other streams or threads) race, so serialise them.
+ * call, after the caller's earlier work on `stream`).  Their (pixel, weight) lists go into one
+ * fixed device array that the library holds on every device that loads it, until the process
+ * exits: at most 2^20 pixel entries summed over all detectors and at most 1024 detectors; a
+ * larger request returns TACAW_ERR_INVALID_ARG before any device work.  The first call on a
+ * device (and the first after its context was made again, e.g. after cudaDeviceReset) looks up
+ * that array's address.  Every call reuses the same array: calls whose work overlaps on the GPU
+ * (other streams or threads) race, so serialise them.  The lists are copied from host memory on
+ * `stream`, so the call is refused (INVALID_ARG) while `stream` is capturing a graph.  d_I, d_S
+ * and mask weights must be device, managed or mapped pinned host memory (INVALID_ARG otherwise,
+ * before any work is enqueued); kx * ky must stay below 2^31.
  * d_S: float32 [p][d][j].  Enqueued on `stream`; returns without waiting for the kernel.  */
 tacaw_status tacaw_detector_spectra_noalloc(const float *d_I, int n_probes, int n_omega, int kx, int ky,
                                             const tacaw_detector *detectors, int n_detectors, float *d_S,

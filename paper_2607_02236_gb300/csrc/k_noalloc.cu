@@ -12,12 +12,14 @@
 // the library, held until exit) and keeps the last call's lists: calls whose work
 // overlaps on the GPU (different streams, or threads) race on it and must be serialised
 // by the caller.  Nothing in it is accumulated, so nothing needs clearing between calls.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "../../include/tacaw.h"
@@ -34,10 +36,41 @@ constexpr size_t kWords = 2 * (size_t)kMaxEntries + kMaxDetectors + 1;
 // then kMaxDetectors + 1 list offsets.  8 MiB + 4 KiB per device.
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kWords];
 
+// The array's device address, looked up once per device and context: a context torn down and
+// made again (cudaDeviceReset, then new work on the device) gets a new id and a new lookup.
 std::mutex g_mu;
 void *g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of the array on the current device, looked up once per device.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Id of the calling thread's current context (0 if the driver does not report one).  Called with
+// g_mu held.
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+        looked = true;
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_cur && get_id && get_cur(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS) return id;
+    return 0;
+}
+
+// Device address of the array on the current device.  The first call on a device (and the
+// first after its context was made again) looks it up with cudaGetSymbolAddress.
 tacaw_status scratch_address(uint32_t **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -46,7 +79,8 @@ tacaw_status scratch_address(uint32_t **out) {
         return TACAW_ERR_CUDA;
     }
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_ptr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -57,6 +91,7 @@ tacaw_status scratch_address(uint32_t **out) {
             return TACAW_ERR_CUDA;
         }
         g_scratch_ptr[dev] = p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = static_cast<uint32_t *>(g_scratch_ptr[dev]);
     return TACAW_OK;
@@ -67,11 +102,8 @@ tacaw_status bad(const char *msg) {
     return TACAW_ERR_INVALID_ARG;
 }
 
-}  // namespace
-
-extern "C" tacaw_status tacaw_detector_spectra_noalloc(const float *d_I, int n_probes, int n_omega, int kx, int ky,
-                                                       const tacaw_detector *detectors, int n_detectors,
-                                                       float *d_S, void *stream) {
+tacaw_status spectra(const float *d_I, int n_probes, int n_omega, int kx, int ky, const tacaw_detector *detectors,
+                     int n_detectors, float *d_S, cudaStream_t cs) {
     if (!d_I || !d_S) return bad("tacaw_detector_spectra_noalloc: d_I and d_S must not be NULL");
     if (n_probes < 1 || n_omega < 1 || kx < 1 || ky < 1)
         return bad("tacaw_detector_spectra_noalloc: n_probes, n_omega, kx, ky must be >= 1");
@@ -82,8 +114,22 @@ extern "C" tacaw_status tacaw_detector_spectra_noalloc(const float *d_I, int n_p
                  n_detectors, kMaxDetectors);
         return bad(buf);
     }
-    if (n_probes > 65535 || n_detectors > 65535) return bad("tacaw_detector_spectra_noalloc: grid limits exceeded");
     const int64_t npix = (int64_t)kx * ky;
+    if (npix > (int64_t)INT32_MAX) return bad("tacaw_detector_spectra_noalloc: kx * ky exceeds 2^31 - 1 pixels");
+    if (n_probes > 65535) return bad("tacaw_detector_spectra_noalloc: more than 65535 probes");
+    // the lists are copied from host memory on `stream`: a graph capturing it could not replay them
+    cudaStreamCaptureStatus capt = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(cs, &capt) != cudaSuccess) {
+        cudaGetLastError();
+        tacaw::set_last_error("tacaw_detector_spectra_noalloc: cudaStreamIsCapturing failed on the stream");
+        return TACAW_ERR_CUDA;
+    }
+    if (capt != cudaStreamCaptureStatusNone)
+        return bad("tacaw_detector_spectra_noalloc: the stream is capturing a graph; this call copies host-side "
+                   "aperture lists and is refused inside a capture");
+    // d_I is read and d_S written by the kernel: device, managed or mapped pinned host memory only
+    if (tacaw::check_device_readable(d_I, "d_I", cs) != TACAW_OK) return TACAW_ERR_INVALID_ARG;
+    if (tacaw::check_device_readable(d_S, "d_S", cs) != TACAW_OK) return TACAW_ERR_INVALID_ARG;
     // aperture lists on the host (same conventions as tacaw_plan_create)
     std::vector<uint32_t> idx, wts;
     std::vector<uint32_t> off(n_detectors + 1, 0);
@@ -94,9 +140,13 @@ extern "C" tacaw_status tacaw_detector_spectra_noalloc(const float *d_I, int n_p
             return bad("tacaw_detector_spectra_noalloc: bad detector kind");
         if (t.kind == TACAW_DET_MASK) {
             if (!t.d_mask) return bad("tacaw_detector_spectra_noalloc: mask pointer is NULL");
+            if (tacaw::check_device_readable(t.d_mask, "d_mask", cs) != TACAW_OK) return TACAW_ERR_INVALID_ARG;
             hmask.resize(npix);
-            cudaError_t e = cudaMemcpy(hmask.data(), t.d_mask, sizeof(float) * npix, cudaMemcpyDeviceToHost);
+            // ordered after the caller's earlier work on `stream` that may write the mask
+            cudaError_t e = cudaMemcpyAsync(hmask.data(), t.d_mask, sizeof(float) * npix, cudaMemcpyDeviceToHost, cs);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
             if (e != cudaSuccess) {
+                cudaGetLastError();
                 tacaw::set_last_error("tacaw_detector_spectra_noalloc: reading a mask failed");
                 return TACAW_ERR_CUDA;
             }
@@ -131,15 +181,15 @@ extern "C" tacaw_status tacaw_detector_spectra_noalloc(const float *d_I, int n_p
     uint32_t *scr = nullptr;
     tacaw_status st = scratch_address(&scr);
     if (st != TACAW_OK) return st;
-    cudaStream_t cs = static_cast<cudaStream_t>(stream);
     const size_t n = idx.size();
     cudaError_t e = cudaSuccess;
-    // pageable host sources: each call returns once the host data has been taken
+    // pageable host sources: each copy returns once the host data has been taken
     if (n) e = cudaMemcpyAsync(scr, idx.data(), n * 4, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess && n) e = cudaMemcpyAsync(scr + kMaxEntries, wts.data(), n * 4, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(scr + 2 * (size_t)kMaxEntries, off.data(), off.size() * 4, cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) {
+        cudaGetLastError();
         tacaw::set_last_error("tacaw_detector_spectra_noalloc: copying the aperture lists failed");
         return TACAW_ERR_CUDA;
     }
@@ -159,4 +209,17 @@ extern "C" tacaw_status tacaw_detector_spectra_noalloc(const float *d_I, int n_p
         return TACAW_ERR_CUDA;
     }
     return TACAW_OK;
+}
+
+}  // namespace
+
+extern "C" tacaw_status tacaw_detector_spectra_noalloc(const float *d_I, int n_probes, int n_omega, int kx, int ky,
+                                                       const tacaw_detector *detectors, int n_detectors,
+                                                       float *d_S, void *stream) {
+    try {
+        return spectra(d_I, n_probes, n_omega, kx, ky, detectors, n_detectors, d_S, static_cast<cudaStream_t>(stream));
+    } catch (const std::bad_alloc &) {
+        tacaw::set_last_error("tacaw_detector_spectra_noalloc: host memory for the aperture lists ran out");
+        return TACAW_ERR_OOM;
+    }
 }

@@ -101,21 +101,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait.  Gives up after kWaitLimitNs, or early when *abort_flag is set (if given).
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+// Bounded wait.  Gives up after limit_ns, or early when *abort_flag is set (if given).  Waits
+// for work that always completes (copies in flight, issued MMAs) keep the default limit.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, uint64_t limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
         if (abort_flag && *abort_flag) return false;
-        if (globaltimer() - t0 > kWaitLimitNs) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     }
 }
 // Warp-uniform bounded wait: lane 0 waits, every lane gets its verdict (so no lane of the warp
 // can leave a loop that the others stay in), and the warp synchronises for memory ordering.
-__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                               uint64_t limit_ns = kWaitLimitNs) {
     int ok = 1;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, limit_ns) ? 1 : 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     __syncwarp();
     return ok != 0;
@@ -341,6 +343,8 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
     tc_fence_after();
     const uint32_t tmem = sh->tmem_addr;
     volatile int *abort_flag = &sh->abort_flag;
+    // pipeline waits give up after the plan's limit (default 4 s); see mbar_wait
+    const uint64_t wait_ns = g.e[0].args.wait_ns ? g.e[0].args.wait_ns : kWaitLimitNs;
     if (trace && threadIdx.x == 0) trace[1] = globaltimer();
 
     // Ring position: slot s and its use parity advance by one per staging block, across tiles
@@ -368,7 +372,7 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
                 const uint8_t *pBlo = static_cast<const uint8_t *>(en.args.B_lo) + b0;
                 const size_t a_step = (size_t)en.args.a_rows * RB, b_step = (size_t)en.args.b_rows * RB;
                 for (int kb = 0; kb < en.args.n_kb; ++kb) {
-                    if (!mbar_wait(smem_u32(&sh->empty[s]), ph ^ 1u, abort_flag)) {
+                    if (!mbar_wait(smem_u32(&sh->empty[s]), ph ^ 1u, abort_flag, wait_ns)) {
                         if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_EMPTY);
                         *abort_flag = 1;
                         break;
@@ -423,7 +427,7 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
                 const uint32_t id = idesc_f32acc(kMTile, N, en.args.f16);
                 if (tiles > 0) {
                     // the previous tile's H and S must be in registers before they are reused
-                    if (!mbar_wait(smem_u32(&sh->chunk_free[1]), tph, abort_flag)) {
+                    if (!mbar_wait(smem_u32(&sh->chunk_free[1]), tph, abort_flag, wait_ns)) {
                         if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
                         *abort_flag = 1;
                         break;
@@ -433,7 +437,7 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
                 }
                 int kc = 0;                           // staging block inside the chunk
                 for (int kb = 0; kb < n_kb; ++kb) {
-                    if (!mbar_wait(smem_u32(&sh->full[s]), ph, abort_flag)) {
+                    if (!mbar_wait(smem_u32(&sh->full[s]), ph, abort_flag, wait_ns)) {
                         if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_FULL);
                         *abort_flag = 1;
                         stop = true;
@@ -454,7 +458,7 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
                     }
                     if (kc == 0 && kb > 0) {
                         // the previous chunk of H must be drained before this chunk overwrites it
-                        if (!mbar_wait(smem_u32(&sh->chunk_free[0]), hph, abort_flag)) {
+                        if (!mbar_wait(smem_u32(&sh->chunk_free[0]), hph, abort_flag, wait_ns)) {
                             if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
                             *abort_flag = 1;
                             stop = true;
@@ -508,7 +512,7 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
 #pragma unroll
             for (int i = 0; i < kDrainCols; ++i) sum[i] = 0.f;
             for (int lc = 0; lc + 1 < n_chunks; ++lc, ++hc) {
-                if (!mbar_wait(smem_u32(&sh->chunk_full[0]), (uint32_t)(hc & 1), abort_flag)) {
+                if (!mbar_wait(smem_u32(&sh->chunk_full[0]), (uint32_t)(hc & 1), abort_flag, wait_ns)) {
                     if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
                     *abort_flag = 1;
                     ok = false;
@@ -521,7 +525,7 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
                 if (lane == 0) mbar_arrive(smem_u32(&sh->chunk_free[0]));
             }
             if (!ok) break;
-            if (!mbar_wait(smem_u32(&sh->chunk_full[1]), (uint32_t)(tiles & 1), abort_flag)) {
+            if (!mbar_wait(smem_u32(&sh->chunk_full[1]), (uint32_t)(tiles & 1), abort_flag, wait_ns)) {
                 if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
                 *abort_flag = 1;
                 ok = false;
@@ -634,12 +638,12 @@ __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.
 template <int KIND>
 __device__ __forceinline__ bool ip_final(const TcInplaceArgs &g, IpShared *sh, float (&sum)[kIpCols], int t,
                                          int cnt, int h, int rr, uint32_t hbase, uint32_t sbase,
-                                         volatile int *abort_flag) {
+                                         volatile int *abort_flag, uint64_t wait_ns) {
     const TcPlanArgs &a = g.a;
     const TcDirectArgs &d = g.d;
     const int lane = threadIdx.x & 31;
-    if (!mbar_wait_warp(smem_u32(&sh->sums_full[cnt & 1]), (uint32_t)((cnt >> 1) & 1), abort_flag) ||
-        !mbar_wait_warp(smem_u32(&sh->chunk_full[1]), (uint32_t)(cnt & 1), abort_flag)) {
+    if (!mbar_wait_warp(smem_u32(&sh->sums_full[cnt & 1]), (uint32_t)((cnt >> 1) & 1), abort_flag, wait_ns) ||
+        !mbar_wait_warp(smem_u32(&sh->chunk_full[1]), (uint32_t)(cnt & 1), abort_flag, wait_ns)) {
         if (lane == 0 && !*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
         *abort_flag = 1;
         return false;
@@ -732,6 +736,7 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
     tc_fence_after();
     const uint32_t tmem = sh->tmem_addr;
     volatile int *abort_flag = &sh->abort_flag;
+    const uint64_t wait_ns = a.wait_ns ? a.wait_ns : kWaitLimitNs;
     if (trace && threadIdx.x == 0) trace[1] = globaltimer();
 
     if (warp == 0) {
@@ -750,7 +755,7 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
                 const int f = kb * BF + lane;
                 const float2 *fp = f < d.n_frames ? d.frame_ptr[f] + off : nullptr;
                 const int nfr = min(BF, d.n_frames - kb * BF);
-                if (!mbar_wait_warp(smem_u32(&sh->raw_empty[r]), rph ^ 1u, abort_flag)) {
+                if (!mbar_wait_warp(smem_u32(&sh->raw_empty[r]), rph ^ 1u, abort_flag, wait_ns)) {
                     if (lane == 0 && !*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
                     *abort_flag = 1;
                     stop = true;
@@ -815,7 +820,7 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
                 const uint8_t *pBlo = static_cast<const uint8_t *>(a.B_lo) +
                                       ((size_t)a.kbB0 * (size_t)a.b_rows + (size_t)wtile * N) * RB;
                 for (int kb = 0; kb < a.n_kb; ++kb) {
-                    if (!mbar_wait(smem_u32(&sh->empty[s]), ph ^ 1u, abort_flag)) {
+                    if (!mbar_wait(smem_u32(&sh->empty[s]), ph ^ 1u, abort_flag, wait_ns)) {
                         if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_EMPTY);
                         *abort_flag = 1;
                         stop = true;
@@ -853,7 +858,7 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
             const int cb = a.drain_kb;
             for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x, ++tiles) {
                 if (tiles > 0) {
-                    if (!mbar_wait(smem_u32(&sh->chunk_free[1]), tph, abort_flag)) {
+                    if (!mbar_wait(smem_u32(&sh->chunk_free[1]), tph, abort_flag, wait_ns)) {
                         if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
                         *abort_flag = 1;
                         break;
@@ -863,7 +868,7 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
                 }
                 int kc = 0;
                 for (int kb = 0; kb < a.n_kb; ++kb) {
-                    if (!mbar_wait(smem_u32(&sh->full[s]), ph, abort_flag)) {
+                    if (!mbar_wait(smem_u32(&sh->full[s]), ph, abort_flag, wait_ns)) {
                         if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
                         *abort_flag = 1;
                         stop = true;
@@ -882,7 +887,7 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
                         mma_bf16_ts(accS, aL + 8u * ks, dBhi0 + adv, id, 1u);
                     }
                     if (kc == 0 && kb > 0) {
-                        if (!mbar_wait(smem_u32(&sh->chunk_free[0]), hph, abort_flag)) {
+                        if (!mbar_wait(smem_u32(&sh->chunk_free[0]), hph, abort_flag, wait_ns)) {
                             if (!*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
                             *abort_flag = 1;
                             stop = true;
@@ -949,8 +954,8 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
                     mu = valid ? d.mu_hat[m] : make_float2(0.f, 0.f);
                     sr = si = cr = ci = 0.f;
                 }
-                if (!mbar_wait_warp(smem_u32(&sh->raw_full[r]), rph, abort_flag) ||
-                    !mbar_wait_warp(smem_u32(&sh->empty[s]), ph ^ 1u, abort_flag)) {
+                if (!mbar_wait_warp(smem_u32(&sh->raw_full[r]), rph, abort_flag, wait_ns) ||
+                    !mbar_wait_warp(smem_u32(&sh->empty[s]), ph ^ 1u, abort_flag, wait_ns)) {
                     if (lane == 0 && !*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_FULL);
                     *abort_flag = 1;
                     break;
@@ -1006,14 +1011,14 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
             // the previous tile's final, once this tile's first `defer` blocks keep the MMAs
             // busy (or after the last tile)
             if (fin_t >= 0 && (!have || kb + 1 == D)) {
-                if (!ip_final<KIND>(g, sh, sum, fin_t, fin_cnt, h, rr, hbase, sbase, abort_flag)) break;
+                if (!ip_final<KIND>(g, sh, sum, fin_t, fin_cnt, h, rr, hbase, sbase, abort_flag, wait_ns)) break;
                 fin_t = -1;
             }
             if (!have) break;
             // the H chunk that ended with block kb - 1 (drained one block late, so this block's
             // small products run on the tensor pipe meanwhile)
             if (kb >= 1 && kb % cb == 0) {
-                if (!mbar_wait_warp(smem_u32(&sh->chunk_full[0]), (uint32_t)(hc & 1), abort_flag)) {
+                if (!mbar_wait_warp(smem_u32(&sh->chunk_full[0]), (uint32_t)(hc & 1), abort_flag, wait_ns)) {
                     if (lane == 0 && !*abort_flag) atomicOr(a.err, DEVERR_TIMEOUT_TMEM);
                     *abort_flag = 1;
                     break;

@@ -142,6 +142,7 @@ struct tacaw_plan_s {
     int bf = 8;                // frames per staged operand row (split path)
     bool in_place = false;     // the contraction reads pushed frames directly (in-place kernel)
     int tc_max_ctas = 0;       // persistent contraction grids: at most this many CTAs (0: all SMs)
+    uint64_t wait_ns = 0;      // tensor-core pipeline waits give up after this (0: the kernels' default)
     // with a capped grid the last flush runs on a highest-priority stream of the plan, forked
     // from and joined back to the caller's stream, so that its CTAs take SMs ahead of other
     // streams' queued work
@@ -344,6 +345,7 @@ TcPlanArgs tc_args(tacaw_plan_s *p, const Stream &s, const EpiArgs &e) {
     a.a_rows = s.M_pad;
     a.b_rows = 2 * s.Nw_pad;
     a.max_ctas = p->tc_max_ctas;
+    a.wait_ns = p->wait_ns;
     a.f16 = p->f16;
     a.err = p->d_err;
     a.trace = nullptr;
@@ -748,6 +750,16 @@ tacaw_status check_kernel_memory(const void *ptr, const char *what, bool allow_h
     }
     return TACAW_OK;
 }
+
+}  // namespace
+
+namespace tacaw {
+int check_device_readable(const void *ptr, const char *what, cudaStream_t st) {
+    return check_kernel_memory(ptr, what, true, st);
+}
+}  // namespace tacaw
+
+namespace {
 
 tacaw_status read_device_error(tacaw_plan_s *p, cudaStream_t st) {
     CU_CHECK(p, cudaStreamSynchronize(st), "cudaStreamSynchronize");
@@ -1367,6 +1379,14 @@ tacaw_status tacaw_plan_get_info(tacaw_plan_t p, tacaw_plan_info *info) {
     info->tc_drain_frames = p->prec == TACAW_PREC_SPLIT_BF16 ? p->drain_kb * p->bf : 0;
     info->accum = p->accum;
     info->flush_launches = p->flush_launches;
+    info->aperture_pixels = p->s.empty() ? 0 : p->s[0].n_adj;
+    return TACAW_OK;
+}
+
+tacaw_status tacaw_set_wait_limit_ns(tacaw_plan_t p, uint64_t limit_ns) {
+    tacaw_status c = check_plan(p);
+    if (c != TACAW_OK) return c;
+    p->wait_ns = limit_ns == 0 ? 0 : std::max<uint64_t>(limit_ns, 1000);
     return TACAW_OK;
 }
 

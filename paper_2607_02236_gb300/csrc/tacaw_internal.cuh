@@ -288,6 +288,7 @@ struct TcPlanArgs {
     int f16;                   // operands are fp16 pieces (split-FP16 path) instead of bf16
     unsigned long long *trace; // null, or kTraceWords globaltimer stamps per CTA (phase boundaries)
     uint32_t *err;
+    uint64_t wait_ns;          // pipeline waits give up after this many ns (0: the default 4 s)
 };
 // In-place operand A: the contraction reads the pushed frames of this flush directly.
 struct TcDirectArgs {
@@ -357,6 +358,10 @@ cudaError_t launch_aperture(const ApertureArgs &a, cudaStream_t st);
 
 // records the calling thread's message for tacaw_last_error()
 void set_last_error(const char *msg);
+// TACAW_OK if kernels may read and write ptr (device, managed, or pinned host memory mapped at
+// the same address); else TACAW_ERR_INVALID_ARG with a message naming `what`.  Not checked while
+// st is capturing a graph.
+int check_device_readable(const void *ptr, const char *what, cudaStream_t st);
 
 struct AdjointArgs {
     const float2 *frames;      // pushed layout, whole segment

@@ -28,7 +28,7 @@ EXPORTS = ["tacaw_plan_create", "tacaw_push_frames", "tacaw_finalize", "tacaw_ou
            "tacaw_backward", "tacaw_reset", "tacaw_plan_get_info", "tacaw_set_timing",
            "tacaw_kernel_time_ms", "tacaw_destroy", "tacaw_last_error", "tacaw_version",
            "tacaw_detector_spectra_noalloc", "tacaw_flush_trace", "tacaw_finalize_async",
-           "tacaw_check_errors", "tacaw_set_log_callback"]
+           "tacaw_check_errors", "tacaw_set_log_callback", "tacaw_set_wait_limit_ns"]
 
 
 class TacawError(RuntimeError):
@@ -66,7 +66,8 @@ class CPlanInfo(ctypes.Structure):
                 ("I_elems", c_int64), ("S_elems", c_int64), ("flushes", c_int64), ("omega_tile", c_int),
                 ("stages", c_int), ("kernel_launches", c_int64), ("tc_block_frames", c_int),
                 ("frames_in_place", c_int), ("tc_drain_frames", c_int), ("tuned_streams", c_int),
-                ("tune_candidates", c_int), ("tune_ms", c_double), ("accum", c_int), ("flush_launches", c_int64)]
+                ("tune_candidates", c_int), ("tune_ms", c_double), ("accum", c_int), ("flush_launches", c_int64),
+                ("aperture_pixels", c_int64)]
 
 
 _lib = None
@@ -90,6 +91,7 @@ def lib():
     L.tacaw_reset.argtypes = [c_void_p, c_void_p]
     L.tacaw_plan_get_info.argtypes = [c_void_p, POINTER(CPlanInfo)]
     L.tacaw_set_timing.argtypes = [c_void_p, c_int]
+    L.tacaw_set_wait_limit_ns.argtypes = [c_void_p, ctypes.c_uint64]
     L.tacaw_kernel_time_ms.argtypes = [c_void_p, POINTER(c_double), POINTER(c_int64), c_int]
     L.tacaw_destroy.argtypes = [c_void_p]
     L.tacaw_flush_trace.argtypes = [c_void_p, c_void_p, c_int64, POINTER(c_int64)]
@@ -246,6 +248,10 @@ class TacawPlan:
         i = CPlanInfo()
         _check(lib().tacaw_plan_get_info(self._h, ctypes.byref(i)))
         return {k: getattr(i, k) for k, _ in CPlanInfo._fields_}
+
+    def set_wait_limit_ns(self, limit_ns: int):
+        """Device pipeline waits of later contraction launches give up after limit_ns (0: default)."""
+        _check(lib().tacaw_set_wait_limit_ns(self._h, int(limit_ns)))
 
     def set_timing(self, on):
         """on: False/True, or 2 to also record per-CTA phase stamps of tensor-core flushes."""

@@ -7,6 +7,12 @@ Tolerances (max |GPU - oracle| / max |oracle|, per output):
                           (each operand carries ~2^-17 relative error; measured 2-7e-6 on the
                           realistic, batched and thick workloads), so the split path is held to the
                           FP32 path's accuracy.
+  white-noise edge cases: TOL_SPLIT_NOISE = 2e-5 for the split path on random_frames inputs in
+                          test_edge_cases (no tones: every bin is an incoherent sum).  Each bf16 hi + lo
+                          operand carries up to 2^-18 relative error (the rounding of lo), so a real MAC
+                          of the three products is off by up to ~3 * 2^-18 |a||b|; over an incoherent sum
+                          the peak bin's |Psi|^2 then moves by up to ~2 * 3 * 2^-18 = 2.3e-5 of itself
+                          (measured 1.2e-5 at T = 48 and 600 energies, under 1e-5 elsewhere).
 """
 import zlib
 
@@ -22,6 +28,7 @@ pytestmark = pytest.mark.gpu
 
 TOL_FP32 = 1e-5
 TOL_SPLIT = 1e-5
+TOL_SPLIT_NOISE = 2e-5
 TOL = {"fp32": TOL_FP32, "split_bf16": TOL_SPLIT, "split_inplace": TOL_SPLIT}
 
 
@@ -39,14 +46,14 @@ def random_frames(P, T, Ky, Kx, seed=0, elastic=1.0, signal=1e-2):
     return (e + s).astype(np.complex64)
 
 
-def check(spec, fr, precision, **kw):
+def check(spec, fr, precision, tol=None, **kw):
     if precision == "split_inplace":      # pushed frames read in place by the contraction
         out = run_gpu(spec, fr, "split_bf16", frames_in_place=True, **kw)
     else:
         out = run_gpu(spec, fr, precision, **kw)
     ref = oracle.forward(fr, **oracle_kw(spec))
     eI = rel_err_peak(out["I"], ref.I)
-    tol = TOL[precision]
+    tol = TOL[precision] if tol is None else tol
     assert eI <= tol, f"I error {eI:.3g} > {tol}"
     if len(spec.detectors):
         eS = rel_err_peak(out["S"], ref.S)
@@ -99,7 +106,10 @@ def test_edge_cases(name, precision):
             run_gpu(spec, fr, "split_bf16", frames_in_place=True, pushes=pushes, k_stage=k_stage)
         assert ei.value.status == ERR_UNSUPPORTED
         return
-    out, ref, e = check(spec, fr, precision, pushes=pushes, k_stage=k_stage)
+    if precision == "split_inplace" and k_stage % 32:
+        k_stage = 32                      # in-place flushes are whole 32-frame blocks
+    out, ref, e = check(spec, fr, precision, tol=TOL_FP32 if precision == "fp32" else TOL_SPLIT_NOISE,
+                        pushes=pushes, k_stage=k_stage)
     if k_stage:
         assert out["info"]["flushes"] > 1
 
@@ -111,8 +121,9 @@ def test_streaming_flushes_match_single_flush(precision, accum):
     spec = StreamSpec(P=2, Kx=32, Ky=16, T=200, Tc=24, n_omega=70, E_max_meV=120.0, window="hann",
                       n_modes=6, detectors=(Detector("circular", 0, 0, -1, 5.0),))
     fr = frames.frames(spec, 3, 0, spec.T)
-    out, ref, e = check(spec, fr, precision, k_stage=48, accum=accum)
-    assert out["info"]["flushes"] == 5
+    k_stage = 64 if precision == "split_inplace" else 48      # in place: whole 32-frame blocks
+    out, ref, e = check(spec, fr, precision, k_stage=k_stage, accum=accum)
+    assert out["info"]["flushes"] == -(-spec.T // k_stage)
 
 
 @pytest.mark.parametrize("k_stage,expect", [(16, 2), (8, 0), (0, 2)])
