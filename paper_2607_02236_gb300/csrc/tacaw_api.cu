@@ -113,6 +113,10 @@ struct Stream {
                                                 // the stream at push time (no host copy)
     // segment state
     int pushed = 0, staged = 0, stage_start = 0, flushes = 0;
+    // a full staging ring whose flush waits for the next push of this stream (or of finalize),
+    // so that the flushes of several streams that fill up together share one launch
+    bool due = false;
+    cudaStream_t due_stream = nullptr;
     int64_t I_off = 0, S_off = 0;
 };
 
@@ -539,6 +543,32 @@ tacaw_status final_flush_grouped(tacaw_plan_s *p, float *d_I, float2 *d_Psi, cud
     return flush_grouped(p, req, st);
 }
 
+// Flushes of staged tensor-core streams are deferred while the caller pushes other streams, so
+// that streams whose rings fill in the same round of pushes share one launch (a Welch lane, an
+// in-place or an FP32 stream flushes at once).
+bool deferrable(const tacaw_plan_s *p, const Stream &s) {
+    return p->prec == TACAW_PREC_SPLIT_BF16 && !p->in_place && p->us[s.user].N <= 1;
+}
+
+// Runs every deferred flush: those pushed on `st` in one grouped launch there, any other on the
+// stream its frames were pushed on.
+tacaw_status flush_due(tacaw_plan_s *p, cudaStream_t st) {
+    std::vector<FlushReq> req;
+    for (int i = 0; i < (int)p->s.size(); ++i) {
+        Stream &s = p->s[i];
+        if (!s.due) continue;
+        s.due = false;
+        const int mode = s.flushes == 0 ? FLUSH_STORE : FLUSH_ADD;
+        if (s.due_stream == st) {
+            req.push_back(FlushReq{i, mode, nullptr, nullptr});
+        } else {
+            tacaw_status r = flush_grouped(p, {FlushReq{i, mode, nullptr, nullptr}}, s.due_stream);
+            if (r != TACAW_OK) return r;
+        }
+    }
+    return req.empty() ? TACAW_OK : flush_grouped(p, req, st);
+}
+
 // Periodic Dolph-Chebyshev window of length T: the symmetric window of M = T + 1 taps without
 // its last tap.  The symmetric taps are the inverse DFT of M samples of the response
 // T_{M-1}(x0 cos(pi k / M)), T_{M-1}(x0) = 10^(at/20), taken about the window's centre and
@@ -793,6 +823,10 @@ tacaw_status finalize_impl(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, 
     if (d_S && !d_I) return fail(TACAW_ERR_INVALID_ARG, "d_S requires d_I");
     for (auto &u : p->us)
         if (d_Psi && u.N > 1) return fail(TACAW_ERR_INVALID_ARG, "d_Psi is not available for Welch-averaged streams");
+    {
+        tacaw_status r = flush_due(p, st);   // none expected: a due stream still awaits frames
+        if (r != TACAW_OK) return r;
+    }
     // single-segment streams: their last flush (Welch lanes finished theirs during the pushes)
     if (!p->in_place)
         for (auto &s : p->s) {
@@ -868,6 +902,11 @@ tacaw_status push_internal(tacaw_plan_s *p, Stream &s, const float2 *frames, int
     g.npix = s.npix;
     g.M = s.M;
     g.base = frames;
+    if (s.due) {
+        // this stream's ring is full: its deferred flush (with any others) goes first
+        tacaw_status r = flush_due(p, st);
+        if (r != TACAW_OK) return r;
+    }
     if (s.pushed == 0 && s.d.subtract_mean) {
         CU_CHECK(p, launch_mean(g, n_frames, s.mu_hat, st), "provisional mean");
         p->launches++;
@@ -898,8 +937,16 @@ tacaw_status push_internal(tacaw_plan_s *p, Stream &s, const float2 *frames, int
         s.pushed += chunk;
         done += chunk;
         if (s.staged == s.ring && s.pushed < s.T) {
-            tacaw_status r = run_flush(p, s, s.flushes == 0 ? FLUSH_STORE : FLUSH_ADD, nullptr, nullptr, st);
-            if (r != TACAW_OK) return r;
+            if (deferrable(p, s)) {
+                s.due = true;
+                s.due_stream = st;
+                // more frames of this push follow: the ring must be emptied now
+                tacaw_status r = done < n_frames ? flush_due(p, st) : TACAW_OK;
+                if (r != TACAW_OK) return r;
+            } else {
+                tacaw_status r = run_flush(p, s, s.flushes == 0 ? FLUSH_STORE : FLUSH_ADD, nullptr, nullptr, st);
+                if (r != TACAW_OK) return r;
+            }
         }
     }
     return TACAW_OK;
@@ -1350,6 +1397,7 @@ tacaw_status tacaw_reset(tacaw_plan_t p, void *stream) {
         CU_CHECK(p, cudaMemsetAsync(s.mu_hat, 0, sizeof(float2) * s.M, st), "reset mean");
         s.pushed = s.staged = s.stage_start = s.flushes = 0;
         s.seg = s.lane;
+        s.due = false;
     }
     for (auto &u : p->us) {
         u.pushed = 0;
