@@ -433,6 +433,37 @@ def test_pixel_gradient_equals_full_gradient_on_pixels():
         assert abs(Lp - Lfull) <= 1e-10 * abs(Lfull)
 
 
+@pytest.mark.parametrize("grid", ["fft", "offgrid"])
+@pytest.mark.parametrize("mean", [True, False])
+@pytest.mark.parametrize("bose_T", [0.0, 300.0])
+@pytest.mark.parametrize("win", [("hann", 0.0), ("gauss", 7.0), ("kaiser", 3 * np.pi)])
+def test_pixel_forward_equals_full_forward_on_pixels(grid, mean, bose_T, win):
+    """forward_pixels, the checker of every sampled full-size parity test, equals the full-array
+    forward (pinned above by numpy.fft, closed forms, Wiener-Khinchin and brute force) element by
+    element: Psi and I at every pixel of every probe, with the Bose factor on and off, FFT and
+    off-grid (signed) energies, the mean removed or kept."""
+    rng = np.random.default_rng(31)
+    P, T, Ky, Kx = 2, 40, 5, 6
+    psi = rand_psi(P, T, Ky, Kx, rng) + 3.0
+    kw = dict(window_kind=win[0], window_param=win[1], dt_fs=5.0, subtract_mean=mean, bose_T_K=bose_T)
+    if grid == "fft":
+        kw["fft_bins"] = 24
+    else:
+        kw["E_meV"] = np.linspace(-37.0, 111.0, 29)
+    full = oracle.forward(psi, **kw)
+    for p in range(P):
+        Psi, I = oracle.forward_pixels(psi[p].reshape(T, -1), **kw)
+        ref_Psi = full.Psi[p].reshape(full.Psi.shape[1], -1)
+        ref_I = full.I[p].reshape(full.I.shape[1], -1)
+        np.testing.assert_allclose(Psi, ref_Psi, rtol=1e-12, atol=1e-12 * np.abs(ref_Psi).max())
+        np.testing.assert_allclose(I, ref_I, rtol=1e-12, atol=1e-12 * np.abs(ref_I).max())
+    # and per selected pixel columns (the sampled form the large tests use)
+    sel = [0, 7, 29]
+    Psi, I = oracle.forward_pixels(psi[1].reshape(T, -1)[:, sel], **kw)
+    np.testing.assert_allclose(I, full.I[1].reshape(full.I.shape[1], -1)[:, sel], rtol=1e-12,
+                               atol=1e-12 * np.abs(full.I).max())
+
+
 # ------------------------------------------------------------------------------------ Welch
 def test_welch_segment_starts_and_stride():
     """s_{n+1} = s_n + L // nu (remainder-less); whole segments only."""
