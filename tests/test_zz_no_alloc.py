@@ -46,7 +46,7 @@ def test_noalloc_spectra_match_oracle_two_calls():
     dets_b = (Detector("annular", 2, 1, 1.0, 3.0),)
     ref_a = oracle.forward(f, window_kind="hann", E_meV=E, dt_fs=5.0, detectors=list(dets_a))
     ref_b = oracle.forward(f, window_kind="hann", E_meV=E, dt_fs=5.0, detectors=list(dets_b))
-    I = torch.from_numpy(ref_a.I.astype(np.float32)).cuda()            # [P][E][ky][kx]
+    I = torch.from_numpy(np.ascontiguousarray(ref_a.I, dtype=np.float32)).cuda()   # [P][E][ky][kx]
     # first call: three geometric apertures and a weighted mask (S of the mask from its definition)
     S_mask = np.einsum("pjyx,yx->pj", ref_a.I, mask.astype(np.float64))[:, None, :]
     calls = [([DetectorConfig(d.kind, d.cx, d.cy, d.r_in, d.r_out) for d in dets_a] +
@@ -108,7 +108,7 @@ def test_noalloc_matches_oracle_after_a_plan_run():
     f, E = oracle_case(P, K, T, Nw, seed=9)
     dets = (Detector("circular", 0, 0, -1, 6.0), Detector("annular", -2, 3, 2.0, 8.0))
     ref = oracle.forward(f, window_kind="hann", E_meV=E, dt_fs=5.0, detectors=list(dets))
-    I = torch.from_numpy(ref.I.astype(np.float32)).cuda()
+    I = torch.from_numpy(np.ascontiguousarray(ref.I, dtype=np.float32)).cuda()
     for _ in range(2):
         S = torch.full((P * len(dets) * Nw,), float("nan"), dtype=torch.float32, device="cuda")
         detector_spectra_noalloc(I, P, Nw, K, K, [DetectorConfig(d.kind, d.cx, d.cy, d.r_in, d.r_out) for d in dets], S)
