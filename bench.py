@@ -41,7 +41,12 @@ FLOP_PER_CMAC_FP32 = 8
 
 # DRAM bytes per CMAC of a contraction kernel from an ncu capture, keyed by the hash of its
 # source file (code only) at capture time: reported only while the source is unchanged.
-KERNEL_TRAFFIC = {}
+KERNEL_TRAFFIC = {
+    # ncu --set full of flush_tc_drain2_kernel on `bench.py --small --no-extras` (the thick workload with
+    # 1 probe: 65536 rows, T = 8192, 1000 energies, 5.369e11 CMAC per launch): 8.589054 GB read +
+    # 0.263988 GB written per launch
+    ("6f83bdc284934e03", "flush_tc_drain2_kernel"): 1.649008e-02,
+}
 
 
 def parse(argv=None):
