@@ -39,14 +39,10 @@ UNIT = "CMAC/s"
 FLOP_PER_CMAC_SPLIT = 24      # hi*hi + hi*lo + lo*hi, each 4 real MAC (8 flop) per complex MAC
 FLOP_PER_CMAC_FP32 = 8
 
-# DRAM bytes per CMAC of a contraction kernel from an ncu capture, keyed by the hash of its
-# source file (code only) at capture time: reported only while the source is unchanged.
-KERNEL_TRAFFIC = {
-    # ncu --set full of flush_tc_drain2_kernel on `bench.py --small --no-extras` (the thick workload with
-    # 1 probe: 65536 rows, T = 8192, 1000 energies, 5.369e11 CMAC per launch): 8.589054 GB read +
-    # 0.263988 GB written per launch
-    ("6f83bdc284934e03", "flush_tc_drain2_kernel"): 1.649008e-02,
-}
+# DRAM bytes per CMAC of a contraction kernel from an ncu capture at one workload's shape, keyed by
+# the hash of the kernel's source file (code only) at capture time, the kernel and the workload:
+# reported only for that workload and while the source is unchanged.
+KERNEL_TRAFFIC = {}
 
 
 def parse(argv=None):
@@ -196,14 +192,14 @@ def file_hash(path, skip=None):
 TC_SRC = os.path.join(ROOT, "paper_2607_02236_gb300", "csrc", "k_tc_gemm.cu")
 
 
-def tensor_roofline(cmac_launch, kernel_ms, kname, launches_per_step, precision="split_bf16"):
+def tensor_roofline(cmac_launch, kernel_ms, kname, launches_per_step, precision="split_bf16", workload=None):
     """Roofline of a tensor-core contraction launch: algorithmic flops (24 per CMAC) over its
     CUDA-event duration, against the measured burst bf16 rate (fp16 has the same dense rate)."""
     peaks, src = measured_peaks()
     achieved = cmac_launch * FLOP_PER_CMAC_SPLIT / (kernel_ms * 1e-3) / 1e12
     peak = peaks.get("bf16_tflops")
     sus = peaks.get("bf16_tflops_sustained")
-    tr = KERNEL_TRAFFIC.get((file_hash(TC_SRC), kname))
+    tr = KERNEL_TRAFFIC.get((file_hash(TC_SRC), kname, workload))
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": tr * cmac_launch if tr else None, "kernel": kname, "flop_per_cmac": FLOP_PER_CMAC_SPLIT,
             "kernel_ms": kernel_ms, "launches_per_step": launches_per_step,
@@ -527,7 +523,8 @@ def thick_leg(ctx, args):
         err = max(err, e)
         cpu = cb or cpu
 
-    roof = tensor_roofline(cmac_step / max(k_per_step, 1), flush_ms, "flush_tc_drain2_kernel", k_per_step)
+    roof = tensor_roofline(cmac_step / max(k_per_step, 1), flush_ms, "flush_tc_drain2_kernel", k_per_step,
+                           workload="thick")
     conv = conversion_roofline(16.0 * B * npix * T * n_batch, push_ms)
 
     # end to end through the public API from pinned host memory: the same step with the ring in

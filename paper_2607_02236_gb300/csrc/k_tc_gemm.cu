@@ -153,6 +153,22 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
                  "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
                  : "memory");
 }
+// The same with an L2 eviction policy (createpolicy) for the lines it brings in.
+__device__ __forceinline__ void bulk_load_hint(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar,
+                                               uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar), "l"(policy)
+        : "memory");
+}
+// Policy that keeps lines in L2 ahead of ordinary ones: the twiddle rows, which every pass of a
+// persistent grid reads again, against the staged rows, which are streamed once per row tile.
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
                  : "memory");
@@ -351,6 +367,7 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
     // (no divisions in the issue loops: the single MMA thread's loop sits on the critical path).
     if (warp == 0) {
         if (lane == 0) {
+            const uint64_t keep = l2_evict_last_policy();
             int s = 0;
             uint32_t ph = 0;                          // parity of the current use of slot s
             int issued = 0;                           // copies in flight that may still land
@@ -383,8 +400,8 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
                     // the tables are pre-swizzled: each operand block is one contiguous copy
                     bulk_load(st, pAhi, kABytes, full);
                     bulk_load(st + kABytes, pAlo, kABytes, full);
-                    bulk_load(st + 2 * kABytes, pBhi, (uint32_t)Nt * RB, full);
-                    bulk_load(st + 2 * kABytes + b_pad, pBlo, (uint32_t)Nt * RB, full);
+                    bulk_load_hint(st + 2 * kABytes, pBhi, (uint32_t)Nt * RB, full, keep);
+                    bulk_load_hint(st + 2 * kABytes + b_pad, pBlo, (uint32_t)Nt * RB, full, keep);
                     pAhi += a_step;
                     pAlo += a_step;
                     pBhi += b_step;
@@ -812,6 +829,7 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
             int op_issued = 0;
             const uint32_t tx_b = 2u * (uint32_t)N * RB;
             const size_t b_step = (size_t)a.b_rows * RB;
+            const uint64_t keep = l2_evict_last_policy();
             bool stop = false;
             for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x) {
                 const int wtile = (int)(t % a.n_wt);
@@ -829,8 +847,8 @@ __global__ void __maxnreg__(168) flush_tc_inplace_kernel(const __grid_constant__
                     const uint32_t full = smem_u32(&sh->full[s]);
                     const uint32_t st = base_s + (uint32_t)s * b_stage;
                     mbar_arrive_expect_tx(full, tx_b);
-                    bulk_load(st, pBhi + (size_t)kb * b_step, (uint32_t)N * RB, full);
-                    bulk_load(st + b_pad, pBlo + (size_t)kb * b_step, (uint32_t)N * RB, full);
+                    bulk_load_hint(st, pBhi + (size_t)kb * b_step, (uint32_t)N * RB, full, keep);
+                    bulk_load_hint(st + b_pad, pBlo + (size_t)kb * b_step, (uint32_t)N * RB, full, keep);
                     op_issued = op_issued < stages ? op_issued + 1 : stages;
                     if (++s == stages) {
                         s = 0;
