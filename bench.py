@@ -42,7 +42,12 @@ FLOP_PER_CMAC_FP32 = 8
 # DRAM bytes per CMAC of a contraction kernel from an ncu capture at one workload's shape, keyed by
 # the hash of the kernel's source file (code only) at capture time, the kernel and the workload:
 # reported only for that workload and while the source is unchanged.
-KERNEL_TRAFFIC = {}
+KERNEL_TRAFFIC = {
+    # ncu --set full of flush_tc_drain2_kernel on `bench.py --small --no-extras` (the thick workload with
+    # 1 probe: 65536 rows, T = 8192, 1000 energies, 5.369e11 CMAC per launch): 8.589699 GB read +
+    # 0.263999 GB written per launch
+    ("511cc0a4043fe6a1", "flush_tc_drain2_kernel", "thick"): 1.649137e-02,
+}
 
 
 def parse(argv=None):
@@ -919,9 +924,11 @@ def main(argv=None):
         return 0
     line = thick_leg(ctx, args)
     if args.extras and not args.small:
-        extra_args = parse(["--steps", "3", "--warmup", "3", "--fp32-steps", str(args.fp32_steps),
-                            "--fp16-steps", str(args.fp16_steps)])
+        # the differentiation step is ~5 ms: more steps for a stable time
         for name, leg in LEGS.items():
+            steps = "20" if name == "diff" else "3"
+            extra_args = parse(["--steps", steps, "--warmup", "3", "--fp32-steps", str(args.fp32_steps),
+                                "--fp16-steps", str(args.fp16_steps)])
             line[name] = leg(ctx, extra_args, sample_clocks=True)
     if ctx.rank == 0:
         print(json.dumps(line), flush=True)

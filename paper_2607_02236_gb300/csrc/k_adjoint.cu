@@ -15,7 +15,7 @@
 // Both contractions are complex GEMMs tiled for the CUDA cores: a 256-thread block owns a
 // 64-row x 64-column tile, each thread a 4 x 4 tile of complex accumulators (rows tx + 16a,
 // columns ty + 16b), with 16-deep slices of both operands staged in shared memory by
-// coalesced loads.
+// coalesced loads, double-buffered (the next slice's loads in flight during the FMAs).
 //   forward  Psi'[m][j] = sum_t (psi[t,m] - psi[0,m]) B[t][j]      (K = T, N = Nw)
 //            Psi = Psi' - (mu - psi_0) W_j  (the first frame as provisional mean keeps the
 //            elastic part out of the FP32 sums; the row sums ride along in the tile loads);
@@ -60,10 +60,12 @@ __device__ __forceinline__ void tile_step(const float2 (*As)[ADJ_TM], const floa
     }
 }
 
-// grid (row tiles, energy tiles): G^T[j][m] for all aperture rows
-__global__ void __launch_bounds__(256) adj_psi_kernel(AdjointArgs a) {
-    __shared__ float2 As[ADJ_TK][ADJ_TM];
-    __shared__ float2 Bs[ADJ_TK][ADJ_TN + 1];
+// grid (row tiles, energy tiles): G^T[j][m] for all aperture rows.  The operand slices are
+// double-buffered: the next slice's global loads are in flight (in registers) while the current
+// slice's FMAs run from shared memory, one barrier per slice.
+__global__ void __launch_bounds__(256, 2) adj_psi_kernel(AdjointArgs a) {
+    __shared__ float2 As[2][ADJ_TK][ADJ_TM];
+    __shared__ float2 Bs[2][ADJ_TK][ADJ_TN + 1];
     __shared__ float2 rsum[4][ADJ_TM];
     __shared__ float2 ref[ADJ_TM];
     __shared__ int64_t roff[ADJ_TM];
@@ -94,28 +96,44 @@ __global__ void __launch_bounds__(256) adj_psi_kernel(AdjointArgs a) {
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) acc[i][jj] = make_float2(0.f, 0.f);
-    for (int t0 = 0; t0 < a.T; t0 += ADJ_TK) {
+    float2 ra[4], rb[4];
+    // slice t0 of both operands into registers (frames minus the provisional mean; twiddles)
+    auto load = [&](int t0) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int kk = lk + 4 * q, t = t0 + kk;
+            const int t = t0 + lk + 4 * q;
             float2 v = make_float2(0.f, 0.f);
             if (row_ok && t < a.T) {
                 v = a.frames[my_off + (int64_t)t * a.pitch_frame];
                 v.x -= my_ref.x;
                 v.y -= my_ref.y;
-                sr += v.x;
-                si += v.y;
             }
-            As[kk][lr] = v;
+            ra[q] = v;
+            const int e = tid + 256 * q, kk = e >> 6, nn = e & 63, tb = t0 + kk, j = n0 + nn;
+            rb[q] = (tb < a.T && j < a.Nw) ? a.B32[(size_t)tb * a.Nw_pad + j] : make_float2(0.f, 0.f);
         }
+    };
+    auto store = [&](int buf) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int e = tid + 256 * q, kk = e >> 6, nn = e & 63, t = t0 + kk, j = n0 + nn;
-            Bs[kk][nn] = (t < a.T && j < a.Nw) ? a.B32[(size_t)t * a.Nw_pad + j] : make_float2(0.f, 0.f);
+            sr += ra[q].x;
+            si += ra[q].y;
+            As[buf][lk + 4 * q][lr] = ra[q];
+            const int e = tid + 256 * q;
+            Bs[buf][e >> 6][e & 63] = rb[q];
         }
+    };
+    load(0);
+    store(0);
+    __syncthreads();
+    int buf = 0;
+    for (int t0 = 0; t0 < a.T; t0 += ADJ_TK) {
+        const bool more = t0 + ADJ_TK < a.T;
+        if (more) load(t0 + ADJ_TK);
+        tile_step(As[buf], Bs[buf], tx, ty, acc);
+        if (more) store(buf ^ 1);
         __syncthreads();
-        tile_step(As, Bs, tx, ty, acc);
-        __syncthreads();
+        buf ^= 1;
     }
     rsum[lk][lr] = make_float2(sr, si);
     __syncthreads();
@@ -149,10 +167,11 @@ __global__ void __launch_bounds__(256) adj_psi_kernel(AdjointArgs a) {
     }
 }
 
-// grid (row tiles, frame tiles): C[m][t] = sum_j Gt[j][m] conj(B[t][j]); grad = 2 scale (C - K)
-__global__ void __launch_bounds__(256) adj_grad_kernel(AdjointArgs a) {
-    __shared__ float2 As[ADJ_TK][ADJ_TM];
-    __shared__ float2 Bs[ADJ_TK][ADJ_TN + 1];
+// grid (row tiles, frame tiles): C[m][t] = sum_j Gt[j][m] conj(B[t][j]); grad = 2 scale (C - K).
+// Double-buffered operand slices as in adj_psi_kernel.
+__global__ void __launch_bounds__(256, 2) adj_grad_kernel(AdjointArgs a) {
+    __shared__ float2 As[2][ADJ_TK][ADJ_TM];
+    __shared__ float2 Bs[2][ADJ_TK][ADJ_TN + 1];
     __shared__ float2 ksum[4][ADJ_TM];
     __shared__ int64_t roff[ADJ_TM];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -169,34 +188,48 @@ __global__ void __launch_bounds__(256) adj_grad_kernel(AdjointArgs a) {
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) acc[i][jj] = make_float2(0.f, 0.f);
-    for (int j0 = 0; j0 < a.Nw; j0 += ADJ_TK) {
+    float2 ra[4], rb[4];
+    // slice j0: G rows (energies j0 + lk + 4q of row lr) and conj(B[t][j]) for 64 frames x 16
+    // energies, 16 consecutive energies of a frame per 16 threads (128-byte rows of the table)
+    auto load = [&](int j0) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int kk = lk + 4 * q, j = j0 + kk;
-            float2 g = make_float2(0.f, 0.f);
-            if (row_ok && j < a.Nw) {
-                g = Gt[(size_t)j * M + m0 + lr];
+            const int j = j0 + lk + 4 * q;
+            ra[q] = (row_ok && j < a.Nw) ? Gt[(size_t)j * M + m0 + lr] : make_float2(0.f, 0.f);
+            const int e = tid + 256 * q, kk = e & 15, nn = e >> 4, t = tb0 + nn, jb = j0 + kk;
+            float2 bv = make_float2(0.f, 0.f);
+            if (t < a.T && jb < a.Nw) {
+                bv = a.B32[(size_t)t * a.Nw_pad + jb];
+                bv.y = -bv.y;
+            }
+            rb[q] = bv;
+        }
+    };
+    auto store = [&](int buf, int j0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + lk + 4 * q;
+            if (j < a.Nw) {
                 const float2 W = a.Wc[j];
-                kr += W.x * g.x + W.y * g.y;               // conj(W) G
-                ki += W.x * g.y - W.y * g.x;
+                kr += W.x * ra[q].x + W.y * ra[q].y;       // conj(W) G
+                ki += W.x * ra[q].y - W.y * ra[q].x;
             }
-            As[kk][lr] = g;
+            As[buf][lk + 4 * q][lr] = ra[q];
+            const int e = tid + 256 * q;
+            Bs[buf][e & 15][e >> 4] = rb[q];
         }
-        // conj(B[t][j]) for 64 frames x 16 energies: 16 consecutive energies of a frame per
-        // 16 threads (128-byte rows of the table)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int e = tid + 256 * q, kk = e & 15, nn = e >> 4, t = tb0 + nn, j = j0 + kk;
-            float2 b = make_float2(0.f, 0.f);
-            if (t < a.T && j < a.Nw) {
-                b = a.B32[(size_t)t * a.Nw_pad + j];
-                b.y = -b.y;
-            }
-            Bs[kk][nn] = b;
-        }
+    };
+    load(0);
+    store(0, 0);
+    __syncthreads();
+    int buf = 0;
+    for (int j0 = 0; j0 < a.Nw; j0 += ADJ_TK) {
+        const bool more = j0 + ADJ_TK < a.Nw;
+        if (more) load(j0 + ADJ_TK);
+        tile_step(As[buf], Bs[buf], tx, ty, acc);
+        if (more) store(buf ^ 1, j0 + ADJ_TK);
         __syncthreads();
-        tile_step(As, Bs, tx, ty, acc);
-        __syncthreads();
+        buf ^= 1;
     }
     ksum[lk][lr] = make_float2(kr, ki);
     __syncthreads();
