@@ -77,6 +77,9 @@ def parse(argv=None):
     ap.add_argument("--fp32-steps", type=int, default=2, help="realistic: FP32-path comparison steps (0: skip)")
     ap.add_argument("--fp16-steps", type=int, default=2, help="realistic: split-FP16 comparison steps (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=1, help="end-to-end steps from pinned host memory (0: skip)")
+    ap.add_argument("--e2e-free-sms", type=int, default=16,
+                    help="thick e2e with two half-batch plans: SMs their contraction grids leave free for the "
+                         "other half's pushes (0: skip that ingest)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU oracle baseline")
     ap.add_argument("--trace", action="store_true", help="per-CTA phase breakdown of one contraction")
     return ap.parse_args(argv)
@@ -565,9 +568,27 @@ def thick_leg(ctx, args):
                "ingest": "zero-copy: the push kernels read each push's ROI rows straight from pinned host "
                          "memory over the host link (only the ROI crosses it)",
                "timed": "host wall clock around the step, device synchronized on both sides"}
+        del ring
+        plan.close()
+        free_device()
+        # the same step with two plans of half a batch each on two CUDA streams: one plan's pushes
+        # (reading the host link) run while the other plan's contraction runs, its grid capped so
+        # that SMs stay free for the pushes; the faster of the two ingests is the e2e figure
+        if B % 2 == 0 and args.e2e_free_sms > 0:
+            pipe = thick_e2e_pipelined(ctx, args, spec, B, n_batch, host, I, S, S_host, R)
+            pipe["link_gbs_measured"] = link
+            pipe["link_gbs_achieved"] = h2d / (pipe["ms_per_step"] * 1e-3) / 1e9
+            pipe["frac"] = pipe["link_gbs_achieved"] / link
+            pipe["input"] = e2e["input"]
+            pipe["link_measure"] = e2e["link_measure"]
+            if pipe["value"] > e2e["value"]:
+                pipe["other_ingest"], e2e = e2e, pipe
+            else:
+                e2e["other_ingest"] = pipe
         del host
-    del ring
-    plan.close()
+    else:
+        del ring
+        plan.close()
     del I, S
     free_device()
 
@@ -598,6 +619,75 @@ def thick_leg(ctx, args):
     if phases:
         line["flush_phases"] = phases
     return line
+
+
+def thick_e2e_pipelined(ctx, args, spec, B, n_batch, host, I, S, S_host, R):
+    """End-to-end thick step with two plans of B/2 probes (probes 0..B/2-1 and B/2..B-1 of every
+    pushed frame, read from the same pinned host ring): their half batches alternate on two CUDA
+    streams, each half's pushes ordered after the other half's pushes, so that one half's
+    zero-copy ingest runs beside the other half's contraction; the contraction grids leave
+    args.e2e_free_sms SMs free for it.  Host wall clock over args.e2e_steps steps."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    K, T, Tc, Nw = spec.Kx, spec.T, spec.Tc, spec.Nw
+    D = len(spec.detectors)
+    gx, gy = spec.full_grid
+    npix = K * K
+    H = B // 2
+    fe = B * gx * gy
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    cap = max(1, sms - args.e2e_free_sms)
+    cfg = stream_config(spec, P=H)
+    cfg.pitch_frame = fe                               # frames of the host ring hold all B probes
+    plans = [TacawPlan([cfg], precision="split_bf16", accum=args.accum, tc_max_ctas=cap, **{
+        k: v for k, v in tiling(args).items() if k != "tc_max_ctas"}) for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    pushed = [torch.cuda.Event(), torch.cuda.Event()]
+    i_h, s_h = H * Nw * npix, H * D * Nw
+    n_push = T // Tc
+    prev = [None]
+
+    def half(b, h):
+        pl, sx = plans[h], streams[h]
+        st = sx.cuda_stream
+        if prev[0] is not None:
+            sx.wait_event(prev[0])                    # the other half's pushes are done
+        pl.reset(st)
+        base = host.data_ptr() + h * H * gx * gy * 8
+        for i in range(n_push):
+            pl.push(0, base + (i % R) * Tc * fe * 8, Tc, st)
+        pushed[h].record(sx)
+        prev[0] = pushed[h]
+        o = (b * B + h * H)
+        pl.finalize_async(I[o * Nw * npix:o * Nw * npix + i_h], S[o * D * Nw:o * D * Nw + s_h] if D else None,
+                          None, st)
+        if D:
+            with torch.cuda.stream(sx):
+                S_host[o * D * Nw:o * D * Nw + s_h].copy_(S[o * D * Nw:o * D * Nw + s_h], non_blocking=True)
+
+    half(0, 0)                                         # warm-up of both plans' host paths
+    half(0, 1)
+    torch.cuda.synchronize()
+    for pl, sx in zip(plans, streams):
+        pl.check_errors(sx.cuda_stream)
+    ctx.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        for b in range(n_batch):
+            half(b, 0)
+            half(b, 1)
+    torch.cuda.synchronize()
+    el = ctx.max_ms((time.perf_counter() - t0) * 1e3) * 1e-3
+    for pl, sx in zip(plans, streams):
+        pl.check_errors(sx.cuda_stream)
+        pl.close()
+    cmac_step = B * npix * T * Nw * n_batch
+    return {"value": job_rate(cmac_step * args.e2e_steps, ctx.world, el), "unit": UNIT,
+            "h2d_bytes_per_step": B * npix * T * 8 * n_batch, "d2h_bytes_per_step": S.numel() * 4,
+            "ms_per_step": 1e3 * el / args.e2e_steps, "steps": args.e2e_steps,
+            "ingest": f"zero-copy pushes; two plans of {H} probes alternate on two CUDA streams, one half's "
+                      f"pushes beside the other half's contraction (grids capped at {cap} of {sms} SMs)",
+            "timed": "host wall clock around the step, device synchronized on both sides"}
 
 
 # ----------------------------------------------------------------------------------------------

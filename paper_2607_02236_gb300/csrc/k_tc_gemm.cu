@@ -40,23 +40,13 @@ struct TcGroup {
     int n;
     int stages, n_max;         // ring stages and ring/TMEM width (widest tile of the group)
     int64_t tiles;             // tiles of all entries
-    int rot;                   // rotate energy tiles across a CTA's passes (see wtile_of)
+    int *counter;              // tile queue: the next tile index to hand out (zero at launch)
 };
-
-// Energy tile of local tile lt on a CTA's k-th pass.  Tiles go out in row-major order (the
-// energy tiles of a row tile run side by side and share its operand rows in L2).  When the
-// grid is a multiple of the tile count per row (one stream), every pass hands each CTA the
-// same energy slot; rotating the slot by the pass number keeps each row tile's set of energy
-// tiles intact while cycling every CTA through all of them (a narrower last tile then shortens
-// every CTA's work alike).
-__device__ __forceinline__ int wtile_of(int64_t lt, int n_wt, int rot, int64_t pass) {
-    const int w = (int)(lt % n_wt);
-    return rot ? (int)((w + pass) % n_wt) : w;
-}
 
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s per wait
 constexpr int kMaxStages = 12;
 constexpr int kSmemLimit = 232448;                 // 227 KB opt-in per block
+constexpr int kTileQueue = 4;                      // tiles handed out ahead (staged kernel)
 
 struct TcShared {
     uint64_t full[kMaxStages];
@@ -66,6 +56,9 @@ struct TcShared {
     int abort_flag;
     uint64_t chunk_full[2];   // [0] a chunk of H is complete, [1] the tile's last H and S are
     uint64_t chunk_free[2];   // the epilogue warps have drained them
+    uint64_t tq_full[kTileQueue];    // tile queue: the producer wrote tile_q[i]
+    uint64_t tq_empty[kTileQueue];   //   the MMA thread and the eight epilogue warps read it
+    int tile_q[kTileQueue];          //   tile index, or -1 when the launch's tiles are all handed out
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -347,6 +340,10 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
             mbar_init(smem_u32(&sh->chunk_full[b]), 1);
             mbar_init(smem_u32(&sh->chunk_free[b]), 8);   // one arrival per epilogue warp
         }
+        for (int q = 0; q < kTileQueue; ++q) {
+            mbar_init(smem_u32(&sh->tq_full[q]), 1);
+            mbar_init(smem_u32(&sh->tq_empty[q]), 9);     // the MMA thread and eight epilogue warps
+        }
         sh->abort_flag = 0;
         fence_mbar_init();
     }
@@ -371,12 +368,29 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
             int s = 0;
             uint32_t ph = 0;                          // parity of the current use of slot s
             int issued = 0;                           // copies in flight that may still land
-            int64_t pass = 0;
-            for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x, ++pass) {
+            int q = 0;
+            uint32_t qph = 0;                         // tile queue slot and its use parity
+            while (!*abort_flag) {
+                // the next tile of the launch (tiles go out in order: longest streams first, the
+                // energy tiles of a row tile side by side, so they share its rows in L2)
+                int64_t t = atomicAdd(g.counter, 1);
+                if (t >= n_tiles) t = -1;
+                if (!mbar_wait(smem_u32(&sh->tq_empty[q]), qph ^ 1u, abort_flag, wait_ns)) {
+                    if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_EMPTY);
+                    *abort_flag = 1;
+                    break;
+                }
+                sh->tile_q[q] = (int)t;
+                mbar_arrive(smem_u32(&sh->tq_full[q]));
+                if (++q == kTileQueue) {
+                    q = 0;
+                    qph ^= 1u;
+                }
+                if (t < 0) break;
                 const int gi = group_entry(g, t);
                 const TcGroupEntry &en = g.e[gi];
                 const int64_t lt = t - en.cta_begin;
-                const int wtile = wtile_of(lt, en.args.n_wt, g.rot, pass);
+                const int wtile = (int)(lt % en.args.n_wt);
                 const int m0 = (int)(lt / en.args.n_wt) * kMTile;
                 const int N = en.args.N;
                 // columns of this tile (N_last: a narrower last energy tile; 0 = full width)
@@ -436,10 +450,23 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
             int64_t tiles = 0, chunks = 0;
             bool stop = false;
             const uint32_t accH = tmem, accS = tmem + 256u;
-            for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x, ++tiles) {
+            int q = 0;
+            uint32_t qph = 0;
+            for (;; ++tiles) {
+                if (!mbar_wait(smem_u32(&sh->tq_full[q]), qph, abort_flag, wait_ns)) {
+                    if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_FULL);
+                    *abort_flag = 1;
+                    break;
+                }
+                const int64_t t = sh->tile_q[q];
+                mbar_arrive(smem_u32(&sh->tq_empty[q]));
+                if (++q == kTileQueue) {
+                    q = 0;
+                    qph ^= 1u;
+                }
+                if (t < 0) break;
                 const TcGroupEntry &en = g.e[group_entry(g, t)];
-                const bool last_w = en.args.N_last > 0 &&
-                                    wtile_of(t - en.cta_begin, en.args.n_wt, g.rot, tiles) == en.args.n_wt - 1;
+                const bool last_w = en.args.N_last > 0 && (t - en.cta_begin) % en.args.n_wt == en.args.n_wt - 1;
                 const int N = last_w ? en.args.N_last : en.args.N, n_kb = en.args.n_kb, cb = en.args.drain_kb;
                 const uint32_t id = idesc_f32acc(kMTile, N, en.args.f16);
                 if (tiles > 0) {
@@ -515,11 +542,26 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
         float sum[kDrainCols];
         int64_t hc = 0, tiles = 0;                    // H drains done, tiles done
         bool ok = true;
-        for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tiles) {
+        int q = 0;
+        uint32_t qph = 0;
+        for (;; ++tiles) {
+            if (!mbar_wait_warp(smem_u32(&sh->tq_full[q]), qph, abort_flag, wait_ns)) {
+                if (lane == 0 && !*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
+                *abort_flag = 1;
+                break;
+            }
+            const int64_t t = sh->tile_q[q];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&sh->tq_empty[q]));
+            if (++q == kTileQueue) {
+                q = 0;
+                qph ^= 1u;
+            }
+            if (t < 0) break;
             const TcGroupEntry &en = g.e[group_entry(g, t)];
             const TcPlanArgs &a = en.args;
             const int64_t lt = t - en.cta_begin;
-            const int wtile = wtile_of(lt, a.n_wt, g.rot, tiles);
+            const int wtile = (int)(lt % a.n_wt);
             const int m0 = (int)(lt / a.n_wt) * kMTile;
             // N / 2 columns per thread (the last energy tile may be narrower)
             const int cols = ((wtile == a.n_wt - 1 && a.N_last > 0) ? a.N_last : a.N) / 2;
@@ -1239,7 +1281,7 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, int n, cudaStream_t st
     int n_max = 0;
     for (int i = 0; i < n; ++i) {
         // one staging row width per launch; register sums of at most kDrainCols columns a thread
-        if (args[i].bf != args[0].bf || args[i].wt > kDrainCols || args[i].drain_kb < 1) {
+        if (args[i].bf != args[0].bf || args[i].wt > kDrainCols || args[i].drain_kb < 1 || !args[0].tile_counter) {
             delete g;
             return cudaErrorInvalidValue;
         }
@@ -1273,9 +1315,10 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, int n, cudaStream_t st
     int64_t cap = (int64_t)occ * sms;
     if (args[0].max_ctas > 0 && args[0].max_ctas < cap) cap = args[0].max_ctas;
     const unsigned grid = (unsigned)(cap < total ? cap : total);
-    // one stream whose row of energy tiles divides the grid: rotate the energy slots
-    g->rot = (n == 1 && args[0].n_wt > 1 && grid % (unsigned)args[0].n_wt == 0) ? 1 : 0;
-    e = launch_persistent(flush_tc_drain2_kernel, grid, 320, smem, st, *g);
+    // the CTAs take tiles from a counter in device memory, zeroed on the stream before the launch
+    g->counter = args[0].tile_counter;
+    e = cudaMemsetAsync(g->counter, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_persistent(flush_tc_drain2_kernel, grid, 320, smem, st, *g);
     delete g;
     return e;
 }

@@ -161,10 +161,10 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
     }
     const size_t a_elems = (size_t)kb2 * rows * 2 * sh.bf;
     const size_t b_elems = (size_t)kb2 * 2 * nw_pad_max * 2 * sh.bf;
-    DevBuf a_hi, a_lo, b_hi, b_lo, wc, bose, iout;
+    DevBuf a_hi, a_lo, b_hi, b_lo, wc, bose, iout, counter;
     if (!a_hi.alloc(a_elems * 2) || !a_lo.alloc(a_elems * 2) || !b_hi.alloc(b_elems * 2) || !b_lo.alloc(b_elems * 2) ||
         !wc.alloc(sizeof(float2) * sh.Nw) || !bose.alloc(sizeof(float) * sh.Nw) ||
-        !iout.alloc(sizeof(float) * (size_t)sh.Nw * rows)) {
+        !iout.alloc(sizeof(float) * (size_t)sh.Nw * rows) || !counter.alloc(sizeof(int))) {
         snprintf(err, errlen, "autotune: scratch allocation failed");
         return false;
     }
@@ -213,6 +213,7 @@ bool tc_autotune(const TuneShape &sh, const char *cache_path, uint32_t *d_err, c
         a.a_rows = rows;
         a.b_rows = 2 * c.wt * c.n_wt;
         a.err = d_err;
+        a.tile_counter = static_cast<int *>(counter.p);
         double t[2] = {0.0, 0.0};
         const int kbs[2] = {kb1, kb2};
         for (int q = 0; q < 2 && ok; ++q) {

@@ -160,6 +160,10 @@ struct tacaw_plan_s {
     bool poisoned = false;
     bool finalized = false;
     uint32_t *d_err = nullptr;
+    // tile counters of the staged kernel's launches: one per launch in a ring, so that launches of
+    // this plan on different CUDA streams (up to kCounterRing of them in flight) never share one
+    int *d_counters = nullptr;
+    int64_t counter_slot = 0;
     std::vector<void *> allocs;
     bool timing = false;
     bool trace = false;                      // record per-CTA phase stamps of tensor-core flushes
@@ -288,6 +292,9 @@ void choose_omega_tile(Stream &s, int requested, int cap) {
     s.n_wt = (s.Nw + best - 1) / best;
     s.Nw_pad = s.wt * s.n_wt;
 }
+
+// Tile counters a plan keeps for its staged-kernel launches (see tacaw_plan_s::d_counters).
+constexpr int kCounterRing = 256;
 
 // Automatic accumulators choose plain FP32 up to this many flushes per segment.
 constexpr int kAutoFp32Flushes = 16;
@@ -461,6 +468,7 @@ tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float
             p->launches++;
         }
         TcPlanArgs a = tc_args(p, s, e);
+        a.tile_counter = p->d_counters + (p->counter_slot++ % kCounterRing);
         r = trace_buffer(p, tc_grid_ctas(a), &a.trace);
         if (r != TACAW_OK) return r;
         CU_CHECK(p, launch_flush_tc(a, st), "flush (tensor cores)");
@@ -518,6 +526,7 @@ tacaw_status flush_grouped(tacaw_plan_s *p, std::vector<FlushReq> req, cudaStrea
         tacaw_status r = trace_buffer(p, nc, &tr);
         if (r != TACAW_OK) return r;
         for (auto &a : args) a.trace = tr;
+        args[0].tile_counter = p->d_counters + (p->counter_slot++ % kCounterRing);
         cudaEvent_t e0, e1;
         r = timing_begin(p, &e0, &e1, st);
         if (r != TACAW_OK) return r;
@@ -1067,7 +1076,8 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     p->f16 = f16 ? 1 : 0;
     p->f16_scale = (float)f16_scale;
     p->accum = desc->accum == TACAW_ACC_AUTO ? TACAW_ACC_KAHAN_FP32 : desc->accum;   // resolved with K_stage
-    if (!dev_alloc(p, &p->d_err, 1) || cudaMemset(p->d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
+    if (!dev_alloc(p, &p->d_err, 1) || cudaMemset(p->d_err, 0, sizeof(uint32_t)) != cudaSuccess ||
+        !dev_alloc(p, &p->d_counters, kCounterRing)) {
         cudaGetLastError();
         free_all(p);
         delete p;

@@ -289,6 +289,8 @@ struct TcPlanArgs {
     unsigned long long *trace; // null, or kTraceWords globaltimer stamps per CTA (phase boundaries)
     uint32_t *err;
     uint64_t wait_ns;          // pipeline waits give up after this many ns (0: the default 4 s)
+    int *tile_counter;         // staged kernel: device int the launch hands out its tiles from (the
+                               // first entry's of a grouped launch is used; zeroed before the launch)
 };
 // In-place operand A: the contraction reads the pushed frames of this flush directly.
 struct TcDirectArgs {

@@ -85,7 +85,13 @@ def test_realistic_full_size(precision):
         assert e <= TOL[precision], (p, e)
 
 
-def test_thick_probe_batches_crop_and_accumulators():
+@pytest.mark.parametrize("k_stage", [0, 2048], ids=["one_flush_per_batch", "four_flushes_kahan"])
+def test_thick_probe_batches_crop_and_accumulators(k_stage):
+    """Config 5: 1024^2 frames cropped to the centred 256^2 ROI while read, T = 8192 in 64-frame
+    pushes, 1000 energies, 32-probe batches through one plan.  k_stage 0 is the bench's launch
+    configuration (the default HBM budget holds the whole segment: one flush per batch, no
+    accumulators; the first and the last batch are checked); 2048 forces four flushes per batch with
+    compensated accumulators (all 8 batches)."""
     import torch
     import synth.gpu as sg
     from paper_2607_02236_gb300 import TacawPlan
@@ -102,8 +108,10 @@ def test_thick_probe_batches_crop_and_accumulators():
     S = torch.empty(B * Nw, dtype=torch.float32, device="cuda")
     rng = np.random.default_rng(9)
     worst = 0.0
-    with TacawPlan([stream_config(spec, P=B)], precision="split_bf16", k_stage=2048) as plan:
-        for b0 in range(0, spec.P, B):
+    batches = list(range(0, spec.P, B)) if k_stage else [0, spec.P - B]
+    with TacawPlan([stream_config(spec, P=B)], precision="split_bf16", k_stage=k_stage, accum="kahan") as plan:
+        assert plan.info()["k_stage"] == (k_stage or T)
+        for b0 in batches:
             plan.reset()
             pb = rng.integers(0, B, 6)
             px = sample_pixels(spec, 6, rng)
@@ -122,8 +130,8 @@ def test_thick_probe_batches_crop_and_accumulators():
             err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
             worst = max(worst, err)
         info = plan.info()
-    print(f"thick: sampled max rel I error {worst:.3g}, flushes {info['flushes']}")
-    assert info["flushes"] == (spec.P // B) * (T // 2048)
+    print(f"thick (k_stage {k_stage}): sampled max rel I error {worst:.3g}, flushes {info['flushes']}")
+    assert info["flushes"] == len(batches) * (T // (k_stage or T))
     assert worst <= TOL["split_bf16"]
 
 
