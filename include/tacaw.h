@@ -297,7 +297,9 @@ tacaw_status tacaw_output_offsets(tacaw_plan_t plan, int stream_id, int64_t *I_o
  * and zero on the skipped frames.
  * d_dL_dS: float32 [p][d][j] on the device.  d_frames, d_grad and d_dL_dS may be device,
  * managed or pinned host memory; outside stream capture any other address is refused
- * (INVALID_ARG) before work is enqueued.  Waits for the work on `stream`.                */
+ * (INVALID_ARG) before work is enqueued.  Waits for the work on `stream`.
+ * The first call that needs it allocates the plan's adjoint scratch, P x (aperture pixels)
+ * x (n_omega + 2) complex64, kept until tacaw_destroy (TACAW_ERR_OOM if that fails).    */
 tacaw_status tacaw_backward(tacaw_plan_t plan, int stream_id, const float *d_dL_dS,
                             const void *d_frames, void *d_grad, void *stream);
 

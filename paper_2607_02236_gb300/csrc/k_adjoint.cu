@@ -12,10 +12,11 @@
 // the frames (the window and twiddles come from the plan's table), never stored between
 // forward and backward.
 //
-// Both contractions are complex GEMMs tiled for the CUDA cores: a 256-thread block owns a
-// 64-row x 64-column tile, each thread a 4 x 4 tile of complex accumulators (rows tx + 16a,
-// columns ty + 16b), with 16-deep slices of both operands staged in shared memory by
-// coalesced loads, double-buffered (the next slice's loads in flight during the FMAs).
+// Both contractions are complex GEMMs tiled for the CUDA cores: a block of 4 x TN threads owns a
+// 64-row x TN-column tile (TN = 64, or 32 for the forward when that pads the energies less),
+// each thread a 4 x 4 tile of complex accumulators (rows tx + 16a, columns ty + (TN/4) b), with
+// 16-deep slices of both operands staged in shared memory by coalesced loads, double-buffered
+// (the next slice's loads in flight during the FMAs).
 //   forward  Psi'[m][j] = sum_t (psi[t,m] - psi[0,m]) B[t][j]      (K = T, N = Nw)
 //            Psi = Psi' - (mu - psi_0) W_j  (the first frame as provisional mean keeps the
 //            elastic part out of the FP32 sums; the row sums ride along in the tile loads);
@@ -43,8 +44,9 @@ __device__ __forceinline__ void cmac(float2 &acc, float2 x, float2 b) {
     acc.y = fmaf(x.x, b.y, fmaf(x.y, b.x, acc.y));
 }
 
-// One 16-deep step of the 4 x 4 complex register tile.
-__device__ __forceinline__ void tile_step(const float2 (*As)[ADJ_TM], const float2 (*Bs)[ADJ_TN + 1], int tx, int ty,
+// One 16-deep step of the 4 x 4 complex register tile: rows tx + 16 i, columns ty + (TN / 4) j.
+template <int TN>
+__device__ __forceinline__ void tile_step(const float2 (*As)[ADJ_TM], const float2 (*Bs)[TN + 1], int tx, int ty,
                                           float2 (&acc)[4][4]) {
 #pragma unroll
     for (int kk = 0; kk < ADJ_TK; ++kk) {
@@ -52,7 +54,7 @@ __device__ __forceinline__ void tile_step(const float2 (*As)[ADJ_TM], const floa
 #pragma unroll
         for (int i = 0; i < 4; ++i) x[i] = As[kk][tx + 16 * i];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) b[i] = Bs[kk][ty + 16 * i];
+        for (int i = 0; i < 4; ++i) b[i] = Bs[kk][ty + (TN / 4) * i];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -60,21 +62,26 @@ __device__ __forceinline__ void tile_step(const float2 (*As)[ADJ_TM], const floa
     }
 }
 
-// grid (row tiles, energy tiles): G^T[j][m] for all aperture rows.  The operand slices are
-// double-buffered: the next slice's global loads are in flight (in registers) while the current
-// slice's FMAs run from shared memory, one barrier per slice.
-__global__ void __launch_bounds__(256, 2) adj_psi_kernel(AdjointArgs a) {
+// grid (row tiles, energy tiles of TN): G^T[j][m] for all aperture rows.  16 x TN/4 threads, each a
+// 4 x 4 complex register tile.  The operand slices are double-buffered: the next slice's global
+// loads are in flight (in registers) while the current slice's FMAs run from shared memory, one
+// barrier per slice.
+template <int TN>
+__global__ void __launch_bounds__(4 * TN, 128 / TN) adj_psi_kernel(AdjointArgs a) {
+    constexpr int NT = 4 * TN;                 // threads
+    constexpr int NA = ADJ_TM * ADJ_TK / NT;   // A elements each thread stages per slice
+    constexpr int NB = TN * ADJ_TK / NT;       // B elements each thread stages per slice (4)
     __shared__ float2 As[2][ADJ_TK][ADJ_TM];
-    __shared__ float2 Bs[2][ADJ_TK][ADJ_TN + 1];
-    __shared__ float2 rsum[4][ADJ_TM];
+    __shared__ float2 Bs[2][ADJ_TK][TN + 1];
+    __shared__ float2 rsum[NT / ADJ_TM][ADJ_TM];
     __shared__ float2 ref[ADJ_TM];
     __shared__ int64_t roff[ADJ_TM];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t M = (int64_t)a.P * a.n_mpix;
     const int64_t m0 = (int64_t)blockIdx.x * ADJ_TM;
-    const int n0 = blockIdx.y * ADJ_TN;
-    // this thread's load slot: row lr of every slice, frames lk and lk + 4, 8, 12
-    const int lr = tid & (ADJ_TM - 1), lk = tid >> 6;
+    const int n0 = blockIdx.y * TN;
+    // this thread's load slot: row lr of every slice, frames lk, lk + NT/64, ...
+    const int lr = tid & (ADJ_TM - 1), lk = tid / ADJ_TM;
     if (tid < ADJ_TM) {
         const int64_t m = m0 + tid;
         float2 v = make_float2(0.f, 0.f);
@@ -96,12 +103,12 @@ __global__ void __launch_bounds__(256, 2) adj_psi_kernel(AdjointArgs a) {
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) acc[i][jj] = make_float2(0.f, 0.f);
-    float2 ra[4], rb[4];
+    float2 ra[NA], rb[NB];
     // slice t0 of both operands into registers (frames minus the provisional mean; twiddles)
     auto load = [&](int t0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int t = t0 + lk + 4 * q;
+        for (int q = 0; q < NA; ++q) {
+            const int t = t0 + lk + (NT / ADJ_TM) * q;
             float2 v = make_float2(0.f, 0.f);
             if (row_ok && t < a.T) {
                 v = a.frames[my_off + (int64_t)t * a.pitch_frame];
@@ -109,18 +116,24 @@ __global__ void __launch_bounds__(256, 2) adj_psi_kernel(AdjointArgs a) {
                 v.y -= my_ref.y;
             }
             ra[q] = v;
-            const int e = tid + 256 * q, kk = e >> 6, nn = e & 63, tb = t0 + kk, j = n0 + nn;
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int e = tid + NT * q, kk = e / TN, nn = e % TN, tb = t0 + kk, j = n0 + nn;
             rb[q] = (tb < a.T && j < a.Nw) ? a.B32[(size_t)tb * a.Nw_pad + j] : make_float2(0.f, 0.f);
         }
     };
     auto store = [&](int buf) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NA; ++q) {
             sr += ra[q].x;
             si += ra[q].y;
-            As[buf][lk + 4 * q][lr] = ra[q];
-            const int e = tid + 256 * q;
-            Bs[buf][e >> 6][e & 63] = rb[q];
+            As[buf][lk + (NT / ADJ_TM) * q][lr] = ra[q];
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int e = tid + NT * q;
+            Bs[buf][e / TN][e % TN] = rb[q];
         }
     };
     load(0);
@@ -130,7 +143,7 @@ __global__ void __launch_bounds__(256, 2) adj_psi_kernel(AdjointArgs a) {
     for (int t0 = 0; t0 < a.T; t0 += ADJ_TK) {
         const bool more = t0 + ADJ_TK < a.T;
         if (more) load(t0 + ADJ_TK);
-        tile_step(As[buf], Bs[buf], tx, ty, acc);
+        tile_step<TN>(As[buf], Bs[buf], tx, ty, acc);
         if (more) store(buf ^ 1);
         __syncthreads();
         buf ^= 1;
@@ -146,15 +159,19 @@ __global__ void __launch_bounds__(256, 2) adj_psi_kernel(AdjointArgs a) {
         // Psi = Psi' - (mu - psi_0) W  (subtract_mean), else Psi' itself (psi_0 = 0)
         float2 dmu = make_float2(0.f, 0.f);
         if (a.subtract_mean) {
-            const float xr = ((rsum[0][r].x + rsum[1][r].x) + rsum[2][r].x) + rsum[3][r].x;
-            const float xi = ((rsum[0][r].y + rsum[1][r].y) + rsum[2][r].y) + rsum[3][r].y;
+            float xr = 0.f, xi = 0.f;
+#pragma unroll
+            for (int h = 0; h < NT / ADJ_TM; ++h) {
+                xr += rsum[h][r].x;
+                xi += rsum[h][r].y;
+            }
             dmu = make_float2(xr / a.T, xi / a.T);
         }
         const int p = (int)(m / a.n_mpix);
         const int64_t ip = m - (int64_t)p * a.n_mpix;
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
-            const int j = n0 + ty + 16 * jj;
+            const int j = n0 + ty + (TN / 4) * jj;
             if (j >= a.Nw) continue;
             const float2 W = a.Wc[j];
             float c = 0.f;
@@ -226,7 +243,7 @@ __global__ void __launch_bounds__(256, 2) adj_grad_kernel(AdjointArgs a) {
     for (int j0 = 0; j0 < a.Nw; j0 += ADJ_TK) {
         const bool more = j0 + ADJ_TK < a.Nw;
         if (more) load(j0 + ADJ_TK);
-        tile_step(As[buf], Bs[buf], tx, ty, acc);
+        tile_step<ADJ_TN>(As[buf], Bs[buf], tx, ty, acc);
         if (more) store(buf ^ 1, j0 + ADJ_TK);
         __syncthreads();
         buf ^= 1;
@@ -284,8 +301,14 @@ cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t st) {
     const int64_t M = (int64_t)a.P * a.n_mpix;
     if (M == 0 || a.T == 0) return cudaSuccess;
     const unsigned mt = (unsigned)((M + ADJ_TM - 1) / ADJ_TM);
-    if ((a.T + ADJ_TN - 1) / ADJ_TN > 65535 || (a.Nw + ADJ_TN - 1) / ADJ_TN > 65535) return cudaErrorInvalidValue;
-    adj_psi_kernel<<<dim3(mt, (a.Nw + ADJ_TN - 1) / ADJ_TN), 256, 0, st>>>(a);
+    if ((a.T + ADJ_TN - 1) / ADJ_TN > 65535 || (a.Nw + 31) / 32 > 65535) return cudaErrorInvalidValue;
+    // energy tiles of 64 or 32: the narrower one when it pads the energies less (200 energies:
+    // 224 columns issued against 256)
+    const int64_t pad64 = (a.Nw + 63) / 64 * 64, pad32 = (a.Nw + 31) / 32 * 32;
+    if (pad32 < pad64)
+        adj_psi_kernel<32><<<dim3(mt, (a.Nw + 31) / 32), 128, 0, st>>>(a);
+    else
+        adj_psi_kernel<64><<<dim3(mt, (a.Nw + 63) / 64), 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     adj_grad_kernel<<<dim3(mt, (a.T + ADJ_TN - 1) / ADJ_TN), 256, 0, st>>>(a);

@@ -164,6 +164,10 @@ struct tacaw_plan_s {
     // this plan on different CUDA streams (up to kCounterRing of them in flight) never share one
     int *d_counters = nullptr;
     int64_t counter_slot = 0;
+    // the adjoint's G matrix and row means: allocated by the first tacaw_backward that needs it
+    // (grown when a later stream needs more), kept until tacaw_destroy
+    float2 *adj_scratch = nullptr;
+    size_t adj_scratch_elems = 0;
     std::vector<void *> allocs;
     bool timing = false;
     bool trace = false;                      // record per-CTA phase stamps of tensor-core flushes
@@ -208,6 +212,9 @@ void free_all(tacaw_plan_s *p) {
     p->ev.clear();
     for (void *q : p->allocs) cudaFree(q);
     p->allocs.clear();
+    if (p->adj_scratch) cudaFree(p->adj_scratch);
+    p->adj_scratch = nullptr;
+    p->adj_scratch_elems = 0;
 }
 
 tacaw_status cuda_fail(tacaw_plan_s *p, cudaError_t e, const char *what) {
@@ -1538,12 +1545,27 @@ tacaw_status tacaw_backward(tacaw_plan_t p, int sid, const float *d_dL_dS, const
     CU_CHECK(p, launch_zero_roi(z, st), "zero gradient");
     p->launches++;
     if (s.n_adj > 0 && s.D > 0) {
-        float2 *scratch = nullptr;
         const size_t n_scr = (size_t)s.d.n_probes * s.n_adj * (s.Nw + 2);
-        CU_CHECK(p, cudaMallocAsync(reinterpret_cast<void **>(&scratch), n_scr * sizeof(float2), st), "scratch");
-        a.scratch = scratch;
+        if (n_scr > p->adj_scratch_elems) {
+            // the previous call ended with a synchronize, so the old buffer is idle
+            if (p->adj_scratch) {
+                cudaFree(p->adj_scratch);
+                p->bytes -= (int64_t)(p->adj_scratch_elems * sizeof(float2));
+            }
+            p->adj_scratch = nullptr;
+            p->adj_scratch_elems = 0;
+            void *q = nullptr;
+            if (cudaMalloc(&q, n_scr * sizeof(float2)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(TACAW_ERR_OOM, "adjoint scratch of %zu bytes", n_scr * sizeof(float2));
+            }
+            p->adj_scratch = static_cast<float2 *>(q);
+            p->adj_scratch_elems = n_scr;
+            p->bytes += (int64_t)(n_scr * sizeof(float2));
+        }
+        a.scratch = p->adj_scratch;
         // one segment, or each Welch segment at its start frame with weight 1/N, its gradient
-        // added where segments overlap
+        // added where segments overlap (one segment stores over the zeros, no read-back)
         const int nseg = u.N > 1 ? u.N : 1;
         cudaError_t e = cudaSuccess;
         for (int n = 0; n < nseg && e == cudaSuccess; ++n) {
@@ -1552,11 +1574,10 @@ tacaw_status tacaw_backward(tacaw_plan_t p, int sid, const float *d_dL_dS, const
             an.frames = a.frames + f0 * s.d.pitch_frame;
             an.grad = a.grad + f0 * s.d.pitch_frame;
             an.scale = 1.f / (float)nseg;
-            an.accumulate = 1;
+            an.accumulate = nseg > 1 ? 1 : 0;
             e = launch_adjoint(an, st);
             p->launches += 2;
         }
-        cudaFreeAsync(scratch, st);
         if (e != cudaSuccess) return cuda_fail(p, e, "adjoint");
     }
     return read_device_error(p, st);
