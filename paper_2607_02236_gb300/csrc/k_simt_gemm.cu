@@ -3,24 +3,66 @@
 // the windowed time->energy transform of Eq. 1 for the frames of one flush.  This is the
 // plain-precision path (and the baseline the tensor-core path is measured against).
 //
-// Tile: 128 rows x 64 complex energies per 256-thread block, 8 frames per step staged in
-// shared memory; each thread owns 8 rows x 4 energies (rows tx + 16 i, energies ty + 16 jj).
+// Tile: 128 rows x SN = 4*TY complex energies per block of 16 x TY threads; each thread owns
+// 8 rows x 4 energies (rows tx + 16 i, energies ty + TY q).  TY (8..16) is chosen per energy
+// count so that the tiles pad the energies least (200 or 400 energies: 40-wide tiles, none
+// padded).  Slices of 8 frames of both operands are copied global -> shared with cp.async
+// (16-byte pieces, no registers) into a 4-deep ring, so three slices are in flight while one is
+// multiplied; one barrier per slice.
 #include "tacaw_internal.cuh"
 
 namespace tacaw {
 
-constexpr int SB_M = 128, SB_N = 64, SB_K = 8;
+constexpr int SB_M = 128, SB_K = 8, SB_STAGES = 4;
 
-__global__ void __launch_bounds__(256) flush_simt_kernel(SimtArgs a, int n_jt) {
-    __shared__ float2 As[SB_K][SB_M];
-    __shared__ float2 Bs[SB_K][SB_N];
+template <int TY>
+constexpr size_t simt_smem_bytes() { return (size_t)SB_STAGES * SB_K * (SB_M + 4 * TY) * sizeof(float2); }
+
+__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, bool valid) {
+    // src-size 0 writes 16 zero bytes and reads nothing
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int TY>
+__global__ void __launch_bounds__(16 * TY) flush_simt_kernel(SimtArgs a, int n_jt) {
+    constexpr int NT = 16 * TY, SN = 4 * TY;
+    constexpr int A_CHUNKS = SB_K * SB_M / 2;    // 16-byte pieces of one A slice
+    constexpr int B_CHUNKS = SB_K * SN / 2;      // ... of one B slice (= NT: one per thread)
+    static_assert(B_CHUNKS == NT, "one B piece per thread");
+    extern __shared__ __align__(16) unsigned char simt_smem[];
+    float2 (*As)[SB_K][SB_M] = reinterpret_cast<float2 (*)[SB_K][SB_M]>(simt_smem);
+    float2 (*Bs)[SB_K][SN] =
+        reinterpret_cast<float2 (*)[SB_K][SN]>(simt_smem + (size_t)SB_STAGES * SB_K * SB_M * sizeof(float2));
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int jt = blockIdx.x % n_jt;
     const int64_t mt = blockIdx.x / n_jt;
     const int64_t m0 = mt * SB_M;
-    const int j0 = jt * SB_N;
+    const int j0 = jt * SN;
     const int64_t M_pad = a.e.M_pad;
+    const int n_slices = (a.n_frames + SB_K - 1) / SB_K;
+
+    // slice s into ring slot s % SB_STAGES; frames past n_frames and energies past the twiddle
+    // table's padded width are zero-filled (their addresses are not read)
+    auto issue = [&](int s) {
+        const int slot = s % SB_STAGES, k0 = s * SB_K;
+        for (int c = tid; c < A_CHUNKS; c += NT) {
+            const int kk = c / (SB_M / 2), ch = c % (SB_M / 2);
+            const bool ok = k0 + kk < a.n_frames;
+            const float2 *src = ok ? a.A32 + (size_t)(k0 + kk) * M_pad + m0 + 2 * ch : a.A32;
+            cp_async16_zfill((uint32_t)__cvta_generic_to_shared(&As[slot][kk][2 * ch]), src, ok);
+        }
+        {
+            const int kk = tid / (SN / 2), ch = tid % (SN / 2), col = j0 + 2 * ch;
+            const bool ok = k0 + kk < a.n_frames && col < a.Nw_pad;
+            const float2 *src = ok ? a.B32 + (size_t)(a.t0 + k0 + kk) * a.Nw_pad + col : a.B32;
+            cp_async16_zfill((uint32_t)__cvta_generic_to_shared(&Bs[slot][kk][2 * ch]), src, ok);
+        }
+    };
 
     float ar[8][4], ai[8][4];
 #pragma unroll
@@ -28,32 +70,24 @@ __global__ void __launch_bounds__(256) flush_simt_kernel(SimtArgs a, int n_jt) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) ar[i][q] = ai[i][q] = 0.f;
 
-    for (int k0 = 0; k0 < a.n_frames; k0 += SB_K) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int idx = tid + 256 * q;
-            int kk = idx >> 7, r = idx & 127;
-            float2 v = make_float2(0.f, 0.f);
-            if (k0 + kk < a.n_frames) v = a.A32[(size_t)(k0 + kk) * M_pad + m0 + r];
-            As[kk][r] = v;
-        }
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            int idx = tid + 256 * q;
-            int kk = idx >> 6, c = idx & 63;
-            float2 v = make_float2(0.f, 0.f);
-            if (k0 + kk < a.n_frames && j0 + c < a.e.Nw)
-                v = a.B32[(size_t)(a.t0 + k0 + kk) * a.Nw_pad + j0 + c];
-            Bs[kk][c] = v;
-        }
-        __syncthreads();
+    for (int s = 0; s < SB_STAGES - 1; ++s) {
+        if (s < n_slices) issue(s);
+        cp_async_commit();
+    }
+    for (int s = 0; s < n_slices; ++s) {
+        cp_async_wait<SB_STAGES - 2>();     // slice s has landed (for this thread's pieces) ...
+        __syncthreads();                    // ... and for every thread's; slot (s-1) is free
+        if (s + SB_STAGES - 1 < n_slices) issue(s + SB_STAGES - 1);
+        cp_async_commit();
+        const int slot = s % SB_STAGES;
 #pragma unroll
         for (int kk = 0; kk < SB_K; ++kk) {
             float2 x[8], b[4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) x[i] = As[kk][tx + 16 * i];
+            for (int i = 0; i < 8; ++i) x[i] = As[slot][kk][tx + 16 * i];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) b[q] = Bs[kk][ty + 16 * q];
+            for (int q = 0; q < 4; ++q) b[q] = Bs[slot][kk][ty + TY * q];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -64,8 +98,8 @@ __global__ void __launch_bounds__(256) flush_simt_kernel(SimtArgs a, int n_jt) {
                     ai[i][q] = fmaf(x[i].y, b[q].x, ai[i][q]);
                 }
         }
-        __syncthreads();
     }
+    cp_async_wait<0>();
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int64_t m = m0 + tx + 16 * i;
@@ -73,19 +107,49 @@ __global__ void __launch_bounds__(256) flush_simt_kernel(SimtArgs a, int n_jt) {
         if (!row.valid) continue;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int j = j0 + ty + 16 * q;
+            const int j = j0 + ty + TY * q;
             if (j < a.e.Nw) epi_element(a.e, row, j, ar[i][q], ai[i][q]);
         }
     }
 }
 
-cudaError_t launch_flush_simt(const SimtArgs &a, cudaStream_t st) {
-    const int n_jt = (a.e.Nw + SB_N - 1) / SB_N;
+// energies per block tile 4*TY, TY in 8..16 even: the width with the fewest padded energy
+// columns, the wider one on ties
+static int simt_tile_ty(int Nw) {
+    int best = 16;
+    int64_t best_cols = INT64_MAX;
+    for (int ty = 16; ty >= 8; ty -= 2) {
+        const int64_t cols = (int64_t)(Nw + 4 * ty - 1) / (4 * ty) * (4 * ty);
+        if (cols < best_cols) {
+            best_cols = cols;
+            best = ty;
+        }
+    }
+    return best;
+}
+
+template <int TY>
+cudaError_t launch_simt_ty(const SimtArgs &a, cudaStream_t st) {
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        flush_simt_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)simt_smem_bytes<TY>());
+    if (attr != cudaSuccess) return attr;
+    const int n_jt = (a.e.Nw + 4 * TY - 1) / (4 * TY);
     const int64_t n_mt = a.e.M_pad / SB_M;
     const int64_t blocks = n_mt * n_jt;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    flush_simt_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, n_jt);
+    flush_simt_kernel<TY><<<(unsigned)blocks, 16 * TY, simt_smem_bytes<TY>(), st>>>(a, n_jt);
     return cudaGetLastError();
+}
+
+cudaError_t launch_flush_simt(const SimtArgs &a, cudaStream_t st) {
+    if (a.e.M_pad % SB_M != 0 || a.Nw_pad % 2 != 0) return cudaErrorInvalidValue;
+    switch (simt_tile_ty(a.e.Nw)) {
+        case 8: return launch_simt_ty<8>(a, st);
+        case 10: return launch_simt_ty<10>(a, st);
+        case 12: return launch_simt_ty<12>(a, st);
+        case 14: return launch_simt_ty<14>(a, st);
+        default: return launch_simt_ty<16>(a, st);
+    }
 }
 
 }  // namespace tacaw
