@@ -4,11 +4,11 @@
 // plain-precision path (and the baseline the tensor-core path is measured against).
 //
 // Tile: 128 rows x SN = 4*TY complex energies per block of 16 x TY threads; each thread owns
-// 8 rows x 4 energies (rows tx + 16 i, energies ty + TY q).  TY (8..16) is chosen per energy
-// count so that the tiles pad the energies least (200 or 400 energies: 40-wide tiles, none
-// padded).  Slices of 8 frames of both operands are copied global -> shared with cp.async
-// (16-byte pieces, no registers) into a 4-deep ring, so three slices are in flight while one is
-// multiplied; one barrier per slice.
+// 8 rows x 4 energies (rows tx + 16 i, energies ty + TY q).  TY = 16 (64 energies) or 8 (32
+// energies), whichever pads the energy count less (200 or 400 energies: 32).  Slices of 8
+// frames of both operands are copied global -> shared with cp.async (16-byte pieces, no
+// registers) into a 4-deep ring, so three slices are in flight while one is multiplied; one
+// barrier per slice.
 #include "tacaw_internal.cuh"
 
 namespace tacaw {
@@ -113,19 +113,12 @@ __global__ void __launch_bounds__(16 * TY) flush_simt_kernel(SimtArgs a, int n_j
     }
 }
 
-// energies per block tile 4*TY, TY in 8..16 even: the width with the fewest padded energy
-// columns, the wider one on ties
+// energies per block tile: 64 (8 warps) unless 32 (4 warps) pads the energies less.  Blocks of 4
+// or 8 warps keep the SM's four schedulers evenly loaded; measured on 200 and 400 energies, the
+// 40-wide tile (5 warps, no padding) is slower than either
 static int simt_tile_ty(int Nw) {
-    int best = 16;
-    int64_t best_cols = INT64_MAX;
-    for (int ty = 16; ty >= 8; ty -= 2) {
-        const int64_t cols = (int64_t)(Nw + 4 * ty - 1) / (4 * ty) * (4 * ty);
-        if (cols < best_cols) {
-            best_cols = cols;
-            best = ty;
-        }
-    }
-    return best;
+    const int64_t cols64 = (int64_t)(Nw + 63) / 64 * 64, cols32 = (int64_t)(Nw + 31) / 32 * 32;
+    return cols64 <= cols32 ? 16 : 8;
 }
 
 template <int TY>
@@ -143,13 +136,7 @@ cudaError_t launch_simt_ty(const SimtArgs &a, cudaStream_t st) {
 
 cudaError_t launch_flush_simt(const SimtArgs &a, cudaStream_t st) {
     if (a.e.M_pad % SB_M != 0 || a.Nw_pad % 2 != 0) return cudaErrorInvalidValue;
-    switch (simt_tile_ty(a.e.Nw)) {
-        case 8: return launch_simt_ty<8>(a, st);
-        case 10: return launch_simt_ty<10>(a, st);
-        case 12: return launch_simt_ty<12>(a, st);
-        case 14: return launch_simt_ty<14>(a, st);
-        default: return launch_simt_ty<16>(a, st);
-    }
+    return simt_tile_ty(a.e.Nw) == 8 ? launch_simt_ty<8>(a, st) : launch_simt_ty<16>(a, st);
 }
 
 }  // namespace tacaw

@@ -268,6 +268,39 @@ __device__ __forceinline__ void drain_add(float (&sum)[C], uint32_t taddr, int c
     }
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// L2 prefetch of what this thread's flush epilogue will read for row m (earlier flushes'
+// accumulators, I when Welch segments add into it).  Each of the epilogue's reads feeds a store
+// that the next read may not pass (the compiler cannot tell the addresses apart), and the 112
+// running sums leave no registers to batch them under the 168-register cap of a 10-warp CTA;
+// so the reads are issued as prefetches while the tile's last chunk of products runs, and the
+// epilogue's chain of reads then waits on L2 rather than DRAM.
+__device__ __forceinline__ void tc_epilogue_prefetch(const TcPlanArgs &a, int64_t m, int col0, int cols, int jbase) {
+    const EpiArgs &e = a.e;
+    if (m >= e.M) return;
+    const int kind = epi_kind(e);
+    const bool acc32 = kind == EPI_ADD_KAHAN || kind == EPI_FINAL_KAHAN;
+    const bool acc64 = kind == EPI_ADD_FP64 || kind == EPI_FINAL_FP64;
+    const bool iadd = (kind == EPI_FINAL || kind == EPI_FINAL_KAHAN || kind == EPI_FINAL_FP64) && e.I_out && e.out_add;
+    if (!acc32 && !acc64 && !iadd) return;
+    const int64_t p = m / e.npix;
+    const int64_t o0 = p * (int64_t)e.Nw * e.npix + (m - p * e.npix);
+    for (int c = 0; c < cols; c += 2) {
+        const int j = jbase + ((col0 + c) >> 1);
+        if (j >= e.Nw) break;
+        const size_t ai = (size_t)j * (size_t)e.M_pad + (size_t)m;
+        if (acc32) {
+            prefetch_l2(e.acc_s + ai);
+            if (e.acc_c) prefetch_l2(e.acc_c + ai);
+        }
+        if (acc64) prefetch_l2(e.acc_d + ai);
+        if (iadd) prefetch_l2(e.I_out + o0 + (int64_t)j * e.npix);
+    }
+}
+
 // Flush epilogue of the split drained form: the tile's result is all in the running sums.
 template <int KIND, int C>
 __device__ __forceinline__ void tc_epilogue_regs(const TcPlanArgs &a, const RowCtx &row, int col0, int cols,
@@ -584,6 +617,7 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
                 if (lane == 0) mbar_arrive(smem_u32(&sh->chunk_free[0]));
             }
             if (!ok) break;
+            tc_epilogue_prefetch(a, (int64_t)m0 + q4 * 32 + lane, col0, cols, wtile * a.wt);
             if (!mbar_wait(smem_u32(&sh->chunk_full[1]), (uint32_t)(tiles & 1), abort_flag, wait_ns)) {
                 if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
                 *abort_flag = 1;

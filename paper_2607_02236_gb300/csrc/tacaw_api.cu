@@ -1253,8 +1253,14 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
                          (long long)budget));
     }
     p->k_stage = K;
+    // each segment in equal flush rounds of at most K frames (the same number of rounds as K
+    // gives, none of them a short remainder): a flush's tiles then all carry about as many
+    // frames as the others, enough to cover their epilogue
+    const int ring_unit = p->in_place ? 32 : (p->prec == TACAW_PREC_SPLIT_BF16 ? p->bf : 8);
     for (auto &s : p->s) {
-        s.ring = std::min(K, s.T_pad);
+        const int rounds = (s.T_pad + K - 1) / K;
+        const int even = (s.T_pad + rounds - 1) / rounds;
+        s.ring = std::min({K, s.T_pad, (even + ring_unit - 1) / ring_unit * ring_unit});
         s.needs_acc = s.T > s.ring;
     }
     if (p->prec == TACAW_PREC_SPLIT_BF16) {

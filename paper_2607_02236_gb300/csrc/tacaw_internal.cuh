@@ -175,6 +175,20 @@ __host__ __device__ inline int epi_kind(const EpiArgs &a) {
     return a.accum ? EPI_FINAL_FP64 : EPI_FINAL_KAHAN;
 }
 
+// Read of an accumulator element that this thread alone reads once and then writes in the
+// launch: written as an asm statement without a memory clobber, so the compiler may issue it
+// ahead of the stores to the other elements (the store that follows it depends on its value).
+__device__ __forceinline__ float2 ld_own(const float2 *p) {
+    float2 v;
+    asm("ld.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double2 ld_own(const double2 *p) {
+    double2 v;
+    asm("ld.global.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
+
 template <int K>
 __device__ __forceinline__ void epi_apply(const EpiArgs &a, const RowCtx &r, int j, float re, float im, float2 W,
                                           float bj) {
@@ -186,7 +200,7 @@ __device__ __forceinline__ void epi_apply(const EpiArgs &a, const RowCtx &r, int
         a.acc_d[ai] = make_double2(re, im);
     } else if (K == EPI_ADD_KAHAN) {
         if (a.acc_c) {
-            float2 s = a.acc_s[ai], c = a.acc_c[ai];
+            float2 s = ld_own(a.acc_s + ai), c = ld_own(a.acc_c + ai);
             float yr = re - c.x, yi = im - c.y;
             float tr = s.x + yr, ti = s.y + yi;
             c.x = (tr - s.x) - yr;
@@ -194,22 +208,24 @@ __device__ __forceinline__ void epi_apply(const EpiArgs &a, const RowCtx &r, int
             a.acc_s[ai] = make_float2(tr, ti);
             a.acc_c[ai] = c;
         } else {
-            const float2 s = a.acc_s[ai];   // plain FP32 accumulators
+            const float2 s = ld_own(a.acc_s + ai);   // plain FP32 accumulators
             a.acc_s[ai] = make_float2(s.x + re, s.y + im);
         }
     } else if (K == EPI_ADD_FP64) {
-        double2 s = a.acc_d[ai];
+        double2 s = ld_own(a.acc_d + ai);
         s.x += re;
         s.y += im;
         a.acc_d[ai] = s;
     } else {
+        // a launch that finalizes a stream writes none of its accumulators, so they are read
+        // through the read-only path: those loads may be moved ahead of this loop's stores
         float pr = re, pi = im;
         if (K == EPI_FINAL_KAHAN) {
-            const float2 s = a.acc_s[ai], c = a.acc_c ? a.acc_c[ai] : make_float2(0.f, 0.f);
+            const float2 s = __ldg(a.acc_s + ai), c = a.acc_c ? __ldg(a.acc_c + ai) : make_float2(0.f, 0.f);
             pr = s.x + (re - c.x);
             pi = s.y + (im - c.y);
         } else if (K == EPI_FINAL_FP64) {
-            double2 s = a.acc_d[ai];
+            const double2 s = __ldg(a.acc_d + ai);
             pr = (float)(s.x + (double)re);
             pi = (float)(s.y + (double)im);
         }
