@@ -44,9 +44,9 @@ FLOP_PER_CMAC_FP32 = 8
 # reported only for that workload and while the source is unchanged.
 KERNEL_TRAFFIC = {
     # ncu --set full of flush_tc_drain2_kernel on `bench.py --small --no-extras` (the thick workload with
-    # 1 probe: 65536 rows, T = 8192, 1000 energies, 5.369e11 CMAC per launch): 8.589699 GB read +
-    # 0.263999 GB written per launch
-    ("511cc0a4043fe6a1", "flush_tc_drain2_kernel", "thick"): 1.649137e-02,
+    # 1 probe: 65536 rows, T = 8192, 1000 energies, 5.369e11 CMAC per launch): 8.586223 GB read +
+    # 0.263617 GB written per launch
+    ("06406ff05b0447e2", "flush_tc_drain2_kernel", "thick"): 1.648411e-02,
 }
 
 

@@ -177,10 +177,13 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t
     if (F16 && amax > kF16Max) atomicOr(err, DEVERR_FP16_RANGE);
 }
 
-// Whole staging blocks (s0 and n multiples of bf): 128 rows per CTA.  Each thread converts
-// its row's bf frames into a shared tile (16-byte chunks XOR-swizzled by row to spread the
-// banks); the CTA then writes the 128 contiguous rows of the block with consecutive
-// threads on consecutive 16-byte chunks, so every warp store is one contiguous 512 bytes.
+// Staging blocks of BF frames, 128 rows per CTA, for pushes whose start s0 and length n are
+// multiples of 4 frames (one 16-byte chunk of a row): the push is walked in pieces that each
+// lie inside one block (a whole block, or part of one when a push is shorter than a block or
+// starts inside one).  Each thread converts its row's frames of the piece into a shared tile
+// (16-byte chunks XOR-swizzled by row to spread the banks); the CTA then writes the piece's
+// chunks of the 128 rows with consecutive threads on consecutive chunks.  The stored swizzle
+// only exchanges chunks inside 32-byte sectors, so a piece always writes whole sectors.
 template <int BF, bool F16>
 __global__ void __launch_bounds__(128) convert_split_tiled_kernel(FrameGeom g, int n, int s0, int64_t M_pad,
                                                                   const float2 *mu_hat, double2 *sum_res,
@@ -199,22 +202,27 @@ __global__ void __launch_bounds__(128) convert_split_tiled_kernel(FrameGeom g, i
     uint4 *Lo = reinterpret_cast<uint4 *>(A_lo);
     double sr = 0.0, si = 0.0;
     float amax = 0.f;
-    for (int t0 = 0; t0 < n; t0 += bf) {
+    for (int t0 = 0; t0 < n;) {
+        const int f0 = (s0 + t0) % bf;                 // first frame of the piece inside its block
+        const int len = min(bf - f0, n - t0);          // a multiple of 4
+        const int c0 = f0 / 4, nc = len / 4;
         float2 v[BF];
 #pragma unroll
         for (int i = 0; i < BF; ++i)
-            v[i] = valid ? __ldcs(src + (int64_t)(t0 + i) * g.pitch_frame) : make_float2(0.f, 0.f);
+            v[i] = (valid && i < len) ? __ldcs(src + (int64_t)(t0 + i) * g.pitch_frame) : make_float2(0.f, 0.f);
         float br = 0.f, bi = 0.f;
 #pragma unroll
-        for (int c = 0; c < cpr; ++c) {
+        for (int k = 0; k < cpr; ++k) {
+            if (k >= nc) break;
             uint32_t h[4], l[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                float2 q = valid ? make_float2(v[4 * c + i].x - mu.x, v[4 * c + i].y - mu.y) : make_float2(0.f, 0.f);
+                float2 q = valid ? make_float2(v[4 * k + i].x - mu.x, v[4 * k + i].y - mu.y) : make_float2(0.f, 0.f);
                 br += q.x;
                 bi += q.y;
                 split2<F16>(q, sc, amax, h[i], l[i]);
             }
+            const int c = c0 + k;
             const int slot = r * cpr + (c ^ (r & (cpr - 1)));
             tile_h[slot] = make_uint4(h[0], h[1], h[2], h[3]);
             tile_l[slot] = make_uint4(l[0], l[1], l[2], l[3]);
@@ -223,8 +231,8 @@ __global__ void __launch_bounds__(128) convert_split_tiled_kernel(FrameGeom g, i
         si += bi;
         __syncthreads();
         const size_t base = ((size_t)((s0 + t0) / bf) * M_pad + m0) * cpr;   // in 16-byte units
-        for (int q = r; q < 128 * cpr; q += 128) {
-            const int rr = q / cpr, c = q - (q / cpr) * cpr;
+        for (int q = r; q < 128 * nc; q += 128) {
+            const int rr = q / nc, c = c0 + (q - (q / nc) * nc);
             const int slot = rr * cpr + (c ^ (rr & (cpr - 1)));
             // stored chunk position of chunk c (m0 is a multiple of 128: row rr's pattern)
             const int cs = swz ? (c ^ (((rr * cpr) >> 3) & (cpr - 1))) : c;
@@ -232,6 +240,7 @@ __global__ void __launch_bounds__(128) convert_split_tiled_kernel(FrameGeom g, i
             Lo[base + rr * cpr + cs] = tile_l[slot];
         }
         __syncthreads();
+        t0 += len;
     }
     if (valid) {
         double2 a = sum_res[m];
@@ -319,7 +328,7 @@ template <bool F16>
 static cudaError_t convert_split(const FrameGeom &g, int n, int s0, int bf, int64_t M_pad, const float2 *mu_hat,
                                  double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz, float sc,
                                  uint32_t *err, cudaStream_t st) {
-    if (bf >= 16 && s0 % bf == 0 && n % bf == 0) {
+    if (bf >= 16 && s0 % 4 == 0 && n % 4 == 0) {
         const unsigned grid = (unsigned)(M_pad / 128);
         if (bf == 32)
             convert_split_tiled_kernel<32, F16><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo,
