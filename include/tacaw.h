@@ -247,6 +247,20 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out);
 tacaw_status tacaw_push_frames(tacaw_plan_t plan, int stream_id, const void *d_frames,
                                int n_frames, void *stream);
 
+/* Sec. III.C / Sec. IV, supercell partitions of uneven size streamed side by side: one push
+ * of each of n distinct streams, with the same result as n calls of tacaw_push_frames
+ * (stream_ids[i], d_frames[i], n_frames[i]) on `stream`.  Pushes on the staged split path
+ * that fit their stream's staging ring, with n_frames and the ring position multiples of 4,
+ * are converted by one kernel launch over all of them (groups of up to 16); the others run
+ * as single pushes.  A ring that fills defers its flush to the next push of any of these
+ * streams, where the due flushes go out as one grouped launch.
+ * stream_ids, d_frames, n_frames: host arrays of n entries (n >= 1).
+ * Errors: every entry is checked as tacaw_push_frames checks it, and a stream_id that
+ * appears twice is INVALID_ARG, all before any work is enqueued; a CUDA error poisons the
+ * plan.                                                                                   */
+tacaw_status tacaw_push_frames_group(tacaw_plan_t plan, int n, const int *stream_ids,
+                                     const void *const *d_frames, const int *n_frames, void *stream);
+
 /* Eq. 1 (I = B(E) |phi_MD|^2) and the DetectorSet sum over apertures (Sec. II.B).
  * Completes the segment of every stream: flushes what is staged, applies the exact
  * mean correction Psi -= (mu - mu_hat) W(E_j), W the window's transform, forms I and

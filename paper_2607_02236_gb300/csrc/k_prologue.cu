@@ -184,16 +184,16 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t
 // (16-byte chunks XOR-swizzled by row to spread the banks); the CTA then writes the piece's
 // chunks of the 128 rows with consecutive threads on consecutive chunks.  The stored swizzle
 // only exchanges chunks inside 32-byte sectors, so a piece always writes whole sectors.
+// The rows of block `blk` (rows 128 blk ..) of one push; run by 128 threads.
 template <int BF, bool F16>
-__global__ void __launch_bounds__(128) convert_split_tiled_kernel(FrameGeom g, int n, int s0, int64_t M_pad,
-                                                                  const float2 *mu_hat, double2 *sum_res,
-                                                                  __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz,
-                                                                  float sc, uint32_t *err) {
+__device__ __forceinline__ void convert_tiled_rows(const FrameGeom &g, int n, int s0, int64_t M_pad,
+                                                   const float2 *mu_hat, double2 *sum_res, __nv_bfloat16 *A_hi,
+                                                   __nv_bfloat16 *A_lo, int swz, float sc, uint32_t *err, int64_t blk) {
     constexpr int bf = BF;
     constexpr int cpr = BF / 4;             // 16-byte chunks per row
     __shared__ uint4 tile_h[128 * cpr], tile_l[128 * cpr];
     const int r = threadIdx.x;
-    const int64_t m0 = (int64_t)blockIdx.x * 128;
+    const int64_t m0 = blk * 128;
     const int64_t m = m0 + r;
     const bool valid = m < g.M;
     const float2 *src = valid ? row_src(g, m) : nullptr;
@@ -249,6 +249,26 @@ __global__ void __launch_bounds__(128) convert_split_tiled_kernel(FrameGeom g, i
         sum_res[m] = a;
     }
     if (F16 && amax > kF16Max) atomicOr(err, DEVERR_FP16_RANGE);
+}
+
+template <int BF, bool F16>
+__global__ void __launch_bounds__(128) convert_split_tiled_kernel(FrameGeom g, int n, int s0, int64_t M_pad,
+                                                                  const float2 *mu_hat, double2 *sum_res,
+                                                                  __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz,
+                                                                  float sc, uint32_t *err) {
+    convert_tiled_rows<BF, F16>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo, swz, sc, err, blockIdx.x);
+}
+
+// One push of each of several streams in one launch: CTA b converts block b - e.cta_begin of
+// the entry whose range holds b (entries in order of cta_begin).
+template <int BF, bool F16>
+__global__ void __launch_bounds__(128) convert_split_group_kernel(const __grid_constant__ ConvGroup cg, int swz,
+                                                                  float sc, uint32_t *err) {
+    int k = 0;
+    while (k + 1 < cg.n && (int64_t)blockIdx.x >= cg.e[k + 1].cta_begin) ++k;
+    const ConvEntry &e = cg.e[k];
+    convert_tiled_rows<BF, F16>(e.g, e.n, e.s0, e.M_pad, e.mu_hat, e.sum_res, e.A_hi, e.A_lo, swz, sc, err,
+                                (int64_t)blockIdx.x - e.cta_begin);
 }
 
 __global__ void convert_fp32_kernel(FrameGeom g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
@@ -328,7 +348,7 @@ template <bool F16>
 static cudaError_t convert_split(const FrameGeom &g, int n, int s0, int bf, int64_t M_pad, const float2 *mu_hat,
                                  double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz, float sc,
                                  uint32_t *err, cudaStream_t st) {
-    if (bf >= 16 && s0 % 4 == 0 && n % 4 == 0) {
+    if (convert_split_groupable(bf, s0, n)) {
         const unsigned grid = (unsigned)(M_pad / 128);
         if (bf == 32)
             convert_split_tiled_kernel<32, F16><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo,
@@ -348,6 +368,31 @@ cudaError_t launch_convert_split(const FrameGeom &g, int n, int s0, int bf, int6
                                  float f16_scale, uint32_t *err, cudaStream_t st) {
     if (f16) return convert_split<true>(g, n, s0, bf, M_pad, mu_hat, sum_res, A_hi, A_lo, swz, f16_scale, err, st);
     return convert_split<false>(g, n, s0, bf, M_pad, mu_hat, sum_res, A_hi, A_lo, swz, 1.f, err, st);
+}
+
+bool convert_split_groupable(int bf, int s0, int n) { return bf >= 16 && s0 % 4 == 0 && n % 4 == 0; }
+
+cudaError_t launch_convert_split_group(ConvGroup &cg, int bf, int swz, int f16, float f16_scale, uint32_t *err,
+                                       cudaStream_t st) {
+    if (cg.n < 1 || cg.n > kConvGroupMax || (bf != 16 && bf != 32)) return cudaErrorInvalidValue;
+    int64_t ctas = 0;
+    for (int i = 0; i < cg.n; ++i) {
+        if (!convert_split_groupable(bf, cg.e[i].s0, cg.e[i].n) || cg.e[i].M_pad % 128) return cudaErrorInvalidValue;
+        cg.e[i].cta_begin = ctas;
+        ctas += cg.e[i].M_pad / 128;
+    }
+    if (ctas == 0) return cudaSuccess;
+    if (ctas > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const unsigned grid = (unsigned)ctas;
+    const float sc = f16 ? f16_scale : 1.f;
+    if (bf == 32) {
+        if (f16) convert_split_group_kernel<32, true><<<grid, 128, 0, st>>>(cg, swz, sc, err);
+        else convert_split_group_kernel<32, false><<<grid, 128, 0, st>>>(cg, swz, sc, err);
+    } else {
+        if (f16) convert_split_group_kernel<16, true><<<grid, 128, 0, st>>>(cg, swz, sc, err);
+        else convert_split_group_kernel<16, false><<<grid, 128, 0, st>>>(cg, swz, sc, err);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_convert_fp32(const FrameGeom &g, int n, int s0, int64_t M_pad, const float2 *mu_hat,

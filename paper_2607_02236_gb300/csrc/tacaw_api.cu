@@ -1331,9 +1331,12 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
     return TACAW_OK;
 }
 
-tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, int n_frames, void *stream) {
-    tacaw_status c = check_plan(p);
-    if (c != TACAW_OK) return c;
+}  // extern "C"
+
+namespace {
+
+// The checks of one push, before any device work.
+tacaw_status validate_push(tacaw_plan_s *p, int sid, const void *d_frames, int n_frames, cudaStream_t st) {
     if (sid < 0 || sid >= (int)p->us.size()) return fail(TACAW_ERR_INVALID_ARG, "stream_id %d out of range", sid);
     if (!d_frames) return fail(TACAW_ERR_INVALID_ARG, "d_frames is NULL");
     if (n_frames < 1) return fail(TACAW_ERR_INVALID_ARG, "n_frames must be >= 1");
@@ -1341,14 +1344,18 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
     if ((reinterpret_cast<uintptr_t>(d_frames) & 7) != 0) return fail(TACAW_ERR_INVALID_ARG, "d_frames must be 8-byte aligned");
     if (p->in_place && (reinterpret_cast<uintptr_t>(d_frames) & 15) != 0)
         return fail(TACAW_ERR_INVALID_ARG, "in-place frames must be 16-byte aligned (contiguous row copies)");
-    tacaw_status pk = check_kernel_memory(d_frames, "d_frames", !p->in_place, static_cast<cudaStream_t>(stream));
+    tacaw_status pk = check_kernel_memory(d_frames, "d_frames", !p->in_place, st);
     if (pk != TACAW_OK) return pk;
-    UserStream &u = p->us[sid];
+    const UserStream &u = p->us[sid];
     if (u.pushed + n_frames > u.total)
         return fail(TACAW_ERR_OVERFLOW, "push of %d frames exceeds %lld (already %lld)", n_frames, (long long)u.total,
                     (long long)u.pushed);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const float2 *base = static_cast<const float2 *>(d_frames);
+    return TACAW_OK;
+}
+
+// One validated push of a user stream.
+tacaw_status push_user(tacaw_plan_s *p, int sid, const float2 *base, int n_frames, cudaStream_t st) {
+    UserStream &u = p->us[sid];
     // leading frames of the stream that precede its first segment are dropped unread
     if (u.pushed + n_frames <= u.skip) {
         u.pushed += n_frames;
@@ -1383,6 +1390,105 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
         }
     }
     u.pushed = u.skip + b;
+    return TACAW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, int n_frames, void *stream) {
+    tacaw_status c = check_plan(p);
+    if (c != TACAW_OK) return c;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c = validate_push(p, sid, d_frames, n_frames, st);
+    if (c != TACAW_OK) return c;
+    return push_user(p, sid, static_cast<const float2 *>(d_frames), n_frames, st);
+}
+
+tacaw_status tacaw_push_frames_group(tacaw_plan_t p, int n, const int *stream_ids, const void *const *d_frames,
+                                     const int *n_frames, void *stream) {
+    tacaw_status c = check_plan(p);
+    if (c != TACAW_OK) return c;
+    if (n < 1 || !stream_ids || !d_frames || !n_frames)
+        return fail(TACAW_ERR_INVALID_ARG, "push group: n >= 1 and non-NULL arrays required");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<char> seen(p->us.size(), 0);
+    for (int i = 0; i < n; ++i) {
+        c = validate_push(p, stream_ids[i], d_frames[i], n_frames[i], st);
+        if (c != TACAW_OK) return c;
+        if (seen[stream_ids[i]]) return fail(TACAW_ERR_INVALID_ARG, "push group: stream_id %d appears twice", stream_ids[i]);
+        seen[stream_ids[i]] = 1;
+    }
+    // deferred flushes of these streams go first (flush_due runs every due flush, grouped)
+    const bool split = p->prec == TACAW_PREC_SPLIT_BF16 && !p->in_place;
+    for (int i = 0; i < n; ++i) {
+        const UserStream &u = p->us[stream_ids[i]];
+        if (u.N <= 1 && p->s[u.first].due) {
+            c = flush_due(p, st);
+            if (c != TACAW_OK) return c;
+            break;
+        }
+    }
+    // pushes that fit their stream's ring as one tiled conversion go out together, the others
+    // one by one as tacaw_push_frames does them
+    std::vector<int> grouped;
+    for (int i = 0; i < n; ++i) {
+        const UserStream &u = p->us[stream_ids[i]];
+        const Stream &s = p->s[u.first];
+        const bool ok = split && u.N <= 1 && u.pushed >= u.skip && !s.due && s.staged + n_frames[i] <= s.ring &&
+                        convert_split_groupable(p->bf, s.staged, n_frames[i]);
+        if (ok) {
+            grouped.push_back(i);
+        } else {
+            c = push_user(p, stream_ids[i], static_cast<const float2 *>(d_frames[i]), n_frames[i], st);
+            if (c != TACAW_OK) return c;
+        }
+    }
+    for (size_t g0 = 0; g0 < grouped.size(); g0 += kConvGroupMax) {
+        ConvGroup cg{};
+        cg.n = (int)std::min(grouped.size() - g0, (size_t)kConvGroupMax);
+        for (int k = 0; k < cg.n; ++k) {
+            const int i = grouped[g0 + k];
+            Stream &s = p->s[p->us[stream_ids[i]].first];
+            ConvEntry &e = cg.e[k];
+            e.g.base = static_cast<const float2 *>(d_frames[i]);
+            e.g.pitch_row = s.d.pitch_row;
+            e.g.pitch_frame = s.d.pitch_frame;
+            e.g.pitch_probe = s.d.pitch_probe;
+            e.g.roi_x0 = s.d.roi_x0;
+            e.g.roi_y0 = s.d.roi_y0;
+            e.g.kx = s.d.kx;
+            e.g.ky = s.d.ky;
+            e.g.npix = s.npix;
+            e.g.M = s.M;
+            e.n = n_frames[i];
+            e.s0 = s.staged;
+            e.M_pad = s.M_pad;
+            e.mu_hat = s.mu_hat;
+            e.sum_res = s.sum_res;
+            e.A_hi = s.A_hi;
+            e.A_lo = s.A_lo;
+            if (s.pushed == 0 && s.d.subtract_mean) {
+                CU_CHECK(p, launch_mean(e.g, e.n, s.mu_hat, st), "provisional mean");
+                p->launches++;
+            }
+        }
+        CU_CHECK(p, launch_convert_split_group(cg, p->bf, 1, p->f16, p->f16_scale, p->d_err, st), "convert (group)");
+        p->launches++;
+        for (int k = 0; k < cg.n; ++k) {
+            const int i = grouped[g0 + k];
+            UserStream &u = p->us[stream_ids[i]];
+            Stream &s = p->s[u.first];
+            s.staged += n_frames[i];
+            s.pushed += n_frames[i];
+            u.pushed += n_frames[i];
+            if (s.staged == s.ring && s.pushed < s.T) {
+                s.due = true;     // deferrable: split, staged, one segment
+                s.due_stream = st;
+            }
+        }
+    }
     return TACAW_OK;
 }
 

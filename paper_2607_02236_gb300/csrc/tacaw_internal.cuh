@@ -51,6 +51,22 @@ struct FrameGeom {
     int64_t M;                 // P*npix
 };
 
+// One push of one stream in a grouped split conversion (launch_convert_split_group).
+struct ConvEntry {
+    FrameGeom g;
+    int n, s0;                 // frames pushed, first ring slot
+    int64_t M_pad;
+    const float2 *mu_hat;
+    double2 *sum_res;
+    __nv_bfloat16 *A_hi, *A_lo;
+    int64_t cta_begin;         // set by the launcher
+};
+constexpr int kConvGroupMax = 16;
+struct ConvGroup {
+    ConvEntry e[kConvGroupMax];
+    int n;
+};
+
 // Per-element epilogue inputs (shared by the tensor-core and the FP32 contraction).
 struct EpiArgs {
     int64_t M, M_pad, npix;
@@ -267,6 +283,12 @@ cudaError_t launch_mean(const FrameGeom &g, int n, float2 *mu_hat, cudaStream_t 
 cudaError_t launch_convert_split(const FrameGeom &g, int n, int s0, int bf, int64_t M_pad, const float2 *mu_hat,
                                  double2 *sum_res, __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz, int f16,
                                  float f16_scale, uint32_t *err, cudaStream_t st);
+// the tiled split conversion takes the push (s0, n multiples of 4 frames, blocks of 16 or 32)
+bool convert_split_groupable(int bf, int s0, int n);
+// one launch over cg.n <= kConvGroupMax pushes of different streams (each groupable; the
+// launcher sets cta_begin); plan-wide block size, swizzle and fp16 settings
+cudaError_t launch_convert_split_group(ConvGroup &cg, int bf, int swz, int f16, float f16_scale, uint32_t *err,
+                                       cudaStream_t st);
 cudaError_t launch_convert_fp32(const FrameGeom &g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
                                 double2 *sum_res, float2 *A32, cudaStream_t st);
 cudaError_t launch_frame_table(const float2 **table, const float2 *base, int64_t pitch_frame, int n, cudaStream_t st);

@@ -28,7 +28,7 @@ EXPORTS = ["tacaw_plan_create", "tacaw_push_frames", "tacaw_finalize", "tacaw_ou
            "tacaw_backward", "tacaw_reset", "tacaw_plan_get_info", "tacaw_set_timing",
            "tacaw_kernel_time_ms", "tacaw_destroy", "tacaw_last_error", "tacaw_version",
            "tacaw_detector_spectra_noalloc", "tacaw_flush_trace", "tacaw_finalize_async",
-           "tacaw_check_errors", "tacaw_set_log_callback", "tacaw_set_wait_limit_ns"]
+           "tacaw_check_errors", "tacaw_set_log_callback", "tacaw_set_wait_limit_ns", "tacaw_push_frames_group"]
 
 
 class TacawError(RuntimeError):
@@ -83,6 +83,8 @@ def lib():
     L = ctypes.CDLL(LIB_PATH)
     L.tacaw_plan_create.argtypes = [POINTER(CPlanDesc), POINTER(c_void_p)]
     L.tacaw_push_frames.argtypes = [c_void_p, c_int, c_void_p, c_int, c_void_p]
+    L.tacaw_push_frames_group.argtypes = [c_void_p, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_void_p),
+                                          ctypes.POINTER(c_int), c_void_p]
     L.tacaw_finalize.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     L.tacaw_finalize_async.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     L.tacaw_check_errors.argtypes = [c_void_p, c_void_p]
@@ -221,6 +223,17 @@ class TacawPlan:
     # ---------------------------------------------------------------------------------
     def push(self, stream_id: int, frames, n_frames: int, cuda_stream=None):
         _check(lib().tacaw_push_frames(self._h, int(stream_id), _ptr(frames), int(n_frames), _stream(cuda_stream)))
+
+    def push_group(self, stream_ids, frames, n_frames, cuda_stream=None):
+        """One push of each of several streams (tacaw_push_frames_group): lists of stream ids,
+        frame buffers (tensors or addresses) and frame counts."""
+        n = len(stream_ids)
+        if len(frames) != n or len(n_frames) != n:
+            raise ValueError("stream_ids, frames and n_frames must have the same length")
+        ids = (c_int * n)(*[int(i) for i in stream_ids])
+        ptrs = (c_void_p * n)(*[_ptr(f) for f in frames])
+        cnt = (c_int * n)(*[int(k) for k in n_frames])
+        _check(lib().tacaw_push_frames_group(self._h, n, ids, ptrs, cnt, _stream(cuda_stream)))
 
     def finalize(self, I=None, S=None, Psi=None, cuda_stream=None):
         _check(lib().tacaw_finalize(self._h, _ptr(I), _ptr(S), _ptr(Psi), _stream(cuda_stream)))

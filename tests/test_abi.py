@@ -68,6 +68,7 @@ def test_invalid_descriptors_rejected_without_device_work(L):
 def test_null_plan_calls_are_errors(L):
     import paper_2607_02236_gb300.tacaw as t
     assert L.tacaw_push_frames(None, 0, None, 1, None) == t.ERR_INVALID_ARG
+    assert L.tacaw_push_frames_group(None, 1, None, None, None, None) == t.ERR_INVALID_ARG
     assert L.tacaw_finalize(None, None, None, None, None) == t.ERR_INVALID_ARG
     assert L.tacaw_destroy(None) == t.OK
 

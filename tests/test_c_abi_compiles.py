@@ -37,6 +37,11 @@ int main(void) {
     st = tacaw_plan_create(&d, &plan);
     if (st != TACAW_OK) { printf("%s\n", tacaw_last_error()); return 1; }
     st = tacaw_push_frames(plan, 0, NULL, 16, NULL);
+    {
+        int ids[1] = {0}, nf[1] = {16};
+        const void *fr[1] = {NULL};
+        st = tacaw_push_frames_group(plan, 1, ids, fr, nf, NULL);
+    }
     st = tacaw_finalize(plan, NULL, NULL, NULL, NULL);
     st = tacaw_finalize_async(plan, NULL, NULL, NULL, NULL);
     st = tacaw_check_errors(plan, NULL);

@@ -281,3 +281,128 @@ def test_flush_rounds_share_launches(capture):
             assert e <= TOL["split_bf16"], (i, e)
             worst = max(worst, e)
     print(f"flush rounds ({'graph' if capture else 'eager'}): worst max rel I error {worst:.3g}")
+
+
+def push_group_rounds(plan, specs, bufs, stream=None):
+    """Round-robin as push_all, but each round is one tacaw_push_frames_group call."""
+    pushed = [0] * len(specs)
+    calls = 0
+    while any(pushed[i] < s.T for i, s in enumerate(specs)):
+        ids, ptrs, cnt = [], [], []
+        for i, s in enumerate(specs):
+            if pushed[i] < s.T:
+                n = min(s.Tc, s.T - pushed[i])
+                fb = s.P * s.Kx * s.Ky * 8
+                ids.append(i)
+                ptrs.append(bufs[i].data_ptr() + pushed[i] * fb)
+                cnt.append(n)
+                pushed[i] += n
+        plan.push_group(ids, ptrs, cnt, cuda_stream=stream)
+        calls += 1
+    return calls
+
+
+def test_push_group_matches_single_pushes():
+    """tacaw_push_frames_group gives the same I and S, bit for bit, as one tacaw_push_frames per
+    stream (the same conversion of every row, the same flushes), with fewer launches: the
+    streams whose pushes are multiples of 4 frames share one conversion launch per round, the
+    ragged one (50-frame pushes) goes through the single-push path.  Both match the oracle."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    frames = [make_frames(s, 900 + i) for i, s in enumerate(SPECS)]
+    bufs = [device_frames(f) for f in frames]
+    out = []
+    for grouped in (False, True):
+        with TacawPlan([stream_config(s) for s in SPECS], precision="split_bf16") as plan:
+            info = plan.info()
+            I = torch.zeros(info["I_elems"], dtype=torch.float32, device="cuda")
+            S = torch.zeros(max(1, info["S_elems"]), dtype=torch.float32, device="cuda")
+            l0 = plan.info()["kernel_launches"]
+            if grouped:
+                push_group_rounds(plan, SPECS, bufs)
+            else:
+                push_all(plan, bufs)
+            pushes = plan.info()["kernel_launches"] - l0
+            plan.finalize(I, S)
+            check_all(plan, I, S, frames, TOL["split_bf16"])
+            out.append((I.cpu().numpy(), S.cpu().numpy(), pushes))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[1][2] < out[0][2], (out[0][2], out[1][2])
+
+
+@pytest.mark.parametrize("capture", [False, True], ids=["eager", "graph"])
+def test_push_group_flush_rounds(capture):
+    """The flush-round workload (K_stage = 64) pushed one group per round: rings that fill in
+    the same round flush together at the next group push -- 4 contraction launches for 9
+    flushes, as with single pushes -- eager and inside a captured CUDA graph, against the
+    oracle."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    frames = [make_frames(s, 950 + i) for i, s in enumerate(ROUNDS)]
+    bufs = [device_frames(f) for f in frames]
+    st = torch.cuda.Stream()
+    with TacawPlan([stream_config(s) for s in ROUNDS], precision="split_bf16", k_stage=64, accum="kahan") as plan:
+        info = plan.info()
+        I = torch.zeros(info["I_elems"], dtype=torch.float32, device="cuda")
+        S = torch.zeros(max(1, info["S_elems"]), dtype=torch.float32, device="cuda")
+        f0, n0 = info["flush_launches"], info["flushes"]
+        with torch.cuda.stream(st):
+            plan.reset(st)
+            push_group_rounds(plan, ROUNDS, bufs, st)
+            plan.finalize_async(I, S, cuda_stream=st)
+            plan.check_errors(st)
+        after = plan.info()
+        assert after["flushes"] - n0 == 9
+        assert after["flush_launches"] - f0 == 4
+        if capture:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=st):
+                cur = torch.cuda.current_stream()
+                plan.reset(cur)
+                push_group_rounds(plan, ROUNDS, bufs, cur)
+                plan.finalize_async(I, S, cuda_stream=cur)
+            frames = [make_frames(s, 980 + i) for i, s in enumerate(ROUNDS)]
+            for b, f in zip(bufs, frames):
+                b.copy_(device_frames(f))
+            I.zero_()
+            torch.cuda.synchronize()
+            g.replay()
+            torch.cuda.synchronize()
+            plan.check_errors(torch.cuda.current_stream())
+            del g
+        torch.cuda.synchronize()
+        for i, s in enumerate(ROUNDS):
+            ref = oracle.forward(frames[i], **oracle_kw(s))
+            io, so = plan.offsets(i)
+            n = s.P * s.Nw * s.Ky * s.Kx
+            e = rel_err_peak(I[io:io + n].cpu().numpy().reshape(s.P, s.Nw, s.Ky, s.Kx), ref.I)
+            assert e <= TOL["split_bf16"], (i, e)
+
+
+def test_push_group_refusals_leave_the_plan_unchanged():
+    """A repeated stream id, an entry past its segment's end, or an unreadable address refuses
+    the whole group before any work; the plan then takes the full segment as usual."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    from paper_2607_02236_gb300.tacaw import TacawError, ERR_INVALID_ARG, ERR_OVERFLOW
+    frames = [make_frames(s, 990 + i) for i, s in enumerate(SPECS)]
+    bufs = [device_frames(f) for f in frames]
+    with TacawPlan([stream_config(s) for s in SPECS], precision="split_bf16") as plan:
+        info = plan.info()
+        I = torch.zeros(info["I_elems"], dtype=torch.float32, device="cuda")
+        S = torch.zeros(max(1, info["S_elems"]), dtype=torch.float32, device="cuda")
+        l0 = plan.info()["kernel_launches"]
+        with pytest.raises(TacawError) as ei:
+            plan.push_group([0, 0], [bufs[0], bufs[0]], [8, 8])
+        assert ei.value.status == ERR_INVALID_ARG and "twice" in str(ei.value)
+        with pytest.raises(TacawError) as ei:
+            plan.push_group([0, 1], [bufs[0], bufs[1]], [8, SPECS[1].T + 4])
+        assert ei.value.status == ERR_OVERFLOW
+        host = np.zeros(64, dtype=np.complex64)
+        with pytest.raises(TacawError) as ei:
+            plan.push_group([0, 1], [bufs[0], host.ctypes.data], [8, 8])
+        assert ei.value.status == ERR_INVALID_ARG and "d_frames" in str(ei.value)
+        assert plan.info()["kernel_launches"] == l0
+        push_group_rounds(plan, SPECS, bufs)
+        plan.finalize(I, S)
+        check_all(plan, I, S, frames, TOL["split_bf16"])
