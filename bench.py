@@ -53,7 +53,7 @@ KERNEL_TRAFFIC = {
 def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="thick", choices=["thick", "realistic", "batched", "diff"],
@@ -227,6 +227,13 @@ def ffma_roofline(cmac_launch, kernel_ms, kname, launches_per_step, sm_max_mhz):
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
 
 
+def step_spread(per_step):
+    """Median, min and max of the timed steps' own durations (ms)."""
+    if not per_step:
+        return None
+    return {"median": statistics.median(per_step), "min": min(per_step), "max": max(per_step), "n": len(per_step)}
+
+
 def conversion_roofline(bytes_per_step, ms_per_step, split=True):
     """HBM roofline of the pushes: each conversion reads a complex64 sample (8 B) and writes its two
     16-bit pieces of Re and Im (or a float2 on the FP32 path): 16 B per (row, frame)."""
@@ -375,10 +382,11 @@ def link_peak_gbs(nbytes=4 << 30):
     return best
 
 
-def timed_steps(ctx, plan_list, step, steps, warmup, sample_clocks=True):
+def timed_steps(ctx, plan_list, step, steps, warmup, sample_clocks=True, per_step=None):
     """Runs `warmup` untimed and `steps` timed calls of step(k); CUDA events on the current stream,
     a barrier and a synchronize on both sides.  Returns (ms per step max over ranks, contraction
-    ms per launch, contraction launches per step, kernel launches per step, clocks)."""
+    ms per launch, contraction launches per step, kernel launches per step, clocks); a list given
+    as per_step receives each timed step's own duration (events between the steps)."""
     import torch
     st = torch.cuda.current_stream()
     for k in range(warmup):
@@ -394,13 +402,21 @@ def timed_steps(ctx, plan_list, step, steps, warmup, sample_clocks=True):
         pl.kernel_time_ms(reset=True)
     l0 = sum(pl.info()["kernel_launches"] for pl in plan_list)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    marks = []
     e0.record(st)
     for k in range(steps):
         step(warmup + k)
+        if per_step is not None and k + 1 < steps:
+            m = torch.cuda.Event(enable_timing=True)
+            m.record(st)
+            marks.append(m)
     e1.record(st)
     torch.cuda.synchronize()
     ctx.barrier()
     clocks = clk.stop() if clk else None
+    if per_step is not None:
+        bounds = [e0] + marks + [e1]
+        per_step.extend(a.elapsed_time(b) for a, b in zip(bounds[:-1], bounds[1:]))
     for pl in plan_list:
         pl.check_errors(st.cuda_stream)
     kms, kn = 0.0, 0
@@ -507,7 +523,9 @@ def thick_leg(ctx, args):
             batch(b, ring.data_ptr(), k if k >= args.warmup else None)
 
     f0 = plan.info()["flush_launches"]
-    ms, flush_ms, k_per_step, launches, clocks = timed_steps(ctx, [plan], step, args.steps, args.warmup)
+    per_step = []
+    ms, flush_ms, k_per_step, launches, clocks = timed_steps(ctx, [plan], step, args.steps, args.warmup,
+                                                             per_step=per_step)
     flushes = (plan.info()["flush_launches"] - f0) // (args.steps + args.warmup)
     push_ms = statistics.median(sum(pev[(k, b)][0].elapsed_time(pev[(k, b)][1]) for b in range(n_batch))
                                 for k in range(args.warmup, args.warmup + args.steps))
@@ -593,7 +611,8 @@ def thick_leg(ctx, args):
     free_device()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ctx.world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "step_ms": step_spread(per_step),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": name, "probes_per_step": spec.P, "probe_batch": B, "batches_per_step": n_batch,
                        "full_grid": f"{gx}x{gy}", "k_roi": f"{K}x{K} at ({rx}, {ry})", "T": T,
