@@ -406,3 +406,65 @@ def test_push_group_refusals_leave_the_plan_unchanged():
         push_group_rounds(plan, SPECS, bufs)
         plan.finalize(I, S)
         check_all(plan, I, S, frames, TOL["split_bf16"])
+
+
+def _welch_mixed_configs():
+    """SPECS with the second stream averaged over Welch segments (N = 3, stride T/2, 8 leading
+    frames skipped): its pushes take the single-push path inside a group."""
+    cfgs = [stream_config(s) for s in SPECS]
+    s1 = SPECS[1]
+    cfgs[1].welch_segments, cfgs[1].welch_stride, cfgs[1].skip_init = 3, s1.T // 2, 8
+    total = [s.T for s in SPECS]
+    total[1] = 8 + s1.T + 2 * (s1.T // 2)
+    return cfgs, total
+
+
+@pytest.mark.parametrize("mode", ["split_fp16", "fp32", "split_inplace", "welch_mixed"])
+def test_push_group_every_path(mode):
+    """A group push gives the same I and S, bit for bit, as single pushes on every path it can
+    meet: split-FP16 (grouped conversion of scaled fp16 pieces), the FP32 path and the in-place
+    path (single pushes inside the group), and a Welch stream with skipped leading frames beside
+    plain streams."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    kw = {"split_fp16": dict(precision="split_fp16"), "fp32": dict(precision="fp32"),
+          "split_inplace": dict(precision="split_bf16", frames_in_place=True),
+          "welch_mixed": dict(precision="split_bf16")}[mode]
+    if mode == "welch_mixed":
+        cfgs, total = _welch_mixed_configs()
+    else:
+        cfgs, total = [stream_config(s) for s in SPECS], [s.T for s in SPECS]
+    rng = np.random.default_rng(1200)
+    frames = []
+    for s, n in zip(SPECS, total):
+        e = rng.standard_normal((s.P, 1, s.Ky, s.Kx)) + 1j * rng.standard_normal((s.P, 1, s.Ky, s.Kx))
+        f = e + 1e-2 * (rng.standard_normal((s.P, n, s.Ky, s.Kx)) + 1j * rng.standard_normal((s.P, n, s.Ky, s.Kx)))
+        frames.append(f.astype(np.complex64))
+    bufs = [device_frames(f) for f in frames]
+    out = []
+    for grouped in (False, True):
+        with TacawPlan(cfgs, **kw) as plan:
+            info = plan.info()
+            I = torch.zeros(info["I_elems"], dtype=torch.float32, device="cuda")
+            S = torch.zeros(max(1, info["S_elems"]), dtype=torch.float32, device="cuda")
+            pushed = [0] * len(SPECS)
+            while any(pushed[i] < total[i] for i in range(len(SPECS))):
+                ids, ptrs, cnt = [], [], []
+                for i, s in enumerate(SPECS):
+                    if pushed[i] < total[i]:
+                        n = min(s.Tc, total[i] - pushed[i])
+                        ids.append(i)
+                        ptrs.append(bufs[i].data_ptr() + pushed[i] * s.P * s.Kx * s.Ky * 8)
+                        cnt.append(n)
+                        pushed[i] += n
+                if grouped:
+                    plan.push_group(ids, ptrs, cnt)
+                else:
+                    for i, ptr, n in zip(ids, ptrs, cnt):
+                        plan.push(i, ptr, n)
+            plan.finalize(I, S)
+            out.append((I.cpu().numpy(), S.cpu().numpy()))
+            if mode != "welch_mixed" and grouped:
+                # the plain streams against the oracle as well
+                check_all(plan, I, S, frames, TOL[kw["precision"]] if kw["precision"] in TOL else 1e-5)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
