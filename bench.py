@@ -969,6 +969,22 @@ def diff_leg(ctx, args, sample_clocks=True):
     ms, fwd_ms, k_n, launches, clocks = timed_steps(ctx, [plan], step, args.steps, args.warmup, sample_clocks)
     adj_ms = statistics.median(aev[k][0].elapsed_time(aev[k][1]) for k in range(args.warmup, args.warmup + args.steps))
 
+    # the FP32 CUDA-core adjoint on the same input, the call alone (the baseline of the tensor-core one)
+    def adjoint_call_ms(precision, reps):
+        plan.set_adjoint_precision(precision)
+        out = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st_t)
+            plan.backward(0, dLdS, x, grad, st)
+            e1.record(st_t)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        plan.set_adjoint_precision("split_bf16")
+        return statistics.median(out)
+
+    adj32_ms = adjoint_call_ms("fp32", max(3, args.steps))
+
     # stated error: spectra of two probes (all aperture pixels) and the gradient at 16 aperture
     # pixels of those probes, against the FP64 oracle
     import oracle
@@ -995,18 +1011,37 @@ def diff_leg(ctx, args, sample_clocks=True):
     del x, grad, I, S
     free_device()
     fwd = ffma_roofline(cmac_fwd, fwd_ms, "flush_simt_kernel", k_n, (clocks or {}).get("sm_max_mhz"))
-    adj = ffma_roofline(cmac_adj, adj_ms, "adj_psi_kernel + adj_grad_kernel", 1, (clocks or {}).get("sm_max_mhz"))
-    adj["timed"] = ("CUDA events around the tacaw_backward call (median per step; includes its zeroing kernel and "
-                    "its closing wait for the device error word)")
+    # the tensor-core adjoint call: its floor is the larger of the tensor time of its two
+    # contractions and the HBM time of the bytes it must move (the gradient over the whole ROI of
+    # every frame written once, the aperture rows' frames read once)
+    adj_bytes = P * T * npix * 8 + P * n_ap * T * 8
+    tc = tensor_roofline(cmac_adj, adj_ms, "tacaw_backward call (split BF16, tensor cores)", 1)
+    peaks, psrc = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    mem_gbs = adj_bytes / (adj_ms * 1e-3) / 1e9
+    adj = {"bound": "hbm", "achieved": mem_gbs, "peak": hbm, "unit": "GB/s", "frac": mem_gbs / hbm, "traffic": None,
+           "kernel": "tacaw_backward call: ROI zero fill, aperture-row staging, two flush_tc_drain2_kernel "
+                     "contractions, scatter into the frame layout",
+           "bytes_per_call": adj_bytes, "tensor": {k: tc[k] for k in ("achieved", "peak", "unit", "frac")},
+           "floor_ms": {"hbm": adj_bytes / (hbm * 1e9) * 1e3, "tensor": cmac_adj * FLOP_PER_CMAC_SPLIT / (tc["peak"] * 1e12) * 1e3},
+           "peak_source": f"{psrc} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+           "timed": ("CUDA events around the tacaw_backward call (median per step; includes its zeroing kernel and "
+                     "its closing wait for the device error word)")}
+    if adj["floor_ms"]["tensor"] > adj["floor_ms"]["hbm"]:
+        adj["bound"] = "tensor"
+    adj32 = ffma_roofline(cmac_adj, adj32_ms, "adj_psi_kernel + adj_grad_kernel", 1, (clocks or {}).get("sm_max_mhz"))
+    adj32["timed"] = "CUDA events around the tacaw_backward call alone (median), same input"
     return {"workload": w.name, "value": job_rate(cmac_fwd + cmac_adj, ctx.world, ms * 1e-3), "unit": UNIT,
             "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
             "config": {"probes": P, "k_roi": f"{K}x{K}", "T": T, "n_omega": Nw, "window": spec.window,
                        "aperture_pixels": n_ap, "cmac_per_step": {"forward": cmac_fwd, "adjoint": cmac_adj},
-                       "step": "reset + push + finalize_async (FP32 path) + tacaw_backward (dL/dS = c(E))",
+                       "step": "reset + push + finalize_async (FP32 path) + tacaw_backward (dL/dS = c(E); "
+                               "adjoint on the tensor cores, split BF16)",
                        "l2": "frames (%.2f GB) and gradient re-read every step, no flush" % (T * P * npix * 8 / 1e9)},
             "max_rel_err_S_vs_fp64": err_s, "rel_l2_err_grad_vs_fp64": err_g,
             "error_sample": "spectra of 2 probes; gradient at 16 aperture pixels of those probes",
-            "gpu_launches": launches, "clocks": clocks, "roofline": fwd, "adjoint": dict(adj, ms=adj_ms)}
+            "gpu_launches": launches, "clocks": clocks, "roofline": fwd, "adjoint": dict(adj, ms=adj_ms),
+            "adjoint_fp32": dict(adj32, ms=adj32_ms, speedup_of_tensor_cores=adj32_ms / adj_ms)}
 
 
 LEGS = {"realistic": realistic_leg, "batched": batched_leg, "diff": diff_leg}

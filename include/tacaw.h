@@ -312,10 +312,22 @@ tacaw_status tacaw_output_offsets(tacaw_plan_t plan, int stream_id, int64_t *I_o
  * d_dL_dS: float32 [p][d][j] on the device.  d_frames, d_grad and d_dL_dS may be device,
  * managed or pinned host memory; outside stream capture any other address is refused
  * (INVALID_ARG) before work is enqueued.  Waits for the work on `stream`.
- * The first call that needs it allocates the plan's adjoint scratch, P x (aperture pixels)
- * x (n_omega + 2) complex64, kept until tacaw_destroy (TACAW_ERR_OOM if that fails).    */
+ * Both contractions of the adjoint (Psi on the aperture pixels, then the projection back onto
+ * the frames) run on the tensor cores in split BF16 by default (tacaw_set_adjoint_precision).
+ * The first call that needs it allocates the plan's adjoint scratch, kept until tacaw_destroy
+ * (TACAW_ERR_OOM if that fails), for R = P x (aperture pixels) rows: tensor cores
+ * R x (8 T' + 8 N' + 8 n_omega + 8 T + max(T', N') / 4 + 16) bytes (T', N': T and n_omega
+ * rounded up to 32), plus, per stream, its tables once (about 16 T' N' bytes); FP32 CUDA
+ * cores R x (n_omega + 2) x 8 bytes.  The tensor-core adjoint runs its zero fill and its
+ * contractions on two streams of the plan, forked from and joined back to `stream`.       */
 tacaw_status tacaw_backward(tacaw_plan_t plan, int stream_id, const float *d_dL_dS,
                             const void *d_frames, void *d_grad, void *stream);
+
+/* Arithmetic of tacaw_backward's two contractions (no counterpart in the paper):
+ * TACAW_PREC_SPLIT_BF16 (the default, for every plan precision): tcgen05 tensor cores,
+ * operands split into bf16 hi + lo pieces, three products, FP32 accumulation;
+ * TACAW_PREC_FP32: FP32 CUDA cores.  Anything else is INVALID_ARG.  Applies to later calls. */
+tacaw_status tacaw_set_adjoint_precision(tacaw_plan_t plan, int precision);
 
 /* Starts a new segment on every stream (e.g. the next probe batch or trajectory chunk):
  * clears frame counters and mean sums.  Enqueued on `stream`.                           */

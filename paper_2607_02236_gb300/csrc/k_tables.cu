@@ -134,6 +134,45 @@ __global__ void twiddles_split_kernel(TableArgs a, __nv_bfloat16 *B_hi, __nv_bfl
     }
 }
 
+// Table of the adjoint's back-projection C[m, t] = sum_j G[m, j] conj(B[t, j]): frames are the
+// output columns and energies the contraction.  One thread per (energy j < e_pad, frame
+// t < t_rows); b = conj(w_t exp(-i theta_jt)) = w_t exp(+i theta_jt) goes to elements 2(j%32),
+// 2(j%32)+1 of rows 2t and 2t+1 of block j/32 (rows of 32 bf16 pairs, pre-swizzled):
+//   row 2t   : ( Re b, -Im b)  ->  Re C_t = Re G Re b - Im G Im b
+//   row 2t+1 : ( Im b,  Re b)  ->  Im C_t = Re G Im b + Im G Re b
+__global__ void twiddles_adjoint_split_kernel(TableArgs a, int t_rows, int e_pad, __nv_bfloat16 *B_hi,
+                                              __nv_bfloat16 *B_lo) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.y * blockDim.y + threadIdx.y;
+    if (j >= e_pad || t >= t_rows) return;
+    double br = 0.0, bi = 0.0;
+    if (j < a.Nw && t < a.T) {
+        double c, s;
+        twiddle(a, j, t, c, s);
+        const double w = window_value(a, t);
+        br = w * c;
+        bi = w * s;
+    }
+    const int kb = j / 32, jj = j % 32;
+    const size_t rows = 2 * (size_t)t_rows;
+    const int r0 = 2 * t, r1 = 2 * t + 1;
+    // 128-byte rows: chunk c of row r stored at c ^ (r mod 8)
+    const int w0 = (((jj >> 2) ^ (r0 & 7)) << 2) | (jj & 3), w1 = (((jj >> 2) ^ (r1 & 7)) << 2) | (jj & 3);
+    const size_t o0 = ((size_t)kb * rows + (size_t)r0) * 64 + 2 * (size_t)w0;
+    const size_t o1 = ((size_t)kb * rows + (size_t)r1) * 64 + 2 * (size_t)w1;
+    const float v0[2] = {(float)br, (float)(-bi)};
+    const float v1[2] = {(float)bi, (float)br};
+    for (int e = 0; e < 2; ++e) {
+        __nv_bfloat16 h, l;
+        split_bf16(v0[e], h, l);
+        B_hi[o0 + e] = h;
+        B_lo[o0 + e] = l;
+        split_bf16(v1[e], h, l);
+        B_hi[o1 + e] = h;
+        B_lo[o1 + e] = l;
+    }
+}
+
 __global__ void twiddles_fp32_kernel(TableArgs a, float2 *B32) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     int t = blockIdx.y * blockDim.y + threadIdx.y;
@@ -186,6 +225,14 @@ cudaError_t launch_twiddles_split(const TableArgs &t, __nv_bfloat16 *B_hi, __nv_
         twiddles_split_kernel<true><<<grd, blk, 0, st>>>(t, B_hi, B_lo);
     else
         twiddles_split_kernel<false><<<grd, blk, 0, st>>>(t, B_hi, B_lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_twiddles_adjoint_split(const TableArgs &t, int t_rows, int e_pad, __nv_bfloat16 *B_hi,
+                                          __nv_bfloat16 *B_lo, cudaStream_t st) {
+    dim3 blk(32, 8);
+    dim3 grd((e_pad + 31) / 32, (t_rows + 7) / 8);
+    twiddles_adjoint_split_kernel<<<grd, blk, 0, st>>>(t, t_rows, e_pad, B_hi, B_lo);
     return cudaGetLastError();
 }
 

@@ -96,6 +96,14 @@ struct Stream {
     int *adj_pix = nullptr;
     float *adj_w = nullptr;
     int n_adj = 0;
+    // tensor-core adjoint tables, built by the stream's first tacaw_backward: forward twiddles in
+    // 32-frame blocks (energy tiles wt1), conj twiddles with frames as columns (frame tiles wt2)
+    __nv_bfloat16 *adjF_hi = nullptr, *adjF_lo = nullptr, *adjC_hi = nullptr, *adjC_lo = nullptr;
+    float2 *adj_ones = nullptr;
+    float *adj_ones_f = nullptr;
+    int64_t *adj_off = nullptr;      // element offset of each aperture pixel within a frame
+    std::vector<int> h_adj_pix;      // host copy of adj_pix
+    int adj_wt1 = 0, adj_nwt1 = 0, adj_wt2 = 0, adj_nwt2 = 0;
     int stages = 0;            // shared-memory pipeline stages of this stream's tiles
     double *win_table = nullptr;   // table-driven windows (Dolph-Chebyshev)
     // Welch lanes: internal stream `lane` of user stream `user` runs segments lane, lane +
@@ -152,6 +160,11 @@ struct tacaw_plan_s {
     // streams' queued work
     cudaStream_t hp_stream = nullptr;
     cudaEvent_t hp_in = nullptr, hp_out = nullptr;
+    // tacaw_backward's streams: the gradient's zero fill (HBM-bound) runs on aux_stream beside the
+    // tensor-core adjoint's contractions, which run on adj_stream at the greatest priority (freed
+    // SMs go to their CTAs ahead of the fill's blocks)
+    cudaStream_t aux_stream = nullptr, adj_stream = nullptr;
+    cudaEvent_t aux_in = nullptr, aux_out = nullptr, adj_out = nullptr;
     int64_t bytes = 0;
     int64_t I_elems = 0, S_elems = 0;
     int64_t flushes_total = 0;
@@ -168,6 +181,10 @@ struct tacaw_plan_s {
     // (grown when a later stream needs more), kept until tacaw_destroy
     float2 *adj_scratch = nullptr;
     size_t adj_scratch_elems = 0;
+    // the tensor-core adjoint's staged operands and intermediates (same lifetime as adj_scratch)
+    void *adj_tc = nullptr;
+    size_t adj_tc_bytes = 0;
+    bool adj_fp32 = false;     // tacaw_set_adjoint_precision(TACAW_PREC_FP32): CUDA-core adjoint
     std::vector<void *> allocs;
     bool timing = false;
     bool trace = false;                      // record per-CTA phase stamps of tensor-core flushes
@@ -203,6 +220,13 @@ void free_all(tacaw_plan_s *p) {
     if (p->hp_out) cudaEventDestroy(p->hp_out);
     p->hp_stream = nullptr;
     p->hp_in = p->hp_out = nullptr;
+    if (p->aux_stream) cudaStreamDestroy(p->aux_stream);
+    if (p->adj_stream) cudaStreamDestroy(p->adj_stream);
+    if (p->aux_in) cudaEventDestroy(p->aux_in);
+    if (p->aux_out) cudaEventDestroy(p->aux_out);
+    if (p->adj_out) cudaEventDestroy(p->adj_out);
+    p->aux_stream = p->adj_stream = nullptr;
+    p->aux_in = p->aux_out = p->adj_out = nullptr;
     if (p->d_trace) cudaFree(p->d_trace);
     p->d_trace = nullptr;
     for (auto &e : p->ev) {
@@ -215,6 +239,9 @@ void free_all(tacaw_plan_s *p) {
     if (p->adj_scratch) cudaFree(p->adj_scratch);
     p->adj_scratch = nullptr;
     p->adj_scratch_elems = 0;
+    if (p->adj_tc) cudaFree(p->adj_tc);
+    p->adj_tc = nullptr;
+    p->adj_tc_bytes = 0;
 }
 
 tacaw_status cuda_fail(tacaw_plan_s *p, cudaError_t e, const char *what) {
@@ -279,22 +306,23 @@ double bose_factor(double E, double TK) {
 // FP32 path pads to 64-wide tiles on its own).  Among multiples of 8 the width with the least
 // padded work plus a fixed per-tile cost (operand A is re-read once per energy tile) wins; a
 // requested width is clamped.
-void choose_omega_tile(Stream &s, int requested, int cap) {
-    const int wt_max = std::max(8, cap / 8 * 8);
+int least_cost_tile(int n_cols, int wt_max) {
     int best = 8;
-    if (requested > 0) {
-        best = std::min(requested, wt_max);
-    } else {
-        int64_t best_cost = INT64_MAX;
-        for (int wt = 8; wt <= wt_max; wt += 8) {
-            const int64_t n = (s.Nw + wt - 1) / wt;
-            const int64_t cost = n * (wt + 24);
-            if (cost < best_cost || (cost == best_cost && wt > best)) {
-                best_cost = cost;
-                best = wt;
-            }
+    int64_t best_cost = INT64_MAX;
+    for (int wt = 8; wt <= wt_max; wt += 8) {
+        const int64_t n = (n_cols + wt - 1) / wt;
+        const int64_t cost = n * (wt + 24);
+        if (cost < best_cost || (cost == best_cost && wt > best)) {
+            best_cost = cost;
+            best = wt;
         }
     }
+    return best;
+}
+
+void choose_omega_tile(Stream &s, int requested, int cap) {
+    const int wt_max = std::max(8, cap / 8 * 8);
+    const int best = requested > 0 ? std::min(requested, wt_max) : least_cost_tile(s.Nw, wt_max);
     s.wt = best;
     s.n_wt = (s.Nw + best - 1) / best;
     s.Nw_pad = s.wt * s.n_wt;
@@ -622,6 +650,23 @@ std::vector<double> chebwin_periodic(int T, double at_db) {
     return w;
 }
 
+// Table arguments of stream s after build_stream (device phase and window inputs in place).
+TableArgs stream_table_args(const Stream &s, int block_frames) {
+    TableArgs ta{};
+    ta.T = s.T;
+    ta.T_pad = s.T_pad;
+    ta.Nw = s.Nw;
+    ta.Nw_pad = s.Nw_pad;
+    ta.window = s.d.window;
+    ta.window_param = s.d.window_param;
+    ta.fft_bins = s.d.fft_bins;
+    ta.block_frames = block_frames;
+    ta.win_table = s.win_table;
+    ta.swz = 1;
+    ta.cj = s.cj;
+    return ta;
+}
+
 tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
     const tacaw_stream_desc &d = s.d;
     TableArgs ta{};
@@ -748,6 +793,7 @@ tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
         for (int k = 0; k < s.D; ++k) aw.push_back(full[(size_t)k * s.npix + pix]);
     }
     s.n_adj = (int)apix.size();
+    s.h_adj_pix = apix;
     if (!dev_alloc(p, &s.adj_pix, apix.size()) || !dev_alloc(p, &s.adj_w, aw.size()))
         return fail(TACAW_ERR_OOM, "cudaMalloc(adjoint lists)");
     if (!apix.empty()) {
@@ -1609,6 +1655,151 @@ tacaw_status tacaw_kernel_time_ms(tacaw_plan_t p, double *flush_ms, int64_t *flu
     return TACAW_OK;
 }
 
+namespace {
+
+// Tables of the tensor-core adjoint for stream s, built on its first backward: the forward
+// twiddles in 32-frame blocks with least-padding energy tiles, and the conj twiddles with the
+// frames as output columns in least-padding frame tiles.
+// Output-column tile of an adjoint contraction over row_tiles row tiles: the multiple of 8 (at
+// most wt_max) with the least cost in rounds of the persistent grid (one tile per SM a round)
+// times columns plus a fixed per-tile cost, as in least_cost_tile.
+int adjoint_tile(int n_cols, int64_t row_tiles, int sms, int wt_max) {
+    int best = 8;
+    int64_t best_cost = INT64_MAX;
+    for (int wt = 8; wt <= wt_max; wt += 8) {
+        const int64_t tiles = row_tiles * ((n_cols + wt - 1) / wt);
+        const int64_t cost = (tiles + sms - 1) / sms * (wt + 24);
+        if (cost < best_cost || (cost == best_cost && wt > best)) {
+            best_cost = cost;
+            best = wt;
+        }
+    }
+    return best;
+}
+
+tacaw_status adjoint_tc_tables(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
+    if (s.adjF_hi) return TACAW_OK;
+    const int wt_max = kDrainMaxOmegaTile;
+    int dev = 0, sms = 0;
+    CU_CHECK(p, cudaGetDevice(&dev), "cudaGetDevice");
+    CU_CHECK(p, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    const int64_t row_tiles = round_up((int64_t)s.d.n_probes * s.n_adj, kMTile) / kMTile;
+    s.adj_wt1 = adjoint_tile(s.Nw, row_tiles, std::max(1, sms), wt_max);
+    s.adj_nwt1 = (s.Nw + s.adj_wt1 - 1) / s.adj_wt1;
+    s.adj_wt2 = adjoint_tile(s.T, row_tiles, std::max(1, sms), wt_max);
+    s.adj_nwt2 = (s.T + s.adj_wt2 - 1) / s.adj_wt2;
+    const int T_pad = (int)round_up(s.T, 32), E_pad = (int)round_up(s.Nw, 32);
+    const int Nw_rows = s.adj_wt1 * s.adj_nwt1, T_rows = s.adj_wt2 * s.adj_nwt2;
+    const size_t nf = (size_t)(T_pad / 32) * 2 * Nw_rows * 64, nc = (size_t)(E_pad / 32) * 2 * T_rows * 64;
+    __nv_bfloat16 *fh, *fl, *ch, *cl;
+    float2 *ones;
+    float *ones_f;
+    int64_t *off;
+    if (!dev_alloc(p, &fh, nf) || !dev_alloc(p, &fl, nf) || !dev_alloc(p, &ch, nc) || !dev_alloc(p, &cl, nc) ||
+        !dev_alloc(p, &ones, (size_t)T_rows) || !dev_alloc(p, &ones_f, (size_t)T_rows) ||
+        !dev_alloc(p, &off, (size_t)s.n_adj))
+        return fail(TACAW_ERR_OOM, "cudaMalloc(adjoint tables)");
+    {
+        const std::vector<int> &pix = s.h_adj_pix;
+        std::vector<int64_t> o((size_t)s.n_adj);
+        for (int i = 0; i < s.n_adj; ++i)
+            o[i] = (int64_t)(s.d.roi_y0 + pix[i] / s.d.kx) * s.d.pitch_row + (s.d.roi_x0 + pix[i] % s.d.kx);
+        CU_CHECK(p, cudaMemcpy(off, o.data(), sizeof(int64_t) * s.n_adj, cudaMemcpyHostToDevice), "copy offsets");
+    }
+    TableArgs ta = stream_table_args(s, 32);
+    ta.T_pad = T_pad;
+    ta.Nw_pad = Nw_rows;
+    CU_CHECK(p, launch_twiddles_split(ta, fh, fl, 0, st), "adjoint twiddles");
+    CU_CHECK(p, launch_twiddles_adjoint_split(ta, T_rows, E_pad, ch, cl, st), "adjoint conj twiddles");
+    std::vector<float2> h1((size_t)T_rows, make_float2(1.f, 0.f));
+    std::vector<float> h2((size_t)T_rows, 1.f);
+    CU_CHECK(p, cudaMemcpy(ones, h1.data(), sizeof(float2) * T_rows, cudaMemcpyHostToDevice), "copy ones");
+    CU_CHECK(p, cudaMemcpy(ones_f, h2.data(), sizeof(float) * T_rows, cudaMemcpyHostToDevice), "copy ones");
+    s.adjF_hi = fh;
+    s.adjF_lo = fl;
+    s.adjC_hi = ch;
+    s.adjC_lo = cl;
+    s.adj_ones = ones;
+    s.adj_ones_f = ones_f;
+    s.adj_off = off;
+    return TACAW_OK;
+}
+
+// Carves the tensor-core adjoint's buffers for stream s out of the plan's scratch (grown, never
+// shrunk, kept until tacaw_destroy).  q.a must be filled.
+tacaw_status adjoint_tc_scratch(tacaw_plan_s *p, const Stream &s, AdjTcArgs &q) {
+    const int64_t M = (int64_t)s.d.n_probes * s.n_adj;
+    q.M_pad = round_up(M, kMTile);
+    q.T_pad = (int)round_up(s.T, 32);
+    q.E_pad = (int)round_up(s.Nw, 32);
+    const size_t a_piece = (size_t)q.T_pad * q.M_pad * 4, g_piece = (size_t)q.E_pad * q.M_pad * 4;
+    const size_t sizes[10] = {a_piece, a_piece, g_piece, g_piece,
+                              (size_t)(std::max(q.T_pad, q.E_pad) / 32) * M * sizeof(float2),
+                              (size_t)M * sizeof(float2), (size_t)M * sizeof(float2),
+                              (size_t)M * s.Nw * sizeof(float2), (size_t)M * s.T * sizeof(float2), 2 * sizeof(int)};
+    size_t off[10], total = 0;
+    for (int i = 0; i < 10; ++i) {
+        off[i] = total;
+        total += (sizes[i] + 255) & ~(size_t)255;
+    }
+    if (total > p->adj_tc_bytes) {
+        // the previous backward ended with a synchronize, so the old buffer is idle
+        if (p->adj_tc) {
+            cudaFree(p->adj_tc);
+            p->bytes -= (int64_t)p->adj_tc_bytes;
+        }
+        p->adj_tc = nullptr;
+        p->adj_tc_bytes = 0;
+        void *b = nullptr;
+        if (cudaMalloc(&b, total) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(TACAW_ERR_OOM, "tensor-core adjoint scratch of %zu bytes", total);
+        }
+        p->adj_tc = b;
+        p->adj_tc_bytes = total;
+        p->bytes += (int64_t)total;
+    }
+    uint8_t *b = static_cast<uint8_t *>(p->adj_tc);
+    q.A_hi = reinterpret_cast<__nv_bfloat16 *>(b + off[0]);
+    q.A_lo = reinterpret_cast<__nv_bfloat16 *>(b + off[1]);
+    q.G_hi = reinterpret_cast<__nv_bfloat16 *>(b + off[2]);
+    q.G_lo = reinterpret_cast<__nv_bfloat16 *>(b + off[3]);
+    q.part = reinterpret_cast<float2 *>(b + off[4]);
+    q.dmu = reinterpret_cast<float2 *>(b + off[5]);
+    q.kmean = reinterpret_cast<float2 *>(b + off[6]);
+    q.psi = reinterpret_cast<float2 *>(b + off[7]);
+    q.cg = reinterpret_cast<float2 *>(b + off[8]);
+    q.counters = reinterpret_cast<int *>(b + off[9]);
+    q.Bf_hi = s.adjF_hi;
+    q.Bf_lo = s.adjF_lo;
+    q.wt1 = s.adj_wt1;
+    q.n_wt1 = s.adj_nwt1;
+    q.Bc_hi = s.adjC_hi;
+    q.Bc_lo = s.adjC_lo;
+    q.wt2 = s.adj_wt2;
+    q.n_wt2 = s.adj_nwt2;
+    q.ones = s.adj_ones;
+    q.ones_f = s.adj_ones_f;
+    q.pix_off = s.adj_off;
+    q.err = p->d_err;
+    q.wait_ns = p->wait_ns;
+    return TACAW_OK;
+}
+
+}  // namespace
+
+tacaw_status tacaw_set_adjoint_precision(tacaw_plan_t p, int precision) {
+    tacaw_status c = check_plan(p);
+    if (c != TACAW_OK) return c;
+    if (precision == TACAW_PREC_SPLIT_BF16)
+        p->adj_fp32 = false;
+    else if (precision == TACAW_PREC_FP32)
+        p->adj_fp32 = true;
+    else
+        return fail(TACAW_ERR_INVALID_ARG, "adjoint precision %d: TACAW_PREC_SPLIT_BF16 or TACAW_PREC_FP32", precision);
+    return TACAW_OK;
+}
+
 tacaw_status tacaw_backward(tacaw_plan_t p, int sid, const float *d_dL_dS, const void *d_frames, void *d_grad,
                             void *stream) {
     tacaw_status c = check_plan(p);
@@ -1654,9 +1845,56 @@ tacaw_status tacaw_backward(tacaw_plan_t p, int sid, const float *d_dL_dS, const
     // the whole push sequence's gradient: skipped frames and frames of no segment get zero
     AdjointArgs z = a;
     z.T = (int)u.total;
-    CU_CHECK(p, launch_zero_roi(z, st), "zero gradient");
-    p->launches++;
-    if (s.n_adj > 0 && s.D > 0) {
+    const bool tc = s.n_adj > 0 && s.D > 0 && !p->adj_fp32;
+    if (!tc) {
+        CU_CHECK(p, launch_zero_roi(z, st), "zero gradient");
+        p->launches++;
+    }
+    if (tc) {
+        // tensor cores, split BF16: one segment, or each Welch segment at its start frame with
+        // weight 1/N, its gradient added where segments overlap
+        tacaw_status r = adjoint_tc_tables(p, s, st);
+        if (r != TACAW_OK) return r;
+        AdjTcArgs q{};
+        q.a = a;
+        r = adjoint_tc_scratch(p, s, q);
+        if (r != TACAW_OK) return r;
+        // the zero fill runs on a side stream beside the contractions (it needs the SMs' memory
+        // pipes, they the tensor cores), the contractions on a stream of the greatest priority;
+        // the first scatter into the gradient waits for the fill, the caller's stream for both
+        if (!p->aux_stream) {
+            int lo = 0, hi = 0;
+            CU_CHECK(p, cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
+            CU_CHECK(p, cudaStreamCreateWithPriority(&p->aux_stream, cudaStreamNonBlocking, lo), "adjoint fill stream");
+            CU_CHECK(p, cudaStreamCreateWithPriority(&p->adj_stream, cudaStreamNonBlocking, hi), "adjoint stream");
+            CU_CHECK(p, cudaEventCreateWithFlags(&p->aux_in, cudaEventDisableTiming), "cudaEventCreate");
+            CU_CHECK(p, cudaEventCreateWithFlags(&p->aux_out, cudaEventDisableTiming), "cudaEventCreate");
+            CU_CHECK(p, cudaEventCreateWithFlags(&p->adj_out, cudaEventDisableTiming), "cudaEventCreate");
+        }
+        CU_CHECK(p, cudaEventRecord(p->aux_in, st), "cudaEventRecord");
+        CU_CHECK(p, cudaStreamWaitEvent(p->aux_stream, p->aux_in, 0), "cudaStreamWaitEvent");
+        CU_CHECK(p, cudaStreamWaitEvent(p->adj_stream, p->aux_in, 0), "cudaStreamWaitEvent");
+        CU_CHECK(p, launch_zero_roi(z, p->aux_stream), "zero gradient");
+        CU_CHECK(p, cudaEventRecord(p->aux_out, p->aux_stream), "cudaEventRecord");
+        p->launches++;
+        q.before_scatter = p->aux_out;
+        cudaStream_t cst = p->adj_stream;
+        const int nseg = u.N > 1 ? u.N : 1;
+        cudaError_t e = cudaSuccess;
+        for (int n = 0; n < nseg && e == cudaSuccess; ++n) {
+            const int64_t f0 = u.skip + (int64_t)n * u.stride;
+            AdjTcArgs qn = q;
+            qn.a.frames = a.frames + f0 * s.d.pitch_frame;
+            qn.a.grad = a.grad + f0 * s.d.pitch_frame;
+            qn.a.scale = 1.f / (float)nseg;
+            qn.a.accumulate = nseg > 1 ? 1 : 0;
+            e = launch_adjoint_tc(qn, cst);
+            p->launches += adjtc_launches();
+        }
+        if (e != cudaSuccess) return cuda_fail(p, e, "tensor-core adjoint");
+        CU_CHECK(p, cudaEventRecord(p->adj_out, cst), "cudaEventRecord");
+        CU_CHECK(p, cudaStreamWaitEvent(st, p->adj_out, 0), "cudaStreamWaitEvent");
+    } else if (s.n_adj > 0 && s.D > 0) {
         const size_t n_scr = (size_t)s.d.n_probes * s.n_adj * (s.Nw + 2);
         if (n_scr > p->adj_scratch_elems) {
             // the previous call ended with a synchronize, so the old buffer is idle

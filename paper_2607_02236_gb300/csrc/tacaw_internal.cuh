@@ -426,4 +426,37 @@ struct AdjointArgs {
 cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t st);
 cudaError_t launch_zero_roi(const AdjointArgs &a, cudaStream_t st);
 
+// Tensor-core adjoint (k_adjoint_tc.cu): both contractions on the staged drained kernel, split
+// BF16, over the aperture rows (M = P * n_mpix rows, padded to M_pad).  Tables per stream,
+// scratch per plan; every staged row is written in full by each call.
+struct AdjTcArgs {
+    AdjointArgs a;                          // geometry, loss weights, gradient (scratch unused)
+    const __nv_bfloat16 *Bf_hi, *Bf_lo;     // forward twiddles, 32-frame blocks [T_pad/32][2 wt1 n_wt1][64]
+    int wt1, n_wt1;                         // energy tiles of the Psi recompute
+    const __nv_bfloat16 *Bc_hi, *Bc_lo;     // conj twiddles, 32-energy blocks [E_pad/32][2 wt2 n_wt2][64]
+    int wt2, n_wt2;                         // frame tiles of the back-projection
+    const float2 *ones;                     // [wt2 n_wt2] (1, 0): the back-projection's "window transform"
+    const float *ones_f;                    // [wt2 n_wt2] 1
+    const int64_t *pix_off;                 // [n_mpix] element offset of each aperture pixel in a frame
+    int64_t M_pad;
+    int T_pad, E_pad;                       // frames and energies rounded up to 32
+    __nv_bfloat16 *A_hi, *A_lo;             // staged frames of the aperture rows [T_pad/32][M_pad][64]
+    __nv_bfloat16 *G_hi, *G_lo;             // staged G [E_pad/32][M_pad][64]
+    float2 *part;                           // per-block row sums [max(T_pad, E_pad)/32][M]
+    float2 *dmu, *kmean;                    // [M]: mu - psi_0, and K
+    float2 *psi;                            // [P][Nw][n_mpix]
+    float2 *cg;                             // [P][T][n_mpix]: C - K
+    int *counters;                          // two tile counters
+    uint32_t *err;
+    uint64_t wait_ns;
+    cudaEvent_t before_scatter;             // if set: the scatter waits for it (the gradient's zero fill)
+};
+cudaError_t launch_adjoint_tc(const AdjTcArgs &q, cudaStream_t st);
+// kernels one launch_adjoint_tc enqueues (its two contractions included)
+int adjtc_launches();
+// conj(B[t][j]) = w_t exp(+i theta_jt) split into bf16 hi/lo: rows 2t, 2t+1 (t < t_rows) of
+// 32-energy blocks (energies padded to e_pad), pre-swizzled like the forward tables
+cudaError_t launch_twiddles_adjoint_split(const TableArgs &t, int t_rows, int e_pad, __nv_bfloat16 *B_hi,
+                                          __nv_bfloat16 *B_lo, cudaStream_t st);
+
 }  // namespace tacaw

@@ -28,7 +28,8 @@ EXPORTS = ["tacaw_plan_create", "tacaw_push_frames", "tacaw_finalize", "tacaw_ou
            "tacaw_backward", "tacaw_reset", "tacaw_plan_get_info", "tacaw_set_timing",
            "tacaw_kernel_time_ms", "tacaw_destroy", "tacaw_last_error", "tacaw_version",
            "tacaw_detector_spectra_noalloc", "tacaw_flush_trace", "tacaw_finalize_async",
-           "tacaw_check_errors", "tacaw_set_log_callback", "tacaw_set_wait_limit_ns", "tacaw_push_frames_group"]
+           "tacaw_check_errors", "tacaw_set_log_callback", "tacaw_set_wait_limit_ns", "tacaw_push_frames_group",
+           "tacaw_set_adjoint_precision"]
 
 
 class TacawError(RuntimeError):
@@ -94,6 +95,7 @@ def lib():
     L.tacaw_plan_get_info.argtypes = [c_void_p, POINTER(CPlanInfo)]
     L.tacaw_set_timing.argtypes = [c_void_p, c_int]
     L.tacaw_set_wait_limit_ns.argtypes = [c_void_p, ctypes.c_uint64]
+    L.tacaw_set_adjoint_precision.argtypes = [c_void_p, c_int]
     L.tacaw_kernel_time_ms.argtypes = [c_void_p, POINTER(c_double), POINTER(c_int64), c_int]
     L.tacaw_destroy.argtypes = [c_void_p]
     L.tacaw_flush_trace.argtypes = [c_void_p, c_void_p, c_int64, POINTER(c_int64)]
@@ -265,6 +267,10 @@ class TacawPlan:
     def set_wait_limit_ns(self, limit_ns: int):
         """Device pipeline waits of later contraction launches give up after limit_ns (0: default)."""
         _check(lib().tacaw_set_wait_limit_ns(self._h, int(limit_ns)))
+
+    def set_adjoint_precision(self, precision: str):
+        """Arithmetic of backward(): "split_bf16" (tensor cores, the default) or "fp32"."""
+        _check(lib().tacaw_set_adjoint_precision(self._h, PRECISIONS.get(precision, -1)))
 
     def set_timing(self, on):
         """on: False/True, or 2 to also record per-CTA phase stamps of tensor-core flushes."""

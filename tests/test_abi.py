@@ -70,6 +70,7 @@ def test_null_plan_calls_are_errors(L):
     assert L.tacaw_push_frames(None, 0, None, 1, None) == t.ERR_INVALID_ARG
     assert L.tacaw_push_frames_group(None, 1, None, None, None, None) == t.ERR_INVALID_ARG
     assert L.tacaw_finalize(None, None, None, None, None) == t.ERR_INVALID_ARG
+    assert L.tacaw_set_adjoint_precision(None, t.PRECISIONS["split_bf16"]) == t.ERR_INVALID_ARG
     assert L.tacaw_destroy(None) == t.OK
 
 

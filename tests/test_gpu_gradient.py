@@ -1,9 +1,11 @@
 """Differentiation workload: 8 probes, 128x128 ROI, T=512, 200 energies over 0-120 meV, Hann,
 FP32.  L = sum_p sum_E c(E) S_p(E) with S the r=20 px aperture spectrum and c ~ N(0,1) seeded.
 
-The adjoint (tacaw_backward behind torch.autograd) is checked against the FP64 oracle gradient
-(relative L2 <= 1e-4 on sampled aperture pixels, exact zeros outside the aperture) and
-against FP64 central finite differences (h = 1e-6) of the oracle loss on 64 random entries.
+The adjoint (tacaw_backward behind torch.autograd), on the tensor cores (split BF16, the default)
+and on the FP32 CUDA cores, is checked against the FP64 oracle gradient (relative L2 <= 1e-4 on
+sampled aperture pixels, exact zeros outside the aperture) and against FP64 central finite
+differences (h = 1e-6) of the oracle loss on 64 random entries; ragged sizes (row tiles, frames
+and energies that fill no whole block) against the oracle's full gradient.
 """
 import numpy as np
 import pytest
@@ -15,8 +17,8 @@ from synth import frames as F
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def case():
+@pytest.fixture(scope="module", params=["split_bf16", "fp32"])
+def case(request):
     import torch
     from paper_2607_02236_gb300 import TacawPlan, build
     from paper_2607_02236_gb300.autograd import spectrum
@@ -29,6 +31,7 @@ def case():
     sg.generate(spec, 4, x.data_ptr(), 0, T, pitch_row=K, pitch_frame=P * K * K, pitch_probe=K * K)
     x = x.view(T, P, K, K).requires_grad_(True)
     plan = TacawPlan([stream_config(spec)], precision="fp32")
+    plan.set_adjoint_precision(request.param)
     c = torch.tensor(synth.loss_weights(Nw, seed=0), dtype=torch.float32, device="cuda")
     S = spectrum(x, plan)
     L = (S * c[None, None, :]).sum()
@@ -108,3 +111,49 @@ def test_gradient_matches_fp64_finite_differences(case):
             scale = max(scale, abs(fd))
     for fd, an in rows:
         assert abs(fd - an) <= 1e-4 * scale, (fd, an, scale)
+
+
+def ragged_frames(P, T, Ky, Kx, seed):
+    rng = np.random.default_rng(seed)
+    e = rng.standard_normal((P, 1, Ky, Kx)) + 1j * rng.standard_normal((P, 1, Ky, Kx))
+    t = np.arange(T)[None, :, None, None]
+    tone = 0.05 * np.exp(2j * np.pi * 0.0731 * t) * rng.standard_normal((P, 1, Ky, Kx))
+    s = 1e-2 * (rng.standard_normal((P, T, Ky, Kx)) + 1j * rng.standard_normal((P, T, Ky, Kx)))
+    return (e + tone + s).astype(np.complex64)
+
+
+@pytest.mark.parametrize("adjoint", ["split_bf16", "fp32"])
+@pytest.mark.parametrize("mean,window,bose_T_K", [(True, "gauss", 300.0), (False, "hann", 0.0)])
+def test_adjoint_ragged_sizes(adjoint, mean, window, bose_T_K):
+    """3 probes x 182 aperture pixels (row tiles of 128 with a ragged tail), T = 50 frames and
+    37 signed off-grid energies (neither fills whole 32-wide staging blocks), a centred disk and
+    an off-axis annulus, the mean removed or kept, Bose factor on or off: the whole gradient
+    against the FP64 oracle's, and exactly zero outside the apertures."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan, build
+    from synth import Detector, StreamSpec
+    from tests.helpers import oracle_kw, stream_config
+    build.build_all()
+    spec = StreamSpec(P=3, Kx=20, Ky=20, T=50, Tc=50, n_omega=37, window=window, subtract_mean=mean,
+                      bose_T_K=bose_T_K,
+                      detectors=(Detector("circular", 0, 0, -1, 7.5), Detector("annular", 2.0, -1.0, 3.0, 6.0)))
+    E = np.linspace(-40.0, 60.0, 37) + 0.137
+    fr = ragged_frames(spec.P, spec.T, spec.Ky, spec.Kx, 8)
+    rng = np.random.default_rng(9)
+    c = rng.standard_normal((spec.P, 2, 37))
+    cfg = stream_config(spec)
+    cfg.E_meV = [float(e) for e in E]
+    buf = torch.from_numpy(np.ascontiguousarray(fr.transpose(1, 0, 2, 3))).to("cuda")   # [T][P][Ky][Kx]
+    grad = torch.full_like(buf, complex(7.0, -7.0))
+    with TacawPlan([cfg], precision="fp32") as plan:
+        plan.set_adjoint_precision(adjoint)
+        plan.backward(0, torch.tensor(c, dtype=torch.float32, device="cuda"), buf, grad)
+    g = grad.cpu().numpy().transpose(1, 0, 2, 3)
+    kw = oracle_kw(spec)
+    kw["E_meV"] = E
+    ref = oracle.gradient(fr, c, **kw)
+    rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    assert rel <= 1e-4, rel
+    inside = oracle.detector_masks(spec.Kx, spec.Ky, spec.detectors).sum(axis=0) > 0
+    assert inside.sum() == 182
+    assert np.all(g[:, :, ~inside] == 0)

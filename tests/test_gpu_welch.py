@@ -158,8 +158,9 @@ def test_welch_errors():
         plan.finalize(I)
 
 
+@pytest.mark.parametrize("adjoint", ["split_bf16", "fp32"])
 @pytest.mark.parametrize("N,stride,skip", [(4, 24, 10), (3, 64, 0), (1, 0, 17)])
-def test_welch_gradient_through_autograd(N, stride, skip):
+def test_welch_gradient_through_autograd(N, stride, skip, adjoint):
     """The adjoint of the averaged spectrum (segments weighted 1/N, overlaps summed, skipped
     frames zero) through torch.autograd, against the FP64 oracle's Welch gradient."""
     import torch
@@ -173,6 +174,7 @@ def test_welch_gradient_through_autograd(N, stride, skip):
     c = rng.standard_normal((spec.P, len(spec.detectors), spec.Nw))
     x = torch.from_numpy(np.ascontiguousarray(fr.transpose(1, 0, 2, 3))).to("cuda").requires_grad_(True)
     with TacawPlan([welch_config(spec, N, stride, skip)], precision="fp32") as plan:
+        plan.set_adjoint_precision(adjoint)
         S = spectrum(x, plan, 0, 20)
         L = (S * torch.tensor(c, dtype=torch.float32, device="cuda")).sum()
         L.backward()
