@@ -157,3 +157,54 @@ def test_adjoint_ragged_sizes(adjoint, mean, window, bose_T_K):
     inside = oracle.detector_masks(spec.Kx, spec.Ky, spec.detectors).sum(axis=0) > 0
     assert inside.sum() == 182
     assert np.all(g[:, :, ~inside] == 0)
+
+
+@pytest.mark.parametrize("adjoint", ["split_bf16", "fp32"])
+@pytest.mark.parametrize("shape", ["narrow", "wide"])
+def test_adjoint_long_segment_and_many_energies(adjoint, shape):
+    """T = 1100 frames and 600 energies: both tensor-core contractions of the adjoint run longer
+    than one 512-deep accumulator chunk (Psi over 35 staging blocks of frames, the back-projection
+    over 19 of energies), so their mid-tile drains into FP32 registers are exercised, with narrow
+    tiles (58 aperture rows: one row tile, 8-wide tiles) and wide ones (4 probes x 1257 aperture
+    pixels: 40 row tiles, 88-wide tiles); against the FP64 oracle's gradient (whole, or at 48
+    sampled aperture pixels a probe), exactly zero outside the aperture."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan, build
+    from synth import Detector, StreamSpec
+    from tests.helpers import oracle_kw, stream_config
+    build.build_all()
+    if shape == "narrow":
+        spec = StreamSpec(P=2, Kx=12, Ky=10, T=1100, Tc=1100, n_omega=600, E_max_meV=150.0, window="hann",
+                          detectors=(Detector("circular", 0, 0, -1, 3.0),))
+    else:
+        spec = StreamSpec(P=4, Kx=48, Ky=48, T=1100, Tc=1100, n_omega=600, E_max_meV=150.0, window="hann",
+                          detectors=(Detector("circular", 0, 0, -1, 20.0),))
+    fr = ragged_frames(spec.P, spec.T, spec.Ky, spec.Kx, 11)
+    c = np.random.default_rng(12).standard_normal((spec.P, 1, spec.Nw))
+    buf = torch.from_numpy(np.ascontiguousarray(fr.transpose(1, 0, 2, 3))).to("cuda")
+    grad = torch.empty_like(buf)
+    with TacawPlan([stream_config(spec)], precision="split_bf16") as plan:
+        plan.set_adjoint_precision(adjoint)
+        for _ in range(2):                          # the plan's scratch reused by the second call
+            plan.backward(0, torch.tensor(c, dtype=torch.float32, device="cuda"), buf, grad)
+    g = grad.cpu().numpy().transpose(1, 0, 2, 3)
+    inside = oracle.detector_masks(spec.Kx, spec.Ky, spec.detectors)[0] > 0
+    assert np.all(g[:, :, ~inside] == 0)
+    kw = oracle_kw(spec)
+    if shape == "narrow":
+        ref = oracle.gradient(fr, c, **kw)
+        rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+        assert rel <= 1e-4, rel
+        return
+    kw.pop("detectors")
+    kw.pop("window_param")
+    ap = np.nonzero(inside.reshape(-1))[0]
+    assert len(ap) == 1257
+    rng = np.random.default_rng(13)
+    for p in range(spec.P):
+        sel = rng.choice(ap, 48, replace=False)
+        series = fr[p].reshape(spec.T, -1)[:, sel]
+        ref = oracle.gradient_pixels(series, c[p], np.ones((len(sel), 1)), **kw)
+        got = g[p].reshape(spec.T, -1)[:, sel]
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert rel <= 1e-4, (p, rel)
