@@ -7,6 +7,7 @@ finished accumulator chunk runs out deterministically.  The kernel then stops: i
 flight are waited for, its issued MMAs complete and its tensor memory is freed before it exits.
 The host reads the error word: finalize returns TACAW_ERR_TIMEOUT and the plan is poisoned.
 A fresh plan on the same device then matches the FP64 oracle, so the context stayed usable.
+The tensor-core adjoint runs the same kernel: its backward reports the timeout the same way.
 """
 import numpy as np
 import pytest
@@ -77,3 +78,34 @@ def test_default_limit_restored():
     torch.cuda.synchronize()
     ref = oracle.forward(fr, **oracle_kw(SPEC))
     assert rel_err_peak(I.cpu().numpy().reshape(ref.I.shape), ref.I) <= 1e-5
+
+
+def test_adjoint_wait_limit_reports_timeout():
+    """tacaw_backward on the tensor cores with a 1 us wait limit: its Psi contraction (32 staging
+    blocks a tile) runs out of a wait, the call returns TACAW_ERR_TIMEOUT and poisons the plan;
+    a fresh plan's backward then matches the oracle's gradient."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan, TacawError
+    from paper_2607_02236_gb300.tacaw import ERR_STATE, ERR_TIMEOUT
+    fr = frames.frames(SPEC, 7, 0, SPEC.T)
+    buf = torch.from_numpy(np.ascontiguousarray(fr.transpose(1, 0, 2, 3))).cuda()      # [T][P][K][K]
+    c = np.random.default_rng(3).standard_normal((SPEC.P, 1, SPEC.Nw))
+    dLdS = torch.tensor(c, dtype=torch.float32, device="cuda")
+    grad = torch.empty_like(buf)
+    plan = TacawPlan([stream_config(SPEC)], precision="split_bf16")
+    try:
+        plan.set_wait_limit_ns(1000)
+        with pytest.raises(TacawError) as ei:
+            plan.backward(0, dLdS, buf, grad)
+        assert ei.value.status == ERR_TIMEOUT, str(ei.value)
+        with pytest.raises(TacawError) as ei:
+            plan.backward(0, dLdS, buf, grad)
+        assert ei.value.status == ERR_STATE and "poisoned" in str(ei.value)
+    finally:
+        plan.close()
+    torch.cuda.synchronize()
+    with TacawPlan([stream_config(SPEC)], precision="split_bf16") as plan:
+        plan.backward(0, dLdS, buf, grad)
+    g = grad.cpu().numpy().transpose(1, 0, 2, 3)
+    ref = oracle.gradient(fr, c, **oracle_kw(SPEC))
+    assert np.linalg.norm(g - ref) / np.linalg.norm(ref) <= 1e-4
