@@ -208,3 +208,35 @@ def test_adjoint_long_segment_and_many_energies(adjoint, shape):
         got = g[p].reshape(spec.T, -1)[:, sel]
         rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert rel <= 1e-4, (p, rel)
+
+
+def test_adjoint_on_each_stream_of_a_multi_stream_plan():
+    """A plan of two streams of different shapes (ROI, T, energies, apertures): backward on
+    stream 0, then on the larger stream 1 (the plan's adjoint scratch grows), then on stream 0
+    again (the grown scratch is reused, stream 0's tables kept): each against the FP64 oracle's
+    gradient of its own stream."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan, build
+    from synth import Detector, StreamSpec
+    from tests.helpers import oracle_kw, stream_config
+    build.build_all()
+    specs = [StreamSpec(P=2, Kx=20, Ky=16, T=96, Tc=96, n_omega=40, E_max_meV=120.0, window="hann",
+                        detectors=(Detector("circular", 0, 0, -1, 5.0),)),
+             StreamSpec(P=3, Kx=40, Ky=36, T=200, Tc=200, n_omega=130, E_max_meV=150.0, window="gauss",
+                        detectors=(Detector("circular", 0, 0, -1, 9.0), Detector("annular", 0, 0, 4.0, 12.0)))]
+    data = []
+    for i, sp in enumerate(specs):
+        fr = ragged_frames(sp.P, sp.T, sp.Ky, sp.Kx, 40 + i)
+        c = np.random.default_rng(50 + i).standard_normal((sp.P, len(sp.detectors), sp.Nw))
+        buf = torch.from_numpy(np.ascontiguousarray(fr.transpose(1, 0, 2, 3))).to("cuda")
+        data.append((fr, c, buf))
+    with TacawPlan([stream_config(sp) for sp in specs], precision="split_bf16") as plan:
+        for sid in (0, 1, 0):
+            sp = specs[sid]
+            fr, c, buf = data[sid]
+            grad = torch.empty_like(buf)
+            plan.backward(sid, torch.tensor(c, dtype=torch.float32, device="cuda"), buf, grad)
+            g = grad.cpu().numpy().transpose(1, 0, 2, 3)
+            ref = oracle.gradient(fr, c, **oracle_kw(sp))
+            rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+            assert rel <= 1e-4, (sid, rel)
