@@ -240,3 +240,22 @@ def test_adjoint_on_each_stream_of_a_multi_stream_plan():
             ref = oracle.gradient(fr, c, **oracle_kw(sp))
             rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
             assert rel <= 1e-4, (sid, rel)
+
+
+def test_adjoint_precision_choices():
+    """tacaw_set_adjoint_precision takes split BF16 (tensor cores) or FP32 (CUDA cores); split FP16
+    or an unknown value is INVALID_ARG and leaves the plan usable."""
+    from paper_2607_02236_gb300 import TacawError, TacawPlan, build
+    from paper_2607_02236_gb300.tacaw import ERR_INVALID_ARG
+    from synth import StreamSpec
+    from tests.helpers import stream_config
+    build.build_all()
+    spec = StreamSpec(P=1, Kx=8, Ky=8, T=32, Tc=32, n_omega=8)
+    with TacawPlan([stream_config(spec)], precision="split_bf16") as plan:
+        plan.set_adjoint_precision("fp32")
+        plan.set_adjoint_precision("split_bf16")
+        for bad in ("split_fp16", "nope"):
+            with pytest.raises(TacawError) as ei:
+                plan.set_adjoint_precision(bad)
+            assert ei.value.status == ERR_INVALID_ARG
+        plan.set_adjoint_precision("fp32")
