@@ -329,6 +329,25 @@ tacaw_status tacaw_backward(tacaw_plan_t plan, int stream_id, const float *d_dL_
  * TACAW_PREC_FP32: FP32 CUDA cores.  Anything else is INVALID_ARG.  Applies to later calls. */
 tacaw_status tacaw_set_adjoint_precision(tacaw_plan_t plan, int precision);
 
+/* Pipelined segments (no counterpart in the paper; Sec. II.B processes batch after batch).
+ * With enable != 0, a finalized segment's contraction is not launched by tacaw_finalize_async:
+ * it is deferred, and the next segment's tacaw_finalize_async launches it together with the
+ * conversion of that next segment's pushes, which two extra warps of the same launch do while
+ * its tensor cores run (the pushes of a segment that follows a deferred one only record their
+ * frame addresses; the frames must stay valid until that launch has run).  Each segment stages
+ * into one of two staging areas in turn: enabling allocates the second (TACAW_ERR_OOM if it
+ * does not fit).  tacaw_drain launches a deferred contraction on its own; tacaw_finalize (the
+ * waiting form) does so before it waits.  Results of a segment are complete once its deferred
+ * contraction has run.  All calls of the plan go to one CUDA stream.
+ * Requirements (else TACAW_ERR_UNSUPPORTED): one stream without Welch averaging, the split-BF16
+ * staged path (not in place) with 32-frame blocks, T a multiple of 32 and K_stage >= T.
+ * Enable between segments (STATE otherwise); disabling while a contraction is deferred is STATE. */
+tacaw_status tacaw_set_pipelined_segments(tacaw_plan_t plan, int enable);
+
+/* Launches a deferred contraction (pipelined segments), on `stream`; no-op without one.
+ * STATE while the current segment's pushes wait for it (finalize that segment first).       */
+tacaw_status tacaw_drain(tacaw_plan_t plan, void *stream);
+
 /* Starts a new segment on every stream (e.g. the next probe batch or trajectory chunk):
  * clears frame counters and mean sums.  Enqueued on `stream`.                           */
 tacaw_status tacaw_reset(tacaw_plan_t plan, void *stream);

@@ -41,6 +41,8 @@ struct TcGroup {
     int stages, n_max;         // ring stages and ring/TMEM width (widest tile of the group)
     int64_t tiles;             // tiles of all entries
     int *counter;              // tile queue: the next tile index to hand out (zero at launch)
+    int conv_on;               // warps 10 and 11 convert the next segment's pushes (conv)
+    TcConvJob conv;
 };
 
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s per wait
@@ -315,6 +317,75 @@ __device__ __forceinline__ void tc_epilogue_regs(const TcPlanArgs &a, const RowC
     }
 }
 
+// Conversion job of a staged contraction launch (pipelined segments), run by its two extra
+// warps beside the tensor-core pipeline: each warp takes row tiles of 128 rows from a counter;
+// lane l converts rows 4l .. 4l + 3 of the tile over every frame of the segment: psi - mu_hat
+// split into bf16 hi/lo, 16-byte chunks of 4 frames stored at their pre-swizzled place (chunk c
+// of row m at c ^ (m mod 8)); per 32-frame block an FP32 sum of the residuals in frame order,
+// added to an FP64 row sum (the roundings of the tiled push conversion of block-aligned pushes).
+__device__ void tc_convert_job(const TcConvJob &j, int lane) {
+    uint4 *Hi = reinterpret_cast<uint4 *>(j.A_hi);
+    uint4 *Lo = reinterpret_cast<uint4 *>(j.A_lo);
+    const int n_kb = j.T / 32;
+    const int64_t n_tiles = j.M_pad / kMTile;
+    for (;;) {
+        int tile = 0;
+        if (lane == 0) tile = atomicAdd(j.counter, 1);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if ((int64_t)tile >= n_tiles) break;
+        int64_t m[4], off[4];
+        float2 mu[4];
+        double sr[4], si[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            m[r] = (int64_t)tile * kMTile + 4 * lane + r;
+            const bool ok = m[r] < j.M;
+            const int64_t p = ok ? m[r] / j.npix : 0;
+            const int64_t pix = ok ? m[r] - p * j.npix : 0;
+            const int64_t y = pix / j.kx, x = pix - y * j.kx;
+            off[r] = ok ? p * j.pitch_probe + (j.roi_y0 + y) * j.pitch_row + (j.roi_x0 + x) : -1;
+            mu[r] = ok ? j.mu_hat[m[r]] : make_float2(0.f, 0.f);
+            sr[r] = si[r] = 0.0;
+        }
+        for (int kb = 0; kb < n_kb; ++kb) {
+            float br[4] = {0.f, 0.f, 0.f, 0.f}, bi[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+            for (int c = 0; c < 8; ++c) {
+                float2 v[4][4];
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    const float2 *fp = j.frame_ptr[kb * 32 + 4 * c + f];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) v[r][f] = off[r] >= 0 ? __ldcs(fp + off[r]) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    uint32_t h[4], l[4];
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        const float2 q = off[r] >= 0 ? make_float2(v[r][f].x - mu[r].x, v[r][f].y - mu[r].y)
+                                                     : make_float2(0.f, 0.f);
+                        br[r] += q.x;
+                        bi[r] += q.y;
+                        split2_bf16(q, h[f], l[f]);
+                    }
+                    const size_t o = ((size_t)kb * (size_t)j.M_pad + (size_t)m[r]) * 8 + (size_t)(c ^ (int)(m[r] & 7));
+                    Hi[o] = make_uint4(h[0], h[1], h[2], h[3]);
+                    Lo[o] = make_uint4(l[0], l[1], l[2], l[3]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                sr[r] += br[r];
+                si[r] += bi[r];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (off[r] >= 0) j.sum_res[m[r]] = make_double2(sr[r], si[r]);
+    }
+}
+
 // --------------------------------------------------------------------------------------
 // Staged contraction (split drained form), persistent: one CTA per SM walks the tiles of all
 // streams of the group (tile t of the concatenated tile lists, t = blockIdx.x, blockIdx.x +
@@ -569,7 +640,7 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
                 trace[5] = (unsigned long long)chunks;
             }
         }
-    } else {
+    } else if (warp < 10) {
         // epilogue warps 2..9: TMEM lane quarter q4 = warp % 4, column half h
         const int q4 = warp & 3, h = (warp - 2) >> 2;
         float sum[kDrainCols];
@@ -645,6 +716,9 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
         // always wait (bounded) for the last commit: no MMA may still write TMEM at release
         if (!mbar_wait(smem_u32(&sh->tmem_full), 0u, nullptr)) atomicOr(err, DEVERR_TIMEOUT_TMEM);
         tc_fence_after();
+    } else if (g.conv_on) {
+        // warps 10 and 11 (launches with a conversion job only): the next segment's pushes
+        tc_convert_job(g.conv, lane);
     }
     tc_fence_before();
     __syncthreads();
@@ -1307,8 +1381,12 @@ int tc_resident_ctas(int N, int bf, int stages) {
 
 int64_t tc_grid_ctas(const TcPlanArgs &a) { return a.e.M_pad / kMTile * a.n_wt; }
 
-cudaError_t launch_flush_tc_group(const TcPlanArgs *args, int n, cudaStream_t st) {
+static cudaError_t launch_flush_tc_group_impl(const TcPlanArgs *args, int n, const TcConvJob *conv,
+                                              cudaStream_t st) {
     if (n < 1 || n > kMaxGroupStreams) return cudaErrorInvalidValue;
+    // 10 warps (producer, MMA, 8 epilogue); 12 with a conversion job.  At 168 registers a thread,
+    // 12 warps put 3 on each of the SM's four register files (16 128 of 16 384 registers).
+    const int threads = conv ? 384 : 320;
     TcGroup *g = new (std::nothrow) TcGroup();
     if (!g) return cudaErrorMemoryAllocation;
     int64_t total = 0;
@@ -1327,6 +1405,8 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, int n, cudaStream_t st
         n_max = std::max(n_max, args[i].N);
     }
     g->n = n;
+    g->conv_on = conv ? 1 : 0;
+    if (conv) g->conv = *conv;
     if (total <= 0 || total > 0x7fffffffLL) {
         delete g;
         return cudaErrorInvalidConfiguration;
@@ -1341,7 +1421,8 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, int n, cudaStream_t st
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(flush_tc_drain2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, flush_tc_drain2_kernel, 320, smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, flush_tc_drain2_kernel, threads, smem);
     if (e != cudaSuccess || g->stages < 2 || n_max > 2 * kDrainCols || occ < 1) {
         delete g;
         return e != cudaSuccess ? e : cudaErrorInvalidConfiguration;
@@ -1352,9 +1433,20 @@ cudaError_t launch_flush_tc_group(const TcPlanArgs *args, int n, cudaStream_t st
     // the CTAs take tiles from a counter in device memory, zeroed on the stream before the launch
     g->counter = args[0].tile_counter;
     e = cudaMemsetAsync(g->counter, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = launch_persistent(flush_tc_drain2_kernel, grid, 320, smem, st, *g);
+    if (e == cudaSuccess && conv) e = cudaMemsetAsync(conv->counter, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_persistent(flush_tc_drain2_kernel, grid, (unsigned)threads, smem, st, *g);
     delete g;
     return e;
+}
+
+cudaError_t launch_flush_tc_group(const TcPlanArgs *args, int n, cudaStream_t st) {
+    return launch_flush_tc_group_impl(args, n, nullptr, st);
+}
+
+cudaError_t launch_flush_tc_group_conv(const TcPlanArgs *args, int n, const TcConvJob &conv, cudaStream_t st) {
+    if (!conv.frame_ptr || !conv.counter || conv.T % 32 || conv.M_pad % kMTile || args[0].bf != 32)
+        return cudaErrorInvalidValue;
+    return launch_flush_tc_group_impl(args, n, &conv, st);
 }
 
 cudaError_t launch_flush_tc(const TcPlanArgs &a, cudaStream_t st) { return launch_flush_tc_group(&a, 1, st); }

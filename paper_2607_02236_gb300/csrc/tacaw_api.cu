@@ -103,6 +103,11 @@ struct Stream {
     float *adj_ones_f = nullptr;
     int64_t *adj_off = nullptr;      // element offset of each aperture pixel within a frame
     std::vector<int> h_adj_pix;      // host copy of adj_pix
+    // pipelined segments (tacaw_set_pipelined_segments): the second staging area and per-row
+    // buffers, swapped with the first at each deferred finalize
+    __nv_bfloat16 *A_hi2 = nullptr, *A_lo2 = nullptr;
+    float2 *mu_hat2 = nullptr, *dmu2 = nullptr;
+    double2 *sum_res2 = nullptr;
     int adj_wt1 = 0, adj_nwt1 = 0, adj_wt2 = 0, adj_nwt2 = 0;
     int stages = 0;            // shared-memory pipeline stages of this stream's tiles
     double *win_table = nullptr;   // table-driven windows (Dolph-Chebyshev)
@@ -185,6 +190,16 @@ struct tacaw_plan_s {
     void *adj_tc = nullptr;
     size_t adj_tc_bytes = 0;
     bool adj_fp32 = false;     // tacaw_set_adjoint_precision(TACAW_PREC_FP32): CUDA-core adjoint
+    // pipelined segments: a finalized segment's contraction is deferred and launched with the
+    // conversion of the next segment's pushes (done by extra warps of the same launch)
+    bool pipe = false;
+    bool deferred_pushes = false;  // this segment's pushes were recorded, not converted
+    struct Pending {
+        bool active = false;
+        Stream snap;                   // the deferred segment (its staging slot, sums, lists)
+        float *I = nullptr, *S = nullptr;
+        float2 *Psi = nullptr;
+    } pend;
     std::vector<void *> allocs;
     bool timing = false;
     bool trace = false;                      // record per-CTA phase stamps of tensor-core flushes
@@ -867,6 +882,94 @@ tacaw_status read_device_error(tacaw_plan_s *p, cudaStream_t st) {
     return TACAW_OK;
 }
 
+// Detector spectra of stream s from its block of I.
+tacaw_status launch_spectra(tacaw_plan_s *p, const Stream &s, const float *I, float *S, cudaStream_t st) {
+    if (s.D <= 0 || !I || !S) return TACAW_OK;
+    ApertureArgs a{};
+    a.I = I;
+    a.S = S;
+    a.P = s.d.n_probes;
+    a.D = s.D;
+    a.Nw = s.Nw;
+    a.npix = s.npix;
+    a.idx = s.det_idx;
+    a.wts = s.det_w;
+    a.off = s.det_off;
+    CU_CHECK(p, launch_aperture(a, st), "aperture");
+    p->launches++;
+    return TACAW_OK;
+}
+
+// Pipelined segments: launches the deferred segment's final contraction (its exact mean
+// correction, I, Psi, then its spectra); with conv, the same launch's extra warps convert the
+// recorded pushes of stream `conv` (the next segment) into its staging area.
+tacaw_status launch_pending(tacaw_plan_s *p, const Stream *conv, cudaStream_t st) {
+    tacaw_plan_s::Pending &q = p->pend;
+    Stream &ps = q.snap;
+    CU_CHECK(p, launch_mean_residual(ps.M, ps.T, ps.d.subtract_mean, ps.sum_res, ps.dmu, p->f16_scale, st),
+             "mean residual");
+    p->launches++;
+    TcPlanArgs a = tc_args(p, ps, epi_args(p, ps, FLUSH_FINAL, q.I, q.Psi));
+    a.tile_counter = p->d_counters + (p->counter_slot++ % kCounterRing);
+    tacaw_status r = trace_buffer(p, tc_grid_ctas(a), &a.trace);
+    if (r != TACAW_OK) return r;
+    cudaEvent_t e0, e1;
+    r = timing_begin(p, &e0, &e1, st);
+    if (r != TACAW_OK) return r;
+    if (conv) {
+        TcConvJob j{};
+        j.frame_ptr = conv->d_frame_ptr;
+        j.T = conv->T;
+        j.M = conv->M;
+        j.M_pad = conv->M_pad;
+        j.npix = conv->npix;
+        j.kx = conv->d.kx;
+        j.pitch_row = conv->d.pitch_row;
+        j.pitch_probe = conv->d.pitch_probe;
+        j.roi_x0 = conv->d.roi_x0;
+        j.roi_y0 = conv->d.roi_y0;
+        j.mu_hat = conv->mu_hat;
+        j.sum_res = conv->sum_res;
+        j.A_hi = conv->A_hi;
+        j.A_lo = conv->A_lo;
+        j.counter = p->d_counters + (p->counter_slot++ % kCounterRing);
+        CU_CHECK(p, launch_flush_tc_group_conv(&a, 1, j, st), "flush (tensor cores) with the next conversion");
+    } else {
+        CU_CHECK(p, launch_flush_tc(a, st), "flush (tensor cores)");
+    }
+    p->launches++;
+    p->flush_launches++;
+    p->flushes_total++;
+    r = timing_end(p, e0, e1, st);
+    if (r != TACAW_OK) return r;
+    q.active = false;
+    return launch_spectra(p, ps, q.I, q.S, st);
+}
+
+// Pipelined finalize: the pending segment's contraction goes out now, converting this segment's
+// recorded pushes; this segment's own contraction is deferred to the next finalize (or
+// tacaw_drain), and the next segment stages into the other area.
+tacaw_status finalize_pipelined(tacaw_plan_s *p, float *d_I, float *d_S, float2 *d_Psi, cudaStream_t st) {
+    Stream &s = p->s[0];
+    if (p->pend.active) {
+        tacaw_status r = launch_pending(p, p->deferred_pushes ? &s : nullptr, st);
+        if (r != TACAW_OK) return r;
+    }
+    p->pend.snap = s;
+    p->pend.I = d_I ? d_I + s.I_off : nullptr;
+    p->pend.S = d_S ? d_S + s.S_off : nullptr;
+    p->pend.Psi = d_Psi ? d_Psi + s.I_off : nullptr;
+    p->pend.active = true;
+    std::swap(s.A_hi, s.A_hi2);
+    std::swap(s.A_lo, s.A_lo2);
+    std::swap(s.mu_hat, s.mu_hat2);
+    std::swap(s.sum_res, s.sum_res2);
+    std::swap(s.dmu, s.dmu2);
+    p->deferred_pushes = false;
+    p->finalized = true;
+    return TACAW_OK;
+}
+
 tacaw_status finalize_impl(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, cudaStream_t st) {
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
@@ -885,6 +988,7 @@ tacaw_status finalize_impl(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, 
     if (d_S && !d_I) return fail(TACAW_ERR_INVALID_ARG, "d_S requires d_I");
     for (auto &u : p->us)
         if (d_Psi && u.N > 1) return fail(TACAW_ERR_INVALID_ARG, "d_Psi is not available for Welch-averaged streams");
+    if (p->pipe) return finalize_pipelined(p, d_I, d_S, static_cast<float2 *>(d_Psi), st);
     {
         tacaw_status r = flush_due(p, st);   // none expected: a due stream still awaits frames
         if (r != TACAW_OK) return r;
@@ -972,6 +1076,16 @@ tacaw_status push_internal(tacaw_plan_s *p, Stream &s, const float2 *frames, int
     if (s.pushed == 0 && s.d.subtract_mean) {
         CU_CHECK(p, launch_mean(g, n_frames, s.mu_hat, st), "provisional mean");
         p->launches++;
+    }
+    if (p->pipe && p->pend.active) {
+        // pipelined segments: the pending contraction's launch converts this segment's frames;
+        // here only their addresses are recorded (by a kernel on the stream)
+        CU_CHECK(p, launch_frame_table(s.d_frame_ptr + s.pushed, frames, g.pitch_frame, n_frames, st), "frame table");
+        p->launches++;
+        s.staged += n_frames;
+        s.pushed += n_frames;
+        p->deferred_pushes = true;
+        return TACAW_OK;
     }
     int done = 0;
     while (done < n_frames) {
@@ -1542,7 +1656,54 @@ tacaw_status tacaw_finalize(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     tacaw_status r = finalize_impl(p, d_I, d_S, d_Psi, st);
     if (r != TACAW_OK) return r;
+    if (p->pend.active) {
+        r = launch_pending(p, nullptr, st);
+        if (r != TACAW_OK) return r;
+    }
     return read_device_error(p, st);
+}
+
+tacaw_status tacaw_drain(tacaw_plan_t p, void *stream) {
+    tacaw_status c = check_plan(p);
+    if (c != TACAW_OK) return c;
+    if (p->deferred_pushes)
+        return fail(TACAW_ERR_STATE, "the segment's pushes wait for the pending contraction: finalize the segment first");
+    if (!p->pend.active) return TACAW_OK;
+    return launch_pending(p, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+tacaw_status tacaw_set_pipelined_segments(tacaw_plan_t p, int enable) {
+    tacaw_status c = check_plan(p);
+    if (c != TACAW_OK) return c;
+    if (!enable) {
+        if (p->pend.active || p->deferred_pushes)
+            return fail(TACAW_ERR_STATE, "a segment's contraction is deferred: call tacaw_drain first");
+        p->pipe = false;
+        return TACAW_OK;
+    }
+    if (p->pipe) return TACAW_OK;
+    if (p->us.size() != 1 || p->s.size() != 1)
+        return fail(TACAW_ERR_UNSUPPORTED, "pipelined segments: one stream without Welch averaging");
+    Stream &s = p->s[0];
+    if (p->prec != TACAW_PREC_SPLIT_BF16 || p->f16 || p->in_place || p->bf != 32)
+        return fail(TACAW_ERR_UNSUPPORTED, "pipelined segments: staged split-BF16 plans with 32-frame blocks");
+    if (s.T % 32 || s.ring < s.T)
+        return fail(TACAW_ERR_UNSUPPORTED, "pipelined segments: T a multiple of 32 and K_stage >= T (one flush a segment)");
+    if (s.pushed != 0) return fail(TACAW_ERR_STATE, "pipelined segments: enable between segments");
+    if (!s.A_hi2) {
+        const size_t na = (size_t)(s.ring / p->bf) * s.M_pad * 2 * p->bf;
+        if (!dev_alloc(p, &s.A_hi2, na) || !dev_alloc(p, &s.A_lo2, na) || !dev_alloc(p, &s.mu_hat2, s.M) ||
+            !dev_alloc(p, &s.dmu2, s.M) || !dev_alloc(p, &s.sum_res2, s.M))
+            return fail(TACAW_ERR_OOM, "cudaMalloc(second staging area of %.1f GB)", 2.0 * na * 2 / 1e9);
+        CU_CHECK(p, cudaMemset(s.A_hi2, 0, na * sizeof(__nv_bfloat16)), "memset staging");
+        CU_CHECK(p, cudaMemset(s.A_lo2, 0, na * sizeof(__nv_bfloat16)), "memset staging");
+        CU_CHECK(p, cudaMemset(s.sum_res2, 0, sizeof(double2) * s.M), "memset sums");
+        CU_CHECK(p, cudaMemset(s.mu_hat2, 0, sizeof(float2) * s.M), "memset mean");
+    }
+    if (!s.d_frame_ptr && !dev_alloc(p, &s.d_frame_ptr, (size_t)s.T))
+        return fail(TACAW_ERR_OOM, "cudaMalloc(frame table)");
+    p->pipe = true;
+    return TACAW_OK;
 }
 
 tacaw_status tacaw_finalize_async(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, void *stream) {
@@ -1578,6 +1739,7 @@ tacaw_status tacaw_reset(tacaw_plan_t p, void *stream) {
         u.pushed = 0;
         if (u.I_acc) CU_CHECK(p, cudaMemsetAsync(u.I_acc, 0, sizeof(float) * u.I_elems, st), "reset Welch average");
     }
+    p->deferred_pushes = false;
     p->finalized = false;
     return TACAW_OK;
 }

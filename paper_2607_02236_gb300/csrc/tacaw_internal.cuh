@@ -346,6 +346,24 @@ struct TcDirectArgs {
     int T;
 };
 cudaError_t launch_flush_tc(const TcPlanArgs &a, cudaStream_t st);
+// Conversion of the next segment's pushes, done by two extra warps of a staged contraction
+// launch while its tensor cores run (pipelined segments): frames t < T of the segment through a
+// table of frame pointers, rows m < M_pad (rows >= M staged as zeros), split BF16, 32-frame
+// blocks, pre-swizzled; sum_res[m] = sum over the segment of (psi - mu_hat) (written, FP64).
+struct TcConvJob {
+    const float2 *const *frame_ptr;   // [T] device pointers to each frame (pushed layout)
+    int T;                            // frames (a multiple of 32)
+    int64_t M, M_pad, npix;
+    int kx;
+    int64_t pitch_row, pitch_probe;
+    int roi_x0, roi_y0;
+    const float2 *mu_hat;             // [M] provisional mean
+    double2 *sum_res;                 // [M] written
+    __nv_bfloat16 *A_hi, *A_lo;       // staging [T/32][M_pad][64]
+    int *counter;                     // row tiles handed out (zero at launch)
+};
+// launch_flush_tc_group with a conversion job for its two extra warps (384 threads a CTA)
+cudaError_t launch_flush_tc_group_conv(const TcPlanArgs *args, int n, const TcConvJob &conv, cudaStream_t st);
 int64_t tc_grid_ctas(const TcPlanArgs &a);
 constexpr int kMaxGroupStreams = 16;
 constexpr int kDrainMaxOmegaTile = 112;   // staged form: complex energies per tile at most

@@ -29,7 +29,7 @@ EXPORTS = ["tacaw_plan_create", "tacaw_push_frames", "tacaw_finalize", "tacaw_ou
            "tacaw_kernel_time_ms", "tacaw_destroy", "tacaw_last_error", "tacaw_version",
            "tacaw_detector_spectra_noalloc", "tacaw_flush_trace", "tacaw_finalize_async",
            "tacaw_check_errors", "tacaw_set_log_callback", "tacaw_set_wait_limit_ns", "tacaw_push_frames_group",
-           "tacaw_set_adjoint_precision"]
+           "tacaw_set_adjoint_precision", "tacaw_set_pipelined_segments", "tacaw_drain"]
 
 
 class TacawError(RuntimeError):
@@ -96,6 +96,8 @@ def lib():
     L.tacaw_set_timing.argtypes = [c_void_p, c_int]
     L.tacaw_set_wait_limit_ns.argtypes = [c_void_p, ctypes.c_uint64]
     L.tacaw_set_adjoint_precision.argtypes = [c_void_p, c_int]
+    L.tacaw_set_pipelined_segments.argtypes = [c_void_p, c_int]
+    L.tacaw_drain.argtypes = [c_void_p, c_void_p]
     L.tacaw_kernel_time_ms.argtypes = [c_void_p, POINTER(c_double), POINTER(c_int64), c_int]
     L.tacaw_destroy.argtypes = [c_void_p]
     L.tacaw_flush_trace.argtypes = [c_void_p, c_void_p, c_int64, POINTER(c_int64)]
@@ -271,6 +273,15 @@ class TacawPlan:
     def set_adjoint_precision(self, precision: str):
         """Arithmetic of backward(): "split_bf16" (tensor cores, the default) or "fp32"."""
         _check(lib().tacaw_set_adjoint_precision(self._h, PRECISIONS.get(precision, -1)))
+
+    def set_pipelined_segments(self, enable: bool = True):
+        """Defer each segment's contraction to the next segment's finalize_async, which converts
+        that segment's pushes in the same launch (see include/tacaw.h)."""
+        _check(lib().tacaw_set_pipelined_segments(self._h, 1 if enable else 0))
+
+    def drain(self, cuda_stream=None):
+        """Launches a deferred contraction (pipelined segments)."""
+        _check(lib().tacaw_drain(self._h, _stream(cuda_stream)))
 
     def set_timing(self, on):
         """on: False/True, or 2 to also record per-CTA phase stamps of tensor-core flushes."""

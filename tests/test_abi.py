@@ -71,6 +71,8 @@ def test_null_plan_calls_are_errors(L):
     assert L.tacaw_push_frames_group(None, 1, None, None, None, None) == t.ERR_INVALID_ARG
     assert L.tacaw_finalize(None, None, None, None, None) == t.ERR_INVALID_ARG
     assert L.tacaw_set_adjoint_precision(None, t.PRECISIONS["split_bf16"]) == t.ERR_INVALID_ARG
+    assert L.tacaw_set_pipelined_segments(None, 1) == t.ERR_INVALID_ARG
+    assert L.tacaw_drain(None, None) == t.ERR_INVALID_ARG
     assert L.tacaw_destroy(None) == t.OK
 
 

@@ -52,6 +52,8 @@ int main(void) {
     st = tacaw_set_timing(plan, 1);
     st = tacaw_set_wait_limit_ns(plan, 0);
     st = tacaw_set_adjoint_precision(plan, TACAW_PREC_SPLIT_BF16);
+    st = tacaw_set_pipelined_segments(plan, 0);
+    st = tacaw_drain(plan, NULL);
     st = tacaw_kernel_time_ms(plan, &ms, &nl, 1);
     st = tacaw_flush_trace(plan, trace, 1, &nc);
     st = tacaw_detector_spectra_noalloc(NULL, 1, 4, 8, 8, &det, 1, NULL, NULL);

@@ -1,0 +1,134 @@
+"""Pipelined segments: each segment's contraction is deferred and launched with the conversion of
+the next segment's pushes (done by extra warps of the same launch).  Over several segments the
+results are the same, bit for bit, as those of a plan that converts at push time and contracts at
+finalize, and match the FP64 oracle; the refusals leave the plan usable."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import Detector, StreamSpec, frames
+from tests.helpers import oracle_kw, rel_err_peak, stream_config
+
+pytestmark = pytest.mark.gpu
+
+# 3 probes x 40 x 36 ROI pixels (ragged row tiles) cropped at (6, 5) from a 52 x 46 grid, T = 128
+# in 32-frame pushes
+SPEC = StreamSpec(P=3, Kx=40, Ky=36, T=128, Tc=32, n_omega=90, E_max_meV=120.0, window="hann", n_modes=6,
+                  noise=1e-3, Gx=52, Gy=46, detectors=(Detector("circular", 0, 0, -1, 7.0),
+                                                       Detector("annular", 1.0, -2.0, 3.0, 9.0)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2607_02236_gb300 import build
+    build.build_all()
+
+
+def full_frames(spec, fr):
+    """[P, T, Ky, Kx] ROI frames -> [T, P, Gy, Gx] full frames (zero outside the ROI)."""
+    gx, gy = spec.full_grid
+    rx, ry = spec.roi_origin
+    P, T = fr.shape[:2]
+    out = np.zeros((T, P, gy, gx), dtype=np.complex64)
+    out[:, :, ry:ry + spec.Ky, rx:rx + spec.Kx] = fr.transpose(1, 0, 2, 3)
+    return out
+
+
+def run_segments(spec, bufs, pipelined, want_psi=False, sync_last=False):
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    gx, gy = spec.full_grid
+    fb = spec.P * gx * gy * 8
+    n_el = spec.P * spec.Nw * spec.Ky * spec.Kx
+    outs = [(torch.full((n_el,), -1.0, device="cuda"), torch.full((spec.P * 2 * spec.Nw,), -1.0, device="cuda"),
+             torch.zeros(n_el, dtype=torch.complex64, device="cuda") if want_psi else None) for _ in bufs]
+    st = torch.cuda.current_stream()
+    with TacawPlan([stream_config(spec)], precision="split_bf16") as plan:
+        if pipelined:
+            plan.set_pipelined_segments(True)
+        for k, buf in enumerate(bufs):
+            plan.reset(st)
+            for t in range(0, spec.T, spec.Tc):
+                plan.push(0, buf.data_ptr() + t * fb, spec.Tc, st)
+            I, S, Psi = outs[k]
+            if sync_last and k == len(bufs) - 1:
+                plan.finalize(I, S, Psi, st)
+            else:
+                plan.finalize_async(I, S, Psi, st)
+        if pipelined and not sync_last:
+            plan.drain(st)
+        plan.check_errors(st)
+        launches = plan.info()["flush_launches"]
+    torch.cuda.synchronize()
+    res = [(I.cpu().numpy().reshape(spec.P, spec.Nw, spec.Ky, spec.Kx), S.cpu().numpy().reshape(spec.P, 2, spec.Nw),
+            Psi.cpu().numpy().reshape(spec.P, spec.Nw, spec.Ky, spec.Kx) if Psi is not None else None)
+           for I, S, Psi in outs]
+    return res, launches
+
+
+@pytest.mark.parametrize("subtract_mean", [True, False])
+@pytest.mark.parametrize("sync_last", [False, True], ids=["drain", "finalize"])
+def test_pipelined_segments_match_unpipelined_and_oracle(subtract_mean, sync_last):
+    import dataclasses
+    import torch
+    spec = dataclasses.replace(SPEC, subtract_mean=subtract_mean)
+    roi = [frames.frames(spec, 60 + k, 0, spec.T) for k in range(4)]        # four segments
+    bufs = [torch.from_numpy(full_frames(spec, fr)).cuda() for fr in roi]
+    want_psi = not subtract_mean
+    ref_gpu, n_plain = run_segments(spec, bufs, False, want_psi)
+    got, n_pipe = run_segments(spec, bufs, True, want_psi, sync_last)
+    assert n_plain == n_pipe == 4                                           # one contraction a segment
+    for k, fr in enumerate(roi):
+        I, S, Psi = got[k]
+        I0, S0, Psi0 = ref_gpu[k]
+        assert np.array_equal(I, I0) and np.array_equal(S, S0), k
+        if want_psi:
+            assert np.array_equal(Psi, Psi0)
+        ref = oracle.forward(fr, **oracle_kw(spec))
+        assert rel_err_peak(I, ref.I) <= 1e-5, k
+        assert rel_err_peak(S, ref.S) <= 1e-5, k
+
+
+def test_pipelined_segments_refusals():
+    import torch
+    from paper_2607_02236_gb300 import TacawError, TacawPlan
+    from paper_2607_02236_gb300.tacaw import ERR_STATE, ERR_UNSUPPORTED
+    other = StreamSpec(P=1, Kx=16, Ky=16, T=64, Tc=32, n_omega=20)
+    cases = [([stream_config(SPEC), stream_config(other)], dict(precision="split_bf16")),   # two streams
+             ([stream_config(SPEC)], dict(precision="fp32")),
+             ([stream_config(SPEC)], dict(precision="split_fp16")),
+             ([stream_config(SPEC)], dict(precision="split_bf16", tc_block_frames=16)),
+             ([stream_config(SPEC)], dict(precision="split_bf16", k_stage=64))]              # two flushes
+    for streams, kw in cases:
+        with TacawPlan(streams, **kw) as plan:
+            with pytest.raises(TacawError) as ei:
+                plan.set_pipelined_segments(True)
+            assert ei.value.status == ERR_UNSUPPORTED, kw
+    gx, gy = SPEC.full_grid
+    buf = torch.zeros(SPEC.T * SPEC.P * gx * gy, dtype=torch.complex64, device="cuda")
+    fb = SPEC.P * gx * gy * 8
+    I = torch.empty(SPEC.P * SPEC.Nw * SPEC.Ky * SPEC.Kx, device="cuda")
+    with TacawPlan([stream_config(SPEC)], precision="split_bf16") as plan:
+        plan.push(0, buf.data_ptr(), 32)
+        with pytest.raises(TacawError) as ei:                       # mid-segment
+            plan.set_pipelined_segments(True)
+        assert ei.value.status == ERR_STATE
+        plan.reset()
+        plan.set_pipelined_segments(True)
+        for t in range(0, SPEC.T, 32):
+            plan.push(0, buf.data_ptr() + t * fb, 32)
+        plan.finalize_async(I)                                     # deferred
+        with pytest.raises(TacawError) as ei:                       # disabling with a deferred contraction
+            plan.set_pipelined_segments(False)
+        assert ei.value.status == ERR_STATE
+        plan.reset()
+        plan.push(0, buf.data_ptr(), 32)                           # recorded for the deferred launch
+        with pytest.raises(TacawError) as ei:
+            plan.drain()
+        assert ei.value.status == ERR_STATE
+        for t in range(32, SPEC.T, 32):
+            plan.push(0, buf.data_ptr() + t * fb, 32)
+        plan.finalize(I)                                           # launches both, waits
+        plan.set_pipelined_segments(False)
+    torch.cuda.synchronize()
+    assert float(I.abs().max()) == 0.0                             # zero frames: zero spectrum
