@@ -44,9 +44,9 @@ FLOP_PER_CMAC_FP32 = 8
 # reported only for that workload and while the source is unchanged.
 KERNEL_TRAFFIC = {
     # ncu --set full of flush_tc_drain2_kernel on `bench.py --small --no-extras` (the thick workload with
-    # 1 probe: 65536 rows, T = 8192, 1000 energies, 5.369e11 CMAC per launch): 8.586223 GB read +
-    # 0.263617 GB written per launch
-    ("06406ff05b0447e2", "flush_tc_drain2_kernel", "thick"): 1.648411e-02,
+    # 1 probe: 65536 rows, T = 8192, 1000 energies, 5.369e11 CMAC per launch): 8.589113 GB read +
+    # 0.263954 GB written per launch
+    ("b80a6bc027f1f76b", "flush_tc_drain2_kernel", "thick"): 1.649012e-02,
 }
 
 
@@ -56,7 +56,8 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="thick", choices=["thick", "realistic", "batched", "diff"],
+    ap.add_argument("--workload", default="thick", choices=["thick", "thick_pipelined", "realistic", "batched",
+                                                            "diff"],
                     help="thick (default): the 256-probe thick-sample scan per step; the others print their "
                          "own line (they are extra keys of the default line)")
     ap.add_argument("--no-extras", dest="extras", action="store_false", default=True,
@@ -1044,7 +1045,95 @@ def diff_leg(ctx, args, sample_clocks=True):
             "adjoint_fp32": dict(adj32, ms=adj32_ms, speedup_of_tensor_cores=adj32_ms / adj_ms)}
 
 
-LEGS = {"realistic": realistic_leg, "batched": batched_leg, "diff": diff_leg}
+# ----------------------------------------------------------------------------------------------
+# Thick sample with pipelined segments: the same 256 probes per step as 16 segments of 16 probes
+# (two staging areas of 16 probes fit in HBM, two of 32 do not); each segment's contraction runs
+# with the conversion of the next segment's pushes (tacaw_set_pipelined_segments)
+# ----------------------------------------------------------------------------------------------
+def thick_pipelined_leg(ctx, args, sample_clocks=True):
+    import numpy as np
+    import torch
+    import synth.gpu as sg
+    from paper_2607_02236_gb300 import TacawPlan
+    name, spec, B = thick_spec(args.small)
+    n_batch = spec.P // B
+    K, T, Tc, Nw = spec.Kx, spec.T, spec.Tc, spec.Nw
+    D = len(spec.detectors)
+    gx, gy = spec.full_grid
+    rx, ry = spec.roi_origin
+    npix = K * K
+    fe = B * gx * gy
+    H = max(1, B // 2)
+    n_seg = spec.P // H
+    cmac_step = spec.P * npix * T * Nw
+    st_t = torch.cuda.current_stream()
+    st = st_t.cuda_stream
+    R = 2
+    ring = torch.zeros(R * Tc * fe, dtype=torch.complex64, device="cuda")
+    for r in range(R):
+        sg.generate(spec, 33 + ctx.rank, ring.data_ptr() + r * Tc * fe * 8, r * Tc, Tc, pitch_row=gx,
+                    pitch_frame=fe, pitch_probe=gx * gy, out_x0=rx, out_y0=ry, p0=0, P=B, stream=st)
+    I = torch.empty(spec.P * Nw * npix, dtype=torch.float32, device="cuda")
+    S = torch.empty(max(1, spec.P * D * Nw), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    cfg = stream_config(spec, P=H)
+    cfg.pitch_frame = fe                       # frames of the ring hold all B probes of a batch
+    plan = TacawPlan([cfg], precision="split_bf16")
+    plan.set_pipelined_segments(True)
+    info = plan.info()
+    n_push = T // Tc
+    i_h, s_h = H * Nw * npix, H * D * Nw
+
+    def step(k):
+        for g in range(n_seg):
+            b, h = divmod(g, B // H)
+            plan.reset(st)
+            base = ring.data_ptr() + h * H * gx * gy * 8
+            for i in range(n_push):
+                plan.push(0, base + (i % R) * Tc * fe * 8, Tc, st)
+            o = b * B + h * H
+            plan.finalize_async(I[o * Nw * npix:o * Nw * npix + i_h], S[o * D * Nw:o * D * Nw + s_h] if D else None,
+                                None, st)
+        plan.drain(st)
+
+    ms, flush_ms, k_per_step, launches, clocks = timed_steps(ctx, [plan], step, args.steps, args.warmup,
+                                                             sample_clocks)
+    # stated error: 16 sampled (probe, pixel) series of the first and the last segment
+    rng = np.random.default_rng(ctx.rank + 7)
+    c = (K // 2) * K + K // 2
+    err = 0.0
+    for g in (0, n_seg - 1):
+        b, h = divmod(g, B // H)
+        pb = rng.integers(0, H, 16)
+        px = np.concatenate([[c, c + 3], rng.integers(0, npix, 14)])
+        rows = (h * H + pb) * gx * gy + (ry + px // K) * gx + (rx + px % K)
+        series = sample_series(ring.view(R * Tc, fe), rows, T, R * Tc)
+        o = b * B + h * H
+        got = gather_I(I[o * Nw * npix:o * Nw * npix + i_h].view(H, Nw, npix), pb, px)
+        e, _ = cpu_leg(series, got, spec, 0.0)
+        err = max(err, e)
+    plan.close()
+    del ring, I, S
+    free_device()
+    roof = tensor_roofline(cmac_step / max(k_per_step, 1), flush_ms, "flush_tc_drain2_kernel + conversion warps",
+                           k_per_step)
+    return {"workload": name + "-pipelined-16", "value": job_rate(cmac_step, ctx.world, ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "dtype": "bf16",
+            "config": {"probes_per_step": spec.P, "segment_probes": H, "segments_per_step": n_seg,
+                       "k_roi": f"{K}x{K} at ({rx}, {ry})", "T": T, "frames_per_push": Tc, "n_omega": Nw,
+                       "plan_device_GB": round(info["device_bytes"] / 1e9, 1),
+                       "step": "per segment: reset + pushes (recorded) + finalize_async, which launches the "
+                               "previous segment's contraction with this segment's conversion in its extra "
+                               "warps; tacaw_drain after the last",
+                       "why_16": "two staging areas of 32 probes (2 x 137 GB) do not fit beside the input ring "
+                                 "and I; two of 16 probes do"},
+            "max_rel_err_I_vs_fp64": err, "error_sample": "16 (probe, pixel) series of the first and the last "
+                                                          "segment, all energies",
+            "gpu_launches": launches, "contraction_launches_per_step": k_per_step, "clocks": clocks,
+            "roofline": roof}
+
+
+LEGS = {"realistic": realistic_leg, "batched": batched_leg, "diff": diff_leg, "thick_pipelined": thick_pipelined_leg}
 
 
 def standalone_line(ctx, args, d):
@@ -1076,7 +1165,7 @@ def main(argv=None):
     if args.extras and not args.small:
         # the differentiation step is ~5 ms: more steps for a stable time
         for name, leg in LEGS.items():
-            steps = "20" if name == "diff" else "3"
+            steps = "20" if name == "diff" else ("2" if name == "thick_pipelined" else "3")
             extra_args = parse(["--steps", steps, "--warmup", "3", "--fp32-steps", str(args.fp32_steps),
                                 "--fp16-steps", str(args.fp16_steps)])
             line[name] = leg(ctx, extra_args, sample_clocks=True)

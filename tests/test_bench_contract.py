@@ -59,7 +59,7 @@ def test_default_run_is_the_thick_headline_with_extra_legs():
     name, spec, B = bench.thick_spec(False)
     assert (spec.P, spec.Kx, spec.T, spec.Nw, B) == (256, 256, 8192, 1000, 32)
     assert spec.full_grid == (1024, 1024) and spec.roi_origin == (384, 384)
-    assert set(bench.LEGS) == {"realistic", "batched", "diff"}
+    assert set(bench.LEGS) == {"realistic", "batched", "diff", "thick_pipelined"}
 
 
 def test_standalone_line_carries_the_contract_keys():
