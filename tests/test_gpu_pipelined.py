@@ -132,3 +132,67 @@ def test_pipelined_segments_refusals():
         plan.set_pipelined_segments(False)
     torch.cuda.synchronize()
     assert float(I.abs().max()) == 0.0                             # zero frames: zero spectrum
+
+
+def test_pipelined_from_pinned_host_memory():
+    """Pushes from pinned host memory: the conversion warps read the frames over the host link
+    through the recorded addresses; bit-identical to the unpipelined plan on the same frames."""
+    import torch
+    roi = [frames.frames(SPEC, 70 + k, 0, SPEC.T) for k in range(3)]
+    bufs = [torch.from_numpy(full_frames(SPEC, fr)).pin_memory() for fr in roi]
+    ref_gpu, _ = run_segments(SPEC, bufs, False)
+    got, _ = run_segments(SPEC, bufs, True)
+    for k, fr in enumerate(roi):
+        assert np.array_equal(got[k][0], ref_gpu[k][0]) and np.array_equal(got[k][1], ref_gpu[k][1]), k
+        assert rel_err_peak(got[k][0], oracle.forward(fr, **oracle_kw(SPEC)).I) <= 1e-5
+
+
+def test_pipelined_segments_in_a_cuda_graph():
+    """Two pipelined segments and the drain captured into one CUDA graph and replayed with new frame
+    contents in the same buffers: each replay bit-identical to an unpipelined plan, and the
+    replays launch nothing through the library."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    gx, gy = SPEC.full_grid
+    fb = SPEC.P * gx * gy * 8
+    n_el = SPEC.P * SPEC.Nw * SPEC.Ky * SPEC.Kx
+    bufs = [torch.zeros(SPEC.T * SPEC.P * gy * gx, dtype=torch.complex64, device="cuda") for _ in range(2)]
+    Is = [torch.zeros(n_el, device="cuda") for _ in range(2)]
+    Ss = [torch.zeros(SPEC.P * 2 * SPEC.Nw, device="cuda") for _ in range(2)]
+    st = torch.cuda.Stream()
+
+    def segments(plan, stream):
+        for k in range(2):
+            plan.reset(stream)
+            for t in range(0, SPEC.T, SPEC.Tc):
+                plan.push(0, bufs[k].data_ptr() + t * fb, SPEC.Tc, stream)
+            plan.finalize_async(Is[k], Ss[k], None, stream)
+        plan.drain(stream)
+
+    with TacawPlan([stream_config(SPEC)], precision="split_bf16") as plan:
+        plan.set_pipelined_segments(True)
+        with torch.cuda.stream(st):                  # eager first (kernel attributes set outside capture)
+            segments(plan, st)
+            plan.check_errors(st)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            segments(plan, torch.cuda.current_stream())
+        launches = plan.info()["kernel_launches"]
+        for seed in (80, 90):
+            roi = [frames.frames(SPEC, seed + k, 0, SPEC.T) for k in range(2)]
+            for b, fr in zip(bufs, roi):
+                b.copy_(torch.from_numpy(full_frames(SPEC, fr)).view(-1))
+            for x in Is + Ss:
+                x.fill_(-1.0)
+            torch.cuda.synchronize()
+            g.replay()
+            torch.cuda.synchronize()
+            plan.check_errors(torch.cuda.current_stream())
+            ref_gpu, _ = run_segments(SPEC, [b.view(SPEC.T, SPEC.P, gy, gx) for b in bufs], False)
+            for k in range(2):
+                I = Is[k].cpu().numpy().reshape(SPEC.P, SPEC.Nw, SPEC.Ky, SPEC.Kx)
+                S = Ss[k].cpu().numpy().reshape(SPEC.P, 2, SPEC.Nw)
+                assert np.array_equal(I, ref_gpu[k][0]) and np.array_equal(S, ref_gpu[k][1]), (seed, k)
+                assert rel_err_peak(I, oracle.forward(roi[k], **oracle_kw(SPEC)).I) <= 1e-5
+        assert plan.info()["kernel_launches"] == launches
+        del g
