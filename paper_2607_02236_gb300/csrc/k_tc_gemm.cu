@@ -347,16 +347,25 @@ __device__ void tc_convert_job(const TcConvJob &j, int lane) {
             mu[r] = ok ? j.mu_hat[m[r]] : make_float2(0.f, 0.f);
             sr[r] = si[r] = 0.0;
         }
+        // rows past M read row 0's place (a valid address) and are zeroed below, so that every
+        // load issues without a branch
+        int64_t roff[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) roff[r] = off[r] >= 0 ? off[r] : (off[0] >= 0 ? off[0] : 0);
+        const bool any = off[0] >= 0;
         for (int kb = 0; kb < n_kb; ++kb) {
             float br[4] = {0.f, 0.f, 0.f, 0.f}, bi[4] = {0.f, 0.f, 0.f, 0.f};
+            // the block's 32 frame addresses, one a lane, handed to the others by shuffles
+            const float2 *my_fp = j.frame_ptr[kb * 32 + lane];
 #pragma unroll 2
             for (int c = 0; c < 8; ++c) {
                 float2 v[4][4];
 #pragma unroll
                 for (int f = 0; f < 4; ++f) {
-                    const float2 *fp = j.frame_ptr[kb * 32 + 4 * c + f];
+                    const float2 *fp = reinterpret_cast<const float2 *>(
+                        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(my_fp), 4 * c + f));
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) v[r][f] = off[r] >= 0 ? __ldcs(fp + off[r]) : make_float2(0.f, 0.f);
+                    for (int r = 0; r < 4; ++r) v[r][f] = any ? __ldcs(fp + roff[r]) : make_float2(0.f, 0.f);
                 }
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
