@@ -184,14 +184,17 @@ __global__ void convert_split_kernel(FrameGeom g, int n, int s0, int bf, int64_t
 // (16-byte chunks XOR-swizzled by row to spread the banks); the CTA then writes the piece's
 // chunks of the 128 rows with consecutive threads on consecutive chunks.  The stored swizzle
 // only exchanges chunks inside 32-byte sectors, so a piece always writes whole sectors.
-// The rows of block `blk` (rows 128 blk ..) of one push; run by 128 threads.
-template <int BF, bool F16>
+// The rows of block `blk` (rows 128 blk ..) of one push; run by 128 threads.  PF: the longest
+// piece the caller passes (BF, or 16 for pushes of at most 16 frames: half the registers and
+// shared memory, twice the CTAs an SM holds; the pieces, and so the sums, are the same).
+template <int BF, int PF, bool F16>
 __device__ __forceinline__ void convert_tiled_rows(const FrameGeom &g, int n, int s0, int64_t M_pad,
                                                    const float2 *mu_hat, double2 *sum_res, __nv_bfloat16 *A_hi,
                                                    __nv_bfloat16 *A_lo, int swz, float sc, uint32_t *err, int64_t blk) {
     constexpr int bf = BF;
-    constexpr int cpr = BF / 4;             // 16-byte chunks per row
-    __shared__ uint4 tile_h[128 * cpr], tile_l[128 * cpr];
+    constexpr int cpr = BF / 4;             // 16-byte chunks per staged row
+    constexpr int lcpr = PF / 4;            // 16-byte chunks of a piece
+    __shared__ uint4 tile_h[128 * lcpr], tile_l[128 * lcpr];
     const int r = threadIdx.x;
     const int64_t m0 = blk * 128;
     const int64_t m = m0 + r;
@@ -206,13 +209,13 @@ __device__ __forceinline__ void convert_tiled_rows(const FrameGeom &g, int n, in
         const int f0 = (s0 + t0) % bf;                 // first frame of the piece inside its block
         const int len = min(bf - f0, n - t0);          // a multiple of 4
         const int c0 = f0 / 4, nc = len / 4;
-        float2 v[BF];
+        float2 v[PF];
 #pragma unroll
-        for (int i = 0; i < BF; ++i)
+        for (int i = 0; i < PF; ++i)
             v[i] = (valid && i < len) ? __ldcs(src + (int64_t)(t0 + i) * g.pitch_frame) : make_float2(0.f, 0.f);
         float br = 0.f, bi = 0.f;
 #pragma unroll
-        for (int k = 0; k < cpr; ++k) {
+        for (int k = 0; k < lcpr; ++k) {
             if (k >= nc) break;
             uint32_t h[4], l[4];
 #pragma unroll
@@ -222,8 +225,7 @@ __device__ __forceinline__ void convert_tiled_rows(const FrameGeom &g, int n, in
                 bi += q.y;
                 split2<F16>(q, sc, amax, h[i], l[i]);
             }
-            const int c = c0 + k;
-            const int slot = r * cpr + (c ^ (r & (cpr - 1)));
+            const int slot = r * lcpr + (k ^ (r & (lcpr - 1)));
             tile_h[slot] = make_uint4(h[0], h[1], h[2], h[3]);
             tile_l[slot] = make_uint4(l[0], l[1], l[2], l[3]);
         }
@@ -232,8 +234,8 @@ __device__ __forceinline__ void convert_tiled_rows(const FrameGeom &g, int n, in
         __syncthreads();
         const size_t base = ((size_t)((s0 + t0) / bf) * M_pad + m0) * cpr;   // in 16-byte units
         for (int q = r; q < 128 * nc; q += 128) {
-            const int rr = q / nc, c = c0 + (q - (q / nc) * nc);
-            const int slot = rr * cpr + (c ^ (rr & (cpr - 1)));
+            const int rr = q / nc, k = q - (q / nc) * nc, c = c0 + k;
+            const int slot = rr * lcpr + (k ^ (rr & (lcpr - 1)));
             // stored chunk position of chunk c (m0 is a multiple of 128: row rr's pattern)
             const int cs = swz ? (c ^ (((rr * cpr) >> 3) & (cpr - 1))) : c;
             Hi[base + rr * cpr + cs] = tile_h[slot];
@@ -251,24 +253,24 @@ __device__ __forceinline__ void convert_tiled_rows(const FrameGeom &g, int n, in
     if (F16 && amax > kF16Max) atomicOr(err, DEVERR_FP16_RANGE);
 }
 
-template <int BF, bool F16>
+template <int BF, int PF, bool F16>
 __global__ void __launch_bounds__(128) convert_split_tiled_kernel(FrameGeom g, int n, int s0, int64_t M_pad,
                                                                   const float2 *mu_hat, double2 *sum_res,
                                                                   __nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, int swz,
                                                                   float sc, uint32_t *err) {
-    convert_tiled_rows<BF, F16>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo, swz, sc, err, blockIdx.x);
+    convert_tiled_rows<BF, PF, F16>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo, swz, sc, err, blockIdx.x);
 }
 
 // One push of each of several streams in one launch: CTA b converts block b - e.cta_begin of
 // the entry whose range holds b (entries in order of cta_begin).
-template <int BF, bool F16>
+template <int BF, int PF, bool F16>
 __global__ void __launch_bounds__(128) convert_split_group_kernel(const __grid_constant__ ConvGroup cg, int swz,
                                                                   float sc, uint32_t *err) {
     int k = 0;
     while (k + 1 < cg.n && (int64_t)blockIdx.x >= cg.e[k + 1].cta_begin) ++k;
     const ConvEntry &e = cg.e[k];
-    convert_tiled_rows<BF, F16>(e.g, e.n, e.s0, e.M_pad, e.mu_hat, e.sum_res, e.A_hi, e.A_lo, swz, sc, err,
-                                (int64_t)blockIdx.x - e.cta_begin);
+    convert_tiled_rows<BF, PF, F16>(e.g, e.n, e.s0, e.M_pad, e.mu_hat, e.sum_res, e.A_hi, e.A_lo, swz, sc, err,
+                                    (int64_t)blockIdx.x - e.cta_begin);
 }
 
 __global__ void convert_fp32_kernel(FrameGeom g, int n, int s0, int64_t M_pad, const float2 *mu_hat,
@@ -350,12 +352,15 @@ static cudaError_t convert_split(const FrameGeom &g, int n, int s0, int bf, int6
                                  uint32_t *err, cudaStream_t st) {
     if (convert_split_groupable(bf, s0, n)) {
         const unsigned grid = (unsigned)(M_pad / 128);
-        if (bf == 32)
-            convert_split_tiled_kernel<32, F16><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo,
-                                                                      swz, sc, err);
+        if (bf == 32 && n > 16)
+            convert_split_tiled_kernel<32, 32, F16><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi,
+                                                                          A_lo, swz, sc, err);
+        else if (bf == 32)
+            convert_split_tiled_kernel<32, 16, F16><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi,
+                                                                          A_lo, swz, sc, err);
         else
-            convert_split_tiled_kernel<16, F16><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi, A_lo,
-                                                                      swz, sc, err);
+            convert_split_tiled_kernel<16, 16, F16><<<grid, 128, 0, st>>>(g, n, s0, M_pad, mu_hat, sum_res, A_hi,
+                                                                          A_lo, swz, sc, err);
         return cudaGetLastError();
     }
     convert_split_kernel<F16><<<blocks_for(g.M, 256), 256, 0, st>>>(g, n, s0, bf, M_pad, mu_hat, sum_res, A_hi,
@@ -385,12 +390,18 @@ cudaError_t launch_convert_split_group(ConvGroup &cg, int bf, int swz, int f16, 
     if (ctas > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const unsigned grid = (unsigned)ctas;
     const float sc = f16 ? f16_scale : 1.f;
-    if (bf == 32) {
-        if (f16) convert_split_group_kernel<32, true><<<grid, 128, 0, st>>>(cg, swz, sc, err);
-        else convert_split_group_kernel<32, false><<<grid, 128, 0, st>>>(cg, swz, sc, err);
+    // pushes of at most 16 frames everywhere: the half-size variant (more CTAs an SM)
+    bool short_pushes = true;
+    for (int i = 0; i < cg.n; ++i) short_pushes = short_pushes && cg.e[i].n <= 16;
+    if (bf == 32 && !short_pushes) {
+        if (f16) convert_split_group_kernel<32, 32, true><<<grid, 128, 0, st>>>(cg, swz, sc, err);
+        else convert_split_group_kernel<32, 32, false><<<grid, 128, 0, st>>>(cg, swz, sc, err);
+    } else if (bf == 32) {
+        if (f16) convert_split_group_kernel<32, 16, true><<<grid, 128, 0, st>>>(cg, swz, sc, err);
+        else convert_split_group_kernel<32, 16, false><<<grid, 128, 0, st>>>(cg, swz, sc, err);
     } else {
-        if (f16) convert_split_group_kernel<16, true><<<grid, 128, 0, st>>>(cg, swz, sc, err);
-        else convert_split_group_kernel<16, false><<<grid, 128, 0, st>>>(cg, swz, sc, err);
+        if (f16) convert_split_group_kernel<16, 16, true><<<grid, 128, 0, st>>>(cg, swz, sc, err);
+        else convert_split_group_kernel<16, 16, false><<<grid, 128, 0, st>>>(cg, swz, sc, err);
     }
     return cudaGetLastError();
 }
