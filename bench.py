@@ -44,9 +44,9 @@ FLOP_PER_CMAC_FP32 = 8
 # reported only for that workload and while the source is unchanged.
 KERNEL_TRAFFIC = {
     # ncu --set full of flush_tc_drain2_kernel on `bench.py --small --no-extras` (the thick workload with
-    # 1 probe: 65536 rows, T = 8192, 1000 energies, 5.369e11 CMAC per launch): 8.587253 GB read +
-    # 0.263871 GB written per launch
-    ("e239afcb52f7e4f4", "flush_tc_drain2_kernel", "thick"): 1.648650e-02,
+    # 1 probe: 65536 rows, T = 8192, 1000 energies, 5.369e11 CMAC per launch): 8.588006 GB read +
+    # 0.263809 GB written per launch
+    ("c203f07464ecfede", "flush_tc_drain2_kernel", "thick"): 1.648779e-02,
 }
 
 

@@ -681,8 +681,25 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
             const int col0 = h * cols;
             const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)col0;
             const int n_chunks = (a.n_kb + a.drain_kb - 1) / a.drain_kb;
+            // plain FP32 accumulators of earlier flushes start this tile's running sums: read while
+            // the tile's first products run, so that the tile's epilogue only stores (the reads
+            // then wait on nothing); compensated and FP64 accumulators are added at the end
+            const int kind0 = epi_kind(a.e);
+            const bool preload = (kind0 == EPI_ADD_KAHAN || kind0 == EPI_FINAL_KAHAN) && a.e.acc_c == nullptr;
+            {
+                // this thread's energies j0 .. j0 + nv - 1 of row mrow (accumulators [Nw_pad][M_pad])
+                const int64_t mrow = (int64_t)m0 + q4 * 32 + lane;
+                const int j0 = wtile * a.wt + (col0 >> 1);
+                const int nv = (preload && mrow < a.e.M) ? max(0, min(cols >> 1, a.e.Nw - j0)) : 0;
+                const float2 *ap = preload ? a.e.acc_s + (size_t)j0 * (size_t)a.e.M_pad + (size_t)mrow : nullptr;
+                const size_t stride = (size_t)a.e.M_pad;
 #pragma unroll
-            for (int i = 0; i < kDrainCols; ++i) sum[i] = 0.f;
+                for (int i = 0; i < kDrainCols / 2; ++i) {
+                    const float2 v = i < nv ? ap[(size_t)i * stride] : make_float2(0.f, 0.f);
+                    sum[2 * i] = v.x;
+                    sum[2 * i + 1] = v.y;
+                }
+            }
             for (int lc = 0; lc + 1 < n_chunks; ++lc, ++hc) {
                 if (!mbar_wait(smem_u32(&sh->chunk_full[0]), (uint32_t)(hc & 1), abort_flag, wait_ns)) {
                     if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
@@ -697,7 +714,7 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
                 if (lane == 0) mbar_arrive(smem_u32(&sh->chunk_free[0]));
             }
             if (!ok) break;
-            tc_epilogue_prefetch(a, (int64_t)m0 + q4 * 32 + lane, col0, cols, wtile * a.wt);
+            if (!preload) tc_epilogue_prefetch(a, (int64_t)m0 + q4 * 32 + lane, col0, cols, wtile * a.wt);
             if (!mbar_wait(smem_u32(&sh->chunk_full[1]), (uint32_t)(tiles & 1), abort_flag, wait_ns)) {
                 if (!*abort_flag) atomicOr(err, DEVERR_TIMEOUT_TMEM);
                 *abort_flag = 1;
@@ -712,7 +729,10 @@ __global__ void __maxnreg__(168) flush_tc_drain2_kernel(const __grid_constant__ 
             if (lane == 0) mbar_arrive(smem_u32(&sh->chunk_free[1]));
             const RowCtx row = make_row(a.e, (int64_t)m0 + q4 * 32 + lane);
             const int jbase = wtile * a.wt;
-            switch (epi_kind(a.e)) {
+            // with preloaded sums an update of the accumulators is a store, a finalize one without
+            // earlier flushes
+            const int kind = preload ? (kind0 == EPI_ADD_KAHAN ? EPI_STORE_KAHAN : EPI_FINAL) : kind0;
+            switch (kind) {
                 case EPI_FINAL: tc_epilogue_regs<EPI_FINAL>(a, row, col0, cols, jbase, sum); break;
                 case EPI_FINAL_KAHAN: tc_epilogue_regs<EPI_FINAL_KAHAN>(a, row, col0, cols, jbase, sum); break;
                 case EPI_FINAL_FP64: tc_epilogue_regs<EPI_FINAL_FP64>(a, row, col0, cols, jbase, sum); break;
