@@ -196,3 +196,61 @@ def test_pipelined_segments_in_a_cuda_graph():
                 assert rel_err_peak(I, oracle.forward(roi[k], **oracle_kw(SPEC)).I) <= 1e-5
         assert plan.info()["kernel_launches"] == launches
         del g
+
+
+def test_pipelined_segments_at_the_thick_shape():
+    """The headline's shape: 1024^2 frames cropped to the centred 256^2 ROI while read, T = 8192 in
+    64-frame pushes, 1000 energies, read from a resident ring of two pushes of full frames (as the
+    bench cycles it); two one-probe segments pipelined against an unpipelined plan (1e-6 of the
+    peak: with 64-frame pushes the two paths add the per-block FP32 sums in another FP64 order) and
+    against the FP64 oracle at sampled (probe, pixel) series (1e-5)."""
+    import torch
+    import synth
+    import synth.gpu as sg
+    from paper_2607_02236_gb300 import TacawPlan
+    spec = synth.thick().streams[0]
+    K, T, Tc, Nw = spec.Kx, spec.T, spec.Tc, spec.Nw
+    gx, gy = spec.full_grid
+    rx, ry = spec.roi_origin
+    npix = K * K
+    B, R = 2, 2                                   # probes in the ring, pushes in the ring
+    fe = B * gx * gy
+    ring = torch.zeros(R * Tc * fe, dtype=torch.complex64, device="cuda")
+    for r in range(R):
+        sg.generate(spec, 41, ring.data_ptr() + r * Tc * fe * 8, r * Tc, Tc, pitch_row=gx, pitch_frame=fe,
+                    pitch_probe=gx * gy, out_x0=rx, out_y0=ry, p0=0, P=B)
+    cfg = stream_config(spec, P=1)
+    cfg.pitch_frame = fe
+    st = torch.cuda.current_stream()
+
+    def run(pipelined):
+        Is = [torch.full((Nw * npix,), -1.0, device="cuda") for _ in range(B)]
+        with TacawPlan([cfg], precision="split_bf16") as plan:
+            if pipelined:
+                plan.set_pipelined_segments(True)
+            for h in range(B):
+                plan.reset(st)
+                for i in range(T // Tc):
+                    plan.push(0, ring.data_ptr() + h * gx * gy * 8 + (i % R) * Tc * fe * 8, Tc, st)
+                plan.finalize_async(Is[h], None, None, st)
+            if pipelined:
+                plan.drain(st)
+            plan.check_errors(st)
+        torch.cuda.synchronize()
+        return [I.view(Nw, npix) for I in Is]
+
+    plain, pipe = run(False), run(True)
+    rng = np.random.default_rng(17)
+    kw = oracle_kw(spec)
+    kw.pop("detectors")
+    for h in range(B):
+        peak = float(plain[h].abs().max())
+        assert float((pipe[h] - plain[h]).abs().max()) <= 1e-6 * peak, h
+        px = np.concatenate([[(K // 2) * K + K // 2], rng.integers(0, npix, 7)])
+        rows = torch.as_tensor(h * gx * gy + (ry + px // K) * gx + (rx + px % K), device="cuda")
+        cyc = ring.view(R * Tc, fe)[:, rows].cpu().numpy()
+        series = cyc[np.arange(T) % (R * Tc)]
+        _, ref = oracle.forward_pixels(series, **kw)
+        got = pipe[h][:, torch.as_tensor(px, device="cuda")].cpu().numpy()
+        assert rel_err_peak(got, ref) <= 1e-5, h
+    del ring
