@@ -352,6 +352,39 @@ tacaw_status tacaw_drain(tacaw_plan_t plan, void *stream);
  * clears frame counters and mean sums.  Enqueued on `stream`.                           */
 tacaw_status tacaw_reset(tacaw_plan_t plan, void *stream);
 
+/* Checkpoint and resume of a segment in progress (no counterpart in the paper, whose runs
+ * resume by recomputing every batch not marked finished: Sec. II.B, batch dispatching).  The
+ * accumulation is a sum over the pushed frames, so between two pushes a plan's progress is a
+ * few buffers, and a plan created from the same descriptor that loads them continues where the
+ * saving plan stopped: the same later pushes give bit-identical results.
+ * tacaw_state_size: bytes of a checkpoint of the plan as it is now (after the pushes enqueued
+ *   so far): a 48-byte header, 48 bytes per internal stream (Welch lanes count one each) and 8
+ *   per stream, then the device sections.  Per internal stream: the provisional mean (8 bytes a
+ *   ROI row) and FP64 residual sums (16 a row); the staged frames not yet contracted (whole
+ *   blocks of the staging layout: 8 bytes a row and frame); once a flush has written them, the
+ *   Psi accumulators of the Nw energies (8 bytes a row and energy for FP32 accumulators, 16 for
+ *   compensated FP32 or FP64).  Per Welch-averaged stream its running average of I (4 bytes an
+ *   element).
+ * tacaw_save_state: writes the checkpoint to h_state (host memory, pageable or pinned, of at
+ *   least tacaw_state_size bytes; INVALID_ARG if smaller or device memory).  The copies run on
+ *   `stream` after the plan's earlier work there; the call returns when they are done and
+ *   reads the device error flag like tacaw_check_errors.
+ * tacaw_restore_state: loads a checkpoint into a plan created from the same descriptor
+ *   (precision, accumulators, K_stage, block frames, ROI, energies, window, time step, mean
+ *   subtraction and Welch segmentation must give the same layout; energy tiles and other
+ *   tuning may differ).  It replaces the plan's segment in progress, finalized or not; the
+ *   copies run on `stream` and the call returns when they are done.  INVALID_ARG, with the plan
+ *   unchanged, for bytes that are not a checkpoint, are truncated or corrupted, or were saved
+ *   by another configuration.
+ * STATE for tacaw_state_size and tacaw_save_state: a finalized segment (nothing to resume), a
+ *   deferred contraction (pipelined segments: tacaw_drain first, also before a restore), or,
+ *   with frames_in_place, pushed frames not yet contracted (the plan holds only their
+ *   addresses: checkpoint where the pushes so far fill whole K_stage rings).
+ * None of the three can be captured into a CUDA graph (they wait on the host).            */
+tacaw_status tacaw_state_size(tacaw_plan_t plan, int64_t *bytes);
+tacaw_status tacaw_save_state(tacaw_plan_t plan, void *h_state, int64_t bytes, void *stream);
+tacaw_status tacaw_restore_state(tacaw_plan_t plan, const void *h_state, int64_t bytes, void *stream);
+
 /* Fills *info.                                                                          */
 tacaw_status tacaw_plan_get_info(tacaw_plan_t plan, tacaw_plan_info *info);
 

@@ -29,7 +29,8 @@ EXPORTS = ["tacaw_plan_create", "tacaw_push_frames", "tacaw_finalize", "tacaw_ou
            "tacaw_kernel_time_ms", "tacaw_destroy", "tacaw_last_error", "tacaw_version",
            "tacaw_detector_spectra_noalloc", "tacaw_flush_trace", "tacaw_finalize_async",
            "tacaw_check_errors", "tacaw_set_log_callback", "tacaw_set_wait_limit_ns", "tacaw_push_frames_group",
-           "tacaw_set_adjoint_precision", "tacaw_set_pipelined_segments", "tacaw_drain"]
+           "tacaw_set_adjoint_precision", "tacaw_set_pipelined_segments", "tacaw_drain",
+           "tacaw_state_size", "tacaw_save_state", "tacaw_restore_state"]
 
 
 class TacawError(RuntimeError):
@@ -98,6 +99,9 @@ def lib():
     L.tacaw_set_adjoint_precision.argtypes = [c_void_p, c_int]
     L.tacaw_set_pipelined_segments.argtypes = [c_void_p, c_int]
     L.tacaw_drain.argtypes = [c_void_p, c_void_p]
+    L.tacaw_state_size.argtypes = [c_void_p, POINTER(c_int64)]
+    L.tacaw_save_state.argtypes = [c_void_p, c_void_p, c_int64, c_void_p]
+    L.tacaw_restore_state.argtypes = [c_void_p, c_void_p, c_int64, c_void_p]
     L.tacaw_kernel_time_ms.argtypes = [c_void_p, POINTER(c_double), POINTER(c_int64), c_int]
     L.tacaw_destroy.argtypes = [c_void_p]
     L.tacaw_flush_trace.argtypes = [c_void_p, c_void_p, c_int64, POINTER(c_int64)]
@@ -282,6 +286,25 @@ class TacawPlan:
     def drain(self, cuda_stream=None):
         """Launches a deferred contraction (pipelined segments)."""
         _check(lib().tacaw_drain(self._h, _stream(cuda_stream)))
+
+    def state_size(self) -> int:
+        """Bytes of a checkpoint of the segment in progress."""
+        n = c_int64()
+        _check(lib().tacaw_state_size(self._h, ctypes.byref(n)))
+        return n.value
+
+    def save_state(self, cuda_stream=None):
+        """Checkpoint of the segment in progress (numpy uint8; waits for the copies)."""
+        import numpy as np
+        out = np.empty(self.state_size(), dtype=np.uint8)
+        _check(lib().tacaw_save_state(self._h, out.ctypes.data, out.size, _stream(cuda_stream)))
+        return out
+
+    def restore_state(self, state, cuda_stream=None):
+        """Continues from a checkpoint of a plan built from the same descriptor (bytes-like)."""
+        import numpy as np
+        buf = np.frombuffer(state, dtype=np.uint8)
+        _check(lib().tacaw_restore_state(self._h, buf.ctypes.data, buf.size, _stream(cuda_stream)))
 
     def set_timing(self, on):
         """on: False/True, or 2 to also record per-CTA phase stamps of tensor-core flushes."""

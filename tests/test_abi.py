@@ -73,6 +73,11 @@ def test_null_plan_calls_are_errors(L):
     assert L.tacaw_set_adjoint_precision(None, t.PRECISIONS["split_bf16"]) == t.ERR_INVALID_ARG
     assert L.tacaw_set_pipelined_segments(None, 1) == t.ERR_INVALID_ARG
     assert L.tacaw_drain(None, None) == t.ERR_INVALID_ARG
+    n = ctypes.c_int64(-1)
+    assert L.tacaw_state_size(None, ctypes.byref(n)) == t.ERR_INVALID_ARG and n.value == -1
+    buf = ctypes.create_string_buffer(64)
+    assert L.tacaw_save_state(None, buf, 64, None) == t.ERR_INVALID_ARG
+    assert L.tacaw_restore_state(None, buf, 64, None) == t.ERR_INVALID_ARG
     assert L.tacaw_destroy(None) == t.OK
 
 

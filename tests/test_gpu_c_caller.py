@@ -1,8 +1,10 @@
 """The boundary driven from C on the GPU: a C99 program (no Python, no PyTorch) allocates device
-memory with the CUDA runtime, creates a plan through include/tacaw.h, pushes a segment in three
-pushes, finalizes into I and the detector spectra, runs tacaw_backward for L = sum c(E) S(E),
-and writes I, S and the gradient to files.  Those are compared here with the FP64 oracle:
-I and S within the split path's 1e-5 of peak, the gradient (FP32 adjoint) within 1e-4 relative L2.
+memory with the CUDA runtime, creates a plan through include/tacaw.h, takes the first of three
+pushes, checkpoints the plan into host memory and destroys it, resumes the segment in a second
+plan from that checkpoint, pushes the rest, finalizes into I and the detector spectra, runs
+tacaw_backward for L = sum c(E) S(E), and writes I, S and the gradient to files.  Those are
+compared here with the FP64 oracle: I and S within the split path's 1e-5 of peak, the gradient
+(FP32 adjoint) within 1e-4 relative L2.
 """
 import os
 import shutil
@@ -78,7 +80,19 @@ int main(int argc, char **argv) {
     tacaw_plan_t plan = NULL;
     tacaw_plan_info info;
     CK(tacaw_plan_create(&d, &plan));
-    for (int t = 0; t < T; t += PUSH)
+    CK(tacaw_push_frames(plan, 0, d_frames, PUSH, NULL));
+    /* checkpoint after the first push; a second plan of the same descriptor resumes from it */
+    int64_t state_bytes = 0;
+    CK(tacaw_state_size(plan, &state_bytes));
+    void *state = malloc((size_t)state_bytes);
+    if (!state) return 1;
+    CK(tacaw_save_state(plan, state, state_bytes, NULL));
+    CK(tacaw_destroy(plan));
+    plan = NULL;
+    CK(tacaw_plan_create(&d, &plan));
+    CK(tacaw_restore_state(plan, state, state_bytes, NULL));
+    free(state);
+    for (int t = PUSH; t < T; t += PUSH)
         CK(tacaw_push_frames(plan, 0, (const char *)d_frames + (size_t)t * P * K * K * 8, PUSH, NULL));
     CK(tacaw_finalize(plan, (float *)d_I, (float *)d_S, NULL, NULL));
     CK(tacaw_backward(plan, 0, (const float *)d_dlds, d_frames, d_grad, NULL));
