@@ -163,6 +163,36 @@ def test_tone_on_bin_lands_in_bin_and_hann_leaks_to_neighbours_only():
     assert I[mask].max() < 1e-20 * I[j0]
 
 
+@pytest.mark.parametrize("kind,slope", [("rect", -1.0), ("hann", -3.0)])
+def test_side_lobe_decay_rates(kind, slope):
+    """Far side lobes of an off-bin tone fall as 1/w (rectangular: a jump at the segment edges)
+    and 1/w^3 (Hann: value and slope vanish there), measured at lobe peaks k + 1/2 bins away."""
+    T, dt = 4096, 5.0
+    c0 = 311.37 / T                                  # cycles per frame, off any bin
+    k = np.array([16.5, 32.5, 64.5, 128.5])
+    E = (c0 + k / T) / oracle.cycles_per_frame(1.0, dt)
+    psi = np.exp(2j * np.pi * c0 * np.arange(T))[None, :, None, None]
+    r = oracle.forward(psi, window_kind=kind, E_meV=E, dt_fs=dt, subtract_mean=False)
+    a = np.abs(r.Psi[0, :, 0, 0])
+    np.testing.assert_allclose(np.diff(np.log(a)) / np.diff(np.log(k)), slope, atol=0.02)
+
+
+def test_hann_side_lobes_below_tukey_and_rect():
+    """The Hann window's side lobes lie below those of Tukey (alpha = 0.1) and of the rectangular
+    window at every offset from 4 to 200 bins (the window comparison of Sec. III.A)."""
+    T, dt = 1024, 5.0
+    c0 = 100.29 / T
+    k = np.linspace(4.0, 200.0, 1571)
+    E = (c0 + k / T) / oracle.cycles_per_frame(1.0, dt)
+    psi = np.exp(2j * np.pi * c0 * np.arange(T))[None, :, None, None]
+    env = {}
+    for kind, par in (("hann", 0.0), ("tukey", 0.1), ("rect", 0.0)):
+        a = np.abs(oracle.forward(psi, window_kind=kind, window_param=par, E_meV=E, dt_fs=dt,
+                                  subtract_mean=False).Psi[0, :, 0, 0])
+        env[kind] = np.array([a[(k >= b) & (k < b + 4)].max() for b in range(4, 200, 4)])   # lobe envelope
+    assert np.all(env["hann"] < env["tukey"]) and np.all(env["hann"] < env["rect"])
+
+
 def test_wiener_khinchin_off_grid():
     """|Psi(w)|^2 = sum_tau R(tau) exp(-i w tau), R(tau) = sum_n y_{n+tau} conj(y_n) (direct lag sums)."""
     T, dt = 60, 5.0
