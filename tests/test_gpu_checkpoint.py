@@ -314,3 +314,64 @@ def test_pipelined_segments_checkpoint_after_drain(data):
         got = outputs(A, SPEC, want_psi=False)
     assert_identical(got, ref)
     check_oracle(ref, fr, SPEC)
+
+
+# three partitions pushed one group per round of 32 frames; K_stage = 64 (rings of 64 frames)
+ROUND_SPECS = [StreamSpec(P=2, Kx=24, Ky=24, T=160, Tc=32, n_omega=50, E_max_meV=120.0, window="hann",
+                          detectors=(Detector(r_out=6.0),)),
+               StreamSpec(P=3, Kx=16, Ky=20, T=96, Tc=32, n_omega=30, E_max_meV=90.0, window="gauss",
+                          detectors=(Detector(r_out=4.0),), stream_id=1),
+               StreamSpec(P=1, Kx=32, Ky=32, T=224, Tc=32, n_omega=70, E_max_meV=150.0, window="hann",
+                          detectors=(), stream_id=2)]
+
+
+def group_rounds(plan, specs, bufs, r0, r1):
+    for r in range(r0, r1):
+        ids, ptrs, cnt = [], [], []
+        for i, s in enumerate(specs):
+            t = 32 * r
+            if t < s.T:
+                ids.append(i)
+                ptrs.append(bufs[i].data_ptr() + t * frame_bytes(s))
+                cnt.append(min(32, s.T - t))
+        if ids:
+            plan.push_group(ids, ptrs, cnt)
+
+
+@pytest.mark.parametrize("cut", [2, 3], ids=["all-rings-due", "mid-ring"])
+def test_resume_grouped_partitions(cut):
+    """Three partitions fed by tacaw_push_frames_group: after round 2 every ring is full and its
+    flush deferred to the next grouped launch; after round 3 the rings are half full.  A plan
+    that loads the checkpoint and takes the remaining rounds matches the uninterrupted plan bit
+    for bit, and the oracle for each partition."""
+    import torch
+    from paper_2607_02236_gb300 import TacawPlan
+    frs = [frames.frames(s, 100 + i, 0, s.T) for i, s in enumerate(ROUND_SPECS)]
+    bufs = [torch.from_numpy(np.ascontiguousarray(f.transpose(1, 0, 2, 3))).cuda() for f in frs]
+    n_rounds = max((s.T + 31) // 32 for s in ROUND_SPECS)
+    kw = dict(precision="split_bf16", k_stage=64, accum="kahan")
+    res = []
+    for resume in (False, True):
+        with TacawPlan([stream_config(s) for s in ROUND_SPECS], **kw) as A:
+            group_rounds(A, ROUND_SPECS, bufs, 0, cut)
+            state = A.save_state()
+            if not resume:
+                group_rounds(A, ROUND_SPECS, bufs, cut, n_rounds)
+                res.append((outputs(A, ROUND_SPECS[0]), [A.offsets(i) for i in range(3)]))
+                continue
+        with TacawPlan([stream_config(s) for s in ROUND_SPECS], **kw) as B:
+            B.restore_state(state)
+            group_rounds(B, ROUND_SPECS, bufs, cut, n_rounds)
+            res.append((outputs(B, ROUND_SPECS[0]), [B.offsets(i) for i in range(3)]))
+    (ref, offs), (got, _) = res
+    assert_identical(got, ref)
+    I, S, Psi = ref
+    for i, s in enumerate(ROUND_SPECS):
+        o = oracle.forward(frs[i], **oracle_kw(s))
+        io, so = offs[i]
+        n = s.P * s.Nw * s.Ky * s.Kx
+        assert rel_err_peak(I[io:io + n].reshape(s.P, s.Nw, s.Ky, s.Kx), o.I) <= TOL
+        assert rel_err_peak(Psi[io:io + n].reshape(s.P, s.Nw, s.Ky, s.Kx), o.Psi) <= TOL
+        D = len(s.detectors)
+        if D:
+            assert rel_err_peak(S[so:so + s.P * D * s.Nw].reshape(s.P, D, s.Nw), o.S) <= TOL
