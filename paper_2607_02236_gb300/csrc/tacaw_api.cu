@@ -1,4 +1,6 @@
-// Host implementation of the C ABI declared in include/tacaw.h.
+// Host implementation of the C ABI declared in include/tacaw.h: plans, pushes, flushes,
+// finalize and the plan queries (tacaw_backward.cu holds the adjoint, tacaw_state.cu the
+// checkpoints; tacaw_plan.cuh the plan's host-side state they share).
 //
 // A plan owns, per stream: the staging ring of K_stage frames (converted on push), the
 // FP64 sums of the mean residual, the twiddle tables (window x exp(-i theta), built on the
@@ -23,6 +25,7 @@
 
 #include "../../include/tacaw.h"
 #include "tacaw_internal.cuh"
+#include "tacaw_plan.cuh"
 
 using namespace tacaw;
 
@@ -46,6 +49,9 @@ void emit_log(int level, const char *msg) {
     if (fn) fn(level, msg, user);
 }
 
+}  // namespace
+
+namespace tacaw {
 tacaw_status fail(tacaw_status st, const char *fmt, ...) {
     char buf[512];
     va_list ap;
@@ -57,177 +63,16 @@ tacaw_status fail(tacaw_status st, const char *fmt, ...) {
     return st;
 }
 
-int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
-
-}  // namespace
-
-namespace tacaw {
 void set_last_error(const char *msg) {
     g_last_error = msg ? msg : "";
     emit_log(TACAW_LOG_ERROR, g_last_error.c_str());
 }
 }  // namespace tacaw
 
-namespace {
 
-struct Stream {
-    tacaw_stream_desc d{};
-    std::vector<double> E;
-    std::vector<tacaw_detector> dets;
-    int64_t npix = 0, M = 0, M_pad = 0;
-    int T = 0, T_pad = 0, n_kb_T = 0;
-    int Nw = 0, wt = 0, n_wt = 0, Nw_pad = 0;
-    int ring = 0;                    // frames the staging ring holds: min(K_stage, T_pad)
-    bool needs_acc = false;
-    // device buffers
-    float2 *mu_hat = nullptr, *dmu = nullptr, *Wc = nullptr;
-    double2 *sum_res = nullptr;
-    double *cj = nullptr;
-    float *bose = nullptr, *win = nullptr;
-    __nv_bfloat16 *A_hi = nullptr, *A_lo = nullptr, *B_hi = nullptr, *B_lo = nullptr;
-    float2 *A32 = nullptr, *B32 = nullptr;
-    float2 *acc_s = nullptr, *acc_c = nullptr;
-    double2 *acc_d = nullptr;
-    int *det_idx = nullptr, *det_off = nullptr;
-    float *det_w = nullptr;
-    int D = 0, n_det_entries = 0;
-    std::vector<int> h_det_off;
-    // adjoint support: pixels inside any aperture and their per-detector weights
-    int *adj_pix = nullptr;
-    float *adj_w = nullptr;
-    int n_adj = 0;
-    // tensor-core adjoint tables, built by the stream's first tacaw_backward: forward twiddles in
-    // 32-frame blocks (energy tiles wt1), conj twiddles with frames as columns (frame tiles wt2)
-    __nv_bfloat16 *adjF_hi = nullptr, *adjF_lo = nullptr, *adjC_hi = nullptr, *adjC_lo = nullptr;
-    float2 *adj_ones = nullptr;
-    float *adj_ones_f = nullptr;
-    int64_t *adj_off = nullptr;      // element offset of each aperture pixel within a frame
-    std::vector<int> h_adj_pix;      // host copy of adj_pix
-    // pipelined segments (tacaw_set_pipelined_segments): the second staging area and per-row
-    // buffers, swapped with the first at each deferred finalize
-    __nv_bfloat16 *A_hi2 = nullptr, *A_lo2 = nullptr;
-    float2 *mu_hat2 = nullptr, *dmu2 = nullptr;
-    double2 *sum_res2 = nullptr;
-    int adj_wt1 = 0, adj_nwt1 = 0, adj_wt2 = 0, adj_nwt2 = 0;
-    int stages = 0;            // shared-memory pipeline stages of this stream's tiles
-    double *win_table = nullptr;   // table-driven windows (Dolph-Chebyshev)
-    // Welch lanes: internal stream `lane` of user stream `user` runs segments lane, lane +
-    // lanes, ... one after another; its last flush adds out_scale * I into the user's average
-    int user = 0, lane = 0;
-    int64_t seg = 0;           // current segment of this lane
-    float out_scale = 1.f;
-    int out_add = 0;
-    bool tuned = false;        // tile picked by the autotuner
-    // in-place frames: per staged frame, a pointer into the pushed buffer
-    // host record of the segment's pushes (first frame, address): a flush whose frames are
-    // evenly spaced reads them through one 2-D tensor map
-    std::vector<std::pair<int, const float2 *>> h_pushes;
-    const float2 **d_frame_ptr = nullptr;       // one slot per frame of the segment, written on
-                                                // the stream at push time (no host copy)
-    // segment state
-    int pushed = 0, staged = 0, stage_start = 0, flushes = 0;
-    // a full staging ring whose flush waits for the next push of this stream (or of finalize),
-    // so that the flushes of several streams that fill up together share one launch
-    bool due = false;
-    cudaStream_t due_stream = nullptr;
-    int64_t I_off = 0, S_off = 0;
-};
-
-}  // namespace
-
-// A stream as the caller sees it: one internal stream, or the lanes of a Welch average.
-struct UserStream {
-    int first = 0, lanes = 1;  // internal streams [first, first + lanes)
-    int N = 1, stride = 0, L = 0;
-    int64_t total = 0;         // frames of the whole push sequence: skip + (N - 1) * stride + L
-    int64_t skip = 0;          // leading frames dropped before the first segment
-    int64_t pushed = 0;
-    float *I_acc = nullptr;    // Welch: plan-owned running average of the segments' I
-    int64_t I_elems = 0;
-    int64_t I_off = 0, S_off = 0;
-};
-
-struct tacaw_plan_s {
-    std::vector<Stream> s;     // internal streams (Welch lanes expanded)
-    std::vector<UserStream> us;
-    int prec = 0, accum = 0, k_stage = 0;   // prec: TACAW_PREC_SPLIT_BF16 for both split paths
-    int prec_user = 0;         // the precision asked for (tacaw_plan_info)
-    int f16 = 0;               // split path with fp16 pieces of the scaled operands
-    float f16_scale = 1.f;     // split FP16: operand A is f16_scale * (psi - mu_hat), a power of two
-    int stages = 0;
-    int drain_kb = 0;          // split path: staging blocks per drained H chunk
-    int bf = 8;                // frames per staged operand row (split path)
-    bool in_place = false;     // the contraction reads pushed frames directly (in-place kernel)
-    int tc_max_ctas = 0;       // persistent contraction grids: at most this many CTAs (0: all SMs)
-    uint64_t wait_ns = 0;      // tensor-core pipeline waits give up after this (0: the kernels' default)
-    // with a capped grid the last flush runs on a highest-priority stream of the plan, forked
-    // from and joined back to the caller's stream, so that its CTAs take SMs ahead of other
-    // streams' queued work
-    cudaStream_t hp_stream = nullptr;
-    cudaEvent_t hp_in = nullptr, hp_out = nullptr;
-    // tacaw_backward's streams: the gradient's zero fill (HBM-bound) runs on aux_stream beside the
-    // tensor-core adjoint's contractions, which run on adj_stream at the greatest priority (freed
-    // SMs go to their CTAs ahead of the fill's blocks)
-    cudaStream_t aux_stream = nullptr, adj_stream = nullptr;
-    cudaEvent_t aux_in = nullptr, aux_out = nullptr, adj_out = nullptr;
-    int64_t bytes = 0;
-    int64_t I_elems = 0, S_elems = 0;
-    int64_t flushes_total = 0;
-    int64_t launches = 0;
-    int64_t flush_launches = 0;    // contraction launches (a grouped launch counts once)
-    bool poisoned = false;
-    bool finalized = false;
-    uint32_t *d_err = nullptr;
-    // tile counters of the staged kernel's launches: one per launch in a ring, so that launches of
-    // this plan on different CUDA streams (up to kCounterRing of them in flight) never share one
-    int *d_counters = nullptr;
-    int64_t counter_slot = 0;
-    // the adjoint's G matrix and row means: allocated by the first tacaw_backward that needs it
-    // (grown when a later stream needs more), kept until tacaw_destroy
-    float2 *adj_scratch = nullptr;
-    size_t adj_scratch_elems = 0;
-    // the tensor-core adjoint's staged operands and intermediates (same lifetime as adj_scratch)
-    void *adj_tc = nullptr;
-    size_t adj_tc_bytes = 0;
-    bool adj_fp32 = false;     // tacaw_set_adjoint_precision(TACAW_PREC_FP32): CUDA-core adjoint
-    // pipelined segments: a finalized segment's contraction is deferred and launched with the
-    // conversion of the next segment's pushes (done by extra warps of the same launch)
-    bool pipe = false;
-    bool deferred_pushes = false;  // this segment's pushes were recorded, not converted
-    struct Pending {
-        bool active = false;
-        Stream snap;                   // the deferred segment (its staging slot, sums, lists)
-        float *I = nullptr, *S = nullptr;
-        float2 *Psi = nullptr;
-    } pend;
-    std::vector<void *> allocs;
-    bool timing = false;
-    bool trace = false;                      // record per-CTA phase stamps of tensor-core flushes
-    unsigned long long *d_trace = nullptr;   // stamps of the last traced flush
-    int64_t trace_ctas = 0, trace_cap = 0;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
-    double timed_ms = 0.0;
-    int64_t timed_launches = 0;
-    int tuned_streams = 0, tune_timed = 0;
-    double tune_ms = 0.0;
-};
 
 namespace {
 
-template <typename T>
-bool dev_alloc(tacaw_plan_s *p, T **ptr, size_t count) {
-    *ptr = nullptr;
-    if (count == 0) count = 1;
-    void *q = nullptr;
-    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    p->allocs.push_back(q);
-    p->bytes += (int64_t)(count * sizeof(T));
-    *ptr = static_cast<T *>(q);
-    return true;
-}
 
 void free_all(tacaw_plan_s *p) {
     if (p->hp_stream) cudaStreamDestroy(p->hp_stream);
@@ -259,16 +104,17 @@ void free_all(tacaw_plan_s *p) {
     p->adj_tc_bytes = 0;
 }
 
+}  // namespace
+
+namespace tacaw {
 tacaw_status cuda_fail(tacaw_plan_s *p, cudaError_t e, const char *what) {
     if (p) p->poisoned = true;
     return fail(TACAW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
+}  // namespace tacaw
 
-#define CU_CHECK(plan, call, what)                                      \
-    do {                                                                \
-        cudaError_t e_ = (call);                                        \
-        if (e_ != cudaSuccess) return cuda_fail((plan), e_, (what));    \
-    } while (0)
+namespace {
+
 
 tacaw_status validate_stream(const tacaw_stream_desc &d, int i) {
     if (d.n_probes < 1 || d.kx < 1 || d.ky < 1) return fail(TACAW_ERR_INVALID_ARG, "stream %d: P, kx, ky must be >= 1", i);
@@ -666,6 +512,9 @@ std::vector<double> chebwin_periodic(int T, double at_db) {
 }
 
 // Table arguments of stream s after build_stream (device phase and window inputs in place).
+}  // namespace
+
+namespace tacaw {
 TableArgs stream_table_args(const Stream &s, int block_frames) {
     TableArgs ta{};
     ta.T = s.T;
@@ -681,6 +530,9 @@ TableArgs stream_table_args(const Stream &s, int block_frames) {
     ta.cj = s.cj;
     return ta;
 }
+}  // namespace tacaw
+
+namespace {
 
 tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
     const tacaw_stream_desc &d = s.d;
@@ -820,11 +672,17 @@ tacaw_status build_stream(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
     return TACAW_OK;
 }
 
+}  // namespace
+
+namespace tacaw {
 tacaw_status check_plan(tacaw_plan_s *p) {
     if (!p) return fail(TACAW_ERR_INVALID_ARG, "plan is NULL");
     if (p->poisoned) return fail(TACAW_ERR_STATE, "plan is poisoned by an earlier CUDA error or device timeout");
     return TACAW_OK;
 }
+}  // namespace tacaw
+
+namespace {
 
 // Buffers that kernels read or write: device or managed memory, or pinned host memory that the
 // device reaches at the same address (for pushes a zero-copy ingest over the host link, on
@@ -833,6 +691,9 @@ tacaw_status check_plan(tacaw_plan_s *p) {
 // know) is refused before any work is enqueued.  Skipped while `st` is capturing a graph (the
 // attribute query is not a stream operation; pointers of a captured segment are the caller's to
 // keep valid).
+}  // namespace
+
+namespace tacaw {
 tacaw_status check_kernel_memory(const void *ptr, const char *what, bool allow_host, cudaStream_t st) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
@@ -858,15 +719,9 @@ tacaw_status check_kernel_memory(const void *ptr, const char *what, bool allow_h
     return TACAW_OK;
 }
 
-}  // namespace
-
-namespace tacaw {
 int check_device_readable(const void *ptr, const char *what, cudaStream_t st) {
     return check_kernel_memory(ptr, what, true, st);
 }
-}  // namespace tacaw
-
-namespace {
 
 tacaw_status read_device_error(tacaw_plan_s *p, cudaStream_t st) {
     CU_CHECK(p, cudaStreamSynchronize(st), "cudaStreamSynchronize");
@@ -881,6 +736,9 @@ tacaw_status read_device_error(tacaw_plan_s *p, cudaStream_t st) {
     }
     return TACAW_OK;
 }
+}  // namespace tacaw
+
+namespace {
 
 // Detector spectra of stream s from its block of I.
 tacaw_status launch_spectra(tacaw_plan_s *p, const Stream &s, const float *I, float *S, cudaStream_t st) {
@@ -1814,597 +1672,6 @@ tacaw_status tacaw_kernel_time_ms(tacaw_plan_t p, double *flush_ms, int64_t *flu
         p->timed_ms = 0.0;
         p->timed_launches = 0;
     }
-    return TACAW_OK;
-}
-
-namespace {
-
-// Tables of the tensor-core adjoint for stream s, built on its first backward: the forward
-// twiddles in 32-frame blocks with least-padding energy tiles, and the conj twiddles with the
-// frames as output columns in least-padding frame tiles.
-// Output-column tile of an adjoint contraction over row_tiles row tiles: the multiple of 8 (at
-// most wt_max) with the least cost in rounds of the persistent grid (one tile per SM a round)
-// times columns plus a fixed per-tile cost, as in least_cost_tile.
-int adjoint_tile(int n_cols, int64_t row_tiles, int sms, int wt_max) {
-    int best = 8;
-    int64_t best_cost = INT64_MAX;
-    for (int wt = 8; wt <= wt_max; wt += 8) {
-        const int64_t tiles = row_tiles * ((n_cols + wt - 1) / wt);
-        const int64_t cost = (tiles + sms - 1) / sms * (wt + 24);
-        if (cost < best_cost || (cost == best_cost && wt > best)) {
-            best_cost = cost;
-            best = wt;
-        }
-    }
-    return best;
-}
-
-tacaw_status adjoint_tc_tables(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
-    if (s.adjF_hi) return TACAW_OK;
-    const int wt_max = kDrainMaxOmegaTile;
-    int dev = 0, sms = 0;
-    CU_CHECK(p, cudaGetDevice(&dev), "cudaGetDevice");
-    CU_CHECK(p, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-    const int64_t row_tiles = round_up((int64_t)s.d.n_probes * s.n_adj, kMTile) / kMTile;
-    s.adj_wt1 = adjoint_tile(s.Nw, row_tiles, std::max(1, sms), wt_max);
-    s.adj_nwt1 = (s.Nw + s.adj_wt1 - 1) / s.adj_wt1;
-    s.adj_wt2 = adjoint_tile(s.T, row_tiles, std::max(1, sms), wt_max);
-    s.adj_nwt2 = (s.T + s.adj_wt2 - 1) / s.adj_wt2;
-    const int T_pad = (int)round_up(s.T, 32), E_pad = (int)round_up(s.Nw, 32);
-    const int Nw_rows = s.adj_wt1 * s.adj_nwt1, T_rows = s.adj_wt2 * s.adj_nwt2;
-    const size_t nf = (size_t)(T_pad / 32) * 2 * Nw_rows * 64, nc = (size_t)(E_pad / 32) * 2 * T_rows * 64;
-    __nv_bfloat16 *fh, *fl, *ch, *cl;
-    float2 *ones;
-    float *ones_f;
-    int64_t *off;
-    if (!dev_alloc(p, &fh, nf) || !dev_alloc(p, &fl, nf) || !dev_alloc(p, &ch, nc) || !dev_alloc(p, &cl, nc) ||
-        !dev_alloc(p, &ones, (size_t)T_rows) || !dev_alloc(p, &ones_f, (size_t)T_rows) ||
-        !dev_alloc(p, &off, (size_t)s.n_adj))
-        return fail(TACAW_ERR_OOM, "cudaMalloc(adjoint tables)");
-    {
-        const std::vector<int> &pix = s.h_adj_pix;
-        std::vector<int64_t> o((size_t)s.n_adj);
-        for (int i = 0; i < s.n_adj; ++i)
-            o[i] = (int64_t)(s.d.roi_y0 + pix[i] / s.d.kx) * s.d.pitch_row + (s.d.roi_x0 + pix[i] % s.d.kx);
-        CU_CHECK(p, cudaMemcpy(off, o.data(), sizeof(int64_t) * s.n_adj, cudaMemcpyHostToDevice), "copy offsets");
-    }
-    TableArgs ta = stream_table_args(s, 32);
-    ta.T_pad = T_pad;
-    ta.Nw_pad = Nw_rows;
-    CU_CHECK(p, launch_twiddles_split(ta, fh, fl, 0, st), "adjoint twiddles");
-    CU_CHECK(p, launch_twiddles_adjoint_split(ta, T_rows, E_pad, ch, cl, st), "adjoint conj twiddles");
-    std::vector<float2> h1((size_t)T_rows, make_float2(1.f, 0.f));
-    std::vector<float> h2((size_t)T_rows, 1.f);
-    CU_CHECK(p, cudaMemcpy(ones, h1.data(), sizeof(float2) * T_rows, cudaMemcpyHostToDevice), "copy ones");
-    CU_CHECK(p, cudaMemcpy(ones_f, h2.data(), sizeof(float) * T_rows, cudaMemcpyHostToDevice), "copy ones");
-    s.adjF_hi = fh;
-    s.adjF_lo = fl;
-    s.adjC_hi = ch;
-    s.adjC_lo = cl;
-    s.adj_ones = ones;
-    s.adj_ones_f = ones_f;
-    s.adj_off = off;
-    return TACAW_OK;
-}
-
-// Carves the tensor-core adjoint's buffers for stream s out of the plan's scratch (grown, never
-// shrunk, kept until tacaw_destroy).  q.a must be filled.
-tacaw_status adjoint_tc_scratch(tacaw_plan_s *p, const Stream &s, AdjTcArgs &q) {
-    const int64_t M = (int64_t)s.d.n_probes * s.n_adj;
-    q.M_pad = round_up(M, kMTile);
-    q.T_pad = (int)round_up(s.T, 32);
-    q.E_pad = (int)round_up(s.Nw, 32);
-    const size_t a_piece = (size_t)q.T_pad * q.M_pad * 4, g_piece = (size_t)q.E_pad * q.M_pad * 4;
-    const size_t sizes[10] = {a_piece, a_piece, g_piece, g_piece,
-                              (size_t)(std::max(q.T_pad, q.E_pad) / 32) * M * sizeof(float2),
-                              (size_t)M * sizeof(float2), (size_t)M * sizeof(float2),
-                              (size_t)M * s.Nw * sizeof(float2), (size_t)M * s.T * sizeof(float2), 2 * sizeof(int)};
-    size_t off[10], total = 0;
-    for (int i = 0; i < 10; ++i) {
-        off[i] = total;
-        total += (sizes[i] + 255) & ~(size_t)255;
-    }
-    if (total > p->adj_tc_bytes) {
-        // the previous backward ended with a synchronize, so the old buffer is idle
-        if (p->adj_tc) {
-            cudaFree(p->adj_tc);
-            p->bytes -= (int64_t)p->adj_tc_bytes;
-        }
-        p->adj_tc = nullptr;
-        p->adj_tc_bytes = 0;
-        void *b = nullptr;
-        if (cudaMalloc(&b, total) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(TACAW_ERR_OOM, "tensor-core adjoint scratch of %zu bytes", total);
-        }
-        p->adj_tc = b;
-        p->adj_tc_bytes = total;
-        p->bytes += (int64_t)total;
-    }
-    uint8_t *b = static_cast<uint8_t *>(p->adj_tc);
-    q.A_hi = reinterpret_cast<__nv_bfloat16 *>(b + off[0]);
-    q.A_lo = reinterpret_cast<__nv_bfloat16 *>(b + off[1]);
-    q.G_hi = reinterpret_cast<__nv_bfloat16 *>(b + off[2]);
-    q.G_lo = reinterpret_cast<__nv_bfloat16 *>(b + off[3]);
-    q.part = reinterpret_cast<float2 *>(b + off[4]);
-    q.dmu = reinterpret_cast<float2 *>(b + off[5]);
-    q.kmean = reinterpret_cast<float2 *>(b + off[6]);
-    q.psi = reinterpret_cast<float2 *>(b + off[7]);
-    q.cg = reinterpret_cast<float2 *>(b + off[8]);
-    q.counters = reinterpret_cast<int *>(b + off[9]);
-    q.Bf_hi = s.adjF_hi;
-    q.Bf_lo = s.adjF_lo;
-    q.wt1 = s.adj_wt1;
-    q.n_wt1 = s.adj_nwt1;
-    q.Bc_hi = s.adjC_hi;
-    q.Bc_lo = s.adjC_lo;
-    q.wt2 = s.adj_wt2;
-    q.n_wt2 = s.adj_nwt2;
-    q.ones = s.adj_ones;
-    q.ones_f = s.adj_ones_f;
-    q.pix_off = s.adj_off;
-    q.err = p->d_err;
-    q.wait_ns = p->wait_ns;
-    return TACAW_OK;
-}
-
-}  // namespace
-
-tacaw_status tacaw_set_adjoint_precision(tacaw_plan_t p, int precision) {
-    tacaw_status c = check_plan(p);
-    if (c != TACAW_OK) return c;
-    if (precision == TACAW_PREC_SPLIT_BF16)
-        p->adj_fp32 = false;
-    else if (precision == TACAW_PREC_FP32)
-        p->adj_fp32 = true;
-    else
-        return fail(TACAW_ERR_INVALID_ARG, "adjoint precision %d: TACAW_PREC_SPLIT_BF16 or TACAW_PREC_FP32", precision);
-    return TACAW_OK;
-}
-
-tacaw_status tacaw_backward(tacaw_plan_t p, int sid, const float *d_dL_dS, const void *d_frames, void *d_grad,
-                            void *stream) {
-    tacaw_status c = check_plan(p);
-    if (c != TACAW_OK) return c;
-    if (sid < 0 || sid >= (int)p->us.size()) return fail(TACAW_ERR_INVALID_ARG, "stream_id %d out of range", sid);
-    if (!d_dL_dS || !d_frames || !d_grad) return fail(TACAW_ERR_INVALID_ARG, "NULL device pointer");
-    {
-        cudaStream_t cs = static_cast<cudaStream_t>(stream);
-        tacaw_status k = check_kernel_memory(d_frames, "d_frames", true, cs);
-        if (k == TACAW_OK) k = check_kernel_memory(d_grad, "d_grad", true, cs);
-        if (k == TACAW_OK) k = check_kernel_memory(d_dL_dS, "d_dL_dS", true, cs);
-        if (k != TACAW_OK) return k;
-    }
-    const UserStream &u = p->us[sid];
-    Stream &s = p->s[u.first];
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    AdjointArgs a{};
-    a.frames = static_cast<const float2 *>(d_frames);
-    a.pitch_row = s.d.pitch_row;
-    a.pitch_frame = s.d.pitch_frame;
-    a.pitch_probe = s.d.pitch_probe;
-    a.roi_x0 = s.d.roi_x0;
-    a.roi_y0 = s.d.roi_y0;
-    a.kx = s.d.kx;
-    a.ky = s.d.ky;
-    a.P = s.d.n_probes;
-    a.T = s.T;
-    a.Nw = s.Nw;
-    a.D = s.D;
-    a.subtract_mean = s.d.subtract_mean;
-    a.w = s.win;
-    a.B32 = s.B32;
-    a.Nw_pad = s.Nw_pad;
-    a.Wc = s.Wc;
-    a.bose = s.bose;
-    a.dLdS = d_dL_dS;
-    a.mpix = s.adj_pix;
-    a.mwts = s.adj_w;
-    a.n_mpix = s.n_adj;
-    a.grad = static_cast<float2 *>(d_grad);
-    a.scale = 1.f;
-    a.accumulate = 0;
-    // the whole push sequence's gradient: skipped frames and frames of no segment get zero
-    AdjointArgs z = a;
-    z.T = (int)u.total;
-    const bool tc = s.n_adj > 0 && s.D > 0 && !p->adj_fp32;
-    if (!tc) {
-        CU_CHECK(p, launch_zero_roi(z, st), "zero gradient");
-        p->launches++;
-    }
-    if (tc) {
-        // tensor cores, split BF16: one segment, or each Welch segment at its start frame with
-        // weight 1/N, its gradient added where segments overlap
-        tacaw_status r = adjoint_tc_tables(p, s, st);
-        if (r != TACAW_OK) return r;
-        AdjTcArgs q{};
-        q.a = a;
-        r = adjoint_tc_scratch(p, s, q);
-        if (r != TACAW_OK) return r;
-        // the zero fill runs on a side stream beside the contractions (it needs the SMs' memory
-        // pipes, they the tensor cores), the contractions on a stream of the greatest priority;
-        // the first scatter into the gradient waits for the fill, the caller's stream for both
-        if (!p->aux_stream) {
-            int lo = 0, hi = 0;
-            CU_CHECK(p, cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
-            CU_CHECK(p, cudaStreamCreateWithPriority(&p->aux_stream, cudaStreamNonBlocking, lo), "adjoint fill stream");
-            CU_CHECK(p, cudaStreamCreateWithPriority(&p->adj_stream, cudaStreamNonBlocking, hi), "adjoint stream");
-            CU_CHECK(p, cudaEventCreateWithFlags(&p->aux_in, cudaEventDisableTiming), "cudaEventCreate");
-            CU_CHECK(p, cudaEventCreateWithFlags(&p->aux_out, cudaEventDisableTiming), "cudaEventCreate");
-            CU_CHECK(p, cudaEventCreateWithFlags(&p->adj_out, cudaEventDisableTiming), "cudaEventCreate");
-        }
-        CU_CHECK(p, cudaEventRecord(p->aux_in, st), "cudaEventRecord");
-        CU_CHECK(p, cudaStreamWaitEvent(p->aux_stream, p->aux_in, 0), "cudaStreamWaitEvent");
-        CU_CHECK(p, cudaStreamWaitEvent(p->adj_stream, p->aux_in, 0), "cudaStreamWaitEvent");
-        CU_CHECK(p, launch_zero_roi(z, p->aux_stream), "zero gradient");
-        CU_CHECK(p, cudaEventRecord(p->aux_out, p->aux_stream), "cudaEventRecord");
-        p->launches++;
-        q.before_scatter = p->aux_out;
-        cudaStream_t cst = p->adj_stream;
-        const int nseg = u.N > 1 ? u.N : 1;
-        cudaError_t e = cudaSuccess;
-        for (int n = 0; n < nseg && e == cudaSuccess; ++n) {
-            const int64_t f0 = u.skip + (int64_t)n * u.stride;
-            AdjTcArgs qn = q;
-            qn.a.frames = a.frames + f0 * s.d.pitch_frame;
-            qn.a.grad = a.grad + f0 * s.d.pitch_frame;
-            qn.a.scale = 1.f / (float)nseg;
-            qn.a.accumulate = nseg > 1 ? 1 : 0;
-            e = launch_adjoint_tc(qn, cst);
-            p->launches += adjtc_launches();
-        }
-        if (e != cudaSuccess) return cuda_fail(p, e, "tensor-core adjoint");
-        CU_CHECK(p, cudaEventRecord(p->adj_out, cst), "cudaEventRecord");
-        CU_CHECK(p, cudaStreamWaitEvent(st, p->adj_out, 0), "cudaStreamWaitEvent");
-    } else if (s.n_adj > 0 && s.D > 0) {
-        const size_t n_scr = (size_t)s.d.n_probes * s.n_adj * (s.Nw + 2);
-        if (n_scr > p->adj_scratch_elems) {
-            // the previous call ended with a synchronize, so the old buffer is idle
-            if (p->adj_scratch) {
-                cudaFree(p->adj_scratch);
-                p->bytes -= (int64_t)(p->adj_scratch_elems * sizeof(float2));
-            }
-            p->adj_scratch = nullptr;
-            p->adj_scratch_elems = 0;
-            void *q = nullptr;
-            if (cudaMalloc(&q, n_scr * sizeof(float2)) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(TACAW_ERR_OOM, "adjoint scratch of %zu bytes", n_scr * sizeof(float2));
-            }
-            p->adj_scratch = static_cast<float2 *>(q);
-            p->adj_scratch_elems = n_scr;
-            p->bytes += (int64_t)(n_scr * sizeof(float2));
-        }
-        a.scratch = p->adj_scratch;
-        // one segment, or each Welch segment at its start frame with weight 1/N, its gradient
-        // added where segments overlap (one segment stores over the zeros, no read-back)
-        const int nseg = u.N > 1 ? u.N : 1;
-        cudaError_t e = cudaSuccess;
-        for (int n = 0; n < nseg && e == cudaSuccess; ++n) {
-            const int64_t f0 = u.skip + (int64_t)n * u.stride;
-            AdjointArgs an = a;
-            an.frames = a.frames + f0 * s.d.pitch_frame;
-            an.grad = a.grad + f0 * s.d.pitch_frame;
-            an.scale = 1.f / (float)nseg;
-            an.accumulate = nseg > 1 ? 1 : 0;
-            e = launch_adjoint(an, st);
-            p->launches += 2;
-        }
-        if (e != cudaSuccess) return cuda_fail(p, e, "adjoint");
-    }
-    return read_device_error(p, st);
-}
-
-}  // extern "C"
-
-namespace {
-
-// Checkpoints (tacaw_save_state).  The accumulation of a segment is a sum over its pushed
-// frames, so between two pushes a plan's progress is a handful of buffers: the provisional
-// means and FP64 residual sums, the staged frames not yet contracted, the running Psi
-// accumulators once a flush has written them, and the Welch averages.  A checkpoint is a fixed
-// header, the host counters of every stream, then those device sections in a fixed order;
-// everything else a plan holds (tables, detector lists) follows from its descriptor, which the
-// fingerprint ties to the checkpoint.
-constexpr uint64_t kStateMagic = 0x314B435741434154ULL;   // the bytes "TACAWCK1"
-constexpr uint32_t kStateVersion = 1;
-
-struct StateHeader {
-    uint64_t magic;
-    uint32_t version;
-    uint32_t n_streams;       // internal streams (Welch lanes counted one each)
-    uint32_t n_user;
-    uint32_t reserved;
-    uint64_t fingerprint;     // plan_fingerprint of the saving plan
-    int64_t total_bytes;      // the whole checkpoint
-    uint64_t counters_hash;   // FNV-1a of the counter records that follow the header
-};
-struct StreamCounters {
-    int64_t pushed, staged, stage_start, flushes, seg;
-    int32_t due, reserved;
-};
-struct UserCounters {
-    int64_t pushed;
-};
-static_assert(sizeof(StateHeader) == 48 && sizeof(StreamCounters) == 48 && sizeof(UserCounters) == 8,
-              "checkpoint records are packed");
-
-// 64-bit FNV-1a (Fowler, Noll and Vo): offset basis 0xcbf29ce484222325, prime 0x100000001b3.
-struct Fnv {
-    uint64_t h = 0xcbf29ce484222325ULL;
-    void add(const void *ptr, size_t n) {
-        const unsigned char *b = static_cast<const unsigned char *>(ptr);
-        for (size_t i = 0; i < n; ++i) {
-            h ^= b[i];
-            h *= 0x100000001b3ULL;
-        }
-    }
-    template <class V>
-    void val(const V &v) { add(&v, sizeof v); }
-};
-
-// What the saved buffers' contents and layout depend on: precision, accumulators, staging
-// geometry, the frames' ROI and the arithmetic of the tables (energies, window, time step,
-// mean subtraction), and the Welch segmentation.  Tuning that does not change a saved layout
-// (energy tiles, pipeline depth, CTA caps) is left out.
-uint64_t plan_fingerprint(const tacaw_plan_s *p) {
-    Fnv f;
-    f.val(p->prec);
-    f.val(p->prec_user);
-    f.val(p->f16);
-    f.val(p->f16_scale);
-    f.val(p->accum);
-    f.val(p->k_stage);
-    f.val(p->bf);
-    f.val((int)p->in_place);
-    f.val((int)p->s.size());
-    f.val((int)p->us.size());
-    for (const Stream &s : p->s) {
-        f.val(s.npix);
-        f.val(s.M);
-        f.val(s.M_pad);
-        f.val(s.T);
-        f.val(s.T_pad);
-        f.val(s.Nw);
-        f.val(s.ring);
-        f.val((int)s.needs_acc);
-        f.val(s.user);
-        f.val(s.lane);
-        f.val(s.d.n_probes);
-        f.val(s.d.kx);
-        f.val(s.d.ky);
-        f.val(s.d.roi_x0);
-        f.val(s.d.roi_y0);
-        f.val(s.d.dt_fs);
-        f.val(s.d.fft_bins);
-        f.val(s.d.window);
-        f.val(s.d.window_param);
-        f.val(s.d.subtract_mean);
-        f.val(s.d.bose_T_K);
-        f.add(s.E.data(), sizeof(double) * s.E.size());
-    }
-    for (const UserStream &u : p->us) {
-        f.val(u.first);
-        f.val(u.lanes);
-        f.val(u.N);
-        f.val(u.stride);
-        f.val(u.L);
-        f.val(u.total);
-        f.val(u.skip);
-    }
-    return f.h;
-}
-
-struct StateSection {
-    void *dev;
-    size_t bytes;
-};
-
-// Device sections of a checkpoint whose streams have the counters c, in checkpoint order.
-std::vector<StateSection> state_sections(const tacaw_plan_s *p, const std::vector<StreamCounters> &c) {
-    std::vector<StateSection> v;
-    for (size_t i = 0; i < p->s.size(); ++i) {
-        const Stream &s = p->s[i];
-        v.push_back({s.mu_hat, sizeof(float2) * (size_t)s.M});
-        v.push_back({s.sum_res, sizeof(double2) * (size_t)s.M});
-        if (c[i].staged > 0) {
-            // staged frames fill ring slots [0, staged): whole blocks of bf frames (split) or
-            // frame-major rows of M_pad (FP32)
-            if (p->prec == TACAW_PREC_SPLIT_BF16) {
-                const size_t n = (size_t)((c[i].staged + p->bf - 1) / p->bf) * (size_t)s.M_pad * 2 * p->bf *
-                                 sizeof(__nv_bfloat16);
-                v.push_back({s.A_hi, n});
-                v.push_back({s.A_lo, n});
-            } else {
-                v.push_back({s.A32, sizeof(float2) * (size_t)c[i].staged * (size_t)s.M_pad});
-            }
-        }
-        if (s.needs_acc && c[i].flushes > 0) {
-            const size_t n = (size_t)s.Nw * (size_t)s.M_pad;   // energies j < Nw, rows of M_pad
-            if (s.acc_d) v.push_back({s.acc_d, sizeof(double2) * n});
-            if (s.acc_s) v.push_back({s.acc_s, sizeof(float2) * n});
-            if (s.acc_c) v.push_back({s.acc_c, sizeof(float2) * n});
-        }
-    }
-    for (const UserStream &u : p->us)
-        if (u.I_acc) v.push_back({u.I_acc, sizeof(float) * (size_t)u.I_elems});
-    return v;
-}
-
-std::vector<StreamCounters> plan_counters(const tacaw_plan_s *p) {
-    std::vector<StreamCounters> c(p->s.size());
-    for (size_t i = 0; i < p->s.size(); ++i) {
-        const Stream &s = p->s[i];
-        c[i] = StreamCounters{s.pushed, s.staged, s.stage_start, s.flushes, s.seg, s.due ? 1 : 0, 0};
-    }
-    return c;
-}
-
-int64_t state_total(const tacaw_plan_s *p, const std::vector<StreamCounters> &c) {
-    int64_t b = (int64_t)sizeof(StateHeader) + (int64_t)(sizeof(StreamCounters) * p->s.size()) +
-                (int64_t)(sizeof(UserCounters) * p->us.size());
-    for (const StateSection &x : state_sections(p, c)) b += (int64_t)x.bytes;
-    return b;
-}
-
-tacaw_status check_saveable(const tacaw_plan_s *p) {
-    if (p->finalized) return fail(TACAW_ERR_STATE, "segment finalized: nothing to resume (tacaw_reset starts the next)");
-    if (p->pend.active || p->deferred_pushes)
-        return fail(TACAW_ERR_STATE, "a segment's contraction is deferred: call tacaw_drain first");
-    if (p->in_place)
-        for (size_t i = 0; i < p->s.size(); ++i)
-            if (p->s[i].staged > 0)
-                return fail(TACAW_ERR_STATE,
-                            "in-place stream %zu holds %d pushed frames not yet contracted (their addresses only): "
-                            "checkpoint when the pushes fill whole K_stage rings",
-                            i, p->s[i].staged);
-    return TACAW_OK;
-}
-
-tacaw_status check_host_buffer(const void *buf, const char *what) {
-    if (!buf) return fail(TACAW_ERR_INVALID_ARG, "%s is NULL", what);
-    cudaPointerAttributes at{};
-    const cudaError_t e = cudaPointerGetAttributes(&at, buf);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return TACAW_OK;   // unknown to CUDA: pageable host memory
-    }
-    if (at.type == cudaMemoryTypeDevice) return fail(TACAW_ERR_INVALID_ARG, "%s must be host memory", what);
-    return TACAW_OK;
-}
-
-// Counters read from a checkpoint that this plan's pushes could have produced.
-tacaw_status check_counters(const tacaw_plan_s *p, const std::vector<StreamCounters> &c,
-                            const std::vector<UserCounters> &uc) {
-    for (size_t i = 0; i < p->s.size(); ++i) {
-        const Stream &s = p->s[i];
-        const StreamCounters &k = c[i];
-        const UserStream &u = p->us[s.user];
-        const bool ok = k.pushed >= 0 && k.pushed <= s.T && k.staged >= 0 && k.staged <= s.ring &&
-                        k.stage_start >= 0 && k.stage_start + k.staged == k.pushed && k.flushes >= 0 &&
-                        k.flushes <= k.stage_start && (s.needs_acc || k.flushes == 0) &&
-                        (!p->in_place || k.staged == 0) && (k.due == 0 || (k.due == 1 && k.staged == s.ring)) &&
-                        k.seg >= s.lane && (k.seg - s.lane) % u.lanes == 0 && k.seg < s.lane + (int64_t)u.lanes * (u.N + 1);
-        if (!ok) return fail(TACAW_ERR_INVALID_ARG, "checkpoint: counters of stream %zu are inconsistent", i);
-    }
-    for (size_t i = 0; i < p->us.size(); ++i)
-        if (uc[i].pushed < 0 || uc[i].pushed > p->us[i].total)
-            return fail(TACAW_ERR_INVALID_ARG, "checkpoint: frame count of stream %zu is out of range", i);
-    return TACAW_OK;
-}
-
-}  // namespace
-
-extern "C" {
-
-tacaw_status tacaw_state_size(tacaw_plan_t p, int64_t *bytes) {
-    tacaw_status c = check_plan(p);
-    if (c != TACAW_OK) return c;
-    if (!bytes) return fail(TACAW_ERR_INVALID_ARG, "bytes is NULL");
-    c = check_saveable(p);
-    if (c != TACAW_OK) return c;
-    *bytes = state_total(p, plan_counters(p));
-    return TACAW_OK;
-}
-
-tacaw_status tacaw_save_state(tacaw_plan_t p, void *h_state, int64_t bytes, void *stream) {
-    tacaw_status c = check_plan(p);
-    if (c != TACAW_OK) return c;
-    c = check_host_buffer(h_state, "h_state");
-    if (c != TACAW_OK) return c;
-    c = check_saveable(p);
-    if (c != TACAW_OK) return c;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const std::vector<StreamCounters> cnt = plan_counters(p);
-    std::vector<UserCounters> uc(p->us.size());
-    for (size_t i = 0; i < p->us.size(); ++i) uc[i].pushed = p->us[i].pushed;
-    const int64_t total = state_total(p, cnt);
-    if (bytes < total)
-        return fail(TACAW_ERR_INVALID_ARG, "h_state holds %lld bytes, the checkpoint needs %lld", (long long)bytes,
-                    (long long)total);
-    unsigned char *o = static_cast<unsigned char *>(h_state);
-    StateHeader h{};
-    h.magic = kStateMagic;
-    h.version = kStateVersion;
-    h.n_streams = (uint32_t)p->s.size();
-    h.n_user = (uint32_t)p->us.size();
-    h.fingerprint = plan_fingerprint(p);
-    h.total_bytes = total;
-    Fnv f;
-    f.add(cnt.data(), sizeof(StreamCounters) * cnt.size());
-    f.add(uc.data(), sizeof(UserCounters) * uc.size());
-    h.counters_hash = f.h;
-    size_t off = 0;
-    std::memcpy(o, &h, sizeof h);
-    off += sizeof h;
-    std::memcpy(o + off, cnt.data(), sizeof(StreamCounters) * cnt.size());
-    off += sizeof(StreamCounters) * cnt.size();
-    std::memcpy(o + off, uc.data(), sizeof(UserCounters) * uc.size());
-    off += sizeof(UserCounters) * uc.size();
-    for (const StateSection &x : state_sections(p, cnt)) {
-        CU_CHECK(p, cudaMemcpyAsync(o + off, x.dev, x.bytes, cudaMemcpyDeviceToHost, st), "checkpoint copy");
-        off += x.bytes;
-    }
-    CU_CHECK(p, cudaStreamSynchronize(st), "checkpoint copies");
-    return read_device_error(p, st);
-}
-
-tacaw_status tacaw_restore_state(tacaw_plan_t p, const void *h_state, int64_t bytes, void *stream) {
-    tacaw_status c = check_plan(p);
-    if (c != TACAW_OK) return c;
-    c = check_host_buffer(h_state, "h_state");
-    if (c != TACAW_OK) return c;
-    if (p->pend.active || p->deferred_pushes)
-        return fail(TACAW_ERR_STATE, "a segment's contraction is deferred: call tacaw_drain first");
-    const unsigned char *in = static_cast<const unsigned char *>(h_state);
-    StateHeader h{};
-    if (bytes < (int64_t)sizeof h) return fail(TACAW_ERR_INVALID_ARG, "checkpoint: %lld bytes is too short", (long long)bytes);
-    std::memcpy(&h, in, sizeof h);
-    if (h.magic != kStateMagic) return fail(TACAW_ERR_INVALID_ARG, "checkpoint: not a plan checkpoint");
-    if (h.version != kStateVersion)
-        return fail(TACAW_ERR_INVALID_ARG, "checkpoint: version %u, this library reads %u", h.version, kStateVersion);
-    if (h.n_streams != p->s.size() || h.n_user != p->us.size() || h.fingerprint != plan_fingerprint(p))
-        return fail(TACAW_ERR_INVALID_ARG, "checkpoint: saved by a plan of another configuration");
-    if (h.total_bytes > bytes)
-        return fail(TACAW_ERR_INVALID_ARG, "checkpoint: truncated (%lld of %lld bytes)", (long long)bytes,
-                    (long long)h.total_bytes);
-    const size_t hdr = sizeof h + sizeof(StreamCounters) * p->s.size() + sizeof(UserCounters) * p->us.size();
-    if ((int64_t)hdr > h.total_bytes) return fail(TACAW_ERR_INVALID_ARG, "checkpoint: truncated counters");
-    std::vector<StreamCounters> cnt(p->s.size());
-    std::vector<UserCounters> uc(p->us.size());
-    size_t off = sizeof h;
-    std::memcpy(cnt.data(), in + off, sizeof(StreamCounters) * cnt.size());
-    off += sizeof(StreamCounters) * cnt.size();
-    std::memcpy(uc.data(), in + off, sizeof(UserCounters) * uc.size());
-    off += sizeof(UserCounters) * uc.size();
-    Fnv f;
-    f.add(cnt.data(), sizeof(StreamCounters) * cnt.size());
-    f.add(uc.data(), sizeof(UserCounters) * uc.size());
-    if (f.h != h.counters_hash) return fail(TACAW_ERR_INVALID_ARG, "checkpoint: counter records corrupted");
-    c = check_counters(p, cnt, uc);
-    if (c != TACAW_OK) return c;
-    if (state_total(p, cnt) != h.total_bytes)
-        return fail(TACAW_ERR_INVALID_ARG, "checkpoint: section sizes do not match its counters");
-    // the checkpoint is this plan's: load the device sections, then the counters
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    for (const StateSection &x : state_sections(p, cnt)) {
-        CU_CHECK(p, cudaMemcpyAsync(x.dev, in + off, x.bytes, cudaMemcpyHostToDevice, st), "checkpoint copy");
-        off += x.bytes;
-    }
-    CU_CHECK(p, cudaStreamSynchronize(st), "checkpoint copies");
-    for (size_t i = 0; i < p->s.size(); ++i) {
-        Stream &s = p->s[i];
-        s.pushed = (int)cnt[i].pushed;
-        s.staged = (int)cnt[i].staged;
-        s.stage_start = (int)cnt[i].stage_start;
-        s.flushes = (int)cnt[i].flushes;
-        s.seg = cnt[i].seg;
-        s.due = cnt[i].due != 0;
-        s.due_stream = st;
-        s.h_pushes.clear();
-    }
-    for (size_t i = 0; i < p->us.size(); ++i) p->us[i].pushed = uc[i].pushed;
-    p->finalized = false;
     return TACAW_OK;
 }
 
