@@ -340,8 +340,8 @@ def group_rounds(plan, specs, bufs, r0, r1):
 
 @pytest.mark.parametrize("cut", [2, 3], ids=["all-rings-due", "mid-ring"])
 def test_resume_grouped_partitions(cut):
-    """Three partitions fed by tacaw_push_frames_group: after round 2 every ring is full and its
-    flush deferred to the next grouped launch; after round 3 the rings are half full.  A plan
+    """Three partitions fed by tacaw_push_frames_group: after two push rounds every ring is full
+    and its flush deferred to the next grouped launch; after three the rings are half full.  A plan
     that loads the checkpoint and takes the remaining rounds matches the uninterrupted plan bit
     for bit, and the oracle for each partition."""
     import torch
