@@ -3,20 +3,20 @@
 // the windowed time->energy transform of Eq. 1 for the frames of one flush.  This is the
 // plain-precision path (and the baseline the tensor-core path is measured against).
 //
-// Tile: 128 rows x SN = 4*TY complex energies per block of 16 x TY threads; each thread owns
-// 8 rows x 4 energies (rows tx + 16 i, energies ty + TY q).  TY = 16 (64 energies) or 8 (32
-// energies), whichever pads the energy count less (200 or 400 energies: 32).  Slices of 8
-// frames of both operands are copied global -> shared with cp.async (16-byte pieces, no
-// registers) into a 4-deep ring, so three slices are in flight while one is multiplied; one
-// barrier per slice.
+// Tile: 128 rows x SN = Q*TY complex energies per block of 16 x TY threads; each thread owns
+// 8 rows x Q energies (rows tx + 16 i, energies ty + TY q).  Shapes: TY = 16, Q = 4 (64
+// energies, 8 warps); TY = 8, Q = 4 (32 energies) or Q = 5 (40 energies, 4 warps): whichever
+// pads the energy count least (200 or 400 energies: 40, no padding).  Slices of 8 frames of
+// both operands are copied global -> shared with cp.async (16-byte pieces, no registers) into
+// a 4-deep ring, so three slices are in flight while one is multiplied; one barrier per slice.
 #include "tacaw_internal.cuh"
 
 namespace tacaw {
 
 constexpr int SB_M = 128, SB_K = 8, SB_STAGES = 4;
 
-template <int TY>
-constexpr size_t simt_smem_bytes() { return (size_t)SB_STAGES * SB_K * (SB_M + 4 * TY) * sizeof(float2); }
+template <int TY, int Q>
+constexpr size_t simt_smem_bytes() { return (size_t)SB_STAGES * SB_K * (SB_M + Q * TY) * sizeof(float2); }
 
 __device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, bool valid) {
     // src-size 0 writes 16 zero bytes and reads nothing
@@ -27,12 +27,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int TY>
+template <int TY, int Q>
 __global__ void __launch_bounds__(16 * TY) flush_simt_kernel(SimtArgs a, int n_jt) {
-    constexpr int NT = 16 * TY, SN = 4 * TY;
+    constexpr int NT = 16 * TY, SN = Q * TY;
     constexpr int A_CHUNKS = SB_K * SB_M / 2;    // 16-byte pieces of one A slice
-    constexpr int B_CHUNKS = SB_K * SN / 2;      // ... of one B slice (= NT: one per thread)
-    static_assert(B_CHUNKS == NT, "one B piece per thread");
+    constexpr int B_CHUNKS = SB_K * SN / 2;      // ... of one B slice
+    static_assert(SN % 2 == 0, "whole 16-byte pieces of B");
     extern __shared__ __align__(16) unsigned char simt_smem[];
     float2 (*As)[SB_K][SB_M] = reinterpret_cast<float2 (*)[SB_K][SB_M]>(simt_smem);
     float2 (*Bs)[SB_K][SN] =
@@ -56,19 +56,19 @@ __global__ void __launch_bounds__(16 * TY) flush_simt_kernel(SimtArgs a, int n_j
             const float2 *src = ok ? a.A32 + (size_t)(k0 + kk) * M_pad + m0 + 2 * ch : a.A32;
             cp_async16_zfill((uint32_t)__cvta_generic_to_shared(&As[slot][kk][2 * ch]), src, ok);
         }
-        {
-            const int kk = tid / (SN / 2), ch = tid % (SN / 2), col = j0 + 2 * ch;
+        for (int c = tid; c < B_CHUNKS; c += NT) {
+            const int kk = c / (SN / 2), ch = c % (SN / 2), col = j0 + 2 * ch;
             const bool ok = k0 + kk < a.n_frames && col < a.Nw_pad;
             const float2 *src = ok ? a.B32 + (size_t)(a.t0 + k0 + kk) * a.Nw_pad + col : a.B32;
             cp_async16_zfill((uint32_t)__cvta_generic_to_shared(&Bs[slot][kk][2 * ch]), src, ok);
         }
     };
 
-    float ar[8][4], ai[8][4];
+    float ar[8][Q], ai[8][Q];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) ar[i][q] = ai[i][q] = 0.f;
+        for (int q = 0; q < Q; ++q) ar[i][q] = ai[i][q] = 0.f;
 
 #pragma unroll
     for (int s = 0; s < SB_STAGES - 1; ++s) {
@@ -83,15 +83,15 @@ __global__ void __launch_bounds__(16 * TY) flush_simt_kernel(SimtArgs a, int n_j
         const int slot = s % SB_STAGES;
 #pragma unroll
         for (int kk = 0; kk < SB_K; ++kk) {
-            float2 x[8], b[4];
+            float2 x[8], b[Q];
 #pragma unroll
             for (int i = 0; i < 8; ++i) x[i] = As[slot][kk][tx + 16 * i];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) b[q] = Bs[slot][kk][ty + TY * q];
+            for (int q = 0; q < Q; ++q) b[q] = Bs[slot][kk][ty + TY * q];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < Q; ++q) {
                     ar[i][q] = fmaf(x[i].x, b[q].x, ar[i][q]);
                     ar[i][q] = fmaf(-x[i].y, b[q].y, ar[i][q]);
                     ai[i][q] = fmaf(x[i].x, b[q].y, ai[i][q]);
@@ -106,37 +106,43 @@ __global__ void __launch_bounds__(16 * TY) flush_simt_kernel(SimtArgs a, int n_j
         RowCtx row = make_row(a.e, m);
         if (!row.valid) continue;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < Q; ++q) {
             const int j = j0 + ty + TY * q;
             if (j < a.e.Nw) epi_element(a.e, row, j, ar[i][q], ai[i][q]);
         }
     }
 }
 
-// energies per block tile: 64 (8 warps) unless 32 (4 warps) pads the energies less.  Blocks of 4
-// or 8 warps keep the SM's four schedulers evenly loaded; measured on 200 and 400 energies, the
-// 40-wide tile (5 warps, no padding) is slower than either
-static int simt_tile_ty(int Nw) {
-    const int64_t cols64 = (int64_t)(Nw + 63) / 64 * 64, cols32 = (int64_t)(Nw + 31) / 32 * 32;
-    return cols64 <= cols32 ? 16 : 8;
+// energies per block tile: 64 (8 warps), 32 or 40 (4 warps), whichever pads the energy count
+// least (ties: 64, then 32).  Blocks of 4 or 8 warps keep the SM's four schedulers evenly
+// loaded (a 5-warp 40-wide tile measured slower than either on 200 and 400 energies).
+static int simt_tile_cols(int Nw) {
+    const int64_t c64 = (int64_t)(Nw + 63) / 64 * 64, c32 = (int64_t)(Nw + 31) / 32 * 32,
+                  c40 = (int64_t)(Nw + 39) / 40 * 40;
+    if (c64 <= c32 && c64 <= c40) return 64;
+    return c32 <= c40 ? 32 : 40;
 }
 
-template <int TY>
-cudaError_t launch_simt_ty(const SimtArgs &a, cudaStream_t st) {
+template <int TY, int Q>
+cudaError_t launch_simt_shape(const SimtArgs &a, cudaStream_t st) {
     static const cudaError_t attr = cudaFuncSetAttribute(
-        flush_simt_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)simt_smem_bytes<TY>());
+        flush_simt_kernel<TY, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)simt_smem_bytes<TY, Q>());
     if (attr != cudaSuccess) return attr;
-    const int n_jt = (a.e.Nw + 4 * TY - 1) / (4 * TY);
+    const int n_jt = (a.e.Nw + Q * TY - 1) / (Q * TY);
     const int64_t n_mt = a.e.M_pad / SB_M;
     const int64_t blocks = n_mt * n_jt;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    flush_simt_kernel<TY><<<(unsigned)blocks, 16 * TY, simt_smem_bytes<TY>(), st>>>(a, n_jt);
+    flush_simt_kernel<TY, Q><<<(unsigned)blocks, 16 * TY, simt_smem_bytes<TY, Q>(), st>>>(a, n_jt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_flush_simt(const SimtArgs &a, cudaStream_t st) {
     if (a.e.M_pad % SB_M != 0 || a.Nw_pad % 2 != 0) return cudaErrorInvalidValue;
-    return simt_tile_ty(a.e.Nw) == 8 ? launch_simt_ty<8>(a, st) : launch_simt_ty<16>(a, st);
+    switch (simt_tile_cols(a.e.Nw)) {
+        case 64: return launch_simt_shape<16, 4>(a, st);
+        case 40: return launch_simt_shape<8, 5>(a, st);
+        default: return launch_simt_shape<8, 4>(a, st);
+    }
 }
 
 }  // namespace tacaw
