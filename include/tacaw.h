@@ -232,7 +232,8 @@ tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out);
  * frame; here they are folded into the segment's transform as they arrive (streaming form
  * of the chunk FFT of Eq. 1's phi_MD).
  * Pushes n_frames frames of stream stream_id (layout: tacaw_stream_desc).  The library
- * reads them, removes the provisional mean (the mean of the first push of the segment),
+ * reads them, removes the provisional mean (the mean of the first frames, at most 32, of the
+ * segment's first push),
  * splits/converts them into its staging area and, when K_stage frames are staged and the
  * segment is not complete, runs a flush (the contraction of the staged frames into Psi).
  * d_frames may be reused once the work enqueued on `stream` has completed.

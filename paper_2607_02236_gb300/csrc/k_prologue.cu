@@ -20,7 +20,7 @@ __device__ __forceinline__ const float2 *row_src(const FrameGeom &g, int64_t m) 
     return g.base + p * g.pitch_probe + (g.roi_y0 + y) * g.pitch_row + (g.roi_x0 + x);
 }
 
-// Provisional mean of each row over the n frames of the first push.  Block = 32 rows x 8
+// Provisional mean of each row over the first n frames of the first push (launch_mean caps n).  Block = 32 rows x 8
 // frame lanes: lane f sums frames f, f + 8, ... of its row (a warp reads 32 consecutive
 // pixels of one frame), the eight partial sums are added in a fixed order.  Any rounding of
 // mu_hat is harmless: the exact mean correction uses the FP64 residual sums of the pushes.
@@ -341,8 +341,12 @@ cudaError_t launch_frame_table(const float2 **table, const float2 *base, int64_t
     return cudaGetLastError();
 }
 
+// The provisional mean of a segment is taken over the first (at most kMeanFrames) frames of its
+// first push: any value is exact after the finalize correction Psi -= (mu - mu_hat) W(E), and a
+// few frames already put mu_hat on the elastic part, which is what keeps the residuals small.
+constexpr int kMeanFrames = 32;
 cudaError_t launch_mean(const FrameGeom &g, int n, float2 *mu_hat, cudaStream_t st) {
-    mean_kernel<<<blocks_for(g.M, 32), 256, 0, st>>>(g, n, mu_hat);
+    mean_kernel<<<blocks_for(g.M, 32), 256, 0, st>>>(g, n < kMeanFrames ? n : kMeanFrames, mu_hat);
     return cudaGetLastError();
 }
 
