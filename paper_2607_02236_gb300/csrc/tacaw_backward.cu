@@ -19,9 +19,6 @@ extern "C" {
 
 namespace {
 
-// Tables of the tensor-core adjoint for stream s, built on its first backward: the forward
-// twiddles in 32-frame blocks with least-padding energy tiles, and the conj twiddles with the
-// frames as output columns in least-padding frame tiles.
 // Output-column tile of an adjoint contraction over row_tiles row tiles: the multiple of 8 (at
 // most wt_max) with the least cost in rounds of the persistent grid (one tile per SM a round)
 // times columns plus a fixed per-tile cost, as in least_cost_tile.
@@ -39,6 +36,9 @@ int adjoint_tile(int n_cols, int64_t row_tiles, int sms, int wt_max) {
     return best;
 }
 
+// Tables of the tensor-core adjoint for stream s, built on its first backward: the forward
+// twiddles in 32-frame blocks with least-padding energy tiles, and the conj twiddles with the
+// frames as output columns in least-padding frame tiles.
 tacaw_status adjoint_tc_tables(tacaw_plan_s *p, Stream &s, cudaStream_t st) {
     if (s.adjF_hi) return TACAW_OK;
     const int wt_max = kDrainMaxOmegaTile;

@@ -163,7 +163,8 @@ int64_t state_total(const tacaw_plan_s *p, const std::vector<StreamCounters> &c)
 }
 
 tacaw_status check_saveable(const tacaw_plan_s *p) {
-    if (p->finalized) return fail(TACAW_ERR_STATE, "segment finalized: nothing to resume (tacaw_reset starts the next)");
+    if (p->finalized)
+        return fail(TACAW_ERR_STATE, "segment finalized: nothing to resume (tacaw_reset starts the next)");
     if (p->pend.active || p->deferred_pushes)
         return fail(TACAW_ERR_STATE, "a segment's contraction is deferred: call tacaw_drain first");
     if (p->in_place)
@@ -199,7 +200,8 @@ tacaw_status check_counters(const tacaw_plan_s *p, const std::vector<StreamCount
                         k.stage_start >= 0 && k.stage_start + k.staged == k.pushed && k.flushes >= 0 &&
                         k.flushes <= k.stage_start && (s.needs_acc || k.flushes == 0) &&
                         (!p->in_place || k.staged == 0) && (k.due == 0 || (k.due == 1 && k.staged == s.ring)) &&
-                        k.seg >= s.lane && (k.seg - s.lane) % u.lanes == 0 && k.seg < s.lane + (int64_t)u.lanes * (u.N + 1);
+                        k.seg >= s.lane && (k.seg - s.lane) % u.lanes == 0 &&
+                        k.seg < s.lane + (int64_t)u.lanes * (u.N + 1);
         if (!ok) return fail(TACAW_ERR_INVALID_ARG, "checkpoint: counters of stream %zu are inconsistent", i);
     }
     for (size_t i = 0; i < p->us.size(); ++i)
@@ -273,7 +275,8 @@ tacaw_status tacaw_restore_state(tacaw_plan_t p, const void *h_state, int64_t by
         return fail(TACAW_ERR_STATE, "a segment's contraction is deferred: call tacaw_drain first");
     const unsigned char *in = static_cast<const unsigned char *>(h_state);
     StateHeader h{};
-    if (bytes < (int64_t)sizeof h) return fail(TACAW_ERR_INVALID_ARG, "checkpoint: %lld bytes is too short", (long long)bytes);
+    if (bytes < (int64_t)sizeof h)
+        return fail(TACAW_ERR_INVALID_ARG, "checkpoint: %lld bytes is too short", (long long)bytes);
     std::memcpy(&h, in, sizeof h);
     if (h.magic != kStateMagic) return fail(TACAW_ERR_INVALID_ARG, "checkpoint: not a plan checkpoint");
     if (h.version != kStateVersion)
