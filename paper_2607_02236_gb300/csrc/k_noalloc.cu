@@ -14,6 +14,7 @@
 // by the caller.  Nothing in it is accumulated, so nothing needs clearing between calls.
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdio>
@@ -216,6 +217,11 @@ tacaw_status spectra(const float *d_I, int n_probes, int n_omega, int kx, int ky
 extern "C" tacaw_status tacaw_detector_spectra_noalloc(const float *d_I, int n_probes, int n_omega, int kx, int ky,
                                                        const tacaw_detector *detectors, int n_detectors,
                                                        float *d_S, void *stream) {
+    // a named range on the profiler timeline (NVTX), as around every entry point of the library
+    struct Range {
+        Range() { nvtxRangePushA("tacaw_detector_spectra_noalloc"); }
+        ~Range() { nvtxRangePop(); }
+    } trace_range;
     try {
         return spectra(d_I, n_probes, n_omega, kx, ky, detectors, n_detectors, d_S, static_cast<cudaStream_t>(stream));
     } catch (const std::bad_alloc &) {

@@ -322,6 +322,9 @@ const float2 *inplace_first_frame(const Stream &s, int a, int n) {
 tacaw_status run_flush(tacaw_plan_s *p, Stream &s, int mode, float *I_out, float2 *Psi_out, cudaStream_t st) {
     const int n = s.staged;
     if (n <= 0) return TACAW_OK;
+    TraceRange trace_range(p->prec != TACAW_PREC_SPLIT_BF16 ? "contraction (FP32)"
+                                                            : (p->in_place ? "contraction (tensor cores, in place)"
+                                                                           : "contraction (tensor cores)"));
     if (mode != FLUSH_FINAL && !s.needs_acc) return fail(TACAW_ERR_STATE, "internal: accumulator missing");
     const EpiArgs e = epi_args(p, s, mode, I_out, Psi_out);
     cudaEvent_t e0, e1;
@@ -406,6 +409,7 @@ tacaw_status flush_grouped(tacaw_plan_s *p, std::vector<FlushReq> req, cudaStrea
     };
     std::stable_sort(req.begin(), req.end(), [&](const FlushReq &a, const FlushReq &b) { return work(a) > work(b); });
     for (size_t g0 = 0; g0 < req.size(); g0 += kMaxGroupStreams) {
+        TraceRange trace_range("contraction (tensor cores, grouped)");
         const size_t g1 = std::min(req.size(), g0 + (size_t)kMaxGroupStreams);
         std::vector<TcPlanArgs> args;
         int64_t nc = 0;
@@ -762,6 +766,7 @@ tacaw_status launch_spectra(tacaw_plan_s *p, const Stream &s, const float *I, fl
 // correction, I, Psi, then its spectra); with conv, the same launch's extra warps convert the
 // recorded pushes of stream `conv` (the next segment) into its staging area.
 tacaw_status launch_pending(tacaw_plan_s *p, const Stream *conv, cudaStream_t st) {
+    TraceRange trace_range(conv ? "contraction (tensor cores) with the next conversion" : "contraction (tensor cores)");
     tacaw_plan_s::Pending &q = p->pend;
     Stream &ps = q.snap;
     CU_CHECK(p, launch_mean_residual(ps.M, ps.T, ps.d.subtract_mean, ps.sum_res, ps.dmu, p->f16_scale, st),
@@ -1018,6 +1023,7 @@ tacaw_status tacaw_set_log_callback(tacaw_log_fn fn, void *user) {
 const char *tacaw_version(void) { return "tacaw-gb300 0.1 (sm_103a)"; }
 
 tacaw_status tacaw_plan_create(const tacaw_plan_desc *desc, tacaw_plan_t *out) {
+    TraceRange trace_range("tacaw_plan_create");
     g_last_error.clear();
     if (!desc || !out) return fail(TACAW_ERR_INVALID_ARG, "desc and out must not be NULL");
     *out = nullptr;
@@ -1416,6 +1422,7 @@ tacaw_status push_user(tacaw_plan_s *p, int sid, const float2 *base, int n_frame
 extern "C" {
 
 tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, int n_frames, void *stream) {
+    TraceRange trace_range("tacaw_push_frames");
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1426,6 +1433,7 @@ tacaw_status tacaw_push_frames(tacaw_plan_t p, int sid, const void *d_frames, in
 
 tacaw_status tacaw_push_frames_group(tacaw_plan_t p, int n, const int *stream_ids, const void *const *d_frames,
                                      const int *n_frames, void *stream) {
+    TraceRange trace_range("tacaw_push_frames_group");
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
     if (n < 1 || !stream_ids || !d_frames || !n_frames)
@@ -1511,6 +1519,7 @@ tacaw_status tacaw_push_frames_group(tacaw_plan_t p, int n, const int *stream_id
 }
 
 tacaw_status tacaw_finalize(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, void *stream) {
+    TraceRange trace_range("tacaw_finalize");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     tacaw_status r = finalize_impl(p, d_I, d_S, d_Psi, st);
     if (r != TACAW_OK) return r;
@@ -1522,6 +1531,7 @@ tacaw_status tacaw_finalize(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi,
 }
 
 tacaw_status tacaw_drain(tacaw_plan_t p, void *stream) {
+    TraceRange trace_range("tacaw_drain");
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
     if (p->deferred_pushes)
@@ -1565,10 +1575,12 @@ tacaw_status tacaw_set_pipelined_segments(tacaw_plan_t p, int enable) {
 }
 
 tacaw_status tacaw_finalize_async(tacaw_plan_t p, float *d_I, float *d_S, void *d_Psi, void *stream) {
+    TraceRange trace_range("tacaw_finalize_async");
     return finalize_impl(p, d_I, d_S, d_Psi, static_cast<cudaStream_t>(stream));
 }
 
 tacaw_status tacaw_check_errors(tacaw_plan_t p, void *stream) {
+    TraceRange trace_range("tacaw_check_errors");
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
     return read_device_error(p, static_cast<cudaStream_t>(stream));
@@ -1583,6 +1595,7 @@ tacaw_status tacaw_output_offsets(tacaw_plan_t p, int sid, int64_t *I_offset, in
 }
 
 tacaw_status tacaw_reset(tacaw_plan_t p, void *stream) {
+    TraceRange trace_range("tacaw_reset");
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1676,6 +1689,7 @@ tacaw_status tacaw_kernel_time_ms(tacaw_plan_t p, double *flush_ms, int64_t *flu
 }
 
 tacaw_status tacaw_destroy(tacaw_plan_t p) {
+    TraceRange trace_range("tacaw_destroy");
     if (!p) return TACAW_OK;
     free_all(p);
     delete p;

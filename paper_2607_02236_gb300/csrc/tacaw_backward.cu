@@ -164,6 +164,7 @@ tacaw_status tacaw_set_adjoint_precision(tacaw_plan_t p, int precision) {
 
 tacaw_status tacaw_backward(tacaw_plan_t p, int sid, const float *d_dL_dS, const void *d_frames, void *d_grad,
                             void *stream) {
+    TraceRange trace_range("tacaw_backward");
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
     if (sid < 0 || sid >= (int)p->us.size()) return fail(TACAW_ERR_INVALID_ARG, "stream_id %d out of range", sid);

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 #include <utility>
@@ -171,6 +172,15 @@ tacaw_status check_kernel_memory(const void *ptr, const char *what, bool allow_h
 tacaw_status read_device_error(tacaw_plan_s *p, cudaStream_t st);
 // Table arguments of stream s after its tables were built.
 TableArgs stream_table_args(const Stream &s, int block_frames);
+
+// A named range on the profiler timeline (NVTX: costs a test of a null function pointer unless
+// a tool such as Nsight Systems is attached), from construction to the end of the scope.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // Device allocation of `count` elements owned by the plan (freed by tacaw_destroy).
 template <typename T>

@@ -225,6 +225,7 @@ tacaw_status tacaw_state_size(tacaw_plan_t p, int64_t *bytes) {
 }
 
 tacaw_status tacaw_save_state(tacaw_plan_t p, void *h_state, int64_t bytes, void *stream) {
+    TraceRange trace_range("tacaw_save_state");
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
     c = check_host_buffer(h_state, "h_state");
@@ -267,6 +268,7 @@ tacaw_status tacaw_save_state(tacaw_plan_t p, void *h_state, int64_t bytes, void
 }
 
 tacaw_status tacaw_restore_state(tacaw_plan_t p, const void *h_state, int64_t bytes, void *stream) {
+    TraceRange trace_range("tacaw_restore_state");
     tacaw_status c = check_plan(p);
     if (c != TACAW_OK) return c;
     c = check_host_buffer(h_state, "h_state");
